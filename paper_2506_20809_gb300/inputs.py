@@ -1,0 +1,307 @@
+"""Seeded synthetic workloads for the spheroidal boundary-integral apply.
+
+This module only *draws inputs*: spheroid shapes, placements, orientations and
+spheroidal-harmonic coefficient vectors.  It contains none of the method's
+arithmetic (no Legendre functions, no layer-potential multipliers, no
+quadrature, no near/far classification), so both the CPU oracle and the CUDA
+path can consume its output without sharing any computation.
+
+Spheroid descriptor (one row per particle), following the problem statement of
+Sec. 5.1 (shape type, semi-axes, centre, unit quaternion):
+
+    kind   0 = prolate (C > A), 1 = oblate (C < A)
+    A      equatorial semi-axis (radius of the circular cross-section), Sec. 2.1
+    C      polar semi-axis (along the local x3 axis), Sec. 2.1
+    center (3,) global position of the centre
+    quat   (4,) unit quaternion (w, x, y, z); x_global = center + R(quat) x_local
+
+Coefficient vectors use the real orthonormal surface-harmonic basis indexed by
+``n*n + n + m`` for 0 <= n <= p, -n <= m <= n (m > 0 cosine, m < 0 sine).
+
+The placement code below needs a spheroid-spheroid separation test.  It uses
+its own sampled point-to-ellipse distance (bisection on the Lagrange
+parameter); it decides only whether a drawn configuration is admissible and is
+never used to compute an operator value.
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+
+import numpy as np
+
+PROLATE = 0
+OBLATE = 1
+
+
+@dataclasses.dataclass
+class Suspension:
+    """A set of M spheroids plus the discretisation order used with it."""
+
+    kind: np.ndarray      # (M,) int32
+    A: np.ndarray         # (M,) float64
+    C: np.ndarray         # (M,) float64
+    center: np.ndarray    # (M, 3) float64
+    quat: np.ndarray      # (M, 4) float64, unit, (w, x, y, z)
+    p: int
+    name: str = ""
+
+    @property
+    def M(self) -> int:
+        return int(self.kind.shape[0])
+
+    def subset(self, idx) -> "Suspension":
+        idx = np.asarray(idx)
+        return Suspension(self.kind[idx].copy(), self.A[idx].copy(), self.C[idx].copy(),
+                          self.center[idx].copy(), self.quat[idx].copy(), self.p, self.name)
+
+
+# ----------------------------------------------------------------------------
+# random primitives
+# ----------------------------------------------------------------------------
+
+def random_quaternions(rng: np.random.Generator, M: int) -> np.ndarray:
+    """Uniform random rotations: normalised 4-D Gaussian vectors."""
+    q = rng.standard_normal((M, 4))
+    q /= np.linalg.norm(q, axis=1, keepdims=True)
+    return q
+
+
+def coefficients(rng: np.random.Generator, M: int, p: int, ndens: int = 1) -> np.ndarray:
+    """i.i.d. N(0,1)/(n+1)^2 coefficients, shape (M, ndens, (p+1)^2) squeezed
+    to (M, (p+1)^2) when ndens == 1."""
+    nc = (p + 1) ** 2
+    n_of = np.floor(np.sqrt(np.arange(nc))).astype(np.int64)
+    scale = 1.0 / (n_of + 1.0) ** 2
+    c = rng.standard_normal((M, ndens, nc)) * scale
+    return c[:, 0, :] if ndens == 1 else c
+
+
+def _quat_to_matrix(q: np.ndarray) -> np.ndarray:
+    w, x, y, z = q[..., 0], q[..., 1], q[..., 2], q[..., 3]
+    R = np.empty(q.shape[:-1] + (3, 3))
+    R[..., 0, 0] = 1 - 2 * (y * y + z * z)
+    R[..., 0, 1] = 2 * (x * y - w * z)
+    R[..., 0, 2] = 2 * (x * z + w * y)
+    R[..., 1, 0] = 2 * (x * y + w * z)
+    R[..., 1, 1] = 1 - 2 * (x * x + z * z)
+    R[..., 1, 2] = 2 * (y * z - w * x)
+    R[..., 2, 0] = 2 * (x * z - w * y)
+    R[..., 2, 1] = 2 * (y * z + w * x)
+    R[..., 2, 2] = 1 - 2 * (x * x + y * y)
+    return R
+
+
+# ----------------------------------------------------------------------------
+# separation test used only to accept / reject a drawn placement
+# ----------------------------------------------------------------------------
+
+def _ellipse_gap(r, z, A, C):
+    """Signed distance from meridian-plane points (r >= 0, z >= 0) to the
+    ellipse r^2/A^2 + z^2/C^2 = 1; negative inside.  Bisection on the
+    Lagrange parameter t of the closest-point condition (exterior points)."""
+    r = np.asarray(r, dtype=np.float64)
+    z = np.asarray(z, dtype=np.float64)
+    inside = (r / A) ** 2 + (z / C) ** 2 < 1.0
+    # exterior: closest point x = (A^2 r/(t+A^2), C^2 z/(t+C^2)), t >= 0 root of F
+    lo = np.zeros_like(r)
+    hi = np.maximum(A, C) * np.hypot(r, z) + 1e-300
+    for _ in range(64):
+        mid = 0.5 * (lo + hi)
+        F = (A * r / (mid + A * A)) ** 2 + (C * z / (mid + C * C)) ** 2 - 1.0
+        pos = F > 0
+        lo = np.where(pos, mid, lo)
+        hi = np.where(pos, hi, mid)
+    t = 0.5 * (lo + hi)
+    xr = A * A * r / (t + A * A)
+    xz = C * C * z / (t + C * C)
+    d = np.hypot(r - xr, z - xz)
+    return np.where(inside, -1.0, d)
+
+
+def _surface_points(A, C, theta, phi):
+    st = np.sin(theta)
+    return np.stack([A * st * np.cos(phi), A * st * np.sin(phi), C * np.cos(theta)], axis=-1)
+
+
+def _gap_one_way(Ai, Ci, ci, Ri, Aj, Cj, cj, Rj):
+    """min over sampled points of spheroid i of the signed distance to spheroid j,
+    with three rounds of local refinement around the best sample."""
+    def dist_of(theta, phi):
+        x = _surface_points(Ai, Ci, theta, phi) @ Ri.T + ci      # global
+        xl = (x - cj) @ Rj                                         # j-local
+        rr = np.hypot(xl[..., 0], xl[..., 1])
+        return _ellipse_gap(rr, np.abs(xl[..., 2]), Aj, Cj)
+
+    th = np.linspace(0.0, np.pi, 13)
+    ph = np.linspace(0.0, 2 * np.pi, 24, endpoint=False)
+    TH, PH = np.meshgrid(th, ph, indexing="ij")
+    d = dist_of(TH, PH)
+    k = np.unravel_index(np.argmin(d), d.shape)
+    best, bt, bp = d[k], TH[k], PH[k]
+    h_t, h_p = np.pi / 12, 2 * np.pi / 24
+    for _ in range(6):
+        lt = bt + h_t * np.linspace(-1, 1, 7)
+        lp = bp + h_p * np.linspace(-1, 1, 7)
+        TT, PP = np.meshgrid(np.clip(lt, 0, np.pi), lp, indexing="ij")
+        dd = dist_of(TT, PP)
+        kk = np.unravel_index(np.argmin(dd), dd.shape)
+        if dd[kk] < best:
+            best, bt, bp = dd[kk], TT[kk], PP[kk]
+        h_t /= 3.0
+        h_p /= 3.0
+    return float(np.min(d)) if np.min(d) < 0 else float(best)
+
+
+def separation(s: Suspension, i: int, j: int, R=None) -> float:
+    """Estimated surface gap between spheroids i and j (<= 0 means overlap)."""
+    if R is None:
+        R = _quat_to_matrix(s.quat)
+    g1 = _gap_one_way(s.A[i], s.C[i], s.center[i], R[i], s.A[j], s.C[j], s.center[j], R[j])
+    if g1 < 0:
+        return g1
+    g2 = _gap_one_way(s.A[j], s.C[j], s.center[j], R[j], s.A[i], s.C[i], s.center[i], R[i])
+    return min(g1, g2)
+
+
+def _admissible(kind, A, C, center, R, new, placed, min_gap):
+    """True if spheroid `new` keeps a gap >= min_gap to every index in `placed`."""
+    if len(placed) == 0:
+        return True
+    placed = np.asarray(placed)
+    d = np.linalg.norm(center[placed] - center[new], axis=1)
+    rmax = np.maximum(A, C)
+    rmin = np.minimum(A, C)
+    if np.any(d - rmin[placed] - rmin[new] < min_gap):
+        return False
+    amb = placed[d - rmax[placed] - rmax[new] < min_gap]
+    for j in amb:
+        g1 = _gap_one_way(A[new], C[new], center[new], R[new], A[j], C[j], center[j], R[j])
+        if g1 < min_gap:
+            return False
+        g2 = _gap_one_way(A[j], C[j], center[j], R[j], A[new], C[new], center[new], R[new])
+        if g2 < min_gap:
+            return False
+    return True
+
+
+# ----------------------------------------------------------------------------
+# workload recipes
+# ----------------------------------------------------------------------------
+
+def lattice_suspension(seed: int = 0, p: int = 8, spacing: float = 5.0,
+                       jitter: float = 0.5, min_gap: float = 0.2) -> Suspension:
+    """Eight spheroids on a jittered 2x2x2 lattice: prolates (A=1, C=2) and
+    oblates (A=1.5, C=0.75) alternating by lattice parity, random orientations.
+    The lattice shape follows the 2x2 prolate lattice test of Sec. 5.2."""
+    rng = np.random.default_rng(seed)
+    idx = np.array([(i, j, k) for i in range(2) for j in range(2) for k in range(2)], dtype=np.float64)
+    kind = (idx.sum(axis=1).astype(np.int64) % 2).astype(np.int32)   # 0 prolate, 1 oblate
+    A = np.where(kind == PROLATE, 1.0, 1.5)
+    C = np.where(kind == PROLATE, 2.0, 0.75)
+    for _ in range(1000):
+        center = idx * spacing + rng.uniform(-jitter, jitter, size=(8, 3))
+        quat = random_quaternions(rng, 8)
+        R = _quat_to_matrix(quat)
+        ok = all(_admissible(kind, A, C, center, R, n, list(range(n)), min_gap) for n in range(1, 8))
+        if ok:
+            return Suspension(kind, A, C, center, quat, p, "lattice8")
+    raise RuntimeError("could not place lattice suspension")
+
+
+def random_shapes(rng: np.random.Generator, M: int, ar_range=(1.2, 5.0), major_range=(0.5, 1.5)):
+    """Polydisperse spheroid shapes: aspect ratio U[ar], major semi-axis
+    U[major], prolate or oblate with probability 1/2."""
+    ar = rng.uniform(*ar_range, size=M)
+    major = rng.uniform(*major_range, size=M)
+    kind = (rng.uniform(size=M) < 0.5).astype(np.int32)     # 1 = oblate
+    A = np.where(kind == PROLATE, major / ar, major)
+    C = np.where(kind == PROLATE, major, major / ar)
+    return kind, A, C
+
+
+def rsa_suspension(M: int, phi_vol: float, seed: int, p: int, ar_range=(1.2, 5.0),
+                   major_range=(0.5, 1.5), min_gap: float = 0.05, name: str = "rsa",
+                   max_attempts: int = 200000) -> Suspension:
+    """Random sequential addition in a cube of side L = (sum V / phi_vol)^(1/3):
+    centres U[0, L]^3, uniform random orientation, rejected while the gap to
+    any placed particle is below `min_gap`."""
+    rng = np.random.default_rng(seed)
+    kind, A, C = random_shapes(rng, M, ar_range, major_range)
+    vol = 4.0 / 3.0 * np.pi * A * A * C
+    L = (vol.sum() / phi_vol) ** (1.0 / 3.0)
+    center = np.zeros((M, 3))
+    quat = np.zeros((M, 4))
+    R = np.zeros((M, 3, 3))
+    attempts = 0
+    for n in range(M):
+        while True:
+            attempts += 1
+            if attempts > max_attempts:
+                raise RuntimeError(f"RSA failed to place {M} particles at phi={phi_vol}")
+            center[n] = rng.uniform(0.0, L, size=3)
+            quat[n] = random_quaternions(rng, 1)[0]
+            R[n] = _quat_to_matrix(quat[n])
+            if _admissible(kind, A, C, center, R, n, list(range(n)), min_gap):
+                break
+    return Suspension(kind, A, C, center, quat, p, name)
+
+
+def config_suspension(cfg: int, seed: int = 0) -> Suspension:
+    """Suspensions of the three single-geometry workloads:
+      1: 8-spheroid jittered lattice, p = 8
+      2: 200 polydisperse spheroids, AR U[1.2,5], major U[0.5,1.5], 20 %, gap 0.05, p = 16
+      3: 100 spheroids, AR U[1.5,4], major U[0.5,1.5], 15 %, gap 0.05, p = 12 (Stokes)
+    """
+    if cfg == 1:
+        return lattice_suspension(seed, p=8)
+    if cfg == 2:
+        return rsa_suspension(200, 0.20, seed, p=16, ar_range=(1.2, 5.0), name="poly200")
+    if cfg == 3:
+        return rsa_suspension(100, 0.15, seed, p=12, ar_range=(1.5, 4.0), name="stokes100")
+    raise ValueError(cfg)
+
+
+def config_coefficients(s: Suspension, seed: int = 0, ndens: int = 2) -> np.ndarray:
+    """Coefficient sets for a suspension: (ndens, M, (p+1)^2); for the Laplace
+    workloads density 0 is the single-layer input (modified basis) and density
+    1 the double-layer input; for Stokes the three Cartesian components."""
+    rng = np.random.default_rng([seed, 7919])
+    c = coefficients(rng, s.M, s.p, ndens)
+    if ndens == 1:
+        return c[None]
+    return np.ascontiguousarray(np.transpose(c, (1, 0, 2)))
+
+
+def batch_suspensions(n: int = 64, base_seed: int = 0, p_choices=(8, 12, 16, 20),
+                      M_range=(10, 400), phi_range=(0.05, 0.25)):
+    """Independent suspensions for the batched workload: suspension s uses
+    seed base_seed + s; M log-uniform in M_range, p uniform over p_choices,
+    volume fraction U[phi_range], shapes as the 200-particle workload."""
+    out = []
+    for s in range(n):
+        rng = np.random.default_rng([base_seed + s, 104729])
+        M = int(round(math.exp(rng.uniform(math.log(M_range[0]), math.log(M_range[1])))))
+        p = int(rng.choice(p_choices))
+        phi = float(rng.uniform(*phi_range))
+        out.append(rsa_suspension(M, phi, base_seed + s, p, name=f"batch{s}"))
+    return out
+
+
+def poisson_requests(rate: float, duration: float, seed: int = 0, M_range=(20, 500),
+                     p_choices=(8, 12, 16), max_requests=None):
+    """Arrival stream for the served workload: Poisson arrivals at `rate`/s for
+    `duration` s; each request has M log-uniform in M_range, p from p_choices
+    and is a Laplace S+D or a Stokes single-layer request with probability 1/2."""
+    rng = np.random.default_rng([seed, 15485863])
+    t = 0.0
+    reqs = []
+    while True:
+        t += rng.exponential(1.0 / rate)
+        if t > duration or (max_requests is not None and len(reqs) >= max_requests):
+            break
+        M = int(round(math.exp(rng.uniform(math.log(M_range[0]), math.log(M_range[1])))))
+        p = int(rng.choice(p_choices))
+        op = "laplace" if rng.uniform() < 0.5 else "stokes"
+        reqs.append({"t": t, "M": M, "p": p, "op": op, "seed": int(rng.integers(1 << 30))})
+    return reqs
