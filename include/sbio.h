@@ -1,0 +1,202 @@
+/*
+ * sbio.h -- C ABI of the GB300 spheroidal boundary-integral-operator library.
+ *
+ * The library applies the Laplace single-layer (S) and double-layer (D)
+ * operators, and the Stokes single layer through the Laplace-to-Stokes
+ * identity, to densities given as spheroidal-harmonic coefficients on a
+ * suspension of prolate and oblate spheroids, at every surface quadrature node
+ * ("Boundary integral equation analysis for spheroidal suspensions", Sec. 4,
+ * eq. (potall) and Algorithm 1; Stokes: Sec. 4.3, eq. (stokes)).
+ *
+ * Conventions shared by every entry point
+ *   - Return value: SBIO_OK (0) or a negative SBIO_E* code.  The message of the
+ *     last failure on the calling thread is available from sbio_last_error().
+ *   - Device pointers are plain CUDA device addresses of the context's device;
+ *     host pointers are ordinary process memory.  The caller owns every buffer
+ *     it passes; the library owns everything behind the opaque handles.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream).  Apply calls are stream-ordered and asynchronous unless their
+ *     description says otherwise; buffers must stay valid until the stream
+ *     reaches the call.
+ *   - Node order: particle-major, then Gauss-Legendre node j in v (ascending),
+ *     then trapezoid node k in phi (phi_k = 2 pi k / n_phi).  A suspension of M
+ *     particles at order p has N = M (p+1) n_phi targets.
+ *   - Coefficient order: per particle, index n*n + n + m for 0 <= n <= p,
+ *     -n <= m <= n, in the real orthonormal surface-harmonic basis
+ *     (m > 0: sqrt(2) N_n^m P_n^m(v) cos(m phi); m = 0: N_n^0 P_n(v);
+ *     m < 0: sqrt(2) N_n^|m| P_n^|m|(v) sin(|m| phi)), Definition 1 with
+ *     Ferrers functions without the Condon-Shortley phase.
+ *   - Geometry and outputs are FP64 in every precision mode.
+ *   - A geometry handle may be used by one thread at a time; calls that
+ *     overlap on the GPU through the same geometry share its workspaces and
+ *     race, so issue them on one stream.
+ */
+#ifndef SBIO_H
+#define SBIO_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- return codes ---------------------------------------------------- */
+#define SBIO_OK 0
+#define SBIO_EINVAL (-1)    /* bad argument: sizes, p, shape, quaternion, pointer */
+#define SBIO_EOVERLAP (-2)  /* a surface node lies inside another spheroid */
+#define SBIO_ENOMEM (-3)    /* allocation failed or the context budget is exceeded */
+#define SBIO_ECUDA (-4)     /* a CUDA runtime call failed */
+#define SBIO_ETIMEOUT (-5)  /* a bounded device-side wait expired */
+#define SBIO_ENOTSUP (-6)   /* valid request this build does not implement */
+
+/* ---- particle kinds, precision modes, parts -------------------------- */
+#define SBIO_PROLATE 0
+#define SBIO_OBLATE 1
+
+#define SBIO_FP64 0   /* every kernel in FP64 */
+#define SBIO_MIXED 1  /* far-field pair sums in FP32 with two-sum compensated
+                         accumulation, near field and self term in FP64 */
+
+#define SBIO_PART_SELF 1u  /* on-surface self interaction (Sec. 4.1 "Near-field") */
+#define SBIO_PART_NEAR 2u  /* neighbour particles by the exterior expansion */
+#define SBIO_PART_FAR 4u   /* smooth quadrature over far particles (Sec. 4.1) */
+#define SBIO_PART_ALL 7u
+
+#define SBIO_MAX_P 24      /* largest expansion order accepted */
+
+typedef struct sbio_ctx sbio_ctx;   /* opaque: device, memory budget, error state */
+typedef struct sbio_geom sbio_geom; /* opaque: resident geometry of one suspension */
+
+/* One spheroid (Sec. 2.1, Table 1; Sec. 5.1 problem statement).
+ *   kind: SBIO_PROLATE (C > A) or SBIO_OBLATE (C < A); spheres are rejected.
+ *   A: equatorial semi-axis, C: polar semi-axis along the local x3 axis.
+ *   center: global position; quat: unit quaternion (w, x, y, z) with
+ *   x_global = center + R(quat) x_local.  Quaternions are normalised if their
+ *   norm is within 1e-6 of 1, otherwise SBIO_EINVAL. */
+typedef struct {
+  int32_t kind;
+  int32_t reserved;
+  double A;
+  double C;
+  double center[3];
+  double quat[4];
+} sbio_spheroid;
+
+/* Discretisation and method options.
+ *   p: expansion order, 1 <= p <= SBIO_MAX_P (Sec. 4, (p+1)^2 coefficients).
+ *   n_phi: trapezoid nodes in phi; 0 selects 2(p+1) (the paper prints 2p;
+ *          with 2p the sin(p phi) mode vanishes at every node).
+ *   near_factor: target x is near to particle i iff the exact distance from x
+ *          to the surface of i is below near_factor * (major semi-axis of i)
+ *          (Sec. 4.1 with eta = near_factor / 2); must be > 0.
+ *   far_upsample: must be 1 (far sources are the same quadrature nodes).
+ *   precision: SBIO_FP64 or SBIO_MIXED. */
+typedef struct {
+  int32_t p;
+  int32_t n_phi;
+  double near_factor;
+  int32_t far_upsample;
+  int32_t precision;
+} sbio_options;
+
+/* Library version string (static storage). */
+const char* sbio_version(void);
+
+/* Message of the last failure on the calling thread ("" if none).  `ctx` may
+ * be NULL.  The pointer stays valid until the next failing call on the thread. */
+const char* sbio_last_error(const sbio_ctx* ctx);
+
+/* Number of kernels this process has launched through the library so far
+ * (all contexts); used to count launches inside a timed region. */
+int64_t sbio_launch_count(void);
+
+/* Create a context on CUDA device `device`.  mem_budget_bytes bounds the
+ * device memory that geometries of this context may hold (0 = no bound);
+ * geometry creation that would exceed it fails with SBIO_ENOMEM. */
+int sbio_ctx_create(int device, size_t mem_budget_bytes, sbio_ctx** out);
+
+/* Destroy a context.  All its geometries must have been destroyed. */
+int sbio_ctx_destroy(sbio_ctx* ctx);
+
+/* Device bytes currently held by geometries of the context. */
+int sbio_ctx_mem_used(const sbio_ctx* ctx, size_t* bytes);
+
+/* Build the resident geometry of a suspension (host FP64 set-up, then upload
+ * on `stream`; the call returns after the upload has completed):
+ *   spheroid parameters a, u0 from the semi-axes (Sec. 2.1), rotations,
+ *   quadrature nodes, outward normals and weights w = w_j^GL (2 pi / n_phi)
+ *   dS-factor (Table 2), the per-particle multipliers of Theorems 1-2 and the
+ *   per-target near sets (Sec. 4.1).
+ *   sph: host array of M descriptors; M >= 1.
+ * Errors: SBIO_EINVAL (bad options or shapes), SBIO_EOVERLAP (a node of one
+ * particle lies inside another), SBIO_ENOMEM, SBIO_ECUDA. */
+int sbio_geom_create(sbio_ctx* ctx, const sbio_spheroid* sph, int32_t M,
+                     const sbio_options* opts, void* stream, sbio_geom** out);
+
+/* Release a geometry (synchronises the device first). */
+int sbio_geom_destroy(sbio_geom* g);
+
+/* Sizes of a geometry: targets N, (target, near particle) pairs, (target,
+ * far source node) pairs of one apply, and the device bytes it holds.  Any
+ * output pointer may be NULL. */
+int sbio_geom_info(const sbio_geom* g, int64_t* n_targets, int64_t* n_near_pairs,
+                   int64_t* n_far_pairs, size_t* device_bytes);
+
+/* Copy node data to host arrays (any may be NULL): global positions (N x 3),
+ * outward unit normals (N x 3), quadrature weights (N). */
+int sbio_geom_nodes(const sbio_geom* g, double* xyz, double* normal, double* weight);
+
+/* Copy the near pairs to host arrays of length n_near_pairs: target node index
+ * and source particle index, in the library's processing order. */
+int sbio_geom_near_pairs(const sbio_geom* g, int32_t* target, int32_t* source);
+
+/* Phase timing (measurement aid).  When enabled, every Laplace apply records
+ * CUDA events on its stream before the synthesis kernel, before the near-field
+ * kernels, before the far-field kernel and after it.  sbio_geom_phase_times()
+ * synchronises on those events and returns the three durations of the last
+ * apply in milliseconds (SBIO_EINVAL if timing is off). */
+int sbio_geom_enable_timing(sbio_geom* g, int32_t on);
+int sbio_geom_phase_times(sbio_geom* g, double* ms_synth, double* ms_near, double* ms_far);
+
+/* Change the precision mode used by later applies (SBIO_FP64 / SBIO_MIXED). */
+int sbio_geom_set_precision(sbio_geom* g, int32_t precision);
+
+/* Laplace apply at all N surface nodes (Algorithm 1 for D; its single-layer
+ * variant for S, Sec. 4.2):
+ *   S_out[t] = S[sigma](x_t),  sigma = sum sigma~_nm Y_nm / sqrt(u0^2 -+ v^2)
+ *              (modified basis, Sec. 3.2);
+ *   D_out[t] = D[mu](x_t),     mu = sum mu^_nm Y_nm, principal value on the
+ *              own surface (Theorem 1).
+ * sigma_tilde, mu_hat: device, M x (p+1)^2 FP64, or NULL to skip that operator.
+ * S_out, D_out: device, N FP64, must be non-NULL iff the matching input is.
+ * Outputs are overwritten.  Asynchronous on `stream`. */
+int sbio_apply_laplace(sbio_geom* g, const double* sigma_tilde, const double* mu_hat,
+                       double* S_out, double* D_out, void* stream);
+
+/* As sbio_apply_laplace, restricted to a subset of the three parts
+ * (SBIO_PART_* bit mask); the outputs hold the sum of the selected parts. */
+int sbio_apply_laplace_parts(sbio_geom* g, const double* sigma_tilde, const double* mu_hat,
+                             double* S_out, double* D_out, uint32_t parts, void* stream);
+
+/* End-to-end apply from and to HOST memory: copies the coefficients to
+ * library-owned device buffers on `stream`, applies, copies the results back
+ * and synchronises `stream` before returning.  Host buffers may be pageable or
+ * pinned (pinned gives overlap-free fast copies). */
+int sbio_apply_laplace_host(sbio_geom* g, const double* sigma_tilde_host, const double* mu_hat_host,
+                            double* S_host, double* D_host, void* stream);
+
+/* Stokes single layer with viscosity 1 at all N nodes (Sec. 4.3, eq. (stokes)):
+ *   u_k = 1/2 { S[f_k] - sum_j x_j d_k S[f_j] + d_k S[y . f] },  k = 1..3,
+ * far particles by the Stokeslet quadrature, near and self by the Laplace
+ * expansions and their gradients (eq. (dSLevalformula)).
+ * f_tilde: device, M x 3 x (p+1)^2 FP64: per particle the modified-basis
+ *          coefficients of the three global Cartesian components of f.
+ * u_out: device, N x 3 FP64 (row t = velocity at node t).  Asynchronous. */
+int sbio_apply_stokes_sl(sbio_geom* g, const double* f_tilde, double* u_out, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SBIO_H */

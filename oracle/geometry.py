@@ -196,25 +196,39 @@ class SuspensionGeom:
     def from_suspension(cls, s, near_factor=1.0, n_phi=None):
         return cls(s.kind, s.A, s.C, s.center, s.quat, s.p, n_phi, near_factor)
 
-    def distances(self):
-        """(N, M) signed target-to-spheroid distances (own particle: 0)."""
-        if self._dist is None:
-            D = np.zeros((self.N, self.M))
-            for i, P in enumerate(self.parts):
-                D[:, i] = point_spheroid_distance(P.to_local(self.x), P.A, P.C)
-                D[self.owner == i, i] = 0.0
+    def distances(self, targets=None):
+        """(T, M) signed target-to-spheroid distances (own particle: 0) for the
+        target node indices `targets` (default all).  Pairs whose bounding
+        sphere is already farther than the near threshold get the lower bound
+        |x - c| - major instead of the exact distance."""
+        if targets is None and self._dist is not None:
+            return self._dist
+        tg = np.arange(self.N) if targets is None else np.asarray(targets)
+        x = self.x[tg]
+        D = np.zeros((len(tg), self.M))
+        for i, P in enumerate(self.parts):
+            lb = np.linalg.norm(x - P.center, axis=1) - P.major
+            exact = lb < 2.0 * self.near_factor * P.major
+            D[:, i] = lb
+            if np.any(exact):
+                D[exact, i] = point_spheroid_distance(P.to_local(x[exact]), P.A, P.C)
+            D[self.owner[tg] == i, i] = 0.0
+        if targets is None:
             self._dist = D
-        return self._dist
+        return D
 
-    def near_matrix(self):
-        """(N, M) bool: source i is near target t (own particle excluded)."""
-        if self._near is None:
-            D = self.distances()
-            thr = np.array([self.near_factor * P.major for P in self.parts])
-            near = D < thr[None, :]
-            near[np.arange(self.N), self.owner] = False
+    def near_matrix(self, targets=None):
+        """(T, M) bool: source i is near target t (own particle excluded)."""
+        if targets is None and self._near is not None:
+            return self._near
+        tg = np.arange(self.N) if targets is None else np.asarray(targets)
+        D = self.distances(targets)
+        thr = np.array([self.near_factor * P.major for P in self.parts])
+        near = D < thr[None, :]
+        near[np.arange(len(tg)), self.owner[tg]] = False
+        if targets is None:
             self._near = near
-        return self._near
+        return near
 
     def near_margin(self):
         """Smallest relative distance of any (target, other particle) from the

@@ -159,7 +159,7 @@ class LaplaceOracle:
         S = np.zeros(tgt.shape[0]) if sigma_t is not None else None
         D = np.zeros(tgt.shape[0]) if mu_h is not None else None
         owner = g.owner[tgt]
-        near = g.near_matrix()[tgt] if mode == "method" else None
+        near = g.near_matrix(None if targets is None else tgt) if mode == "method" else None
         for i, P in enumerate(g.parts):
             si = None if sigma_t is None else sigma_t[i]
             mi = None if mu_h is None else mu_h[i]
@@ -196,7 +196,7 @@ class LaplaceOracle:
         """Number of (target, far source node) pairs of the method."""
         g = self.g
         tgt = np.arange(g.N) if targets is None else np.asarray(targets)
-        near = g.near_matrix()[tgt]
+        near = g.near_matrix(None if targets is None else tgt)
         n_skip = near.sum(axis=1) + 1
         return int(np.sum((g.M - n_skip) * g.G))
 

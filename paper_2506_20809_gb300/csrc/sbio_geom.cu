@@ -1,0 +1,599 @@
+// Context, error state and resident geometry of the spheroidal BIO library:
+// host FP64 set-up (Sec. 2.1-2.2 geometry, Theorems 1-2 multipliers, Sec. 4.1
+// near sets) and the upload of everything an apply reads.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <thread>
+
+#include "sbio_internal.cuh"
+#include "sbio_near.cuh"
+
+namespace sbio {
+
+static thread_local std::string t_err;
+static std::atomic<int64_t> g_launches{0};
+
+int set_error(int code, const char* fmt, ...) {
+  char buf[1024];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  t_err = buf;
+  return code;
+}
+
+void clear_error() { t_err.clear(); }
+
+void count_launch(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+
+int dev_alloc(sbio_geom* g, void** ptr, size_t bytes, const char* what) {
+  *ptr = nullptr;
+  if (bytes == 0) return SBIO_OK;
+  sbio_ctx* c = g->ctx;
+  size_t prev = c->used.fetch_add(bytes);
+  if (c->budget && prev + bytes > c->budget) {
+    c->used.fetch_sub(bytes);
+    return set_error(SBIO_ENOMEM, "device budget exceeded allocating %s (%zu bytes, %zu of %zu in use)", what,
+                     bytes, prev, c->budget);
+  }
+  cudaError_t e = cudaMalloc(ptr, bytes);
+  if (e != cudaSuccess) {
+    c->used.fetch_sub(bytes);
+    *ptr = nullptr;
+    return set_error(SBIO_ENOMEM, "cudaMalloc of %s (%zu bytes) failed: %s", what, bytes, cudaGetErrorString(e));
+  }
+  g->bytes += bytes;
+  g->allocs.push_back(*ptr);
+  return SBIO_OK;
+}
+
+// ---------------------------------------------------------------------------
+// numerical helpers of the set-up
+// ---------------------------------------------------------------------------
+
+// Gauss-Legendre nodes (ascending) and weights by Newton's method on P_n.
+static void gauss_legendre(int n, std::vector<double>& x, std::vector<double>& w) {
+  x.assign(n, 0.0);
+  w.assign(n, 0.0);
+  for (int i = 0; i < n; ++i) {
+    double z = std::cos(kPi * (i + 0.75) / (n + 0.5));
+    double dp = 1.0;
+    for (int it = 0; it < 100; ++it) {
+      double p0 = 1.0, p1 = z;
+      for (int k = 2; k <= n; ++k) {
+        double p2 = ((2.0 * k - 1.0) * z * p1 - (k - 1.0) * p0) / k;
+        p0 = p1;
+        p1 = p2;
+      }
+      double pn = (n == 1) ? z : p1;
+      double pm1 = (n == 1) ? 1.0 : p0;
+      dp = n * (z * pn - pm1) / (z * z - 1.0);
+      double dz = pn / dp;
+      z -= dz;
+      if (std::fabs(dz) < 1e-16) break;
+    }
+    double p0 = 1.0, p1 = z;
+    for (int k = 2; k <= n; ++k) {
+      double p2 = ((2.0 * k - 1.0) * z * p1 - (k - 1.0) * p0) / k;
+      p0 = p1;
+      p1 = p2;
+    }
+    double pn = (n == 1) ? z : p1, pm1 = (n == 1) ? 1.0 : p0;
+    dp = n * (z * pn - pm1) / (z * z - 1.0);
+    x[n - 1 - i] = z;
+    w[n - 1 - i] = 2.0 / ((1.0 - z * z) * dp * dp);
+  }
+}
+
+// Ferrers functions Pbar_n^m(v) (no Condon-Shortley phase), [nm_index(n,m)].
+static void ferrers(double v, int N, double* P) {
+  const double sv = std::sqrt(std::max(0.0, 1.0 - v * v));
+  double pmm = 1.0;
+  for (int m = 0; m <= N; ++m) {
+    if (m > 0) pmm *= (2.0 * m - 1.0) * sv;
+    P[nm_index(m, m)] = pmm;
+    if (m + 1 <= N) P[nm_index(m + 1, m)] = (2.0 * m + 1.0) * v * pmm;
+    for (int n = m + 1; n < N; ++n)
+      P[nm_index(n + 1, m)] = ((2.0 * n + 1.0) * v * P[nm_index(n, m)] - (n + m) * P[nm_index(n - 1, m)]) / (n - m + 1.0);
+  }
+}
+
+// (n-m)!/(n+m)!
+static double kfact(int n, int m) {
+  double r = 1.0;
+  for (int j = n - m + 1; j <= n + m; ++j) r /= j;
+  return r;
+}
+
+// Distance from (y0, y1) >= 0 to the ellipse (t0/e0)^2 + (t1/e1)^2 = 1 with
+// e0 >= e1 > 0, for points outside it: bisection on the Lagrange parameter of
+// the closest-point condition (D. Eberly, "Distance from a point to an
+// ellipse, an ellipsoid, or a hyperellipsoid", Geometric Tools).
+static double ellipse_distance(double e0, double e1, double y0, double y1) {
+  if (y1 > 0.0) {
+    if (y0 > 0.0) {
+      const double z0 = y0 / e0, z1 = y1 / e1;
+      const double g0 = z0 * z0 + z1 * z1 - 1.0;
+      if (g0 == 0.0) return 0.0;
+      const double r0 = (e0 / e1) * (e0 / e1);
+      const double n0 = r0 * z0;
+      double s0 = z1 - 1.0;
+      double s1 = (g0 < 0.0) ? 0.0 : std::hypot(n0, z1) - 1.0;
+      double s = 0.0;
+      for (int it = 0; it < 2000; ++it) {
+        s = 0.5 * (s0 + s1);
+        if (s == s0 || s == s1) break;
+        const double r0s = n0 / (s + r0), r1s = z1 / (s + 1.0);
+        const double g = r0s * r0s + r1s * r1s - 1.0;
+        if (g > 0.0) s0 = s;
+        else if (g < 0.0) s1 = s;
+        else break;
+      }
+      const double x0 = r0 * y0 / (s + r0), x1 = y1 / (s + 1.0);
+      return std::hypot(x0 - y0, x1 - y1);
+    }
+    return std::fabs(y1 - e1);
+  }
+  const double num = e0 * y0, den = e0 * e0 - e1 * e1;
+  if (num < den) {
+    const double xd = num / den;
+    const double x0 = e0 * xd, x1 = e1 * std::sqrt(std::max(0.0, 1.0 - xd * xd));
+    return std::hypot(x0 - y0, x1);
+  }
+  return std::fabs(y0 - e0);
+}
+
+// Signed distance from a local point to the spheroid (negative inside).
+static double spheroid_distance(const PartGeom& P, double x, double y, double z) {
+  const double rho = std::hypot(x, y), az = std::fabs(z);
+  const double f = (rho / P.A) * (rho / P.A) + (az / P.C) * (az / P.C);
+  if (f < 1.0) return -1.0;
+  // meridian-plane ellipse with semi-axes A (rho) and C (z); major axis first
+  if (P.C >= P.A) return ellipse_distance(P.C, P.A, az, rho);
+  return ellipse_distance(P.A, P.C, rho, az);
+}
+
+static void quat_rot(const double* q, double* R) {
+  const double w = q[0], x = q[1], y = q[2], z = q[3];
+  R[0] = 1 - 2 * (y * y + z * z); R[1] = 2 * (x * y - w * z);     R[2] = 2 * (x * z + w * y);
+  R[3] = 2 * (x * y + w * z);     R[4] = 1 - 2 * (x * x + z * z); R[5] = 2 * (y * z - w * x);
+  R[6] = 2 * (x * z - w * y);     R[7] = 2 * (y * z + w * x);     R[8] = 1 - 2 * (x * x + y * y);
+}
+
+static void split_f32(double v, float& hi, float& lo) {
+  hi = (float)v;
+  lo = (float)(v - (double)hi);
+}
+
+// ---------------------------------------------------------------------------
+// geometry construction
+// ---------------------------------------------------------------------------
+
+static int validate(const sbio_spheroid* sph, int32_t M, const sbio_options* o) {
+  if (!sph || !o) return set_error(SBIO_EINVAL, "null spheroid array or options");
+  if (M < 1) return set_error(SBIO_EINVAL, "M = %d: need at least one spheroid", M);
+  if (o->p < 1 || o->p > SBIO_MAX_P) return set_error(SBIO_EINVAL, "p = %d outside [1, %d]", o->p, SBIO_MAX_P);
+  const int nphi = o->n_phi ? o->n_phi : 2 * (o->p + 1);
+  if (nphi < 2 * o->p || nphi > 4096) return set_error(SBIO_EINVAL, "n_phi = %d must be in [2p, 4096]", nphi);
+  if (!(o->near_factor > 0.0) || !std::isfinite(o->near_factor))
+    return set_error(SBIO_EINVAL, "near_factor must be positive and finite");
+  if (o->far_upsample != 1) return set_error(SBIO_ENOTSUP, "far_upsample = %d: only 1 is implemented", o->far_upsample);
+  if (o->precision != SBIO_FP64 && o->precision != SBIO_MIXED)
+    return set_error(SBIO_EINVAL, "precision %d unknown", o->precision);
+  if ((int64_t)M * (o->p + 1) * nphi > (int64_t)INT32_MAX / 2)
+    return set_error(SBIO_EINVAL, "too many nodes");
+  for (int i = 0; i < M; ++i) {
+    const sbio_spheroid& s = sph[i];
+    if (s.kind != SBIO_PROLATE && s.kind != SBIO_OBLATE) return set_error(SBIO_EINVAL, "particle %d: kind %d", i, s.kind);
+    if (!(s.A > 0.0) || !(s.C > 0.0) || !std::isfinite(s.A) || !std::isfinite(s.C))
+      return set_error(SBIO_EINVAL, "particle %d: semi-axes must be positive", i);
+    if (s.kind == SBIO_PROLATE && !(s.C > s.A * (1.0 + 1e-9)))
+      return set_error(SBIO_EINVAL, "particle %d: prolate needs C > A (spheres are not supported)", i);
+    if (s.kind == SBIO_OBLATE && !(s.C < s.A * (1.0 - 1e-9)))
+      return set_error(SBIO_EINVAL, "particle %d: oblate needs C < A (spheres are not supported)", i);
+    const double qn = std::sqrt(s.quat[0] * s.quat[0] + s.quat[1] * s.quat[1] + s.quat[2] * s.quat[2] + s.quat[3] * s.quat[3]);
+    if (!(std::fabs(qn - 1.0) <= 1e-6)) return set_error(SBIO_EINVAL, "particle %d: quaternion norm %g", i, qn);
+    for (int k = 0; k < 3; ++k)
+      if (!std::isfinite(s.center[k])) return set_error(SBIO_EINVAL, "particle %d: centre not finite", i);
+  }
+  return SBIO_OK;
+}
+
+static int build_host(GeomHost& h, const sbio_spheroid* sph, int32_t M, const sbio_options* o) {
+  h.M = M;
+  h.p = o->p;
+  h.n_v = o->p + 1;
+  h.n_phi = o->n_phi ? o->n_phi : 2 * (o->p + 1);
+  h.G = h.n_v * h.n_phi;
+  h.N = (int64_t)M * h.G;
+  h.near_factor = o->near_factor;
+  h.precision = o->precision;
+  h.parts.resize(M);
+  for (int i = 0; i < M; ++i) {
+    const sbio_spheroid& s = sph[i];
+    PartGeom& P = h.parts[i];
+    std::memset(&P, 0, sizeof(P));
+    P.kind = s.kind;
+    P.A = s.A;
+    P.C = s.C;
+    P.sgn = (s.kind == SBIO_PROLATE) ? -1.0 : 1.0;
+    P.a = (s.kind == SBIO_PROLATE) ? std::sqrt((s.C - s.A) * (s.C + s.A)) : std::sqrt((s.A - s.C) * (s.A + s.C));
+    P.u0 = s.C / P.a;
+    double q[4];
+    const double qn = std::sqrt(s.quat[0] * s.quat[0] + s.quat[1] * s.quat[1] + s.quat[2] * s.quat[2] + s.quat[3] * s.quat[3]);
+    for (int k = 0; k < 4; ++k) q[k] = s.quat[k] / qn;
+    quat_rot(q, P.R);
+    for (int k = 0; k < 3; ++k) P.c[k] = s.center[k];
+  }
+  // nodes
+  std::vector<double> gv, gw;
+  gauss_legendre(h.n_v, gv, gw);
+  h.xyz.resize(h.N * 3);
+  h.nrm.resize(h.N * 3);
+  h.w.resize(h.N);
+  for (int i = 0; i < M; ++i) {
+    const PartGeom& P = h.parts[i];
+    for (int j = 0; j < h.n_v; ++j) {
+      const double v = gv[j], sv = std::sqrt(std::max(0.0, (1.0 - v) * (1.0 + v)));
+      // dS = a^2 sqrt(u0^2 + sgn v^2) sqrt(u0^2 + sgn) dv dphi = A sqrt(C^2 + sgn a^2 v^2) dv dphi
+      const double dsf = P.A * std::sqrt(P.C * P.C * (P.kind == SBIO_PROLATE ? (1.0 - v * v) : 1.0) +
+                                         (P.kind == SBIO_PROLATE ? P.A * P.A * v * v : P.a * P.a * v * v));
+      for (int k = 0; k < h.n_phi; ++k) {
+        const double ph = 2.0 * kPi * k / h.n_phi;
+        const double xl[3] = {P.A * sv * std::cos(ph), P.A * sv * std::sin(ph), P.C * v};
+        double nl[3] = {xl[0] / (P.A * P.A), xl[1] / (P.A * P.A), xl[2] / (P.C * P.C)};
+        const double nn = std::sqrt(nl[0] * nl[0] + nl[1] * nl[1] + nl[2] * nl[2]);
+        for (int c = 0; c < 3; ++c) nl[c] /= nn;
+        const int64_t t = (int64_t)i * h.G + (int64_t)j * h.n_phi + k;
+        for (int r = 0; r < 3; ++r) {
+          h.xyz[t * 3 + r] = P.c[r] + P.R[r * 3 + 0] * xl[0] + P.R[r * 3 + 1] * xl[1] + P.R[r * 3 + 2] * xl[2];
+          h.nrm[t * 3 + r] = P.R[r * 3 + 0] * nl[0] + P.R[r * 3 + 1] * nl[1] + P.R[r * 3 + 2] * nl[2];
+        }
+        h.w[t] = gw[j] * (2.0 * kPi / h.n_phi) * dsf;
+      }
+    }
+  }
+  return SBIO_OK;
+}
+
+// Per-target near sets (exact distances), in parallel over targets.
+static int build_near(GeomHost& h) {
+  const int M = h.M;
+  const int64_t N = h.N;
+  std::vector<double> rmax(M), thr(M);
+  for (int i = 0; i < M; ++i) {
+    rmax[i] = std::max(h.parts[i].A, h.parts[i].C);
+    thr[i] = h.near_factor * rmax[i];
+  }
+  unsigned nth = std::max(1u, std::min(32u, std::thread::hardware_concurrency()));
+  std::vector<std::vector<std::pair<int32_t, int32_t>>> local(nth);
+  std::vector<int> overlap(nth, -1);
+  auto work = [&](unsigned tid) {
+    for (int64_t t = tid; t < N; t += nth) {
+      const int own = (int)(t / h.G);
+      const double* x = &h.xyz[t * 3];
+      for (int i = 0; i < M; ++i) {
+        if (i == own) continue;
+        const PartGeom& P = h.parts[i];
+        const double d0 = x[0] - P.c[0], d1 = x[1] - P.c[1], d2 = x[2] - P.c[2];
+        const double dc = std::sqrt(d0 * d0 + d1 * d1 + d2 * d2);
+        if (dc - rmax[i] >= thr[i]) continue;
+        const double xl = P.R[0] * d0 + P.R[3] * d1 + P.R[6] * d2;
+        const double yl = P.R[1] * d0 + P.R[4] * d1 + P.R[7] * d2;
+        const double zl = P.R[2] * d0 + P.R[5] * d1 + P.R[8] * d2;
+        const double d = spheroid_distance(P, xl, yl, zl);
+        if (d < 0.0) {
+          overlap[tid] = (int)t;
+          return;
+        }
+        if (d < thr[i]) local[tid].push_back({(int32_t)t, (int32_t)i});
+      }
+    }
+  };
+  std::vector<std::thread> th;
+  for (unsigned k = 0; k < nth; ++k) th.emplace_back(work, k);
+  for (auto& t : th) t.join();
+  for (unsigned k = 0; k < nth; ++k)
+    if (overlap[k] >= 0)
+      return set_error(SBIO_EOVERLAP, "node %d of particle %d lies inside another spheroid", overlap[k],
+                       (int)(overlap[k] / h.G));
+  std::vector<std::pair<int32_t, int32_t>> pairs;
+  for (auto& v : local) pairs.insert(pairs.end(), v.begin(), v.end());
+  // order (kind of source, source, target): warps share a source and its kind
+  std::sort(pairs.begin(), pairs.end(), [&](const std::pair<int32_t, int32_t>& a, const std::pair<int32_t, int32_t>& b) {
+    const int ka = h.parts[a.second].kind, kb = h.parts[b.second].kind;
+    if (ka != kb) return ka < kb;
+    if (a.second != b.second) return a.second < b.second;
+    return a.first < b.first;
+  });
+  h.pair_t.resize(pairs.size());
+  h.pair_s.resize(pairs.size());
+  h.n_pairs_prolate = 0;
+  std::vector<int32_t> cnt(N, 0);
+  for (size_t k = 0; k < pairs.size(); ++k) {
+    h.pair_t[k] = pairs[k].first;
+    h.pair_s[k] = pairs[k].second;
+    if (h.parts[pairs[k].second].kind == SBIO_PROLATE) h.n_pairs_prolate++;
+    cnt[pairs[k].first]++;
+  }
+  h.far_pairs = 0;
+  for (int64_t t = 0; t < N; ++t) h.far_pairs += (int64_t)(M - 1 - cnt[t]) * h.G;
+  // far-field source tiles
+  h.tiles.clear();
+  for (int i = 0; i < M; ++i)
+    for (int s = 0; s < h.G; s += kFarTile)
+      h.tiles.push_back(make_int4(i, i * h.G + s, std::min(kFarTile, h.G - s), 0));
+  return SBIO_OK;
+}
+
+template <typename T>
+static int upload(sbio_geom* g, T** dst, const T* src, size_t count, const char* what) {
+  int rc = dev_alloc(g, (void**)dst, count * sizeof(T), what);
+  if (rc) return rc;
+  if (count) SBIO_CUDA_TRY(cudaMemcpyAsync(*dst, src, count * sizeof(T), cudaMemcpyHostToDevice, g->setup_stream));
+  return SBIO_OK;
+}
+
+static int build_device(sbio_geom* g) {
+  GeomHost& h = g->h;
+  DevGeom& d = g->d;
+  const int p = h.p, M = h.M, nm = nm_count(p), nc = (p + 1) * (p + 1);
+  const int64_t N = h.N;
+  int rc;
+  if ((rc = upload(g, &d.parts, h.parts.data(), M, "particles"))) return rc;
+  if ((rc = upload(g, &d.xyz, h.xyz.data(), N * 3, "node positions"))) return rc;
+  if ((rc = upload(g, &d.nrm, h.nrm.data(), N * 3, "node normals"))) return rc;
+  if ((rc = upload(g, &d.w, h.w.data(), N, "node weights"))) return rc;
+  // Legendre table at the GL nodes, trig table, modified-basis weights
+  std::vector<double> gv, gw;
+  gauss_legendre(h.n_v, gv, gw);
+  std::vector<double> ptab((size_t)h.n_v * nm), tmp(nm_count(p + 2));
+  for (int j = 0; j < h.n_v; ++j) {
+    ferrers(gv[j], p, tmp.data());
+    for (int n = 0; n <= p; ++n)
+      for (int m = 0; m <= n; ++m)
+        ptab[(size_t)j * nm + nm_index(n, m)] = std::sqrt((2.0 * n + 1.0) / (4.0 * kPi) * kfact(n, m)) * tmp[nm_index(n, m)];
+  }
+  if ((rc = upload(g, &d.ptab, ptab.data(), ptab.size(), "Legendre table"))) return rc;
+  std::vector<double> trig((size_t)h.n_phi * (p + 1) * 2);
+  for (int k = 0; k < h.n_phi; ++k)
+    for (int m = 0; m <= p; ++m) {
+      const double ph = 2.0 * kPi * k / h.n_phi;
+      trig[((size_t)k * (p + 1) + m) * 2 + 0] = std::cos(m * ph);
+      trig[((size_t)k * (p + 1) + m) * 2 + 1] = std::sin(m * ph);
+    }
+  if ((rc = upload(g, &d.trig, trig.data(), trig.size(), "trig table"))) return rc;
+  std::vector<double> sqrtw((size_t)M * h.n_v);
+  for (int i = 0; i < M; ++i) {
+    const PartGeom& P = h.parts[i];
+    for (int j = 0; j < h.n_v; ++j) {
+      const double v = gv[j];
+      const double c2 = (P.kind == SBIO_PROLATE) ? P.C * P.C * (1.0 - v * v) + P.A * P.A * v * v
+                                                 : P.C * P.C + P.a * P.a * v * v;
+      sqrtw[(size_t)i * h.n_v + j] = std::sqrt(c2) / P.a;   // sqrt(u0^2 + sgn v^2)
+    }
+  }
+  if ((rc = upload(g, &d.sqrtw, sqrtw.data(), sqrtw.size(), "modified-basis weights"))) return rc;
+  // Theorems 1-2 multipliers per particle
+  std::vector<double> mult((size_t)M * 4 * nm);
+  std::vector<double> Pr(nm_count(p + 1)), Qr(nm_count(p + 1));
+  for (int i = 0; i < M; ++i) {
+    const PartGeom& P = h.parts[i];
+    const double u0 = P.u0, sgn = P.sgn, s0 = P.A / P.a, den = u0 * u0 + sgn;
+    radial_P(u0, sgn, p + 1, Pr.data());
+    radial_Q(u0, sgn, p + 1, Qr.data());
+    for (int n = 0; n <= p; ++n)
+      for (int m = 0; m <= n; ++m) {
+        const double K = kfact(n, m) * ((m & 1) ? -1.0 : 1.0);
+        const double pn = Pr[nm_index(n, m)], qn = Qr[nm_index(n, m)];
+        const double pn1 = Pr[nm_index(n + 1, m)], qn1 = Qr[nm_index(n + 1, m)];
+        const double dp = ((n - m + 1.0) * pn1 - (n + 1.0) * u0 * pn) / den;
+        const double dq = (-sgn * (n - m + 1.0) * qn1 - (n + 1.0) * u0 * qn) / den;
+        const double extS = P.a * K * s0 * pn;
+        const double extD = K * s0 * s0 * dp;
+        const double Dp = extD * qn, Dm = K * s0 * s0 * dq * pn;
+        double* mm = &mult[(size_t)i * 4 * nm];
+        mm[0 * nm + nm_index(n, m)] = extS;
+        mm[1 * nm + nm_index(n, m)] = extD;
+        mm[2 * nm + nm_index(n, m)] = extS * qn;
+        mm[3 * nm + nm_index(n, m)] = 0.5 * (Dp + Dm);
+      }
+  }
+  if ((rc = upload(g, &d.mult, mult.data(), mult.size(), "multipliers"))) return rc;
+  std::vector<double> normc(nc);
+  for (int n = 0; n <= p; ++n)
+    for (int m = -n; m <= n; ++m) {
+      const int am = m < 0 ? -m : m;
+      normc[coef_index(n, m)] = std::sqrt((2.0 * n + 1.0) / (4.0 * kPi) * kfact(n, am)) * (m ? std::sqrt(2.0) : 1.0);
+    }
+  if ((rc = upload(g, &d.normc, normc.data(), normc.size(), "normalisation"))) return rc;
+  // near pairs and far skip lists (own particle + near particles, ascending)
+  if ((rc = upload(g, &d.pair_t, h.pair_t.data(), h.pair_t.size(), "near pairs"))) return rc;
+  if ((rc = upload(g, &d.pair_s, h.pair_s.data(), h.pair_s.size(), "near pairs"))) return rc;
+  std::vector<std::vector<int32_t>> skip(N);
+  for (int64_t t = 0; t < N; ++t) skip[t].push_back((int32_t)(t / h.G));
+  for (size_t k = 0; k < h.pair_t.size(); ++k) skip[h.pair_t[k]].push_back(h.pair_s[k]);
+  std::vector<int32_t> sptr(N + 1, 0), sidx;
+  for (int64_t t = 0; t < N; ++t) {
+    std::sort(skip[t].begin(), skip[t].end());
+    skip[t].push_back(INT32_MAX);   // sentinel
+    sptr[t + 1] = sptr[t] + (int32_t)skip[t].size();
+    sidx.insert(sidx.end(), skip[t].begin(), skip[t].end());
+  }
+  if ((rc = upload(g, &d.skip_ptr, sptr.data(), sptr.size(), "skip lists"))) return rc;
+  if ((rc = upload(g, &d.skip_idx, sidx.data(), sidx.size(), "skip lists"))) return rc;
+  if ((rc = upload(g, &d.tiles, h.tiles.data(), h.tiles.size(), "far tiles"))) return rc;
+  std::vector<double> inv(kInvTable, 0.0);
+  for (int k = 1; k < kInvTable; ++k) inv[k] = 1.0 / k;
+  if ((rc = upload(g, &d.inv, inv.data(), inv.size(), "inverse table"))) return rc;
+  // FP32 hi/lo target positions and centres for the mixed far field
+  std::vector<float4> tgt(N * 2), cen(M * 2);
+  for (int64_t t = 0; t < N; ++t) {
+    float hi[3], lo[3];
+    for (int c = 0; c < 3; ++c) split_f32(h.xyz[t * 3 + c], hi[c], lo[c]);
+    tgt[t * 2 + 0] = make_float4(hi[0], hi[1], hi[2], 0.f);
+    tgt[t * 2 + 1] = make_float4(lo[0], lo[1], lo[2], 0.f);
+  }
+  for (int i = 0; i < M; ++i) {
+    float hi[3], lo[3];
+    for (int c = 0; c < 3; ++c) split_f32(h.parts[i].c[c], hi[c], lo[c]);
+    cen[i * 2 + 0] = make_float4(hi[0], hi[1], hi[2], 0.f);
+    cen[i * 2 + 1] = make_float4(lo[0], lo[1], lo[2], 0.f);
+  }
+  if ((rc = upload(g, &d.tgt32, tgt.data(), tgt.size(), "fp32 targets"))) return rc;
+  if ((rc = upload(g, &d.cen32, cen.data(), cen.size(), "fp32 centres"))) return rc;
+  // workspaces
+  if ((rc = dev_alloc(g, (void**)&d.src64, (size_t)N * 8 * sizeof(double), "fp64 sources"))) return rc;
+  if ((rc = dev_alloc(g, (void**)&d.src32, (size_t)N * 2 * sizeof(float4), "fp32 sources"))) return rc;
+  if ((rc = dev_alloc(g, (void**)&d.alpha, (size_t)M * nc * sizeof(double), "near S coefficients"))) return rc;
+  if ((rc = dev_alloc(g, (void**)&d.beta, (size_t)M * nc * sizeof(double), "near D coefficients"))) return rc;
+  if ((rc = dev_alloc(g, (void**)&d.host_in, (size_t)2 * M * nc * sizeof(double), "host staging"))) return rc;
+  if ((rc = dev_alloc(g, (void**)&d.host_out, (size_t)2 * N * sizeof(double), "host staging"))) return rc;
+  SBIO_CUDA_TRY(cudaStreamSynchronize(g->setup_stream));
+  return SBIO_OK;
+}
+
+static void free_geom(sbio_geom* g) {
+  if (!g) return;
+  for (int k = 0; k < 4; ++k)
+    if (g->ev[k]) {
+      cudaEventDestroy(g->ev[k]);
+      g->ev[k] = nullptr;
+    }
+  for (void* p : g->allocs) cudaFree(p);
+  if (g->ctx) g->ctx->used.fetch_sub(g->bytes);
+  g->allocs.clear();
+  g->bytes = 0;
+}
+
+}  // namespace sbio
+
+using namespace sbio;
+
+extern "C" {
+
+const char* sbio_version(void) { return "sbio 0.1 (sm_103a)"; }
+
+const char* sbio_last_error(const sbio_ctx*) { return t_err.c_str(); }
+
+int64_t sbio_launch_count(void) { return g_launches.load(); }
+
+int sbio_ctx_create(int device, size_t mem_budget_bytes, sbio_ctx** out) {
+  clear_error();
+  if (!out) return set_error(SBIO_EINVAL, "null output pointer");
+  *out = nullptr;
+  int n = 0;
+  SBIO_CUDA_TRY(cudaGetDeviceCount(&n));
+  if (device < 0 || device >= n) return set_error(SBIO_EINVAL, "device %d of %d", device, n);
+  SBIO_CUDA_TRY(cudaSetDevice(device));
+  sbio_ctx* c = new sbio_ctx();
+  c->device = device;
+  c->budget = mem_budget_bytes;
+  *out = c;
+  return SBIO_OK;
+}
+
+int sbio_ctx_destroy(sbio_ctx* ctx) {
+  if (!ctx) return SBIO_OK;
+  if (ctx->n_geoms.load() != 0) return set_error(SBIO_EINVAL, "context still owns %d geometries", ctx->n_geoms.load());
+  delete ctx;
+  return SBIO_OK;
+}
+
+int sbio_ctx_mem_used(const sbio_ctx* ctx, size_t* bytes) {
+  if (!ctx || !bytes) return set_error(SBIO_EINVAL, "null argument");
+  *bytes = ctx->used.load();
+  return SBIO_OK;
+}
+
+int sbio_geom_create(sbio_ctx* ctx, const sbio_spheroid* sph, int32_t M, const sbio_options* opts, void* stream,
+                     sbio_geom** out) {
+  clear_error();
+  if (!ctx || !out) return set_error(SBIO_EINVAL, "null context or output pointer");
+  *out = nullptr;
+  int rc = validate(sph, M, opts);
+  if (rc) return rc;
+  SBIO_CUDA_TRY(cudaSetDevice(ctx->device));
+  sbio_geom* g = new sbio_geom();
+  g->ctx = ctx;
+  g->setup_stream = (cudaStream_t)stream;
+  rc = build_host(g->h, sph, M, opts);
+  if (!rc) rc = build_near(g->h);
+  if (!rc) rc = build_device(g);
+  if (rc) {
+    free_geom(g);
+    delete g;
+    return rc;
+  }
+  ctx->n_geoms.fetch_add(1);
+  *out = g;
+  return SBIO_OK;
+}
+
+int sbio_geom_destroy(sbio_geom* g) {
+  if (!g) return SBIO_OK;
+  cudaSetDevice(g->ctx->device);
+  cudaDeviceSynchronize();
+  free_geom(g);
+  g->ctx->n_geoms.fetch_sub(1);
+  delete g;
+  return SBIO_OK;
+}
+
+int sbio_geom_info(const sbio_geom* g, int64_t* n_targets, int64_t* n_near_pairs, int64_t* n_far_pairs,
+                   size_t* device_bytes) {
+  if (!g) return set_error(SBIO_EINVAL, "null geometry");
+  if (n_targets) *n_targets = g->h.N;
+  if (n_near_pairs) *n_near_pairs = (int64_t)g->h.pair_t.size();
+  if (n_far_pairs) *n_far_pairs = g->h.far_pairs;
+  if (device_bytes) *device_bytes = g->bytes;
+  return SBIO_OK;
+}
+
+int sbio_geom_nodes(const sbio_geom* g, double* xyz, double* normal, double* weight) {
+  if (!g) return set_error(SBIO_EINVAL, "null geometry");
+  if (xyz) std::memcpy(xyz, g->h.xyz.data(), g->h.xyz.size() * sizeof(double));
+  if (normal) std::memcpy(normal, g->h.nrm.data(), g->h.nrm.size() * sizeof(double));
+  if (weight) std::memcpy(weight, g->h.w.data(), g->h.w.size() * sizeof(double));
+  return SBIO_OK;
+}
+
+int sbio_geom_near_pairs(const sbio_geom* g, int32_t* target, int32_t* source) {
+  if (!g) return set_error(SBIO_EINVAL, "null geometry");
+  if (target) std::memcpy(target, g->h.pair_t.data(), g->h.pair_t.size() * sizeof(int32_t));
+  if (source) std::memcpy(source, g->h.pair_s.data(), g->h.pair_s.size() * sizeof(int32_t));
+  return SBIO_OK;
+}
+
+int sbio_geom_enable_timing(sbio_geom* g, int32_t on) {
+  if (!g) return set_error(SBIO_EINVAL, "null geometry");
+  SBIO_CUDA_TRY(cudaSetDevice(g->ctx->device));
+  if (on && !g->ev[0])
+    for (int k = 0; k < 4; ++k) SBIO_CUDA_TRY(cudaEventCreate(&g->ev[k]));
+  g->timing = on != 0;
+  return SBIO_OK;
+}
+
+int sbio_geom_phase_times(sbio_geom* g, double* ms_synth, double* ms_near, double* ms_far) {
+  if (!g) return set_error(SBIO_EINVAL, "null geometry");
+  if (!g->timing) return set_error(SBIO_EINVAL, "timing not enabled");
+  float t[3] = {0.f, 0.f, 0.f};
+  SBIO_CUDA_TRY(cudaEventSynchronize(g->ev[3]));
+  for (int k = 0; k < 3; ++k) SBIO_CUDA_TRY(cudaEventElapsedTime(&t[k], g->ev[k], g->ev[k + 1]));
+  if (ms_synth) *ms_synth = t[0];
+  if (ms_near) *ms_near = t[1];
+  if (ms_far) *ms_far = t[2];
+  return SBIO_OK;
+}
+
+int sbio_geom_set_precision(sbio_geom* g, int32_t precision) {
+  if (!g) return set_error(SBIO_EINVAL, "null geometry");
+  if (precision != SBIO_FP64 && precision != SBIO_MIXED) return set_error(SBIO_EINVAL, "precision %d", precision);
+  g->h.precision = precision;
+  return SBIO_OK;
+}
+
+}  // extern "C"

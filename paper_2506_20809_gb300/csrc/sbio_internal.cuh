@@ -1,0 +1,127 @@
+// Host-side internal state of the library (context, geometry) and the kernel
+// launch interface between the set-up code and the kernel translation units.
+#pragma once
+
+#include <atomic>
+#include <cstdarg>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "sbio_common.cuh"
+
+struct sbio_ctx {
+  int device = 0;
+  size_t budget = 0;                 // 0 = unbounded
+  std::atomic<size_t> used{0};
+  std::atomic<int> n_geoms{0};
+};
+
+namespace sbio {
+
+constexpr int kFarTile = 128;        // sources per far-field tile (= threads per CTA)
+
+// Per-apply device workspaces and per-geometry device tables.
+struct DevGeom {
+  PartGeom* parts = nullptr;     // M
+  double* xyz = nullptr;         // N x 3 global node positions
+  double* nrm = nullptr;         // N x 3 outward unit normals
+  double* w = nullptr;           // N quadrature weights
+  double* ptab = nullptr;        // (p+1) x nm_count(p): N_n^m Pbar_n^m(v_j)
+  double* trig = nullptr;        // n_phi x (p+1) x 2: cos(m phi_k), sin(m phi_k)
+  double* sqrtw = nullptr;       // M x (p+1): sqrt(u0^2 + sgn v_j^2)
+  double* mult = nullptr;        // M x 4 x nm_count(p): extS, extD, selfS, selfD
+  double* normc = nullptr;       // (p+1)^2: N_n^|m| (sqrt 2 for m != 0) per coefficient
+  int32_t* pair_t = nullptr;     // near pairs: target node
+  int32_t* pair_s = nullptr;     // near pairs: source particle
+  int32_t* skip_ptr = nullptr;   // N+1 CSR of per-target skipped particles (own + near), ascending
+  int32_t* skip_idx = nullptr;
+  int4* tiles = nullptr;         // far source tiles (particle, first node, count, -)
+  double* inv = nullptr;         // 1/k, k < kInvTable (k = 0 holds 0)
+  float4* tgt32 = nullptr;       // N x 2: hi, lo parts of the global node position
+  float4* cen32 = nullptr;       // M x 2: hi, lo parts of the centres
+  // workspaces written by every apply
+  double* src64 = nullptr;       // N x 8: y - c_own (3), q, d (3), 0
+  float4* src32 = nullptr;       // N x 2: (y - c_own, q), (d, 0)
+  double* alpha = nullptr;       // M x (p+1)^2 folded exterior S coefficients
+  double* beta = nullptr;        // M x (p+1)^2 folded exterior D coefficients
+  double* host_in = nullptr;     // 2 x M x (p+1)^2 staging for the host-memory entry point
+  double* host_out = nullptr;    // 2 x N
+  // Stokes workspaces (allocated on first Stokes apply)
+  double* st_src64 = nullptr;    // N x 4: f * w (3), 0
+  float4* st_src32 = nullptr;    // N x 1: (f w)
+  double* st_coef = nullptr;     // M x 5 x (p+2)^2 folded coefficients (f1,f2,f3,y.f at p+1)
+  double* st_tab = nullptr;      // Stokes self tables
+};
+
+struct GeomHost {
+  int M = 0, p = 0, n_v = 0, n_phi = 0, G = 0;
+  int64_t N = 0;
+  double near_factor = 1.0;
+  int precision = SBIO_FP64;
+  std::vector<PartGeom> parts;
+  std::vector<double> xyz, nrm, w;
+  std::vector<int32_t> pair_t, pair_s;   // sorted by (kind, source, target)
+  int64_t n_pairs_prolate = 0;           // pairs [0, n_pairs_prolate) have prolate sources
+  int64_t far_pairs = 0;
+  std::vector<int4> tiles;
+};
+
+}  // namespace sbio
+
+struct sbio_geom {
+  sbio_ctx* ctx = nullptr;
+  sbio::GeomHost h;
+  sbio::DevGeom d;
+  size_t bytes = 0;
+  std::vector<void*> allocs;
+  cudaStream_t setup_stream = nullptr;
+  // optional phase timing: events recorded on the launch stream around the
+  // synth, near and far phases of the last apply
+  bool timing = false;
+  cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+};
+
+namespace sbio {
+
+// error reporting (thread-local message)
+int set_error(int code, const char* fmt, ...);
+void clear_error();
+void count_launch(int n = 1);
+
+// device allocation tracked against the context budget
+int dev_alloc(sbio_geom* g, void** ptr, size_t bytes, const char* what);
+
+struct DevGeom;
+typedef void (*near_launcher)(const DevGeom&, int64_t, int64_t, const double*, double*, double*, cudaStream_t);
+near_launcher near_lookup_a(int p);
+near_launcher near_lookup_b(int p);
+near_launcher near_lookup_c(int p);
+near_launcher near_lookup_d(int p);
+inline near_launcher near_for_p(int p) {
+  near_launcher f = near_lookup_a(p);
+  if (!f) f = near_lookup_b(p);
+  if (!f) f = near_lookup_c(p);
+  if (!f) f = near_lookup_d(p);
+  return f;
+}
+
+// record phase event k (0..3) when timing is enabled
+inline void phase_mark(sbio_geom* g, int k, cudaStream_t st) {
+  if (g->timing && g->ev[k]) cudaEventRecord(g->ev[k], st);
+}
+
+// kernel entry points (defined in the kernel translation units)
+int launch_laplace(sbio_geom* g, const double* sigma, const double* mu, double* S, double* D,
+                   uint32_t parts, cudaStream_t st);
+int launch_stokes(sbio_geom* g, const double* f, double* u, cudaStream_t st);
+
+}  // namespace sbio
+
+#define SBIO_CUDA_TRY(call)                                                                   \
+  do {                                                                                        \
+    cudaError_t err_ = (call);                                                                \
+    if (err_ != cudaSuccess)                                                                  \
+      return ::sbio::set_error(SBIO_ECUDA, "%s failed: %s (%s:%d)", #call, cudaGetErrorString(err_), \
+                               __FILE__, __LINE__);                                           \
+  } while (0)

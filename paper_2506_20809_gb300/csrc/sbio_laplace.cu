@@ -1,0 +1,431 @@
+// Laplace single / double layer apply at all surface nodes (Algorithm 1 and
+// its single-layer variant, Sec. 4.2), as three kernels on one stream:
+//   synth  : per particle, node values of the densities (inverse surface
+//            transform), the far-field source strengths q = w sigma and
+//            d = w mu nu, the folded near-field coefficients, and the self
+//            term (diagonal multipliers of Theorems 1-2 followed by the
+//            inverse transform), which initialises the outputs;
+//   near   : one thread per (target, near source particle) pair, exterior
+//            expansion (sbio_near.cuh), FP64, atomically added;
+//   far    : tiled all-pairs smooth quadrature over the nodes of far
+//            particles (Sec. 4.1 "Far-field"), FP64 or FP32 with two-sum
+//            compensated accumulation, atomically added.
+#include <algorithm>
+#include <vector>
+
+#include "sbio_internal.cuh"
+#include "sbio_near.cuh"
+
+namespace sbio {
+
+constexpr double kInv4Pi = 0.07957747154594767;   // 1/(4 pi)
+
+struct alignas(32) dbl4 {
+  double x, y, z, w;
+};
+
+// ---------------------------------------------------------------------------
+// synth: densities at the nodes, far-field sources, near coefficients, self
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) synth_kernel(int p, int n_v, int n_phi, const PartGeom* __restrict__ parts,
+                                                    const double* __restrict__ xyz, const double* __restrict__ nrm,
+                                                    const double* __restrict__ w, const double* __restrict__ ptab,
+                                                    const double* __restrict__ trig,
+                                                    const double* __restrict__ sqrtw,
+                                                    const double* __restrict__ mult,
+                                                    const double* __restrict__ normc,
+                                                    const double* __restrict__ sigma, const double* __restrict__ mu,
+                                                    int write_self, double* __restrict__ S_out,
+                                                    double* __restrict__ D_out, double* __restrict__ src64,
+                                                    float4* __restrict__ src32, double* __restrict__ alpha,
+                                                    double* __restrict__ beta) {
+  extern __shared__ double sm[];
+  const int i = blockIdx.x;
+  const int nc = (p + 1) * (p + 1), nm = nm_count(p), nmw = 2 * p + 1;
+  const int G = n_v * n_phi;
+  double* c_sig = sm;                 // nc
+  double* c_mu = c_sig + nc;          // nc
+  double* F = c_mu + nc;              // 4 x n_v x nmw: sigma, mu, S self, D self
+  const bool hs = sigma != nullptr, hm = mu != nullptr;
+  const double* mlt = mult + (size_t)i * 4 * nm;
+  for (int k = threadIdx.x; k < nc; k += blockDim.x) {
+    const int n = (int)sqrt((double)k);
+    const int m = k - n * n - n;
+    const int am = m < 0 ? -m : m;
+    const double cs = hs ? sigma[(size_t)i * nc + k] : 0.0;
+    const double cmu = hm ? mu[(size_t)i * nc + k] : 0.0;
+    c_sig[k] = cs;
+    c_mu[k] = cmu;
+    alpha[(size_t)i * nc + k] = mlt[0 * nm + nm_index(n, am)] * normc[k] * cs;
+    beta[(size_t)i * nc + k] = mlt[1 * nm + nm_index(n, am)] * normc[k] * cmu;
+  }
+  __syncthreads();
+  // stage 1: Legendre sums  F[j][m] = sum_n c_nm sqrt2^[m!=0] N P(v_j)
+  for (int idx = threadIdx.x; idx < n_v * nmw; idx += blockDim.x) {
+    const int j = idx / nmw, ms = idx - j * nmw, m = ms - p, am = m < 0 ? -m : m;
+    const double s2 = m ? 1.4142135623730951 : 1.0;
+    double fs = 0.0, fm = 0.0, fS = 0.0, fD = 0.0;
+    for (int n = am; n <= p; ++n) {
+      const int k = n * n + n + m;
+      const double pt = s2 * ptab[(size_t)j * nm + nm_index(n, am)];
+      const double a = c_sig[k] * pt, b = c_mu[k] * pt;
+      fs += a;
+      fm += b;
+      fS = fma(mlt[2 * nm + nm_index(n, am)], a, fS);
+      fD = fma(mlt[3 * nm + nm_index(n, am)], b, fD);
+    }
+    F[(0 * n_v + j) * nmw + ms] = fs;
+    F[(1 * n_v + j) * nmw + ms] = fm;
+    F[(2 * n_v + j) * nmw + ms] = fS;
+    F[(3 * n_v + j) * nmw + ms] = fD;
+  }
+  __syncthreads();
+  // stage 2: Fourier sums at every node of the particle
+  const PartGeom P = parts[i];
+  for (int l = threadIdx.x; l < G; l += blockDim.x) {
+    const int j = l / n_phi, k = l - j * n_phi;
+    const double* tr = trig + (size_t)k * (p + 1) * 2;
+    const double* f0 = F + (0 * n_v + j) * nmw + p;
+    const double* f1 = F + (1 * n_v + j) * nmw + p;
+    const double* f2 = F + (2 * n_v + j) * nmw + p;
+    const double* f3 = F + (3 * n_v + j) * nmw + p;
+    double vs = f0[0], vm = f1[0], vS = f2[0], vD = f3[0];
+    for (int m = 1; m <= p; ++m) {
+      const double cth = tr[2 * m], sth = tr[2 * m + 1];
+      vs = fma(f0[m], cth, fma(f0[-m], sth, vs));
+      vm = fma(f1[m], cth, fma(f1[-m], sth, vm));
+      vS = fma(f2[m], cth, fma(f2[-m], sth, vS));
+      vD = fma(f3[m], cth, fma(f3[-m], sth, vD));
+    }
+    const int64_t t = (int64_t)i * G + l;
+    const double sig_val = vs / sqrtw[(size_t)i * n_v + j];   // modified basis (Sec. 3.2)
+    const double q = w[t] * sig_val;
+    const double wm = w[t] * vm;
+    const double d0 = wm * nrm[t * 3 + 0], d1 = wm * nrm[t * 3 + 1], d2 = wm * nrm[t * 3 + 2];
+    const double y0 = xyz[t * 3 + 0] - P.c[0], y1 = xyz[t * 3 + 1] - P.c[1], y2 = xyz[t * 3 + 2] - P.c[2];
+    double* s = src64 + t * 8;
+    s[0] = y0; s[1] = y1; s[2] = y2; s[3] = q;
+    s[4] = d0; s[5] = d1; s[6] = d2; s[7] = 0.0;
+    src32[t * 2 + 0] = make_float4((float)y0, (float)y1, (float)y2, (float)q);
+    src32[t * 2 + 1] = make_float4((float)d0, (float)d1, (float)d2, 0.f);
+    if (S_out) S_out[t] = write_self ? vS : 0.0;
+    if (D_out) D_out[t] = write_self ? vD : 0.0;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// far: tiled all-pairs quadrature over far source nodes
+// ---------------------------------------------------------------------------
+
+// Knuth's TwoSum: s + e == a + b exactly.
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = a + b;
+  const float bb = s - a;
+  e = (a - (s - bb)) + (b - bb);
+}
+
+__device__ __forceinline__ float rsqrt_approx(float x) {
+  float r;
+  asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+
+// FP64 form: one target per thread, kFarTile sources per smem tile.
+template <bool DO_S, bool DO_D>
+__global__ void __launch_bounds__(kFarTile) far_fp64_kernel(const int4* __restrict__ tiles, int n_tiles,
+                                                            const double* __restrict__ src64,
+                                                            const double* __restrict__ xyz,
+                                                            const PartGeom* __restrict__ parts,
+                                                            const int32_t* __restrict__ skip_ptr,
+                                                            const int32_t* __restrict__ skip_idx, int64_t N,
+                                                            double* __restrict__ S_out, double* __restrict__ D_out) {
+  __shared__ dbl4 sh[kFarTile * 2];
+  const int64_t t = (int64_t)blockIdx.x * kFarTile + threadIdx.x;
+  const bool valid = t < N;
+  double x = 0, y = 0, z = 0;
+  int sp = 0, nxt = INT32_MAX;
+  if (valid) {
+    x = xyz[t * 3 + 0];
+    y = xyz[t * 3 + 1];
+    z = xyz[t * 3 + 2];
+    sp = skip_ptr[t];
+    nxt = skip_idx[sp];
+  }
+  double accS = 0.0, accD = 0.0;
+  int cur = -1;
+  bool skip = true;
+  double X = 0, Y = 0, Z = 0;
+  for (int tl = 0; tl < n_tiles; ++tl) {
+    const int4 tile = tiles[tl];
+    if (tile.x != cur) {
+      cur = tile.x;
+      if (valid) {
+        while (nxt < cur) nxt = skip_idx[++sp];
+        skip = (nxt == cur);
+        X = x - parts[cur].c[0];
+        Y = y - parts[cur].c[1];
+        Z = z - parts[cur].c[2];
+      }
+    }
+    if (__syncthreads_and(skip)) continue;
+    if (threadIdx.x < tile.z) {
+      const dbl4* s = reinterpret_cast<const dbl4*>(src64 + (int64_t)(tile.y + threadIdx.x) * 8);
+      sh[threadIdx.x * 2 + 0] = s[0];
+      sh[threadIdx.x * 2 + 1] = s[1];
+    }
+    __syncthreads();
+    if (!skip) {
+      for (int j = 0; j < tile.z; ++j) {
+        const dbl4 a = sh[j * 2], b = sh[j * 2 + 1];
+        const double dx = X - a.x, dy = Y - a.y, dz = Z - a.z;
+        const double r2 = dx * dx + dy * dy + dz * dz;
+        const double ri = rsqrt(r2);
+        if (DO_S) accS = fma(a.w, ri, accS);
+        if (DO_D) accD = fma((b.x * dx + b.y * dy + b.z * dz) * ri, ri * ri, accD);
+      }
+    }
+    __syncthreads();
+  }
+  if (valid) {
+    if (DO_S) atomicAdd(S_out + t, accS * kInv4Pi);
+    if (DO_D) atomicAdd(D_out + t, accD * kInv4Pi);
+  }
+}
+
+// Mixed form: FP32 pair sums, TT targets per thread.  The target position is
+// taken relative to each source particle's centre through hi/lo FP32 parts
+// (X = (x_hi - c_hi) + (x_lo - c_lo)), the sources are stored relative to
+// their own centre, so the FP32 difference X - y_rel carries an error
+// relative to |x - y| rather than to the box size.  Each tile's FP32 partial
+// sum is folded into an (hi, lo) pair by TwoSum.
+template <int TT, bool DO_S, bool DO_D>
+__global__ void __launch_bounds__(kFarTile) far_mixed_kernel(const int4* __restrict__ tiles, int n_tiles,
+                                                             const float4* __restrict__ src32,
+                                                             const float4* __restrict__ tgt32,
+                                                             const float4* __restrict__ cen32,
+                                                             const int32_t* __restrict__ skip_ptr,
+                                                             const int32_t* __restrict__ skip_idx, int64_t N,
+                                                             double* __restrict__ S_out, double* __restrict__ D_out) {
+  __shared__ float4 sh[kFarTile * 2];
+  int64_t tg[TT];
+  bool valid[TT];
+  float xh[TT][3], xo[TT][3];
+  int sp[TT], nxt[TT];
+#pragma unroll
+  for (int q = 0; q < TT; ++q) {
+    tg[q] = ((int64_t)blockIdx.x * TT + q) * kFarTile + threadIdx.x;
+    valid[q] = tg[q] < N;
+    xh[q][0] = xh[q][1] = xh[q][2] = 0.f;
+    xo[q][0] = xo[q][1] = xo[q][2] = 0.f;
+    sp[q] = 0;
+    nxt[q] = INT32_MAX;
+    if (valid[q]) {
+      const float4 hi = tgt32[tg[q] * 2], lo = tgt32[tg[q] * 2 + 1];
+      xh[q][0] = hi.x; xh[q][1] = hi.y; xh[q][2] = hi.z;
+      xo[q][0] = lo.x; xo[q][1] = lo.y; xo[q][2] = lo.z;
+      sp[q] = skip_ptr[tg[q]];
+      nxt[q] = skip_idx[sp[q]];
+    }
+  }
+  float sS[TT], eS[TT], sD[TT], eD[TT];
+  float X[TT], Y[TT], Z[TT];
+  bool skip[TT];
+#pragma unroll
+  for (int q = 0; q < TT; ++q) {
+    sS[q] = eS[q] = sD[q] = eD[q] = 0.f;
+    X[q] = Y[q] = Z[q] = 0.f;
+    skip[q] = true;
+  }
+  int cur = -1;
+  for (int tl = 0; tl < n_tiles; ++tl) {
+    const int4 tile = tiles[tl];
+    if (tile.x != cur) {
+      cur = tile.x;
+      const float4 ch = cen32[cur * 2], cl = cen32[cur * 2 + 1];
+#pragma unroll
+      for (int q = 0; q < TT; ++q) {
+        if (valid[q]) {
+          while (nxt[q] < cur) nxt[q] = skip_idx[++sp[q]];
+          skip[q] = (nxt[q] == cur);
+        }
+        X[q] = (xh[q][0] - ch.x) + (xo[q][0] - cl.x);
+        Y[q] = (xh[q][1] - ch.y) + (xo[q][1] - cl.y);
+        Z[q] = (xh[q][2] - ch.z) + (xo[q][2] - cl.z);
+      }
+    }
+    bool all_skip = true;
+#pragma unroll
+    for (int q = 0; q < TT; ++q) all_skip = all_skip && skip[q];
+    if (__syncthreads_and(all_skip)) continue;
+    if (threadIdx.x < tile.z) {
+      sh[threadIdx.x * 2 + 0] = src32[(int64_t)(tile.y + threadIdx.x) * 2 + 0];
+      sh[threadIdx.x * 2 + 1] = src32[(int64_t)(tile.y + threadIdx.x) * 2 + 1];
+    }
+    __syncthreads();
+    if (!all_skip) {
+      float pS[TT], pD[TT];
+#pragma unroll
+      for (int q = 0; q < TT; ++q) pS[q] = pD[q] = 0.f;
+#pragma unroll 4
+      for (int j = 0; j < tile.z; ++j) {
+        const float4 a = sh[j * 2], b = sh[j * 2 + 1];
+#pragma unroll
+        for (int q = 0; q < TT; ++q) {
+          const float dx = X[q] - a.x, dy = Y[q] - a.y, dz = Z[q] - a.z;
+          const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
+          const float ri = rsqrt_approx(r2);
+          if (DO_S) pS[q] = fmaf(a.w, ri, pS[q]);
+          if (DO_D) {
+            const float dn = fmaf(b.z, dz, fmaf(b.y, dy, b.x * dx));
+            pD[q] = fmaf(dn * ri, ri * ri, pD[q]);
+          }
+        }
+      }
+#pragma unroll
+      for (int q = 0; q < TT; ++q) {
+        if (!skip[q]) {
+          float s, e;
+          if (DO_S) {
+            two_sum(sS[q], pS[q], s, e);
+            sS[q] = s;
+            eS[q] += e;
+          }
+          if (DO_D) {
+            two_sum(sD[q], pD[q], s, e);
+            sD[q] = s;
+            eD[q] += e;
+          }
+        }
+      }
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int q = 0; q < TT; ++q) {
+    if (valid[q]) {
+      if (DO_S) atomicAdd(S_out + tg[q], ((double)sS[q] + (double)eS[q]) * kInv4Pi);
+      if (DO_D) atomicAdd(D_out + tg[q], ((double)sD[q] + (double)eD[q]) * kInv4Pi);
+    }
+  }
+}
+
+constexpr int kMixedTT = 2;
+
+static void launch_far(sbio_geom* g, double* S, double* D, cudaStream_t st) {
+  const DevGeom& d = g->d;
+  const GeomHost& h = g->h;
+  const int nt = (int)h.tiles.size();
+  if (h.precision == SBIO_FP64) {
+    const unsigned blocks = (unsigned)((h.N + kFarTile - 1) / kFarTile);
+    if (S && D)
+      far_fp64_kernel<true, true><<<blocks, kFarTile, 0, st>>>(d.tiles, nt, d.src64, d.xyz, d.parts, d.skip_ptr,
+                                                               d.skip_idx, h.N, S, D);
+    else if (S)
+      far_fp64_kernel<true, false><<<blocks, kFarTile, 0, st>>>(d.tiles, nt, d.src64, d.xyz, d.parts, d.skip_ptr,
+                                                                d.skip_idx, h.N, S, D);
+    else
+      far_fp64_kernel<false, true><<<blocks, kFarTile, 0, st>>>(d.tiles, nt, d.src64, d.xyz, d.parts, d.skip_ptr,
+                                                                d.skip_idx, h.N, S, D);
+  } else {
+    const unsigned blocks = (unsigned)((h.N + kFarTile * kMixedTT - 1) / (kFarTile * kMixedTT));
+    if (S && D)
+      far_mixed_kernel<kMixedTT, true, true><<<blocks, kFarTile, 0, st>>>(d.tiles, nt, d.src32, d.tgt32, d.cen32,
+                                                                          d.skip_ptr, d.skip_idx, h.N, S, D);
+    else if (S)
+      far_mixed_kernel<kMixedTT, true, false><<<blocks, kFarTile, 0, st>>>(d.tiles, nt, d.src32, d.tgt32, d.cen32,
+                                                                           d.skip_ptr, d.skip_idx, h.N, S, D);
+    else
+      far_mixed_kernel<kMixedTT, false, true><<<blocks, kFarTile, 0, st>>>(d.tiles, nt, d.src32, d.tgt32, d.cen32,
+                                                                           d.skip_ptr, d.skip_idx, h.N, S, D);
+  }
+  count_launch();
+}
+
+int launch_laplace(sbio_geom* g, const double* sigma, const double* mu, double* S, double* D, uint32_t parts,
+                   cudaStream_t st) {
+  const GeomHost& h = g->h;
+  const DevGeom& d = g->d;
+  const double* inv = d.inv;
+  const int nmw = 2 * h.p + 1, nc = (h.p + 1) * (h.p + 1);
+  const size_t smem = (size_t)(2 * nc + 4 * h.n_v * nmw) * sizeof(double);
+  phase_mark(g, 0, st);
+  if (smem > 48 * 1024) {
+    SBIO_CUDA_TRY(cudaFuncSetAttribute(synth_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  }
+  synth_kernel<<<h.M, 256, smem, st>>>(h.p, h.n_v, h.n_phi, d.parts, d.xyz, d.nrm, d.w, d.ptab, d.trig, d.sqrtw,
+                                       d.mult, d.normc, sigma, mu, (parts & SBIO_PART_SELF) ? 1 : 0, S, D, d.src64,
+                                       d.src32, d.alpha, d.beta);
+  count_launch();
+  SBIO_CUDA_TRY(cudaGetLastError());
+  phase_mark(g, 1, st);
+  if ((parts & SBIO_PART_NEAR) && !h.pair_t.empty()) {
+    near_launcher f = near_for_p(h.p);
+    if (!f) return set_error(SBIO_ENOTSUP, "no near-field kernel for p = %d", h.p);
+    f(d, h.n_pairs_prolate, (int64_t)h.pair_t.size(), inv, S, D, st);
+    SBIO_CUDA_TRY(cudaGetLastError());
+  }
+  phase_mark(g, 2, st);
+  if (parts & SBIO_PART_FAR) {
+    launch_far(g, S, D, st);
+    SBIO_CUDA_TRY(cudaGetLastError());
+  }
+  phase_mark(g, 3, st);
+  return SBIO_OK;
+}
+
+}  // namespace sbio
+
+using namespace sbio;
+
+extern "C" {
+
+int sbio_apply_laplace_parts(sbio_geom* g, const double* sigma_tilde, const double* mu_hat, double* S_out,
+                             double* D_out, uint32_t parts, void* stream) {
+  clear_error();
+  if (!g) return set_error(SBIO_EINVAL, "null geometry");
+  if ((sigma_tilde == nullptr) != (S_out == nullptr) || (mu_hat == nullptr) != (D_out == nullptr))
+    return set_error(SBIO_EINVAL, "each output must be given exactly when its input is");
+  if (!sigma_tilde && !mu_hat) return set_error(SBIO_EINVAL, "nothing to apply");
+  if (parts & ~SBIO_PART_ALL) return set_error(SBIO_EINVAL, "unknown part bits 0x%x", parts);
+  SBIO_CUDA_TRY(cudaSetDevice(g->ctx->device));
+  return launch_laplace(g, sigma_tilde, mu_hat, S_out, D_out, parts, (cudaStream_t)stream);
+}
+
+int sbio_apply_laplace(sbio_geom* g, const double* sigma_tilde, const double* mu_hat, double* S_out, double* D_out,
+                       void* stream) {
+  return sbio_apply_laplace_parts(g, sigma_tilde, mu_hat, S_out, D_out, SBIO_PART_ALL, stream);
+}
+
+int sbio_apply_laplace_host(sbio_geom* g, const double* sigma_host, const double* mu_host, double* S_host,
+                            double* D_host, void* stream) {
+  clear_error();
+  if (!g) return set_error(SBIO_EINVAL, "null geometry");
+  if ((sigma_host == nullptr) != (S_host == nullptr) || (mu_host == nullptr) != (D_host == nullptr))
+    return set_error(SBIO_EINVAL, "each output must be given exactly when its input is");
+  if (!sigma_host && !mu_host) return set_error(SBIO_EINVAL, "nothing to apply");
+  SBIO_CUDA_TRY(cudaSetDevice(g->ctx->device));
+  cudaStream_t st = (cudaStream_t)stream;
+  const size_t nc = (size_t)(g->h.p + 1) * (g->h.p + 1) * g->h.M;
+  const size_t N = (size_t)g->h.N;
+  double* ds = sigma_host ? g->d.host_in : nullptr;
+  double* dm = mu_host ? g->d.host_in + nc : nullptr;
+  double* oS = S_host ? g->d.host_out : nullptr;
+  double* oD = D_host ? g->d.host_out + N : nullptr;
+  if (ds) SBIO_CUDA_TRY(cudaMemcpyAsync(ds, sigma_host, nc * sizeof(double), cudaMemcpyHostToDevice, st));
+  if (dm) SBIO_CUDA_TRY(cudaMemcpyAsync(dm, mu_host, nc * sizeof(double), cudaMemcpyHostToDevice, st));
+  int rc = launch_laplace(g, ds, dm, oS, oD, SBIO_PART_ALL, st);
+  if (rc) return rc;
+  if (oS) SBIO_CUDA_TRY(cudaMemcpyAsync(S_host, oS, N * sizeof(double), cudaMemcpyDeviceToHost, st));
+  if (oD) SBIO_CUDA_TRY(cudaMemcpyAsync(D_host, oD, N * sizeof(double), cudaMemcpyDeviceToHost, st));
+  SBIO_CUDA_TRY(cudaStreamSynchronize(st));
+  return SBIO_OK;
+}
+
+int sbio_apply_stokes_sl(sbio_geom* g, const double* f_tilde, double* u_out, void* stream) {
+  clear_error();
+  if (!g || !f_tilde || !u_out) return set_error(SBIO_EINVAL, "null argument");
+  SBIO_CUDA_TRY(cudaSetDevice(g->ctx->device));
+  return launch_stokes(g, f_tilde, u_out, (cudaStream_t)stream);
+}
+
+}  // extern "C"

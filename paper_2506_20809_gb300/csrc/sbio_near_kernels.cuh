@@ -1,0 +1,76 @@
+// Near-field kernel templates and their launchers; instantiated for ranges of
+// the expansion order p in the sbio_near_p*.cu translation units so that the
+// fully unrolled variants compile in parallel.
+#pragma once
+
+#include "sbio_internal.cuh"
+#include "sbio_near.cuh"
+
+namespace sbio {
+
+// ---------------------------------------------------------------------------
+// near: one thread per (target, near source) pair
+// ---------------------------------------------------------------------------
+template <int P, int KIND, bool DO_S, bool DO_D>
+__global__ void __launch_bounds__(128) near_kernel(const int32_t* __restrict__ pair_t,
+                                                   const int32_t* __restrict__ pair_s, int64_t first, int64_t count,
+                                                   const PartGeom* __restrict__ parts, const double* __restrict__ xyz,
+                                                   const double* __restrict__ alpha,
+                                                   const double* __restrict__ beta,
+                                                   const double* __restrict__ inv_tab, double* __restrict__ S_out,
+                                                   double* __restrict__ D_out) {
+  const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= count) return;
+  const int64_t idx = first + r;
+  const int t = pair_t[idx], i = pair_s[idx];
+  const PartGeom& G = parts[i];
+  const double dx = xyz[(int64_t)t * 3 + 0] - G.c[0];
+  const double dy = xyz[(int64_t)t * 3 + 1] - G.c[1];
+  const double dz = xyz[(int64_t)t * 3 + 2] - G.c[2];
+  const double xl = G.R[0] * dx + G.R[3] * dy + G.R[6] * dz;
+  const double yl = G.R[1] * dx + G.R[4] * dy + G.R[7] * dz;
+  const double zl = G.R[2] * dx + G.R[5] * dy + G.R[8] * dz;
+  constexpr int NC = (P + 1) * (P + 1);
+  double S, D;
+  near_pair<P, KIND, DO_S, DO_D>(xl, yl, zl, G.a, alpha + (size_t)i * NC, beta + (size_t)i * NC, inv_tab, S, D);
+  if (DO_S) atomicAdd(S_out + t, S);
+  if (DO_D) atomicAdd(D_out + t, D);
+}
+
+template <int P, int KIND>
+static void launch_near_pk(const DevGeom& d, int64_t first, int64_t count, const double* inv_tab, double* S,
+                           double* D, cudaStream_t st) {
+  if (count <= 0) return;
+  const int threads = 128;
+  const unsigned blocks = (unsigned)((count + threads - 1) / threads);
+  if (S && D)
+    near_kernel<P, KIND, true, true><<<blocks, threads, 0, st>>>(d.pair_t, d.pair_s, first, count, d.parts, d.xyz,
+                                                                 d.alpha, d.beta, inv_tab, S, D);
+  else if (S)
+    near_kernel<P, KIND, true, false><<<blocks, threads, 0, st>>>(d.pair_t, d.pair_s, first, count, d.parts, d.xyz,
+                                                                  d.alpha, d.beta, inv_tab, S, D);
+  else
+    near_kernel<P, KIND, false, true><<<blocks, threads, 0, st>>>(d.pair_t, d.pair_s, first, count, d.parts, d.xyz,
+                                                                  d.alpha, d.beta, inv_tab, S, D);
+  count_launch();
+}
+
+template <int P>
+static void launch_near_p(const DevGeom& d, int64_t n_pro, int64_t n_all, const double* inv_tab, double* S,
+                          double* D, cudaStream_t st) {
+  launch_near_pk<P, SBIO_PROLATE>(d, 0, n_pro, inv_tab, S, D, st);
+  launch_near_pk<P, SBIO_OBLATE>(d, n_pro, n_all - n_pro, inv_tab, S, D, st);
+}
+
+template <int... Ps>
+struct NearTable {
+  static near_launcher get(int p) {
+    near_launcher tab[] = {launch_near_p<Ps>...};
+    int ps[] = {Ps...};
+    for (size_t k = 0; k < sizeof(ps) / sizeof(int); ++k)
+      if (ps[k] == p) return tab[k];
+    return nullptr;
+  }
+};
+
+}  // namespace sbio

@@ -1,0 +1,263 @@
+"""ctypes binding of libsbio.so (the C ABI declared in include/sbio.h).
+
+Argument marshalling only: every computation runs in the library's CUDA
+kernels.  Device buffers are passed as torch CUDA tensors (raw pointers are
+taken from them), streams as torch.cuda.Stream or raw handles.  Importing this
+module raises if the compiled library is missing: there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libsbio.so")
+
+SBIO_OK = 0
+SBIO_EINVAL = -1
+SBIO_EOVERLAP = -2
+SBIO_ENOMEM = -3
+SBIO_ECUDA = -4
+SBIO_ETIMEOUT = -5
+SBIO_ENOTSUP = -6
+SBIO_PROLATE = 0
+SBIO_OBLATE = 1
+SBIO_FP64 = 0
+SBIO_MIXED = 1
+SBIO_PART_SELF = 1
+SBIO_PART_NEAR = 2
+SBIO_PART_FAR = 4
+SBIO_PART_ALL = 7
+SBIO_MAX_P = 24
+
+ERRNAMES = {0: "SBIO_OK", -1: "SBIO_EINVAL", -2: "SBIO_EOVERLAP", -3: "SBIO_ENOMEM", -4: "SBIO_ECUDA",
+            -5: "SBIO_ETIMEOUT", -6: "SBIO_ENOTSUP"}
+
+
+class sbio_spheroid(C.Structure):
+    _fields_ = [("kind", C.c_int32), ("reserved", C.c_int32), ("A", C.c_double), ("C", C.c_double),
+                ("center", C.c_double * 3), ("quat", C.c_double * 4)]
+
+
+class sbio_options(C.Structure):
+    _fields_ = [("p", C.c_int32), ("n_phi", C.c_int32), ("near_factor", C.c_double),
+                ("far_upsample", C.c_int32), ("precision", C.c_int32)]
+
+
+class SbioError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{ERRNAMES.get(code, code)}: {msg}")
+        self.code = code
+
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(f"libsbio.so not built at {LIB_PATH}; run __graft_entry__.build() "
+                      "(python -m paper_2506_20809_gb300.build)")
+
+_lib = C.CDLL(LIB_PATH)
+
+_vp = C.c_void_p
+_SIGS = {
+    "sbio_version": (C.c_char_p, []),
+    "sbio_last_error": (C.c_char_p, [_vp]),
+    "sbio_launch_count": (C.c_int64, []),
+    "sbio_ctx_create": (C.c_int, [C.c_int, C.c_size_t, C.POINTER(_vp)]),
+    "sbio_ctx_destroy": (C.c_int, [_vp]),
+    "sbio_ctx_mem_used": (C.c_int, [_vp, C.POINTER(C.c_size_t)]),
+    "sbio_geom_create": (C.c_int, [_vp, C.POINTER(sbio_spheroid), C.c_int32, C.POINTER(sbio_options), _vp,
+                                   C.POINTER(_vp)]),
+    "sbio_geom_destroy": (C.c_int, [_vp]),
+    "sbio_geom_info": (C.c_int, [_vp, C.POINTER(C.c_int64), C.POINTER(C.c_int64), C.POINTER(C.c_int64),
+                                 C.POINTER(C.c_size_t)]),
+    "sbio_geom_nodes": (C.c_int, [_vp, _vp, _vp, _vp]),
+    "sbio_geom_near_pairs": (C.c_int, [_vp, _vp, _vp]),
+    "sbio_geom_set_precision": (C.c_int, [_vp, C.c_int32]),
+    "sbio_geom_enable_timing": (C.c_int, [_vp, C.c_int32]),
+    "sbio_geom_phase_times": (C.c_int, [_vp, C.POINTER(C.c_double), C.POINTER(C.c_double),
+                                        C.POINTER(C.c_double)]),
+    "sbio_apply_laplace": (C.c_int, [_vp, _vp, _vp, _vp, _vp, _vp]),
+    "sbio_apply_laplace_parts": (C.c_int, [_vp, _vp, _vp, _vp, _vp, C.c_uint32, _vp]),
+    "sbio_apply_laplace_host": (C.c_int, [_vp, _vp, _vp, _vp, _vp, _vp]),
+    "sbio_apply_stokes_sl": (C.c_int, [_vp, _vp, _vp, _vp]),
+}
+
+EXPORTED = []
+for _name, (_res, _args) in _SIGS.items():
+    _f = getattr(_lib, _name)
+    _f.restype = _res
+    _f.argtypes = _args
+    EXPORTED.append(_name)
+
+
+def _check(code):
+    if code != SBIO_OK:
+        raise SbioError(code, _lib.sbio_last_error(None).decode())
+    return code
+
+
+def _ptr(t):
+    """Raw address of a torch tensor / numpy array / None."""
+    if t is None:
+        return None
+    if isinstance(t, np.ndarray):
+        return t.ctypes.data
+    return t.data_ptr()
+
+
+def _stream(s):
+    if s is None:
+        try:
+            import torch
+            return torch.cuda.current_stream().cuda_stream
+        except Exception:
+            return None
+    if isinstance(s, int):
+        return s
+    return s.cuda_stream
+
+
+# ---- same-name thin wrappers -------------------------------------------------
+
+def sbio_version() -> str:
+    return _lib.sbio_version().decode()
+
+
+def sbio_last_error() -> str:
+    return _lib.sbio_last_error(None).decode()
+
+
+def sbio_launch_count() -> int:
+    return int(_lib.sbio_launch_count())
+
+
+def sbio_ctx_create(device: int = 0, mem_budget_bytes: int = 0):
+    h = _vp()
+    _check(_lib.sbio_ctx_create(device, mem_budget_bytes, C.byref(h)))
+    return h
+
+
+def sbio_ctx_destroy(ctx):
+    _check(_lib.sbio_ctx_destroy(ctx))
+
+
+def sbio_ctx_mem_used(ctx) -> int:
+    b = C.c_size_t()
+    _check(_lib.sbio_ctx_mem_used(ctx, C.byref(b)))
+    return int(b.value)
+
+
+def make_spheroids(kind, A, Cax, center, quat):
+    M = len(kind)
+    arr = (sbio_spheroid * M)()
+    for i in range(M):
+        arr[i].kind = int(kind[i])
+        arr[i].A = float(A[i])
+        arr[i].C = float(Cax[i])
+        for k in range(3):
+            arr[i].center[k] = float(center[i][k])
+        for k in range(4):
+            arr[i].quat[k] = float(quat[i][k])
+    return arr
+
+
+def sbio_geom_create(ctx, spheroids, p, n_phi=0, near_factor=1.0, precision=SBIO_FP64, stream=None,
+                     far_upsample=1):
+    opts = sbio_options(p, n_phi, near_factor, far_upsample, precision)
+    h = _vp()
+    _check(_lib.sbio_geom_create(ctx, spheroids, len(spheroids), C.byref(opts), _stream(stream), C.byref(h)))
+    return h
+
+
+def sbio_geom_destroy(g):
+    _check(_lib.sbio_geom_destroy(g))
+
+
+def sbio_geom_info(g):
+    nt, nn, nf, b = C.c_int64(), C.c_int64(), C.c_int64(), C.c_size_t()
+    _check(_lib.sbio_geom_info(g, C.byref(nt), C.byref(nn), C.byref(nf), C.byref(b)))
+    return {"n_targets": nt.value, "n_near_pairs": nn.value, "n_far_pairs": nf.value, "device_bytes": b.value}
+
+
+def sbio_geom_nodes(g):
+    n = sbio_geom_info(g)["n_targets"]
+    xyz = np.zeros((n, 3))
+    nrm = np.zeros((n, 3))
+    w = np.zeros(n)
+    _check(_lib.sbio_geom_nodes(g, xyz.ctypes.data, nrm.ctypes.data, w.ctypes.data))
+    return xyz, nrm, w
+
+
+def sbio_geom_near_pairs(g):
+    n = sbio_geom_info(g)["n_near_pairs"]
+    t = np.zeros(n, dtype=np.int32)
+    s = np.zeros(n, dtype=np.int32)
+    _check(_lib.sbio_geom_near_pairs(g, t.ctypes.data, s.ctypes.data))
+    return t, s
+
+
+def sbio_geom_set_precision(g, precision):
+    _check(_lib.sbio_geom_set_precision(g, precision))
+
+
+def sbio_geom_enable_timing(g, on=True):
+    _check(_lib.sbio_geom_enable_timing(g, 1 if on else 0))
+
+
+def sbio_geom_phase_times(g):
+    """(synth, near, far) milliseconds of the last apply (timing enabled)."""
+    a, b, c = C.c_double(), C.c_double(), C.c_double()
+    _check(_lib.sbio_geom_phase_times(g, C.byref(a), C.byref(b), C.byref(c)))
+    return a.value, b.value, c.value
+
+
+def sbio_apply_laplace(g, sigma_tilde, mu_hat, S_out, D_out, stream=None):
+    _check(_lib.sbio_apply_laplace(g, _ptr(sigma_tilde), _ptr(mu_hat), _ptr(S_out), _ptr(D_out), _stream(stream)))
+
+
+def sbio_apply_laplace_parts(g, sigma_tilde, mu_hat, S_out, D_out, parts, stream=None):
+    _check(_lib.sbio_apply_laplace_parts(g, _ptr(sigma_tilde), _ptr(mu_hat), _ptr(S_out), _ptr(D_out), parts,
+                                         _stream(stream)))
+
+
+def sbio_apply_laplace_host(g, sigma_tilde, mu_hat, S_out, D_out, stream=None):
+    """Host numpy arrays in and out (C-contiguous float64)."""
+    for a in (sigma_tilde, mu_hat, S_out, D_out):
+        if a is not None:
+            assert a.dtype == np.float64 and a.flags.c_contiguous
+    _check(_lib.sbio_apply_laplace_host(g, _ptr(sigma_tilde), _ptr(mu_hat), _ptr(S_out), _ptr(D_out),
+                                        _stream(stream)))
+
+
+def sbio_apply_stokes_sl(g, f_tilde, u_out, stream=None):
+    _check(_lib.sbio_apply_stokes_sl(g, _ptr(f_tilde), _ptr(u_out), _stream(stream)))
+
+
+# ---- convenience object ------------------------------------------------------
+
+class Geometry:
+    """Resident geometry of one suspension (owns its library handle)."""
+
+    def __init__(self, ctx, susp, p=None, near_factor=1.0, precision=SBIO_FP64, n_phi=0, stream=None):
+        self.ctx = ctx
+        self.p = susp.p if p is None else p
+        sph = make_spheroids(susp.kind, susp.A, susp.C, susp.center, susp.quat)
+        self.h = sbio_geom_create(ctx, sph, self.p, n_phi, near_factor, precision, stream)
+        self.M = len(sph)
+        info = sbio_geom_info(self.h)
+        self.N = info["n_targets"]
+        self.n_near = info["n_near_pairs"]
+        self.n_far = info["n_far_pairs"]
+        self.device_bytes = info["device_bytes"]
+
+    def close(self):
+        if self.h:
+            sbio_geom_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

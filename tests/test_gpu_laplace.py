@@ -1,0 +1,224 @@
+"""GPU parity of the Laplace apply (C ABI) against the CPU oracle.
+
+FP64 path: normwise relative error <= 1e-10 against the oracle's O-method
+(same nodes, same near sets, analytic self + near, smooth far quadrature).
+Mixed path: normwise relative error <= 1e-6 against the GPU FP64 path."""
+import math
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from oracle import geometry as OG
+from oracle import laplace as OL
+from paper_2506_20809_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+TOL64 = 1e-10
+TOLMIX = 1e-6
+
+
+@pytest.fixture(scope="module")
+def S():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    import __graft_entry__ as G
+
+    G.build()
+    import paper_2506_20809_gb300.sbio as S
+
+    return S
+
+
+@pytest.fixture(scope="module")
+def ctx(S):
+    c = S.sbio_ctx_create(0, 0)
+    yield c
+
+
+def gpu_apply(S, geom, sig, mu, parts=7, precision=None):
+    if precision is not None:
+        S.sbio_geom_set_precision(geom.h, precision)
+    sg = None if sig is None else torch.from_numpy(np.ascontiguousarray(sig)).cuda()
+    mg = None if mu is None else torch.from_numpy(np.ascontiguousarray(mu)).cuda()
+    So = None if sig is None else torch.full((geom.N,), float("nan"), dtype=torch.float64, device="cuda")
+    Do = None if mu is None else torch.full((geom.N,), float("nan"), dtype=torch.float64, device="cuda")
+    S.sbio_apply_laplace_parts(geom.h, sg, mg, So, Do, parts)
+    torch.cuda.synchronize()
+    return (None if So is None else So.cpu().numpy(), None if Do is None else Do.cpu().numpy())
+
+
+def small_suspension(seed, M=3, p=5, ar=(1.3, 4.0)):
+    s = I.rsa_suspension(M, 0.12, seed, p, ar_range=ar, min_gap=0.05, name="small")
+    return s
+
+
+@pytest.fixture(scope="module")
+def lattice(S, ctx):
+    s = I.config_suspension(1)
+    c = I.config_coefficients(s, 0)
+    g = S.Geometry(ctx, s)
+    og = OG.SuspensionGeom.from_suspension(s)
+    return s, c, g, og, OL.LaplaceOracle(og)
+
+
+def test_nodes_and_near_sets_match_oracle(S, lattice):
+    s, c, g, og, O = lattice
+    xyz, nrm, w = S.sbio_geom_nodes(g.h)
+    np.testing.assert_allclose(xyz, og.x, atol=1e-13)
+    np.testing.assert_allclose(nrm, np.concatenate([P.nrm for P in og.parts]), atol=1e-13)
+    np.testing.assert_allclose(w, np.concatenate([P.w for P in og.parts]), rtol=1e-13)
+    t, src = S.sbio_geom_near_pairs(g.h)
+    lib_pairs = set(zip(t.tolist(), src.tolist()))
+    nt, ns = np.nonzero(og.near_matrix())
+    assert lib_pairs == set(zip(nt.tolist(), ns.tolist()))
+    assert g.n_far == O.far_pair_count()
+
+
+@pytest.mark.parametrize("parts,name", [(1, "self"), (2, "near"), (4, "far"), (7, "all")])
+def test_lattice_fp64_parts(S, lattice, parts, name):
+    s, c, g, og, O = lattice
+    sel = {1: ("self",), 2: ("near",), 4: ("far",), 7: ("self", "near", "far")}[parts]
+    Sr, Dr = O.apply(c[0], c[1], "method", parts=sel)
+    Sg, Dg = gpu_apply(S, g, c[0], c[1], parts, S.SBIO_FP64)
+    assert OL.normwise_rel_err(Sg, Sr) < TOL64, name
+    assert OL.normwise_rel_err(Dg, Dr) < TOL64, name
+
+
+def test_lattice_mixed(S, lattice):
+    s, c, g, og, O = lattice
+    S64, D64 = gpu_apply(S, g, c[0], c[1], 7, S.SBIO_FP64)
+    Sm, Dm = gpu_apply(S, g, c[0], c[1], 7, S.SBIO_MIXED)
+    S.sbio_geom_set_precision(g.h, S.SBIO_FP64)
+    assert OL.normwise_rel_err(Sm, S64) < TOLMIX
+    assert OL.normwise_rel_err(Dm, D64) < TOLMIX
+
+
+def test_single_operators(S, lattice):
+    s, c, g, og, O = lattice
+    Sr, _ = O.apply(c[0], None, "method")
+    _, Dr = O.apply(None, c[1], "method")
+    Sg, _ = gpu_apply(S, g, c[0], None)
+    _, Dg = gpu_apply(S, g, None, c[1])
+    assert OL.normwise_rel_err(Sg, Sr) < TOL64
+    assert OL.normwise_rel_err(Dg, Dr) < TOL64
+
+
+def test_host_memory_entry_point(S, lattice):
+    s, c, g, og, O = lattice
+    Sd, Dd = gpu_apply(S, g, c[0], c[1])
+    Sh = np.zeros(g.N)
+    Dh = np.zeros(g.N)
+    S.sbio_apply_laplace_host(g.h, np.ascontiguousarray(c[0]), np.ascontiguousarray(c[1]), Sh, Dh)
+    np.testing.assert_allclose(Sh, Sd, rtol=0, atol=1e-14 * np.abs(Sd).max())
+    np.testing.assert_allclose(Dh, Dd, rtol=0, atol=1e-14 * np.abs(Dd).max())
+
+
+@pytest.mark.parametrize("p", [1, 2, 3, 5, 7, 10, 13, 16, 19, 22, 24])
+def test_orders_ragged(S, ctx, p):
+    """Every compiled order, on a close 3-particle cluster (ragged tiles)."""
+    s = small_suspension(100 + p, M=3, p=p)
+    rng = np.random.default_rng(p)
+    sig = I.coefficients(rng, 3, p)
+    mu = I.coefficients(rng, 3, p)
+    g = S.Geometry(ctx, s, near_factor=2.0)
+    O = OL.LaplaceOracle(OG.SuspensionGeom.from_suspension(s, near_factor=2.0))
+    Sr, Dr = O.apply(sig, mu, "method")
+    Sg, Dg = gpu_apply(S, g, sig, mu, 7, S.SBIO_FP64)
+    assert g.n_near > 0
+    assert OL.normwise_rel_err(Sg, Sr) < TOL64
+    assert OL.normwise_rel_err(Dg, Dr) < TOL64
+    g.close()
+
+
+def test_single_particle_self_only(S, ctx):
+    s = I.Suspension(np.array([1], np.int32), np.array([1.3]), np.array([0.5]), np.zeros((1, 3)),
+                     np.array([[0.9, 0.1, -0.3, 0.2]]) / np.linalg.norm([0.9, 0.1, -0.3, 0.2]), 6)
+    rng = np.random.default_rng(0)
+    sig = I.coefficients(rng, 1, 6)
+    mu = I.coefficients(rng, 1, 6)
+    g = S.Geometry(ctx, s)
+    O = OL.LaplaceOracle(OG.SuspensionGeom.from_suspension(s))
+    Sr, Dr = O.apply(sig, mu, "method")
+    Sg, Dg = gpu_apply(S, g, sig, mu)
+    assert g.n_near == 0 and g.n_far == 0
+    assert OL.normwise_rel_err(Sg, Sr) < TOL64 and OL.normwise_rel_err(Dg, Dr) < TOL64
+    # Gauss: D[1] = -1/2 on the surface
+    mu1 = np.zeros_like(mu)
+    mu1[0, 0] = math.sqrt(4 * math.pi)
+    _, D1 = gpu_apply(S, g, None, mu1)
+    np.testing.assert_allclose(D1, -0.5, atol=1e-13)
+    g.close()
+
+
+def test_paper_style_nonuniform_phi_grid(S, ctx):
+    """n_phi = 2p as printed in Sec. 4 (aliasing of sin(p phi) is the user's)."""
+    s = small_suspension(7, M=3, p=6)
+    rng = np.random.default_rng(1)
+    sig = I.coefficients(rng, 3, 6)
+    mu = I.coefficients(rng, 3, 6)
+    g = S.Geometry(ctx, s, n_phi=12)
+    O = OL.LaplaceOracle(OG.SuspensionGeom.from_suspension(s, n_phi=12))
+    Sr, Dr = O.apply(sig, mu, "method")
+    Sg, Dg = gpu_apply(S, g, sig, mu)
+    assert OL.normwise_rel_err(Sg, Sr) < TOL64 and OL.normwise_rel_err(Dg, Dr) < TOL64
+    g.close()
+
+
+def test_invalid_inputs(S, ctx):
+    base = small_suspension(3, M=2, p=4)
+    sph = S.make_spheroids(base.kind, base.A, base.C, base.center, base.quat)
+    with pytest.raises(S.SbioError) as e:
+        S.sbio_geom_create(ctx, sph, 0)
+    assert e.value.code == S.SBIO_EINVAL
+    with pytest.raises(S.SbioError) as e:
+        S.sbio_geom_create(ctx, sph, 4, far_upsample=2)
+    assert e.value.code == S.SBIO_ENOTSUP
+    bad = S.make_spheroids(base.kind, base.A, base.C, np.zeros((2, 3)), base.quat)   # same centre
+    with pytest.raises(S.SbioError) as e:
+        S.sbio_geom_create(ctx, bad, 4)
+    assert e.value.code == S.SBIO_EOVERLAP
+    sphere = S.make_spheroids([0], [1.0], [1.0], [[0, 0, 0]], [[1, 0, 0, 0]])
+    with pytest.raises(S.SbioError) as e:
+        S.sbio_geom_create(ctx, sphere, 4)
+    assert e.value.code == S.SBIO_EINVAL
+    small_budget = S.sbio_ctx_create(0, 4096)
+    with pytest.raises(S.SbioError) as e:
+        S.sbio_geom_create(small_budget, sph, 4)
+    assert e.value.code == S.SBIO_ENOMEM
+    assert S.sbio_ctx_mem_used(small_budget) == 0
+    S.sbio_ctx_destroy(small_budget)
+
+
+@pytest.fixture(scope="module")
+def poly200(S, ctx):
+    s = I.config_suspension(2)
+    c = I.config_coefficients(s, 0)
+    g = S.Geometry(ctx, s)
+    og = OG.SuspensionGeom.from_suspension(s)
+    return s, c, g, og
+
+
+def test_poly200_sampled_fp64(S, poly200):
+    """Full 200-spheroid, p = 16 workload in the benchmark's launch
+    configuration; the oracle evaluates a sample of targets one by one."""
+    s, c, g, og = poly200
+    Sg, Dg = gpu_apply(S, g, c[0], c[1], 7, S.SBIO_FP64)
+    rng = np.random.default_rng(0)
+    tg = np.sort(rng.choice(g.N, 240, replace=False))
+    O = OL.LaplaceOracle(og)
+    Sr, Dr = O.apply(c[0], c[1], "method", targets=tg)
+    # normwise over the sample, relative to the max over all targets
+    assert np.max(np.abs(Sg[tg] - Sr)) / np.max(np.abs(Sg)) < TOL64
+    assert np.max(np.abs(Dg[tg] - Dr)) / np.max(np.abs(Dg)) < TOL64
+
+
+def test_poly200_mixed_vs_fp64(S, poly200):
+    s, c, g, og = poly200
+    S64, D64 = gpu_apply(S, g, c[0], c[1], 7, S.SBIO_FP64)
+    Sm, Dm = gpu_apply(S, g, c[0], c[1], 7, S.SBIO_MIXED)
+    S.sbio_geom_set_precision(g.h, S.SBIO_FP64)
+    eS, eD = OL.normwise_rel_err(Sm, S64), OL.normwise_rel_err(Dm, D64)
+    print(f"mixed vs fp64: S {eS:.3e} D {eD:.3e}")
+    assert eS < TOLMIX and eD < TOLMIX
