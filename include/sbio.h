@@ -195,6 +195,35 @@ int sbio_apply_laplace_host(sbio_geom* g, const double* sigma_tilde_host, const 
  * u_out: device, N x 3 FP64 (row t = velocity at node t).  Asynchronous. */
 int sbio_apply_stokes_sl(sbio_geom* g, const double* f_tilde, double* u_out, void* stream);
 
+/* Allocation-free self interaction (no counterpart in the paper; a service for
+ * callers that cannot allocate device memory).
+ *
+ * Computes the on-surface self part only -- for each spheroid, S and D of its
+ * own density at its own nodes (the diagonal multipliers of Theorems 1-2
+ * followed by the inverse transform, i.e. the block-diagonal part of
+ * sbio_apply_laplace) -- without creating a geometry and without calling
+ * cudaMalloc, cudaFree or any allocating routine.  It is meant for code that
+ * must not allocate: a solver running inside a framework whose allocator or
+ * start-up reservation already owns the device memory (a private cudaMalloc
+ * could fail or fragment that pool), or a loop that was promised never to
+ * allocate after initialisation.  The caller passes its own device buffers:
+ *   sph: host array of M descriptors; p, n_phi as in sbio_options (n_phi 0 =
+ *        2(p+1)); sigma_tilde / mu_hat: device, M x (p+1)^2 (either may be
+ *        NULL); S_out / D_out: device, N (given exactly when the matching
+ *        input is).  Outputs are overwritten; asynchronous on `stream`.
+ * All other device data lives in one fixed array of 8 MiB that every GPU
+ * holding the library's module keeps reserved until the process exits.  A
+ * request whose tables and workspaces do not fit (about 80 spheroids at
+ * p = 16) fails with SBIO_EINVAL before any device work.
+ * The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current; make that first call
+ * before any stream capture.  All calls share the one array: calls whose GPU
+ * work overlaps (other streams, other host threads) race and must be
+ * serialised by the caller.  Nothing in the array needs to start at zero. */
+int sbio_apply_self_noalloc(const sbio_spheroid* sph, int32_t M, int32_t p, int32_t n_phi,
+                            const double* sigma_tilde, const double* mu_hat, double* S_out,
+                            double* D_out, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -55,7 +55,7 @@ int dev_alloc(sbio_geom* g, void** ptr, size_t bytes, const char* what) {
 // ---------------------------------------------------------------------------
 
 // Gauss-Legendre nodes (ascending) and weights by Newton's method on P_n.
-static void gauss_legendre(int n, std::vector<double>& x, std::vector<double>& w) {
+void gauss_legendre(int n, std::vector<double>& x, std::vector<double>& w) {
   x.assign(n, 0.0);
   w.assign(n, 0.0);
   for (int i = 0; i < n; ++i) {
@@ -89,7 +89,7 @@ static void gauss_legendre(int n, std::vector<double>& x, std::vector<double>& w
 }
 
 // Ferrers functions Pbar_n^m(v) (no Condon-Shortley phase), [nm_index(n,m)].
-static void ferrers(double v, int N, double* P) {
+void ferrers(double v, int N, double* P) {
   const double sv = std::sqrt(std::max(0.0, 1.0 - v * v));
   double pmm = 1.0;
   for (int m = 0; m <= N; ++m) {
@@ -102,7 +102,7 @@ static void ferrers(double v, int N, double* P) {
 }
 
 // (n-m)!/(n+m)!
-static double kfact(int n, int m) {
+double kfact(int n, int m) {
   double r = 1.0;
   for (int j = n - m + 1; j <= n + m; ++j) r /= j;
   return r;
@@ -172,7 +172,7 @@ static void split_f32(double v, float& hi, float& lo) {
 // geometry construction
 // ---------------------------------------------------------------------------
 
-static int validate(const sbio_spheroid* sph, int32_t M, const sbio_options* o) {
+int validate(const sbio_spheroid* sph, int32_t M, const sbio_options* o) {
   if (!sph || !o) return set_error(SBIO_EINVAL, "null spheroid array or options");
   if (M < 1) return set_error(SBIO_EINVAL, "M = %d: need at least one spheroid", M);
   if (o->p < 1 || o->p > SBIO_MAX_P) return set_error(SBIO_EINVAL, "p = %d outside [1, %d]", o->p, SBIO_MAX_P);
@@ -202,7 +202,7 @@ static int validate(const sbio_spheroid* sph, int32_t M, const sbio_options* o) 
   return SBIO_OK;
 }
 
-static int build_host(GeomHost& h, const sbio_spheroid* sph, int32_t M, const sbio_options* o) {
+int build_host(GeomHost& h, const sbio_spheroid* sph, int32_t M, const sbio_options* o) {
   h.M = M;
   h.p = o->p;
   h.n_v = o->p + 1;

@@ -89,6 +89,13 @@ int set_error(int code, const char* fmt, ...);
 void clear_error();
 void count_launch(int n = 1);
 
+// host set-up helpers shared by the translation units (defined in sbio_geom.cu)
+void gauss_legendre(int n, std::vector<double>& x, std::vector<double>& w);
+void ferrers(double v, int N, double* P);
+double kfact(int n, int m);
+int validate(const sbio_spheroid* sph, int32_t M, const sbio_options* o);
+int build_host(GeomHost& h, const sbio_spheroid* sph, int32_t M, const sbio_options* o);
+
 // device allocation tracked against the context budget
 int dev_alloc(sbio_geom* g, void** ptr, size_t bytes, const char* what);
 

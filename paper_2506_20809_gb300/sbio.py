@@ -81,6 +81,8 @@ _SIGS = {
     "sbio_apply_laplace_parts": (C.c_int, [_vp, _vp, _vp, _vp, _vp, C.c_uint32, _vp]),
     "sbio_apply_laplace_host": (C.c_int, [_vp, _vp, _vp, _vp, _vp, _vp]),
     "sbio_apply_stokes_sl": (C.c_int, [_vp, _vp, _vp, _vp]),
+    "sbio_apply_self_noalloc": (C.c_int, [C.POINTER(sbio_spheroid), C.c_int32, C.c_int32, C.c_int32, _vp, _vp,
+                                          _vp, _vp, _vp]),
 }
 
 EXPORTED = []
@@ -232,6 +234,13 @@ def sbio_apply_laplace_host(g, sigma_tilde, mu_hat, S_out, D_out, stream=None):
 
 def sbio_apply_stokes_sl(g, f_tilde, u_out, stream=None):
     _check(_lib.sbio_apply_stokes_sl(g, _ptr(f_tilde), _ptr(u_out), _stream(stream)))
+
+
+def sbio_apply_self_noalloc(spheroids, p, sigma_tilde, mu_hat, S_out, D_out, n_phi=0, stream=None):
+    """Self interaction without any device allocation by the library (see
+    include/sbio.h): for callers whose device memory is owned by someone else."""
+    _check(_lib.sbio_apply_self_noalloc(spheroids, len(spheroids), p, n_phi, _ptr(sigma_tilde), _ptr(mu_hat),
+                                        _ptr(S_out), _ptr(D_out), _stream(stream)))
 
 
 # ---- convenience object ------------------------------------------------------
