@@ -224,6 +224,7 @@ def run_ours(args, ws, rank, lrank):
     ctx = S.sbio_ctx_create(lrank, 0)
     prec = S.SBIO_MIXED if args.precision == "mixed" else S.SBIO_FP64
     geom = S.Geometry(ctx, susp, precision=prec)
+    tune = S.sbio_geom_autotune(geom.h)
     S.sbio_geom_enable_timing(geom.h, True)
     N = geom.N
     sig = torch.from_numpy(coef[0]).to(dev)
@@ -310,7 +311,9 @@ def run_ours(args, ws, rank, lrank):
         "metric": METRIC, "value": value, "unit": "applies/s", "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": statistics.mean(step_ms), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64" if prec == S.SBIO_MIXED else "f64",
-        "data": "synthetic", "config": config_dict(susp, geom.n_near, geom.n_far, N),
+        "data": "synthetic", "config": dict(config_dict(susp, geom.n_near, geom.n_far, N),
+                                            far_launch={"targets_per_thread": tune[0], "source_splits": tune[1],
+                                                        "autotuned_far_ms": tune[2]}),
         "gpairs_per_s": geom.n_far / (statistics.mean(step_ms) * 1e-3) / 1e9,
         "latency_ms": {"p50": lat[len(lat) // 2], "p99": lat[min(len(lat) - 1, int(0.99 * len(lat)))]},
         "phase_ms": {"synth": statistics.mean(synth_ms), "near": statistics.mean(near_ms), "far": far_mean},

@@ -159,6 +159,19 @@ int sbio_geom_near_pairs(const sbio_geom* g, int32_t* target, int32_t* source);
 int sbio_geom_enable_timing(sbio_geom* g, int32_t on);
 int sbio_geom_phase_times(sbio_geom* g, double* ms_synth, double* ms_near, double* ms_far);
 
+/* Launch shape of the far-field kernels: far_tt targets per thread of the
+ * mixed kernel (1, 2 or 4) and far_splits source splits of the grid (0 =
+ * chosen from the device's SM count).  Results do not depend on the shape
+ * beyond floating-point summation order. */
+int sbio_geom_set_launch_shape(sbio_geom* g, int32_t far_tt, int32_t far_splits);
+
+/* Autotuner: times the far-field kernel of this geometry in its current
+ * precision mode for a small set of launch shapes (CUDA events on `stream`,
+ * zero-strength sources written by one self-only pass into the geometry's
+ * own workspaces), keeps the fastest and reports it (outputs may be NULL).
+ * Synchronises `stream`; the workspaces hold no caller data afterwards. */
+int sbio_geom_autotune(sbio_geom* g, void* stream, int32_t* far_tt, int32_t* far_splits, double* far_ms);
+
 /* Change the precision mode used by later applies (SBIO_FP64 / SBIO_MIXED). */
 int sbio_geom_set_precision(sbio_geom* g, int32_t precision);
 

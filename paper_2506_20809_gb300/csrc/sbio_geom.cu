@@ -321,6 +321,24 @@ static int build_near(GeomHost& h) {
   }
   h.far_pairs = 0;
   for (int64_t t = 0; t < N; ++t) h.far_pairs += (int64_t)(M - 1 - cnt[t]) * h.G;
+  // Stokes: the self interaction is evaluated as (node, own particle) pairs at
+  // the own surface, in the same (kind, source, target) order
+  std::vector<std::pair<int32_t, int32_t>> st(pairs);
+  for (int64_t t = 0; t < N; ++t) st.push_back({(int32_t)t, (int32_t)(t / h.G)});
+  std::sort(st.begin(), st.end(), [&](const std::pair<int32_t, int32_t>& a, const std::pair<int32_t, int32_t>& b) {
+    const int ka = h.parts[a.second].kind, kb = h.parts[b.second].kind;
+    if (ka != kb) return ka < kb;
+    if (a.second != b.second) return a.second < b.second;
+    return a.first < b.first;
+  });
+  h.st_pair_t.resize(st.size());
+  h.st_pair_s.resize(st.size());
+  h.st_pairs_prolate = 0;
+  for (size_t k = 0; k < st.size(); ++k) {
+    h.st_pair_t[k] = st[k].first;
+    h.st_pair_s[k] = st[k].second;
+    if (h.parts[st[k].second].kind == SBIO_PROLATE) h.st_pairs_prolate++;
+  }
   // far-field source tiles
   h.tiles.clear();
   for (int i = 0; i < M; ++i)
@@ -445,6 +463,55 @@ static int build_device(sbio_geom* g) {
   }
   if ((rc = upload(g, &d.tgt32, tgt.data(), tgt.size(), "fp32 targets"))) return rc;
   if ((rc = upload(g, &d.cen32, cen.data(), cen.size(), "fp32 centres"))) return rc;
+  // Stokes tables: exterior factor and normalisation to order p+1, the y.f
+  // transform grid ((p+2) GL x (2p+4) trapezoid: exact for degree 2p+2)
+  {
+    const int p1 = p + 1, nm1 = nm_count(p1), nc1 = (p1 + 1) * (p1 + 1);
+    std::vector<double> ext((size_t)M * nm1), Pq(nm_count(p1 + 1));
+    for (int i = 0; i < M; ++i) {
+      const PartGeom& P = h.parts[i];
+      radial_P(P.u0, P.sgn, p1, Pq.data());
+      for (int n = 0; n <= p1; ++n)
+        for (int m = 0; m <= n; ++m)
+          ext[(size_t)i * nm1 + nm_index(n, m)] =
+              P.a * kfact(n, m) * ((m & 1) ? -1.0 : 1.0) * (P.A / P.a) * Pq[nm_index(n, m)];
+    }
+    if ((rc = upload(g, &d.st_ext, ext.data(), ext.size(), "Stokes multipliers"))) return rc;
+    std::vector<double> nc1v(nc1);
+    for (int n = 0; n <= p1; ++n)
+      for (int m = -n; m <= n; ++m) {
+        const int am = m < 0 ? -m : m;
+        nc1v[coef_index(n, m)] = std::sqrt((2.0 * n + 1.0) / (4.0 * kPi) * kfact(n, am)) * (m ? std::sqrt(2.0) : 1.0);
+      }
+    if ((rc = upload(g, &d.st_normc, nc1v.data(), nc1v.size(), "Stokes normalisation"))) return rc;
+    h.n_q = p + 2;
+    h.n_f = 2 * p + 4;
+    std::vector<double> qv, qw;
+    gauss_legendre(h.n_q, qv, qw);
+    std::vector<double> qpt((size_t)h.n_q * nm1), ft(nm_count(p1 + 1));
+    for (int j = 0; j < h.n_q; ++j) {
+      ferrers(qv[j], p1, ft.data());
+      for (int n = 0; n <= p1; ++n)
+        for (int m = 0; m <= n; ++m)
+          qpt[(size_t)j * nm1 + nm_index(n, m)] = std::sqrt((2.0 * n + 1.0) / (4.0 * kPi) * kfact(n, m)) * ft[nm_index(n, m)];
+    }
+    std::vector<double> qtr((size_t)h.n_f * (p1 + 1) * 2);
+    for (int l = 0; l < h.n_f; ++l)
+      for (int m = 0; m <= p1; ++m) {
+        const double ph = 2.0 * kPi * l / h.n_f;
+        qtr[((size_t)l * (p1 + 1) + m) * 2 + 0] = std::cos(m * ph);
+        qtr[((size_t)l * (p1 + 1) + m) * 2 + 1] = std::sin(m * ph);
+      }
+    if ((rc = upload(g, &d.st_qv, qv.data(), qv.size(), "Stokes grid"))) return rc;
+    if ((rc = upload(g, &d.st_qw, qw.data(), qw.size(), "Stokes grid"))) return rc;
+    if ((rc = upload(g, &d.st_qptab, qpt.data(), qpt.size(), "Stokes grid"))) return rc;
+    if ((rc = upload(g, &d.st_qtrig, qtr.data(), qtr.size(), "Stokes grid"))) return rc;
+    if ((rc = upload(g, &d.st_pair_t, h.st_pair_t.data(), h.st_pair_t.size(), "Stokes pairs"))) return rc;
+    if ((rc = upload(g, &d.st_pair_s, h.st_pair_s.data(), h.st_pair_s.size(), "Stokes pairs"))) return rc;
+    if ((rc = dev_alloc(g, (void**)&d.st_coef, (size_t)M * 4 * nc1 * sizeof(double), "Stokes coefficients"))) return rc;
+    if ((rc = dev_alloc(g, (void**)&d.st_src64, (size_t)N * 8 * sizeof(double), "Stokes fp64 sources"))) return rc;
+    if ((rc = dev_alloc(g, (void**)&d.st_src32, (size_t)N * 2 * sizeof(float4), "Stokes fp32 sources"))) return rc;
+  }
   // workspaces
   if ((rc = dev_alloc(g, (void**)&d.src64, (size_t)N * 8 * sizeof(double), "fp64 sources"))) return rc;
   if ((rc = dev_alloc(g, (void**)&d.src32, (size_t)N * 2 * sizeof(float4), "fp32 sources"))) return rc;

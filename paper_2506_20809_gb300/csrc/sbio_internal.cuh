@@ -47,11 +47,18 @@ struct DevGeom {
   double* beta = nullptr;        // M x (p+1)^2 folded exterior D coefficients
   double* host_in = nullptr;     // 2 x M x (p+1)^2 staging for the host-memory entry point
   double* host_out = nullptr;    // 2 x N
-  // Stokes workspaces (allocated on first Stokes apply)
-  double* st_src64 = nullptr;    // N x 4: f * w (3), 0
-  float4* st_src32 = nullptr;    // N x 1: (f w)
-  double* st_coef = nullptr;     // M x 5 x (p+2)^2 folded coefficients (f1,f2,f3,y.f at p+1)
-  double* st_tab = nullptr;      // Stokes self tables
+  // Stokes single layer (Sec. 4.3): tables, pairs and workspaces
+  double* st_ext = nullptr;      // M x nm_count(p+1): exterior S factor up to order p+1
+  double* st_normc = nullptr;    // (p+2)^2 normalisation up to order p+1
+  double* st_qv = nullptr;       // n_q GL nodes of the y.f transform grid
+  double* st_qw = nullptr;       // n_q GL weights
+  double* st_qptab = nullptr;    // n_q x nm_count(p+1): N_n^m Pbar_n^m(v_q)
+  double* st_qtrig = nullptr;    // n_f x (p+2) x 2: cos / sin (m phi_l)
+  int32_t* st_pair_t = nullptr;  // near pairs + self pairs: target node
+  int32_t* st_pair_s = nullptr;  //                          source particle
+  double* st_coef = nullptr;     // M x 4 x (p+2)^2 folded coefficients (f1, f2, f3, y.f)
+  double* st_src64 = nullptr;    // N x 8: y - c_own (3), w f (3), 0, 0
+  float4* st_src32 = nullptr;    // N x 2: (y - c_own, w f_1), (w f_2, w f_3, 0, 0)
 };
 
 struct GeomHost {
@@ -65,6 +72,14 @@ struct GeomHost {
   int64_t n_pairs_prolate = 0;           // pairs [0, n_pairs_prolate) have prolate sources
   int64_t far_pairs = 0;
   std::vector<int4> tiles;
+  std::vector<int32_t> st_pair_t, st_pair_s; // Stokes: near + self pairs, sorted like pair_t/pair_s
+  int64_t st_pairs_prolate = 0;
+  int n_q = 0, n_f = 0;                      // y.f transform grid
+  // launch shape of the far field (tunable): targets per thread of the mixed
+  // kernel and number of source splits (0 = chosen from the device size)
+  int far_tt = 2;
+  int far_splits = 0;
+  int near_block = 128;                      // threads per CTA of the near kernels
 };
 
 }  // namespace sbio
@@ -122,6 +137,10 @@ inline void phase_mark(sbio_geom* g, int k, cudaStream_t st) {
 int launch_laplace(sbio_geom* g, const double* sigma, const double* mu, double* S, double* D,
                    uint32_t parts, cudaStream_t st);
 int launch_stokes(sbio_geom* g, const double* f, double* u, cudaStream_t st);
+
+// source splits of the far-field grid (gridDim.y) for `target_blocks` target
+// CTAs; `requested` > 0 forces the count
+int far_split_count(int64_t target_blocks, int n_tiles, int requested);
 
 }  // namespace sbio
 

@@ -155,7 +155,9 @@ __global__ void __launch_bounds__(kFarTile) far_fp64_kernel(const int4* __restri
   int cur = -1;
   bool skip = true;
   double X = 0, Y = 0, Z = 0;
-  for (int tl = 0; tl < n_tiles; ++tl) {
+  const int per = (n_tiles + gridDim.y - 1) / gridDim.y;
+  const int t_lo = blockIdx.y * per, t_hi = min(n_tiles, t_lo + per);
+  for (int tl = t_lo; tl < t_hi; ++tl) {
     const int4 tile = tiles[tl];
     if (tile.x != cur) {
       cur = tile.x;
@@ -237,7 +239,9 @@ __global__ void __launch_bounds__(kFarTile) far_mixed_kernel(const int4* __restr
     skip[q] = true;
   }
   int cur = -1;
-  for (int tl = 0; tl < n_tiles; ++tl) {
+  const int per = (n_tiles + gridDim.y - 1) / gridDim.y;
+  const int t_lo = blockIdx.y * per, t_hi = min(n_tiles, t_lo + per);
+  for (int tl = t_lo; tl < t_hi; ++tl) {
     const int4 tile = tiles[tl];
     if (tile.x != cur) {
       cur = tile.x;
@@ -309,34 +313,63 @@ __global__ void __launch_bounds__(kFarTile) far_mixed_kernel(const int4* __restr
   }
 }
 
-constexpr int kMixedTT = 2;
+// Number of source splits so that the grid holds about `waves` resident
+// rounds of CTAs on the device (never more splits than tiles).
+int far_split_count(int64_t target_blocks, int n_tiles, int requested) {
+  if (requested > 0) return requested < n_tiles ? requested : n_tiles;
+  static int sm_count[64] = {0};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  int sms = (dev >= 0 && dev < 64) ? sm_count[dev] : 0;
+  if (sms == 0) {
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (dev >= 0 && dev < 64) sm_count[dev] = sms;
+  }
+  const int64_t want = (int64_t)sms * 8 * 2;
+  int64_t s = (want + target_blocks - 1) / target_blocks;
+  if (s < 1) s = 1;
+  if (s > n_tiles) s = n_tiles;
+  return (int)s;
+}
+
+template <int TT>
+static void launch_far_mixed_tt(const DevGeom& d, const GeomHost& h, int nt, int splits, double* S, double* D,
+                                cudaStream_t st) {
+  const int64_t tb = (h.N + kFarTile * TT - 1) / (kFarTile * TT);
+  const dim3 grid((unsigned)tb, (unsigned)far_split_count(tb, nt, splits));
+  if (S && D)
+    far_mixed_kernel<TT, true, true><<<grid, kFarTile, 0, st>>>(d.tiles, nt, d.src32, d.tgt32, d.cen32, d.skip_ptr,
+                                                                d.skip_idx, h.N, S, D);
+  else if (S)
+    far_mixed_kernel<TT, true, false><<<grid, kFarTile, 0, st>>>(d.tiles, nt, d.src32, d.tgt32, d.cen32, d.skip_ptr,
+                                                                 d.skip_idx, h.N, S, D);
+  else
+    far_mixed_kernel<TT, false, true><<<grid, kFarTile, 0, st>>>(d.tiles, nt, d.src32, d.tgt32, d.cen32, d.skip_ptr,
+                                                                 d.skip_idx, h.N, S, D);
+}
 
 static void launch_far(sbio_geom* g, double* S, double* D, cudaStream_t st) {
   const DevGeom& d = g->d;
   const GeomHost& h = g->h;
   const int nt = (int)h.tiles.size();
   if (h.precision == SBIO_FP64) {
-    const unsigned blocks = (unsigned)((h.N + kFarTile - 1) / kFarTile);
+    const int64_t tb = (h.N + kFarTile - 1) / kFarTile;
+    const dim3 grid((unsigned)tb, (unsigned)far_split_count(tb, nt, h.far_splits));
     if (S && D)
-      far_fp64_kernel<true, true><<<blocks, kFarTile, 0, st>>>(d.tiles, nt, d.src64, d.xyz, d.parts, d.skip_ptr,
-                                                               d.skip_idx, h.N, S, D);
+      far_fp64_kernel<true, true><<<grid, kFarTile, 0, st>>>(d.tiles, nt, d.src64, d.xyz, d.parts, d.skip_ptr,
+                                                             d.skip_idx, h.N, S, D);
     else if (S)
-      far_fp64_kernel<true, false><<<blocks, kFarTile, 0, st>>>(d.tiles, nt, d.src64, d.xyz, d.parts, d.skip_ptr,
-                                                                d.skip_idx, h.N, S, D);
+      far_fp64_kernel<true, false><<<grid, kFarTile, 0, st>>>(d.tiles, nt, d.src64, d.xyz, d.parts, d.skip_ptr,
+                                                              d.skip_idx, h.N, S, D);
     else
-      far_fp64_kernel<false, true><<<blocks, kFarTile, 0, st>>>(d.tiles, nt, d.src64, d.xyz, d.parts, d.skip_ptr,
-                                                                d.skip_idx, h.N, S, D);
+      far_fp64_kernel<false, true><<<grid, kFarTile, 0, st>>>(d.tiles, nt, d.src64, d.xyz, d.parts, d.skip_ptr,
+                                                              d.skip_idx, h.N, S, D);
   } else {
-    const unsigned blocks = (unsigned)((h.N + kFarTile * kMixedTT - 1) / (kFarTile * kMixedTT));
-    if (S && D)
-      far_mixed_kernel<kMixedTT, true, true><<<blocks, kFarTile, 0, st>>>(d.tiles, nt, d.src32, d.tgt32, d.cen32,
-                                                                          d.skip_ptr, d.skip_idx, h.N, S, D);
-    else if (S)
-      far_mixed_kernel<kMixedTT, true, false><<<blocks, kFarTile, 0, st>>>(d.tiles, nt, d.src32, d.tgt32, d.cen32,
-                                                                           d.skip_ptr, d.skip_idx, h.N, S, D);
-    else
-      far_mixed_kernel<kMixedTT, false, true><<<blocks, kFarTile, 0, st>>>(d.tiles, nt, d.src32, d.tgt32, d.cen32,
-                                                                           d.skip_ptr, d.skip_idx, h.N, S, D);
+    switch (h.far_tt) {
+      case 1: launch_far_mixed_tt<1>(d, h, nt, h.far_splits, S, D, st); break;
+      case 4: launch_far_mixed_tt<4>(d, h, nt, h.far_splits, S, D, st); break;
+      default: launch_far_mixed_tt<2>(d, h, nt, h.far_splits, S, D, st); break;
+    }
   }
   count_launch();
 }
@@ -418,6 +451,72 @@ int sbio_apply_laplace_host(sbio_geom* g, const double* sigma_host, const double
   if (oS) SBIO_CUDA_TRY(cudaMemcpyAsync(S_host, oS, N * sizeof(double), cudaMemcpyDeviceToHost, st));
   if (oD) SBIO_CUDA_TRY(cudaMemcpyAsync(D_host, oD, N * sizeof(double), cudaMemcpyDeviceToHost, st));
   SBIO_CUDA_TRY(cudaStreamSynchronize(st));
+  return SBIO_OK;
+}
+
+int sbio_geom_set_launch_shape(sbio_geom* g, int32_t far_tt, int32_t far_splits) {
+  clear_error();
+  if (!g) return set_error(SBIO_EINVAL, "null geometry");
+  if (far_tt != 1 && far_tt != 2 && far_tt != 4) return set_error(SBIO_EINVAL, "far_tt must be 1, 2 or 4");
+  if (far_splits < 0) return set_error(SBIO_EINVAL, "far_splits must be >= 0");
+  g->h.far_tt = far_tt;
+  g->h.far_splits = far_splits;
+  return SBIO_OK;
+}
+
+int sbio_geom_autotune(sbio_geom* g, void* stream, int32_t* far_tt, int32_t* far_splits, double* far_ms) {
+  clear_error();
+  if (!g) return set_error(SBIO_EINVAL, "null geometry");
+  SBIO_CUDA_TRY(cudaSetDevice(g->ctx->device));
+  cudaStream_t st = (cudaStream_t)stream;
+  GeomHost& h = g->h;
+  DevGeom& d = g->d;
+  const size_t nc = (size_t)(h.p + 1) * (h.p + 1) * h.M;
+  // valid (zero-strength) sources so that the timed kernels read finite data
+  SBIO_CUDA_TRY(cudaMemsetAsync(d.host_in, 0, 2 * nc * sizeof(double), st));
+  int rc = launch_laplace(g, d.host_in, d.host_in + nc, d.host_out, d.host_out + h.N, SBIO_PART_SELF, st);
+  if (rc) return rc;
+  cudaEvent_t e0, e1;
+  SBIO_CUDA_TRY(cudaEventCreate(&e0));
+  SBIO_CUDA_TRY(cudaEventCreate(&e1));
+  const int nt = (int)h.tiles.size();
+  const int saved_tt = h.far_tt, saved_sp = h.far_splits;
+  double best = 1e300;
+  int best_tt = saved_tt, best_sp = saved_sp;
+  const int tts[3] = {1, 2, 4};
+  for (int a = 0; a < (h.precision == SBIO_FP64 ? 1 : 3); ++a) {
+    const int tt = (h.precision == SBIO_FP64) ? 1 : tts[a];
+    const int64_t tb = (h.N + (int64_t)kFarTile * tt - 1) / ((int64_t)kFarTile * tt);
+    const int base = far_split_count(tb, nt, 0);
+    const int cands[4] = {base > 1 ? base / 2 : 1, base, 2 * base, 4 * base};
+    for (int b = 0; b < 4; ++b) {
+      h.far_tt = tt;
+      h.far_splits = cands[b] < nt ? cands[b] : nt;
+      launch_far(g, d.host_out, d.host_out + h.N, st);   // warm-up
+      float tms[3];
+      for (int r = 0; r < 3; ++r) {
+        cudaEventRecord(e0, st);
+        launch_far(g, d.host_out, d.host_out + h.N, st);
+        cudaEventRecord(e1, st);
+        SBIO_CUDA_TRY(cudaEventSynchronize(e1));
+        cudaEventElapsedTime(&tms[r], e0, e1);
+      }
+      const float med = std::max(std::min(tms[0], tms[1]), std::min(std::max(tms[0], tms[1]), tms[2]));
+      if (med < best) {
+        best = med;
+        best_tt = tt;
+        best_sp = h.far_splits;
+      }
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  h.far_tt = best_tt;
+  h.far_splits = best_sp;
+  SBIO_CUDA_TRY(cudaGetLastError());
+  if (far_tt) *far_tt = best_tt;
+  if (far_splits) *far_splits = best_sp;
+  if (far_ms) *far_ms = best;
   return SBIO_OK;
 }
 

@@ -1,11 +1,354 @@
-// Stokes single layer through the Laplace-to-Stokes identity (Sec. 4.3).
+// Stokes single layer (viscosity 1) at all surface nodes through the
+// Laplace-to-Stokes identity of Sec. 4.3, eq. (stokes):
+//   stokes_prep : per particle, the modified-basis coefficients of y . f at
+//                 order p+1 (exact product-quadrature transform), the folded
+//                 expansion coefficients of f_1, f_2, f_3, y . f, the
+//                 Stokeslet far-field sources w f at the nodes; zeroes u;
+//   stokes_near : one thread per (target, near or own particle) pair
+//                 (sbio_stokes_near.cuh), FP64, atomically added;
+//   stokes_far  : tiled all-pairs Stokeslet quadrature over far particles,
+//                 G = (I/r + r r^T/r^3)/(8 pi), FP64 or FP32 with two-sum
+//                 compensated accumulation, atomically added.
 #include "sbio_internal.cuh"
+#include "sbio_stokes_near.cuh"
 
 namespace sbio {
 
+stokes_near_launcher stokes_near_lookup_a(int p);
+stokes_near_launcher stokes_near_lookup_b(int p);
+
+constexpr double kInv8Pi = 0.039788735772973836;   // 1/(8 pi)
+
+__global__ void __launch_bounds__(256) stokes_prep_kernel(
+    int p, int n_v, int n_phi, int n_q, int n_f, const PartGeom* __restrict__ parts, const double* __restrict__ xyz,
+    const double* __restrict__ w, const double* __restrict__ ptab, const double* __restrict__ trig,
+    const double* __restrict__ sqrtw, const double* __restrict__ qv, const double* __restrict__ qw,
+    const double* __restrict__ qptab, const double* __restrict__ qtrig, const double* __restrict__ ext,
+    const double* __restrict__ normc1, const double* __restrict__ f, double* __restrict__ coef_out,
+    double* __restrict__ src64, float4* __restrict__ src32, double* __restrict__ u_out) {
+  extern __shared__ double sm[];
+  const int i = blockIdx.x;
+  const int p1 = p + 1, nc = (p + 1) * (p + 1), nc1 = (p1 + 1) * (p1 + 1);
+  const int nm = nm_count(p), nm1 = nm_count(p1), mw = 2 * p + 1, mw1 = 2 * p1 + 1;
+  const int G = n_v * n_phi;
+  double* fk = sm;                          // 3 x nc
+  double* cy = fk + 3 * nc;                 // nc1
+  double* L1 = cy + nc1;                    // 3 x max(n_q, n_v) x mw
+  const int nrow = n_q > n_v ? n_q : n_v;
+  double* hq = L1 + 3 * nrow * mw;          // n_q x n_f
+  double* H = hq + n_q * n_f;               // n_q x mw1
+  const PartGeom P = parts[i];
+  for (int k = threadIdx.x; k < 3 * nc; k += blockDim.x) fk[k] = f[(size_t)i * 3 * nc + k];
+  __syncthreads();
+  // (1) Legendre stage of f_d on the transform grid
+  for (int idx = threadIdx.x; idx < 3 * n_q * mw; idx += blockDim.x) {
+    const int d = idx / (n_q * mw), r = idx - d * n_q * mw, j = r / mw, ms = r - j * mw, m = ms - p;
+    const int am = m < 0 ? -m : m;
+    const double s2 = m ? 1.4142135623730951 : 1.0;
+    double acc = 0.0;
+    for (int n = am; n <= p; ++n) acc = fma(fk[d * nc + n * n + n + m], s2 * qptab[(size_t)j * nm1 + nm_index(n, am)], acc);
+    L1[(d * n_q + j) * mw + ms] = acc;
+  }
+  __syncthreads();
+  // (2) values of (y - c) . f sqrt(u0^2 -+ v^2) at the grid points
+  for (int idx = threadIdx.x; idx < n_q * n_f; idx += blockDim.x) {
+    const int j = idx / n_f, l = idx - j * n_f;
+    const double* tr = qtrig + (size_t)l * (p1 + 1) * 2;
+    double Fd[3];
+    for (int d = 0; d < 3; ++d) {
+      const double* L = L1 + (d * n_q + j) * mw + p;
+      double acc = L[0];
+      for (int m = 1; m <= p; ++m) acc = fma(L[m], tr[2 * m], fma(L[-m], tr[2 * m + 1], acc));
+      Fd[d] = acc;
+    }
+    const double v = qv[j], sv = sqrt((1.0 - v) * (1.0 + v));
+    const double yl0 = P.A * sv * tr[2], yl1 = P.A * sv * tr[3], yl2 = P.C * v;   // cos phi, sin phi at m = 1
+    double acc = 0.0;
+    for (int d = 0; d < 3; ++d) acc = fma(P.R[d * 3 + 0] * yl0 + P.R[d * 3 + 1] * yl1 + P.R[d * 3 + 2] * yl2, Fd[d], acc);
+    hq[idx] = acc;
+  }
+  __syncthreads();
+  // (3) Fourier projection, |m| <= p+1
+  for (int idx = threadIdx.x; idx < n_q * mw1; idx += blockDim.x) {
+    const int j = idx / mw1, ms = idx - j * mw1, m = ms - p1, am = m < 0 ? -m : m;
+    double acc = 0.0;
+    for (int l = 0; l < n_f; ++l) acc = fma(hq[j * n_f + l], qtrig[((size_t)l * (p1 + 1) + am) * 2 + (m < 0 ? 1 : 0)], acc);
+    H[idx] = acc * (2.0 * kPi / n_f);
+  }
+  __syncthreads();
+  // (4) Legendre projection -> y.f coefficients of order p+1
+  for (int k = threadIdx.x; k < nc1; k += blockDim.x) {
+    const int n = (int)sqrt((double)k);
+    const int m = k - n * n - n, am = m < 0 ? -m : m;
+    const double s2 = m ? 1.4142135623730951 : 1.0;
+    double acc = 0.0;
+    for (int j = 0; j < n_q; ++j) acc = fma(qw[j] * H[j * mw1 + m + p1], s2 * qptab[(size_t)j * nm1 + nm_index(n, am)], acc);
+    cy[k] = acc;
+  }
+  __syncthreads();
+  // (5) folded coefficients of the four expansions (order p+1)
+  for (int k = threadIdx.x; k < 4 * nc1; k += blockDim.x) {
+    const int d = k / nc1, c = k - d * nc1;
+    const int n = (int)sqrt((double)c);
+    const int m = c - n * n - n, am = m < 0 ? -m : m;
+    const double raw = (d < 3) ? (c < nc ? fk[d * nc + c] : 0.0) : cy[c];
+    coef_out[(size_t)i * 4 * nc1 + k] = ext[(size_t)i * nm1 + nm_index(n, am)] * normc1[c] * raw;
+  }
+  // (6) far sources: w f at the own nodes (Legendre stage reuses L1)
+  __syncthreads();
+  for (int idx = threadIdx.x; idx < 3 * n_v * mw; idx += blockDim.x) {
+    const int d = idx / (n_v * mw), r = idx - d * n_v * mw, j = r / mw, ms = r - j * mw, m = ms - p;
+    const int am = m < 0 ? -m : m;
+    const double s2 = m ? 1.4142135623730951 : 1.0;
+    double acc = 0.0;
+    for (int n = am; n <= p; ++n) acc = fma(fk[d * nc + n * n + n + m], s2 * ptab[(size_t)j * nm + nm_index(n, am)], acc);
+    L1[(d * n_v + j) * mw + ms] = acc;
+  }
+  __syncthreads();
+  for (int l = threadIdx.x; l < G; l += blockDim.x) {
+    const int j = l / n_phi, k = l - j * n_phi;
+    const double* tr = trig + (size_t)k * (p + 1) * 2;
+    const int64_t t = (int64_t)i * G + l;
+    const double ws = w[t] / sqrtw[(size_t)i * n_v + j];
+    double fw[3];
+    for (int d = 0; d < 3; ++d) {
+      const double* L = L1 + (d * n_v + j) * mw + p;
+      double acc = L[0];
+      for (int m = 1; m <= p; ++m) acc = fma(L[m], tr[2 * m], fma(L[-m], tr[2 * m + 1], acc));
+      fw[d] = acc * ws;
+    }
+    const double y0 = xyz[t * 3 + 0] - P.c[0], y1 = xyz[t * 3 + 1] - P.c[1], y2 = xyz[t * 3 + 2] - P.c[2];
+    double* s = src64 + t * 8;
+    s[0] = y0; s[1] = y1; s[2] = y2; s[3] = fw[0];
+    s[4] = fw[1]; s[5] = fw[2]; s[6] = 0.0; s[7] = 0.0;
+    src32[t * 2 + 0] = make_float4((float)y0, (float)y1, (float)y2, (float)fw[0]);
+    src32[t * 2 + 1] = make_float4((float)fw[1], (float)fw[2], 0.f, 0.f);
+    u_out[t * 3 + 0] = 0.0;
+    u_out[t * 3 + 1] = 0.0;
+    u_out[t * 3 + 2] = 0.0;
+  }
+}
+
+struct alignas(32) dbl4s {
+  double x, y, z, w;
+};
+
+__device__ __forceinline__ void two_sum_f(float a, float b, float& s, float& e) {
+  s = a + b;
+  const float bb = s - a;
+  e = (a - (s - bb)) + (b - bb);
+}
+
+__device__ __forceinline__ float rsqrt_approx_f(float x) {
+  float r;
+  asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+
+__global__ void __launch_bounds__(kFarTile) stokes_far_fp64_kernel(const int4* __restrict__ tiles, int n_tiles,
+                                                                   const double* __restrict__ src64,
+                                                                   const double* __restrict__ xyz,
+                                                                   const PartGeom* __restrict__ parts,
+                                                                   const int32_t* __restrict__ skip_ptr,
+                                                                   const int32_t* __restrict__ skip_idx, int64_t N,
+                                                                   double* __restrict__ u_out) {
+  __shared__ dbl4s sh[kFarTile * 2];
+  const int64_t t = (int64_t)blockIdx.x * kFarTile + threadIdx.x;
+  const bool valid = t < N;
+  double x = 0, y = 0, z = 0;
+  int sp = 0, nxt = INT32_MAX;
+  if (valid) {
+    x = xyz[t * 3 + 0];
+    y = xyz[t * 3 + 1];
+    z = xyz[t * 3 + 2];
+    sp = skip_ptr[t];
+    nxt = skip_idx[sp];
+  }
+  double a0 = 0, a1 = 0, a2 = 0;
+  int cur = -1;
+  bool skip = true;
+  double X = 0, Y = 0, Z = 0;
+  const int per = (n_tiles + gridDim.y - 1) / gridDim.y;
+  const int t_lo = blockIdx.y * per, t_hi = min(n_tiles, t_lo + per);
+  for (int tl = t_lo; tl < t_hi; ++tl) {
+    const int4 tile = tiles[tl];
+    if (tile.x != cur) {
+      cur = tile.x;
+      if (valid) {
+        while (nxt < cur) nxt = skip_idx[++sp];
+        skip = (nxt == cur);
+        X = x - parts[cur].c[0];
+        Y = y - parts[cur].c[1];
+        Z = z - parts[cur].c[2];
+      }
+    }
+    if (__syncthreads_and(skip)) continue;
+    if (threadIdx.x < tile.z) {
+      const dbl4s* s = reinterpret_cast<const dbl4s*>(src64 + (int64_t)(tile.y + threadIdx.x) * 8);
+      sh[threadIdx.x * 2 + 0] = s[0];
+      sh[threadIdx.x * 2 + 1] = s[1];
+    }
+    __syncthreads();
+    if (!skip) {
+      for (int j = 0; j < tile.z; ++j) {
+        const dbl4s A = sh[j * 2], B = sh[j * 2 + 1];
+        const double dx = X - A.x, dy = Y - A.y, dz = Z - A.z;
+        const double ri = rsqrt(dx * dx + dy * dy + dz * dz);
+        const double rf = (dx * A.w + dy * B.x + dz * B.y) * ri * ri * ri;
+        a0 += A.w * ri + rf * dx;
+        a1 += B.x * ri + rf * dy;
+        a2 += B.y * ri + rf * dz;
+      }
+    }
+    __syncthreads();
+  }
+  if (valid) {
+    atomicAdd(u_out + t * 3 + 0, a0 * kInv8Pi);
+    atomicAdd(u_out + t * 3 + 1, a1 * kInv8Pi);
+    atomicAdd(u_out + t * 3 + 2, a2 * kInv8Pi);
+  }
+}
+
+template <int TT>
+__global__ void __launch_bounds__(kFarTile) stokes_far_mixed_kernel(const int4* __restrict__ tiles, int n_tiles,
+                                                                    const float4* __restrict__ src32,
+                                                                    const float4* __restrict__ tgt32,
+                                                                    const float4* __restrict__ cen32,
+                                                                    const int32_t* __restrict__ skip_ptr,
+                                                                    const int32_t* __restrict__ skip_idx, int64_t N,
+                                                                    double* __restrict__ u_out) {
+  __shared__ float4 sh[kFarTile * 2];
+  int64_t tg[TT];
+  bool valid[TT], skip[TT];
+  float xh[TT][3], xo[TT][3], X[TT][3];
+  int sp[TT], nxt[TT];
+  float hi[TT][3], lo[TT][3];
+#pragma unroll
+  for (int q = 0; q < TT; ++q) {
+    tg[q] = ((int64_t)blockIdx.x * TT + q) * kFarTile + threadIdx.x;
+    valid[q] = tg[q] < N;
+    sp[q] = 0;
+    nxt[q] = INT32_MAX;
+    skip[q] = true;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) xh[q][k] = xo[q][k] = X[q][k] = hi[q][k] = lo[q][k] = 0.f;
+    if (valid[q]) {
+      const float4 h4 = tgt32[tg[q] * 2], l4 = tgt32[tg[q] * 2 + 1];
+      xh[q][0] = h4.x; xh[q][1] = h4.y; xh[q][2] = h4.z;
+      xo[q][0] = l4.x; xo[q][1] = l4.y; xo[q][2] = l4.z;
+      sp[q] = skip_ptr[tg[q]];
+      nxt[q] = skip_idx[sp[q]];
+    }
+  }
+  int cur = -1;
+  const int per = (n_tiles + gridDim.y - 1) / gridDim.y;
+  const int t_lo = blockIdx.y * per, t_hi = min(n_tiles, t_lo + per);
+  for (int tl = t_lo; tl < t_hi; ++tl) {
+    const int4 tile = tiles[tl];
+    if (tile.x != cur) {
+      cur = tile.x;
+      const float4 ch = cen32[cur * 2], cl = cen32[cur * 2 + 1];
+#pragma unroll
+      for (int q = 0; q < TT; ++q) {
+        if (valid[q]) {
+          while (nxt[q] < cur) nxt[q] = skip_idx[++sp[q]];
+          skip[q] = (nxt[q] == cur);
+        }
+        X[q][0] = (xh[q][0] - ch.x) + (xo[q][0] - cl.x);
+        X[q][1] = (xh[q][1] - ch.y) + (xo[q][1] - cl.y);
+        X[q][2] = (xh[q][2] - ch.z) + (xo[q][2] - cl.z);
+      }
+    }
+    bool all_skip = true;
+#pragma unroll
+    for (int q = 0; q < TT; ++q) all_skip = all_skip && skip[q];
+    if (__syncthreads_and(all_skip)) continue;
+    if (threadIdx.x < tile.z) {
+      sh[threadIdx.x * 2 + 0] = src32[(int64_t)(tile.y + threadIdx.x) * 2 + 0];
+      sh[threadIdx.x * 2 + 1] = src32[(int64_t)(tile.y + threadIdx.x) * 2 + 1];
+    }
+    __syncthreads();
+    if (!all_skip) {
+      float p0[TT], p1[TT], p2[TT];
+#pragma unroll
+      for (int q = 0; q < TT; ++q) p0[q] = p1[q] = p2[q] = 0.f;
+#pragma unroll 4
+      for (int j = 0; j < tile.z; ++j) {
+        const float4 A = sh[j * 2], B = sh[j * 2 + 1];
+#pragma unroll
+        for (int q = 0; q < TT; ++q) {
+          const float dx = X[q][0] - A.x, dy = X[q][1] - A.y, dz = X[q][2] - A.z;
+          const float ri = rsqrt_approx_f(fmaf(dz, dz, fmaf(dy, dy, dx * dx)));
+          const float rf = fmaf(dz, B.y, fmaf(dy, B.x, dx * A.w)) * ri * (ri * ri);
+          p0[q] = fmaf(A.w, ri, fmaf(rf, dx, p0[q]));
+          p1[q] = fmaf(B.x, ri, fmaf(rf, dy, p1[q]));
+          p2[q] = fmaf(B.y, ri, fmaf(rf, dz, p2[q]));
+        }
+      }
+#pragma unroll
+      for (int q = 0; q < TT; ++q) {
+        if (!skip[q]) {
+          float s, e;
+          two_sum_f(hi[q][0], p0[q], s, e);
+          hi[q][0] = s;
+          lo[q][0] += e;
+          two_sum_f(hi[q][1], p1[q], s, e);
+          hi[q][1] = s;
+          lo[q][1] += e;
+          two_sum_f(hi[q][2], p2[q], s, e);
+          hi[q][2] = s;
+          lo[q][2] += e;
+        }
+      }
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int q = 0; q < TT; ++q)
+    if (valid[q])
+      for (int k = 0; k < 3; ++k) atomicAdd(u_out + tg[q] * 3 + k, ((double)hi[q][k] + (double)lo[q][k]) * kInv8Pi);
+}
+
 int launch_stokes(sbio_geom* g, const double* f, double* u, cudaStream_t st) {
-  (void)g; (void)f; (void)u; (void)st;
-  return set_error(SBIO_ENOTSUP, "Stokes single layer not built yet");
+  const GeomHost& h = g->h;
+  const DevGeom& d = g->d;
+  const int p = h.p;
+  if (p > 20) return set_error(SBIO_ENOTSUP, "Stokes single layer is built for p <= 20 (p = %d)", p);
+  stokes_near_launcher nl = stokes_near_lookup_a(p);
+  if (!nl) nl = stokes_near_lookup_b(p);
+  if (!nl) return set_error(SBIO_ENOTSUP, "no Stokes near-field kernel for p = %d", p);
+  const int p1 = p + 1, nc = (p + 1) * (p + 1), nc1 = (p1 + 1) * (p1 + 1), mw = 2 * p + 1, mw1 = 2 * p1 + 1;
+  const int nrow = h.n_q > h.n_v ? h.n_q : h.n_v;
+  const size_t smem = (size_t)(3 * nc + nc1 + 3 * nrow * mw + h.n_q * h.n_f + h.n_q * mw1) * sizeof(double);
+  if (smem > 48 * 1024)
+    SBIO_CUDA_TRY(cudaFuncSetAttribute(stokes_prep_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  phase_mark(g, 0, st);
+  stokes_prep_kernel<<<h.M, 256, smem, st>>>(p, h.n_v, h.n_phi, h.n_q, h.n_f, d.parts, d.xyz, d.w, d.ptab, d.trig,
+                                             d.sqrtw, d.st_qv, d.st_qw, d.st_qptab, d.st_qtrig, d.st_ext,
+                                             d.st_normc, f, d.st_coef, d.st_src64, d.st_src32, u);
+  count_launch();
+  SBIO_CUDA_TRY(cudaGetLastError());
+  phase_mark(g, 1, st);
+  nl(d, h.st_pairs_prolate, (int64_t)h.st_pair_t.size(), d.inv, u, st);
+  SBIO_CUDA_TRY(cudaGetLastError());
+  phase_mark(g, 2, st);
+  const int nt = (int)h.tiles.size();
+  if (h.precision == SBIO_FP64) {
+    const int64_t tb = (h.N + kFarTile - 1) / kFarTile;
+    const dim3 grid((unsigned)tb, (unsigned)far_split_count(tb, nt, h.far_splits));
+    stokes_far_fp64_kernel<<<grid, kFarTile, 0, st>>>(d.tiles, nt, d.st_src64, d.xyz, d.parts, d.skip_ptr,
+                                                      d.skip_idx, h.N, u);
+  } else {
+    constexpr int TT = 2;
+    const int64_t tb = (h.N + kFarTile * TT - 1) / (kFarTile * TT);
+    const dim3 grid((unsigned)tb, (unsigned)far_split_count(tb, nt, h.far_splits));
+    stokes_far_mixed_kernel<TT><<<grid, kFarTile, 0, st>>>(d.tiles, nt, d.st_src32, d.tgt32, d.cen32, d.skip_ptr,
+                                                           d.skip_idx, h.N, u);
+  }
+  count_launch();
+  SBIO_CUDA_TRY(cudaGetLastError());
+  phase_mark(g, 3, st);
+  return SBIO_OK;
 }
 
 }  // namespace sbio

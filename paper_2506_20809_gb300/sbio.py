@@ -75,6 +75,9 @@ _SIGS = {
     "sbio_geom_near_pairs": (C.c_int, [_vp, _vp, _vp]),
     "sbio_geom_set_precision": (C.c_int, [_vp, C.c_int32]),
     "sbio_geom_enable_timing": (C.c_int, [_vp, C.c_int32]),
+    "sbio_geom_set_launch_shape": (C.c_int, [_vp, C.c_int32, C.c_int32]),
+    "sbio_geom_autotune": (C.c_int, [_vp, _vp, C.POINTER(C.c_int32), C.POINTER(C.c_int32),
+                                     C.POINTER(C.c_double)]),
     "sbio_geom_phase_times": (C.c_int, [_vp, C.POINTER(C.c_double), C.POINTER(C.c_double),
                                         C.POINTER(C.c_double)]),
     "sbio_apply_laplace": (C.c_int, [_vp, _vp, _vp, _vp, _vp, _vp]),
@@ -201,6 +204,17 @@ def sbio_geom_near_pairs(g):
 
 def sbio_geom_set_precision(g, precision):
     _check(_lib.sbio_geom_set_precision(g, precision))
+
+
+def sbio_geom_set_launch_shape(g, far_tt, far_splits):
+    _check(_lib.sbio_geom_set_launch_shape(g, far_tt, far_splits))
+
+
+def sbio_geom_autotune(g, stream=None):
+    """Pick the fastest far-field launch shape; returns (tt, splits, ms)."""
+    a, b, c = C.c_int32(), C.c_int32(), C.c_double()
+    _check(_lib.sbio_geom_autotune(g, _stream(stream), C.byref(a), C.byref(b), C.byref(c)))
+    return a.value, b.value, c.value
 
 
 def sbio_geom_enable_timing(g, on=True):

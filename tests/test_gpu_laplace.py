@@ -95,6 +95,32 @@ def test_lattice_mixed(S, lattice):
     assert OL.normwise_rel_err(Dm, D64) < TOLMIX
 
 
+@pytest.mark.parametrize("tt,splits", [(1, 1), (2, 3), (4, 0), (1, 7)])
+def test_launch_shapes_agree(S, lattice, tt, splits):
+    """Far-field launch shapes (targets per thread, source splits) change only
+    the summation order."""
+    s, c, g, og, O = lattice
+    S64, D64 = gpu_apply(S, g, c[0], c[1], 7, S.SBIO_FP64)
+    S.sbio_geom_set_launch_shape(g.h, tt, splits)
+    S64b, D64b = gpu_apply(S, g, c[0], c[1], 7, S.SBIO_FP64)
+    Sm, Dm = gpu_apply(S, g, c[0], c[1], 7, S.SBIO_MIXED)
+    S.sbio_geom_set_launch_shape(g.h, 2, 0)
+    S.sbio_geom_set_precision(g.h, S.SBIO_FP64)
+    assert OL.normwise_rel_err(S64b, S64) < 1e-13 and OL.normwise_rel_err(D64b, D64) < 1e-13
+    assert OL.normwise_rel_err(Sm, S64) < TOLMIX and OL.normwise_rel_err(Dm, D64) < TOLMIX
+
+
+def test_autotune_keeps_results(S, lattice):
+    s, c, g, og, O = lattice
+    S.sbio_geom_set_precision(g.h, S.SBIO_MIXED)
+    tt, sp, ms = S.sbio_geom_autotune(g.h)
+    assert tt in (1, 2, 4) and sp >= 1 and ms > 0
+    Sm, Dm = gpu_apply(S, g, c[0], c[1], 7, S.SBIO_MIXED)
+    S64, D64 = gpu_apply(S, g, c[0], c[1], 7, S.SBIO_FP64)
+    S.sbio_geom_set_launch_shape(g.h, 2, 0)
+    assert OL.normwise_rel_err(Sm, S64) < TOLMIX and OL.normwise_rel_err(Dm, D64) < TOLMIX
+
+
 def test_single_operators(S, lattice):
     s, c, g, og, O = lattice
     Sr, _ = O.apply(c[0], None, "method")
