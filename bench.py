@@ -46,6 +46,10 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64-context", action="store_true")
     ap.add_argument("--oracle-sample", type=int, default=48, help="targets in the oracle's timed sample")
+    ap.add_argument("--workload", default="poly200", choices=["poly200", "stokes100", "batch64", "serve"])
+    ap.add_argument("--rates", default="50,100,200,500,1000,2000", help="serve: arrival rates (req/s)")
+    ap.add_argument("--requests", type=int, default=48, help="serve: requests per rate")
+    ap.add_argument("--slots", type=int, default=4, help="serve: concurrent request slots")
     return ap.parse_args()
 
 
@@ -342,11 +346,231 @@ def run_ours(args, ws, rank, lrank):
         print(json.dumps(line), flush=True)
 
 
+def _event_time(stream, fn):
+    import torch
+
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    fn()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1)
+
+
+def run_stokes100(args, ws, rank, lrank):
+    import torch
+
+    import __graft_entry__ as GE
+
+    GE.build()
+    from paper_2506_20809_gb300 import inputs as I
+    from paper_2506_20809_gb300 import sbio as S
+
+    torch.cuda.set_device(lrank)
+    susp = I.config_suspension(3)
+    f = I.config_coefficients(susp, 0, ndens=3).transpose(1, 0, 2).copy()
+    ctx = S.sbio_ctx_create(lrank, 0)
+    g = S.Geometry(ctx, susp, precision=S.SBIO_MIXED)
+    tune = S.sbio_geom_autotune(g.h)
+    S.sbio_geom_enable_timing(g.h, True)
+    fd = torch.from_numpy(f).cuda()
+    u = torch.empty((g.N, 3), dtype=torch.float64, device="cuda")
+    st = torch.cuda.current_stream()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    for _ in range(args.warmup):
+        S.sbio_apply_stokes_sl(g.h, fd, u)
+    ms, ph = [], []
+    l0 = S.sbio_launch_count()
+    for _ in range(args.steps):
+        flush.zero_()
+        ms.append(_event_time(st, lambda: S.sbio_apply_stokes_sl(g.h, fd, u)))
+        ph.append(S.sbio_geom_phase_times(g.h))
+    launches = S.sbio_launch_count() - l0
+    um = u.clone()
+    S.sbio_geom_set_precision(g.h, S.SBIO_FP64)
+    S.sbio_apply_stokes_sl(g.h, fd, u)
+    t64 = _event_time(st, lambda: S.sbio_apply_stokes_sl(g.h, fd, u))
+    err = float((um - u).abs().max() / u.abs().max())
+    far_ms = statistics.mean(x[2] for x in ph)
+    ach = 28 * g.n_far / (far_ms * 1e-3) / 1e12
+    line = {"metric": "Stokes single-layer applies/s (all surface nodes)", "value": 1e3 / statistics.mean(ms),
+            "unit": "applies/s", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": statistics.mean(ms), "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32+f64", "data": "synthetic",
+            "config": {"workload": "stokes100_p12", "M": susp.M, "p": susp.p, "targets": g.N,
+                       "near_and_self_pairs": g.n_near + g.N, "far_pairs_per_apply": g.n_far,
+                       "far_launch": {"targets_per_thread": tune[0], "source_splits": tune[1]}},
+            "phase_ms": {"prep": statistics.mean(x[0] for x in ph), "near_self": statistics.mean(x[1] for x in ph),
+                         "far": far_ms},
+            "roofline": {"kernel": "stokes_far_mixed_kernel", "bound": "alu", "achieved": ach,
+                         "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": ach / FP32_PEAK_TFLOPS,
+                         "traffic": None},
+            "fp64_gpu_applies_per_s": 1e3 / t64, "rel_err_vs_fp64_gpu": err, "gpu_launches": int(launches)}
+    g.close()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+def run_batch64(args, ws, rank, lrank):
+    import numpy as np
+    import torch
+
+    from paper_2506_20809_gb300 import inputs as I
+
+    susps = I.batch_suspensions(64, workers=min(16, os.cpu_count() or 1))   # before CUDA starts
+    import __graft_entry__ as GE
+
+    GE.build()
+    from paper_2506_20809_gb300 import sbio as S
+
+    torch.cuda.set_device(lrank)
+    ctx = S.sbio_ctx_create(lrank, 0)
+    geoms = [S.Geometry(ctx, s, precision=S.SBIO_MIXED) for s in susps]
+    coefs = [I.config_coefficients(s, 1) for s in susps]
+    sig = [torch.from_numpy(c[0]).cuda() for c in coefs]
+    mu = [torch.from_numpy(c[1]).cuda() for c in coefs]
+    So = [torch.empty(g.N, dtype=torch.float64, device="cuda") for g in geoms]
+    Do = [torch.empty_like(o) for o in So]
+    st = torch.cuda.current_stream()
+    b = S.sbio_batch_create(ctx, geoms)
+    best = None
+    for tt in (1, 2, 4):                               # autotune the persistent far kernel
+        S.sbio_batch_set_far_tt(b, tt)
+        S.sbio_batch_apply(b, sig, mu, So, Do)
+        t = min(_event_time(st, lambda: S.sbio_batch_apply(b, sig, mu, So, Do)) for _ in range(2))
+        if best is None or t < best[1]:
+            best = (tt, t)
+    S.sbio_batch_set_far_tt(b, best[0])
+    for _ in range(args.warmup):
+        S.sbio_batch_apply(b, sig, mu, So, Do)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    ms = []
+    l0 = S.sbio_launch_count()
+    for _ in range(args.steps):
+        flush.zero_()
+        ms.append(_event_time(st, lambda: S.sbio_batch_apply(b, sig, mu, So, Do)))
+    launches = S.sbio_launch_count() - l0
+    info = S.sbio_batch_info(b)
+    # the same work as one apply per suspension, one after another (mixed)
+    seq = _event_time(st, lambda: [S.sbio_apply_laplace(g.h, sig[k], mu[k], So[k], Do[k]) for k, g in enumerate(geoms)])
+    # plain FP64 form, one apply per suspension
+    for g in geoms:
+        S.sbio_geom_set_precision(g.h, S.SBIO_FP64)
+    f64 = _event_time(st, lambda: [S.sbio_apply_laplace(g.h, sig[k], mu[k], So[k], Do[k]) for k, g in enumerate(geoms)])
+    mean = statistics.mean(ms)
+    line = {"metric": "BIO applies/s (batched Laplace S+D, 64 suspensions per step)",
+            "value": 64 * 1e3 / mean, "unit": "applies/s", "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": mean, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+            "config": {"workload": "batch64", "suspensions": 64, "M": [s.M for s in susps], "p": [s.p for s in susps],
+                       "far_pairs_per_step": info["far_pairs"], "work_items": info["n_items"],
+                       "persistent_grid": info["grid"], "far_targets_per_thread": best[0],
+                       "l2": "flushed by a 256 MiB write before every timed step"},
+            "gpairs_per_s": info["far_pairs"] / (mean * 1e-3) / 1e9,
+            "sequential_mixed_ms": seq, "fp64_plain_ms": f64,
+            "speedup_vs_fp64_plain": f64 / mean, "speedup_vs_sequential_mixed": seq / mean,
+            "gpu_launches": int(launches)}
+    S.sbio_batch_destroy(b)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+def run_serve(args, ws, rank, lrank):
+    import math
+    import numpy as np
+    import torch
+
+    from paper_2506_20809_gb300 import inputs as I
+
+    # a pool of request geometries (drawn before CUDA starts), sampled by the stream
+    rng = np.random.default_rng(2024)
+    specs = []
+    for k in range(16):
+        M = int(round(math.exp(rng.uniform(math.log(20), math.log(500)))))
+        specs.append((M, int(rng.choice([8, 12, 16]))))
+    import concurrent.futures as cf
+    import multiprocessing as mp
+
+    with cf.ProcessPoolExecutor(max_workers=min(16, os.cpu_count() or 1), mp_context=mp.get_context("spawn")) as ex:
+        pool = list(ex.map(I.rsa_suspension, [m for m, _ in specs], [0.20] * 16, range(1000, 1016),
+                           [p for _, p in specs]))
+    import __graft_entry__ as GE
+
+    GE.build()
+    from paper_2506_20809_gb300 import sbio as S
+
+    torch.cuda.set_device(lrank)
+    ctx = S.sbio_ctx_create(lrank, 0)
+    free, total = torch.cuda.mem_get_info()
+    budget = int(0.5 * free)
+
+    def stream_of(rate, seed, precision, n_req):
+        reqs = I.poisson_requests(rate, 1e9, seed=seed, M_range=(20, 500), max_requests=n_req)
+        prepared = []
+        for k, r in enumerate(reqs):
+            s = pool[r["seed"] % len(pool)]
+            op = S.SBIO_OP_LAPLACE if r["op"] == "laplace" else S.SBIO_OP_STOKES
+            N = s.M * (s.p + 1) * 2 * (s.p + 1)
+            nc = (s.p + 1) ** 2
+            crng = np.random.default_rng([seed, k])
+            if op == S.SBIO_OP_LAPLACE:
+                coef = np.ascontiguousarray(np.stack([I.coefficients(crng, s.M, s.p, 2).transpose(1, 0, 2)
+                                                      for _ in range(10)]))
+                out = np.zeros((10, 2 * N))
+            else:
+                coef = np.ascontiguousarray(np.stack([I.coefficients(crng, s.M, s.p, 3) for _ in range(10)]))
+                out = np.zeros((10, N, 3))
+            sph = S.make_spheroids(s.kind, s.A, s.C, s.center, s.quat)
+            prepared.append((r["t"], op, sph, s.p, coef, out))
+        srv = S.sbio_server_create(ctx, args.slots, budget)
+        t0 = time.perf_counter()
+        tickets = []
+        for (ta, op, sph, p, coef, out) in prepared:
+            delay = t0 + ta - time.perf_counter()
+            if delay > 0:
+                time.sleep(delay)
+            tickets.append(S.sbio_server_submit(srv, op, sph, p, coef, out, 10, precision=precision))
+        lat = []
+        for t in tickets:
+            stt, l, svc = S.sbio_server_wait(srv, t, 3600.0)
+            assert stt == 0
+            lat.append(l)
+        makespan = time.perf_counter() - t0
+        S.sbio_server_destroy(srv)
+        lat.sort()
+        return {"rate": rate, "requests": len(lat), "applies_per_s": 10 * len(lat) / makespan,
+                "p50_ms": lat[len(lat) // 2], "p99_ms": lat[min(len(lat) - 1, int(0.99 * len(lat)))],
+                "makespan_s": makespan}
+
+    rates = [float(x) for x in args.rates.split(",")]
+    rows = [stream_of(r, 7, S.SBIO_MIXED, args.requests) for r in rates]
+    ref = stream_of(rates[-1], 7, S.SBIO_FP64, min(12, args.requests))
+    mixed_same = stream_of(rates[-1], 7, S.SBIO_MIXED, min(12, args.requests))
+    best = max(rows, key=lambda r: r["applies_per_s"])
+    line = {"metric": "served BIO applies/s (Poisson stream, 10 applies per request) and p50/p99 latency",
+            "value": best["applies_per_s"], "unit": "applies/s", "n_gpus": ws, "steps": len(rates),
+            "warmup": 0, "ms_per_step": None, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32+f64", "data": "synthetic",
+            "config": {"workload": "serve", "slots": args.slots, "requests_per_rate": args.requests,
+                       "pool": [{"M": m, "p": p} for m, p in specs], "mem_budget_bytes": budget,
+                       "ops": "Laplace S+D or Stokes single layer, probability 1/2"},
+            "sweep": rows, "fp64_plain_at_max_rate": ref, "mixed_same_requests_as_fp64": mixed_same,
+            "speedup_vs_fp64_plain": mixed_same["applies_per_s"] / ref["applies_per_s"]}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     ws, rank, lrank = dist_setup()
     if args.impl == "reference":
         run_reference(args, ws, rank)
+    elif args.workload == "stokes100":
+        run_stokes100(args, ws, rank, lrank)
+    elif args.workload == "batch64":
+        run_batch64(args, ws, rank, lrank)
+    elif args.workload == "serve":
+        run_serve(args, ws, rank, lrank)
     else:
         run_ours(args, ws, rank, lrank)
     if ws > 1:

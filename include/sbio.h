@@ -208,6 +208,89 @@ int sbio_apply_laplace_host(sbio_geom* g, const double* sigma_tilde_host, const 
  * u_out: device, N x 3 FP64 (row t = velocity at node t).  Asynchronous. */
 int sbio_apply_stokes_sl(sbio_geom* g, const double* f_tilde, double* u_out, void* stream);
 
+/* ---- batched apply over many suspensions ------------------------------
+ * A batch groups resident geometries (any mix of M and p, all in SBIO_MIXED
+ * mode, same context).  One batch apply computes S[sigma_s] and D[mu_s] for
+ * every suspension s as one CUDA graph: the synthesis/self kernels, the
+ * near-field kernels on a second branch, and a single persistent far-field
+ * kernel whose CTAs pull (suspension, target block, source-tile range) work
+ * items from an atomic counter, longest first.  No data is shared between
+ * suspensions (SURVEY: independent problems).  The graph is captured on the
+ * first apply and replayed while the same buffers are passed; new buffers
+ * trigger a re-capture (which synchronises `stream`). */
+typedef struct sbio_batch sbio_batch;
+
+/* geoms: host array of n geometry handles, kept alive by the caller until
+ * sbio_batch_destroy.  Errors: SBIO_EINVAL (null, other context, FP64 mode). */
+int sbio_batch_create(sbio_ctx* ctx, sbio_geom* const* geoms, int32_t n, sbio_batch** out);
+int sbio_batch_destroy(sbio_batch* b);
+
+/* Work items, total far pairs per apply, targets per thread of the far
+ * kernel and its persistent grid size (outputs may be NULL). */
+int sbio_batch_info(const sbio_batch* b, int64_t* n_items, int64_t* far_pairs, int32_t* far_tt, int32_t* grid);
+
+/* Targets per thread (1, 2, 4) of the persistent far kernel; rebuilds the
+ * work list and drops the captured graph. */
+int sbio_batch_set_far_tt(sbio_batch* b, int32_t far_tt);
+
+/* sigma, mu, S_out, D_out: host arrays of n device pointers (layouts as in
+ * sbio_apply_laplace for each suspension).  Asynchronous on `stream`. */
+int sbio_batch_apply(sbio_batch* b, const double* const* sigma, const double* const* mu,
+                     double* const* S_out, double* const* D_out, void* stream);
+
+/* ---- request serving with continuous batching ----------------------------
+ * A server owns n_slots worker threads, each with its own CUDA stream, and a
+ * device-memory budget.  Requests are admitted first-in first-out as soon as
+ * a slot is free and the request's estimated footprint fits the budget (a
+ * request that does not fit waits until running ones release memory; a lone
+ * request is always admitted).  An admitted request builds its geometry once,
+ * runs n_applies applies with fresh coefficients while geometry and near
+ * lists stay resident, writes every result to its host buffer and releases the
+ * geometry.  Work of different slots overlaps on the device. */
+#define SBIO_OP_LAPLACE 0   /* S[sigma] and D[mu] (sbio_apply_laplace) */
+#define SBIO_OP_STOKES 1    /* Stokes single layer (sbio_apply_stokes_sl) */
+
+typedef struct sbio_server sbio_server;
+
+/* One request.  coef_host: n_applies consecutive coefficient sets in host
+ * memory (Laplace: sigma~ then mu^, 2 x M x (p+1)^2 each; Stokes: M x 3 x
+ * (p+1)^2 each).  out_host: n_applies consecutive results (Laplace: S then D,
+ * 2 x N each; Stokes: N x 3 each).  Both buffers stay owned by the caller and
+ * must stay valid until sbio_server_wait returns for the ticket; sph is copied
+ * at submission. */
+typedef struct {
+  int32_t op;
+  int32_t n_applies;
+  const sbio_spheroid* sph;
+  int32_t M;
+  int32_t reserved;
+  sbio_options opts;
+  const double* coef_host;
+  double* out_host;
+} sbio_request;
+
+/* mem_budget_bytes = 0: no budget.  The server's geometries belong to ctx. */
+int sbio_server_create(sbio_ctx* ctx, int32_t n_slots, size_t mem_budget_bytes, sbio_server** out);
+
+/* Validates and queues a request; returns its ticket. */
+int sbio_server_submit(sbio_server* s, const sbio_request* r, int64_t* ticket);
+
+/* Waits at most timeout_s seconds for a ticket (SBIO_ETIMEOUT if not done; the
+ * ticket stays valid).  status: 0 or the request's error code; latency_ms:
+ * submission to last result on the host; service_ms: admission to last result.
+ * A ticket can be waited for successfully once. */
+int sbio_server_wait(sbio_server* s, int64_t ticket, double timeout_s, int32_t* status, double* latency_ms,
+                     double* service_ms);
+
+/* Completed requests and applies so far, running and queued requests, device
+ * bytes currently reserved by admitted requests (outputs may be NULL). */
+int sbio_server_stats(sbio_server* s, int64_t* completed, int64_t* applies, int32_t* running, int32_t* queued,
+                      size_t* reserved);
+
+/* Drains the queue (every submitted request runs), joins the workers and
+ * releases the server. */
+int sbio_server_destroy(sbio_server* s);
+
 /* Allocation-free self interaction (no counterpart in the paper; a service for
  * callers that cannot allocate device memory).
  *

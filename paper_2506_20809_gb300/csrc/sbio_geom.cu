@@ -29,6 +29,8 @@ void clear_error() { t_err.clear(); }
 
 void count_launch(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 
+int64_t launch_counter() { return g_launches.load(); }
+
 int dev_alloc(sbio_geom* g, void** ptr, size_t bytes, const char* what) {
   *ptr = nullptr;
   if (bytes == 0) return SBIO_OK;
@@ -39,7 +41,7 @@ int dev_alloc(sbio_geom* g, void** ptr, size_t bytes, const char* what) {
     return set_error(SBIO_ENOMEM, "device budget exceeded allocating %s (%zu bytes, %zu of %zu in use)", what,
                      bytes, prev, c->budget);
   }
-  cudaError_t e = cudaMalloc(ptr, bytes);
+  cudaError_t e = g->async_alloc ? cudaMallocAsync(ptr, bytes, g->setup_stream) : cudaMalloc(ptr, bytes);
   if (e != cudaSuccess) {
     c->used.fetch_sub(bytes);
     *ptr = nullptr;
@@ -525,6 +527,10 @@ static int build_device(sbio_geom* g) {
 
 static void free_geom(sbio_geom* g) {
   if (!g) return;
+  if (g->async_alloc) {
+    for (void* p : g->allocs) cudaFreeAsync(p, g->setup_stream);
+    g->allocs.clear();
+  }
   for (int k = 0; k < 4; ++k)
     if (g->ev[k]) {
       cudaEventDestroy(g->ev[k]);
@@ -534,6 +540,44 @@ static void free_geom(sbio_geom* g) {
   if (g->ctx) g->ctx->used.fetch_sub(g->bytes);
   g->allocs.clear();
   g->bytes = 0;
+}
+
+static int geom_create_impl(sbio_ctx* ctx, const sbio_spheroid* sph, int32_t M, const sbio_options* opts,
+                            cudaStream_t stream, bool async_alloc, sbio_geom** out) {
+  clear_error();
+  if (!ctx || !out) return set_error(SBIO_EINVAL, "null context or output pointer");
+  *out = nullptr;
+  int rc = validate(sph, M, opts);
+  if (rc) return rc;
+  SBIO_CUDA_TRY(cudaSetDevice(ctx->device));
+  sbio_geom* g = new sbio_geom();
+  g->ctx = ctx;
+  g->setup_stream = stream;
+  g->async_alloc = async_alloc;
+  rc = build_host(g->h, sph, M, opts);
+  if (!rc) rc = build_near(g->h);
+  if (!rc) rc = build_device(g);
+  if (rc) {
+    free_geom(g);
+    delete g;
+    return rc;
+  }
+  ctx->n_geoms.fetch_add(1);
+  *out = g;
+  return SBIO_OK;
+}
+
+int geom_create_async(sbio_ctx* ctx, const sbio_spheroid* sph, int32_t M, const sbio_options* opts,
+                      cudaStream_t st, sbio_geom** out) {
+  return geom_create_impl(ctx, sph, M, opts, st, true, out);
+}
+
+void geom_destroy_async(sbio_geom* g, cudaStream_t st) {
+  if (!g) return;
+  g->setup_stream = st;
+  free_geom(g);
+  g->ctx->n_geoms.fetch_sub(1);
+  delete g;
 }
 
 }  // namespace sbio
@@ -578,26 +622,7 @@ int sbio_ctx_mem_used(const sbio_ctx* ctx, size_t* bytes) {
 
 int sbio_geom_create(sbio_ctx* ctx, const sbio_spheroid* sph, int32_t M, const sbio_options* opts, void* stream,
                      sbio_geom** out) {
-  clear_error();
-  if (!ctx || !out) return set_error(SBIO_EINVAL, "null context or output pointer");
-  *out = nullptr;
-  int rc = validate(sph, M, opts);
-  if (rc) return rc;
-  SBIO_CUDA_TRY(cudaSetDevice(ctx->device));
-  sbio_geom* g = new sbio_geom();
-  g->ctx = ctx;
-  g->setup_stream = (cudaStream_t)stream;
-  rc = build_host(g->h, sph, M, opts);
-  if (!rc) rc = build_near(g->h);
-  if (!rc) rc = build_device(g);
-  if (rc) {
-    free_geom(g);
-    delete g;
-    return rc;
-  }
-  ctx->n_geoms.fetch_add(1);
-  *out = g;
-  return SBIO_OK;
+  return geom_create_impl(ctx, sph, M, opts, (cudaStream_t)stream, false, out);
 }
 
 int sbio_geom_destroy(sbio_geom* g) {

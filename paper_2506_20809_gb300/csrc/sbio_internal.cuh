@@ -95,6 +95,10 @@ struct sbio_geom {
   // synth, near and far phases of the last apply
   bool timing = false;
   cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+  // stream-ordered allocation on setup_stream (used by the serving engine so
+  // that creating / releasing one request's geometry does not synchronise the
+  // device)
+  bool async_alloc = false;
 };
 
 namespace sbio {
@@ -103,6 +107,7 @@ namespace sbio {
 int set_error(int code, const char* fmt, ...);
 void clear_error();
 void count_launch(int n = 1);
+int64_t launch_counter();
 
 // host set-up helpers shared by the translation units (defined in sbio_geom.cu)
 void gauss_legendre(int n, std::vector<double>& x, std::vector<double>& w);
@@ -110,6 +115,11 @@ void ferrers(double v, int N, double* P);
 double kfact(int n, int m);
 int validate(const sbio_spheroid* sph, int32_t M, const sbio_options* o);
 int build_host(GeomHost& h, const sbio_spheroid* sph, int32_t M, const sbio_options* o);
+
+// geometry creation / release with stream-ordered allocation on `st`
+int geom_create_async(sbio_ctx* ctx, const sbio_spheroid* sph, int32_t M, const sbio_options* opts,
+                      cudaStream_t st, sbio_geom** out);
+void geom_destroy_async(sbio_geom* g, cudaStream_t st);
 
 // device allocation tracked against the context budget
 int dev_alloc(sbio_geom* g, void** ptr, size_t bytes, const char* what);
@@ -128,6 +138,21 @@ inline near_launcher near_for_p(int p) {
   return f;
 }
 
+// Far-field view of one suspension for the persistent batched kernel.
+struct FarDesc {
+  const int4* tiles;
+  const float4* src32;
+  const float4* tgt32;
+  const float4* cen32;
+  const int32_t* skip_ptr;
+  const int32_t* skip_idx;
+  int64_t N;
+  double* S;
+  double* D;
+};
+int launch_far_persistent(const FarDesc* descs, const int4* items, int n_items, int* counter, int tt, int grid,
+                          cudaStream_t st);
+
 // record phase event k (0..3) when timing is enabled
 inline void phase_mark(sbio_geom* g, int k, cudaStream_t st) {
   if (g->timing && g->ev[k]) cudaEventRecord(g->ev[k], st);
@@ -136,6 +161,9 @@ inline void phase_mark(sbio_geom* g, int k, cudaStream_t st) {
 // kernel entry points (defined in the kernel translation units)
 int launch_laplace(sbio_geom* g, const double* sigma, const double* mu, double* S, double* D,
                    uint32_t parts, cudaStream_t st);
+int launch_synth(sbio_geom* g, const double* sigma, const double* mu, double* S, double* D, bool write_self,
+                 cudaStream_t st);
+int launch_near(sbio_geom* g, double* S, double* D, cudaStream_t st);
 int launch_stokes(sbio_geom* g, const double* f, double* u, cudaStream_t st);
 
 // source splits of the far-field grid (gridDim.y) for `target_blocks` target

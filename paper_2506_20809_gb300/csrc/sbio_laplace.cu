@@ -27,20 +27,17 @@ struct alignas(32) dbl4 {
 // ---------------------------------------------------------------------------
 // synth: densities at the nodes, far-field sources, near coefficients, self
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) synth_kernel(int p, int n_v, int n_phi, const PartGeom* __restrict__ parts,
-                                                    const double* __restrict__ xyz, const double* __restrict__ nrm,
-                                                    const double* __restrict__ w, const double* __restrict__ ptab,
-                                                    const double* __restrict__ trig,
-                                                    const double* __restrict__ sqrtw,
-                                                    const double* __restrict__ mult,
-                                                    const double* __restrict__ normc,
-                                                    const double* __restrict__ sigma, const double* __restrict__ mu,
-                                                    int write_self, double* __restrict__ S_out,
-                                                    double* __restrict__ D_out, double* __restrict__ src64,
-                                                    float4* __restrict__ src32, double* __restrict__ alpha,
-                                                    double* __restrict__ beta) {
-  extern __shared__ double sm[];
-  const int i = blockIdx.x;
+// One CTA, one particle i.  `sm` holds 2 (p+1)^2 + 4 (p+1)(2p+1) doubles.
+__device__ __forceinline__ void synth_particle(int i, double* sm, int p, int n_v, int n_phi,
+                                               const PartGeom* __restrict__ parts, const double* __restrict__ xyz,
+                                               const double* __restrict__ nrm, const double* __restrict__ w,
+                                               const double* __restrict__ ptab, const double* __restrict__ trig,
+                                               const double* __restrict__ sqrtw, const double* __restrict__ mult,
+                                               const double* __restrict__ normc, const double* __restrict__ sigma,
+                                               const double* __restrict__ mu, int write_self,
+                                               double* __restrict__ S_out, double* __restrict__ D_out,
+                                               double* __restrict__ src64, float4* __restrict__ src32,
+                                               double* __restrict__ alpha, double* __restrict__ beta) {
   const int nc = (p + 1) * (p + 1), nm = nm_count(p), nmw = 2 * p + 1;
   const int G = n_v * n_phi;
   double* c_sig = sm;                 // nc
@@ -111,6 +108,23 @@ __global__ void __launch_bounds__(256) synth_kernel(int p, int n_v, int n_phi, c
     if (S_out) S_out[t] = write_self ? vS : 0.0;
     if (D_out) D_out[t] = write_self ? vD : 0.0;
   }
+}
+
+__global__ void __launch_bounds__(256) synth_kernel(int p, int n_v, int n_phi, const PartGeom* __restrict__ parts,
+                                                    const double* __restrict__ xyz, const double* __restrict__ nrm,
+                                                    const double* __restrict__ w, const double* __restrict__ ptab,
+                                                    const double* __restrict__ trig,
+                                                    const double* __restrict__ sqrtw,
+                                                    const double* __restrict__ mult,
+                                                    const double* __restrict__ normc,
+                                                    const double* __restrict__ sigma, const double* __restrict__ mu,
+                                                    int write_self, double* __restrict__ S_out,
+                                                    double* __restrict__ D_out, double* __restrict__ src64,
+                                                    float4* __restrict__ src32, double* __restrict__ alpha,
+                                                    double* __restrict__ beta) {
+  extern __shared__ double sm[];
+  synth_particle(blockIdx.x, sm, p, n_v, n_phi, parts, xyz, nrm, w, ptab, trig, sqrtw, mult, normc, sigma, mu,
+                 write_self, S_out, D_out, src64, src32, alpha, beta);
 }
 
 // ---------------------------------------------------------------------------
@@ -200,22 +214,21 @@ __global__ void __launch_bounds__(kFarTile) far_fp64_kernel(const int4* __restri
 // their own centre, so the FP32 difference X - y_rel carries an error
 // relative to |x - y| rather than to the box size.  Each tile's FP32 partial
 // sum is folded into an (hi, lo) pair by TwoSum.
+// One CTA: targets of target block `tb` against source tiles [t_lo, t_hi).
 template <int TT, bool DO_S, bool DO_D>
-__global__ void __launch_bounds__(kFarTile) far_mixed_kernel(const int4* __restrict__ tiles, int n_tiles,
-                                                             const float4* __restrict__ src32,
-                                                             const float4* __restrict__ tgt32,
-                                                             const float4* __restrict__ cen32,
-                                                             const int32_t* __restrict__ skip_ptr,
-                                                             const int32_t* __restrict__ skip_idx, int64_t N,
-                                                             double* __restrict__ S_out, double* __restrict__ D_out) {
-  __shared__ float4 sh[kFarTile * 2];
+__device__ __forceinline__ void far_mixed_block(float4* sh, int64_t tb, int t_lo, int t_hi,
+                                                const int4* __restrict__ tiles, const float4* __restrict__ src32,
+                                                const float4* __restrict__ tgt32, const float4* __restrict__ cen32,
+                                                const int32_t* __restrict__ skip_ptr,
+                                                const int32_t* __restrict__ skip_idx, int64_t N,
+                                                double* __restrict__ S_out, double* __restrict__ D_out) {
   int64_t tg[TT];
   bool valid[TT];
   float xh[TT][3], xo[TT][3];
   int sp[TT], nxt[TT];
 #pragma unroll
   for (int q = 0; q < TT; ++q) {
-    tg[q] = ((int64_t)blockIdx.x * TT + q) * kFarTile + threadIdx.x;
+    tg[q] = (tb * TT + q) * kFarTile + threadIdx.x;
     valid[q] = tg[q] < N;
     xh[q][0] = xh[q][1] = xh[q][2] = 0.f;
     xo[q][0] = xo[q][1] = xo[q][2] = 0.f;
@@ -239,8 +252,6 @@ __global__ void __launch_bounds__(kFarTile) far_mixed_kernel(const int4* __restr
     skip[q] = true;
   }
   int cur = -1;
-  const int per = (n_tiles + gridDim.y - 1) / gridDim.y;
-  const int t_lo = blockIdx.y * per, t_hi = min(n_tiles, t_lo + per);
   for (int tl = t_lo; tl < t_hi; ++tl) {
     const int4 tile = tiles[tl];
     if (tile.x != cur) {
@@ -313,6 +324,21 @@ __global__ void __launch_bounds__(kFarTile) far_mixed_kernel(const int4* __restr
   }
 }
 
+template <int TT, bool DO_S, bool DO_D>
+__global__ void __launch_bounds__(kFarTile) far_mixed_kernel(const int4* __restrict__ tiles, int n_tiles,
+                                                             const float4* __restrict__ src32,
+                                                             const float4* __restrict__ tgt32,
+                                                             const float4* __restrict__ cen32,
+                                                             const int32_t* __restrict__ skip_ptr,
+                                                             const int32_t* __restrict__ skip_idx, int64_t N,
+                                                             double* __restrict__ S_out, double* __restrict__ D_out) {
+  __shared__ float4 sh[kFarTile * 2];
+  const int per = (n_tiles + gridDim.y - 1) / gridDim.y;
+  const int t_lo = blockIdx.y * per, t_hi = min(n_tiles, t_lo + per);
+  far_mixed_block<TT, DO_S, DO_D>(sh, blockIdx.x, t_lo, t_hi, tiles, src32, tgt32, cen32, skip_ptr, skip_idx, N,
+                                  S_out, D_out);
+}
+
 // Number of source splits so that the grid holds about `waves` resident
 // rounds of CTAs on the device (never more splits than tiles).
 int far_split_count(int64_t target_blocks, int n_tiles, int requested) {
@@ -374,28 +400,76 @@ static void launch_far(sbio_geom* g, double* S, double* D, cudaStream_t st) {
   count_launch();
 }
 
-int launch_laplace(sbio_geom* g, const double* sigma, const double* mu, double* S, double* D, uint32_t parts,
-                   cudaStream_t st) {
+// Persistent far field over many suspensions: CTAs pull work items
+// (suspension, target block, first tile, end tile) from an atomic counter
+// until the list is exhausted (items are ordered longest first).
+template <int TT>
+__global__ void __launch_bounds__(kFarTile) far_persistent_kernel(const FarDesc* __restrict__ descs,
+                                                                  const int4* __restrict__ items, int n_items,
+                                                                  int* __restrict__ counter) {
+  __shared__ float4 sh[kFarTile * 2];
+  __shared__ int s_item;
+  for (;;) {
+    if (threadIdx.x == 0) s_item = atomicAdd(counter, 1);
+    __syncthreads();
+    const int it = s_item;
+    __syncthreads();
+    if (it >= n_items) break;
+    const int4 w = items[it];
+    const FarDesc& D = descs[w.x];
+    far_mixed_block<TT, true, true>(sh, w.y, w.z, w.w, D.tiles, D.src32, D.tgt32, D.cen32, D.skip_ptr, D.skip_idx,
+                                    D.N, D.S, D.D);
+  }
+}
+
+int launch_far_persistent(const FarDesc* descs, const int4* items, int n_items, int* counter, int tt, int grid,
+                          cudaStream_t st) {
+  switch (tt) {
+    case 1: far_persistent_kernel<1><<<grid, kFarTile, 0, st>>>(descs, items, n_items, counter); break;
+    case 4: far_persistent_kernel<4><<<grid, kFarTile, 0, st>>>(descs, items, n_items, counter); break;
+    default: far_persistent_kernel<2><<<grid, kFarTile, 0, st>>>(descs, items, n_items, counter); break;
+  }
+  count_launch();
+  SBIO_CUDA_TRY(cudaGetLastError());
+  return SBIO_OK;
+}
+
+int launch_synth(sbio_geom* g, const double* sigma, const double* mu, double* S, double* D, bool write_self,
+                 cudaStream_t st) {
   const GeomHost& h = g->h;
   const DevGeom& d = g->d;
-  const double* inv = d.inv;
   const int nmw = 2 * h.p + 1, nc = (h.p + 1) * (h.p + 1);
   const size_t smem = (size_t)(2 * nc + 4 * h.n_v * nmw) * sizeof(double);
-  phase_mark(g, 0, st);
   if (smem > 48 * 1024) {
     SBIO_CUDA_TRY(cudaFuncSetAttribute(synth_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   }
   synth_kernel<<<h.M, 256, smem, st>>>(h.p, h.n_v, h.n_phi, d.parts, d.xyz, d.nrm, d.w, d.ptab, d.trig, d.sqrtw,
-                                       d.mult, d.normc, sigma, mu, (parts & SBIO_PART_SELF) ? 1 : 0, S, D, d.src64,
-                                       d.src32, d.alpha, d.beta);
+                                       d.mult, d.normc, sigma, mu, write_self ? 1 : 0, S, D, d.src64, d.src32,
+                                       d.alpha, d.beta);
   count_launch();
   SBIO_CUDA_TRY(cudaGetLastError());
+  return SBIO_OK;
+}
+
+int launch_near(sbio_geom* g, double* S, double* D, cudaStream_t st) {
+  const GeomHost& h = g->h;
+  if (h.pair_t.empty()) return SBIO_OK;
+  near_launcher f = near_for_p(h.p);
+  if (!f) return set_error(SBIO_ENOTSUP, "no near-field kernel for p = %d", h.p);
+  f(g->d, h.n_pairs_prolate, (int64_t)h.pair_t.size(), g->d.inv, S, D, st);
+  SBIO_CUDA_TRY(cudaGetLastError());
+  return SBIO_OK;
+}
+
+int launch_laplace(sbio_geom* g, const double* sigma, const double* mu, double* S, double* D, uint32_t parts,
+                   cudaStream_t st) {
+  phase_mark(g, 0, st);
+  int rc = launch_synth(g, sigma, mu, S, D, (parts & SBIO_PART_SELF) != 0, st);
+  if (rc) return rc;
   phase_mark(g, 1, st);
-  if ((parts & SBIO_PART_NEAR) && !h.pair_t.empty()) {
-    near_launcher f = near_for_p(h.p);
-    if (!f) return set_error(SBIO_ENOTSUP, "no near-field kernel for p = %d", h.p);
-    f(d, h.n_pairs_prolate, (int64_t)h.pair_t.size(), inv, S, D, st);
-    SBIO_CUDA_TRY(cudaGetLastError());
+  if (parts & SBIO_PART_NEAR) {
+    rc = launch_near(g, S, D, st);
+    if (rc) return rc;
   }
   phase_mark(g, 2, st);
   if (parts & SBIO_PART_FAR) {
@@ -488,8 +562,9 @@ int sbio_geom_autotune(sbio_geom* g, void* stream, int32_t* far_tt, int32_t* far
     const int tt = (h.precision == SBIO_FP64) ? 1 : tts[a];
     const int64_t tb = (h.N + (int64_t)kFarTile * tt - 1) / ((int64_t)kFarTile * tt);
     const int base = far_split_count(tb, nt, 0);
-    const int cands[4] = {base > 1 ? base / 2 : 1, base, 2 * base, 4 * base};
-    for (int b = 0; b < 4; ++b) {
+    const int cands[6] = {base > 1 ? base / 2 : 1, base, 2 * base, 4 * base, 8 * base, 16 * base};
+    for (int b = 0; b < 6; ++b) {
+      if (b > 0 && cands[b - 1] >= nt) break;
       h.far_tt = tt;
       h.far_splits = cands[b] < nt ? cands[b] : nt;
       launch_far(g, d.host_out, d.host_out + h.N, st);   // warm-up

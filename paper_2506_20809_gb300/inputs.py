@@ -98,23 +98,26 @@ def _quat_to_matrix(q: np.ndarray) -> np.ndarray:
 
 def _ellipse_gap(r, z, A, C):
     """Signed distance from meridian-plane points (r >= 0, z >= 0) to the
-    ellipse r^2/A^2 + z^2/C^2 = 1; negative inside.  Bisection on the
-    Lagrange parameter t of the closest-point condition (exterior points)."""
+    ellipse r^2/A^2 + z^2/C^2 = 1; negative inside.  For exterior points the
+    closest point is x = (A^2 r/(t+A^2), C^2 z/(t+C^2)) with t >= 0 the root of
+    the convex decreasing F(t) = (A r/(t+A^2))^2 + (C z/(t+C^2))^2 - 1;
+    Newton's method from t = 0 approaches it monotonically from the left."""
     r = np.asarray(r, dtype=np.float64)
     z = np.asarray(z, dtype=np.float64)
     inside = (r / A) ** 2 + (z / C) ** 2 < 1.0
-    # exterior: closest point x = (A^2 r/(t+A^2), C^2 z/(t+C^2)), t >= 0 root of F
-    lo = np.zeros_like(r)
-    hi = np.maximum(A, C) * np.hypot(r, z) + 1e-300
-    for _ in range(64):
-        mid = 0.5 * (lo + hi)
-        F = (A * r / (mid + A * A)) ** 2 + (C * z / (mid + C * C)) ** 2 - 1.0
-        pos = F > 0
-        lo = np.where(pos, mid, lo)
-        hi = np.where(pos, hi, mid)
-    t = 0.5 * (lo + hi)
-    xr = A * A * r / (t + A * A)
-    xz = C * C * z / (t + C * C)
+    ar, cz = A * r, C * z
+    A2, C2 = A * A, C * C
+    t = np.zeros_like(r)
+    for _ in range(40):
+        ea, ec = ar / (t + A2), cz / (t + C2)
+        F = ea * ea + ec * ec - 1.0
+        dF = -2.0 * (ea * ea / (t + A2) + ec * ec / (t + C2))
+        step = np.where(inside | (dF == 0.0), 0.0, F / np.where(dF == 0.0, 1.0, dF))
+        t = t - step
+        if np.all(np.abs(step) <= 1e-15 * (np.abs(t) + 1e-300)):
+            break
+    xr = A2 * r / (t + A2)
+    xz = C2 * z / (t + C2)
     d = np.hypot(r - xr, z - xz)
     return np.where(inside, -1.0, d)
 
@@ -175,6 +178,19 @@ def _admissible(kind, A, C, center, R, new, placed, min_gap):
     if np.any(d - rmin[placed] - rmin[new] < min_gap):
         return False
     amb = placed[d - rmax[placed] - rmax[new] < min_gap]
+    if len(amb):
+        # separating-axis bound along the centre line: the gap is at least the
+        # centre distance minus both support functions in that direction
+        u = (center[new] - center[amb]) / np.linalg.norm(center[new] - center[amb], axis=1, keepdims=True)
+        ax_new = R[new][:, 2]
+        ax_amb = R[amb][:, :, 2]
+
+        def support(Aa, Cc, cos_t):
+            return np.sqrt(Aa * Aa + (Cc * Cc - Aa * Aa) * cos_t * cos_t)
+
+        lb = (np.linalg.norm(center[new] - center[amb], axis=1) - support(A[new], C[new], u @ ax_new)
+              - support(A[amb], C[amb], np.sum(u * ax_amb, axis=1)))
+        amb = amb[lb < min_gap]
     for j in amb:
         g1 = _gap_one_way(A[new], C[new], center[new], R[new], A[j], C[j], center[j], R[j])
         if g1 < min_gap:
@@ -273,19 +289,29 @@ def config_coefficients(s: Suspension, seed: int = 0, ndens: int = 2) -> np.ndar
     return np.ascontiguousarray(np.transpose(c, (1, 0, 2)))
 
 
+def _batch_member(args):
+    s, base_seed, p_choices, M_range, phi_range = args
+    rng = np.random.default_rng([base_seed + s, 104729])
+    M = int(round(math.exp(rng.uniform(math.log(M_range[0]), math.log(M_range[1])))))
+    p = int(rng.choice(p_choices))
+    phi = float(rng.uniform(*phi_range))
+    return rsa_suspension(M, phi, base_seed + s, p, name=f"batch{s}")
+
+
 def batch_suspensions(n: int = 64, base_seed: int = 0, p_choices=(8, 12, 16, 20),
-                      M_range=(10, 400), phi_range=(0.05, 0.25)):
+                      M_range=(10, 400), phi_range=(0.05, 0.25), workers: int = 1):
     """Independent suspensions for the batched workload: suspension s uses
     seed base_seed + s; M log-uniform in M_range, p uniform over p_choices,
-    volume fraction U[phi_range], shapes as the 200-particle workload."""
-    out = []
-    for s in range(n):
-        rng = np.random.default_rng([base_seed + s, 104729])
-        M = int(round(math.exp(rng.uniform(math.log(M_range[0]), math.log(M_range[1])))))
-        p = int(rng.choice(p_choices))
-        phi = float(rng.uniform(*phi_range))
-        out.append(rsa_suspension(M, phi, base_seed + s, p, name=f"batch{s}"))
-    return out
+    volume fraction U[phi_range], shapes as the 200-particle workload.
+    workers > 1 draws them in spawned processes (same result)."""
+    jobs = [(s, base_seed, tuple(p_choices), tuple(M_range), tuple(phi_range)) for s in range(n)]
+    if workers <= 1:
+        return [_batch_member(j) for j in jobs]
+    import concurrent.futures as cf
+    import multiprocessing as mp
+
+    with cf.ProcessPoolExecutor(max_workers=workers, mp_context=mp.get_context("spawn")) as ex:
+        return list(ex.map(_batch_member, jobs))
 
 
 def poisson_requests(rate: float, duration: float, seed: int = 0, M_range=(20, 500),

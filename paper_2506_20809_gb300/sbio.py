@@ -46,6 +46,16 @@ class sbio_options(C.Structure):
                 ("far_upsample", C.c_int32), ("precision", C.c_int32)]
 
 
+class sbio_request(C.Structure):
+    _fields_ = [("op", C.c_int32), ("n_applies", C.c_int32), ("sph", C.c_void_p), ("M", C.c_int32),
+                ("reserved", C.c_int32), ("opts", sbio_options), ("coef_host", C.c_void_p),
+                ("out_host", C.c_void_p)]
+
+
+SBIO_OP_LAPLACE = 0
+SBIO_OP_STOKES = 1
+
+
 class SbioError(RuntimeError):
     def __init__(self, code, msg):
         super().__init__(f"{ERRNAMES.get(code, code)}: {msg}")
@@ -84,6 +94,19 @@ _SIGS = {
     "sbio_apply_laplace_parts": (C.c_int, [_vp, _vp, _vp, _vp, _vp, C.c_uint32, _vp]),
     "sbio_apply_laplace_host": (C.c_int, [_vp, _vp, _vp, _vp, _vp, _vp]),
     "sbio_apply_stokes_sl": (C.c_int, [_vp, _vp, _vp, _vp]),
+    "sbio_batch_create": (C.c_int, [_vp, C.POINTER(_vp), C.c_int32, C.POINTER(_vp)]),
+    "sbio_batch_destroy": (C.c_int, [_vp]),
+    "sbio_batch_info": (C.c_int, [_vp, C.POINTER(C.c_int64), C.POINTER(C.c_int64), C.POINTER(C.c_int32),
+                                  C.POINTER(C.c_int32)]),
+    "sbio_batch_set_far_tt": (C.c_int, [_vp, C.c_int32]),
+    "sbio_batch_apply": (C.c_int, [_vp, C.POINTER(_vp), C.POINTER(_vp), C.POINTER(_vp), C.POINTER(_vp), _vp]),
+    "sbio_server_create": (C.c_int, [_vp, C.c_int32, C.c_size_t, C.POINTER(_vp)]),
+    "sbio_server_submit": (C.c_int, [_vp, C.POINTER(sbio_request), C.POINTER(C.c_int64)]),
+    "sbio_server_wait": (C.c_int, [_vp, C.c_int64, C.c_double, C.POINTER(C.c_int32), C.POINTER(C.c_double),
+                                   C.POINTER(C.c_double)]),
+    "sbio_server_stats": (C.c_int, [_vp, C.POINTER(C.c_int64), C.POINTER(C.c_int64), C.POINTER(C.c_int32),
+                                    C.POINTER(C.c_int32), C.POINTER(C.c_size_t)]),
+    "sbio_server_destroy": (C.c_int, [_vp]),
     "sbio_apply_self_noalloc": (C.c_int, [C.POINTER(sbio_spheroid), C.c_int32, C.c_int32, C.c_int32, _vp, _vp,
                                           _vp, _vp, _vp]),
 }
@@ -255,6 +278,74 @@ def sbio_apply_self_noalloc(spheroids, p, sigma_tilde, mu_hat, S_out, D_out, n_p
     include/sbio.h): for callers whose device memory is owned by someone else."""
     _check(_lib.sbio_apply_self_noalloc(spheroids, len(spheroids), p, n_phi, _ptr(sigma_tilde), _ptr(mu_hat),
                                         _ptr(S_out), _ptr(D_out), _stream(stream)))
+
+
+def _ptr_array(ts):
+    arr = (_vp * len(ts))()
+    for k, t in enumerate(ts):
+        arr[k] = _ptr(t)
+    return arr
+
+
+def sbio_batch_create(ctx, geoms):
+    hs = (_vp * len(geoms))(*[g.h if hasattr(g, "h") else g for g in geoms])
+    h = _vp()
+    _check(_lib.sbio_batch_create(ctx, hs, len(geoms), C.byref(h)))
+    return h
+
+
+def sbio_batch_destroy(b):
+    _check(_lib.sbio_batch_destroy(b))
+
+
+def sbio_batch_info(b):
+    a, c, d, e = C.c_int64(), C.c_int64(), C.c_int32(), C.c_int32()
+    _check(_lib.sbio_batch_info(b, C.byref(a), C.byref(c), C.byref(d), C.byref(e)))
+    return {"n_items": a.value, "far_pairs": c.value, "far_tt": d.value, "grid": e.value}
+
+
+def sbio_batch_set_far_tt(b, tt):
+    _check(_lib.sbio_batch_set_far_tt(b, tt))
+
+
+def sbio_batch_apply(b, sigmas, mus, S_outs, D_outs, stream=None):
+    _check(_lib.sbio_batch_apply(b, _ptr_array(sigmas), _ptr_array(mus), _ptr_array(S_outs), _ptr_array(D_outs),
+                                 _stream(stream)))
+
+
+def sbio_server_create(ctx, n_slots, mem_budget_bytes=0):
+    h = _vp()
+    _check(_lib.sbio_server_create(ctx, n_slots, mem_budget_bytes, C.byref(h)))
+    return h
+
+
+def sbio_server_submit(srv, op, spheroids, p, coef_host, out_host, n_applies, near_factor=1.0,
+                       precision=SBIO_MIXED, n_phi=0):
+    """coef_host / out_host: C-contiguous float64 numpy arrays kept alive by
+    the caller until sbio_server_wait returns for the ticket."""
+    req = sbio_request(op, n_applies, C.cast(spheroids, C.c_void_p), len(spheroids), 0,
+                       sbio_options(p, n_phi, near_factor, 1, precision), coef_host.ctypes.data,
+                       out_host.ctypes.data)
+    t = C.c_int64()
+    _check(_lib.sbio_server_submit(srv, C.byref(req), C.byref(t)))
+    return t.value
+
+
+def sbio_server_wait(srv, ticket, timeout_s=600.0):
+    """Returns (status, latency_ms, service_ms)."""
+    st, lat, svc = C.c_int32(), C.c_double(), C.c_double()
+    _check(_lib.sbio_server_wait(srv, ticket, timeout_s, C.byref(st), C.byref(lat), C.byref(svc)))
+    return st.value, lat.value, svc.value
+
+
+def sbio_server_stats(srv):
+    a, b, c, d, e = C.c_int64(), C.c_int64(), C.c_int32(), C.c_int32(), C.c_size_t()
+    _check(_lib.sbio_server_stats(srv, C.byref(a), C.byref(b), C.byref(c), C.byref(d), C.byref(e)))
+    return {"completed": a.value, "applies": b.value, "running": c.value, "queued": d.value, "reserved": e.value}
+
+
+def sbio_server_destroy(srv):
+    _check(_lib.sbio_server_destroy(srv))
 
 
 # ---- convenience object ------------------------------------------------------

@@ -1,0 +1,85 @@
+"""Batched apply (one graph, persistent far-field kernel over many suspensions)
+against the single-geometry FP64 path, within the mixed-precision bound."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from paper_2506_20809_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+TOLMIX = 1e-6
+
+
+@pytest.fixture(scope="module")
+def S():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    import __graft_entry__ as G
+
+    G.build()
+    import paper_2506_20809_gb300.sbio as S
+
+    return S
+
+
+def relerr(a, b):
+    return float(np.max(np.abs(a - b)) / np.max(np.abs(b)))
+
+
+def test_batch_matches_single_geometry(S):
+    ctx = S.sbio_ctx_create(0, 0)
+    specs = [(3, 4), (7, 6), (12, 8), (5, 12), (20, 5), (9, 16)]
+    susps = [I.rsa_suspension(M, 0.1, 300 + k, p, name=f"b{k}") for k, (M, p) in enumerate(specs)]
+    geoms = [S.Geometry(ctx, s, precision=S.SBIO_MIXED) for s in susps]
+    refs = []
+    for s, g in zip(susps, geoms):
+        c = I.config_coefficients(s, 5)
+        sig, mu = torch.from_numpy(c[0]).cuda(), torch.from_numpy(c[1]).cuda()
+        So = torch.empty(g.N, dtype=torch.float64, device="cuda")
+        Do = torch.empty_like(So)
+        S.sbio_geom_set_precision(g.h, S.SBIO_FP64)
+        S.sbio_apply_laplace(g.h, sig, mu, So, Do)
+        S.sbio_geom_set_precision(g.h, S.SBIO_MIXED)
+        refs.append((sig, mu, So.clone(), Do.clone()))
+    b = S.sbio_batch_create(ctx, geoms)
+    info = S.sbio_batch_info(b)
+    assert info["n_items"] > 0 and info["far_pairs"] == sum(g.n_far for g in geoms)
+    outS = [torch.full((g.N,), float("nan"), dtype=torch.float64, device="cuda") for g in geoms]
+    outD = [torch.full_like(o, float("nan")) for o in outS]
+    for rep in range(2):                      # capture, then replay
+        S.sbio_batch_apply(b, [r[0] for r in refs], [r[1] for r in refs], outS, outD)
+        torch.cuda.synchronize()
+        for k, r in enumerate(refs):
+            assert relerr(outS[k].cpu().numpy(), r[2].cpu().numpy()) < TOLMIX
+            assert relerr(outD[k].cpu().numpy(), r[3].cpu().numpy()) < TOLMIX
+    # new values in the same buffers: the replay must see them
+    for r in refs:
+        r[0].mul_(-2.0)
+    S.sbio_batch_apply(b, [r[0] for r in refs], [r[1] for r in refs], outS, outD)
+    torch.cuda.synchronize()
+    for k, r in enumerate(refs):
+        assert relerr(outS[k].cpu().numpy(), -2.0 * r[2].cpu().numpy()) < TOLMIX
+    # new output buffers: re-capture
+    outS2 = [torch.empty_like(o) for o in outS]
+    outD2 = [torch.empty_like(o) for o in outD]
+    S.sbio_batch_set_far_tt(b, 4)
+    S.sbio_batch_apply(b, [r[0] for r in refs], [r[1] for r in refs], outS2, outD2)
+    torch.cuda.synchronize()
+    for k, r in enumerate(refs):
+        assert relerr(outD2[k].cpu().numpy(), r[3].cpu().numpy()) < TOLMIX
+    S.sbio_batch_destroy(b)
+    for g in geoms:
+        g.close()
+    S.sbio_ctx_destroy(ctx)
+
+
+def test_batch_rejects_fp64_geometries(S):
+    ctx = S.sbio_ctx_create(0, 0)
+    s = I.rsa_suspension(3, 0.1, 7, 4)
+    g = S.Geometry(ctx, s, precision=S.SBIO_FP64)
+    with pytest.raises(S.SbioError) as e:
+        S.sbio_batch_create(ctx, [g])
+    assert e.value.code == S.SBIO_EINVAL
+    g.close()
+    S.sbio_ctx_destroy(ctx)

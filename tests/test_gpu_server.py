@@ -1,0 +1,118 @@
+"""Serving engine: continuous batching of Laplace and Stokes requests.
+
+Each request's results are the same alone and in a mix of concurrent
+requests, and equal to direct applies on a resident geometry; a tight memory
+budget still completes every request (admission waits for memory)."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from paper_2506_20809_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+NAPPLY = 3
+
+
+@pytest.fixture(scope="module")
+def S():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    import __graft_entry__ as G
+
+    G.build()
+    import paper_2506_20809_gb300.sbio as S
+
+    return S
+
+
+def make_requests():
+    reqs = []
+    for k, (M, p, op) in enumerate([(6, 6, "laplace"), (9, 8, "stokes"), (14, 8, "laplace"), (5, 12, "stokes"),
+                                    (11, 5, "laplace")]):
+        s = I.rsa_suspension(M, 0.12, 500 + k, p, name=f"r{k}")
+        nc = (p + 1) ** 2
+        rng = np.random.default_rng(k)
+        nd = 2 if op == "laplace" else 3
+        coef = np.stack([I.coefficients(rng, M, p, nd) for _ in range(NAPPLY)])     # (A, M, nd, nc)
+        if op == "laplace":
+            coef = np.ascontiguousarray(np.transpose(coef, (0, 2, 1, 3)))          # (A, 2, M, nc)
+        N = M * (p + 1) * 2 * (p + 1)
+        reqs.append({"s": s, "p": p, "op": op, "coef": coef, "N": N, "nc": nc})
+    return reqs
+
+
+def run(S, ctx, reqs, slots, budget=0):
+    srv = S.sbio_server_create(ctx, slots, budget)
+    outs, tickets, sphs = [], [], []
+    for r in reqs:
+        op = S.SBIO_OP_LAPLACE if r["op"] == "laplace" else S.SBIO_OP_STOKES
+        out = np.zeros((NAPPLY, 2 * r["N"]) if r["op"] == "laplace" else (NAPPLY, r["N"], 3))
+        sph = S.make_spheroids(r["s"].kind, r["s"].A, r["s"].C, r["s"].center, r["s"].quat)
+        sphs.append(sph)
+        outs.append(out)
+        tickets.append(S.sbio_server_submit(srv, op, sph, r["p"], r["coef"], out, NAPPLY))
+    lat = []
+    for t in tickets:
+        st, l, svc = S.sbio_server_wait(srv, t, 600.0)
+        assert st == 0
+        lat.append(l)
+    S.sbio_server_destroy(srv)
+    return outs, lat
+
+
+def test_alone_equals_in_the_mix_and_direct_apply(S):
+    ctx = S.sbio_ctx_create(0, 0)
+    reqs = make_requests()
+    alone = [run(S, ctx, [r], 1)[0][0] for r in reqs]
+    mixed, lat = run(S, ctx, reqs, 4)
+    for a, m in zip(alone, mixed):
+        assert np.max(np.abs(a - m)) <= 1e-12 * np.max(np.abs(a))
+    # direct applies on a resident geometry give the same numbers
+    for r, a in zip(reqs, alone):
+        g = S.Geometry(ctx, r["s"], precision=S.SBIO_MIXED)
+        for k in range(NAPPLY):
+            if r["op"] == "laplace":
+                sig = torch.from_numpy(r["coef"][k, 0].copy()).cuda()
+                mu = torch.from_numpy(r["coef"][k, 1].copy()).cuda()
+                So = torch.empty(g.N, dtype=torch.float64, device="cuda")
+                Do = torch.empty_like(So)
+                S.sbio_apply_laplace(g.h, sig, mu, So, Do)
+                ref = torch.cat([So, Do]).cpu().numpy()
+            else:
+                f = torch.from_numpy(r["coef"][k].copy()).cuda()
+                u = torch.empty((g.N, 3), dtype=torch.float64, device="cuda")
+                S.sbio_apply_stokes_sl(g.h, f, u)
+                ref = u.cpu().numpy()
+            torch.cuda.synchronize()
+            assert np.max(np.abs(a[k] - ref)) <= 1e-12 * np.max(np.abs(ref))
+        g.close()
+    S.sbio_ctx_destroy(ctx)
+
+
+def test_memory_budget_admission_completes_everything(S):
+    ctx = S.sbio_ctx_create(0, 0)
+    reqs = make_requests()
+    ref, _ = run(S, ctx, reqs, 1)
+    # budget smaller than the sum of the requests: admission must wait for memory
+    out, lat = run(S, ctx, reqs, 4, budget=12 << 20)
+    for a, b in zip(ref, out):
+        assert np.max(np.abs(a - b)) <= 1e-12 * np.max(np.abs(a))
+    S.sbio_ctx_destroy(ctx)
+
+
+def test_invalid_request_rejected(S):
+    ctx = S.sbio_ctx_create(0, 0)
+    srv = S.sbio_server_create(ctx, 1)
+    s = I.rsa_suspension(2, 0.1, 1, 4)
+    sph = S.make_spheroids(s.kind, s.A, s.C, s.center, s.quat)
+    coef = np.zeros((1, 2, 2, 25))
+    out = np.zeros((1, 2 * 2 * 50))
+    with pytest.raises(S.SbioError) as e:
+        S.sbio_server_submit(srv, 7, sph, 4, coef, out, 1)
+    assert e.value.code == S.SBIO_EINVAL
+    with pytest.raises(S.SbioError) as e:
+        S.sbio_server_wait(srv, 12345, 0.1)
+    assert e.value.code == S.SBIO_EINVAL
+    S.sbio_server_destroy(srv)
+    S.sbio_ctx_destroy(ctx)
