@@ -46,6 +46,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64-context", action="store_true")
     ap.add_argument("--oracle-sample", type=int, default=48, help="targets in the oracle's timed sample")
+    ap.add_argument("--far-shape", default="", help="TT,SPLITS: fixed far-field launch shape (skips the autotuner)")
     ap.add_argument("--workload", default="poly200", choices=["poly200", "stokes100", "batch64", "serve"])
     ap.add_argument("--rates", default="50,100,200,500,1000,2000", help="serve: arrival rates (req/s)")
     ap.add_argument("--requests", type=int, default=48, help="serve: requests per rate")
@@ -228,8 +229,12 @@ def run_ours(args, ws, rank, lrank):
     ctx = S.sbio_ctx_create(lrank, 0)
     prec = S.SBIO_MIXED if args.precision == "mixed" else S.SBIO_FP64
     geom = S.Geometry(ctx, susp, precision=prec)
-    tune = S.sbio_geom_autotune(geom.h)
-    S.sbio_geom_enable_timing(geom.h, True)
+    if args.far_shape:
+        tt, sp = (int(x) for x in args.far_shape.split(","))
+        S.sbio_geom_set_launch_shape(geom.h, tt, sp)
+        tune = (tt, sp, None)
+    else:
+        tune = S.sbio_geom_autotune(geom.h)
     N = geom.N
     sig = torch.from_numpy(coef[0]).to(dev)
     mu = torch.from_numpy(coef[1]).to(dev)
@@ -245,7 +250,6 @@ def run_ours(args, ws, rank, lrank):
     clocks = ClockSampler(lrank)
     clocks.start()
     time.sleep(0.3)
-    step_ms, far_ms, near_ms, synth_ms = [], [], [], []
     evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     barrier(ws)
     torch.cuda.synchronize()
@@ -253,12 +257,8 @@ def run_ours(args, ws, rank, lrank):
     for k in range(args.steps):
         flush.zero_()
         evs[k][0].record(stream)
-        S.sbio_apply_laplace(geom.h, sig, mu, So, Do)
+        S.sbio_apply_laplace(geom.h, sig, mu, So, Do)    # near (FP64) overlaps far (FP32)
         evs[k][1].record(stream)
-        a, b, c = S.sbio_geom_phase_times(geom.h)    # synchronises on this step's events
-        synth_ms.append(a)
-        near_ms.append(b)
-        far_ms.append(c)
     torch.cuda.synchronize()
     launches = S.sbio_launch_count() - l0
     barrier(ws)
@@ -266,6 +266,23 @@ def run_ours(args, ws, rank, lrank):
     step_ms = [e0.elapsed_time(e1) for e0, e1 in evs]
     total_s = allmax(ws, sum(step_ms) / 1e3)
     value = args.steps * ws / total_s
+
+    # per-kernel durations: a phase-timed pass (phases in order, events on the launch stream)
+    S.sbio_geom_enable_timing(geom.h, True)
+    far_ms, near_ms, synth_ms, inorder_ms = [], [], [], []
+    for _ in range(min(args.steps, 10)):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        S.sbio_apply_laplace(geom.h, sig, mu, So, Do)
+        e1.record(stream)
+        a, b, c = S.sbio_geom_phase_times(geom.h)
+        synth_ms.append(a)
+        near_ms.append(b)
+        far_ms.append(c)
+        torch.cuda.synchronize()
+        inorder_ms.append(e0.elapsed_time(e1))
+    S.sbio_geom_enable_timing(geom.h, False)
 
     # end to end through the host-memory entry point (pinned buffers)
     hs = torch.from_numpy(coef[0]).pin_memory().numpy()
@@ -288,6 +305,7 @@ def run_ours(args, ws, rank, lrank):
         S64 = torch.empty_like(So)
         D64 = torch.empty_like(Do)
         S.sbio_geom_set_precision(geom.h, S.SBIO_FP64)
+        S.sbio_geom_enable_timing(geom.h, True)
         S.sbio_apply_laplace(geom.h, sig, mu, S64, D64)
         torch.cuda.synchronize()
         t64 = []
@@ -299,6 +317,7 @@ def run_ours(args, ws, rank, lrank):
             torch.cuda.synchronize()
             t64.append(e0.elapsed_time(e1))
         f64_phase = S.sbio_geom_phase_times(geom.h)
+        S.sbio_geom_enable_timing(geom.h, False)
         S.sbio_geom_set_precision(geom.h, prec)
         S.sbio_apply_laplace(geom.h, sig, mu, So, Do)
         torch.cuda.synchronize()
@@ -320,7 +339,8 @@ def run_ours(args, ws, rank, lrank):
                                                         "autotuned_far_ms": tune[2]}),
         "gpairs_per_s": geom.n_far / (statistics.mean(step_ms) * 1e-3) / 1e9,
         "latency_ms": {"p50": lat[len(lat) // 2], "p99": lat[min(len(lat) - 1, int(0.99 * len(lat)))]},
-        "phase_ms": {"synth": statistics.mean(synth_ms), "near": statistics.mean(near_ms), "far": far_mean},
+        "phase_ms": {"synth": statistics.mean(synth_ms), "near": statistics.mean(near_ms), "far": far_mean,
+                     "in_order_apply": statistics.mean(inorder_ms)},
         "roofline": {"kernel": "far_mixed_kernel" if prec == S.SBIO_MIXED else "far_fp64_kernel",
                      "bound": "alu", "achieved": achieved,
                      "peak": FP32_PEAK_TFLOPS if prec == S.SBIO_MIXED else FP64_PEAK_TFLOPS,
@@ -434,7 +454,7 @@ def run_batch64(args, ws, rank, lrank):
     st = torch.cuda.current_stream()
     b = S.sbio_batch_create(ctx, geoms)
     best = None
-    for tt in (1, 2, 4):                               # autotune the persistent far kernel
+    for tt in (1, 2, 4, 8):                            # autotune the persistent far kernel
         S.sbio_batch_set_far_tt(b, tt)
         S.sbio_batch_apply(b, sig, mu, So, Do)
         t = min(_event_time(st, lambda: S.sbio_batch_apply(b, sig, mu, So, Do)) for _ in range(2))

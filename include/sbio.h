@@ -160,7 +160,7 @@ int sbio_geom_enable_timing(sbio_geom* g, int32_t on);
 int sbio_geom_phase_times(sbio_geom* g, double* ms_synth, double* ms_near, double* ms_far);
 
 /* Launch shape of the far-field kernels: far_tt targets per thread of the
- * mixed kernel (1, 2 or 4) and far_splits source splits of the grid (0 =
+ * mixed kernel (1, 2, 4 or 8) and far_splits source splits of the grid (0 =
  * chosen from the device's SM count).  Results do not depend on the shape
  * beyond floating-point summation order. */
 int sbio_geom_set_launch_shape(sbio_geom* g, int32_t far_tt, int32_t far_splits);
@@ -171,6 +171,13 @@ int sbio_geom_set_launch_shape(sbio_geom* g, int32_t far_tt, int32_t far_splits)
  * own workspaces), keeps the fastest and reports it (outputs may be NULL).
  * Synchronises `stream`; the workspaces hold no caller data afterwards. */
 int sbio_geom_autotune(sbio_geom* g, void* stream, int32_t* far_tt, int32_t* far_splits, double* far_ms);
+
+/* Near/far overlap (default on): the FP64 near-field kernels of an apply run
+ * on a high-priority stream forked from the caller's stream, beside the FP32
+ * far-field kernel, and are joined back before the call's work ends on the
+ * caller's stream.  Phase timing (sbio_geom_enable_timing) runs the phases in
+ * order instead.  Off: everything on the caller's stream. */
+int sbio_geom_set_overlap(sbio_geom* g, int32_t on);
 
 /* Change the precision mode used by later applies (SBIO_FP64 / SBIO_MIXED). */
 int sbio_geom_set_precision(sbio_geom* g, int32_t precision);
@@ -229,7 +236,7 @@ int sbio_batch_destroy(sbio_batch* b);
  * kernel and its persistent grid size (outputs may be NULL). */
 int sbio_batch_info(const sbio_batch* b, int64_t* n_items, int64_t* far_pairs, int32_t* far_tt, int32_t* grid);
 
-/* Targets per thread (1, 2, 4) of the persistent far kernel; rebuilds the
+/* Targets per thread (1, 2, 4, 8) of the persistent far kernel; rebuilds the
  * work list and drops the captured graph. */
 int sbio_batch_set_far_tt(sbio_batch* b, int32_t far_tt);
 

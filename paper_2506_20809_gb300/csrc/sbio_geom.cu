@@ -527,6 +527,14 @@ static int build_device(sbio_geom* g) {
 
 static void free_geom(sbio_geom* g) {
   if (!g) return;
+  if (g->near_stream) {
+    cudaStreamSynchronize(g->near_stream);
+    cudaStreamDestroy(g->near_stream);
+    g->near_stream = nullptr;
+  }
+  if (g->ev_fork) cudaEventDestroy(g->ev_fork);
+  if (g->ev_join) cudaEventDestroy(g->ev_join);
+  g->ev_fork = g->ev_join = nullptr;
   if (g->async_alloc) {
     for (void* p : g->allocs) cudaFreeAsync(p, g->setup_stream);
     g->allocs.clear();
@@ -561,6 +569,19 @@ static int geom_create_impl(sbio_ctx* ctx, const sbio_spheroid* sph, int32_t M, 
     free_geom(g);
     delete g;
     return rc;
+  }
+  if (!async_alloc) {
+    // near/far overlap resources (the serving engine's geometries run in order)
+    int lo = 0, hi = 0;
+    cudaDeviceGetStreamPriorityRange(&lo, &hi);
+    if (cudaStreamCreateWithPriority(&g->near_stream, cudaStreamNonBlocking, hi) != cudaSuccess ||
+        cudaEventCreateWithFlags(&g->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&g->ev_join, cudaEventDisableTiming) != cudaSuccess) {
+      cudaGetLastError();
+      g->overlap = false;
+    }
+  } else {
+    g->overlap = false;
   }
   ctx->n_geoms.fetch_add(1);
   *out = g;
@@ -678,6 +699,13 @@ int sbio_geom_phase_times(sbio_geom* g, double* ms_synth, double* ms_near, doubl
   if (ms_synth) *ms_synth = t[0];
   if (ms_near) *ms_near = t[1];
   if (ms_far) *ms_far = t[2];
+  return SBIO_OK;
+}
+
+int sbio_geom_set_overlap(sbio_geom* g, int32_t on) {
+  if (!g) return set_error(SBIO_EINVAL, "null geometry");
+  if (on && !g->near_stream) return set_error(SBIO_ENOTSUP, "this geometry has no overlap stream");
+  g->overlap = on != 0;
   return SBIO_OK;
 }
 

@@ -99,6 +99,11 @@ struct sbio_geom {
   // that creating / releasing one request's geometry does not synchronise the
   // device)
   bool async_alloc = false;
+  // near/far overlap: the FP64 near kernels run on a high-priority stream
+  // forked from the caller's stream, beside the FP32 far kernel
+  bool overlap = true;
+  cudaStream_t near_stream = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
 };
 
 namespace sbio {

@@ -214,7 +214,11 @@ __global__ void __launch_bounds__(kFarTile) far_fp64_kernel(const int4* __restri
 // their own centre, so the FP32 difference X - y_rel carries an error
 // relative to |x - y| rather than to the box size.  Each tile's FP32 partial
 // sum is folded into an (hi, lo) pair by TwoSum.
-// One CTA: targets of target block `tb` against source tiles [t_lo, t_hi).
+// One CTA: targets of target block `tb` (kFarTile * TT consecutive nodes, TT
+// per thread) against source tiles [t_lo, t_hi).  Only the target positions
+// relative to the current source particle and the running tile partials live
+// in registers; the two-sum accumulators and the skip-list cursors live in
+// shared memory and are touched once per tile.
 template <int TT, bool DO_S, bool DO_D>
 __device__ __forceinline__ void far_mixed_block(float4* sh, int64_t tb, int t_lo, int t_hi,
                                                 const int4* __restrict__ tiles, const float4* __restrict__ src32,
@@ -222,66 +226,61 @@ __device__ __forceinline__ void far_mixed_block(float4* sh, int64_t tb, int t_lo
                                                 const int32_t* __restrict__ skip_ptr,
                                                 const int32_t* __restrict__ skip_idx, int64_t N,
                                                 double* __restrict__ S_out, double* __restrict__ D_out) {
-  int64_t tg[TT];
-  bool valid[TT];
-  float xh[TT][3], xo[TT][3];
-  int sp[TT], nxt[TT];
+  __shared__ float acc[4 * TT * kFarTile];   // per target: S hi, S lo, D hi, D lo
+  __shared__ int cursor[2 * TT * kFarTile];  // per target: skip-list position, next skipped particle
+  const int tid = threadIdx.x;
+  const int64_t t0 = tb * TT * kFarTile + tid;
 #pragma unroll
   for (int q = 0; q < TT; ++q) {
-    tg[q] = (tb * TT + q) * kFarTile + threadIdx.x;
-    valid[q] = tg[q] < N;
-    xh[q][0] = xh[q][1] = xh[q][2] = 0.f;
-    xo[q][0] = xo[q][1] = xo[q][2] = 0.f;
-    sp[q] = 0;
-    nxt[q] = INT32_MAX;
-    if (valid[q]) {
-      const float4 hi = tgt32[tg[q] * 2], lo = tgt32[tg[q] * 2 + 1];
-      xh[q][0] = hi.x; xh[q][1] = hi.y; xh[q][2] = hi.z;
-      xo[q][0] = lo.x; xo[q][1] = lo.y; xo[q][2] = lo.z;
-      sp[q] = skip_ptr[tg[q]];
-      nxt[q] = skip_idx[sp[q]];
-    }
+    const int64_t t = t0 + (int64_t)q * kFarTile;
+    acc[(4 * q + 0) * kFarTile + tid] = 0.f;
+    acc[(4 * q + 1) * kFarTile + tid] = 0.f;
+    acc[(4 * q + 2) * kFarTile + tid] = 0.f;
+    acc[(4 * q + 3) * kFarTile + tid] = 0.f;
+    const int sp = (t < N) ? skip_ptr[t] : 0;
+    cursor[(2 * q + 0) * kFarTile + tid] = sp;
+    cursor[(2 * q + 1) * kFarTile + tid] = (t < N) ? skip_idx[sp] : INT32_MAX;
   }
-  float sS[TT], eS[TT], sD[TT], eD[TT];
   float X[TT], Y[TT], Z[TT];
-  bool skip[TT];
-#pragma unroll
-  for (int q = 0; q < TT; ++q) {
-    sS[q] = eS[q] = sD[q] = eD[q] = 0.f;
-    X[q] = Y[q] = Z[q] = 0.f;
-    skip[q] = true;
-  }
+  unsigned skipmask = (1u << TT) - 1u;
   int cur = -1;
   for (int tl = t_lo; tl < t_hi; ++tl) {
     const int4 tile = tiles[tl];
     if (tile.x != cur) {
       cur = tile.x;
       const float4 ch = cen32[cur * 2], cl = cen32[cur * 2 + 1];
+      skipmask = 0u;
 #pragma unroll
       for (int q = 0; q < TT; ++q) {
-        if (valid[q]) {
-          while (nxt[q] < cur) nxt[q] = skip_idx[++sp[q]];
-          skip[q] = (nxt[q] == cur);
+        const int64_t t = t0 + (int64_t)q * kFarTile;
+        int sp = cursor[(2 * q + 0) * kFarTile + tid];
+        int nxt = cursor[(2 * q + 1) * kFarTile + tid];
+        while (nxt < cur) nxt = skip_idx[++sp];
+        cursor[(2 * q + 0) * kFarTile + tid] = sp;
+        cursor[(2 * q + 1) * kFarTile + tid] = nxt;
+        if (t >= N || nxt == cur) skipmask |= 1u << q;
+        float4 hi = make_float4(0.f, 0.f, 0.f, 0.f), lo = hi;
+        if (t < N) {
+          hi = tgt32[t * 2];
+          lo = tgt32[t * 2 + 1];
         }
-        X[q] = (xh[q][0] - ch.x) + (xo[q][0] - cl.x);
-        Y[q] = (xh[q][1] - ch.y) + (xo[q][1] - cl.y);
-        Z[q] = (xh[q][2] - ch.z) + (xo[q][2] - cl.z);
+        X[q] = (hi.x - ch.x) + (lo.x - cl.x);
+        Y[q] = (hi.y - ch.y) + (lo.y - cl.y);
+        Z[q] = (hi.z - ch.z) + (lo.z - cl.z);
       }
     }
-    bool all_skip = true;
-#pragma unroll
-    for (int q = 0; q < TT; ++q) all_skip = all_skip && skip[q];
-    if (__syncthreads_and(all_skip)) continue;
-    if (threadIdx.x < tile.z) {
-      sh[threadIdx.x * 2 + 0] = src32[(int64_t)(tile.y + threadIdx.x) * 2 + 0];
-      sh[threadIdx.x * 2 + 1] = src32[(int64_t)(tile.y + threadIdx.x) * 2 + 1];
+    const bool mine = skipmask != (1u << TT) - 1u;
+    if (!__syncthreads_or(mine)) continue;
+    if (tid < tile.z) {
+      sh[tid * 2 + 0] = src32[(int64_t)(tile.y + tid) * 2 + 0];
+      sh[tid * 2 + 1] = src32[(int64_t)(tile.y + tid) * 2 + 1];
     }
     __syncthreads();
-    if (!all_skip) {
+    if (mine) {
       float pS[TT], pD[TT];
 #pragma unroll
       for (int q = 0; q < TT; ++q) pS[q] = pD[q] = 0.f;
-#pragma unroll 4
+#pragma unroll 2
       for (int j = 0; j < tile.z; ++j) {
         const float4 a = sh[j * 2], b = sh[j * 2 + 1];
 #pragma unroll
@@ -298,17 +297,17 @@ __device__ __forceinline__ void far_mixed_block(float4* sh, int64_t tb, int t_lo
       }
 #pragma unroll
       for (int q = 0; q < TT; ++q) {
-        if (!skip[q]) {
-          float s, e;
+        if (!((skipmask >> q) & 1u)) {
+          float sum, err;
           if (DO_S) {
-            two_sum(sS[q], pS[q], s, e);
-            sS[q] = s;
-            eS[q] += e;
+            two_sum(acc[(4 * q + 0) * kFarTile + tid], pS[q], sum, err);
+            acc[(4 * q + 0) * kFarTile + tid] = sum;
+            acc[(4 * q + 1) * kFarTile + tid] += err;
           }
           if (DO_D) {
-            two_sum(sD[q], pD[q], s, e);
-            sD[q] = s;
-            eD[q] += e;
+            two_sum(acc[(4 * q + 2) * kFarTile + tid], pD[q], sum, err);
+            acc[(4 * q + 2) * kFarTile + tid] = sum;
+            acc[(4 * q + 3) * kFarTile + tid] += err;
           }
         }
       }
@@ -317,11 +316,15 @@ __device__ __forceinline__ void far_mixed_block(float4* sh, int64_t tb, int t_lo
   }
 #pragma unroll
   for (int q = 0; q < TT; ++q) {
-    if (valid[q]) {
-      if (DO_S) atomicAdd(S_out + tg[q], ((double)sS[q] + (double)eS[q]) * kInv4Pi);
-      if (DO_D) atomicAdd(D_out + tg[q], ((double)sD[q] + (double)eD[q]) * kInv4Pi);
+    const int64_t t = t0 + (int64_t)q * kFarTile;
+    if (t < N) {
+      if (DO_S)
+        atomicAdd(S_out + t, ((double)acc[(4 * q + 0) * kFarTile + tid] + (double)acc[(4 * q + 1) * kFarTile + tid]) * kInv4Pi);
+      if (DO_D)
+        atomicAdd(D_out + t, ((double)acc[(4 * q + 2) * kFarTile + tid] + (double)acc[(4 * q + 3) * kFarTile + tid]) * kInv4Pi);
     }
   }
+  __syncthreads();   // the shared arrays are reused by the next block of a persistent CTA
 }
 
 template <int TT, bool DO_S, bool DO_D>
@@ -394,6 +397,7 @@ static void launch_far(sbio_geom* g, double* S, double* D, cudaStream_t st) {
     switch (h.far_tt) {
       case 1: launch_far_mixed_tt<1>(d, h, nt, h.far_splits, S, D, st); break;
       case 4: launch_far_mixed_tt<4>(d, h, nt, h.far_splits, S, D, st); break;
+      case 8: launch_far_mixed_tt<8>(d, h, nt, h.far_splits, S, D, st); break;
       default: launch_far_mixed_tt<2>(d, h, nt, h.far_splits, S, D, st); break;
     }
   }
@@ -427,6 +431,7 @@ int launch_far_persistent(const FarDesc* descs, const int4* items, int n_items, 
   switch (tt) {
     case 1: far_persistent_kernel<1><<<grid, kFarTile, 0, st>>>(descs, items, n_items, counter); break;
     case 4: far_persistent_kernel<4><<<grid, kFarTile, 0, st>>>(descs, items, n_items, counter); break;
+    case 8: far_persistent_kernel<8><<<grid, kFarTile, 0, st>>>(descs, items, n_items, counter); break;
     default: far_persistent_kernel<2><<<grid, kFarTile, 0, st>>>(descs, items, n_items, counter); break;
   }
   count_launch();
@@ -467,7 +472,16 @@ int launch_laplace(sbio_geom* g, const double* sigma, const double* mu, double* 
   int rc = launch_synth(g, sigma, mu, S, D, (parts & SBIO_PART_SELF) != 0, st);
   if (rc) return rc;
   phase_mark(g, 1, st);
-  if (parts & SBIO_PART_NEAR) {
+  // with phase timing on, run the phases in order so that each is timed alone
+  const bool fork = g->overlap && !g->timing && g->near_stream && (parts & SBIO_PART_NEAR) &&
+                    (parts & SBIO_PART_FAR) && !g->h.pair_t.empty();
+  if (fork) {
+    SBIO_CUDA_TRY(cudaEventRecord(g->ev_fork, st));
+    SBIO_CUDA_TRY(cudaStreamWaitEvent(g->near_stream, g->ev_fork, 0));
+    rc = launch_near(g, S, D, g->near_stream);
+    if (rc) return rc;
+    SBIO_CUDA_TRY(cudaEventRecord(g->ev_join, g->near_stream));
+  } else if (parts & SBIO_PART_NEAR) {
     rc = launch_near(g, S, D, st);
     if (rc) return rc;
   }
@@ -476,6 +490,7 @@ int launch_laplace(sbio_geom* g, const double* sigma, const double* mu, double* 
     launch_far(g, S, D, st);
     SBIO_CUDA_TRY(cudaGetLastError());
   }
+  if (fork) SBIO_CUDA_TRY(cudaStreamWaitEvent(st, g->ev_join, 0));
   phase_mark(g, 3, st);
   return SBIO_OK;
 }
@@ -531,7 +546,8 @@ int sbio_apply_laplace_host(sbio_geom* g, const double* sigma_host, const double
 int sbio_geom_set_launch_shape(sbio_geom* g, int32_t far_tt, int32_t far_splits) {
   clear_error();
   if (!g) return set_error(SBIO_EINVAL, "null geometry");
-  if (far_tt != 1 && far_tt != 2 && far_tt != 4) return set_error(SBIO_EINVAL, "far_tt must be 1, 2 or 4");
+  if (far_tt != 1 && far_tt != 2 && far_tt != 4 && far_tt != 8)
+    return set_error(SBIO_EINVAL, "far_tt must be 1, 2, 4 or 8");
   if (far_splits < 0) return set_error(SBIO_EINVAL, "far_splits must be >= 0");
   g->h.far_tt = far_tt;
   g->h.far_splits = far_splits;
@@ -557,8 +573,8 @@ int sbio_geom_autotune(sbio_geom* g, void* stream, int32_t* far_tt, int32_t* far
   const int saved_tt = h.far_tt, saved_sp = h.far_splits;
   double best = 1e300;
   int best_tt = saved_tt, best_sp = saved_sp;
-  const int tts[3] = {1, 2, 4};
-  for (int a = 0; a < (h.precision == SBIO_FP64 ? 1 : 3); ++a) {
+  const int tts[4] = {1, 2, 4, 8};
+  for (int a = 0; a < (h.precision == SBIO_FP64 ? 1 : 4); ++a) {
     const int tt = (h.precision == SBIO_FP64) ? 1 : tts[a];
     const int64_t tb = (h.N + (int64_t)kFarTile * tt - 1) / ((int64_t)kFarTile * tt);
     const int base = far_split_count(tb, nt, 0);

@@ -329,8 +329,19 @@ int launch_stokes(sbio_geom* g, const double* f, double* u, cudaStream_t st) {
   count_launch();
   SBIO_CUDA_TRY(cudaGetLastError());
   phase_mark(g, 1, st);
-  nl(d, h.st_pairs_prolate, (int64_t)h.st_pair_t.size(), d.inv, u, st);
-  SBIO_CUDA_TRY(cudaGetLastError());
+  // the FP64 near/self kernels run beside the FP32 Stokeslet kernel unless
+  // phases are being timed one by one
+  const bool fork = g->overlap && !g->timing && g->near_stream;
+  if (fork) {
+    SBIO_CUDA_TRY(cudaEventRecord(g->ev_fork, st));
+    SBIO_CUDA_TRY(cudaStreamWaitEvent(g->near_stream, g->ev_fork, 0));
+    nl(d, h.st_pairs_prolate, (int64_t)h.st_pair_t.size(), d.inv, u, g->near_stream);
+    SBIO_CUDA_TRY(cudaGetLastError());
+    SBIO_CUDA_TRY(cudaEventRecord(g->ev_join, g->near_stream));
+  } else {
+    nl(d, h.st_pairs_prolate, (int64_t)h.st_pair_t.size(), d.inv, u, st);
+    SBIO_CUDA_TRY(cudaGetLastError());
+  }
   phase_mark(g, 2, st);
   const int nt = (int)h.tiles.size();
   if (h.precision == SBIO_FP64) {
@@ -347,6 +358,7 @@ int launch_stokes(sbio_geom* g, const double* f, double* u, cudaStream_t st) {
   }
   count_launch();
   SBIO_CUDA_TRY(cudaGetLastError());
+  if (fork) SBIO_CUDA_TRY(cudaStreamWaitEvent(st, g->ev_join, 0));
   phase_mark(g, 3, st);
   return SBIO_OK;
 }

@@ -86,6 +86,7 @@ _SIGS = {
     "sbio_geom_set_precision": (C.c_int, [_vp, C.c_int32]),
     "sbio_geom_enable_timing": (C.c_int, [_vp, C.c_int32]),
     "sbio_geom_set_launch_shape": (C.c_int, [_vp, C.c_int32, C.c_int32]),
+    "sbio_geom_set_overlap": (C.c_int, [_vp, C.c_int32]),
     "sbio_geom_autotune": (C.c_int, [_vp, _vp, C.POINTER(C.c_int32), C.POINTER(C.c_int32),
                                      C.POINTER(C.c_double)]),
     "sbio_geom_phase_times": (C.c_int, [_vp, C.POINTER(C.c_double), C.POINTER(C.c_double),
@@ -227,6 +228,10 @@ def sbio_geom_near_pairs(g):
 
 def sbio_geom_set_precision(g, precision):
     _check(_lib.sbio_geom_set_precision(g, precision))
+
+
+def sbio_geom_set_overlap(g, on=True):
+    _check(_lib.sbio_geom_set_overlap(g, 1 if on else 0))
 
 
 def sbio_geom_set_launch_shape(g, far_tt, far_splits):

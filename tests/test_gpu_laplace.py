@@ -95,7 +95,7 @@ def test_lattice_mixed(S, lattice):
     assert OL.normwise_rel_err(Dm, D64) < TOLMIX
 
 
-@pytest.mark.parametrize("tt,splits", [(1, 1), (2, 3), (4, 0), (1, 7)])
+@pytest.mark.parametrize("tt,splits", [(1, 1), (2, 3), (4, 0), (1, 7), (8, 0), (8, 5)])
 def test_launch_shapes_agree(S, lattice, tt, splits):
     """Far-field launch shapes (targets per thread, source splits) change only
     the summation order."""
@@ -108,6 +108,19 @@ def test_launch_shapes_agree(S, lattice, tt, splits):
     S.sbio_geom_set_precision(g.h, S.SBIO_FP64)
     assert OL.normwise_rel_err(S64b, S64) < 1e-13 and OL.normwise_rel_err(D64b, D64) < 1e-13
     assert OL.normwise_rel_err(Sm, S64) < TOLMIX and OL.normwise_rel_err(Dm, D64) < TOLMIX
+
+
+def test_overlap_matches_in_order(S, poly200):
+    """Near kernels on the forked high-priority stream give the in-order result."""
+    s, c, g, og = poly200
+    S.sbio_geom_set_precision(g.h, S.SBIO_MIXED)
+    S.sbio_geom_set_overlap(g.h, True)
+    So, Do = gpu_apply(S, g, c[0], c[1], 7)
+    S.sbio_geom_set_overlap(g.h, False)
+    Si, Di = gpu_apply(S, g, c[0], c[1], 7)
+    S.sbio_geom_set_overlap(g.h, True)
+    S.sbio_geom_set_precision(g.h, S.SBIO_FP64)
+    assert OL.normwise_rel_err(So, Si) < 1e-12 and OL.normwise_rel_err(Do, Di) < 1e-12
 
 
 def test_autotune_keeps_results(S, lattice):
