@@ -165,11 +165,20 @@ int sbio_geom_phase_times(sbio_geom* g, double* ms_synth, double* ms_near, doubl
  * beyond floating-point summation order. */
 int sbio_geom_set_launch_shape(sbio_geom* g, int32_t far_tt, int32_t far_splits);
 
+/* Near-field CTAs per SM while the near field overlaps the far field (grid-
+ * stride near kernels; 0 = one CTA per 128 pairs, no cap).  Default 2. */
+int sbio_geom_set_near_cap(sbio_geom* g, int32_t ctas_per_sm);
+
+/* Current launch shape (outputs may be NULL). */
+int sbio_geom_get_tuning(const sbio_geom* g, int32_t* far_tt, int32_t* far_splits, int32_t* near_ctas_per_sm);
+
 /* Autotuner: times the far-field kernel of this geometry in its current
  * precision mode for a small set of launch shapes (CUDA events on `stream`,
  * zero-strength sources written by one self-only pass into the geometry's
- * own workspaces), keeps the fastest and reports it (outputs may be NULL).
- * Synchronises `stream`; the workspaces hold no caller data afterwards. */
+ * own workspaces) and keeps the fastest; then, when the near field overlaps
+ * the far field, times whole applies for a few near CTA caps and keeps the
+ * fastest.  Reports the far shape (outputs may be NULL).  Synchronises
+ * `stream`; the workspaces hold no caller data afterwards. */
 int sbio_geom_autotune(sbio_geom* g, void* stream, int32_t* far_tt, int32_t* far_splits, double* far_ms);
 
 /* Near/far overlap (default on): the FP64 near-field kernels of an apply run

@@ -323,24 +323,6 @@ static int build_near(GeomHost& h) {
   }
   h.far_pairs = 0;
   for (int64_t t = 0; t < N; ++t) h.far_pairs += (int64_t)(M - 1 - cnt[t]) * h.G;
-  // Stokes: the self interaction is evaluated as (node, own particle) pairs at
-  // the own surface, in the same (kind, source, target) order
-  std::vector<std::pair<int32_t, int32_t>> st(pairs);
-  for (int64_t t = 0; t < N; ++t) st.push_back({(int32_t)t, (int32_t)(t / h.G)});
-  std::sort(st.begin(), st.end(), [&](const std::pair<int32_t, int32_t>& a, const std::pair<int32_t, int32_t>& b) {
-    const int ka = h.parts[a.second].kind, kb = h.parts[b.second].kind;
-    if (ka != kb) return ka < kb;
-    if (a.second != b.second) return a.second < b.second;
-    return a.first < b.first;
-  });
-  h.st_pair_t.resize(st.size());
-  h.st_pair_s.resize(st.size());
-  h.st_pairs_prolate = 0;
-  for (size_t k = 0; k < st.size(); ++k) {
-    h.st_pair_t[k] = st[k].first;
-    h.st_pair_s[k] = st[k].second;
-    if (h.parts[st[k].second].kind == SBIO_PROLATE) h.st_pairs_prolate++;
-  }
   // far-field source tiles
   h.tiles.clear();
   for (int i = 0; i < M; ++i)
@@ -508,8 +490,48 @@ static int build_device(sbio_geom* g) {
     if ((rc = upload(g, &d.st_qw, qw.data(), qw.size(), "Stokes grid"))) return rc;
     if ((rc = upload(g, &d.st_qptab, qpt.data(), qpt.size(), "Stokes grid"))) return rc;
     if ((rc = upload(g, &d.st_qtrig, qtr.data(), qtr.size(), "Stokes grid"))) return rc;
-    if ((rc = upload(g, &d.st_pair_t, h.st_pair_t.data(), h.st_pair_t.size(), "Stokes pairs"))) return rc;
-    if ((rc = upload(g, &d.st_pair_s, h.st_pair_s.data(), h.st_pair_s.size(), "Stokes pairs"))) return rc;
+    // self term at u = u0: radial values and derivatives per particle, Ferrers
+    // tables at the GL nodes (unnormalised), trig up to order p+1
+    std::vector<double> qu((size_t)M * nm1), dqu((size_t)M * nm1), Qr1(nm_count(p1 + 1));
+    for (int i = 0; i < M; ++i) {
+      const PartGeom& P = h.parts[i];
+      radial_Q(P.u0, P.sgn, p1 + 1, Qr1.data());
+      const double den = P.u0 * P.u0 + P.sgn;
+      for (int n = 0; n <= p1; ++n)
+        for (int m = 0; m <= n; ++m) {
+          qu[(size_t)i * nm1 + nm_index(n, m)] = Qr1[nm_index(n, m)];
+          dqu[(size_t)i * nm1 + nm_index(n, m)] =
+              (-P.sgn * (n - m + 1.0) * Qr1[nm_index(n + 1, m)] - (n + 1.0) * P.u0 * Qr1[nm_index(n, m)]) / den;
+        }
+    }
+    std::vector<double> fP((size_t)h.n_v * nm1), fV((size_t)h.n_v * nm1), fF((size_t)h.n_v * nm1);
+    std::vector<double> fr(nm_count(p1 + 2));
+    for (int j = 0; j < h.n_v; ++j) {
+      const double v = gv[j], sv = std::sqrt((1.0 - v) * (1.0 + v));
+      ferrers(v, p1 + 1, fr.data());
+      for (int n = 0; n <= p1; ++n)
+        for (int m = 0; m <= n; ++m) {
+          const double Pn = fr[nm_index(n, m)], Pn1 = fr[nm_index(n + 1, m)];
+          fP[(size_t)j * nm1 + nm_index(n, m)] = Pn;
+          // sqrt(1-v^2) dP/dv from eq. (derivative) on the cut; GL nodes have sv > 0
+          fV[(size_t)j * nm1 + nm_index(n, m)] = ((n + 1.0) * v * Pn - (n - m + 1.0) * Pn1) / sv;
+          fF[(size_t)j * nm1 + nm_index(n, m)] = m * Pn / sv;
+        }
+    }
+    std::vector<double> tr1((size_t)h.n_phi * (p1 + 1) * 2);
+    for (int k = 0; k < h.n_phi; ++k)
+      for (int m = 0; m <= p1; ++m) {
+        const double ph = 2.0 * kPi * k / h.n_phi;
+        tr1[((size_t)k * (p1 + 1) + m) * 2 + 0] = std::cos(m * ph);
+        tr1[((size_t)k * (p1 + 1) + m) * 2 + 1] = std::sin(m * ph);
+      }
+    if ((rc = upload(g, &d.st_qu0, qu.data(), qu.size(), "Stokes self radial"))) return rc;
+    if ((rc = upload(g, &d.st_dqu0, dqu.data(), dqu.size(), "Stokes self radial"))) return rc;
+    if ((rc = upload(g, &d.st_fP, fP.data(), fP.size(), "Stokes self Ferrers"))) return rc;
+    if ((rc = upload(g, &d.st_fV, fV.data(), fV.size(), "Stokes self Ferrers"))) return rc;
+    if ((rc = upload(g, &d.st_fF, fF.data(), fF.size(), "Stokes self Ferrers"))) return rc;
+    if ((rc = upload(g, &d.st_trig1, tr1.data(), tr1.size(), "Stokes self trig"))) return rc;
+    if ((rc = upload(g, &d.st_glv, gv.data(), gv.size(), "GL nodes"))) return rc;
     if ((rc = dev_alloc(g, (void**)&d.st_coef, (size_t)M * 4 * nc1 * sizeof(double), "Stokes coefficients"))) return rc;
     if ((rc = dev_alloc(g, (void**)&d.st_src64, (size_t)N * 8 * sizeof(double), "Stokes fp64 sources"))) return rc;
     if ((rc = dev_alloc(g, (void**)&d.st_src32, (size_t)N * 2 * sizeof(float4), "Stokes fp32 sources"))) return rc;

@@ -38,6 +38,7 @@ struct DevGeom {
   int32_t* skip_idx = nullptr;
   int4* tiles = nullptr;         // far source tiles (particle, first node, count, -)
   double* inv = nullptr;         // 1/k, k < kInvTable (k = 0 holds 0)
+  int near_grid_cap = 0;         // > 0: at most this many near CTAs (grid-stride), set while overlapping
   float4* tgt32 = nullptr;       // N x 2: hi, lo parts of the global node position
   float4* cen32 = nullptr;       // M x 2: hi, lo parts of the centres
   // workspaces written by every apply
@@ -54,8 +55,13 @@ struct DevGeom {
   double* st_qw = nullptr;       // n_q GL weights
   double* st_qptab = nullptr;    // n_q x nm_count(p+1): N_n^m Pbar_n^m(v_q)
   double* st_qtrig = nullptr;    // n_f x (p+2) x 2: cos / sin (m phi_l)
-  int32_t* st_pair_t = nullptr;  // near pairs + self pairs: target node
-  int32_t* st_pair_s = nullptr;  //                          source particle
+  double* st_qu0 = nullptr;      // M x nm_count(p+1): q_n^m(u0) (self term)
+  double* st_dqu0 = nullptr;     // M x nm_count(p+1): dq_n^m/du (u0)
+  double* st_fP = nullptr;       // (p+1) x nm_count(p+1): Pbar_n^m(v_j), unnormalised
+  double* st_fV = nullptr;       //   sqrt(1-v_j^2) dPbar/dv
+  double* st_fF = nullptr;       //   m Pbar / sqrt(1-v_j^2)
+  double* st_trig1 = nullptr;    // n_phi x (p+2) x 2: cos / sin (m phi_k), m <= p+1
+  double* st_glv = nullptr;      // p+1 GL nodes v_j of the surface grid
   double* st_coef = nullptr;     // M x 4 x (p+2)^2 folded coefficients (f1, f2, f3, y.f)
   double* st_src64 = nullptr;    // N x 8: y - c_own (3), w f (3), 0, 0
   float4* st_src32 = nullptr;    // N x 2: (y - c_own, w f_1), (w f_2, w f_3, 0, 0)
@@ -72,14 +78,13 @@ struct GeomHost {
   int64_t n_pairs_prolate = 0;           // pairs [0, n_pairs_prolate) have prolate sources
   int64_t far_pairs = 0;
   std::vector<int4> tiles;
-  std::vector<int32_t> st_pair_t, st_pair_s; // Stokes: near + self pairs, sorted like pair_t/pair_s
-  int64_t st_pairs_prolate = 0;
   int n_q = 0, n_f = 0;                      // y.f transform grid
   // launch shape of the far field (tunable): targets per thread of the mixed
   // kernel and number of source splits (0 = chosen from the device size)
   int far_tt = 2;
   int far_splits = 0;
   int near_block = 128;                      // threads per CTA of the near kernels
+  int near_ctas_per_sm = 2;                  // near CTAs per SM while overlapping with the far field (0 = no cap)
 };
 
 }  // namespace sbio
@@ -174,6 +179,7 @@ int launch_stokes(sbio_geom* g, const double* f, double* u, cudaStream_t st);
 // source splits of the far-field grid (gridDim.y) for `target_blocks` target
 // CTAs; `requested` > 0 forces the count
 int far_split_count(int64_t target_blocks, int n_tiles, int requested);
+int sm_count();   // multiprocessors of the current device (cached)
 
 }  // namespace sbio
 

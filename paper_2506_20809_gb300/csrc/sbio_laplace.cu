@@ -344,16 +344,21 @@ __global__ void __launch_bounds__(kFarTile) far_mixed_kernel(const int4* __restr
 
 // Number of source splits so that the grid holds about `waves` resident
 // rounds of CTAs on the device (never more splits than tiles).
-int far_split_count(int64_t target_blocks, int n_tiles, int requested) {
-  if (requested > 0) return requested < n_tiles ? requested : n_tiles;
-  static int sm_count[64] = {0};
+int sm_count() {
+  static int cache[64] = {0};
   int dev = 0;
   cudaGetDevice(&dev);
-  int sms = (dev >= 0 && dev < 64) ? sm_count[dev] : 0;
+  int sms = (dev >= 0 && dev < 64) ? cache[dev] : 0;
   if (sms == 0) {
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (dev >= 0 && dev < 64) sm_count[dev] = sms;
+    if (dev >= 0 && dev < 64) cache[dev] = sms;
   }
+  return sms;
+}
+
+int far_split_count(int64_t target_blocks, int n_tiles, int requested) {
+  if (requested > 0) return requested < n_tiles ? requested : n_tiles;
+  const int sms = sm_count();
   const int64_t want = (int64_t)sms * 8 * 2;
   int64_t s = (want + target_blocks - 1) / target_blocks;
   if (s < 1) s = 1;
@@ -478,7 +483,10 @@ int launch_laplace(sbio_geom* g, const double* sigma, const double* mu, double* 
   if (fork) {
     SBIO_CUDA_TRY(cudaEventRecord(g->ev_fork, st));
     SBIO_CUDA_TRY(cudaStreamWaitEvent(g->near_stream, g->ev_fork, 0));
+    // a few near CTAs per SM leave room for the far kernel's CTAs
+    g->d.near_grid_cap = g->h.near_ctas_per_sm > 0 ? g->h.near_ctas_per_sm * sm_count() : 0;
     rc = launch_near(g, S, D, g->near_stream);
+    g->d.near_grid_cap = 0;
     if (rc) return rc;
     SBIO_CUDA_TRY(cudaEventRecord(g->ev_join, g->near_stream));
   } else if (parts & SBIO_PART_NEAR) {
@@ -554,6 +562,22 @@ int sbio_geom_set_launch_shape(sbio_geom* g, int32_t far_tt, int32_t far_splits)
   return SBIO_OK;
 }
 
+int sbio_geom_set_near_cap(sbio_geom* g, int32_t ctas_per_sm) {
+  clear_error();
+  if (!g) return set_error(SBIO_EINVAL, "null geometry");
+  if (ctas_per_sm < 0) return set_error(SBIO_EINVAL, "ctas_per_sm must be >= 0");
+  g->h.near_ctas_per_sm = ctas_per_sm;
+  return SBIO_OK;
+}
+
+int sbio_geom_get_tuning(const sbio_geom* g, int32_t* far_tt, int32_t* far_splits, int32_t* near_ctas_per_sm) {
+  if (!g) return set_error(SBIO_EINVAL, "null geometry");
+  if (far_tt) *far_tt = g->h.far_tt;
+  if (far_splits) *far_splits = g->h.far_splits;
+  if (near_ctas_per_sm) *near_ctas_per_sm = g->h.near_ctas_per_sm;
+  return SBIO_OK;
+}
+
 int sbio_geom_autotune(sbio_geom* g, void* stream, int32_t* far_tt, int32_t* far_splits, double* far_ms) {
   clear_error();
   if (!g) return set_error(SBIO_EINVAL, "null geometry");
@@ -600,10 +624,36 @@ int sbio_geom_autotune(sbio_geom* g, void* stream, int32_t* far_tt, int32_t* far
       }
     }
   }
-  cudaEventDestroy(e0);
-  cudaEventDestroy(e1);
   h.far_tt = best_tt;
   h.far_splits = best_sp;
+  // near CTAs per SM while the near field overlaps the far field: time whole applies
+  if (g->overlap && g->near_stream && !g->timing && !h.pair_t.empty()) {
+    const int caps[4] = {1, 2, 4, 0};
+    float best_apply = 1e30f;
+    int best_cap = h.near_ctas_per_sm;
+    for (int c = 0; c < 4; ++c) {
+      h.near_ctas_per_sm = caps[c];
+      rc = launch_laplace(g, d.host_in, d.host_in + nc, d.host_out, d.host_out + h.N, SBIO_PART_ALL, st);
+      if (rc) break;
+      float tms[2];
+      for (int r = 0; r < 2 && !rc; ++r) {
+        cudaEventRecord(e0, st);
+        rc = launch_laplace(g, d.host_in, d.host_in + nc, d.host_out, d.host_out + h.N, SBIO_PART_ALL, st);
+        cudaEventRecord(e1, st);
+        SBIO_CUDA_TRY(cudaEventSynchronize(e1));
+        cudaEventElapsedTime(&tms[r], e0, e1);
+      }
+      const float m = std::min(tms[0], tms[1]);
+      if (m < best_apply) {
+        best_apply = m;
+        best_cap = caps[c];
+      }
+    }
+    h.near_ctas_per_sm = best_cap;
+    if (rc) return rc;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
   SBIO_CUDA_TRY(cudaGetLastError());
   if (far_tt) *far_tt = best_tt;
   if (far_splits) *far_splits = best_sp;

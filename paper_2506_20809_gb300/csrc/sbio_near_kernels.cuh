@@ -19,22 +19,24 @@ __global__ void __launch_bounds__(128) near_kernel(const int32_t* __restrict__ p
                                                    const double* __restrict__ beta,
                                                    const double* __restrict__ inv_tab, double* __restrict__ S_out,
                                                    double* __restrict__ D_out) {
-  const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (r >= count) return;
-  const int64_t idx = first + r;
-  const int t = pair_t[idx], i = pair_s[idx];
-  const PartGeom& G = parts[i];
-  const double dx = xyz[(int64_t)t * 3 + 0] - G.c[0];
-  const double dy = xyz[(int64_t)t * 3 + 1] - G.c[1];
-  const double dz = xyz[(int64_t)t * 3 + 2] - G.c[2];
-  const double xl = G.R[0] * dx + G.R[3] * dy + G.R[6] * dz;
-  const double yl = G.R[1] * dx + G.R[4] * dy + G.R[7] * dz;
-  const double zl = G.R[2] * dx + G.R[5] * dy + G.R[8] * dz;
+  // grid-stride over the pairs: a capped grid lets the near kernel share the
+  // SMs with a concurrently running far-field kernel
   constexpr int NC = (P + 1) * (P + 1);
-  double S, D;
-  near_pair<P, KIND, DO_S, DO_D>(xl, yl, zl, G.a, alpha + (size_t)i * NC, beta + (size_t)i * NC, inv_tab, S, D);
-  if (DO_S) atomicAdd(S_out + t, S);
-  if (DO_D) atomicAdd(D_out + t, D);
+  for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < count; r += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t idx = first + r;
+    const int t = pair_t[idx], i = pair_s[idx];
+    const PartGeom& G = parts[i];
+    const double dx = xyz[(int64_t)t * 3 + 0] - G.c[0];
+    const double dy = xyz[(int64_t)t * 3 + 1] - G.c[1];
+    const double dz = xyz[(int64_t)t * 3 + 2] - G.c[2];
+    const double xl = G.R[0] * dx + G.R[3] * dy + G.R[6] * dz;
+    const double yl = G.R[1] * dx + G.R[4] * dy + G.R[7] * dz;
+    const double zl = G.R[2] * dx + G.R[5] * dy + G.R[8] * dz;
+    double S, D;
+    near_pair<P, KIND, DO_S, DO_D>(xl, yl, zl, G.a, alpha + (size_t)i * NC, beta + (size_t)i * NC, inv_tab, S, D);
+    if (DO_S) atomicAdd(S_out + t, S);
+    if (DO_D) atomicAdd(D_out + t, D);
+  }
 }
 
 template <int P, int KIND>
@@ -42,7 +44,9 @@ static void launch_near_pk(const DevGeom& d, int64_t first, int64_t count, const
                            double* D, cudaStream_t st) {
   if (count <= 0) return;
   const int threads = 128;
-  const unsigned blocks = (unsigned)((count + threads - 1) / threads);
+  int64_t nb = (count + threads - 1) / threads;
+  if (d.near_grid_cap > 0 && nb > d.near_grid_cap) nb = d.near_grid_cap;
+  const unsigned blocks = (unsigned)nb;
   if (S && D)
     near_kernel<P, KIND, true, true><<<blocks, threads, 0, st>>>(d.pair_t, d.pair_s, first, count, d.parts, d.xyz,
                                                                  d.alpha, d.beta, inv_tab, S, D);

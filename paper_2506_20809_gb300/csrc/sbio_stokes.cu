@@ -123,9 +123,82 @@ __global__ void __launch_bounds__(256) stokes_prep_kernel(
     s[4] = fw[1]; s[5] = fw[2]; s[6] = 0.0; s[7] = 0.0;
     src32[t * 2 + 0] = make_float4((float)y0, (float)y1, (float)y2, (float)fw[0]);
     src32[t * 2 + 1] = make_float4((float)fw[1], (float)fw[2], 0.f, 0.f);
-    u_out[t * 3 + 0] = 0.0;
-    u_out[t * 3 + 1] = 0.0;
-    u_out[t * 3 + 2] = 0.0;
+  }
+}
+
+// Self term (own particle) at u = u0, separable: for each of the four
+// expansions the value and the three unit-vector derivatives are inverse
+// transforms of the folded coefficients times q(u0) or q'(u0), with the
+// Ferrers tables P, sqrt(1-v^2) dP/dv and m P / sqrt(1-v^2) at the GL nodes
+// (the exterior limit of eq. (dSLevalformula) applied mode by mode).  Writes u.
+__global__ void __launch_bounds__(256) stokes_self_kernel(int p, int n_v, int n_phi, const PartGeom* __restrict__ parts,
+                                                          const double* __restrict__ xyz,
+                                                          const double* __restrict__ coef,
+                                                          const double* __restrict__ qu0,
+                                                          const double* __restrict__ dqu0,
+                                                          const double* __restrict__ fP,
+                                                          const double* __restrict__ fV,
+                                                          const double* __restrict__ fF,
+                                                          const double* __restrict__ trig1,
+                                                          const double* __restrict__ gl_v,
+                                                          double* __restrict__ u_out) {
+  extern __shared__ double sm[];
+  const int i = blockIdx.x;
+  const int p1 = p + 1, nc1 = (p1 + 1) * (p1 + 1), nm1 = nm_count(p1), mw1 = 2 * p1 + 1;
+  const int G = n_v * n_phi;
+  const PartGeom P = parts[i];
+  const double* cf = coef + (size_t)i * 4 * nc1;
+  const double* q0 = qu0 + (size_t)i * nm1;
+  const double* dq0 = dqu0 + (size_t)i * nm1;
+  // L[(d * 4 + qty) * n_v + j][ms]: qty 0 value, 1 d/du, 2 sv d/dv, 3 d/dphi / sv
+  for (int idx = threadIdx.x; idx < 16 * n_v * mw1; idx += blockDim.x) {
+    const int row = idx / mw1, ms = idx - row * mw1, m = ms - p1, am = m < 0 ? -m : m;
+    const int dq = row / n_v, j = row - dq * n_v, dd = dq >> 2, qty = dq & 3;
+    const double* tab = (qty == 2) ? fV : (qty == 3 ? fF : fP);
+    const double* rad = (qty == 1) ? dq0 : q0;
+    double acc = 0.0;
+    for (int n = am; n <= p1; ++n)
+      acc = fma(cf[dd * nc1 + n * n + n + m] * rad[nm_index(n, am)], tab[(size_t)j * nm1 + nm_index(n, am)], acc);
+    sm[idx] = acc;
+  }
+  __syncthreads();
+  const double sgn = P.sgn, u = P.u0;
+  const double su = P.A / P.a;                  // sqrt(u0^2 + sgn)
+  const double ia = 1.0 / P.a;
+  for (int l = threadIdx.x; l < G; l += blockDim.x) {
+    const int j = l / n_phi, k = l - j * n_phi;
+    const double* tr = trig1 + (size_t)k * (p1 + 1) * 2;
+    double F[4][4];
+    for (int dq = 0; dq < 16; ++dq) {
+      const double* L = sm + ((size_t)dq * n_v + j) * mw1 + p1;
+      double acc;
+      if ((dq & 3) == 3) {   // d/dphi: cos -> -m sin, sin -> m cos (m inside the table)
+        acc = 0.0;
+        for (int m = 1; m <= p1; ++m) acc = fma(-L[m], tr[2 * m + 1], fma(L[-m], tr[2 * m], acc));
+      } else {
+        acc = L[0];
+        for (int m = 1; m <= p1; ++m) acc = fma(L[m], tr[2 * m], fma(L[-m], tr[2 * m + 1], acc));
+      }
+      F[dq >> 2][dq & 3] = acc;
+    }
+    const double v = gl_v[j], sv = sqrt((1.0 - v) * (1.0 + v));
+    const double c1 = tr[2], s1 = tr[3];
+    const double iW = rsqrt(u * u + sgn * v * v);
+    const double eu0 = u * sv * c1 * iW, eu1 = u * sv * s1 * iW, eu2 = v * su * iW;
+    const double ev0 = -su * v * c1 * iW, ev1 = -su * v * s1 * iW, ev2 = u * sv * iW;
+    double g[4][3];
+    for (int dd = 0; dd < 4; ++dd) {
+      const double gu = F[dd][1] * su * ia * iW, gv = F[dd][2] * ia * iW, gp = F[dd][3] * ia / su;
+      g[dd][0] = gu * eu0 + gv * ev0 - gp * s1;
+      g[dd][1] = gu * eu1 + gv * ev1 + gp * c1;
+      g[dd][2] = gu * eu2 + gv * ev2;
+    }
+    const int64_t t = (int64_t)i * G + l;
+    const double X0 = xyz[t * 3 + 0] - P.c[0], X1 = xyz[t * 3 + 1] - P.c[1], X2 = xyz[t * 3 + 2] - P.c[2];
+    double w[3];
+    for (int c = 0; c < 3; ++c) w[c] = g[3][c] - (X0 * g[0][c] + X1 * g[1][c] + X2 * g[2][c]);
+    for (int c = 0; c < 3; ++c)
+      u_out[t * 3 + c] = 0.5 * (F[c][0] + P.R[c * 3 + 0] * w[0] + P.R[c * 3 + 1] * w[1] + P.R[c * 3 + 2] * w[2]);
   }
 }
 
@@ -318,6 +391,7 @@ int launch_stokes(sbio_geom* g, const double* f, double* u, cudaStream_t st) {
   if (!nl) nl = stokes_near_lookup_b(p);
   if (!nl) return set_error(SBIO_ENOTSUP, "no Stokes near-field kernel for p = %d", p);
   const int p1 = p + 1, nc = (p + 1) * (p + 1), nc1 = (p1 + 1) * (p1 + 1), mw = 2 * p + 1, mw1 = 2 * p1 + 1;
+  (void)nc1;
   const int nrow = h.n_q > h.n_v ? h.n_q : h.n_v;
   const size_t smem = (size_t)(3 * nc + nc1 + 3 * nrow * mw + h.n_q * h.n_f + h.n_q * mw1) * sizeof(double);
   if (smem > 48 * 1024)
@@ -328,18 +402,27 @@ int launch_stokes(sbio_geom* g, const double* f, double* u, cudaStream_t st) {
                                              d.st_normc, f, d.st_coef, d.st_src64, d.st_src32, u);
   count_launch();
   SBIO_CUDA_TRY(cudaGetLastError());
+  const size_t smem_self = (size_t)16 * h.n_v * mw1 * sizeof(double);
+  if (smem_self > 48 * 1024)
+    SBIO_CUDA_TRY(cudaFuncSetAttribute(stokes_self_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_self));
+  stokes_self_kernel<<<h.M, 256, smem_self, st>>>(p, h.n_v, h.n_phi, d.parts, d.xyz, d.st_coef, d.st_qu0, d.st_dqu0,
+                                                  d.st_fP, d.st_fV, d.st_fF, d.st_trig1, d.st_glv, u);
+  count_launch();
+  SBIO_CUDA_TRY(cudaGetLastError());
   phase_mark(g, 1, st);
-  // the FP64 near/self kernels run beside the FP32 Stokeslet kernel unless
-  // phases are being timed one by one
-  const bool fork = g->overlap && !g->timing && g->near_stream;
+  // the FP64 near kernels run beside the FP32 Stokeslet kernel unless phases
+  // are being timed one by one
+  const bool fork = g->overlap && !g->timing && g->near_stream && !h.pair_t.empty();
   if (fork) {
     SBIO_CUDA_TRY(cudaEventRecord(g->ev_fork, st));
     SBIO_CUDA_TRY(cudaStreamWaitEvent(g->near_stream, g->ev_fork, 0));
-    nl(d, h.st_pairs_prolate, (int64_t)h.st_pair_t.size(), d.inv, u, g->near_stream);
+    g->d.near_grid_cap = h.near_ctas_per_sm > 0 ? h.near_ctas_per_sm * sm_count() : 0;
+    nl(g->d, h.n_pairs_prolate, (int64_t)h.pair_t.size(), d.inv, u, g->near_stream);
+    g->d.near_grid_cap = 0;
     SBIO_CUDA_TRY(cudaGetLastError());
     SBIO_CUDA_TRY(cudaEventRecord(g->ev_join, g->near_stream));
-  } else {
-    nl(d, h.st_pairs_prolate, (int64_t)h.st_pair_t.size(), d.inv, u, st);
+  } else if (!h.pair_t.empty()) {
+    nl(d, h.n_pairs_prolate, (int64_t)h.pair_t.size(), d.inv, u, st);
     SBIO_CUDA_TRY(cudaGetLastError());
   }
   phase_mark(g, 2, st);

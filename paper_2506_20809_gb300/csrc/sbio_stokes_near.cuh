@@ -137,23 +137,23 @@ __global__ void __launch_bounds__(128) stokes_near_kernel(const int32_t* __restr
                                                           const double* __restrict__ coef,
                                                           const double* __restrict__ inv_tab,
                                                           double* __restrict__ u_out) {
-  const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (r >= count) return;
-  const int64_t idx = first + r;
-  const int t = pair_t[idx], i = pair_s[idx];
-  const PartGeom& G = parts[i];
-  const double X0 = xyz[(int64_t)t * 3 + 0] - G.c[0];
-  const double X1 = xyz[(int64_t)t * 3 + 1] - G.c[1];
-  const double X2 = xyz[(int64_t)t * 3 + 2] - G.c[2];
-  const double xl = G.R[0] * X0 + G.R[3] * X1 + G.R[6] * X2;
-  const double yl = G.R[1] * X0 + G.R[4] * X1 + G.R[7] * X2;
-  const double zl = G.R[2] * X0 + G.R[5] * X1 + G.R[8] * X2;
   constexpr int NC = (P1 + 1) * (P1 + 1);
-  double o[3];
-  stokes_pair<P1, KIND>(xl, yl, zl, G.a, G.R, X0, X1, X2, coef + (size_t)i * 4 * NC, inv_tab, o);
-  atomicAdd(u_out + (int64_t)t * 3 + 0, o[0]);
-  atomicAdd(u_out + (int64_t)t * 3 + 1, o[1]);
-  atomicAdd(u_out + (int64_t)t * 3 + 2, o[2]);
+  for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < count; r += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t idx = first + r;
+    const int t = pair_t[idx], i = pair_s[idx];
+    const PartGeom& G = parts[i];
+    const double X0 = xyz[(int64_t)t * 3 + 0] - G.c[0];
+    const double X1 = xyz[(int64_t)t * 3 + 1] - G.c[1];
+    const double X2 = xyz[(int64_t)t * 3 + 2] - G.c[2];
+    const double xl = G.R[0] * X0 + G.R[3] * X1 + G.R[6] * X2;
+    const double yl = G.R[1] * X0 + G.R[4] * X1 + G.R[7] * X2;
+    const double zl = G.R[2] * X0 + G.R[5] * X1 + G.R[8] * X2;
+    double o[3];
+    stokes_pair<P1, KIND>(xl, yl, zl, G.a, G.R, X0, X1, X2, coef + (size_t)i * 4 * NC, inv_tab, o);
+    atomicAdd(u_out + (int64_t)t * 3 + 0, o[0]);
+    atomicAdd(u_out + (int64_t)t * 3 + 1, o[1]);
+    atomicAdd(u_out + (int64_t)t * 3 + 2, o[2]);
+  }
 }
 
 typedef void (*stokes_near_launcher)(const DevGeom&, int64_t, int64_t, const double*, double*, cudaStream_t);
@@ -162,8 +162,10 @@ template <int P1, int KIND>
 static void launch_stokes_near_pk(const DevGeom& d, int64_t first, int64_t count, const double* inv, double* u,
                                   cudaStream_t st) {
   if (count <= 0) return;
-  const unsigned blocks = (unsigned)((count + 127) / 128);
-  stokes_near_kernel<P1, KIND><<<blocks, 128, 0, st>>>(d.st_pair_t, d.st_pair_s, first, count, d.parts, d.xyz,
+  int64_t nb = (count + 127) / 128;
+  if (d.near_grid_cap > 0 && nb > d.near_grid_cap) nb = d.near_grid_cap;
+  const unsigned blocks = (unsigned)nb;
+  stokes_near_kernel<P1, KIND><<<blocks, 128, 0, st>>>(d.pair_t, d.pair_s, first, count, d.parts, d.xyz,
                                                         d.st_coef, inv, u);
   count_launch();
 }

@@ -87,6 +87,8 @@ _SIGS = {
     "sbio_geom_enable_timing": (C.c_int, [_vp, C.c_int32]),
     "sbio_geom_set_launch_shape": (C.c_int, [_vp, C.c_int32, C.c_int32]),
     "sbio_geom_set_overlap": (C.c_int, [_vp, C.c_int32]),
+    "sbio_geom_set_near_cap": (C.c_int, [_vp, C.c_int32]),
+    "sbio_geom_get_tuning": (C.c_int, [_vp, C.POINTER(C.c_int32), C.POINTER(C.c_int32), C.POINTER(C.c_int32)]),
     "sbio_geom_autotune": (C.c_int, [_vp, _vp, C.POINTER(C.c_int32), C.POINTER(C.c_int32),
                                      C.POINTER(C.c_double)]),
     "sbio_geom_phase_times": (C.c_int, [_vp, C.POINTER(C.c_double), C.POINTER(C.c_double),
@@ -232,6 +234,16 @@ def sbio_geom_set_precision(g, precision):
 
 def sbio_geom_set_overlap(g, on=True):
     _check(_lib.sbio_geom_set_overlap(g, 1 if on else 0))
+
+
+def sbio_geom_set_near_cap(g, ctas_per_sm):
+    _check(_lib.sbio_geom_set_near_cap(g, ctas_per_sm))
+
+
+def sbio_geom_get_tuning(g):
+    a, b, c = C.c_int32(), C.c_int32(), C.c_int32()
+    _check(_lib.sbio_geom_get_tuning(g, C.byref(a), C.byref(b), C.byref(c)))
+    return {"far_tt": a.value, "far_splits": b.value, "near_ctas_per_sm": c.value}
 
 
 def sbio_geom_set_launch_shape(g, far_tt, far_splits):
