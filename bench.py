@@ -461,7 +461,7 @@ def run_batch64(args, ws, rank, lrank):
     st = torch.cuda.current_stream()
     b = S.sbio_batch_create(ctx, geoms)
     best = None
-    for tt in (1, 2, 4, 8):                            # autotune the persistent far kernel
+    for tt in (1, 2, 4, 8, -2, -4, -8):                # autotune the persistent far kernel
         S.sbio_batch_set_far_tt(b, tt)
         S.sbio_batch_apply(b, sig, mu, So, Do)
         t = min(_event_time(st, lambda: S.sbio_batch_apply(b, sig, mu, So, Do)) for _ in range(2))

@@ -160,7 +160,8 @@ int sbio_geom_enable_timing(sbio_geom* g, int32_t on);
 int sbio_geom_phase_times(sbio_geom* g, double* ms_synth, double* ms_near, double* ms_far);
 
 /* Launch shape of the far-field kernels: far_tt targets per thread of the
- * mixed kernel (1, 2, 4 or 8) and far_splits source splits of the grid (0 =
+ * mixed kernel (1, 2, 4 or 8; -2, -4, -8 select the same counts computed two
+ * targets per packed f32x2 instruction) and far_splits source splits of the grid (0 =
  * chosen from the device's SM count).  Results do not depend on the shape
  * beyond floating-point summation order. */
 int sbio_geom_set_launch_shape(sbio_geom* g, int32_t far_tt, int32_t far_splits);
@@ -245,7 +246,8 @@ int sbio_batch_destroy(sbio_batch* b);
  * kernel and its persistent grid size (outputs may be NULL). */
 int sbio_batch_info(const sbio_batch* b, int64_t* n_items, int64_t* far_pairs, int32_t* far_tt, int32_t* grid);
 
-/* Targets per thread (1, 2, 4, 8) of the persistent far kernel; rebuilds the
+/* Targets per thread (1, 2, 4, 8, or -2, -4, -8 for the packed f32x2 form) of
+ * the persistent far kernel; rebuilds the
  * work list and drops the captured graph. */
 int sbio_batch_set_far_tt(sbio_batch* b, int32_t far_tt);
 

@@ -40,7 +40,7 @@ static int build_items(sbio_batch* b) {
     int64_t cost;
   };
   std::vector<Item> items;
-  const int tt = b->far_tt;
+  const int tt = b->far_tt < 0 ? -b->far_tt : b->far_tt;
   for (size_t s = 0; s < b->geoms.size(); ++s) {
     const GeomHost& h = b->geoms[s]->h;
     const int nt = (int)h.tiles.size();
@@ -188,7 +188,8 @@ int sbio_batch_info(const sbio_batch* b, int64_t* n_items, int64_t* far_pairs, i
 int sbio_batch_set_far_tt(sbio_batch* b, int32_t tt) {
   clear_error();
   if (!b) return set_error(SBIO_EINVAL, "null batch");
-  if (tt != 1 && tt != 2 && tt != 4 && tt != 8) return set_error(SBIO_EINVAL, "far_tt must be 1, 2, 4 or 8");
+  if (tt != 1 && tt != 2 && tt != 4 && tt != 8 && tt != -2 && tt != -4 && tt != -8)
+    return set_error(SBIO_EINVAL, "far_tt must be 1, 2, 4, 8 or -2, -4, -8 (packed)");
   SBIO_CUDA_TRY(cudaSetDevice(b->ctx->device));
   SBIO_CUDA_TRY(cudaStreamSynchronize(b->sa));
   b->far_tt = tt;

@@ -219,13 +219,17 @@ __global__ void __launch_bounds__(kFarTile) far_fp64_kernel(const int4* __restri
 // relative to the current source particle and the running tile partials live
 // in registers; the two-sum accumulators and the skip-list cursors live in
 // shared memory and are touched once per tile.
-template <int TT, bool DO_S, bool DO_D>
-__device__ __forceinline__ void far_mixed_block(float4* sh, int64_t tb, int t_lo, int t_hi,
+template <int TT, bool DO_S, bool DO_D, bool PK>
+__device__ __forceinline__ void far_mixed_block(int64_t tb, int t_lo, int t_hi,
                                                 const int4* __restrict__ tiles, const float4* __restrict__ src32,
                                                 const float4* __restrict__ tgt32, const float4* __restrict__ cen32,
                                                 const int32_t* __restrict__ skip_ptr,
                                                 const int32_t* __restrict__ skip_idx, int64_t N,
                                                 double* __restrict__ S_out, double* __restrict__ D_out) {
+  // tile of sources: scalar form (y - c, q), (d, 0); packed form every value
+  // duplicated into an f32x2 pair and y negated: (-y.x,-y.x,-y.y,-y.y),
+  // (-y.z,-y.z,q,q), (d.x,d.x,d.y,d.y), (d.z,d.z,0,0)
+  __shared__ float4 sh[(PK ? 4 : 2) * kFarTile];
   __shared__ float acc[4 * TT * kFarTile];   // per target: S hi, S lo, D hi, D lo
   __shared__ int cursor[2 * TT * kFarTile];  // per target: skip-list position, next skipped particle
   const int tid = threadIdx.x;
@@ -272,26 +276,74 @@ __device__ __forceinline__ void far_mixed_block(float4* sh, int64_t tb, int t_lo
     const bool mine = skipmask != (1u << TT) - 1u;
     if (!__syncthreads_or(mine)) continue;
     if (tid < tile.z) {
-      sh[tid * 2 + 0] = src32[(int64_t)(tile.y + tid) * 2 + 0];
-      sh[tid * 2 + 1] = src32[(int64_t)(tile.y + tid) * 2 + 1];
+      const float4 a = src32[(int64_t)(tile.y + tid) * 2 + 0];
+      const float4 b = src32[(int64_t)(tile.y + tid) * 2 + 1];
+      if (PK) {
+        sh[tid * 4 + 0] = make_float4(-a.x, -a.x, -a.y, -a.y);
+        sh[tid * 4 + 1] = make_float4(-a.z, -a.z, a.w, a.w);
+        sh[tid * 4 + 2] = make_float4(b.x, b.x, b.y, b.y);
+        sh[tid * 4 + 3] = make_float4(b.z, b.z, 0.f, 0.f);
+      } else {
+        sh[tid * 2 + 0] = a;
+        sh[tid * 2 + 1] = b;
+      }
     }
     __syncthreads();
     if (mine) {
       float pS[TT], pD[TT];
 #pragma unroll
       for (int q = 0; q < TT; ++q) pS[q] = pD[q] = 0.f;
-#pragma unroll 2
-      for (int j = 0; j < tile.z; ++j) {
-        const float4 a = sh[j * 2], b = sh[j * 2 + 1];
+      if constexpr (PK) {
+        // two targets per f32x2 operation (sm_100+ packed FP32), one MUFU rsqrt per pair
+        constexpr int TP = TT / 2 > 0 ? TT / 2 : 1;
+        float2 Xp[TP], Yp[TP], Zp[TP], sS2[TP], sD2[TP];
 #pragma unroll
-        for (int q = 0; q < TT; ++q) {
-          const float dx = X[q] - a.x, dy = Y[q] - a.y, dz = Z[q] - a.z;
-          const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
-          const float ri = rsqrt_approx(r2);
-          if (DO_S) pS[q] = fmaf(a.w, ri, pS[q]);
-          if (DO_D) {
-            const float dn = fmaf(b.z, dz, fmaf(b.y, dy, b.x * dx));
-            pD[q] = fmaf(dn * ri, ri * ri, pD[q]);
+        for (int k = 0; k < TT / 2; ++k) {
+          Xp[k] = make_float2(X[2 * k], X[2 * k + 1]);
+          Yp[k] = make_float2(Y[2 * k], Y[2 * k + 1]);
+          Zp[k] = make_float2(Z[2 * k], Z[2 * k + 1]);
+          sS2[k] = make_float2(0.f, 0.f);
+          sD2[k] = make_float2(0.f, 0.f);
+        }
+#pragma unroll 2
+        for (int j = 0; j < tile.z; ++j) {
+          const float4 A = sh[j * 4 + 0], B = sh[j * 4 + 1], Cc = sh[j * 4 + 2], Dd = sh[j * 4 + 3];
+          const float2 my = make_float2(A.x, A.y), myy = make_float2(A.z, A.w), myz = make_float2(B.x, B.y);
+          const float2 q2 = make_float2(B.z, B.w), dwx = make_float2(Cc.x, Cc.y), dwy = make_float2(Cc.z, Cc.w);
+          const float2 dwz = make_float2(Dd.x, Dd.y);
+#pragma unroll
+          for (int k = 0; k < TT / 2; ++k) {
+            const float2 dx = __fadd2_rn(Xp[k], my), dy = __fadd2_rn(Yp[k], myy), dz = __fadd2_rn(Zp[k], myz);
+            const float2 r2 = __ffma2_rn(dz, dz, __ffma2_rn(dy, dy, __fmul2_rn(dx, dx)));
+            const float2 ri = make_float2(rsqrt_approx(r2.x), rsqrt_approx(r2.y));
+            if (DO_S) sS2[k] = __ffma2_rn(q2, ri, sS2[k]);
+            if (DO_D) {
+              const float2 dn = __ffma2_rn(dwz, dz, __ffma2_rn(dwy, dy, __fmul2_rn(dwx, dx)));
+              sD2[k] = __ffma2_rn(__fmul2_rn(dn, ri), __fmul2_rn(ri, ri), sD2[k]);
+            }
+          }
+        }
+#pragma unroll
+        for (int k = 0; k < TT / 2; ++k) {
+          pS[2 * k] = sS2[k].x;
+          pS[2 * k + 1] = sS2[k].y;
+          pD[2 * k] = sD2[k].x;
+          pD[2 * k + 1] = sD2[k].y;
+        }
+      } else {
+#pragma unroll 2
+        for (int j = 0; j < tile.z; ++j) {
+          const float4 a = sh[j * 2], b = sh[j * 2 + 1];
+#pragma unroll
+          for (int q = 0; q < TT; ++q) {
+            const float dx = X[q] - a.x, dy = Y[q] - a.y, dz = Z[q] - a.z;
+            const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
+            const float ri = rsqrt_approx(r2);
+            if (DO_S) pS[q] = fmaf(a.w, ri, pS[q]);
+            if (DO_D) {
+              const float dn = fmaf(b.z, dz, fmaf(b.y, dy, b.x * dx));
+              pD[q] = fmaf(dn * ri, ri * ri, pD[q]);
+            }
           }
         }
       }
@@ -327,7 +379,7 @@ __device__ __forceinline__ void far_mixed_block(float4* sh, int64_t tb, int t_lo
   __syncthreads();   // the shared arrays are reused by the next block of a persistent CTA
 }
 
-template <int TT, bool DO_S, bool DO_D>
+template <int TT, bool DO_S, bool DO_D, bool PK>
 __global__ void __launch_bounds__(kFarTile) far_mixed_kernel(const int4* __restrict__ tiles, int n_tiles,
                                                              const float4* __restrict__ src32,
                                                              const float4* __restrict__ tgt32,
@@ -335,11 +387,10 @@ __global__ void __launch_bounds__(kFarTile) far_mixed_kernel(const int4* __restr
                                                              const int32_t* __restrict__ skip_ptr,
                                                              const int32_t* __restrict__ skip_idx, int64_t N,
                                                              double* __restrict__ S_out, double* __restrict__ D_out) {
-  __shared__ float4 sh[kFarTile * 2];
   const int per = (n_tiles + gridDim.y - 1) / gridDim.y;
   const int t_lo = blockIdx.y * per, t_hi = min(n_tiles, t_lo + per);
-  far_mixed_block<TT, DO_S, DO_D>(sh, blockIdx.x, t_lo, t_hi, tiles, src32, tgt32, cen32, skip_ptr, skip_idx, N,
-                                  S_out, D_out);
+  far_mixed_block<TT, DO_S, DO_D, PK>(blockIdx.x, t_lo, t_hi, tiles, src32, tgt32, cen32, skip_ptr, skip_idx, N,
+                                      S_out, D_out);
 }
 
 // Number of source splits so that the grid holds about `waves` resident
@@ -366,20 +417,21 @@ int far_split_count(int64_t target_blocks, int n_tiles, int requested) {
   return (int)s;
 }
 
-template <int TT>
+template <int TT, bool PK>
 static void launch_far_mixed_tt(const DevGeom& d, const GeomHost& h, int nt, int splits, double* S, double* D,
                                 cudaStream_t st) {
+  static_assert(!PK || TT % 2 == 0, "packed form pairs targets");
   const int64_t tb = (h.N + kFarTile * TT - 1) / (kFarTile * TT);
   const dim3 grid((unsigned)tb, (unsigned)far_split_count(tb, nt, splits));
   if (S && D)
-    far_mixed_kernel<TT, true, true><<<grid, kFarTile, 0, st>>>(d.tiles, nt, d.src32, d.tgt32, d.cen32, d.skip_ptr,
-                                                                d.skip_idx, h.N, S, D);
+    far_mixed_kernel<TT, true, true, PK><<<grid, kFarTile, 0, st>>>(d.tiles, nt, d.src32, d.tgt32, d.cen32,
+                                                                    d.skip_ptr, d.skip_idx, h.N, S, D);
   else if (S)
-    far_mixed_kernel<TT, true, false><<<grid, kFarTile, 0, st>>>(d.tiles, nt, d.src32, d.tgt32, d.cen32, d.skip_ptr,
-                                                                 d.skip_idx, h.N, S, D);
+    far_mixed_kernel<TT, true, false, PK><<<grid, kFarTile, 0, st>>>(d.tiles, nt, d.src32, d.tgt32, d.cen32,
+                                                                     d.skip_ptr, d.skip_idx, h.N, S, D);
   else
-    far_mixed_kernel<TT, false, true><<<grid, kFarTile, 0, st>>>(d.tiles, nt, d.src32, d.tgt32, d.cen32, d.skip_ptr,
-                                                                 d.skip_idx, h.N, S, D);
+    far_mixed_kernel<TT, false, true, PK><<<grid, kFarTile, 0, st>>>(d.tiles, nt, d.src32, d.tgt32, d.cen32,
+                                                                     d.skip_ptr, d.skip_idx, h.N, S, D);
 }
 
 static void launch_far(sbio_geom* g, double* S, double* D, cudaStream_t st) {
@@ -399,11 +451,15 @@ static void launch_far(sbio_geom* g, double* S, double* D, cudaStream_t st) {
       far_fp64_kernel<false, true><<<grid, kFarTile, 0, st>>>(d.tiles, nt, d.src64, d.xyz, d.parts, d.skip_ptr,
                                                               d.skip_idx, h.N, S, D);
   } else {
+    // far_tt < 0 selects the packed f32x2 form with |far_tt| targets per thread
     switch (h.far_tt) {
-      case 1: launch_far_mixed_tt<1>(d, h, nt, h.far_splits, S, D, st); break;
-      case 4: launch_far_mixed_tt<4>(d, h, nt, h.far_splits, S, D, st); break;
-      case 8: launch_far_mixed_tt<8>(d, h, nt, h.far_splits, S, D, st); break;
-      default: launch_far_mixed_tt<2>(d, h, nt, h.far_splits, S, D, st); break;
+      case 1: launch_far_mixed_tt<1, false>(d, h, nt, h.far_splits, S, D, st); break;
+      case 4: launch_far_mixed_tt<4, false>(d, h, nt, h.far_splits, S, D, st); break;
+      case 8: launch_far_mixed_tt<8, false>(d, h, nt, h.far_splits, S, D, st); break;
+      case -2: launch_far_mixed_tt<2, true>(d, h, nt, h.far_splits, S, D, st); break;
+      case -4: launch_far_mixed_tt<4, true>(d, h, nt, h.far_splits, S, D, st); break;
+      case -8: launch_far_mixed_tt<8, true>(d, h, nt, h.far_splits, S, D, st); break;
+      default: launch_far_mixed_tt<2, false>(d, h, nt, h.far_splits, S, D, st); break;
     }
   }
   count_launch();
@@ -412,11 +468,10 @@ static void launch_far(sbio_geom* g, double* S, double* D, cudaStream_t st) {
 // Persistent far field over many suspensions: CTAs pull work items
 // (suspension, target block, first tile, end tile) from an atomic counter
 // until the list is exhausted (items are ordered longest first).
-template <int TT>
+template <int TT, bool PK>
 __global__ void __launch_bounds__(kFarTile) far_persistent_kernel(const FarDesc* __restrict__ descs,
                                                                   const int4* __restrict__ items, int n_items,
                                                                   int* __restrict__ counter) {
-  __shared__ float4 sh[kFarTile * 2];
   __shared__ int s_item;
   for (;;) {
     if (threadIdx.x == 0) s_item = atomicAdd(counter, 1);
@@ -426,18 +481,21 @@ __global__ void __launch_bounds__(kFarTile) far_persistent_kernel(const FarDesc*
     if (it >= n_items) break;
     const int4 w = items[it];
     const FarDesc& D = descs[w.x];
-    far_mixed_block<TT, true, true>(sh, w.y, w.z, w.w, D.tiles, D.src32, D.tgt32, D.cen32, D.skip_ptr, D.skip_idx,
-                                    D.N, D.S, D.D);
+    far_mixed_block<TT, true, true, PK>(w.y, w.z, w.w, D.tiles, D.src32, D.tgt32, D.cen32, D.skip_ptr, D.skip_idx,
+                                        D.N, D.S, D.D);
   }
 }
 
 int launch_far_persistent(const FarDesc* descs, const int4* items, int n_items, int* counter, int tt, int grid,
                           cudaStream_t st) {
   switch (tt) {
-    case 1: far_persistent_kernel<1><<<grid, kFarTile, 0, st>>>(descs, items, n_items, counter); break;
-    case 4: far_persistent_kernel<4><<<grid, kFarTile, 0, st>>>(descs, items, n_items, counter); break;
-    case 8: far_persistent_kernel<8><<<grid, kFarTile, 0, st>>>(descs, items, n_items, counter); break;
-    default: far_persistent_kernel<2><<<grid, kFarTile, 0, st>>>(descs, items, n_items, counter); break;
+    case 1: far_persistent_kernel<1, false><<<grid, kFarTile, 0, st>>>(descs, items, n_items, counter); break;
+    case 4: far_persistent_kernel<4, false><<<grid, kFarTile, 0, st>>>(descs, items, n_items, counter); break;
+    case 8: far_persistent_kernel<8, false><<<grid, kFarTile, 0, st>>>(descs, items, n_items, counter); break;
+    case -2: far_persistent_kernel<2, true><<<grid, kFarTile, 0, st>>>(descs, items, n_items, counter); break;
+    case -4: far_persistent_kernel<4, true><<<grid, kFarTile, 0, st>>>(descs, items, n_items, counter); break;
+    case -8: far_persistent_kernel<8, true><<<grid, kFarTile, 0, st>>>(descs, items, n_items, counter); break;
+    default: far_persistent_kernel<2, false><<<grid, kFarTile, 0, st>>>(descs, items, n_items, counter); break;
   }
   count_launch();
   SBIO_CUDA_TRY(cudaGetLastError());
@@ -554,8 +612,8 @@ int sbio_apply_laplace_host(sbio_geom* g, const double* sigma_host, const double
 int sbio_geom_set_launch_shape(sbio_geom* g, int32_t far_tt, int32_t far_splits) {
   clear_error();
   if (!g) return set_error(SBIO_EINVAL, "null geometry");
-  if (far_tt != 1 && far_tt != 2 && far_tt != 4 && far_tt != 8)
-    return set_error(SBIO_EINVAL, "far_tt must be 1, 2, 4 or 8");
+  if (far_tt != 1 && far_tt != 2 && far_tt != 4 && far_tt != 8 && far_tt != -2 && far_tt != -4 && far_tt != -8)
+    return set_error(SBIO_EINVAL, "far_tt must be 1, 2, 4, 8 or -2, -4, -8 (packed)");
   if (far_splits < 0) return set_error(SBIO_EINVAL, "far_splits must be >= 0");
   g->h.far_tt = far_tt;
   g->h.far_splits = far_splits;
@@ -597,10 +655,11 @@ int sbio_geom_autotune(sbio_geom* g, void* stream, int32_t* far_tt, int32_t* far
   const int saved_tt = h.far_tt, saved_sp = h.far_splits;
   double best = 1e300;
   int best_tt = saved_tt, best_sp = saved_sp;
-  const int tts[4] = {1, 2, 4, 8};
-  for (int a = 0; a < (h.precision == SBIO_FP64 ? 1 : 4); ++a) {
+  const int tts[7] = {1, 2, 4, 8, -2, -4, -8};
+  for (int a = 0; a < (h.precision == SBIO_FP64 ? 1 : 7); ++a) {
     const int tt = (h.precision == SBIO_FP64) ? 1 : tts[a];
-    const int64_t tb = (h.N + (int64_t)kFarTile * tt - 1) / ((int64_t)kFarTile * tt);
+    const int att = tt < 0 ? -tt : tt;
+    const int64_t tb = (h.N + (int64_t)kFarTile * att - 1) / ((int64_t)kFarTile * att);
     const int base = far_split_count(tb, nt, 0);
     const int cands[6] = {base > 1 ? base / 2 : 1, base, 2 * base, 4 * base, 8 * base, 16 * base};
     for (int b = 0; b < 6; ++b) {

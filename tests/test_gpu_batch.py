@@ -63,7 +63,7 @@ def test_batch_matches_single_geometry(S):
     # new output buffers: re-capture
     outS2 = [torch.empty_like(o) for o in outS]
     outD2 = [torch.empty_like(o) for o in outD]
-    S.sbio_batch_set_far_tt(b, 4)
+    S.sbio_batch_set_far_tt(b, -4)
     S.sbio_batch_apply(b, [r[0] for r in refs], [r[1] for r in refs], outS2, outD2)
     torch.cuda.synchronize()
     for k, r in enumerate(refs):

@@ -95,7 +95,7 @@ def test_lattice_mixed(S, lattice):
     assert OL.normwise_rel_err(Dm, D64) < TOLMIX
 
 
-@pytest.mark.parametrize("tt,splits", [(1, 1), (2, 3), (4, 0), (1, 7), (8, 0), (8, 5)])
+@pytest.mark.parametrize("tt,splits", [(1, 1), (2, 3), (4, 0), (1, 7), (8, 0), (8, 5), (-2, 0), (-4, 3), (-8, 0)])
 def test_launch_shapes_agree(S, lattice, tt, splits):
     """Far-field launch shapes (targets per thread, source splits) change only
     the summation order."""
