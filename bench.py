@@ -33,6 +33,17 @@ sys.path.insert(0, ROOT)
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12     # SMs x FP32 lanes x FMA x max SM clock
 FP64_PEAK_TFLOPS = 1.25                               # nominal GB300 FP64 rate
 FAR_FLOP_PER_PAIR = {"SD": 19, "S": 10, "D": 14}
+
+
+def near_flop_per_pair(p: int) -> int:
+    """Algorithmic FP64 flops of one near (target, source) pair for S and D:
+    the two contractions (FMA over (p+1)^2 coefficients each), the radial x
+    angular product per (n, |m|), the order recurrence of Q (3 flops) and the
+    Ferrers recurrence (4 flops) per (n, |m|), and about 12 flops of angle
+    recurrence and cos/sin combination per order m.  The data-dependent Miller
+    start of Q_n^0, Q_n^1 is not counted."""
+    nm = (p + 1) * (p + 2) // 2
+    return 4 * (p + 1) ** 2 + nm * (1 + 3 + 4) + 12 * (p + 1)
 METRIC = "BIO applies/s (Laplace S+D, all surface nodes)"
 
 
@@ -350,6 +361,12 @@ def run_ours(args, ws, rank, lrank):
                      "traffic": None,
                      "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz" if prec == S.SBIO_MIXED
                      else "nominal FP64 1.25 TFLOP/s"},
+        "roofline_near": {"kernel": "near_kernel", "bound": "alu", "unit": "TFLOP/s",
+                          "achieved": near_flop_per_pair(susp.p) * geom.n_near / (statistics.mean(near_ms) * 1e-3) / 1e12,
+                          "peak": FP64_PEAK_TFLOPS,
+                          "frac": near_flop_per_pair(susp.p) * geom.n_near / (statistics.mean(near_ms) * 1e-3) / 1e12
+                          / FP64_PEAK_TFLOPS, "flop_per_pair": near_flop_per_pair(susp.p),
+                          "peak_source": "nominal GB300 FP64 1.25 TFLOP/s"},
         "e2e": {"value": e2e_val, "unit": "applies/s", "h2d_bytes_per_step": int(hs.nbytes + hm.nbytes),
                 "d2h_bytes_per_step": int(hS.nbytes + hD.nbytes)},
         "gpu_launches": int(launches),
@@ -444,7 +461,12 @@ def run_batch64(args, ws, rank, lrank):
 
     from paper_2506_20809_gb300 import inputs as I
 
-    susps = I.batch_suspensions(64, workers=min(16, os.cpu_count() or 1))   # before CUDA starts
+    all_susps = I.batch_suspensions(64, workers=min(16, os.cpu_count() or 1))   # before CUDA starts
+    from paper_2506_20809_gb300 import replicas as RP
+
+    # several GPUs: each rank owns whole suspensions (no exchange between them)
+    cost = [float((s.M * (s.p + 1) * 2 * (s.p + 1)) ** 2) for s in all_susps]
+    susps = [all_susps[k] for k in RP.shard(len(all_susps), rank, ws, cost)]
     import __graft_entry__ as GE
 
     GE.build()
@@ -484,12 +506,13 @@ def run_batch64(args, ws, rank, lrank):
     for g in geoms:
         S.sbio_geom_set_precision(g.h, S.SBIO_FP64)
     f64 = _event_time(st, lambda: [S.sbio_apply_laplace(g.h, sig[k], mu[k], So[k], Do[k]) for k, g in enumerate(geoms)])
-    mean = statistics.mean(ms)
+    mean = RP.max_over_ranks(statistics.mean(ms), ws)
     line = {"metric": "BIO applies/s (batched Laplace S+D, 64 suspensions per step)",
             "value": 64 * 1e3 / mean, "unit": "applies/s", "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": mean, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
-            "config": {"workload": "batch64", "suspensions": 64, "M": [s.M for s in susps], "p": [s.p for s in susps],
+            "config": {"workload": "batch64", "suspensions": 64, "suspensions_on_rank0": len(susps),
+                       "M": [s.M for s in susps], "p": [s.p for s in susps],
                        "far_pairs_per_step": info["far_pairs"], "work_items": info["n_items"],
                        "persistent_grid": info["grid"], "far_targets_per_thread": best[0],
                        "l2": "flushed by a 256 MiB write before every timed step"},

@@ -282,7 +282,10 @@ __global__ void __launch_bounds__(kFarTile) stokes_far_fp64_kernel(const int4* _
   }
 }
 
-template <int TT>
+// Stokeslet far field for one CTA: TT targets per thread against source tiles
+// [t_lo, t_hi); two-sum accumulators and skip cursors in shared memory (as in
+// the Laplace far kernel); PK computes two targets per f32x2 instruction.
+template <int TT, bool PK>
 __global__ void __launch_bounds__(kFarTile) stokes_far_mixed_kernel(const int4* __restrict__ tiles, int n_tiles,
                                                                     const float4* __restrict__ src32,
                                                                     const float4* __restrict__ tgt32,
@@ -290,96 +293,152 @@ __global__ void __launch_bounds__(kFarTile) stokes_far_mixed_kernel(const int4* 
                                                                     const int32_t* __restrict__ skip_ptr,
                                                                     const int32_t* __restrict__ skip_idx, int64_t N,
                                                                     double* __restrict__ u_out) {
-  __shared__ float4 sh[kFarTile * 2];
-  int64_t tg[TT];
-  bool valid[TT], skip[TT];
-  float xh[TT][3], xo[TT][3], X[TT][3];
-  int sp[TT], nxt[TT];
-  float hi[TT][3], lo[TT][3];
-#pragma unroll
-  for (int q = 0; q < TT; ++q) {
-    tg[q] = ((int64_t)blockIdx.x * TT + q) * kFarTile + threadIdx.x;
-    valid[q] = tg[q] < N;
-    sp[q] = 0;
-    nxt[q] = INT32_MAX;
-    skip[q] = true;
-#pragma unroll
-    for (int k = 0; k < 3; ++k) xh[q][k] = xo[q][k] = X[q][k] = hi[q][k] = lo[q][k] = 0.f;
-    if (valid[q]) {
-      const float4 h4 = tgt32[tg[q] * 2], l4 = tgt32[tg[q] * 2 + 1];
-      xh[q][0] = h4.x; xh[q][1] = h4.y; xh[q][2] = h4.z;
-      xo[q][0] = l4.x; xo[q][1] = l4.y; xo[q][2] = l4.z;
-      sp[q] = skip_ptr[tg[q]];
-      nxt[q] = skip_idx[sp[q]];
-    }
-  }
-  int cur = -1;
+  __shared__ float4 sh[(PK ? 3 : 2) * kFarTile];
+  __shared__ float acc[6 * TT * kFarTile];     // per target: (hi, lo) of u_x, u_y, u_z
+  __shared__ int cursor[2 * TT * kFarTile];
+  const int tid = threadIdx.x;
   const int per = (n_tiles + gridDim.y - 1) / gridDim.y;
   const int t_lo = blockIdx.y * per, t_hi = min(n_tiles, t_lo + per);
+  const int64_t t0 = (int64_t)blockIdx.x * TT * kFarTile + tid;
+#pragma unroll
+  for (int q = 0; q < TT; ++q) {
+    const int64_t t = t0 + (int64_t)q * kFarTile;
+#pragma unroll
+    for (int c = 0; c < 6; ++c) acc[(6 * q + c) * kFarTile + tid] = 0.f;
+    const int sp = (t < N) ? skip_ptr[t] : 0;
+    cursor[(2 * q + 0) * kFarTile + tid] = sp;
+    cursor[(2 * q + 1) * kFarTile + tid] = (t < N) ? skip_idx[sp] : INT32_MAX;
+  }
+  float X[TT], Y[TT], Z[TT];
+  unsigned skipmask = (1u << TT) - 1u;
+  int cur = -1;
   for (int tl = t_lo; tl < t_hi; ++tl) {
     const int4 tile = tiles[tl];
     if (tile.x != cur) {
       cur = tile.x;
       const float4 ch = cen32[cur * 2], cl = cen32[cur * 2 + 1];
+      skipmask = 0u;
 #pragma unroll
       for (int q = 0; q < TT; ++q) {
-        if (valid[q]) {
-          while (nxt[q] < cur) nxt[q] = skip_idx[++sp[q]];
-          skip[q] = (nxt[q] == cur);
+        const int64_t t = t0 + (int64_t)q * kFarTile;
+        int sp = cursor[(2 * q + 0) * kFarTile + tid];
+        int nxt = cursor[(2 * q + 1) * kFarTile + tid];
+        while (nxt < cur) nxt = skip_idx[++sp];
+        cursor[(2 * q + 0) * kFarTile + tid] = sp;
+        cursor[(2 * q + 1) * kFarTile + tid] = nxt;
+        if (t >= N || nxt == cur) skipmask |= 1u << q;
+        float4 hi = make_float4(0.f, 0.f, 0.f, 0.f), lo = hi;
+        if (t < N) {
+          hi = tgt32[t * 2];
+          lo = tgt32[t * 2 + 1];
         }
-        X[q][0] = (xh[q][0] - ch.x) + (xo[q][0] - cl.x);
-        X[q][1] = (xh[q][1] - ch.y) + (xo[q][1] - cl.y);
-        X[q][2] = (xh[q][2] - ch.z) + (xo[q][2] - cl.z);
+        X[q] = (hi.x - ch.x) + (lo.x - cl.x);
+        Y[q] = (hi.y - ch.y) + (lo.y - cl.y);
+        Z[q] = (hi.z - ch.z) + (lo.z - cl.z);
       }
     }
-    bool all_skip = true;
-#pragma unroll
-    for (int q = 0; q < TT; ++q) all_skip = all_skip && skip[q];
-    if (__syncthreads_and(all_skip)) continue;
-    if (threadIdx.x < tile.z) {
-      sh[threadIdx.x * 2 + 0] = src32[(int64_t)(tile.y + threadIdx.x) * 2 + 0];
-      sh[threadIdx.x * 2 + 1] = src32[(int64_t)(tile.y + threadIdx.x) * 2 + 1];
+    const bool mine = skipmask != (1u << TT) - 1u;
+    if (!__syncthreads_or(mine)) continue;
+    if (tid < tile.z) {
+      const float4 A = src32[(int64_t)(tile.y + tid) * 2 + 0];
+      const float4 B = src32[(int64_t)(tile.y + tid) * 2 + 1];
+      if (PK) {
+        sh[tid * 3 + 0] = make_float4(-A.x, -A.x, -A.y, -A.y);
+        sh[tid * 3 + 1] = make_float4(-A.z, -A.z, A.w, A.w);
+        sh[tid * 3 + 2] = make_float4(B.x, B.x, B.y, B.y);
+      } else {
+        sh[tid * 2 + 0] = A;
+        sh[tid * 2 + 1] = B;
+      }
     }
     __syncthreads();
-    if (!all_skip) {
+    if (mine) {
       float p0[TT], p1[TT], p2[TT];
+      if constexpr (PK) {
+        constexpr int TP = TT / 2 > 0 ? TT / 2 : 1;
+        float2 Xp[TP], Yp[TP], Zp[TP], a0[TP], a1[TP], a2[TP];
 #pragma unroll
-      for (int q = 0; q < TT; ++q) p0[q] = p1[q] = p2[q] = 0.f;
-#pragma unroll 4
-      for (int j = 0; j < tile.z; ++j) {
-        const float4 A = sh[j * 2], B = sh[j * 2 + 1];
+        for (int k = 0; k < TP; ++k) {
+          Xp[k] = make_float2(X[2 * k], X[2 * k + 1]);
+          Yp[k] = make_float2(Y[2 * k], Y[2 * k + 1]);
+          Zp[k] = make_float2(Z[2 * k], Z[2 * k + 1]);
+          a0[k] = a1[k] = a2[k] = make_float2(0.f, 0.f);
+        }
+#pragma unroll 2
+        for (int j = 0; j < tile.z; ++j) {
+          const float4 A = sh[j * 3 + 0], B = sh[j * 3 + 1], Cc = sh[j * 3 + 2];
+          const float2 myx = make_float2(A.x, A.y), myy = make_float2(A.z, A.w), myz = make_float2(B.x, B.y);
+          const float2 fx = make_float2(B.z, B.w), fy = make_float2(Cc.x, Cc.y), fz = make_float2(Cc.z, Cc.w);
 #pragma unroll
-        for (int q = 0; q < TT; ++q) {
-          const float dx = X[q][0] - A.x, dy = X[q][1] - A.y, dz = X[q][2] - A.z;
-          const float ri = rsqrt_approx_f(fmaf(dz, dz, fmaf(dy, dy, dx * dx)));
-          const float rf = fmaf(dz, B.y, fmaf(dy, B.x, dx * A.w)) * ri * (ri * ri);
-          p0[q] = fmaf(A.w, ri, fmaf(rf, dx, p0[q]));
-          p1[q] = fmaf(B.x, ri, fmaf(rf, dy, p1[q]));
-          p2[q] = fmaf(B.y, ri, fmaf(rf, dz, p2[q]));
+          for (int k = 0; k < TP; ++k) {
+            const float2 dx = __fadd2_rn(Xp[k], myx), dy = __fadd2_rn(Yp[k], myy), dz = __fadd2_rn(Zp[k], myz);
+            const float2 r2 = __ffma2_rn(dz, dz, __ffma2_rn(dy, dy, __fmul2_rn(dx, dx)));
+            const float2 ri = make_float2(rsqrt_approx_f(r2.x), rsqrt_approx_f(r2.y));
+            const float2 rf = __ffma2_rn(fz, dz, __ffma2_rn(fy, dy, __fmul2_rn(fx, dx)));
+            const float2 sc = __fmul2_rn(__fmul2_rn(rf, ri), __fmul2_rn(ri, ri));
+            a0[k] = __ffma2_rn(fx, ri, __ffma2_rn(sc, dx, a0[k]));
+            a1[k] = __ffma2_rn(fy, ri, __ffma2_rn(sc, dy, a1[k]));
+            a2[k] = __ffma2_rn(fz, ri, __ffma2_rn(sc, dz, a2[k]));
+          }
+        }
+#pragma unroll
+        for (int k = 0; k < TP; ++k) {
+          p0[2 * k] = a0[k].x; p0[2 * k + 1] = a0[k].y;
+          p1[2 * k] = a1[k].x; p1[2 * k + 1] = a1[k].y;
+          p2[2 * k] = a2[k].x; p2[2 * k + 1] = a2[k].y;
+        }
+      } else {
+#pragma unroll
+        for (int q = 0; q < TT; ++q) p0[q] = p1[q] = p2[q] = 0.f;
+#pragma unroll 2
+        for (int j = 0; j < tile.z; ++j) {
+          const float4 A = sh[j * 2], B = sh[j * 2 + 1];
+#pragma unroll
+          for (int q = 0; q < TT; ++q) {
+            const float dx = X[q] - A.x, dy = Y[q] - A.y, dz = Z[q] - A.z;
+            const float ri = rsqrt_approx_f(fmaf(dz, dz, fmaf(dy, dy, dx * dx)));
+            const float rf = fmaf(dz, B.y, fmaf(dy, B.x, dx * A.w));
+            const float sc = (rf * ri) * (ri * ri);
+            p0[q] = fmaf(A.w, ri, fmaf(sc, dx, p0[q]));
+            p1[q] = fmaf(B.x, ri, fmaf(sc, dy, p1[q]));
+            p2[q] = fmaf(B.y, ri, fmaf(sc, dz, p2[q]));
+          }
         }
       }
 #pragma unroll
       for (int q = 0; q < TT; ++q) {
-        if (!skip[q]) {
-          float s, e;
-          two_sum_f(hi[q][0], p0[q], s, e);
-          hi[q][0] = s;
-          lo[q][0] += e;
-          two_sum_f(hi[q][1], p1[q], s, e);
-          hi[q][1] = s;
-          lo[q][1] += e;
-          two_sum_f(hi[q][2], p2[q], s, e);
-          hi[q][2] = s;
-          lo[q][2] += e;
+        if (!((skipmask >> q) & 1u)) {
+          const float pv[3] = {p0[q], p1[q], p2[q]};
+#pragma unroll
+          for (int c = 0; c < 3; ++c) {
+            float sum, err;
+            two_sum_f(acc[(6 * q + 2 * c) * kFarTile + tid], pv[c], sum, err);
+            acc[(6 * q + 2 * c) * kFarTile + tid] = sum;
+            acc[(6 * q + 2 * c + 1) * kFarTile + tid] += err;
+          }
         }
       }
     }
     __syncthreads();
   }
 #pragma unroll
-  for (int q = 0; q < TT; ++q)
-    if (valid[q])
-      for (int k = 0; k < 3; ++k) atomicAdd(u_out + tg[q] * 3 + k, ((double)hi[q][k] + (double)lo[q][k]) * kInv8Pi);
+  for (int q = 0; q < TT; ++q) {
+    const int64_t t = t0 + (int64_t)q * kFarTile;
+    if (t < N)
+      for (int c = 0; c < 3; ++c)
+        atomicAdd(u_out + t * 3 + c,
+                  ((double)acc[(6 * q + 2 * c) * kFarTile + tid] + (double)acc[(6 * q + 2 * c + 1) * kFarTile + tid]) *
+                      kInv8Pi);
+  }
+}
+
+template <int TT, bool PK>
+static void launch_stokes_far_tt(const DevGeom& d, const GeomHost& h, double* u, cudaStream_t st) {
+  const int nt = (int)h.tiles.size();
+  const int64_t tb = (h.N + (int64_t)kFarTile * TT - 1) / ((int64_t)kFarTile * TT);
+  const dim3 grid((unsigned)tb, (unsigned)far_split_count(tb, nt, h.far_splits));
+  stokes_far_mixed_kernel<TT, PK><<<grid, kFarTile, 0, st>>>(d.tiles, nt, d.st_src32, d.tgt32, d.cen32, d.skip_ptr,
+                                                             d.skip_idx, h.N, u);
 }
 
 int launch_stokes(sbio_geom* g, const double* f, double* u, cudaStream_t st) {
@@ -433,11 +492,16 @@ int launch_stokes(sbio_geom* g, const double* f, double* u, cudaStream_t st) {
     stokes_far_fp64_kernel<<<grid, kFarTile, 0, st>>>(d.tiles, nt, d.st_src64, d.xyz, d.parts, d.skip_ptr,
                                                       d.skip_idx, h.N, u);
   } else {
-    constexpr int TT = 2;
-    const int64_t tb = (h.N + kFarTile * TT - 1) / (kFarTile * TT);
-    const dim3 grid((unsigned)tb, (unsigned)far_split_count(tb, nt, h.far_splits));
-    stokes_far_mixed_kernel<TT><<<grid, kFarTile, 0, st>>>(d.tiles, nt, d.st_src32, d.tgt32, d.cen32, d.skip_ptr,
-                                                           d.skip_idx, h.N, u);
+    // the geometry's tuned far shape (targets per thread, packed if negative)
+    switch (h.far_tt) {
+      case 1: launch_stokes_far_tt<1, false>(d, h, u, st); break;
+      case 4: launch_stokes_far_tt<4, false>(d, h, u, st); break;
+      case 8: launch_stokes_far_tt<8, false>(d, h, u, st); break;
+      case -2: launch_stokes_far_tt<2, true>(d, h, u, st); break;
+      case -4: launch_stokes_far_tt<4, true>(d, h, u, st); break;
+      case -8: launch_stokes_far_tt<8, true>(d, h, u, st); break;
+      default: launch_stokes_far_tt<2, false>(d, h, u, st); break;
+    }
   }
   count_launch();
   SBIO_CUDA_TRY(cudaGetLastError());

@@ -126,27 +126,30 @@ def test_overlap_matches_in_order(S, poly200):
 def test_autotune_keeps_results(S, lattice):
     s, c, g, og, O = lattice
     S.sbio_geom_set_precision(g.h, S.SBIO_MIXED)
-    tt, sp, ms = S.sbio_geom_autotune(g.h)
-    assert tt in (1, 2, 4) and sp >= 1 and ms > 0
-    Sm, Dm = gpu_apply(S, g, c[0], c[1], 7, S.SBIO_MIXED)
-    S64, D64 = gpu_apply(S, g, c[0], c[1], 7, S.SBIO_FP64)
-    S.sbio_geom_set_launch_shape(g.h, 2, 0)
-    assert OL.normwise_rel_err(Sm, S64) < TOLMIX and OL.normwise_rel_err(Dm, D64) < TOLMIX
+    try:
+        tt, sp, ms = S.sbio_geom_autotune(g.h)
+        assert tt in (1, 2, 4, 8, -2, -4, -8) and sp >= 1 and ms > 0
+        Sm, Dm = gpu_apply(S, g, c[0], c[1], 7, S.SBIO_MIXED)
+        S64, D64 = gpu_apply(S, g, c[0], c[1], 7, S.SBIO_FP64)
+        assert OL.normwise_rel_err(Sm, S64) < TOLMIX and OL.normwise_rel_err(Dm, D64) < TOLMIX
+    finally:
+        S.sbio_geom_set_launch_shape(g.h, 2, 0)
+        S.sbio_geom_set_precision(g.h, S.SBIO_FP64)
 
 
 def test_single_operators(S, lattice):
     s, c, g, og, O = lattice
     Sr, _ = O.apply(c[0], None, "method")
     _, Dr = O.apply(None, c[1], "method")
-    Sg, _ = gpu_apply(S, g, c[0], None)
-    _, Dg = gpu_apply(S, g, None, c[1])
+    Sg, _ = gpu_apply(S, g, c[0], None, 7, S.SBIO_FP64)
+    _, Dg = gpu_apply(S, g, None, c[1], 7, S.SBIO_FP64)
     assert OL.normwise_rel_err(Sg, Sr) < TOL64
     assert OL.normwise_rel_err(Dg, Dr) < TOL64
 
 
 def test_host_memory_entry_point(S, lattice):
     s, c, g, og, O = lattice
-    Sd, Dd = gpu_apply(S, g, c[0], c[1])
+    Sd, Dd = gpu_apply(S, g, c[0], c[1], 7, S.SBIO_FP64)
     Sh = np.zeros(g.N)
     Dh = np.zeros(g.N)
     S.sbio_apply_laplace_host(g.h, np.ascontiguousarray(c[0]), np.ascontiguousarray(c[1]), Sh, Dh)
