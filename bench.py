@@ -247,6 +247,7 @@ def run_ours(args, ws, rank, lrank):
     else:
         tune = S.sbio_geom_autotune(geom.h)
     tuning = S.sbio_geom_get_tuning(geom.h)
+    setup_ms = S.sbio_geom_setup_times(geom.h)
     N = geom.N
     sig = torch.from_numpy(coef[0]).to(dev)
     mu = torch.from_numpy(coef[1]).to(dev)
@@ -371,6 +372,8 @@ def run_ours(args, ws, rank, lrank):
                 "d2h_bytes_per_step": int(hS.nbytes + hD.nbytes)},
         "gpu_launches": int(launches),
         "clocks": clk,
+        "geometry_setup_ms": {"host_nodes": setup_ms[0], "host_near_sets": setup_ms[1],
+                              "device_tables_upload": setup_ms[2]},
     }
     line.update(extra)
     geom.close()
@@ -410,7 +413,8 @@ def run_stokes100(args, ws, rank, lrank):
     f = I.config_coefficients(susp, 0, ndens=3).transpose(1, 0, 2).copy()
     ctx = S.sbio_ctx_create(lrank, 0)
     g = S.Geometry(ctx, susp, precision=S.SBIO_MIXED)
-    tune = S.sbio_geom_autotune(g.h)
+    tune = S.sbio_geom_autotune_stokes(g.h)
+    near_cap = S.sbio_geom_get_stokes_tuning(g.h)["near_ctas_per_sm"]
     fd = torch.from_numpy(f).cuda()
     u = torch.empty((g.N, 3), dtype=torch.float64, device="cuda")
     st = torch.cuda.current_stream()
@@ -423,6 +427,19 @@ def run_stokes100(args, ws, rank, lrank):
         flush.zero_()
         ms.append(_event_time(st, lambda: S.sbio_apply_stokes_sl(g.h, fd, u)))
     launches = S.sbio_launch_count() - l0
+    # end to end through the host entry point: pinned host forces in, velocities out
+    fh = torch.from_numpy(f).pin_memory()
+    uh = torch.empty((g.N, 3), dtype=torch.float64).pin_memory()
+    fh_np, uh_np = fh.numpy(), uh.numpy()
+    for _ in range(2):
+        S.sbio_apply_stokes_sl_host(g.h, fh_np, uh_np)
+    e2e = []
+    for _ in range(args.steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        S.sbio_apply_stokes_sl_host(g.h, fh_np, uh_np)
+        e2e.append((time.perf_counter() - t0) * 1e3)
     S.sbio_geom_enable_timing(g.h, True)        # phase-timed pass, phases in order
     ph = []
     for _ in range(min(args.steps, 10)):
@@ -443,7 +460,10 @@ def run_stokes100(args, ws, rank, lrank):
             "dtype": "f32+f64", "data": "synthetic",
             "config": {"workload": "stokes100_p12", "M": susp.M, "p": susp.p, "targets": g.N,
                        "near_pairs": g.n_near, "far_pairs_per_apply": g.n_far,
-                       "far_launch": {"targets_per_thread": tune[0], "source_splits": tune[1]}},
+                       "far_launch": {"targets_per_thread": tune[0], "source_splits": tune[1]},
+                       "near_ctas_per_sm_overlapped": near_cap, "l2": "flushed (256 MiB write) before each step"},
+            "e2e": {"value": 1e3 / statistics.mean(e2e), "unit": "applies/s", "h2d_bytes_per_step": int(fh.nbytes),
+                    "d2h_bytes_per_step": int(uh.nbytes)},
             "phase_ms": {"prep_and_self": statistics.mean(x[0] for x in ph), "near": statistics.mean(x[1] for x in ph),
                          "far": far_ms},
             "roofline": {"kernel": "stokes_far_mixed_kernel", "bound": "alu", "achieved": ach,

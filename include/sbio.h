@@ -143,6 +143,10 @@ int sbio_geom_destroy(sbio_geom* g);
 int sbio_geom_info(const sbio_geom* g, int64_t* n_targets, int64_t* n_near_pairs,
                    int64_t* n_far_pairs, size_t* device_bytes);
 
+/* Wall-clock milliseconds of the geometry's creation: host nodes and
+ * multipliers, host near sets, device tables and upload (any may be NULL). */
+int sbio_geom_setup_times(const sbio_geom* g, double* host_ms, double* near_ms, double* device_ms);
+
 /* Copy node data to host arrays (any may be NULL): global positions (N x 3),
  * outward unit normals (N x 3), quadrature weights (N). */
 int sbio_geom_nodes(const sbio_geom* g, double* xyz, double* normal, double* weight);
@@ -224,6 +228,25 @@ int sbio_apply_laplace_host(sbio_geom* g, const double* sigma_tilde_host, const 
  *          coefficients of the three global Cartesian components of f.
  * u_out: device, N x 3 FP64 (row t = velocity at node t).  Asynchronous. */
 int sbio_apply_stokes_sl(sbio_geom* g, const double* f_tilde, double* u_out, void* stream);
+
+/* End-to-end Stokes apply from and to HOST memory (f_tilde_host M x 3 x
+ * (p+1)^2, u_host N x 3): copies in through library-owned device buffers on
+ * `stream`, applies, copies out and synchronises `stream` before returning. */
+int sbio_apply_stokes_sl_host(sbio_geom* g, const double* f_tilde_host, double* u_host, void* stream);
+
+/* Launch settings of the Stokes kernels, kept apart from the Laplace ones
+ * (the Stokeslet far kernel carries three accumulators per target and its
+ * near field is the larger share of an apply): far_tt and far_splits as in
+ * sbio_geom_set_launch_shape, near_ctas_per_sm as in sbio_geom_set_near_cap
+ * (default 2, 0, 0).  SBIO_EINVAL on values outside those sets. */
+int sbio_geom_set_stokes_tuning(sbio_geom* g, int32_t far_tt, int32_t far_splits, int32_t near_ctas_per_sm);
+int sbio_geom_get_stokes_tuning(const sbio_geom* g, int32_t* far_tt, int32_t* far_splits, int32_t* near_ctas_per_sm);
+
+/* Autotuner of the Stokes kernels: as sbio_geom_autotune, timing the
+ * Stokeslet far kernel and whole Stokes applies (zero forces through the
+ * geometry's own workspaces).  SBIO_ENOTSUP for p > 20.  Synchronises
+ * `stream`. */
+int sbio_geom_autotune_stokes(sbio_geom* g, void* stream, int32_t* far_tt, int32_t* far_splits, double* far_ms);
 
 /* ---- batched apply over many suspensions ------------------------------
  * A batch groups resident geometries (any mix of M and p, all in SBIO_MIXED

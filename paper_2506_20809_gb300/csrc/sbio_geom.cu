@@ -2,6 +2,7 @@
 // host FP64 set-up (Sec. 2.1-2.2 geometry, Theorems 1-2 multipliers, Sec. 4.1
 // near sets) and the upload of everything an apply reads.
 #include <algorithm>
+#include <chrono>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -541,8 +542,8 @@ static int build_device(sbio_geom* g) {
   if ((rc = dev_alloc(g, (void**)&d.src32, (size_t)N * 2 * sizeof(float4), "fp32 sources"))) return rc;
   if ((rc = dev_alloc(g, (void**)&d.alpha, (size_t)M * nc * sizeof(double), "near S coefficients"))) return rc;
   if ((rc = dev_alloc(g, (void**)&d.beta, (size_t)M * nc * sizeof(double), "near D coefficients"))) return rc;
-  if ((rc = dev_alloc(g, (void**)&d.host_in, (size_t)2 * M * nc * sizeof(double), "host staging"))) return rc;
-  if ((rc = dev_alloc(g, (void**)&d.host_out, (size_t)2 * N * sizeof(double), "host staging"))) return rc;
+  if ((rc = dev_alloc(g, (void**)&d.host_in, (size_t)3 * M * nc * sizeof(double), "host staging"))) return rc;
+  if ((rc = dev_alloc(g, (void**)&d.host_out, (size_t)3 * N * sizeof(double), "host staging"))) return rc;
   SBIO_CUDA_TRY(cudaStreamSynchronize(g->setup_stream));
   return SBIO_OK;
 }
@@ -584,9 +585,17 @@ static int geom_create_impl(sbio_ctx* ctx, const sbio_spheroid* sph, int32_t M, 
   g->ctx = ctx;
   g->setup_stream = stream;
   g->async_alloc = async_alloc;
+  using clk = std::chrono::steady_clock;
+  const auto t0 = clk::now();
   rc = build_host(g->h, sph, M, opts);
+  const auto t1 = clk::now();
   if (!rc) rc = build_near(g->h);
+  const auto t2 = clk::now();
   if (!rc) rc = build_device(g);
+  const auto t3 = clk::now();
+  g->setup_ms[0] = std::chrono::duration<double, std::milli>(t1 - t0).count();
+  g->setup_ms[1] = std::chrono::duration<double, std::milli>(t2 - t1).count();
+  g->setup_ms[2] = std::chrono::duration<double, std::milli>(t3 - t2).count();
   if (rc) {
     free_geom(g);
     delete g;
@@ -721,6 +730,14 @@ int sbio_geom_phase_times(sbio_geom* g, double* ms_synth, double* ms_near, doubl
   if (ms_synth) *ms_synth = t[0];
   if (ms_near) *ms_near = t[1];
   if (ms_far) *ms_far = t[2];
+  return SBIO_OK;
+}
+
+int sbio_geom_setup_times(const sbio_geom* g, double* host_ms, double* near_ms, double* device_ms) {
+  if (!g) return set_error(SBIO_EINVAL, "null geometry");
+  if (host_ms) *host_ms = g->setup_ms[0];
+  if (near_ms) *near_ms = g->setup_ms[1];
+  if (device_ms) *device_ms = g->setup_ms[2];
   return SBIO_OK;
 }
 

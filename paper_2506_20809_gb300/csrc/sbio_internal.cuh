@@ -85,6 +85,10 @@ struct GeomHost {
   int far_splits = 0;
   int near_block = 128;                      // threads per CTA of the near kernels
   int near_ctas_per_sm = 2;                  // near CTAs per SM while overlapping with the far field (0 = no cap)
+  // the same three settings for the Stokes single layer (its own kernels)
+  int st_far_tt = 2;
+  int st_far_splits = 0;
+  int st_near_ctas_per_sm = 0;
 };
 
 }  // namespace sbio
@@ -107,6 +111,7 @@ struct sbio_geom {
   // near/far overlap: the FP64 near kernels run on a high-priority stream
   // forked from the caller's stream, beside the FP32 far kernel
   bool overlap = true;
+  double setup_ms[3] = {0.0, 0.0, 0.0};   // host geometry, near sets, device tables + upload
   cudaStream_t near_stream = nullptr;
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
 };
@@ -175,6 +180,22 @@ int launch_synth(sbio_geom* g, const double* sigma, const double* mu, double* S,
                  cudaStream_t st);
 int launch_near(sbio_geom* g, double* S, double* D, cudaStream_t st);
 int launch_stokes(sbio_geom* g, const double* f, double* u, cudaStream_t st);
+int launch_stokes_far(sbio_geom* g, double* u, cudaStream_t st);
+
+// Launch-shape search shared by the Laplace and Stokes autotuners: times
+// far(g, out, st) for every targets-per-thread form and a ladder of source
+// splits (writing *tt / *splits before each launch), keeps the fastest, then,
+// if whole(...) is given and the near field overlaps the far field, times
+// whole applies for a few near CTA caps written to *cap.  `out` is the
+// launch's output workspace.
+struct TuneOps {
+  int (*far)(sbio_geom* g, double* out, cudaStream_t st);
+  int (*whole)(sbio_geom* g, double* out, cudaStream_t st);
+  int* tt;
+  int* splits;
+  int* cap;
+};
+int tune_launch_shape(sbio_geom* g, const TuneOps& ops, double* out, cudaStream_t st, double* best_far_ms);
 
 // source splits of the far-field grid (gridDim.y) for `target_blocks` target
 // CTAs; `requested` > 0 forces the count

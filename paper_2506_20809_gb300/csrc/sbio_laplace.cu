@@ -561,6 +561,79 @@ int launch_laplace(sbio_geom* g, const double* sigma, const double* mu, double* 
   return SBIO_OK;
 }
 
+int tune_launch_shape(sbio_geom* g, const TuneOps& ops, double* out, cudaStream_t st, double* best_far_ms) {
+  GeomHost& h = g->h;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  SBIO_CUDA_TRY(cudaEventCreate(&e0));
+  if (cudaEventCreate(&e1) != cudaSuccess) {
+    cudaEventDestroy(e0);
+    return set_error(SBIO_ECUDA, "event create failed");
+  }
+  // median of three event-timed launches after one warm-up
+  auto time3 = [&](int (*fn)(sbio_geom*, double*, cudaStream_t), float* ms) -> int {
+    int r = fn(g, out, st);
+    float t[3] = {0.f, 0.f, 0.f};
+    for (int k = 0; k < 3 && !r; ++k) {
+      cudaEventRecord(e0, st);
+      r = fn(g, out, st);
+      cudaEventRecord(e1, st);
+      if (cudaEventSynchronize(e1) != cudaSuccess) r = set_error(SBIO_ECUDA, "autotune timing failed");
+      cudaEventElapsedTime(&t[k], e0, e1);
+    }
+    *ms = std::max(std::min(t[0], t[1]), std::min(std::max(t[0], t[1]), t[2]));
+    return r;
+  };
+  const int nt = (int)h.tiles.size();
+  double best = 1e300;
+  int best_tt = *ops.tt, best_sp = *ops.splits;
+  const int tts[7] = {1, 2, 4, 8, -2, -4, -8};
+  int rc = SBIO_OK;
+  for (int a = 0; a < (h.precision == SBIO_FP64 ? 1 : 7) && !rc; ++a) {
+    const int tt = (h.precision == SBIO_FP64) ? 1 : tts[a];
+    const int att = tt < 0 ? -tt : tt;
+    const int64_t tb = (h.N + (int64_t)kFarTile * att - 1) / ((int64_t)kFarTile * att);
+    const int base = far_split_count(tb, nt, 0);
+    const int cands[6] = {base > 1 ? base / 2 : 1, base, 2 * base, 4 * base, 8 * base, 16 * base};
+    for (int b = 0; b < 6 && !rc; ++b) {
+      if (b > 0 && cands[b - 1] >= nt) break;
+      *ops.tt = tt;
+      *ops.splits = cands[b] < nt ? cands[b] : nt;
+      float med = 0.f;
+      rc = time3(ops.far, &med);
+      if (!rc && med < best) {
+        best = med;
+        best_tt = tt;
+        best_sp = *ops.splits;
+      }
+    }
+  }
+  *ops.tt = best_tt;
+  *ops.splits = best_sp;
+  // near CTAs per SM while the near field overlaps the far field: whole applies
+  if (!rc && ops.whole && g->overlap && g->near_stream && !g->timing && !h.pair_t.empty()) {
+    const int caps[4] = {1, 2, 4, 0};
+    float best_apply = 1e30f;
+    int best_cap = *ops.cap;
+    for (int c = 0; c < 4 && !rc; ++c) {
+      *ops.cap = caps[c];
+      float m = 0.f;
+      rc = time3(ops.whole, &m);
+      if (!rc && m < best_apply) {
+        best_apply = m;
+        best_cap = caps[c];
+      }
+    }
+    *ops.cap = best_cap;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (rc) return rc;
+  SBIO_CUDA_TRY(cudaGetLastError());
+  *best_far_ms = best;
+  return SBIO_OK;
+}
+
+
 }  // namespace sbio
 
 using namespace sbio;
@@ -648,74 +721,23 @@ int sbio_geom_autotune(sbio_geom* g, void* stream, int32_t* far_tt, int32_t* far
   SBIO_CUDA_TRY(cudaMemsetAsync(d.host_in, 0, 2 * nc * sizeof(double), st));
   int rc = launch_laplace(g, d.host_in, d.host_in + nc, d.host_out, d.host_out + h.N, SBIO_PART_SELF, st);
   if (rc) return rc;
-  cudaEvent_t e0, e1;
-  SBIO_CUDA_TRY(cudaEventCreate(&e0));
-  SBIO_CUDA_TRY(cudaEventCreate(&e1));
-  const int nt = (int)h.tiles.size();
-  const int saved_tt = h.far_tt, saved_sp = h.far_splits;
-  double best = 1e300;
-  int best_tt = saved_tt, best_sp = saved_sp;
-  const int tts[7] = {1, 2, 4, 8, -2, -4, -8};
-  for (int a = 0; a < (h.precision == SBIO_FP64 ? 1 : 7); ++a) {
-    const int tt = (h.precision == SBIO_FP64) ? 1 : tts[a];
-    const int att = tt < 0 ? -tt : tt;
-    const int64_t tb = (h.N + (int64_t)kFarTile * att - 1) / ((int64_t)kFarTile * att);
-    const int base = far_split_count(tb, nt, 0);
-    const int cands[6] = {base > 1 ? base / 2 : 1, base, 2 * base, 4 * base, 8 * base, 16 * base};
-    for (int b = 0; b < 6; ++b) {
-      if (b > 0 && cands[b - 1] >= nt) break;
-      h.far_tt = tt;
-      h.far_splits = cands[b] < nt ? cands[b] : nt;
-      launch_far(g, d.host_out, d.host_out + h.N, st);   // warm-up
-      float tms[3];
-      for (int r = 0; r < 3; ++r) {
-        cudaEventRecord(e0, st);
-        launch_far(g, d.host_out, d.host_out + h.N, st);
-        cudaEventRecord(e1, st);
-        SBIO_CUDA_TRY(cudaEventSynchronize(e1));
-        cudaEventElapsedTime(&tms[r], e0, e1);
-      }
-      const float med = std::max(std::min(tms[0], tms[1]), std::min(std::max(tms[0], tms[1]), tms[2]));
-      if (med < best) {
-        best = med;
-        best_tt = tt;
-        best_sp = h.far_splits;
-      }
-    }
-  }
-  h.far_tt = best_tt;
-  h.far_splits = best_sp;
-  // near CTAs per SM while the near field overlaps the far field: time whole applies
-  if (g->overlap && g->near_stream && !g->timing && !h.pair_t.empty()) {
-    const int caps[4] = {1, 2, 4, 0};
-    float best_apply = 1e30f;
-    int best_cap = h.near_ctas_per_sm;
-    for (int c = 0; c < 4; ++c) {
-      h.near_ctas_per_sm = caps[c];
-      rc = launch_laplace(g, d.host_in, d.host_in + nc, d.host_out, d.host_out + h.N, SBIO_PART_ALL, st);
-      if (rc) break;
-      float tms[2];
-      for (int r = 0; r < 2 && !rc; ++r) {
-        cudaEventRecord(e0, st);
-        rc = launch_laplace(g, d.host_in, d.host_in + nc, d.host_out, d.host_out + h.N, SBIO_PART_ALL, st);
-        cudaEventRecord(e1, st);
-        SBIO_CUDA_TRY(cudaEventSynchronize(e1));
-        cudaEventElapsedTime(&tms[r], e0, e1);
-      }
-      const float m = std::min(tms[0], tms[1]);
-      if (m < best_apply) {
-        best_apply = m;
-        best_cap = caps[c];
-      }
-    }
-    h.near_ctas_per_sm = best_cap;
-    if (rc) return rc;
-  }
-  cudaEventDestroy(e0);
-  cudaEventDestroy(e1);
-  SBIO_CUDA_TRY(cudaGetLastError());
-  if (far_tt) *far_tt = best_tt;
-  if (far_splits) *far_splits = best_sp;
+  TuneOps ops;
+  ops.far = [](sbio_geom* gg, double* out, cudaStream_t s) {
+    launch_far(gg, out, out + gg->h.N, s);
+    return SBIO_OK;
+  };
+  ops.whole = [](sbio_geom* gg, double* out, cudaStream_t s) {
+    const size_t n = (size_t)(gg->h.p + 1) * (gg->h.p + 1) * gg->h.M;
+    return launch_laplace(gg, gg->d.host_in, gg->d.host_in + n, out, out + gg->h.N, SBIO_PART_ALL, s);
+  };
+  ops.tt = &h.far_tt;
+  ops.splits = &h.far_splits;
+  ops.cap = &h.near_ctas_per_sm;
+  double best = 0.0;
+  rc = tune_launch_shape(g, ops, d.host_out, st, &best);
+  if (rc) return rc;
+  if (far_tt) *far_tt = h.far_tt;
+  if (far_splits) *far_splits = h.far_splits;
   if (far_ms) *far_ms = best;
   return SBIO_OK;
 }
@@ -725,6 +747,68 @@ int sbio_apply_stokes_sl(sbio_geom* g, const double* f_tilde, double* u_out, voi
   if (!g || !f_tilde || !u_out) return set_error(SBIO_EINVAL, "null argument");
   SBIO_CUDA_TRY(cudaSetDevice(g->ctx->device));
   return launch_stokes(g, f_tilde, u_out, (cudaStream_t)stream);
+}
+
+int sbio_apply_stokes_sl_host(sbio_geom* g, const double* f_host, double* u_host, void* stream) {
+  clear_error();
+  if (!g || !f_host || !u_host) return set_error(SBIO_EINVAL, "null argument");
+  SBIO_CUDA_TRY(cudaSetDevice(g->ctx->device));
+  cudaStream_t st = (cudaStream_t)stream;
+  const size_t nc3 = (size_t)3 * (g->h.p + 1) * (g->h.p + 1) * g->h.M;
+  const size_t n3 = (size_t)3 * g->h.N;
+  SBIO_CUDA_TRY(cudaMemcpyAsync(g->d.host_in, f_host, nc3 * sizeof(double), cudaMemcpyHostToDevice, st));
+  int rc = launch_stokes(g, g->d.host_in, g->d.host_out, st);
+  if (rc) return rc;
+  SBIO_CUDA_TRY(cudaMemcpyAsync(u_host, g->d.host_out, n3 * sizeof(double), cudaMemcpyDeviceToHost, st));
+  SBIO_CUDA_TRY(cudaStreamSynchronize(st));
+  return SBIO_OK;
+}
+
+int sbio_geom_set_stokes_tuning(sbio_geom* g, int32_t far_tt, int32_t far_splits, int32_t near_ctas_per_sm) {
+  clear_error();
+  if (!g) return set_error(SBIO_EINVAL, "null geometry");
+  if (far_tt != 1 && far_tt != 2 && far_tt != 4 && far_tt != 8 && far_tt != -2 && far_tt != -4 && far_tt != -8)
+    return set_error(SBIO_EINVAL, "far_tt must be 1, 2, 4, 8 or -2, -4, -8 (packed)");
+  if (far_splits < 0 || near_ctas_per_sm < 0) return set_error(SBIO_EINVAL, "far_splits and near cap must be >= 0");
+  g->h.st_far_tt = far_tt;
+  g->h.st_far_splits = far_splits;
+  g->h.st_near_ctas_per_sm = near_ctas_per_sm;
+  return SBIO_OK;
+}
+
+int sbio_geom_get_stokes_tuning(const sbio_geom* g, int32_t* far_tt, int32_t* far_splits, int32_t* near_ctas_per_sm) {
+  if (!g) return set_error(SBIO_EINVAL, "null geometry");
+  if (far_tt) *far_tt = g->h.st_far_tt;
+  if (far_splits) *far_splits = g->h.st_far_splits;
+  if (near_ctas_per_sm) *near_ctas_per_sm = g->h.st_near_ctas_per_sm;
+  return SBIO_OK;
+}
+
+int sbio_geom_autotune_stokes(sbio_geom* g, void* stream, int32_t* far_tt, int32_t* far_splits, double* far_ms) {
+  clear_error();
+  if (!g) return set_error(SBIO_EINVAL, "null geometry");
+  SBIO_CUDA_TRY(cudaSetDevice(g->ctx->device));
+  cudaStream_t st = (cudaStream_t)stream;
+  GeomHost& h = g->h;
+  DevGeom& d = g->d;
+  const size_t nc3 = (size_t)3 * (h.p + 1) * (h.p + 1) * h.M;
+  // zero forces: one whole apply writes finite Stokeslet sources for the far timings
+  SBIO_CUDA_TRY(cudaMemsetAsync(d.host_in, 0, nc3 * sizeof(double), st));
+  int rc = launch_stokes(g, d.host_in, d.host_out, st);
+  if (rc) return rc;
+  TuneOps ops;
+  ops.far = [](sbio_geom* gg, double* out, cudaStream_t s) { return launch_stokes_far(gg, out, s); };
+  ops.whole = [](sbio_geom* gg, double* out, cudaStream_t s) { return launch_stokes(gg, gg->d.host_in, out, s); };
+  ops.tt = &h.st_far_tt;
+  ops.splits = &h.st_far_splits;
+  ops.cap = &h.st_near_ctas_per_sm;
+  double best = 0.0;
+  rc = tune_launch_shape(g, ops, d.host_out, st, &best);
+  if (rc) return rc;
+  if (far_tt) *far_tt = h.st_far_tt;
+  if (far_splits) *far_splits = h.st_far_splits;
+  if (far_ms) *far_ms = best;
+  return SBIO_OK;
 }
 
 }  // extern "C"

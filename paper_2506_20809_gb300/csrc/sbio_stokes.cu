@@ -436,9 +436,37 @@ template <int TT, bool PK>
 static void launch_stokes_far_tt(const DevGeom& d, const GeomHost& h, double* u, cudaStream_t st) {
   const int nt = (int)h.tiles.size();
   const int64_t tb = (h.N + (int64_t)kFarTile * TT - 1) / ((int64_t)kFarTile * TT);
-  const dim3 grid((unsigned)tb, (unsigned)far_split_count(tb, nt, h.far_splits));
+  const dim3 grid((unsigned)tb, (unsigned)far_split_count(tb, nt, h.st_far_splits));
   stokes_far_mixed_kernel<TT, PK><<<grid, kFarTile, 0, st>>>(d.tiles, nt, d.st_src32, d.tgt32, d.cen32, d.skip_ptr,
                                                              d.skip_idx, h.N, u);
+}
+
+// The Stokeslet far field alone (sources written by the prep kernel of the
+// same or an earlier apply), in the geometry's precision and Stokes launch shape.
+int launch_stokes_far(sbio_geom* g, double* u, cudaStream_t st) {
+  const GeomHost& h = g->h;
+  const DevGeom& d = g->d;
+  const int nt = (int)h.tiles.size();
+  if (h.precision == SBIO_FP64) {
+    const int64_t tb = (h.N + kFarTile - 1) / kFarTile;
+    const dim3 grid((unsigned)tb, (unsigned)far_split_count(tb, nt, h.st_far_splits));
+    stokes_far_fp64_kernel<<<grid, kFarTile, 0, st>>>(d.tiles, nt, d.st_src64, d.xyz, d.parts, d.skip_ptr,
+                                                      d.skip_idx, h.N, u);
+  } else {
+    // targets per thread, packed f32x2 form if negative
+    switch (h.st_far_tt) {
+      case 1: launch_stokes_far_tt<1, false>(d, h, u, st); break;
+      case 4: launch_stokes_far_tt<4, false>(d, h, u, st); break;
+      case 8: launch_stokes_far_tt<8, false>(d, h, u, st); break;
+      case -2: launch_stokes_far_tt<2, true>(d, h, u, st); break;
+      case -4: launch_stokes_far_tt<4, true>(d, h, u, st); break;
+      case -8: launch_stokes_far_tt<8, true>(d, h, u, st); break;
+      default: launch_stokes_far_tt<2, false>(d, h, u, st); break;
+    }
+  }
+  count_launch();
+  SBIO_CUDA_TRY(cudaGetLastError());
+  return SBIO_OK;
 }
 
 int launch_stokes(sbio_geom* g, const double* f, double* u, cudaStream_t st) {
@@ -475,7 +503,7 @@ int launch_stokes(sbio_geom* g, const double* f, double* u, cudaStream_t st) {
   if (fork) {
     SBIO_CUDA_TRY(cudaEventRecord(g->ev_fork, st));
     SBIO_CUDA_TRY(cudaStreamWaitEvent(g->near_stream, g->ev_fork, 0));
-    g->d.near_grid_cap = h.near_ctas_per_sm > 0 ? h.near_ctas_per_sm * sm_count() : 0;
+    g->d.near_grid_cap = h.st_near_ctas_per_sm > 0 ? h.st_near_ctas_per_sm * sm_count() : 0;
     nl(g->d, h.n_pairs_prolate, (int64_t)h.pair_t.size(), d.inv, u, g->near_stream);
     g->d.near_grid_cap = 0;
     SBIO_CUDA_TRY(cudaGetLastError());
@@ -485,26 +513,8 @@ int launch_stokes(sbio_geom* g, const double* f, double* u, cudaStream_t st) {
     SBIO_CUDA_TRY(cudaGetLastError());
   }
   phase_mark(g, 2, st);
-  const int nt = (int)h.tiles.size();
-  if (h.precision == SBIO_FP64) {
-    const int64_t tb = (h.N + kFarTile - 1) / kFarTile;
-    const dim3 grid((unsigned)tb, (unsigned)far_split_count(tb, nt, h.far_splits));
-    stokes_far_fp64_kernel<<<grid, kFarTile, 0, st>>>(d.tiles, nt, d.st_src64, d.xyz, d.parts, d.skip_ptr,
-                                                      d.skip_idx, h.N, u);
-  } else {
-    // the geometry's tuned far shape (targets per thread, packed if negative)
-    switch (h.far_tt) {
-      case 1: launch_stokes_far_tt<1, false>(d, h, u, st); break;
-      case 4: launch_stokes_far_tt<4, false>(d, h, u, st); break;
-      case 8: launch_stokes_far_tt<8, false>(d, h, u, st); break;
-      case -2: launch_stokes_far_tt<2, true>(d, h, u, st); break;
-      case -4: launch_stokes_far_tt<4, true>(d, h, u, st); break;
-      case -8: launch_stokes_far_tt<8, true>(d, h, u, st); break;
-      default: launch_stokes_far_tt<2, false>(d, h, u, st); break;
-    }
-  }
-  count_launch();
-  SBIO_CUDA_TRY(cudaGetLastError());
+  int rc = launch_stokes_far(g, u, st);
+  if (rc) return rc;
   if (fork) SBIO_CUDA_TRY(cudaStreamWaitEvent(st, g->ev_join, 0));
   phase_mark(g, 3, st);
   return SBIO_OK;

@@ -82,6 +82,8 @@ _SIGS = {
     "sbio_geom_info": (C.c_int, [_vp, C.POINTER(C.c_int64), C.POINTER(C.c_int64), C.POINTER(C.c_int64),
                                  C.POINTER(C.c_size_t)]),
     "sbio_geom_nodes": (C.c_int, [_vp, _vp, _vp, _vp]),
+    "sbio_geom_setup_times": (C.c_int, [_vp, C.POINTER(C.c_double), C.POINTER(C.c_double),
+                                        C.POINTER(C.c_double)]),
     "sbio_geom_near_pairs": (C.c_int, [_vp, _vp, _vp]),
     "sbio_geom_set_precision": (C.c_int, [_vp, C.c_int32]),
     "sbio_geom_enable_timing": (C.c_int, [_vp, C.c_int32]),
@@ -97,6 +99,12 @@ _SIGS = {
     "sbio_apply_laplace_parts": (C.c_int, [_vp, _vp, _vp, _vp, _vp, C.c_uint32, _vp]),
     "sbio_apply_laplace_host": (C.c_int, [_vp, _vp, _vp, _vp, _vp, _vp]),
     "sbio_apply_stokes_sl": (C.c_int, [_vp, _vp, _vp, _vp]),
+    "sbio_apply_stokes_sl_host": (C.c_int, [_vp, _vp, _vp, _vp]),
+    "sbio_geom_set_stokes_tuning": (C.c_int, [_vp, C.c_int32, C.c_int32, C.c_int32]),
+    "sbio_geom_get_stokes_tuning": (C.c_int, [_vp, C.POINTER(C.c_int32), C.POINTER(C.c_int32),
+                                              C.POINTER(C.c_int32)]),
+    "sbio_geom_autotune_stokes": (C.c_int, [_vp, _vp, C.POINTER(C.c_int32), C.POINTER(C.c_int32),
+                                            C.POINTER(C.c_double)]),
     "sbio_batch_create": (C.c_int, [_vp, C.POINTER(_vp), C.c_int32, C.POINTER(_vp)]),
     "sbio_batch_destroy": (C.c_int, [_vp]),
     "sbio_batch_info": (C.c_int, [_vp, C.POINTER(C.c_int64), C.POINTER(C.c_int64), C.POINTER(C.c_int32),
@@ -211,6 +219,13 @@ def sbio_geom_info(g):
     return {"n_targets": nt.value, "n_near_pairs": nn.value, "n_far_pairs": nf.value, "device_bytes": b.value}
 
 
+def sbio_geom_setup_times(g):
+    """(host nodes/multipliers, near sets, device tables + upload) in ms."""
+    a, b, c = C.c_double(), C.c_double(), C.c_double()
+    _check(_lib.sbio_geom_setup_times(g, C.byref(a), C.byref(b), C.byref(c)))
+    return a.value, b.value, c.value
+
+
 def sbio_geom_nodes(g):
     n = sbio_geom_info(g)["n_targets"]
     xyz = np.zeros((n, 3))
@@ -288,6 +303,30 @@ def sbio_apply_laplace_host(g, sigma_tilde, mu_hat, S_out, D_out, stream=None):
 
 def sbio_apply_stokes_sl(g, f_tilde, u_out, stream=None):
     _check(_lib.sbio_apply_stokes_sl(g, _ptr(f_tilde), _ptr(u_out), _stream(stream)))
+
+
+def sbio_apply_stokes_sl_host(g, f_tilde, u_out, stream=None):
+    """Host numpy arrays in and out (C-contiguous float64)."""
+    for a in (f_tilde, u_out):
+        assert a.dtype == np.float64 and a.flags.c_contiguous
+    _check(_lib.sbio_apply_stokes_sl_host(g, _ptr(f_tilde), _ptr(u_out), _stream(stream)))
+
+
+def sbio_geom_set_stokes_tuning(g, far_tt, far_splits, near_ctas_per_sm=0):
+    _check(_lib.sbio_geom_set_stokes_tuning(g, far_tt, far_splits, near_ctas_per_sm))
+
+
+def sbio_geom_get_stokes_tuning(g):
+    a, b, c = C.c_int32(), C.c_int32(), C.c_int32()
+    _check(_lib.sbio_geom_get_stokes_tuning(g, C.byref(a), C.byref(b), C.byref(c)))
+    return {"far_tt": a.value, "far_splits": b.value, "near_ctas_per_sm": c.value}
+
+
+def sbio_geom_autotune_stokes(g, stream=None):
+    """Pick the fastest Stokes far-field shape and near cap; returns (tt, splits, ms)."""
+    a, b, c = C.c_int32(), C.c_int32(), C.c_double()
+    _check(_lib.sbio_geom_autotune_stokes(g, _stream(stream), C.byref(a), C.byref(b), C.byref(c)))
+    return a.value, b.value, c.value
 
 
 def sbio_apply_self_noalloc(spheroids, p, sigma_tilde, mu_hat, S_out, D_out, n_phi=0, stream=None):

@@ -96,3 +96,46 @@ def test_stokes100_mixed_vs_fp64(S, stokes100):
     e = relerr(Um, U64)
     print(f"stokes mixed vs fp64: {e:.3e}")
     assert e < TOLMIX
+
+
+@pytest.mark.parametrize("tt,splits", [(1, 0), (4, 2), (8, 0), (-2, 0), (-4, 3), (-8, 0)])
+def test_stokes_far_launch_shapes(S, stokes100, tt, splits):
+    """Every far-field launch shape of the Stokeslet kernel stays within the
+    mixed-precision bound of the FP64 path."""
+    s, f, g = stokes100
+    U64 = gpu_stokes(S, g, f, S.SBIO_FP64)
+    saved = S.sbio_geom_get_stokes_tuning(g.h)
+    try:
+        S.sbio_geom_set_stokes_tuning(g.h, tt, splits, 1)
+        Um = gpu_stokes(S, g, f, S.SBIO_MIXED)
+    finally:
+        S.sbio_geom_set_stokes_tuning(g.h, saved["far_tt"], saved["far_splits"], saved["near_ctas_per_sm"])
+        S.sbio_geom_set_precision(g.h, S.SBIO_FP64)
+    assert relerr(Um, U64) < TOLMIX
+
+
+def test_stokes_autotune_and_host_entry(S, stokes100):
+    """The Stokes autotuner picks a valid shape, leaves the Laplace settings
+    alone, and the host entry point gives the device path's numbers."""
+    s, f, g = stokes100
+    S.sbio_geom_set_precision(g.h, S.SBIO_MIXED)
+    lap = S.sbio_geom_get_tuning(g.h)
+    try:
+        tt, sp, ms = S.sbio_geom_autotune_stokes(g.h)
+        assert tt in (1, 2, 4, 8, -2, -4, -8) and sp >= 1 and ms > 0
+        assert S.sbio_geom_get_tuning(g.h) == lap
+        assert S.sbio_geom_get_stokes_tuning(g.h)["far_tt"] == tt
+        Ud = gpu_stokes(S, g, f)
+        Uh = np.zeros((g.N, 3))
+        S.sbio_apply_stokes_sl_host(g.h, np.ascontiguousarray(f), Uh)
+        assert np.max(np.abs(Uh - Ud)) <= 1e-12 * np.max(np.abs(Ud))
+    finally:
+        S.sbio_geom_set_precision(g.h, S.SBIO_FP64)
+
+
+def test_stokes_tuning_rejects_bad_values(S, stokes100):
+    g = stokes100[2]
+    for args in [(3, 0, 0), (2, -1, 0), (2, 0, -1)]:
+        with pytest.raises(S.SbioError) as e:
+            S.sbio_geom_set_stokes_tuning(g.h, *args)
+        assert e.value.code == S.SBIO_EINVAL
