@@ -226,10 +226,12 @@ __device__ __forceinline__ void far_mixed_block(int64_t tb, int t_lo, int t_hi,
                                                 const int32_t* __restrict__ skip_ptr,
                                                 const int32_t* __restrict__ skip_idx, int64_t N,
                                                 double* __restrict__ S_out, double* __restrict__ D_out) {
-  // tile of sources: scalar form (y - c, q), (d, 0); packed form every value
-  // duplicated into an f32x2 pair and y negated: (-y.x,-y.x,-y.y,-y.y),
-  // (-y.z,-y.z,q,q), (d.x,d.x,d.y,d.y), (d.z,d.z,0,0)
-  __shared__ float4 sh[(PK ? 4 : 2) * kFarTile];
+  // tile of sources: scalar form (y - c, q), (d, 0).  The packed form uses
+  // the expanded distance |x - y|^2 = (|x|^2 + |y|^2) - 2 x.y and
+  // d.(x - y) = d.x - d.y, so that a pair costs 11 FP32 operations instead of
+  // 13; per source it holds every value duplicated into an f32x2 pair:
+  // (-2y.x, -2y.y), (-2y.z, |y|^2), (q, -d.y), (d.x, d.y), (d.z, 0)
+  __shared__ float4 sh[(PK ? 5 : 2) * kFarTile];
   __shared__ float acc[4 * TT * kFarTile];   // per target: S hi, S lo, D hi, D lo
   __shared__ int cursor[2 * TT * kFarTile];  // per target: skip-list position, next skipped particle
   const int tid = threadIdx.x;
@@ -245,7 +247,7 @@ __device__ __forceinline__ void far_mixed_block(int64_t tb, int t_lo, int t_hi,
     cursor[(2 * q + 0) * kFarTile + tid] = sp;
     cursor[(2 * q + 1) * kFarTile + tid] = (t < N) ? skip_idx[sp] : INT32_MAX;
   }
-  float X[TT], Y[TT], Z[TT];
+  float X[TT], Y[TT], Z[TT], XX[TT];
   unsigned skipmask = (1u << TT) - 1u;
   int cur = -1;
   for (int tl = t_lo; tl < t_hi; ++tl) {
@@ -271,6 +273,7 @@ __device__ __forceinline__ void far_mixed_block(int64_t tb, int t_lo, int t_hi,
         X[q] = (hi.x - ch.x) + (lo.x - cl.x);
         Y[q] = (hi.y - ch.y) + (lo.y - cl.y);
         Z[q] = (hi.z - ch.z) + (lo.z - cl.z);
+        if constexpr (PK) XX[q] = fmaf(Z[q], Z[q], fmaf(Y[q], Y[q], X[q] * X[q]));
       }
     }
     const bool mine = skipmask != (1u << TT) - 1u;
@@ -279,10 +282,13 @@ __device__ __forceinline__ void far_mixed_block(int64_t tb, int t_lo, int t_hi,
       const float4 a = src32[(int64_t)(tile.y + tid) * 2 + 0];
       const float4 b = src32[(int64_t)(tile.y + tid) * 2 + 1];
       if (PK) {
-        sh[tid * 4 + 0] = make_float4(-a.x, -a.x, -a.y, -a.y);
-        sh[tid * 4 + 1] = make_float4(-a.z, -a.z, a.w, a.w);
-        sh[tid * 4 + 2] = make_float4(b.x, b.x, b.y, b.y);
-        sh[tid * 4 + 3] = make_float4(b.z, b.z, 0.f, 0.f);
+        const float yy = fmaf(a.z, a.z, fmaf(a.y, a.y, a.x * a.x));
+        const float dy = fmaf(b.z, a.z, fmaf(b.y, a.y, b.x * a.x));
+        sh[tid * 5 + 0] = make_float4(-2.f * a.x, -2.f * a.x, -2.f * a.y, -2.f * a.y);
+        sh[tid * 5 + 1] = make_float4(-2.f * a.z, -2.f * a.z, yy, yy);
+        sh[tid * 5 + 2] = make_float4(a.w, a.w, -dy, -dy);
+        sh[tid * 5 + 3] = make_float4(b.x, b.x, b.y, b.y);
+        sh[tid * 5 + 4] = make_float4(b.z, b.z, 0.f, 0.f);
       } else {
         sh[tid * 2 + 0] = a;
         sh[tid * 2 + 1] = b;
@@ -296,29 +302,31 @@ __device__ __forceinline__ void far_mixed_block(int64_t tb, int t_lo, int t_hi,
       if constexpr (PK) {
         // two targets per f32x2 operation (sm_100+ packed FP32), one MUFU rsqrt per pair
         constexpr int TP = TT / 2 > 0 ? TT / 2 : 1;
-        float2 Xp[TP], Yp[TP], Zp[TP], sS2[TP], sD2[TP];
+        float2 Xp[TP], Yp[TP], Zp[TP], XXp[TP], sS2[TP], sD2[TP];
 #pragma unroll
         for (int k = 0; k < TT / 2; ++k) {
           Xp[k] = make_float2(X[2 * k], X[2 * k + 1]);
           Yp[k] = make_float2(Y[2 * k], Y[2 * k + 1]);
           Zp[k] = make_float2(Z[2 * k], Z[2 * k + 1]);
+          XXp[k] = make_float2(XX[2 * k], XX[2 * k + 1]);
           sS2[k] = make_float2(0.f, 0.f);
           sD2[k] = make_float2(0.f, 0.f);
         }
 #pragma unroll 2
         for (int j = 0; j < tile.z; ++j) {
-          const float4 A = sh[j * 4 + 0], B = sh[j * 4 + 1], Cc = sh[j * 4 + 2], Dd = sh[j * 4 + 3];
-          const float2 my = make_float2(A.x, A.y), myy = make_float2(A.z, A.w), myz = make_float2(B.x, B.y);
-          const float2 q2 = make_float2(B.z, B.w), dwx = make_float2(Cc.x, Cc.y), dwy = make_float2(Cc.z, Cc.w);
-          const float2 dwz = make_float2(Dd.x, Dd.y);
+          const float4 A = sh[j * 5 + 0], B = sh[j * 5 + 1], Cc = sh[j * 5 + 2], Dd = sh[j * 5 + 3],
+                       Ee = sh[j * 5 + 4];
+          const float2 mx = make_float2(A.x, A.y), my = make_float2(A.z, A.w), mz = make_float2(B.x, B.y);
+          const float2 yy = make_float2(B.z, B.w), q2 = make_float2(Cc.x, Cc.y), ndy = make_float2(Cc.z, Cc.w);
+          const float2 dwx = make_float2(Dd.x, Dd.y), dwy = make_float2(Dd.z, Dd.w), dwz = make_float2(Ee.x, Ee.y);
 #pragma unroll
           for (int k = 0; k < TT / 2; ++k) {
-            const float2 dx = __fadd2_rn(Xp[k], my), dy = __fadd2_rn(Yp[k], myy), dz = __fadd2_rn(Zp[k], myz);
-            const float2 r2 = __ffma2_rn(dz, dz, __ffma2_rn(dy, dy, __fmul2_rn(dx, dx)));
+            const float2 r2 =
+                __ffma2_rn(Xp[k], mx, __ffma2_rn(Yp[k], my, __ffma2_rn(Zp[k], mz, __fadd2_rn(XXp[k], yy))));
             const float2 ri = make_float2(rsqrt_approx(r2.x), rsqrt_approx(r2.y));
             if (DO_S) sS2[k] = __ffma2_rn(q2, ri, sS2[k]);
             if (DO_D) {
-              const float2 dn = __ffma2_rn(dwz, dz, __ffma2_rn(dwy, dy, __fmul2_rn(dwx, dx)));
+              const float2 dn = __ffma2_rn(dwx, Xp[k], __ffma2_rn(dwy, Yp[k], __ffma2_rn(dwz, Zp[k], ndy)));
               sD2[k] = __ffma2_rn(__fmul2_rn(dn, ri), __fmul2_rn(ri, ri), sD2[k]);
             }
           }
