@@ -188,6 +188,7 @@ class SuspensionGeom:
         self.N = self.M * self.G
         self.near_factor = near_factor
         self.x = np.concatenate([P.x for P in self.parts]) if self.M else np.zeros((0, 3))
+        self.nrm = np.concatenate([P.nrm for P in self.parts]) if self.M else np.zeros((0, 3))
         self.owner = np.repeat(np.arange(self.M), self.G)
         self._near = None
         self._dist = None
@@ -216,6 +217,36 @@ class SuspensionGeom:
         if targets is None:
             self._dist = D
         return D
+
+    def point_distances(self, X):
+        """(T, M) signed distances from arbitrary points X (T, 3) to every
+        spheroid (negative inside), with the same bounding-sphere shortcut as
+        distances() for pairs that are certainly far."""
+        X = np.atleast_2d(np.asarray(X, dtype=np.float64))
+        D = np.zeros((X.shape[0], self.M))
+        for i, P in enumerate(self.parts):
+            lb = np.linalg.norm(X - P.center, axis=1) - P.major
+            exact = lb < 2.0 * self.near_factor * P.major
+            D[:, i] = lb
+            if np.any(exact):
+                D[exact, i] = point_spheroid_distance(P.to_local(X[exact]), P.A, P.C)
+        return D
+
+    def point_near_matrix(self, X):
+        """(T, M) bool for arbitrary points in the fluid: particle i is near
+        point x iff dist(x, Gamma_i) < near_factor x major semi-axis of i
+        (Sec. 4.1, particle-to-target algorithm: classification per point).
+        Raises ValueError for a point inside a spheroid."""
+        D = self.point_distances(X)
+        thr = np.array([self.near_factor * P.major for P in self.parts])
+        # a point on a surface to rounding (|D| <= 1e-12 x major) is taken
+        # as the exterior limit
+        maj = np.array([P.major for P in self.parts])
+        bad = D < -1e-12 * maj[None, :]
+        if np.any(bad):
+            t, i = np.argwhere(bad)[0]
+            raise ValueError(f"point {t} lies inside spheroid {i}")
+        return D < thr[None, :]
 
     def near_matrix(self, targets=None):
         """(T, M) bool: source i is near target t (own particle excluded)."""

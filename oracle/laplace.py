@@ -192,6 +192,41 @@ class LaplaceOracle:
                     D[sel_far] += Df
         return S, D
 
+    def eval_points(self, X, sigma_t=None, mu_h=None, mode="method"):
+        """S and D at arbitrary points X (T, 3) in the fluid (Sec. 4.1,
+        particle-to-target algorithm): every (point, particle) pair is
+        classified by the point's own exact distance; near particles by the
+        exterior expansion of Theorems 1-2, far particles by the smooth
+        quadrature.  mode 'exact': exterior expansion for every particle.
+        Raises ValueError for a point inside a spheroid."""
+        g = self.g
+        X = np.atleast_2d(np.asarray(X, dtype=np.float64))
+        near = g.point_near_matrix(X)
+        if mode == "exact":
+            near = np.ones_like(near)
+        S = np.zeros(X.shape[0]) if sigma_t is not None else None
+        D = np.zeros(X.shape[0]) if mu_h is not None else None
+        for i, P in enumerate(g.parts):
+            si = None if sigma_t is None else sigma_t[i]
+            mi = None if mu_h is None else mu_h[i]
+            for sel, fn in ((near[:, i], "near"), (~near[:, i], "far")):
+                if not np.any(sel):
+                    continue
+                if fn == "near":
+                    Sv, Dv = solid_eval(P, self.mult[i], X[sel], si, mi, "exterior")
+                else:
+                    Sv, Dv = quadrature_eval(P, X[sel], si, mi)
+                if S is not None:
+                    S[sel] += Sv
+                if D is not None:
+                    D[sel] += Dv
+        return S, D
+
+    def point_far_pair_count(self, X):
+        """(point, far source node) pairs of eval_points in method mode."""
+        near = self.g.point_near_matrix(X)
+        return int(np.sum(~near) * self.g.G)
+
     def far_pair_count(self, targets=None):
         """Number of (target, far source node) pairs of the method."""
         g = self.g
