@@ -229,6 +229,20 @@ int sbio_apply_laplace_host(sbio_geom* g, const double* sigma_tilde_host, const 
  * u_out: device, N x 3 FP64 (row t = velocity at node t).  Asynchronous. */
 int sbio_apply_stokes_sl(sbio_geom* g, const double* f_tilde, double* u_out, void* stream);
 
+/* Normal derivatives of the layer potentials at all N nodes (Sec. 3.3,
+ * Theorem 3 and eq. (dSLevalformula); Sec. 4.2 "Other layer potentials"):
+ *   Sp_out[t] = S'[sigma](x_t) = d/dnu(x_t) S[sigma](x_t), on the own surface
+ *               the principal value (average of the exterior and interior
+ *               limits; S'+ = S' - sigma/2, S'- = S' + sigma/2),
+ *   Dp_out[t] = D'[mu](x_t) = d/dnu(x_t) D[mu](x_t) (continuous across the
+ *               surface; hypersingular, evaluated through the multipliers),
+ * nu the outward unit normal at the target node.  Inputs, layouts, precision
+ * modes, near sets and the far-field rule are those of sbio_apply_laplace
+ * (either input may be NULL; each output is given exactly when its input
+ * is); outputs overwritten.  SBIO_ENOTSUP for p > 20.  Asynchronous. */
+int sbio_apply_laplace_deriv(sbio_geom* g, const double* sigma_tilde, const double* mu_hat, double* Sp_out,
+                             double* Dp_out, void* stream);
+
 /* End-to-end Stokes apply from and to HOST memory (f_tilde_host M x 3 x
  * (p+1)^2, u_host N x 3): copies in through library-owned device buffers on
  * `stream`, applies, copies out and synchronises `stream` before returning. */
@@ -248,6 +262,39 @@ int sbio_geom_get_stokes_tuning(const sbio_geom* g, int32_t* far_tt, int32_t* fa
  * `stream`. */
 int sbio_geom_autotune_stokes(sbio_geom* g, void* stream, int32_t* far_tt, int32_t* far_splits, double* far_ms);
 
+
+/* ---- particle-to-target evaluation (Sec. 4.1, "Particle-to-target
+ * algorithm") ---------------------------------------------------------------
+ * S[sigma] and D[mu] of every spheroid of a geometry at T arbitrary points in
+ * the fluid (outside every spheroid).  The classification is per point: the
+ * pair (point, spheroid i) is near iff the exact distance from the point to
+ * the surface of i is below near_factor x (major semi-axis of i), the same
+ * rule as for surface nodes; near pairs use the exterior expansions of
+ * Theorems 1-2, all other pairs the smooth GL x trapezoid quadrature.
+ * A target set is resident like the geometry it belongs to: creation
+ * classifies the points on the host and uploads the pair lists; every
+ * evaluation then runs on the device only. */
+typedef struct sbio_targets sbio_targets;   /* opaque: points, near pairs, skip lists */
+
+/* xyz_host: T x 3 global coordinates (host, row-major), copied.  Points on a
+ * surface to rounding (level-set value within 1e-11 of 1) count as exterior
+ * points; a point inside a spheroid fails with SBIO_EINVAL.  T = 0 is
+ * allowed.  The set must be destroyed before its geometry (sbio_geom_destroy
+ * returns SBIO_EINVAL while sets are alive).  Synchronises `stream`. */
+int sbio_targets_create(sbio_geom* g, const double* xyz_host, int64_t T, void* stream, sbio_targets** out);
+int sbio_targets_destroy(sbio_targets* ts);
+/* Points, near (point, spheroid) pairs, far (point, source node) pairs and
+ * device bytes of the set (outputs may be NULL). */
+int sbio_targets_info(const sbio_targets* ts, int64_t* n_points, int64_t* n_near_pairs, int64_t* n_far_pairs,
+                      size_t* device_bytes);
+/* S_out[t] = S[sigma](x_t), D_out[t] = D[mu](x_t): inputs as
+ * sbio_apply_laplace (device, M x (p+1)^2, either may be NULL), outputs
+ * device arrays of T doubles, overwritten.  Precision and far-field launch
+ * shape are the geometry's.  Uses the geometry's workspaces: stream-ordered
+ * with every other call on the same geometry.  Asynchronous. */
+int sbio_eval_targets(sbio_targets* ts, const double* sigma_tilde, const double* mu_hat, double* S_out,
+                      double* D_out, void* stream);
+
 /* ---- batched apply over many suspensions ------------------------------
  * A batch groups resident geometries (any mix of M and p, all in SBIO_MIXED
  * mode, same context).  One batch apply computes S[sigma_s] and D[mu_s] for
@@ -255,7 +302,7 @@ int sbio_geom_autotune_stokes(sbio_geom* g, void* stream, int32_t* far_tt, int32
  * near-field kernels on a second branch, and a single persistent far-field
  * kernel whose CTAs pull (suspension, target block, source-tile range) work
  * items from an atomic counter, longest first.  No data is shared between
- * suspensions (SURVEY: independent problems).  The graph is captured on the
+ * suspensions (they are independent problems).  The graph is captured on the
  * first apply and replayed while the same buffers are passed; new buffers
  * trigger a re-capture (which synchronises `stream`). */
 typedef struct sbio_batch sbio_batch;

@@ -1,0 +1,319 @@
+// Normal-derivative operators S'[sigma] and D'[mu] at every surface node
+// (Sec. 3.3, Theorem 3 and eq. (dSLevalformula); Sec. 4.2 "Other layer
+// potentials"), with the same three-way split as the layer potentials:
+//   self: the synthesis kernel with the derivative multipliers (S' the
+//         average of the exterior and interior limits, D' continuous) and
+//         the 1/h_u surface factor;
+//   near: gradient of the source's exterior expansions dotted with the
+//         target's normal (sbio_deriv_near.cuh);
+//   far:  smooth quadrature of the differentiated kernels
+//         S': -q nu_x . r / (4 pi |r|^3)
+//         D': (d . nu_x / |r|^3 - 3 (d . r)(nu_x . r) / |r|^5) / (4 pi),
+//         r = x - y, q = w sigma, d = w mu nu_y (the far sources of the
+//         synthesis kernel).
+#include "sbio_deriv_near.cuh"
+#include "sbio_internal.cuh"
+
+namespace sbio {
+
+deriv_near_launcher deriv_near_lookup_a(int p);
+deriv_near_launcher deriv_near_lookup_b(int p);
+
+namespace {
+
+constexpr double kInv4PiD = 0.07957747154594767;   // 1/(4 pi)
+
+struct alignas(32) dd4 {
+  double x, y, z, w;
+};
+
+__device__ __forceinline__ float rsqrt_apx(float x) {
+  float r;
+  asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+
+__device__ __forceinline__ void two_sum_f(float a, float b, float& s, float& e) {
+  s = a + b;
+  const float bb = s - a;
+  e = (a - (s - bb)) + (b - bb);
+}
+
+// FP64 form: one target per thread, kFarTile sources per shared-memory tile.
+template <bool DO_S, bool DO_D>
+__global__ void __launch_bounds__(kFarTile) far_deriv_fp64_kernel(const int4* __restrict__ tiles, int n_tiles,
+                                                                  const double* __restrict__ src64,
+                                                                  const double* __restrict__ xyz,
+                                                                  const double* __restrict__ nrm,
+                                                                  const PartGeom* __restrict__ parts,
+                                                                  const int32_t* __restrict__ skip_ptr,
+                                                                  const int32_t* __restrict__ skip_idx, int64_t N,
+                                                                  double* __restrict__ Sp_out,
+                                                                  double* __restrict__ Dp_out) {
+  __shared__ dd4 sh[kFarTile * 2];
+  const int64_t t = (int64_t)blockIdx.x * kFarTile + threadIdx.x;
+  const bool valid = t < N;
+  double x = 0, y = 0, z = 0, nx = 0, ny = 0, nz = 0;
+  int sp = 0, nxt = INT32_MAX;
+  if (valid) {
+    x = xyz[t * 3 + 0];
+    y = xyz[t * 3 + 1];
+    z = xyz[t * 3 + 2];
+    nx = nrm[t * 3 + 0];
+    ny = nrm[t * 3 + 1];
+    nz = nrm[t * 3 + 2];
+    sp = skip_ptr[t];
+    nxt = skip_idx[sp];
+  }
+  double accS = 0.0, accD = 0.0;
+  int cur = -1;
+  bool skip = true;
+  double X = 0, Y = 0, Z = 0;
+  const int per = (n_tiles + gridDim.y - 1) / gridDim.y;
+  const int t_lo = blockIdx.y * per, t_hi = min(n_tiles, t_lo + per);
+  for (int tl = t_lo; tl < t_hi; ++tl) {
+    const int4 tile = tiles[tl];
+    if (tile.x != cur) {
+      cur = tile.x;
+      if (valid) {
+        while (nxt < cur) nxt = skip_idx[++sp];
+        skip = (nxt == cur);
+        X = x - parts[cur].c[0];
+        Y = y - parts[cur].c[1];
+        Z = z - parts[cur].c[2];
+      }
+    }
+    if (__syncthreads_and(skip)) continue;
+    if (threadIdx.x < tile.z) {
+      const dd4* s = reinterpret_cast<const dd4*>(src64 + (int64_t)(tile.y + threadIdx.x) * 8);
+      sh[threadIdx.x * 2 + 0] = s[0];
+      sh[threadIdx.x * 2 + 1] = s[1];
+    }
+    __syncthreads();
+    if (!skip) {
+      for (int j = 0; j < tile.z; ++j) {
+        const dd4 a = sh[j * 2], b = sh[j * 2 + 1];
+        const double dx = X - a.x, dy = Y - a.y, dz = Z - a.z;
+        const double r2 = dx * dx + dy * dy + dz * dz;
+        const double ri = rsqrt(r2);
+        const double ri2 = ri * ri, ri3 = ri2 * ri;
+        const double rn = dx * nx + dy * ny + dz * nz;
+        if (DO_S) accS = fma(-a.w * rn, ri3, accS);
+        if (DO_D) {
+          const double dr = b.x * dx + b.y * dy + b.z * dz;
+          const double dn = b.x * nx + b.y * ny + b.z * nz;
+          accD = fma(fma(-3.0 * dr * rn, ri2, dn), ri3, accD);
+        }
+      }
+    }
+    __syncthreads();
+  }
+  if (valid) {
+    if (DO_S) atomicAdd(Sp_out + t, accS * kInv4PiD);
+    if (DO_D) atomicAdd(Dp_out + t, accD * kInv4PiD);
+  }
+}
+
+// Mixed form: FP32 pair sums, TT targets per thread, the targets taken
+// relative to each source particle's centre through hi/lo FP32 parts, per-tile
+// partials folded into (hi, lo) pairs by TwoSum in shared memory (the same
+// scheme as the layer-potential far field).
+template <int TT, bool DO_S, bool DO_D>
+__global__ void __launch_bounds__(kFarTile) far_deriv_mixed_kernel(const int4* __restrict__ tiles, int n_tiles,
+                                                                   const float4* __restrict__ src32,
+                                                                   const float4* __restrict__ tgt32,
+                                                                   const float4* __restrict__ cen32,
+                                                                   const double* __restrict__ nrm,
+                                                                   const int32_t* __restrict__ skip_ptr,
+                                                                   const int32_t* __restrict__ skip_idx, int64_t N,
+                                                                   double* __restrict__ Sp_out,
+                                                                   double* __restrict__ Dp_out) {
+  __shared__ float4 sh[2 * kFarTile];        // (y - c, -q), (d, 0)
+  __shared__ float acc[4 * TT * kFarTile];   // per target: S' hi, lo, D' hi, lo
+  __shared__ int cursor[2 * TT * kFarTile];  // per target: skip-list position, next skipped particle
+  const int tid = threadIdx.x;
+  const int per = (n_tiles + gridDim.y - 1) / gridDim.y;
+  const int t_lo = blockIdx.y * per, t_hi = min(n_tiles, t_lo + per);
+  const int64_t t0 = (int64_t)blockIdx.x * TT * kFarTile + tid;
+  float NX[TT], NY[TT], NZ[TT];
+#pragma unroll
+  for (int q = 0; q < TT; ++q) {
+    const int64_t t = t0 + (int64_t)q * kFarTile;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) acc[(4 * q + k) * kFarTile + tid] = 0.f;
+    const int sp = (t < N) ? skip_ptr[t] : 0;
+    cursor[(2 * q + 0) * kFarTile + tid] = sp;
+    cursor[(2 * q + 1) * kFarTile + tid] = (t < N) ? skip_idx[sp] : INT32_MAX;
+    NX[q] = (t < N) ? (float)nrm[t * 3 + 0] : 0.f;
+    NY[q] = (t < N) ? (float)nrm[t * 3 + 1] : 0.f;
+    NZ[q] = (t < N) ? (float)nrm[t * 3 + 2] : 0.f;
+  }
+  float X[TT], Y[TT], Z[TT];
+  unsigned skipmask = (1u << TT) - 1u;
+  int cur = -1;
+  for (int tl = t_lo; tl < t_hi; ++tl) {
+    const int4 tile = tiles[tl];
+    if (tile.x != cur) {
+      cur = tile.x;
+      const float4 ch = cen32[cur * 2], cl = cen32[cur * 2 + 1];
+      skipmask = 0u;
+#pragma unroll
+      for (int q = 0; q < TT; ++q) {
+        const int64_t t = t0 + (int64_t)q * kFarTile;
+        int sp = cursor[(2 * q + 0) * kFarTile + tid];
+        int nxt = cursor[(2 * q + 1) * kFarTile + tid];
+        while (nxt < cur) nxt = skip_idx[++sp];
+        cursor[(2 * q + 0) * kFarTile + tid] = sp;
+        cursor[(2 * q + 1) * kFarTile + tid] = nxt;
+        if (t >= N || nxt == cur) skipmask |= 1u << q;
+        float4 hi = make_float4(0.f, 0.f, 0.f, 0.f), lo = hi;
+        if (t < N) {
+          hi = tgt32[t * 2];
+          lo = tgt32[t * 2 + 1];
+        }
+        X[q] = (hi.x - ch.x) + (lo.x - cl.x);
+        Y[q] = (hi.y - ch.y) + (lo.y - cl.y);
+        Z[q] = (hi.z - ch.z) + (lo.z - cl.z);
+      }
+    }
+    const bool mine = skipmask != (1u << TT) - 1u;
+    if (!__syncthreads_or(mine)) continue;
+    if (tid < tile.z) {
+      const float4 a = src32[(int64_t)(tile.y + tid) * 2 + 0];
+      sh[tid * 2 + 0] = make_float4(a.x, a.y, a.z, -a.w);
+      sh[tid * 2 + 1] = src32[(int64_t)(tile.y + tid) * 2 + 1];
+    }
+    __syncthreads();
+    if (mine) {
+      float pS[TT], pD[TT];
+#pragma unroll
+      for (int q = 0; q < TT; ++q) pS[q] = pD[q] = 0.f;
+#pragma unroll 2
+      for (int j = 0; j < tile.z; ++j) {
+        const float4 a = sh[j * 2], b = sh[j * 2 + 1];
+#pragma unroll
+        for (int q = 0; q < TT; ++q) {
+          const float dx = X[q] - a.x, dy = Y[q] - a.y, dz = Z[q] - a.z;
+          const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
+          const float ri = rsqrt_apx(r2);
+          const float ri2 = ri * ri, ri3 = ri2 * ri;
+          const float rn = fmaf(dz, NZ[q], fmaf(dy, NY[q], dx * NX[q]));
+          if (DO_S) pS[q] = fmaf(a.w * rn, ri3, pS[q]);
+          if (DO_D) {
+            const float dr = fmaf(b.z, dz, fmaf(b.y, dy, b.x * dx));
+            const float dn = fmaf(b.z, NZ[q], fmaf(b.y, NY[q], b.x * NX[q]));
+            pD[q] = fmaf(fmaf(-3.f * dr * rn, ri2, dn), ri3, pD[q]);
+          }
+        }
+      }
+#pragma unroll
+      for (int q = 0; q < TT; ++q) {
+        if (!((skipmask >> q) & 1u)) {
+          float sum, err;
+          if (DO_S) {
+            two_sum_f(acc[(4 * q + 0) * kFarTile + tid], pS[q], sum, err);
+            acc[(4 * q + 0) * kFarTile + tid] = sum;
+            acc[(4 * q + 1) * kFarTile + tid] += err;
+          }
+          if (DO_D) {
+            two_sum_f(acc[(4 * q + 2) * kFarTile + tid], pD[q], sum, err);
+            acc[(4 * q + 2) * kFarTile + tid] = sum;
+            acc[(4 * q + 3) * kFarTile + tid] += err;
+          }
+        }
+      }
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int q = 0; q < TT; ++q) {
+    const int64_t t = t0 + (int64_t)q * kFarTile;
+    if (t < N) {
+      if (DO_S)
+        atomicAdd(Sp_out + t,
+                  ((double)acc[(4 * q + 0) * kFarTile + tid] + (double)acc[(4 * q + 1) * kFarTile + tid]) * kInv4PiD);
+      if (DO_D)
+        atomicAdd(Dp_out + t,
+                  ((double)acc[(4 * q + 2) * kFarTile + tid] + (double)acc[(4 * q + 3) * kFarTile + tid]) * kInv4PiD);
+    }
+  }
+}
+
+constexpr int kDerivTT = 4;   // targets per thread of the mixed derivative far kernel
+
+template <bool DO_S, bool DO_D>
+void launch_far_deriv_sd(const DevGeom& d, const GeomHost& h, double* Sp, double* Dp, cudaStream_t st) {
+  const int nt = (int)h.tiles.size();
+  if (h.precision == SBIO_FP64) {
+    const int64_t tb = (h.N + kFarTile - 1) / kFarTile;
+    const dim3 grid((unsigned)tb, (unsigned)far_split_count(tb, nt, 0));
+    far_deriv_fp64_kernel<DO_S, DO_D><<<grid, kFarTile, 0, st>>>(d.tiles, nt, d.src64, d.xyz, d.nrm, d.parts,
+                                                                 d.skip_ptr, d.skip_idx, h.N, Sp, Dp);
+  } else {
+    const int64_t tb = (h.N + (int64_t)kFarTile * kDerivTT - 1) / ((int64_t)kFarTile * kDerivTT);
+    const dim3 grid((unsigned)tb, (unsigned)far_split_count(tb, nt, 0));
+    far_deriv_mixed_kernel<kDerivTT, DO_S, DO_D><<<grid, kFarTile, 0, st>>>(
+        d.tiles, nt, d.src32, d.tgt32, d.cen32, d.nrm, d.skip_ptr, d.skip_idx, h.N, Sp, Dp);
+  }
+  count_launch();
+}
+
+}  // namespace
+
+int launch_laplace_deriv(sbio_geom* g, const double* sigma, const double* mu, double* Sp, double* Dp,
+                         cudaStream_t st) {
+  const GeomHost& h = g->h;
+  if (h.p > 20) return set_error(SBIO_ENOTSUP, "S' / D' are built for p <= 20 (p = %d)", h.p);
+  deriv_near_launcher nl = deriv_near_lookup_a(h.p);
+  if (!nl) nl = deriv_near_lookup_b(h.p);
+  if (!nl) return set_error(SBIO_ENOTSUP, "no S' / D' near-field kernel for p = %d", h.p);
+  phase_mark(g, 0, st);
+  // self: writes (initialises) the outputs, and the far sources and near
+  // coefficients of this apply
+  int rc = launch_synth_mode(g, sigma, mu, Sp, Dp, 2, st);
+  if (rc) return rc;
+  phase_mark(g, 1, st);
+  const bool fork = g->overlap && !g->timing && g->near_stream && !h.pair_t.empty();
+  if (fork) {
+    SBIO_CUDA_TRY(cudaEventRecord(g->ev_fork, st));
+    SBIO_CUDA_TRY(cudaStreamWaitEvent(g->near_stream, g->ev_fork, 0));
+    g->d.near_grid_cap = h.near_ctas_per_sm > 0 ? h.near_ctas_per_sm * sm_count() : 0;
+    nl(g->d, h.n_pairs_prolate, (int64_t)h.pair_t.size(), Sp, Dp, g->near_stream);
+    g->d.near_grid_cap = 0;
+    SBIO_CUDA_TRY(cudaGetLastError());
+    SBIO_CUDA_TRY(cudaEventRecord(g->ev_join, g->near_stream));
+  } else if (!h.pair_t.empty()) {
+    nl(g->d, h.n_pairs_prolate, (int64_t)h.pair_t.size(), Sp, Dp, st);
+    SBIO_CUDA_TRY(cudaGetLastError());
+  }
+  phase_mark(g, 2, st);
+  if (Sp && Dp)
+    launch_far_deriv_sd<true, true>(g->d, h, Sp, Dp, st);
+  else if (Sp)
+    launch_far_deriv_sd<true, false>(g->d, h, Sp, Dp, st);
+  else
+    launch_far_deriv_sd<false, true>(g->d, h, Sp, Dp, st);
+  SBIO_CUDA_TRY(cudaGetLastError());
+  if (fork) SBIO_CUDA_TRY(cudaStreamWaitEvent(st, g->ev_join, 0));
+  phase_mark(g, 3, st);
+  return SBIO_OK;
+}
+
+}  // namespace sbio
+
+using namespace sbio;
+
+extern "C" {
+
+int sbio_apply_laplace_deriv(sbio_geom* g, const double* sigma_tilde, const double* mu_hat, double* Sp_out,
+                             double* Dp_out, void* stream) {
+  clear_error();
+  if (!g) return set_error(SBIO_EINVAL, "null geometry");
+  if ((sigma_tilde == nullptr) != (Sp_out == nullptr) || (mu_hat == nullptr) != (Dp_out == nullptr))
+    return set_error(SBIO_EINVAL, "each output must be given exactly when its input is");
+  if (!sigma_tilde && !mu_hat) return set_error(SBIO_EINVAL, "nothing to apply");
+  SBIO_CUDA_TRY(cudaSetDevice(g->ctx->device));
+  return launch_laplace_deriv(g, sigma_tilde, mu_hat, Sp_out, Dp_out, (cudaStream_t)stream);
+}
+
+}  // extern "C"

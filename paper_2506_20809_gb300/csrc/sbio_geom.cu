@@ -166,7 +166,16 @@ static void quat_rot(const double* q, double* R) {
   R[6] = 2 * (x * z - w * y);     R[7] = 2 * (y * z + w * x);     R[8] = 1 - 2 * (x * x + y * y);
 }
 
-static void split_f32(double v, float& hi, float& lo) {
+double spheroid_distance_local(const PartGeom& P, double x, double y, double z, double tol, bool* inside) {
+  const double rho = std::hypot(x, y), az = std::fabs(z);
+  const double f = (rho / P.A) * (rho / P.A) + (az / P.C) * (az / P.C);
+  *inside = f < 1.0 - tol;
+  if (*inside) return 0.0;
+  if (P.C >= P.A) return ellipse_distance(P.C, P.A, az, rho);
+  return ellipse_distance(P.A, P.C, rho, az);
+}
+
+void split_f32(double v, float& hi, float& lo) {
   hi = (float)v;
   lo = (float)(v - (double)hi);
 }
@@ -381,7 +390,7 @@ static int build_device(sbio_geom* g) {
   }
   if ((rc = upload(g, &d.sqrtw, sqrtw.data(), sqrtw.size(), "modified-basis weights"))) return rc;
   // Theorems 1-2 multipliers per particle
-  std::vector<double> mult((size_t)M * 4 * nm);
+  std::vector<double> mult((size_t)M * 4 * nm), dmult((size_t)M * 4 * nm);
   std::vector<double> Pr(nm_count(p + 1)), Qr(nm_count(p + 1));
   for (int i = 0; i < M; ++i) {
     const PartGeom& P = h.parts[i];
@@ -403,9 +412,18 @@ static int build_device(sbio_geom* g) {
         mm[1 * nm + nm_index(n, m)] = extD;
         mm[2 * nm + nm_index(n, m)] = extS * qn;
         mm[3 * nm + nm_index(n, m)] = 0.5 * (Dp + Dm);
+        // normal derivatives on the surface (Theorem 3 and its D' analogue),
+        // as d/du of the exterior / interior expansions at u0; the 1/h_u
+        // factor is applied per node.  S' = (S'+ + S'-)/2, D' continuous.
+        double* dd = &dmult[(size_t)i * 4 * nm];
+        dd[0 * nm + nm_index(n, m)] = extS;
+        dd[1 * nm + nm_index(n, m)] = extD;
+        dd[2 * nm + nm_index(n, m)] = 0.5 * (extS * dq + P.a * K * s0 * qn * dp);
+        dd[3 * nm + nm_index(n, m)] = extD * dq;
       }
   }
   if ((rc = upload(g, &d.mult, mult.data(), mult.size(), "multipliers"))) return rc;
+  if ((rc = upload(g, &d.dmult, dmult.data(), dmult.size(), "derivative multipliers"))) return rc;
   std::vector<double> normc(nc);
   for (int n = 0; n <= p; ++n)
     for (int m = -n; m <= n; ++m) {
@@ -678,7 +696,10 @@ int sbio_geom_create(sbio_ctx* ctx, const sbio_spheroid* sph, int32_t M, const s
 }
 
 int sbio_geom_destroy(sbio_geom* g) {
+  clear_error();
   if (!g) return SBIO_OK;
+  if (g->n_target_sets.load() > 0)
+    return set_error(SBIO_EINVAL, "geometry still has %d target set(s); destroy them first", g->n_target_sets.load());
   cudaSetDevice(g->ctx->device);
   cudaDeviceSynchronize();
   free_geom(g);

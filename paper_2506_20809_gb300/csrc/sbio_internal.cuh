@@ -31,6 +31,7 @@ struct DevGeom {
   double* trig = nullptr;        // n_phi x (p+1) x 2: cos(m phi_k), sin(m phi_k)
   double* sqrtw = nullptr;       // M x (p+1): sqrt(u0^2 + sgn v_j^2)
   double* mult = nullptr;        // M x 4 x nm_count(p): extS, extD, selfS, selfD
+  double* dmult = nullptr;       // M x 4 x nm_count(p): extS, extD, S' (principal value), D' (d/du at u0)
   double* normc = nullptr;       // (p+1)^2: N_n^|m| (sqrt 2 for m != 0) per coefficient
   int32_t* pair_t = nullptr;     // near pairs: target node
   int32_t* pair_s = nullptr;     // near pairs: source particle
@@ -114,6 +115,7 @@ struct sbio_geom {
   double setup_ms[3] = {0.0, 0.0, 0.0};   // host geometry, near sets, device tables + upload
   cudaStream_t near_stream = nullptr;
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  std::atomic<int> n_target_sets{0};       // live sbio_targets of this geometry
 };
 
 namespace sbio {
@@ -178,8 +180,19 @@ int launch_laplace(sbio_geom* g, const double* sigma, const double* mu, double* 
                    uint32_t parts, cudaStream_t st);
 int launch_synth(sbio_geom* g, const double* sigma, const double* mu, double* S, double* D, bool write_self,
                  cudaStream_t st);
+int launch_synth_mode(sbio_geom* g, const double* sigma, const double* mu, double* S, double* D, int self_mode,
+                      cudaStream_t st);
 int launch_near(sbio_geom* g, double* S, double* D, cudaStream_t st);
 int launch_stokes(sbio_geom* g, const double* f, double* u, cudaStream_t st);
+// far field of the geometry's sources at the NT targets of `d` (d.xyz,
+// d.tgt32, d.skip_ptr, d.skip_idx; the node targets of the geometry itself
+// when d is g->d and NT = N), in the geometry's precision and launch shape
+void launch_far_on(const DevGeom& d, const GeomHost& h, int64_t NT, double* S, double* D, cudaStream_t st);
+// host geometry helpers shared by the set-up code
+void split_f32(double v, float& hi, float& lo);
+// distance from a point in the particle's local frame to its surface;
+// *inside set when the level set (rho/A)^2 + (z/C)^2 is below 1 - tol
+double spheroid_distance_local(const PartGeom& P, double x, double y, double z, double tol, bool* inside);
 int launch_stokes_far(sbio_geom* g, double* u, cudaStream_t st);
 
 // Launch-shape search shared by the Laplace and Stokes autotuners: times

@@ -28,6 +28,9 @@ struct alignas(32) dbl4 {
 // synth: densities at the nodes, far-field sources, near coefficients, self
 // ---------------------------------------------------------------------------
 // One CTA, one particle i.  `sm` holds 2 (p+1)^2 + 4 (p+1)(2p+1) doubles.
+// write_self: 0 = no self output (zeros written where outputs are given),
+// 1 = the on-surface S and D, 2 = normal derivatives S' and D' (with the
+// derivative multiplier table passed as `mult`).
 __device__ __forceinline__ void synth_particle(int i, double* sm, int p, int n_v, int n_phi,
                                                const PartGeom* __restrict__ parts, const double* __restrict__ xyz,
                                                const double* __restrict__ nrm, const double* __restrict__ w,
@@ -105,8 +108,12 @@ __device__ __forceinline__ void synth_particle(int i, double* sm, int p, int n_v
     s[4] = d0; s[5] = d1; s[6] = d2; s[7] = 0.0;
     src32[t * 2 + 0] = make_float4((float)y0, (float)y1, (float)y2, (float)q);
     src32[t * 2 + 1] = make_float4((float)d0, (float)d1, (float)d2, 0.f);
-    if (S_out) S_out[t] = write_self ? vS : 0.0;
-    if (D_out) D_out[t] = write_self ? vD : 0.0;
+    // write_self == 2: the self sums are normal derivatives (multipliers of
+    // Theorem 3 and its D' counterpart, in d/du), scaled by 1/h_u =
+    // sqrt(u0^2 + sgn) / (a sqrt(u0^2 + sgn v^2)) on the surface (Table 2)
+    const double sc = (write_self == 2) ? (P.A / P.a) / (P.a * sqrtw[(size_t)i * n_v + j]) : 1.0;
+    if (S_out) S_out[t] = write_self ? vS * sc : 0.0;
+    if (D_out) D_out[t] = write_self ? vD * sc : 0.0;
   }
 }
 
@@ -426,51 +433,54 @@ int far_split_count(int64_t target_blocks, int n_tiles, int requested) {
 }
 
 template <int TT, bool PK>
-static void launch_far_mixed_tt(const DevGeom& d, const GeomHost& h, int nt, int splits, double* S, double* D,
+static void launch_far_mixed_tt(const DevGeom& d, int64_t NT, int nt, int splits, double* S, double* D,
                                 cudaStream_t st) {
   static_assert(!PK || TT % 2 == 0, "packed form pairs targets");
-  const int64_t tb = (h.N + kFarTile * TT - 1) / (kFarTile * TT);
+  const int64_t tb = (NT + kFarTile * TT - 1) / (kFarTile * TT);
   const dim3 grid((unsigned)tb, (unsigned)far_split_count(tb, nt, splits));
   if (S && D)
     far_mixed_kernel<TT, true, true, PK><<<grid, kFarTile, 0, st>>>(d.tiles, nt, d.src32, d.tgt32, d.cen32,
-                                                                    d.skip_ptr, d.skip_idx, h.N, S, D);
+                                                                    d.skip_ptr, d.skip_idx, NT, S, D);
   else if (S)
     far_mixed_kernel<TT, true, false, PK><<<grid, kFarTile, 0, st>>>(d.tiles, nt, d.src32, d.tgt32, d.cen32,
-                                                                     d.skip_ptr, d.skip_idx, h.N, S, D);
+                                                                     d.skip_ptr, d.skip_idx, NT, S, D);
   else
     far_mixed_kernel<TT, false, true, PK><<<grid, kFarTile, 0, st>>>(d.tiles, nt, d.src32, d.tgt32, d.cen32,
-                                                                     d.skip_ptr, d.skip_idx, h.N, S, D);
+                                                                     d.skip_ptr, d.skip_idx, NT, S, D);
 }
 
-static void launch_far(sbio_geom* g, double* S, double* D, cudaStream_t st) {
-  const DevGeom& d = g->d;
-  const GeomHost& h = g->h;
+void launch_far_on(const DevGeom& d, const GeomHost& h, int64_t NT, double* S, double* D, cudaStream_t st) {
+  if (NT <= 0) return;
   const int nt = (int)h.tiles.size();
   if (h.precision == SBIO_FP64) {
-    const int64_t tb = (h.N + kFarTile - 1) / kFarTile;
+    const int64_t tb = (NT + kFarTile - 1) / kFarTile;
     const dim3 grid((unsigned)tb, (unsigned)far_split_count(tb, nt, h.far_splits));
     if (S && D)
       far_fp64_kernel<true, true><<<grid, kFarTile, 0, st>>>(d.tiles, nt, d.src64, d.xyz, d.parts, d.skip_ptr,
-                                                             d.skip_idx, h.N, S, D);
+                                                             d.skip_idx, NT, S, D);
     else if (S)
       far_fp64_kernel<true, false><<<grid, kFarTile, 0, st>>>(d.tiles, nt, d.src64, d.xyz, d.parts, d.skip_ptr,
-                                                              d.skip_idx, h.N, S, D);
+                                                              d.skip_idx, NT, S, D);
     else
       far_fp64_kernel<false, true><<<grid, kFarTile, 0, st>>>(d.tiles, nt, d.src64, d.xyz, d.parts, d.skip_ptr,
-                                                              d.skip_idx, h.N, S, D);
+                                                              d.skip_idx, NT, S, D);
   } else {
     // far_tt < 0 selects the packed f32x2 form with |far_tt| targets per thread
     switch (h.far_tt) {
-      case 1: launch_far_mixed_tt<1, false>(d, h, nt, h.far_splits, S, D, st); break;
-      case 4: launch_far_mixed_tt<4, false>(d, h, nt, h.far_splits, S, D, st); break;
-      case 8: launch_far_mixed_tt<8, false>(d, h, nt, h.far_splits, S, D, st); break;
-      case -2: launch_far_mixed_tt<2, true>(d, h, nt, h.far_splits, S, D, st); break;
-      case -4: launch_far_mixed_tt<4, true>(d, h, nt, h.far_splits, S, D, st); break;
-      case -8: launch_far_mixed_tt<8, true>(d, h, nt, h.far_splits, S, D, st); break;
-      default: launch_far_mixed_tt<2, false>(d, h, nt, h.far_splits, S, D, st); break;
+      case 1: launch_far_mixed_tt<1, false>(d, NT, nt, h.far_splits, S, D, st); break;
+      case 4: launch_far_mixed_tt<4, false>(d, NT, nt, h.far_splits, S, D, st); break;
+      case 8: launch_far_mixed_tt<8, false>(d, NT, nt, h.far_splits, S, D, st); break;
+      case -2: launch_far_mixed_tt<2, true>(d, NT, nt, h.far_splits, S, D, st); break;
+      case -4: launch_far_mixed_tt<4, true>(d, NT, nt, h.far_splits, S, D, st); break;
+      case -8: launch_far_mixed_tt<8, true>(d, NT, nt, h.far_splits, S, D, st); break;
+      default: launch_far_mixed_tt<2, false>(d, NT, nt, h.far_splits, S, D, st); break;
     }
   }
   count_launch();
+}
+
+static void launch_far(sbio_geom* g, double* S, double* D, cudaStream_t st) {
+  launch_far_on(g->d, g->h, g->h.N, S, D, st);
 }
 
 // Persistent far field over many suspensions: CTAs pull work items
@@ -510,21 +520,27 @@ int launch_far_persistent(const FarDesc* descs, const int4* items, int n_items, 
   return SBIO_OK;
 }
 
-int launch_synth(sbio_geom* g, const double* sigma, const double* mu, double* S, double* D, bool write_self,
-                 cudaStream_t st) {
+int launch_synth_mode(sbio_geom* g, const double* sigma, const double* mu, double* S, double* D, int self_mode,
+                      cudaStream_t st) {
   const GeomHost& h = g->h;
   const DevGeom& d = g->d;
+  const double* mult = self_mode == 2 ? d.dmult : d.mult;
   const int nmw = 2 * h.p + 1, nc = (h.p + 1) * (h.p + 1);
   const size_t smem = (size_t)(2 * nc + 4 * h.n_v * nmw) * sizeof(double);
   if (smem > 48 * 1024) {
     SBIO_CUDA_TRY(cudaFuncSetAttribute(synth_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   }
   synth_kernel<<<h.M, 256, smem, st>>>(h.p, h.n_v, h.n_phi, d.parts, d.xyz, d.nrm, d.w, d.ptab, d.trig, d.sqrtw,
-                                       d.mult, d.normc, sigma, mu, write_self ? 1 : 0, S, D, d.src64, d.src32,
-                                       d.alpha, d.beta);
+                                       mult, d.normc, sigma, mu, self_mode, S, D, d.src64, d.src32, d.alpha,
+                                       d.beta);
   count_launch();
   SBIO_CUDA_TRY(cudaGetLastError());
   return SBIO_OK;
+}
+
+int launch_synth(sbio_geom* g, const double* sigma, const double* mu, double* S, double* D, bool write_self,
+                 cudaStream_t st) {
+  return launch_synth_mode(g, sigma, mu, S, D, write_self ? 1 : 0, st);
 }
 
 int launch_near(sbio_geom* g, double* S, double* D, cudaStream_t st) {

@@ -331,3 +331,36 @@ def poisson_requests(rate: float, duration: float, seed: int = 0, M_range=(20, 5
         op = "laplace" if rng.uniform() < 0.5 else "stokes"
         reqs.append({"t": t, "M": M, "p": p, "op": op, "seed": int(rng.integers(1 << 30))})
     return reqs
+
+
+def shell_points(s: Suspension, distances=(1e-1, 1e-2, 1e-3, 1e-4, 1e-5, 1e-6), per_particle: int = 4,
+                 seed: int = 0, far_points: int = 0) -> np.ndarray:
+    """Evaluation points shaped like the shell tests of the paper's numerical
+    section: for every particle and every distance d, `per_particle` points
+    offset by d along the outward normal of random surface points (distance
+    to that surface d, or less on strongly curved parts); plus `far_points`
+    points uniform in the suspension's bounding box.  Points that fall
+    inside (or within 1e-9 of) any spheroid are dropped.  Returns (T, 3)."""
+    rng = np.random.default_rng([seed, 271828])
+    R = _quat_to_matrix(s.quat)
+    pts = []
+    for i in range(s.M):
+        for d in distances:
+            th = np.arccos(rng.uniform(-1.0, 1.0, per_particle))
+            ph = rng.uniform(0.0, 2 * math.pi, per_particle)
+            xl = np.stack([s.A[i] * np.sin(th) * np.cos(ph), s.A[i] * np.sin(th) * np.sin(ph),
+                           s.C[i] * np.cos(th)], -1)
+            g = xl / np.array([s.A[i] ** 2, s.A[i] ** 2, s.C[i] ** 2])
+            nl = g / np.linalg.norm(g, axis=1, keepdims=True)
+            pts.append((xl + d * nl) @ R[i].T + s.center[i])
+    if far_points:
+        lo = s.center.min(0) - np.maximum(s.A, s.C).max()
+        hi = s.center.max(0) + np.maximum(s.A, s.C).max()
+        pts.append(rng.uniform(lo, hi, (far_points, 3)))
+    X = np.concatenate(pts) if pts else np.zeros((0, 3))
+    keep = np.ones(len(X), bool)
+    for i in range(s.M):
+        xl = (X - s.center[i]) @ R[i]
+        f = (xl[:, 0] ** 2 + xl[:, 1] ** 2) / s.A[i] ** 2 + xl[:, 2] ** 2 / s.C[i] ** 2
+        keep &= f > 1.0 + 1e-9
+    return np.ascontiguousarray(X[keep])

@@ -100,6 +100,12 @@ _SIGS = {
     "sbio_apply_laplace_host": (C.c_int, [_vp, _vp, _vp, _vp, _vp, _vp]),
     "sbio_apply_stokes_sl": (C.c_int, [_vp, _vp, _vp, _vp]),
     "sbio_apply_stokes_sl_host": (C.c_int, [_vp, _vp, _vp, _vp]),
+    "sbio_apply_laplace_deriv": (C.c_int, [_vp, _vp, _vp, _vp, _vp, _vp]),
+    "sbio_targets_create": (C.c_int, [_vp, _vp, C.c_int64, _vp, C.POINTER(_vp)]),
+    "sbio_targets_destroy": (C.c_int, [_vp]),
+    "sbio_targets_info": (C.c_int, [_vp, C.POINTER(C.c_int64), C.POINTER(C.c_int64), C.POINTER(C.c_int64),
+                                    C.POINTER(C.c_size_t)]),
+    "sbio_eval_targets": (C.c_int, [_vp, _vp, _vp, _vp, _vp, _vp]),
     "sbio_geom_set_stokes_tuning": (C.c_int, [_vp, C.c_int32, C.c_int32, C.c_int32]),
     "sbio_geom_get_stokes_tuning": (C.c_int, [_vp, C.POINTER(C.c_int32), C.POINTER(C.c_int32),
                                               C.POINTER(C.c_int32)]),
@@ -305,6 +311,35 @@ def sbio_apply_stokes_sl(g, f_tilde, u_out, stream=None):
     _check(_lib.sbio_apply_stokes_sl(g, _ptr(f_tilde), _ptr(u_out), _stream(stream)))
 
 
+def sbio_apply_laplace_deriv(g, sigma_tilde, mu_hat, Sp_out, Dp_out, stream=None):
+    """S'[sigma] and D'[mu] at all nodes (device tensors; either input may be None)."""
+    _check(_lib.sbio_apply_laplace_deriv(g, _ptr(sigma_tilde), _ptr(mu_hat), _ptr(Sp_out), _ptr(Dp_out),
+                                         _stream(stream)))
+
+
+def sbio_targets_create(g, xyz, stream=None):
+    """Resident set of points (host float64 array T x 3) of geometry g."""
+    xyz = np.ascontiguousarray(np.asarray(xyz, dtype=np.float64).reshape(-1, 3))
+    h = _vp()
+    _check(_lib.sbio_targets_create(g, _ptr(xyz) if len(xyz) else None, len(xyz), _stream(stream), C.byref(h)))
+    return h.value
+
+
+def sbio_targets_destroy(ts):
+    _check(_lib.sbio_targets_destroy(ts))
+
+
+def sbio_targets_info(ts):
+    a, b, c, d = C.c_int64(), C.c_int64(), C.c_int64(), C.c_size_t()
+    _check(_lib.sbio_targets_info(ts, C.byref(a), C.byref(b), C.byref(c), C.byref(d)))
+    return {"n_points": a.value, "n_near_pairs": b.value, "n_far_pairs": c.value, "device_bytes": d.value}
+
+
+def sbio_eval_targets(ts, sigma_tilde, mu_hat, S_out, D_out, stream=None):
+    """S and D at the set's points (device tensors; either input may be None)."""
+    _check(_lib.sbio_eval_targets(ts, _ptr(sigma_tilde), _ptr(mu_hat), _ptr(S_out), _ptr(D_out), _stream(stream)))
+
+
 def sbio_apply_stokes_sl_host(g, f_tilde, u_out, stream=None):
     """Host numpy arrays in and out (C-contiguous float64)."""
     for a in (f_tilde, u_out):
@@ -424,6 +459,29 @@ class Geometry:
     def close(self):
         if self.h:
             sbio_geom_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class TargetSet:
+    """Resident points of a geometry for particle-to-target evaluation."""
+
+    def __init__(self, geom, xyz, stream=None):
+        self.geom = geom
+        self.h = sbio_targets_create(geom.h, xyz, stream)
+        info = sbio_targets_info(self.h)
+        self.T = info["n_points"]
+        self.n_near = info["n_near_pairs"]
+        self.n_far = info["n_far_pairs"]
+
+    def close(self):
+        if self.h:
+            sbio_targets_destroy(self.h)
             self.h = None
 
     def __del__(self):

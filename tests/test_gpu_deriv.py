@@ -1,0 +1,128 @@
+"""GPU parity of the normal-derivative operators S' and D' (C ABI
+sbio_apply_laplace_deriv) against the CPU oracle (Theorem 3, eq.
+(dSLevalformula)): FP64 <= 1e-10 normwise vs the oracle's method; mixed
+(FP32 compensated far field) <= 1e-6 vs the GPU FP64 path."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from oracle import deriv as OD
+from oracle import geometry as OG
+from oracle import laplace as OL
+from paper_2506_20809_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+TOL64 = 1e-10
+TOLMIX = 1e-6
+
+
+@pytest.fixture(scope="module")
+def S():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    import __graft_entry__ as G
+
+    G.build()
+    import paper_2506_20809_gb300.sbio as S
+
+    return S
+
+
+@pytest.fixture(scope="module")
+def ctx(S):
+    return S.sbio_ctx_create(0, 0)
+
+
+def gpu_deriv(S, geom, sig, mu, precision=None):
+    if precision is not None:
+        S.sbio_geom_set_precision(geom.h, precision)
+    sg = None if sig is None else torch.from_numpy(np.ascontiguousarray(sig)).cuda()
+    mg = None if mu is None else torch.from_numpy(np.ascontiguousarray(mu)).cuda()
+    Sp = None if sig is None else torch.full((geom.N,), float("nan"), dtype=torch.float64, device="cuda")
+    Dp = None if mu is None else torch.full((geom.N,), float("nan"), dtype=torch.float64, device="cuda")
+    S.sbio_apply_laplace_deriv(geom.h, sg, mg, Sp, Dp)
+    torch.cuda.synchronize()
+    return (None if Sp is None else Sp.cpu().numpy()), (None if Dp is None else Dp.cpu().numpy())
+
+
+@pytest.mark.parametrize("p", [1, 3, 6, 9, 12, 16, 20])
+def test_cluster_fp64(S, ctx, p):
+    """Several spheroids of both kinds close enough for near pairs (near
+    factor 2): self + near gradients + far quadrature, every order p."""
+    s = I.rsa_suspension(4, 0.12, 600 + p, p, ar_range=(1.3, 4.0), name="d4")
+    c = I.config_coefficients(s, p)
+    g = S.Geometry(ctx, s, near_factor=2.0)
+    og = OG.SuspensionGeom.from_suspension(s, near_factor=2.0)
+    Spr, Dpr = OD.DerivOracle(og).apply(c[0], c[1], "method")
+    Spg, Dpg = gpu_deriv(S, g, c[0], c[1], S.SBIO_FP64)
+    assert g.n_near > 0
+    assert OL.normwise_rel_err(Spg, Spr) < TOL64
+    assert OL.normwise_rel_err(Dpg, Dpr) < TOL64
+    # one operator at a time gives the same numbers
+    Sp1, _ = gpu_deriv(S, g, c[0], None)
+    _, Dp1 = gpu_deriv(S, g, None, c[1])
+    assert np.array_equal(Sp1, Spg) and np.array_equal(Dp1, Dpg)
+    g.close()
+
+
+def test_conductor_field(S, ctx):
+    """One spheroid with the equilibrium density: S' = -sigma/2 at every node."""
+    s = I.Suspension(np.array([1], np.int32), np.array([1.3]), np.array([0.6]), np.zeros((1, 3)),
+                     np.array([[0.9, 0.2, -0.3, 0.25]]) / np.linalg.norm([0.9, 0.2, -0.3, 0.25]), 10)
+    sig = np.zeros((1, 121))
+    sig[0, 0] = 1.0
+    g = S.Geometry(ctx, s)
+    og = OG.SuspensionGeom.from_suspension(s)
+    sval, _ = OL.density_values(og.parts[0], sig[0], None)
+    Sp, _ = gpu_deriv(S, g, sig, None, S.SBIO_FP64)
+    assert np.max(np.abs(Sp + 0.5 * sval)) < 1e-12 * np.max(np.abs(sval))
+    g.close()
+
+
+@pytest.fixture(scope="module")
+def stokes100(S, ctx):
+    s = I.config_suspension(3)
+    c = I.config_coefficients(s, 1)
+    g = S.Geometry(ctx, s)
+    yield s, c, g
+    g.close()
+
+
+def test_mixed_vs_fp64(S, stokes100):
+    s, c, g = stokes100
+    Sp64, Dp64 = gpu_deriv(S, g, c[0], c[1], S.SBIO_FP64)
+    Spm, Dpm = gpu_deriv(S, g, c[0], c[1], S.SBIO_MIXED)
+    S.sbio_geom_set_precision(g.h, S.SBIO_FP64)
+    eS, eD = OL.normwise_rel_err(Spm, Sp64), OL.normwise_rel_err(Dpm, Dp64)
+    print(f"deriv mixed vs fp64: S' {eS:.3e} D' {eD:.3e}")
+    assert eS < TOLMIX and eD < TOLMIX
+
+
+def test_sampled_against_oracle(S, stokes100):
+    """100 spheroids, p = 12: sampled nodes against the oracle's method."""
+    s, c, g = stokes100
+    Spg, Dpg = gpu_deriv(S, g, c[0], c[1], S.SBIO_FP64)
+    og = OG.SuspensionGeom.from_suspension(s)
+    tg = np.sort(np.random.default_rng(11).choice(g.N, 120, replace=False))
+    Spr, Dpr = OD.DerivOracle(og).apply(c[0], c[1], "method", targets=tg)
+    assert np.max(np.abs(Spg[tg] - Spr)) / np.max(np.abs(Spg)) < TOL64
+    assert np.max(np.abs(Dpg[tg] - Dpr)) / np.max(np.abs(Dpg)) < TOL64
+
+
+def test_invalid_arguments(S, ctx):
+    s = I.rsa_suspension(2, 0.1, 3, 22)
+    g = S.Geometry(ctx, s)
+    c = I.config_coefficients(s, 0)
+    with pytest.raises(S.SbioError) as e:
+        gpu_deriv(S, g, c[0], c[1])
+    assert e.value.code == S.SBIO_ENOTSUP
+    g.close()
+    s = I.rsa_suspension(2, 0.1, 3, 4)
+    g = S.Geometry(ctx, s)
+    x = torch.zeros(2 * 25, dtype=torch.float64, device="cuda")
+    out = torch.zeros(g.N, dtype=torch.float64, device="cuda")
+    with pytest.raises(S.SbioError) as e:
+        S.sbio_apply_laplace_deriv(g.h, x, None, None, out)
+    assert e.value.code == S.SBIO_EINVAL
+    g.close()
