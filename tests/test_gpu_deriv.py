@@ -59,10 +59,11 @@ def test_cluster_fp64(S, ctx, p):
     assert g.n_near > 0
     assert OL.normwise_rel_err(Spg, Spr) < TOL64
     assert OL.normwise_rel_err(Dpg, Dpr) < TOL64
-    # one operator at a time gives the same numbers
+    # one operator at a time gives the same numbers (up to the order of the
+    # atomic accumulation)
     Sp1, _ = gpu_deriv(S, g, c[0], None)
     _, Dp1 = gpu_deriv(S, g, None, c[1])
-    assert np.array_equal(Sp1, Spg) and np.array_equal(Dp1, Dpg)
+    assert OL.normwise_rel_err(Sp1, Spg) < 1e-13 and OL.normwise_rel_err(Dp1, Dpg) < 1e-13
     g.close()
 
 
