@@ -45,6 +45,9 @@ def near_flop_per_pair(p: int) -> int:
     nm = (p + 1) * (p + 2) // 2
     return 4 * (p + 1) ** 2 + nm * (1 + 3 + 4) + 12 * (p + 1)
 METRIC = "BIO applies/s (Laplace S+D, all surface nodes)"
+# far pair of S' + D': 3 sub, 5 (r^2), 2 (r^-2, r^-3), 5 (r.nu_x), 3 (S' product
+# and FMA), 5 (d.r), 5 (d.nu_x), 2 (products), 2 + 2 (the two FMAs) = 34
+DERIV_FAR_FLOP_PER_PAIR = 34
 
 
 def parse():
@@ -58,7 +61,8 @@ def parse():
     ap.add_argument("--no-fp64-context", action="store_true")
     ap.add_argument("--oracle-sample", type=int, default=48, help="targets in the oracle's timed sample")
     ap.add_argument("--far-shape", default="", help="TT,SPLITS: fixed far-field launch shape (skips the autotuner)")
-    ap.add_argument("--workload", default="poly200", choices=["poly200", "stokes100", "batch64", "serve"])
+    ap.add_argument("--workload", default="poly200",
+                    choices=["poly200", "stokes100", "batch64", "serve", "deriv200", "targets200"])
     ap.add_argument("--rates", default="50,100,200,500,1000,2000", help="serve: arrival rates (req/s)")
     ap.add_argument("--requests", type=int, default=48, help="serve: requests per rate")
     ap.add_argument("--slots", type=int, default=4, help="serve: concurrent request slots")
@@ -630,6 +634,139 @@ def run_serve(args, ws, rank, lrank):
         print(json.dumps(line), flush=True)
 
 
+def run_deriv200(args, ws, rank, lrank):
+    """S' + D' (normal derivatives) at all nodes of the 200-spheroid, p = 16
+    suspension, mixed precision, L2 flushed before every step."""
+    import torch
+
+    import __graft_entry__ as GE
+
+    GE.build()
+    from paper_2506_20809_gb300 import inputs as I
+    from paper_2506_20809_gb300 import sbio as S
+
+    torch.cuda.set_device(lrank)
+    susp = I.config_suspension(2)
+    c = I.config_coefficients(susp, 0)
+    ctx = S.sbio_ctx_create(lrank, 0)
+    g = S.Geometry(ctx, susp, precision=S.SBIO_MIXED)
+    S.sbio_geom_autotune(g.h)                   # near CTA cap for the overlapped near field
+    sg, mg = torch.from_numpy(c[0]).cuda(), torch.from_numpy(c[1]).cuda()
+    Sp = torch.empty(g.N, dtype=torch.float64, device="cuda")
+    Dp = torch.empty_like(Sp)
+    st = torch.cuda.current_stream()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    for _ in range(args.warmup):
+        S.sbio_apply_laplace_deriv(g.h, sg, mg, Sp, Dp)
+    clocks = ClockSampler(lrank)
+    clocks.start()
+    ms = []
+    l0 = S.sbio_launch_count()
+    for _ in range(args.steps):
+        flush.zero_()
+        ms.append(_event_time(st, lambda: S.sbio_apply_laplace_deriv(g.h, sg, mg, Sp, Dp)))
+    launches = S.sbio_launch_count() - l0
+    clk = clocks.stop()
+    S.sbio_geom_enable_timing(g.h, True)
+    ph = []
+    for _ in range(min(args.steps, 10)):
+        flush.zero_()
+        S.sbio_apply_laplace_deriv(g.h, sg, mg, Sp, Dp)
+        ph.append(S.sbio_geom_phase_times(g.h))
+    S.sbio_geom_enable_timing(g.h, False)
+    spm, dpm = Sp.clone(), Dp.clone()
+    S.sbio_geom_set_precision(g.h, S.SBIO_FP64)
+    S.sbio_apply_laplace_deriv(g.h, sg, mg, Sp, Dp)
+    t64 = _event_time(st, lambda: S.sbio_apply_laplace_deriv(g.h, sg, mg, Sp, Dp))
+    err = {"Sp": float((spm - Sp).abs().max() / Sp.abs().max()), "Dp": float((dpm - Dp).abs().max() / Dp.abs().max())}
+    far_ms = statistics.mean(x[2] for x in ph)
+    ach = DERIV_FAR_FLOP_PER_PAIR * g.n_far / (far_ms * 1e-3) / 1e12
+    line = {"metric": "BIO applies/s (Laplace S'+D', all surface nodes)", "value": 1e3 / statistics.mean(ms),
+            "unit": "applies/s", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": statistics.mean(ms), "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32+f64", "data": "synthetic",
+            "config": {"workload": "poly200_p16_laplace_SpDp", "M": susp.M, "p": susp.p, "targets": g.N,
+                       "near_pairs": g.n_near, "far_pairs_per_apply": g.n_far,
+                       "l2": "flushed (256 MiB write) before each step"},
+            "phase_ms": {"self": statistics.mean(x[0] for x in ph), "near": statistics.mean(x[1] for x in ph),
+                         "far": far_ms},
+            "roofline": {"kernel": "far_deriv_mixed_kernel", "bound": "alu", "achieved": ach,
+                         "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": ach / FP32_PEAK_TFLOPS,
+                         "flop_per_pair": DERIV_FAR_FLOP_PER_PAIR, "traffic": None},
+            "fp64_gpu_applies_per_s": 1e3 / t64, "rel_err_vs_fp64_gpu": err, "gpu_launches": int(launches),
+            "clocks": clk}
+    g.close()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+def run_targets200(args, ws, rank, lrank):
+    """S + D of the 200-spheroid, p = 16 suspension at about 124,000 points:
+    shells at distances 1e-1 .. 1e-6 from every surface (20 points per
+    spheroid and distance) plus 100,000 points spread through the box;
+    mixed precision, L2 flushed before every step."""
+    import torch
+
+    import __graft_entry__ as GE
+
+    GE.build()
+    from paper_2506_20809_gb300 import inputs as I
+    from paper_2506_20809_gb300 import sbio as S
+
+    torch.cuda.set_device(lrank)
+    susp = I.config_suspension(2)
+    c = I.config_coefficients(susp, 0)
+    X = I.shell_points(susp, per_particle=20, seed=0, far_points=100000)
+    ctx = S.sbio_ctx_create(lrank, 0)
+    g = S.Geometry(ctx, susp, precision=S.SBIO_MIXED)
+    tune = S.sbio_geom_autotune(g.h)
+    t0 = time.perf_counter()
+    ts = S.TargetSet(g, X)
+    setup_ms = (time.perf_counter() - t0) * 1e3
+    sg, mg = torch.from_numpy(c[0]).cuda(), torch.from_numpy(c[1]).cuda()
+    So = torch.empty(ts.T, dtype=torch.float64, device="cuda")
+    Do = torch.empty_like(So)
+    st = torch.cuda.current_stream()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    for _ in range(args.warmup):
+        S.sbio_eval_targets(ts.h, sg, mg, So, Do)
+    clocks = ClockSampler(lrank)
+    clocks.start()
+    ms = []
+    l0 = S.sbio_launch_count()
+    for _ in range(args.steps):
+        flush.zero_()
+        ms.append(_event_time(st, lambda: S.sbio_eval_targets(ts.h, sg, mg, So, Do)))
+    launches = S.sbio_launch_count() - l0
+    clk = clocks.stop()
+    som, dom = So.clone(), Do.clone()
+    S.sbio_geom_set_precision(g.h, S.SBIO_FP64)
+    S.sbio_eval_targets(ts.h, sg, mg, So, Do)
+    t64 = _event_time(st, lambda: S.sbio_eval_targets(ts.h, sg, mg, So, Do))
+    err = {"S": float((som - So).abs().max() / So.abs().max()), "D": float((dom - Do).abs().max() / Do.abs().max())}
+    mean = statistics.mean(ms)
+    ach = 19 * ts.n_far / (mean * 1e-3) / 1e12
+    line = {"metric": "point evaluations/s (Laplace S+D at arbitrary points)", "value": ts.T * 1e3 / mean,
+            "unit": "points/s", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup, "ms_per_step": mean,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64",
+            "data": "synthetic",
+            "config": {"workload": "targets200_p16", "M": susp.M, "p": susp.p, "points": ts.T,
+                       "near_pairs": ts.n_near, "far_pairs": ts.n_far,
+                       "points_recipe": "shells at 1e-1..1e-6 (20 per spheroid and distance) + 100,000 in the box",
+                       "far_launch": {"targets_per_thread": tune[0], "source_splits": tune[1]},
+                       "l2": "flushed (256 MiB write) before each step"},
+            "evaluations_per_s": 1e3 / mean, "target_set_setup_ms": setup_ms,
+            "roofline": {"kernel": "whole evaluation (far_mixed_kernel dominant)", "bound": "alu",
+                         "achieved": ach, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": ach / FP32_PEAK_TFLOPS,
+                         "traffic": None},
+            "fp64_gpu_points_per_s": ts.T * 1e3 / t64, "rel_err_vs_fp64_gpu": err, "gpu_launches": int(launches),
+            "clocks": clk}
+    ts.close()
+    g.close()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     ws, rank, lrank = dist_setup()
@@ -641,6 +778,10 @@ def main():
         run_batch64(args, ws, rank, lrank)
     elif args.workload == "serve":
         run_serve(args, ws, rank, lrank)
+    elif args.workload == "deriv200":
+        run_deriv200(args, ws, rank, lrank)
+    elif args.workload == "targets200":
+        run_targets200(args, ws, rank, lrank)
     else:
         run_ours(args, ws, rank, lrank)
     if ws > 1:

@@ -228,14 +228,26 @@ int sbio_eval_targets(sbio_targets* ts, const double* sigma_tilde, const double*
   // far sources and near coefficients of these densities (no self output)
   int rc = launch_synth_mode(g, sigma_tilde, mu_hat, nullptr, nullptr, 0, st);
   if (rc) return rc;
-  if (ts->n_pairs > 0) {
-    near_launcher nl = near_for_p(h.p);
-    if (!nl) return set_error(SBIO_ENOTSUP, "no near-field kernel for p = %d", h.p);
+  near_launcher nl = near_for_p(h.p);
+  if (ts->n_pairs > 0 && !nl) return set_error(SBIO_ENOTSUP, "no near-field kernel for p = %d", h.p);
+  // the FP64 near pairs run beside the FP32 far field on the geometry's
+  // high-priority stream (capped CTAs per SM), as in the on-surface apply
+  const bool fork = g->overlap && !g->timing && g->near_stream && ts->n_pairs > 0;
+  if (fork) {
+    SBIO_CUDA_TRY(cudaEventRecord(g->ev_fork, st));
+    SBIO_CUDA_TRY(cudaStreamWaitEvent(g->near_stream, g->ev_fork, 0));
+    ts->view.near_grid_cap = h.near_ctas_per_sm > 0 ? h.near_ctas_per_sm * sm_count() : 0;
+    nl(ts->view, ts->n_pro, ts->n_pairs, ts->view.inv, S_out, D_out, g->near_stream);
+    ts->view.near_grid_cap = 0;
+    SBIO_CUDA_TRY(cudaGetLastError());
+    SBIO_CUDA_TRY(cudaEventRecord(g->ev_join, g->near_stream));
+  } else if (ts->n_pairs > 0) {
     nl(ts->view, ts->n_pro, ts->n_pairs, ts->view.inv, S_out, D_out, st);
     SBIO_CUDA_TRY(cudaGetLastError());
   }
   launch_far_on(ts->view, h, ts->T, S_out, D_out, st);
   SBIO_CUDA_TRY(cudaGetLastError());
+  if (fork) SBIO_CUDA_TRY(cudaStreamWaitEvent(st, g->ev_join, 0));
   return SBIO_OK;
 }
 
