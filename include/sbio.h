@@ -295,6 +295,66 @@ int sbio_targets_info(const sbio_targets* ts, int64_t* n_points, int64_t* n_near
 int sbio_eval_targets(sbio_targets* ts, const double* sigma_tilde, const double* mu_hat, double* S_out,
                       double* D_out, void* stream);
 
+
+/* ---- forward transform and exterior boundary-value solves (Sec. 2.3,
+ * Sec. 5.1) -----------------------------------------------------------------
+ * Forward transform: coefficients of node values f (device, N, the node
+ * layout of the outputs), f^_nm = sum_j w_j (2 pi / n_phi) sum_k f_jk Y_nm,
+ * exact for band-limited f of degree <= p; modified != 0 gives the
+ * modified-basis coefficients (those of f sqrt(u0^2 -+ v^2), Sec. 3.2).
+ * coef_out: device, M x (p+1)^2.  Asynchronous. */
+int sbio_forward_transform(sbio_geom* g, const double* values, int32_t modified, double* coef_out, void* stream);
+
+/* Completion terms of the Dirichlet formulation (Sec. 5.1): C_I places at
+ * each centre a charge equal to int sigma_i dS with kernel 1/|x - c_i| (as
+ * printed, no 1/(4 pi)); S adds the single layer of the same density; the
+ * ETA forms scale particle i's term by eta_i from the paper's table of
+ * heuristic scalings (eps = 1/aspect ratio; C_I: eps / area of the spheroid
+ * with major semi-axis 1, 0.06 for oblates with aspect ratio > 3; S: prolate
+ * 0.5 or 1/(2 eps log(1/eps)) above aspect ratio 3, oblate 1/(4 eps) + 1/4 or
+ * 1 above 3). */
+#define SBIO_COMPLETION_CI 0
+#define SBIO_COMPLETION_ETA_CI 1
+#define SBIO_COMPLETION_S 2
+#define SBIO_COMPLETION_ETA_S 3
+
+typedef struct {
+  int32_t iterations;   /* Arnoldi steps (operator applications, not counting residual checks) */
+  int32_t restarts;     /* completed restart cycles that had not converged */
+  int32_t converged;    /* 1 if the true relative residual reached tol */
+  double rel_residual;  /* ||b - K x|| / ||b|| at exit (coefficient space) */
+  double ms;            /* wall time of the call */
+} sbio_solve_info;
+
+/* Exterior Dirichlet problem with the completed double layer: finds sigma
+ * with 1/2 sigma + D[sigma] + C[sigma] = f on every surface, so that
+ * u = D[sigma] + C[sigma] solves it in the fluid.  Solved in coefficient
+ * space (unknown: the plain coefficients of sigma; operator: the forward
+ * transform of the node values of D + C; right-hand side: the transform of
+ * f) by restarted GMRES(restart) from zero to relative residual tol, at most
+ * max_iter Arnoldi steps.  f_nodes: device, N.  Outputs (device): mu_hat_out
+ * M x (p+1)^2 = sigma's coefficients; sigma_tilde_out (M x (p+1)^2, may be
+ * NULL) = modified coefficients of the S completion term (zeros for C_I),
+ * charges_out (M, may be NULL) = the C_I charges (zeros for S), so that
+ * u(x) = D[mu_hat](x) + S[sigma_tilde](x) + sum_i charges_i/|x - c_i| (the
+ * first two through sbio_eval_targets).  Uses the geometry's precision and
+ * workspaces; allocates its Krylov basis ((restart+1) M (p+1)^2 doubles,
+ * stream-ordered, charged to the context budget: SBIO_ENOMEM); synchronises
+ * `stream` (the iteration is driven from the host).  info may be NULL;
+ * non-convergence is reported in info, not as an error. */
+int sbio_solve_dirichlet(sbio_geom* g, const double* f_nodes, int32_t completion, double tol, int32_t max_iter,
+                         int32_t restart, double* mu_hat_out, double* sigma_tilde_out, double* charges_out,
+                         sbio_solve_info* info, void* stream);
+
+/* Exterior Neumann problem with the single layer: finds rho with
+ * -1/2 rho + S'[rho] = g on every surface (u = S[rho]); unknown and output
+ * rho_tilde_out: device, M x (p+1)^2 modified coefficients (the input
+ * convention of the S apply); right-hand side g_nodes: device, N (the outward
+ * normal derivative of u).  As sbio_solve_dirichlet otherwise; SBIO_ENOTSUP
+ * for p > 20. */
+int sbio_solve_neumann(sbio_geom* g, const double* g_nodes, double tol, int32_t max_iter, int32_t restart,
+                       double* rho_tilde_out, sbio_solve_info* info, void* stream);
+
 /* ---- batched apply over many suspensions ------------------------------
  * A batch groups resident geometries (any mix of M and p, all in SBIO_MIXED
  * mode, same context).  One batch apply computes S[sigma_s] and D[mu_s] for

@@ -370,6 +370,7 @@ static int build_device(sbio_geom* g) {
         ptab[(size_t)j * nm + nm_index(n, m)] = std::sqrt((2.0 * n + 1.0) / (4.0 * kPi) * kfact(n, m)) * tmp[nm_index(n, m)];
   }
   if ((rc = upload(g, &d.ptab, ptab.data(), ptab.size(), "Legendre table"))) return rc;
+  if ((rc = upload(g, &d.glw, gw.data(), gw.size(), "GL weights"))) return rc;
   std::vector<double> trig((size_t)h.n_phi * (p + 1) * 2);
   for (int k = 0; k < h.n_phi; ++k)
     for (int m = 0; m <= p; ++m) {

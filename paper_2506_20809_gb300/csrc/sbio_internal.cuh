@@ -28,6 +28,7 @@ struct DevGeom {
   double* nrm = nullptr;         // N x 3 outward unit normals
   double* w = nullptr;           // N quadrature weights
   double* ptab = nullptr;        // (p+1) x nm_count(p): N_n^m Pbar_n^m(v_j)
+  double* glw = nullptr;         // p+1 Gauss-Legendre weights of the v nodes
   double* trig = nullptr;        // n_phi x (p+1) x 2: cos(m phi_k), sin(m phi_k)
   double* sqrtw = nullptr;       // M x (p+1): sqrt(u0^2 + sgn v_j^2)
   double* mult = nullptr;        // M x 4 x nm_count(p): extS, extD, selfS, selfD
@@ -194,6 +195,8 @@ void split_f32(double v, float& hi, float& lo);
 // *inside set when the level set (rho/A)^2 + (z/C)^2 is below 1 - tol
 double spheroid_distance_local(const PartGeom& P, double x, double y, double z, double tol, bool* inside);
 int launch_stokes_far(sbio_geom* g, double* u, cudaStream_t st);
+int launch_laplace_deriv(sbio_geom* g, const double* sigma, const double* mu, double* Sp, double* Dp,
+                         cudaStream_t st);
 
 // Launch-shape search shared by the Laplace and Stokes autotuners: times
 // far(g, out, st) for every targets-per-thread form and a ladder of source

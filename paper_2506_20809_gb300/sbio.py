@@ -55,6 +55,16 @@ class sbio_request(C.Structure):
 SBIO_OP_LAPLACE = 0
 SBIO_OP_STOKES = 1
 
+SBIO_COMPLETION_CI = 0
+SBIO_COMPLETION_ETA_CI = 1
+SBIO_COMPLETION_S = 2
+SBIO_COMPLETION_ETA_S = 3
+
+
+class sbio_solve_info(C.Structure):
+    _fields_ = [("iterations", C.c_int32), ("restarts", C.c_int32), ("converged", C.c_int32),
+                ("rel_residual", C.c_double), ("ms", C.c_double)]
+
 
 class SbioError(RuntimeError):
     def __init__(self, code, msg):
@@ -101,6 +111,11 @@ _SIGS = {
     "sbio_apply_stokes_sl": (C.c_int, [_vp, _vp, _vp, _vp]),
     "sbio_apply_stokes_sl_host": (C.c_int, [_vp, _vp, _vp, _vp]),
     "sbio_apply_laplace_deriv": (C.c_int, [_vp, _vp, _vp, _vp, _vp, _vp]),
+    "sbio_forward_transform": (C.c_int, [_vp, _vp, C.c_int32, _vp, _vp]),
+    "sbio_solve_dirichlet": (C.c_int, [_vp, _vp, C.c_int32, C.c_double, C.c_int32, C.c_int32, _vp, _vp, _vp,
+                                       C.POINTER(sbio_solve_info), _vp]),
+    "sbio_solve_neumann": (C.c_int, [_vp, _vp, C.c_double, C.c_int32, C.c_int32, _vp,
+                                     C.POINTER(sbio_solve_info), _vp]),
     "sbio_targets_create": (C.c_int, [_vp, _vp, C.c_int64, _vp, C.POINTER(_vp)]),
     "sbio_targets_destroy": (C.c_int, [_vp]),
     "sbio_targets_info": (C.c_int, [_vp, C.POINTER(C.c_int64), C.POINTER(C.c_int64), C.POINTER(C.c_int64),
@@ -315,6 +330,33 @@ def sbio_apply_laplace_deriv(g, sigma_tilde, mu_hat, Sp_out, Dp_out, stream=None
     """S'[sigma] and D'[mu] at all nodes (device tensors; either input may be None)."""
     _check(_lib.sbio_apply_laplace_deriv(g, _ptr(sigma_tilde), _ptr(mu_hat), _ptr(Sp_out), _ptr(Dp_out),
                                          _stream(stream)))
+
+
+def sbio_forward_transform(g, values, coef_out, modified=False, stream=None):
+    """Coefficients (device, M x (p+1)^2) of node values (device, N)."""
+    _check(_lib.sbio_forward_transform(g, _ptr(values), 1 if modified else 0, _ptr(coef_out), _stream(stream)))
+
+
+def _info_dict(info):
+    return {"iterations": info.iterations, "restarts": info.restarts, "converged": bool(info.converged),
+            "rel_residual": info.rel_residual, "ms": info.ms}
+
+
+def sbio_solve_dirichlet(g, f_nodes, mu_hat_out, completion=SBIO_COMPLETION_ETA_S, tol=1e-10, max_iter=500,
+                         restart=50, sigma_tilde_out=None, charges_out=None, stream=None):
+    """Completed double-layer Dirichlet solve; returns the solver info dict."""
+    info = sbio_solve_info()
+    _check(_lib.sbio_solve_dirichlet(g, _ptr(f_nodes), completion, tol, max_iter, restart, _ptr(mu_hat_out),
+                                     _ptr(sigma_tilde_out), _ptr(charges_out), C.byref(info), _stream(stream)))
+    return _info_dict(info)
+
+
+def sbio_solve_neumann(g, g_nodes, rho_tilde_out, tol=1e-10, max_iter=500, restart=50, stream=None):
+    """Single-layer Neumann solve; returns the solver info dict."""
+    info = sbio_solve_info()
+    _check(_lib.sbio_solve_neumann(g, _ptr(g_nodes), tol, max_iter, restart, _ptr(rho_tilde_out), C.byref(info),
+                                   _stream(stream)))
+    return _info_dict(info)
 
 
 def sbio_targets_create(g, xyz, stream=None):
