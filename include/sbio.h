@@ -341,7 +341,9 @@ typedef struct {
  * workspaces; allocates its Krylov basis ((restart+1) M (p+1)^2 doubles,
  * stream-ordered, charged to the context budget: SBIO_ENOMEM); synchronises
  * `stream` (the iteration is driven from the host).  info may be NULL;
- * non-convergence is reported in info, not as an error. */
+ * non-convergence is reported in info, not as an error.  In SBIO_MIXED the
+ * operator carries the far field's FP32 rounding (about 1e-7 relative), which
+ * bounds the reachable residual: use tol >= 1e-6 there. */
 int sbio_solve_dirichlet(sbio_geom* g, const double* f_nodes, int32_t completion, double tol, int32_t max_iter,
                          int32_t restart, double* mu_hat_out, double* sigma_tilde_out, double* charges_out,
                          sbio_solve_info* info, void* stream);

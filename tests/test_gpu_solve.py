@@ -162,10 +162,13 @@ def test_mixed_precision_solve(S, ctx):
     g = S.Geometry(ctx, s)
     xyz, _, _ = S.sbio_geom_nodes(g.h)
     out = []
-    for prec in (S.SBIO_FP64, S.SBIO_MIXED):
+    # the mixed operator carries FP32 rounding (~1e-7 relative), which bounds
+    # the residual GMRES can reach with it
+    for prec, tol in ((S.SBIO_FP64, 1e-10), (S.SBIO_MIXED, 1e-6)):
         S.sbio_geom_set_precision(g.h, prec)
         mu = torch.empty((3, 121), dtype=torch.float64, device="cuda")
-        info = S.sbio_solve_dirichlet(g.h, dev(f_of(xs, qs, xyz)), mu, COMP["etaS"], tol=1e-10)
+        info = S.sbio_solve_dirichlet(g.h, dev(f_of(xs, qs, xyz)), mu, COMP["etaS"], tol=tol)
+        print(prec, info)
         assert info["converged"]
         out.append(mu.cpu().numpy())
     assert rel(out[1], out[0]) < 1e-5
