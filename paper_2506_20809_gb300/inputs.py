@@ -364,3 +364,14 @@ def shell_points(s: Suspension, distances=(1e-1, 1e-2, 1e-3, 1e-4, 1e-5, 1e-6), 
         f = (xl[:, 0] ** 2 + xl[:, 1] ** 2) / s.A[i] ** 2 + xl[:, 2] ** 2 / s.C[i] ** 2
         keep &= f > 1.0 + 1e-9
     return np.ascontiguousarray(X[keep])
+
+
+def interior_charges(s: Suspension, per_particle: int = 2, seed: int = 0, spread: float = 0.05):
+    """Point charges inside the particles, as in the paper's boundary-value
+    tests: `per_particle` charges per spheroid at centre + R (U(-spread,
+    spread)^3 * (A, A, C)), strengths U(-0.5, 0.5).  Returns (xs (K, 3), qs (K,))."""
+    rng = np.random.default_rng([seed, 314159])
+    R = _quat_to_matrix(s.quat)
+    xs = np.concatenate([s.center[i] + (rng.uniform(-spread, spread, (per_particle, 3))
+                                        * np.array([s.A[i], s.A[i], s.C[i]])) @ R[i].T for i in range(s.M)])
+    return xs, rng.uniform(-0.5, 0.5, len(xs))
