@@ -73,3 +73,18 @@ def brute_stokeslet(kind, A, C, center, quat, p, x, f_t, nv=160, nphi=320, chunk
         rf = np.einsum("tjk,jk->tj", r, f)
         U[c0:c0 + chunk] = (np.einsum("jk,tj->tk", f, 1.0 / d) + np.einsum("tjk,tj->tk", r, rf / d ** 3)) / (8 * math.pi)
     return U
+
+
+def brute_stokes_pressure(kind, A, C, center, quat, p, x, f_t, nv=160, nphi=320, chunk=64):
+    """Pressure of the Stokes single layer, p(x) = int P(x, y) . f(y) dS(y)
+    with the printed kernel P = r / (4 pi |r|^3), r = x - y."""
+    V, PHI, W, y, ny, sw = fine_surface(kind, A, C, center, quat, nv, nphi)
+    Y = L.real_Y(V, PHI, p)
+    f = np.stack([(Y @ f_t[k]) / sw for k in range(3)], axis=-1) * W[:, None]
+    x = np.atleast_2d(x)
+    out = np.zeros(len(x))
+    for c0 in range(0, len(x), chunk):
+        r = x[c0:c0 + chunk, None, :] - y[None, :, :]
+        d = np.linalg.norm(r, axis=-1)
+        out[c0:c0 + chunk] = (np.einsum("tjk,jk->tj", r, f) / d ** 3).sum(1) / (4 * math.pi)
+    return out

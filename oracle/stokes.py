@@ -172,6 +172,54 @@ class StokesOracle:
                 U[sel_far] += stokeslet_quadrature(P, f_t[i], g.x[tgt[sel_far]])
         return U
 
+    def eval_points(self, X, f_t, mode="method"):
+        """Velocity (T, 3) and pressure (T,) of the single layer at arbitrary
+        points in the fluid (Sec. 4.1 particle-to-target algorithm with
+        eq. (stokes)).  Pressure p = -sum_j d_j S[f_j]: the printed pressure
+        kernel r / (4 pi |r|^3); the printed identity in terms of gradients of
+        S carries the opposite sign (d_j (1/r) = -r_j / r^3)."""
+        g = self.g
+        p = g.p
+        X = np.atleast_2d(np.asarray(X, dtype=np.float64))
+        near = g.point_near_matrix(X)
+        if mode == "exact":
+            near = np.ones_like(near)
+        U = np.zeros((len(X), 3))
+        Pr = np.zeros(len(X))
+        for i, P in enumerate(g.parts):
+            sel = near[:, i]
+            if np.any(sel):
+                x = X[sel]
+                xc = x - P.center
+                cs = [self._ext_coef(i, np.pad(f_t[i, k], (0, (p + 2) ** 2 - (p + 1) ** 2)), p + 1) for k in range(3)]
+                cy = self._ext_coef(i, ydotf_modified_coefficients(P, f_t[i], p), p + 1)
+                Fk, Gk = zip(*[solid_value_and_gradient(P, cs[k], x, p + 1) for k in range(3)])
+                _, Gy = solid_value_and_gradient(P, cy, x, p + 1)
+                for k in range(3):
+                    val = Fk[k] + Gy[:, k]
+                    for j in range(3):
+                        val = val - xc[:, j] * Gk[j][:, k]
+                    U[sel, k] += 0.5 * val
+                Pr[sel] -= Gk[0][:, 0] + Gk[1][:, 1] + Gk[2][:, 2]
+            far = ~sel
+            if np.any(far):
+                U[far] += stokeslet_quadrature(P, f_t[i], X[far])
+                Pr[far] += pressure_quadrature(P, f_t[i], X[far])
+        return U, Pr
+
+
+def pressure_quadrature(part, f_t, x, chunk=2048):
+    """sum_j w_j P(x, y_j) . f(y_j), P = r / (4 pi |r|^3)."""
+    Y = L.real_Y(part.v, part.phi, part.p)
+    f = np.stack([(Y @ f_t[k]) / part.sqrt_w for k in range(3)], -1) * part.w[:, None]
+    x = np.atleast_2d(x)
+    out = np.zeros(len(x))
+    for c0 in range(0, len(x), chunk):
+        r = x[c0:c0 + chunk, None, :] - part.x[None]
+        d = np.linalg.norm(r, axis=-1)
+        out[c0:c0 + chunk] = (np.einsum("tjk,jk->tj", r, f) / d ** 3).sum(1) / (4 * math.pi)
+    return out
+
 
 def stokeslet_quadrature(part, f_t, x, chunk=2048):
     """sum_j w_j G_stk(x, y_j) f(y_j) over the particle's nodes."""
