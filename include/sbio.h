@@ -295,6 +295,16 @@ int sbio_targets_info(const sbio_targets* ts, int64_t* n_points, int64_t* n_near
 int sbio_eval_targets(sbio_targets* ts, const double* sigma_tilde, const double* mu_hat, double* S_out,
                       double* D_out, void* stream);
 
+/* Stokes single layer (viscosity 1) at the set's points (Sec. 4.3 with the
+ * particle-to-target algorithm): u_out (device, T x 3) = S_stk[f](x_t) by
+ * eq. (stokes) for near pairs and the Stokeslet quadrature otherwise;
+ * p_out (device, T, may be NULL) = the pressure with the printed kernel
+ * P = r / (4 pi |r|^3), i.e. -sum_j d_j S[f_j] for near pairs (the printed
+ * identity in terms of gradients of S has the opposite sign).  f_tilde as in
+ * sbio_apply_stokes_sl.  Outputs overwritten; SBIO_ENOTSUP for p > 20;
+ * stream-ordered with the geometry's other calls.  Asynchronous. */
+int sbio_eval_targets_stokes(sbio_targets* ts, const double* f_tilde, double* u_out, double* p_out, void* stream);
+
 
 /* ---- forward transform and exterior boundary-value solves (Sec. 2.3,
  * Sec. 5.1) -----------------------------------------------------------------

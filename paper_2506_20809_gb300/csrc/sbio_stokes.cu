@@ -433,37 +433,58 @@ __global__ void __launch_bounds__(kFarTile) stokes_far_mixed_kernel(const int4* 
 }
 
 template <int TT, bool PK>
-static void launch_stokes_far_tt(const DevGeom& d, const GeomHost& h, double* u, cudaStream_t st) {
+static void launch_stokes_far_tt(const DevGeom& d, const GeomHost& h, int64_t NT, double* u, cudaStream_t st) {
   const int nt = (int)h.tiles.size();
-  const int64_t tb = (h.N + (int64_t)kFarTile * TT - 1) / ((int64_t)kFarTile * TT);
+  const int64_t tb = (NT + (int64_t)kFarTile * TT - 1) / ((int64_t)kFarTile * TT);
   const dim3 grid((unsigned)tb, (unsigned)far_split_count(tb, nt, h.st_far_splits));
   stokes_far_mixed_kernel<TT, PK><<<grid, kFarTile, 0, st>>>(d.tiles, nt, d.st_src32, d.tgt32, d.cen32, d.skip_ptr,
-                                                             d.skip_idx, h.N, u);
+                                                             d.skip_idx, NT, u);
 }
 
 // The Stokeslet far field alone (sources written by the prep kernel of the
-// same or an earlier apply), in the geometry's precision and Stokes launch shape.
-int launch_stokes_far(sbio_geom* g, double* u, cudaStream_t st) {
-  const GeomHost& h = g->h;
-  const DevGeom& d = g->d;
+// same or an earlier apply) at the NT targets of `d`, in the geometry's
+// precision and Stokes launch shape.
+int launch_stokes_far_on(const DevGeom& d, const GeomHost& h, int64_t NT, double* u, cudaStream_t st) {
+  if (NT <= 0) return SBIO_OK;
   const int nt = (int)h.tiles.size();
   if (h.precision == SBIO_FP64) {
-    const int64_t tb = (h.N + kFarTile - 1) / kFarTile;
+    const int64_t tb = (NT + kFarTile - 1) / kFarTile;
     const dim3 grid((unsigned)tb, (unsigned)far_split_count(tb, nt, h.st_far_splits));
     stokes_far_fp64_kernel<<<grid, kFarTile, 0, st>>>(d.tiles, nt, d.st_src64, d.xyz, d.parts, d.skip_ptr,
-                                                      d.skip_idx, h.N, u);
+                                                      d.skip_idx, NT, u);
   } else {
     // targets per thread, packed f32x2 form if negative
     switch (h.st_far_tt) {
-      case 1: launch_stokes_far_tt<1, false>(d, h, u, st); break;
-      case 4: launch_stokes_far_tt<4, false>(d, h, u, st); break;
-      case 8: launch_stokes_far_tt<8, false>(d, h, u, st); break;
-      case -2: launch_stokes_far_tt<2, true>(d, h, u, st); break;
-      case -4: launch_stokes_far_tt<4, true>(d, h, u, st); break;
-      case -8: launch_stokes_far_tt<8, true>(d, h, u, st); break;
-      default: launch_stokes_far_tt<2, false>(d, h, u, st); break;
+      case 1: launch_stokes_far_tt<1, false>(d, h, NT, u, st); break;
+      case 4: launch_stokes_far_tt<4, false>(d, h, NT, u, st); break;
+      case 8: launch_stokes_far_tt<8, false>(d, h, NT, u, st); break;
+      case -2: launch_stokes_far_tt<2, true>(d, h, NT, u, st); break;
+      case -4: launch_stokes_far_tt<4, true>(d, h, NT, u, st); break;
+      case -8: launch_stokes_far_tt<8, true>(d, h, NT, u, st); break;
+      default: launch_stokes_far_tt<2, false>(d, h, NT, u, st); break;
     }
   }
+  count_launch();
+  SBIO_CUDA_TRY(cudaGetLastError());
+  return SBIO_OK;
+}
+
+int launch_stokes_far(sbio_geom* g, double* u, cudaStream_t st) { return launch_stokes_far_on(g->d, g->h, g->h.N, u, st); }
+
+// Per-apply Stokes sources: the y.f coefficients at order p+1 and the folded
+// near coefficients (st_coef), and the Stokeslet far sources (st_src64/32).
+int launch_stokes_prep(sbio_geom* g, const double* f, cudaStream_t st) {
+  const GeomHost& h = g->h;
+  const DevGeom& d = g->d;
+  const int p = h.p;
+  const int p1 = p + 1, nc = (p + 1) * (p + 1), nc1 = (p1 + 1) * (p1 + 1), mw = 2 * p + 1, mw1 = 2 * p1 + 1;
+  const int nrow = h.n_q > h.n_v ? h.n_q : h.n_v;
+  const size_t smem = (size_t)(3 * nc + nc1 + 3 * nrow * mw + h.n_q * h.n_f + h.n_q * mw1) * sizeof(double);
+  if (smem > 48 * 1024)
+    SBIO_CUDA_TRY(cudaFuncSetAttribute(stokes_prep_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  stokes_prep_kernel<<<h.M, 256, smem, st>>>(p, h.n_v, h.n_phi, h.n_q, h.n_f, d.parts, d.xyz, d.w, d.ptab, d.trig,
+                                             d.sqrtw, d.st_qv, d.st_qw, d.st_qptab, d.st_qtrig, d.st_ext,
+                                             d.st_normc, f, d.st_coef, d.st_src64, d.st_src32, nullptr);
   count_launch();
   SBIO_CUDA_TRY(cudaGetLastError());
   return SBIO_OK;
@@ -477,18 +498,10 @@ int launch_stokes(sbio_geom* g, const double* f, double* u, cudaStream_t st) {
   stokes_near_launcher nl = stokes_near_lookup_a(p);
   if (!nl) nl = stokes_near_lookup_b(p);
   if (!nl) return set_error(SBIO_ENOTSUP, "no Stokes near-field kernel for p = %d", p);
-  const int p1 = p + 1, nc = (p + 1) * (p + 1), nc1 = (p1 + 1) * (p1 + 1), mw = 2 * p + 1, mw1 = 2 * p1 + 1;
-  (void)nc1;
-  const int nrow = h.n_q > h.n_v ? h.n_q : h.n_v;
-  const size_t smem = (size_t)(3 * nc + nc1 + 3 * nrow * mw + h.n_q * h.n_f + h.n_q * mw1) * sizeof(double);
-  if (smem > 48 * 1024)
-    SBIO_CUDA_TRY(cudaFuncSetAttribute(stokes_prep_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  const int p1 = p + 1, mw1 = 2 * p1 + 1;
   phase_mark(g, 0, st);
-  stokes_prep_kernel<<<h.M, 256, smem, st>>>(p, h.n_v, h.n_phi, h.n_q, h.n_f, d.parts, d.xyz, d.w, d.ptab, d.trig,
-                                             d.sqrtw, d.st_qv, d.st_qw, d.st_qptab, d.st_qtrig, d.st_ext,
-                                             d.st_normc, f, d.st_coef, d.st_src64, d.st_src32, u);
-  count_launch();
-  SBIO_CUDA_TRY(cudaGetLastError());
+  int rc0 = launch_stokes_prep(g, f, st);
+  if (rc0) return rc0;
   const size_t smem_self = (size_t)16 * h.n_v * mw1 * sizeof(double);
   if (smem_self > 48 * 1024)
     SBIO_CUDA_TRY(cudaFuncSetAttribute(stokes_self_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_self));

@@ -1,0 +1,271 @@
+// Stokes single layer at arbitrary points (Sec. 4.3 with the Sec. 4.1
+// particle-to-target algorithm): velocity by eq. (stokes) for near pairs and
+// the Stokeslet quadrature for far pairs (the kernels of the on-surface
+// apply, through a view of the geometry's tables whose targets are the
+// points), and the pressure p = int P(x, y) . f dS with the printed kernel
+// P = r / (4 pi |r|^3): the divergence of the Laplace expansions for near
+// pairs (sbio_stokes_points.cuh), the smooth quadrature for far pairs here.
+#include "sbio_internal.cuh"
+#include "sbio_stokes_near.cuh"
+#include "sbio_stokes_points.cuh"
+
+struct sbio_targets;
+
+namespace sbio {
+
+stokes_near_launcher stokes_near_lookup_a(int p);
+stokes_near_launcher stokes_near_lookup_b(int p);
+stokes_point_near_launcher stokes_point_near_lookup_a(int p);
+stokes_point_near_launcher stokes_point_near_lookup_b(int p);
+
+// target-set internals shared with sbio_targets.cu
+int targets_view(sbio_targets* ts, sbio_geom** g, const DevGeom** view, int64_t* T, int64_t* n_pro,
+                 int64_t* n_pairs);
+
+namespace {
+
+constexpr double kInv4PiP = 0.07957747154594767;   // 1/(4 pi)
+
+struct alignas(32) pd4 {
+  double x, y, z, w;
+};
+
+__device__ __forceinline__ float rsqrt_apx_p(float x) {
+  float r;
+  asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+
+__device__ __forceinline__ void two_sum_p(float a, float b, float& s, float& e) {
+  s = a + b;
+  const float bb = s - a;
+  e = (a - (s - bb)) + (b - bb);
+}
+
+// FP64: one target per thread; sources (y - c, w f_1), (w f_2, w f_3, 0, 0).
+__global__ void __launch_bounds__(kFarTile) pressure_far_fp64_kernel(const int4* __restrict__ tiles, int n_tiles,
+                                                                     const double* __restrict__ src64,
+                                                                     const double* __restrict__ xyz,
+                                                                     const PartGeom* __restrict__ parts,
+                                                                     const int32_t* __restrict__ skip_ptr,
+                                                                     const int32_t* __restrict__ skip_idx, int64_t N,
+                                                                     double* __restrict__ p_out) {
+  __shared__ pd4 sh[kFarTile * 2];
+  const int64_t t = (int64_t)blockIdx.x * kFarTile + threadIdx.x;
+  const bool valid = t < N;
+  double x = 0, y = 0, z = 0;
+  int sp = 0, nxt = INT32_MAX;
+  if (valid) {
+    x = xyz[t * 3 + 0];
+    y = xyz[t * 3 + 1];
+    z = xyz[t * 3 + 2];
+    sp = skip_ptr[t];
+    nxt = skip_idx[sp];
+  }
+  double acc = 0.0;
+  int cur = -1;
+  bool skip = true;
+  double X = 0, Y = 0, Z = 0;
+  const int per = (n_tiles + gridDim.y - 1) / gridDim.y;
+  const int t_lo = blockIdx.y * per, t_hi = min(n_tiles, t_lo + per);
+  for (int tl = t_lo; tl < t_hi; ++tl) {
+    const int4 tile = tiles[tl];
+    if (tile.x != cur) {
+      cur = tile.x;
+      if (valid) {
+        while (nxt < cur) nxt = skip_idx[++sp];
+        skip = (nxt == cur);
+        X = x - parts[cur].c[0];
+        Y = y - parts[cur].c[1];
+        Z = z - parts[cur].c[2];
+      }
+    }
+    if (__syncthreads_and(skip)) continue;
+    if (threadIdx.x < tile.z) {
+      const pd4* s = reinterpret_cast<const pd4*>(src64 + (int64_t)(tile.y + threadIdx.x) * 8);
+      sh[threadIdx.x * 2 + 0] = s[0];
+      sh[threadIdx.x * 2 + 1] = s[1];
+    }
+    __syncthreads();
+    if (!skip) {
+      for (int j = 0; j < tile.z; ++j) {
+        const pd4 a = sh[j * 2], b = sh[j * 2 + 1];
+        const double dx = X - a.x, dy = Y - a.y, dz = Z - a.z;
+        const double ri = rsqrt(dx * dx + dy * dy + dz * dz);
+        acc = fma(a.w * dx + b.x * dy + b.y * dz, ri * ri * ri, acc);
+      }
+    }
+    __syncthreads();
+  }
+  if (valid) atomicAdd(p_out + t, acc * kInv4PiP);
+}
+
+// Mixed: FP32 pair sums, TT targets per thread, hi/lo target offsets per
+// source particle, per-tile partials folded by TwoSum (the far-field scheme
+// of the velocity kernels).
+template <int TT>
+__global__ void __launch_bounds__(kFarTile) pressure_far_mixed_kernel(const int4* __restrict__ tiles, int n_tiles,
+                                                                      const float4* __restrict__ src32,
+                                                                      const float4* __restrict__ tgt32,
+                                                                      const float4* __restrict__ cen32,
+                                                                      const int32_t* __restrict__ skip_ptr,
+                                                                      const int32_t* __restrict__ skip_idx,
+                                                                      int64_t N, double* __restrict__ p_out) {
+  __shared__ float4 sh[2 * kFarTile];
+  __shared__ float acc[2 * TT * kFarTile];
+  __shared__ int cursor[2 * TT * kFarTile];
+  const int tid = threadIdx.x;
+  const int per = (n_tiles + gridDim.y - 1) / gridDim.y;
+  const int t_lo = blockIdx.y * per, t_hi = min(n_tiles, t_lo + per);
+  const int64_t t0 = (int64_t)blockIdx.x * TT * kFarTile + tid;
+#pragma unroll
+  for (int q = 0; q < TT; ++q) {
+    const int64_t t = t0 + (int64_t)q * kFarTile;
+    acc[(2 * q + 0) * kFarTile + tid] = 0.f;
+    acc[(2 * q + 1) * kFarTile + tid] = 0.f;
+    const int sp = (t < N) ? skip_ptr[t] : 0;
+    cursor[(2 * q + 0) * kFarTile + tid] = sp;
+    cursor[(2 * q + 1) * kFarTile + tid] = (t < N) ? skip_idx[sp] : INT32_MAX;
+  }
+  float X[TT], Y[TT], Z[TT];
+  unsigned skipmask = (1u << TT) - 1u;
+  int cur = -1;
+  for (int tl = t_lo; tl < t_hi; ++tl) {
+    const int4 tile = tiles[tl];
+    if (tile.x != cur) {
+      cur = tile.x;
+      const float4 ch = cen32[cur * 2], cl = cen32[cur * 2 + 1];
+      skipmask = 0u;
+#pragma unroll
+      for (int q = 0; q < TT; ++q) {
+        const int64_t t = t0 + (int64_t)q * kFarTile;
+        int sp = cursor[(2 * q + 0) * kFarTile + tid];
+        int nxt = cursor[(2 * q + 1) * kFarTile + tid];
+        while (nxt < cur) nxt = skip_idx[++sp];
+        cursor[(2 * q + 0) * kFarTile + tid] = sp;
+        cursor[(2 * q + 1) * kFarTile + tid] = nxt;
+        if (t >= N || nxt == cur) skipmask |= 1u << q;
+        float4 hi = make_float4(0.f, 0.f, 0.f, 0.f), lo = hi;
+        if (t < N) {
+          hi = tgt32[t * 2];
+          lo = tgt32[t * 2 + 1];
+        }
+        X[q] = (hi.x - ch.x) + (lo.x - cl.x);
+        Y[q] = (hi.y - ch.y) + (lo.y - cl.y);
+        Z[q] = (hi.z - ch.z) + (lo.z - cl.z);
+      }
+    }
+    const bool mine = skipmask != (1u << TT) - 1u;
+    if (!__syncthreads_or(mine)) continue;
+    if (tid < tile.z) {
+      sh[tid * 2 + 0] = src32[(int64_t)(tile.y + tid) * 2 + 0];
+      sh[tid * 2 + 1] = src32[(int64_t)(tile.y + tid) * 2 + 1];
+    }
+    __syncthreads();
+    if (mine) {
+      float pp[TT];
+#pragma unroll
+      for (int q = 0; q < TT; ++q) pp[q] = 0.f;
+#pragma unroll 2
+      for (int j = 0; j < tile.z; ++j) {
+        const float4 a = sh[j * 2], b = sh[j * 2 + 1];
+#pragma unroll
+        for (int q = 0; q < TT; ++q) {
+          const float dx = X[q] - a.x, dy = Y[q] - a.y, dz = Z[q] - a.z;
+          const float ri = rsqrt_apx_p(fmaf(dz, dz, fmaf(dy, dy, dx * dx)));
+          pp[q] = fmaf(fmaf(b.y, dz, fmaf(b.x, dy, a.w * dx)), ri * ri * ri, pp[q]);
+        }
+      }
+#pragma unroll
+      for (int q = 0; q < TT; ++q) {
+        if (!((skipmask >> q) & 1u)) {
+          float sum, err;
+          two_sum_p(acc[(2 * q + 0) * kFarTile + tid], pp[q], sum, err);
+          acc[(2 * q + 0) * kFarTile + tid] = sum;
+          acc[(2 * q + 1) * kFarTile + tid] += err;
+        }
+      }
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int q = 0; q < TT; ++q) {
+    const int64_t t = t0 + (int64_t)q * kFarTile;
+    if (t < N)
+      atomicAdd(p_out + t,
+                ((double)acc[(2 * q + 0) * kFarTile + tid] + (double)acc[(2 * q + 1) * kFarTile + tid]) * kInv4PiP);
+  }
+}
+
+void launch_pressure_far(const DevGeom& d, const GeomHost& h, int64_t NT, double* pr, cudaStream_t st) {
+  if (NT <= 0) return;
+  const int nt = (int)h.tiles.size();
+  if (h.precision == SBIO_FP64) {
+    const int64_t tb = (NT + kFarTile - 1) / kFarTile;
+    const dim3 grid((unsigned)tb, (unsigned)far_split_count(tb, nt, 0));
+    pressure_far_fp64_kernel<<<grid, kFarTile, 0, st>>>(d.tiles, nt, d.st_src64, d.xyz, d.parts, d.skip_ptr,
+                                                        d.skip_idx, NT, pr);
+  } else {
+    constexpr int TT = 4;
+    const int64_t tb = (NT + (int64_t)kFarTile * TT - 1) / ((int64_t)kFarTile * TT);
+    const dim3 grid((unsigned)tb, (unsigned)far_split_count(tb, nt, 0));
+    pressure_far_mixed_kernel<TT><<<grid, kFarTile, 0, st>>>(d.tiles, nt, d.st_src32, d.tgt32, d.cen32, d.skip_ptr,
+                                                             d.skip_idx, NT, pr);
+  }
+  count_launch();
+}
+
+}  // namespace
+}  // namespace sbio
+
+using namespace sbio;
+
+extern "C" {
+
+int sbio_eval_targets_stokes(sbio_targets* ts, const double* f_tilde, double* u_out, double* p_out, void* stream) {
+  clear_error();
+  if (!ts || !f_tilde || !u_out) return set_error(SBIO_EINVAL, "null argument");
+  sbio_geom* g = nullptr;
+  const DevGeom* view = nullptr;
+  int64_t T = 0, n_pro = 0, n_pairs = 0;
+  int rc = targets_view(ts, &g, &view, &T, &n_pro, &n_pairs);
+  if (rc) return rc;
+  const GeomHost& h = g->h;
+  if (h.p > 20) return set_error(SBIO_ENOTSUP, "Stokes single layer is built for p <= 20 (p = %d)", h.p);
+  SBIO_CUDA_TRY(cudaSetDevice(g->ctx->device));
+  cudaStream_t st = (cudaStream_t)stream;
+  if (T == 0) return SBIO_OK;
+  SBIO_CUDA_TRY(cudaMemsetAsync(u_out, 0, T * 3 * sizeof(double), st));
+  if (p_out) SBIO_CUDA_TRY(cudaMemsetAsync(p_out, 0, T * sizeof(double), st));
+  if ((rc = launch_stokes_prep(g, f_tilde, st))) return rc;
+  DevGeom v = *view;   // a copy: the near grid cap is per launch
+  const bool fork = g->overlap && !g->timing && g->near_stream && n_pairs > 0;
+  cudaStream_t ns = fork ? g->near_stream : st;
+  if (fork) {
+    SBIO_CUDA_TRY(cudaEventRecord(g->ev_fork, st));
+    SBIO_CUDA_TRY(cudaStreamWaitEvent(ns, g->ev_fork, 0));
+    v.near_grid_cap = h.st_near_ctas_per_sm > 0 ? h.st_near_ctas_per_sm * sm_count() : 0;
+  }
+  if (n_pairs > 0) {
+    if (p_out) {
+      stokes_point_near_launcher nl = stokes_point_near_lookup_a(h.p);
+      if (!nl) nl = stokes_point_near_lookup_b(h.p);
+      if (!nl) return set_error(SBIO_ENOTSUP, "no Stokes point kernel for p = %d", h.p);
+      nl(v, n_pro, n_pairs, u_out, p_out, ns);
+    } else {
+      stokes_near_launcher nl = stokes_near_lookup_a(h.p);
+      if (!nl) nl = stokes_near_lookup_b(h.p);
+      if (!nl) return set_error(SBIO_ENOTSUP, "no Stokes near-field kernel for p = %d", h.p);
+      nl(v, n_pro, n_pairs, v.inv, u_out, ns);
+    }
+    SBIO_CUDA_TRY(cudaGetLastError());
+  }
+  if (fork) SBIO_CUDA_TRY(cudaEventRecord(g->ev_join, ns));
+  if ((rc = launch_stokes_far_on(v, h, T, u_out, st))) return rc;
+  if (p_out) launch_pressure_far(v, h, T, p_out, st);
+  SBIO_CUDA_TRY(cudaGetLastError());
+  if (fork) SBIO_CUDA_TRY(cudaStreamWaitEvent(st, g->ev_join, 0));
+  return SBIO_OK;
+}
+
+}  // extern "C"

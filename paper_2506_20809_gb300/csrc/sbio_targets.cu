@@ -121,6 +121,17 @@ static void classify(const GeomHost& h, const double* xyz, int64_t T, std::vecto
   });
 }
 
+int targets_view(sbio_targets* ts, sbio_geom** g, const DevGeom** view, int64_t* T, int64_t* n_pro,
+                 int64_t* n_pairs) {
+  if (!ts) return set_error(SBIO_EINVAL, "null target set");
+  *g = ts->g;
+  *view = &ts->view;
+  *T = ts->T;
+  *n_pro = ts->n_pro;
+  *n_pairs = ts->n_pairs;
+  return SBIO_OK;
+}
+
 }  // namespace sbio
 
 using namespace sbio;

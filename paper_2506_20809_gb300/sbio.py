@@ -121,6 +121,7 @@ _SIGS = {
     "sbio_targets_info": (C.c_int, [_vp, C.POINTER(C.c_int64), C.POINTER(C.c_int64), C.POINTER(C.c_int64),
                                     C.POINTER(C.c_size_t)]),
     "sbio_eval_targets": (C.c_int, [_vp, _vp, _vp, _vp, _vp, _vp]),
+    "sbio_eval_targets_stokes": (C.c_int, [_vp, _vp, _vp, _vp, _vp]),
     "sbio_geom_set_stokes_tuning": (C.c_int, [_vp, C.c_int32, C.c_int32, C.c_int32]),
     "sbio_geom_get_stokes_tuning": (C.c_int, [_vp, C.POINTER(C.c_int32), C.POINTER(C.c_int32),
                                               C.POINTER(C.c_int32)]),
@@ -380,6 +381,11 @@ def sbio_targets_info(ts):
 def sbio_eval_targets(ts, sigma_tilde, mu_hat, S_out, D_out, stream=None):
     """S and D at the set's points (device tensors; either input may be None)."""
     _check(_lib.sbio_eval_targets(ts, _ptr(sigma_tilde), _ptr(mu_hat), _ptr(S_out), _ptr(D_out), _stream(stream)))
+
+
+def sbio_eval_targets_stokes(ts, f_tilde, u_out, p_out=None, stream=None):
+    """Stokes velocity (T x 3) and optionally pressure (T) at the set's points."""
+    _check(_lib.sbio_eval_targets_stokes(ts, _ptr(f_tilde), _ptr(u_out), _ptr(p_out), _stream(stream)))
 
 
 def sbio_apply_stokes_sl_host(g, f_tilde, u_out, stream=None):
