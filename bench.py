@@ -62,7 +62,8 @@ def parse():
     ap.add_argument("--oracle-sample", type=int, default=48, help="targets in the oracle's timed sample")
     ap.add_argument("--far-shape", default="", help="TT,SPLITS: fixed far-field launch shape (skips the autotuner)")
     ap.add_argument("--workload", default="poly200",
-                    choices=["poly200", "stokes100", "batch64", "serve", "deriv200", "targets200", "dirichlet200"])
+                    choices=["poly200", "stokes100", "batch64", "serve", "deriv200", "targets200", "dirichlet200",
+                             "stokespoints100"])
     ap.add_argument("--rates", default="50,100,200,500,1000,2000", help="serve: arrival rates (req/s)")
     ap.add_argument("--requests", type=int, default=48, help="serve: requests per rate")
     ap.add_argument("--slots", type=int, default=4, help="serve: concurrent request slots")
@@ -852,6 +853,64 @@ def run_dirichlet200(args, ws, rank, lrank):
         print(json.dumps(line), flush=True)
 
 
+def run_stokespoints100(args, ws, rank, lrank):
+    """Stokes velocity and pressure of the 100-spheroid, p = 12 suspension at
+    shell points (1e-1 .. 1e-6, 10 per spheroid and distance) plus 30,000
+    points in the box; mixed precision, L2 flushed before every step."""
+    import torch
+
+    import __graft_entry__ as GE
+
+    GE.build()
+    from paper_2506_20809_gb300 import inputs as I
+    from paper_2506_20809_gb300 import sbio as S
+
+    torch.cuda.set_device(lrank)
+    susp = I.config_suspension(3)
+    f = I.config_coefficients(susp, 0, ndens=3).transpose(1, 0, 2).copy()
+    X = I.shell_points(susp, per_particle=10, seed=0, far_points=30000)
+    ctx = S.sbio_ctx_create(lrank, 0)
+    g = S.Geometry(ctx, susp, precision=S.SBIO_MIXED)
+    S.sbio_geom_autotune_stokes(g.h)
+    ts = S.TargetSet(g, X)
+    fd = torch.from_numpy(f).cuda()
+    u = torch.empty((ts.T, 3), dtype=torch.float64, device="cuda")
+    pr = torch.empty(ts.T, dtype=torch.float64, device="cuda")
+    st = torch.cuda.current_stream()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    for _ in range(args.warmup):
+        S.sbio_eval_targets_stokes(ts.h, fd, u, pr)
+    clocks = ClockSampler(lrank)
+    clocks.start()
+    ms = []
+    l0 = S.sbio_launch_count()
+    for _ in range(args.steps):
+        flush.zero_()
+        ms.append(_event_time(st, lambda: S.sbio_eval_targets_stokes(ts.h, fd, u, pr)))
+    launches = S.sbio_launch_count() - l0
+    clk = clocks.stop()
+    um, pm = u.clone(), pr.clone()
+    S.sbio_geom_set_precision(g.h, S.SBIO_FP64)
+    S.sbio_eval_targets_stokes(ts.h, fd, u, pr)
+    t64 = _event_time(st, lambda: S.sbio_eval_targets_stokes(ts.h, fd, u, pr))
+    err = {"u": float((um - u).abs().max() / u.abs().max()), "p": float((pm - pr).abs().max() / pr.abs().max())}
+    mean = statistics.mean(ms)
+    line = {"metric": "point evaluations/s (Stokes velocity + pressure at arbitrary points)",
+            "value": ts.T * 1e3 / mean, "unit": "points/s", "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": mean, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+            "config": {"workload": "stokespoints100_p12", "M": susp.M, "p": susp.p, "points": ts.T,
+                       "near_pairs": ts.n_near, "far_pairs": ts.n_far,
+                       "points_recipe": "shells at 1e-1..1e-6 (10 per spheroid and distance) + 30,000 in the box",
+                       "l2": "flushed (256 MiB write) before each step"},
+            "evaluations_per_s": 1e3 / mean, "fp64_gpu_points_per_s": ts.T * 1e3 / t64,
+            "rel_err_vs_fp64_gpu": err, "gpu_launches": int(launches), "clocks": clk}
+    ts.close()
+    g.close()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     ws, rank, lrank = dist_setup()
@@ -869,6 +928,8 @@ def main():
         run_targets200(args, ws, rank, lrank)
     elif args.workload == "dirichlet200":
         run_dirichlet200(args, ws, rank, lrank)
+    elif args.workload == "stokespoints100":
+        run_stokespoints100(args, ws, rank, lrank)
     else:
         run_ours(args, ws, rank, lrank)
     if ws > 1:
