@@ -59,6 +59,7 @@ def parse():
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64-context", action="store_true")
+    ap.add_argument("--no-all-cores", action="store_true", help="skip the all-cores oracle timing")
     ap.add_argument("--oracle-sample", type=int, default=48, help="targets in the oracle's timed sample")
     ap.add_argument("--far-shape", default="", help="TT,SPLITS: fixed far-field launch shape (skips the autotuner)")
     ap.add_argument("--workload", default="poly200",
@@ -147,9 +148,11 @@ class ClockSampler:
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def oracle_sample_time(npz_path, n_sample, p_threads=1):
+def oracle_sample_time(npz_path, n_sample, p_threads=1, seed=1, start_at=None):
     """Time the oracle's O-method apply on a bounded sample of targets in a
-    fresh single-threaded process; returns (seconds, targets, N)."""
+    fresh single-threaded process; returns (seconds, targets, N).  With
+    start_at (a time.time() value) the process waits until then before the
+    timed part, so that several processes run it together."""
     code = f"""
 import os, sys, time, json
 import numpy as np
@@ -160,9 +163,12 @@ d = np.load({npz_path!r})
 s = I.Suspension(d['kind'], d['A'], d['C'], d['center'], d['quat'], int(d['p']))
 og = OG.SuspensionGeom.from_suspension(s)
 O = OL.LaplaceOracle(og)
-tg = np.sort(np.random.default_rng(1).choice(og.N, {n_sample}, replace=False))
+tg = np.sort(np.random.default_rng({seed}).choice(og.N, {n_sample}, replace=False))
 near = og.near_matrix(tg)
 og.near_matrix = lambda targets=None: near
+start_at = {start_at!r}
+if start_at is not None:
+    time.sleep(max(0.0, start_at - time.time()))
 t0 = time.perf_counter()
 O.apply(d['sig'], d['mu'], 'method', targets=tg)
 t1 = time.perf_counter()
@@ -175,6 +181,20 @@ print(json.dumps({{"seconds": t1 - t0, "targets": len(tg), "N": og.N}}))
         raise RuntimeError(r.stderr[-2000:])
     out = json.loads(r.stdout.strip().splitlines()[-1])
     return out["seconds"], out["targets"], out["N"]
+
+
+def oracle_all_cores(npz_path, n_sample, cores):
+    """The same oracle sample on `cores` concurrent single-threaded processes
+    (disjoint random target samples), started together; returns
+    (targets per second over all processes, wall seconds, processes)."""
+    import concurrent.futures as cf
+
+    start_at = time.time() + 20.0       # after every process has loaded numpy and the geometry
+    with cf.ThreadPoolExecutor(cores) as ex:
+        res = list(ex.map(lambda k: oracle_sample_time(npz_path, n_sample, 1, seed=100 + k, start_at=start_at),
+                          range(cores)))
+    wall = max(r[0] for r in res)
+    return sum(r[1] for r in res) / wall, wall, cores
 
 
 def make_workload():
@@ -388,6 +408,13 @@ def run_ours(args, ws, rank, lrank):
         per_apply = sec * NN / nt
         line["cpu_baseline"] = {"value": 1.0 / per_apply, "unit": "applies/s", "cores": 1, "kind": "oracle",
                                 "sample": f"{nt} random targets of {NN} ({sec:.1f} s), scaled to a full apply"}
+        cores = max(1, min(os.cpu_count() or 1, 16))
+        if cores > 1 and not args.no_all_cores:
+            tps, wall, nproc = oracle_all_cores(path, args.oracle_sample, cores)
+            line["cpu_baseline_all_cores"] = {
+                "value": tps / NN, "unit": "applies/s", "cores": nproc, "kind": "oracle",
+                "sample": f"{nproc} concurrent single-threaded processes, {args.oracle_sample} targets each "
+                          f"({wall:.1f} s wall), scaled to a full apply"}
     os.unlink(path)
     if rank == 0:
         print(json.dumps(line), flush=True)
