@@ -88,3 +88,21 @@ def brute_stokes_pressure(kind, A, C, center, quat, p, x, f_t, nv=160, nphi=320,
         d = np.linalg.norm(r, axis=-1)
         out[c0:c0 + chunk] = (np.einsum("tjk,jk->tj", r, f) / d ** 3).sum(1) / (4 * math.pi)
     return out
+
+
+def brute_stresslet(kind, A, C, center, quat, p, x, q_h, nv=160, nphi=320, chunk=64):
+    """Stokes double layer, D[q](x)_i = 3/(4 pi) int (r.q)(r.nu) r_i / |r|^5 dS,
+    r = x - y, nu the outward normal (the sign that makes D[const] = -q
+    inside, like the Laplace double layer); q by its plain coefficients q_h[k]
+    per Cartesian component."""
+    V, PHI, W, y, ny, sw = fine_surface(kind, A, C, center, quat, nv, nphi)
+    Y = L.real_Y(V, PHI, p)
+    q = np.stack([Y @ q_h[k] for k in range(3)], axis=-1) * W[:, None]
+    x = np.atleast_2d(x)
+    out = np.zeros((len(x), 3))
+    for c0 in range(0, len(x), chunk):
+        r = x[c0:c0 + chunk, None, :] - y[None, :, :]
+        d = np.linalg.norm(r, axis=-1)
+        s = np.einsum("tjk,jk->tj", r, q) * np.einsum("tjk,jk->tj", r, ny) / d ** 5
+        out[c0:c0 + chunk] = 3.0 / (4 * math.pi) * np.einsum("tjk,tj->tk", r, s)
+    return out
