@@ -243,6 +243,19 @@ int sbio_apply_stokes_sl(sbio_geom* g, const double* f_tilde, double* u_out, voi
 int sbio_apply_laplace_deriv(sbio_geom* g, const double* sigma_tilde, const double* mu_hat, double* Sp_out,
                              double* Dp_out, void* stream);
 
+/* Stokes double layer (viscosity 1) at all N nodes, principal value:
+ *   D_stk[q](x)_i = 3/(4 pi) int (r.q)(r.nu) r_i / |r|^5 dS, r = x - y,
+ * nu the outward normal (the sign that makes D_stk[const] = -q inside and
+ * -q/2 on the surface, like sbio_apply_laplace's D).  The paper only remarks
+ * (Sec. 4.3) that the Stokes double layer can be evaluated through Laplace
+ * potentials; here D_stk_i = -x_i sum_j d_j D[q_j] + sum_j d_j D[y_i q_j] -
+ * d_i S[q.nu] for near and own pairs (thirteen expansions, exact at order
+ * p+1) and the stresslet quadrature for far pairs.  q_hat: device,
+ * M x 3 x (p+1)^2 plain coefficients (the D input convention) of the three
+ * Cartesian components; u_out: device, N x 3, overwritten.  SBIO_ENOTSUP for
+ * p > 20.  Asynchronous. */
+int sbio_apply_stokes_dl(sbio_geom* g, const double* q_hat, double* u_out, void* stream);
+
 /* End-to-end Stokes apply from and to HOST memory (f_tilde_host M x 3 x
  * (p+1)^2, u_host N x 3): copies in through library-owned device buffers on
  * `stream`, applies, copies out and synchronises `stream` before returning. */
@@ -304,6 +317,10 @@ int sbio_eval_targets(sbio_targets* ts, const double* sigma_tilde, const double*
  * sbio_apply_stokes_sl.  Outputs overwritten; SBIO_ENOTSUP for p > 20;
  * stream-ordered with the geometry's other calls.  Asynchronous. */
 int sbio_eval_targets_stokes(sbio_targets* ts, const double* f_tilde, double* u_out, double* p_out, void* stream);
+
+/* Stokes double layer (as sbio_apply_stokes_dl) at the set's points: u_out
+ * device T x 3, overwritten.  SBIO_ENOTSUP for p > 20.  Asynchronous. */
+int sbio_eval_targets_stokes_dl(sbio_targets* ts, const double* q_hat, double* u_out, void* stream);
 
 
 /* ---- forward transform and exterior boundary-value solves (Sec. 2.3,

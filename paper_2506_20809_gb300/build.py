@@ -22,7 +22,8 @@ SOURCES = ["sbio_geom.cu", "sbio_laplace.cu", "sbio_stokes.cu", "sbio_near_pa.cu
            "sbio_near_pc.cu", "sbio_near_pd.cu", "sbio_noalloc.cu", "sbio_stokes_near_pa.cu",
            "sbio_stokes_near_pb.cu", "sbio_batch.cu", "sbio_server.cu", "sbio_deriv.cu", "sbio_deriv_near_pa.cu",
            "sbio_deriv_near_pb.cu", "sbio_targets.cu", "sbio_solve.cu",
-           "sbio_stokes_points.cu", "sbio_stokes_points_pa.cu", "sbio_stokes_points_pb.cu"]
+           "sbio_stokes_points.cu", "sbio_stokes_points_pa.cu", "sbio_stokes_points_pb.cu",
+           "sbio_stokes_dl.cu", "sbio_stokes_dl_near_pa.cu", "sbio_stokes_dl_near_pb.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

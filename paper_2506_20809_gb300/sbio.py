@@ -122,6 +122,8 @@ _SIGS = {
                                     C.POINTER(C.c_size_t)]),
     "sbio_eval_targets": (C.c_int, [_vp, _vp, _vp, _vp, _vp, _vp]),
     "sbio_eval_targets_stokes": (C.c_int, [_vp, _vp, _vp, _vp, _vp]),
+    "sbio_eval_targets_stokes_dl": (C.c_int, [_vp, _vp, _vp, _vp]),
+    "sbio_apply_stokes_dl": (C.c_int, [_vp, _vp, _vp, _vp]),
     "sbio_geom_set_stokes_tuning": (C.c_int, [_vp, C.c_int32, C.c_int32, C.c_int32]),
     "sbio_geom_get_stokes_tuning": (C.c_int, [_vp, C.POINTER(C.c_int32), C.POINTER(C.c_int32),
                                               C.POINTER(C.c_int32)]),
@@ -386,6 +388,16 @@ def sbio_eval_targets(ts, sigma_tilde, mu_hat, S_out, D_out, stream=None):
 def sbio_eval_targets_stokes(ts, f_tilde, u_out, p_out=None, stream=None):
     """Stokes velocity (T x 3) and optionally pressure (T) at the set's points."""
     _check(_lib.sbio_eval_targets_stokes(ts, _ptr(f_tilde), _ptr(u_out), _ptr(p_out), _stream(stream)))
+
+
+def sbio_apply_stokes_dl(g, q_hat, u_out, stream=None):
+    """Stokes double layer (principal value) at all nodes; device tensors."""
+    _check(_lib.sbio_apply_stokes_dl(g, _ptr(q_hat), _ptr(u_out), _stream(stream)))
+
+
+def sbio_eval_targets_stokes_dl(ts, q_hat, u_out, stream=None):
+    """Stokes double layer at the set's points; device tensors."""
+    _check(_lib.sbio_eval_targets_stokes_dl(ts, _ptr(q_hat), _ptr(u_out), _stream(stream)))
 
 
 def sbio_apply_stokes_sl_host(g, f_tilde, u_out, stream=None):
