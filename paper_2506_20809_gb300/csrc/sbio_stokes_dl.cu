@@ -349,20 +349,24 @@ __global__ void __launch_bounds__(kFarTile) stresslet_far_mixed_kernel(const int
   }
 }
 
-void launch_stresslet_far(const DevGeom& d, const GeomHost& h, int64_t NT, double* u, cudaStream_t st) {
+// tg: the targets (positions, hi/lo parts, skip lists; a point set's view or
+// the geometry itself); src: the geometry, whose source-side arrays (tiles,
+// sources, source normals, centres) are always taken from it.
+void launch_stresslet_far(const DevGeom& tg, const DevGeom& src, const GeomHost& h, int64_t NT, double* u,
+                          cudaStream_t st) {
   if (NT <= 0) return;
   const int nt = (int)h.tiles.size();
   if (h.precision == SBIO_FP64) {
     const int64_t tb = (NT + kFarTile - 1) / kFarTile;
     const dim3 grid((unsigned)tb, (unsigned)far_split_count(tb, nt, 0));
-    stresslet_far_fp64_kernel<<<grid, kFarTile, 0, st>>>(d.tiles, nt, d.st_src64, d.nrm, d.xyz, d.parts,
-                                                         d.skip_ptr, d.skip_idx, NT, u);
+    stresslet_far_fp64_kernel<<<grid, kFarTile, 0, st>>>(src.tiles, nt, src.st_src64, src.nrm, tg.xyz, src.parts,
+                                                         tg.skip_ptr, tg.skip_idx, NT, u);
   } else {
     constexpr int TT = 4;
     const int64_t tb = (NT + (int64_t)kFarTile * TT - 1) / ((int64_t)kFarTile * TT);
     const dim3 grid((unsigned)tb, (unsigned)far_split_count(tb, nt, 0));
-    stresslet_far_mixed_kernel<TT><<<grid, kFarTile, 0, st>>>(d.tiles, nt, d.st_src32, d.nrm32, d.tgt32, d.cen32,
-                                                              d.skip_ptr, d.skip_idx, NT, u);
+    stresslet_far_mixed_kernel<TT><<<grid, kFarTile, 0, st>>>(src.tiles, nt, src.st_src32, src.nrm32, tg.tgt32,
+                                                              src.cen32, tg.skip_ptr, tg.skip_idx, NT, u);
   }
   count_launch();
 }
@@ -422,7 +426,7 @@ int sbio_apply_stokes_dl(sbio_geom* g, const double* q_hat, double* u_out, void*
   if (!h.pair_t.empty()) nl(v, d.pair_t, d.pair_s, h.n_pairs_prolate, (int64_t)h.pair_t.size(), u_out, ns);
   SBIO_CUDA_TRY(cudaGetLastError());
   if (fork) SBIO_CUDA_TRY(cudaEventRecord(g->ev_join, ns));
-  launch_stresslet_far(d, h, h.N, u_out, st);
+  launch_stresslet_far(d, d, h, h.N, u_out, st);
   SBIO_CUDA_TRY(cudaGetLastError());
   if (fork) SBIO_CUDA_TRY(cudaStreamWaitEvent(st, g->ev_join, 0));
   return SBIO_OK;
@@ -446,7 +450,7 @@ int sbio_eval_targets_stokes_dl(sbio_targets* ts, const double* q_hat, double* u
   SBIO_CUDA_TRY(cudaMemsetAsync(u_out, 0, T * 3 * sizeof(double), st));
   if ((rc = sdl_prep(g, q_hat, nullptr, st))) return rc;
   if (n_pairs > 0) nl(*view, view->pair_t, view->pair_s, n_pro, n_pairs, u_out, st);
-  launch_stresslet_far(*view, h, T, u_out, st);
+  launch_stresslet_far(*view, g->d, h, T, u_out, st);
   SBIO_CUDA_TRY(cudaGetLastError());
   return SBIO_OK;
 }

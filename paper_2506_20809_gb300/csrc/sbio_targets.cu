@@ -23,7 +23,10 @@ struct sbio_targets {
   sbio_geom* g = nullptr;
   int64_t T = 0;
   int64_t n_pro = 0, n_pairs = 0, far_pairs = 0;
-  sbio::DevGeom view;                 // the geometry's tables with the points as targets
+  // the geometry's tables with the points as targets: xyz, tgt32, the near
+  // pairs and the skip lists are the points'; nrm is null (points carry no
+  // normal), so kernels that need source normals take them from the geometry
+  sbio::DevGeom view;
   std::vector<void*> allocs;
   size_t bytes = 0;
 };
