@@ -64,7 +64,7 @@ def parse():
     ap.add_argument("--far-shape", default="", help="TT,SPLITS: fixed far-field launch shape (skips the autotuner)")
     ap.add_argument("--workload", default="poly200",
                     choices=["poly200", "stokes100", "batch64", "serve", "deriv200", "targets200", "dirichlet200",
-                             "stokespoints100"])
+                             "stokespoints100", "stokesdl100"])
     ap.add_argument("--rates", default="50,100,200,500,1000,2000", help="serve: arrival rates (req/s)")
     ap.add_argument("--requests", type=int, default=48, help="serve: requests per rate")
     ap.add_argument("--slots", type=int, default=4, help="serve: concurrent request slots")
@@ -938,6 +938,58 @@ def run_stokespoints100(args, ws, rank, lrank):
         print(json.dumps(line), flush=True)
 
 
+def run_stokesdl100(args, ws, rank, lrank):
+    """Stokes double layer (principal value) at all nodes of the 100-spheroid,
+    p = 12 suspension; mixed precision, L2 flushed before every step."""
+    import torch
+
+    import __graft_entry__ as GE
+
+    GE.build()
+    from paper_2506_20809_gb300 import inputs as I
+    from paper_2506_20809_gb300 import sbio as S
+
+    torch.cuda.set_device(lrank)
+    susp = I.config_suspension(3)
+    q = I.config_coefficients(susp, 1, ndens=3).transpose(1, 0, 2).copy()
+    ctx = S.sbio_ctx_create(lrank, 0)
+    g = S.Geometry(ctx, susp, precision=S.SBIO_MIXED)
+    S.sbio_geom_autotune_stokes(g.h)
+    qd = torch.from_numpy(q).cuda()
+    u = torch.empty((g.N, 3), dtype=torch.float64, device="cuda")
+    st = torch.cuda.current_stream()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    for _ in range(args.warmup):
+        S.sbio_apply_stokes_dl(g.h, qd, u)
+    clocks = ClockSampler(lrank)
+    clocks.start()
+    ms = []
+    l0 = S.sbio_launch_count()
+    for _ in range(args.steps):
+        flush.zero_()
+        ms.append(_event_time(st, lambda: S.sbio_apply_stokes_dl(g.h, qd, u)))
+    launches = S.sbio_launch_count() - l0
+    clk = clocks.stop()
+    um = u.clone()
+    S.sbio_geom_set_precision(g.h, S.SBIO_FP64)
+    S.sbio_apply_stokes_dl(g.h, qd, u)
+    t64 = _event_time(st, lambda: S.sbio_apply_stokes_dl(g.h, qd, u))
+    err = float((um - u).abs().max() / u.abs().max())
+    mean = statistics.mean(ms)
+    line = {"metric": "Stokes double-layer applies/s (all surface nodes)", "value": 1e3 / mean, "unit": "applies/s",
+            "n_gpus": ws, "steps": args.steps, "warmup": args.warmup, "ms_per_step": mean,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64",
+            "data": "synthetic",
+            "config": {"workload": "stokesdl100_p12", "M": susp.M, "p": susp.p, "targets": g.N,
+                       "near_pairs": g.n_near, "far_pairs_per_apply": g.n_far,
+                       "l2": "flushed (256 MiB write) before each step"},
+            "fp64_gpu_applies_per_s": 1e3 / t64, "rel_err_vs_fp64_gpu": err, "gpu_launches": int(launches),
+            "clocks": clk}
+    g.close()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     ws, rank, lrank = dist_setup()
@@ -957,6 +1009,8 @@ def main():
         run_dirichlet200(args, ws, rank, lrank)
     elif args.workload == "stokespoints100":
         run_stokespoints100(args, ws, rank, lrank)
+    elif args.workload == "stokesdl100":
+        run_stokesdl100(args, ws, rank, lrank)
     else:
         run_ours(args, ws, rank, lrank)
     if ws > 1:
