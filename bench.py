@@ -644,6 +644,28 @@ def run_serve(args, ws, rank, lrank):
                 "p50_ms": lat[len(lat) // 2], "p99_ms": lat[min(len(lat) - 1, int(0.99 * len(lat)))],
                 "makespan_s": makespan}
 
+    # where a request's time goes: geometry set-up (host phases) against its
+    # ten applies (Laplace S + D, mixed, one at a time)
+    prof = []
+    st = torch.cuda.current_stream()
+    for s in pool:
+        t0 = time.perf_counter()
+        g = S.Geometry(ctx, s, precision=S.SBIO_MIXED)
+        torch.cuda.synchronize()
+        create_ms = (time.perf_counter() - t0) * 1e3
+        host, near, dev = S.sbio_geom_setup_times(g.h)
+        c = I.config_coefficients(s, 0)
+        sg, mg = torch.from_numpy(c[0]).cuda(), torch.from_numpy(c[1]).cuda()
+        So = torch.empty(g.N, dtype=torch.float64, device="cuda")
+        Do = torch.empty_like(So)
+        S.sbio_apply_laplace(g.h, sg, mg, So, Do)
+        ap = _event_time(st, lambda: [S.sbio_apply_laplace(g.h, sg, mg, So, Do) for _ in range(10)])
+        prof.append({"M": s.M, "p": s.p, "create_ms": create_ms, "host_nodes_ms": host, "near_sets_ms": near,
+                     "device_tables_ms": dev, "ten_applies_ms": ap})
+        g.close()
+    profile = {"geometries": prof, "total_create_ms": sum(x["create_ms"] for x in prof),
+               "total_ten_applies_ms": sum(x["ten_applies_ms"] for x in prof)}
+
     rates = [float(x) for x in args.rates.split(",")]
     rows = [stream_of(r, 7, S.SBIO_MIXED, args.requests) for r in rates]
     ref = stream_of(rates[-1], 7, S.SBIO_FP64, min(12, args.requests))
@@ -656,7 +678,8 @@ def run_serve(args, ws, rank, lrank):
             "config": {"workload": "serve", "slots": args.slots, "requests_per_rate": args.requests,
                        "pool": [{"M": m, "p": p} for m, p in specs], "mem_budget_bytes": budget,
                        "ops": "Laplace S+D or Stokes single layer, probability 1/2"},
-            "sweep": rows, "fp64_plain_at_max_rate": ref, "mixed_same_requests_as_fp64": mixed_same,
+            "sweep": rows, "pool_profile": profile, "fp64_plain_at_max_rate": ref,
+            "mixed_same_requests_as_fp64": mixed_same,
             "speedup_vs_fp64_plain": mixed_same["applies_per_s"] / ref["applies_per_s"]}
     if rank == 0:
         print(json.dumps(line), flush=True)

@@ -64,6 +64,45 @@ struct PartGeom {
   int32_t pad;
 };
 
+// Distance from (y0, y1) >= 0 to the ellipse (t0/e0)^2 + (t1/e1)^2 = 1 with
+// e0 >= e1 > 0, for points outside it: bisection on the Lagrange parameter of
+// the closest-point condition (D. Eberly, "Distance from a point to an
+// ellipse, an ellipsoid, or a hyperellipsoid", Geometric Tools); shared by the
+// host set-up and the device near-set kernels.
+__host__ __device__ inline double ellipse_distance_hd(double e0, double e1, double y0, double y1) {
+  if (y1 > 0.0) {
+    if (y0 > 0.0) {
+      const double z0 = y0 / e0, z1 = y1 / e1;
+      const double g0 = z0 * z0 + z1 * z1 - 1.0;
+      if (g0 == 0.0) return 0.0;
+      const double r0 = (e0 / e1) * (e0 / e1);
+      const double n0 = r0 * z0;
+      double s0 = z1 - 1.0;
+      double s1 = (g0 < 0.0) ? 0.0 : hypot(n0, z1) - 1.0;
+      double s = 0.0;
+      for (int it = 0; it < 2000; ++it) {
+        s = 0.5 * (s0 + s1);
+        if (s == s0 || s == s1) break;
+        const double r0s = n0 / (s + r0), r1s = z1 / (s + 1.0);
+        const double g = r0s * r0s + r1s * r1s - 1.0;
+        if (g > 0.0) s0 = s;
+        else if (g < 0.0) s1 = s;
+        else break;
+      }
+      const double x0 = r0 * y0 / (s + r0), x1 = y1 / (s + 1.0);
+      return hypot(x0 - y0, x1 - y1);
+    }
+    return fabs(y1 - e1);
+  }
+  const double num = e0 * y0, den = e0 * e0 - e1 * e1;
+  if (num < den) {
+    const double xd = num / den;
+    const double x0 = e0 * xd, x1 = e1 * sqrt(fmax(0.0, 1.0 - xd * xd));
+    return hypot(x0 - y0, x1);
+  }
+  return fabs(y0 - e0);
+}
+
 // Local Cartesian -> (u, v, sqrt(1-v^2), cos phi, sin phi) for a spheroid with
 // half focal distance a.  Cancellation-free positive root of the quadratic
 //   prolate: s = u^2-1,  s^2 + (1 - R^2) s - X^2 = 0

@@ -6,7 +6,6 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
-#include <thread>
 
 #include "sbio_internal.cuh"
 #include "sbio_near.cuh"
@@ -111,54 +110,6 @@ double kfact(int n, int m) {
   return r;
 }
 
-// Distance from (y0, y1) >= 0 to the ellipse (t0/e0)^2 + (t1/e1)^2 = 1 with
-// e0 >= e1 > 0, for points outside it: bisection on the Lagrange parameter of
-// the closest-point condition (D. Eberly, "Distance from a point to an
-// ellipse, an ellipsoid, or a hyperellipsoid", Geometric Tools).
-static double ellipse_distance(double e0, double e1, double y0, double y1) {
-  if (y1 > 0.0) {
-    if (y0 > 0.0) {
-      const double z0 = y0 / e0, z1 = y1 / e1;
-      const double g0 = z0 * z0 + z1 * z1 - 1.0;
-      if (g0 == 0.0) return 0.0;
-      const double r0 = (e0 / e1) * (e0 / e1);
-      const double n0 = r0 * z0;
-      double s0 = z1 - 1.0;
-      double s1 = (g0 < 0.0) ? 0.0 : std::hypot(n0, z1) - 1.0;
-      double s = 0.0;
-      for (int it = 0; it < 2000; ++it) {
-        s = 0.5 * (s0 + s1);
-        if (s == s0 || s == s1) break;
-        const double r0s = n0 / (s + r0), r1s = z1 / (s + 1.0);
-        const double g = r0s * r0s + r1s * r1s - 1.0;
-        if (g > 0.0) s0 = s;
-        else if (g < 0.0) s1 = s;
-        else break;
-      }
-      const double x0 = r0 * y0 / (s + r0), x1 = y1 / (s + 1.0);
-      return std::hypot(x0 - y0, x1 - y1);
-    }
-    return std::fabs(y1 - e1);
-  }
-  const double num = e0 * y0, den = e0 * e0 - e1 * e1;
-  if (num < den) {
-    const double xd = num / den;
-    const double x0 = e0 * xd, x1 = e1 * std::sqrt(std::max(0.0, 1.0 - xd * xd));
-    return std::hypot(x0 - y0, x1);
-  }
-  return std::fabs(y0 - e0);
-}
-
-// Signed distance from a local point to the spheroid (negative inside).
-static double spheroid_distance(const PartGeom& P, double x, double y, double z) {
-  const double rho = std::hypot(x, y), az = std::fabs(z);
-  const double f = (rho / P.A) * (rho / P.A) + (az / P.C) * (az / P.C);
-  if (f < 1.0) return -1.0;
-  // meridian-plane ellipse with semi-axes A (rho) and C (z); major axis first
-  if (P.C >= P.A) return ellipse_distance(P.C, P.A, az, rho);
-  return ellipse_distance(P.A, P.C, rho, az);
-}
-
 static void quat_rot(const double* q, double* R) {
   const double w = q[0], x = q[1], y = q[2], z = q[3];
   R[0] = 1 - 2 * (y * y + z * z); R[1] = 2 * (x * y - w * z);     R[2] = 2 * (x * z + w * y);
@@ -171,8 +122,8 @@ double spheroid_distance_local(const PartGeom& P, double x, double y, double z, 
   const double f = (rho / P.A) * (rho / P.A) + (az / P.C) * (az / P.C);
   *inside = f < 1.0 - tol;
   if (*inside) return 0.0;
-  if (P.C >= P.A) return ellipse_distance(P.C, P.A, az, rho);
-  return ellipse_distance(P.A, P.C, rho, az);
+  if (P.C >= P.A) return ellipse_distance_hd(P.C, P.A, az, rho);
+  return ellipse_distance_hd(P.A, P.C, rho, az);
 }
 
 void split_f32(double v, float& hi, float& lo) {
@@ -272,72 +223,170 @@ int build_host(GeomHost& h, const sbio_spheroid* sph, int32_t M, const sbio_opti
 }
 
 // Per-target near sets (exact distances), in parallel over targets.
-static int build_near(GeomHost& h) {
+// Near sets on the device.  One thread per target node loops over the
+// particles in ascending order: a bounding-sphere test, then (for candidates)
+// the exact point-to-spheroid distance; near iff below near_factor x the
+// source's major semi-axis (strict).  Count pass: near particles per node and
+// the smallest node lying inside another spheroid.  Fill pass: the node's
+// near pairs at its offset (ascending source) and its far skip list (own and
+// near particles ascending, then a sentinel) at its CSR offset.
+__global__ void __launch_bounds__(128) near_sets_kernel(int M, int G, int64_t N, const PartGeom* __restrict__ parts,
+                                                        const double* __restrict__ xyz, double near_factor, int fill,
+                                                        int32_t* __restrict__ count,
+                                                        unsigned long long* __restrict__ overlap_min,
+                                                        const int64_t* __restrict__ pair_off,
+                                                        int32_t* __restrict__ pair_t, int32_t* __restrict__ pair_s,
+                                                        const int32_t* __restrict__ skip_ptr,
+                                                        int32_t* __restrict__ skip_idx) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= N) return;
+  const int own = (int)(t / G);
+  const double x0 = xyz[t * 3 + 0], x1 = xyz[t * 3 + 1], x2 = xyz[t * 3 + 2];
+  int c = 0;
+  const int64_t po = fill ? pair_off[t] : 0;
+  int32_t so = fill ? skip_ptr[t] : 0;
+  bool own_done = false;
+  for (int i = 0; i < M; ++i) {
+    if (i == own) continue;
+    const PartGeom& P = parts[i];
+    const double rmax = fmax(P.A, P.C), thr = near_factor * rmax;
+    const double d0 = x0 - P.c[0], d1 = x1 - P.c[1], d2 = x2 - P.c[2];
+    const double dc = sqrt(d0 * d0 + d1 * d1 + d2 * d2);
+    if (dc - rmax >= thr) continue;
+    const double xl = P.R[0] * d0 + P.R[3] * d1 + P.R[6] * d2;
+    const double yl = P.R[1] * d0 + P.R[4] * d1 + P.R[7] * d2;
+    const double zl = P.R[2] * d0 + P.R[5] * d1 + P.R[8] * d2;
+    const double rho = hypot(xl, yl), az = fabs(zl);
+    const double f = (rho / P.A) * (rho / P.A) + (az / P.C) * (az / P.C);
+    if (f < 1.0) {
+      if (!fill) atomicMin(overlap_min, (unsigned long long)t);
+      continue;
+    }
+    const double dist = (P.C >= P.A) ? ellipse_distance_hd(P.C, P.A, az, rho) : ellipse_distance_hd(P.A, P.C, rho, az);
+    if (!(dist < thr)) continue;
+    if (fill) {
+      pair_t[po + c] = (int32_t)t;
+      pair_s[po + c] = i;
+      if (!own_done && own < i) {
+        skip_idx[so++] = own;
+        own_done = true;
+      }
+      skip_idx[so++] = i;
+    }
+    ++c;
+  }
+  if (fill) {
+    if (!own_done) skip_idx[so++] = own;
+    skip_idx[so] = INT32_MAX;   // sentinel
+  } else {
+    count[t] = c;
+  }
+}
+
+template <typename T>
+static int upload(sbio_geom* g, T** dst, const T* src, size_t count, const char* what);
+
+// Near pairs (sorted by source kind, source, target), far pair count,
+// source tiles and the device skip lists.
+static int build_near(sbio_geom* g) {
+  GeomHost& h = g->h;
+  DevGeom& d = g->d;
   const int M = h.M;
   const int64_t N = h.N;
-  std::vector<double> rmax(M), thr(M);
-  for (int i = 0; i < M; ++i) {
-    rmax[i] = std::max(h.parts[i].A, h.parts[i].C);
-    thr[i] = h.near_factor * rmax[i];
-  }
-  unsigned nth = std::max(1u, std::min(32u, std::thread::hardware_concurrency()));
-  std::vector<std::vector<std::pair<int32_t, int32_t>>> local(nth);
-  std::vector<int> overlap(nth, -1);
-  auto work = [&](unsigned tid) {
-    for (int64_t t = tid; t < N; t += nth) {
-      const int own = (int)(t / h.G);
-      const double* x = &h.xyz[t * 3];
-      for (int i = 0; i < M; ++i) {
-        if (i == own) continue;
-        const PartGeom& P = h.parts[i];
-        const double d0 = x[0] - P.c[0], d1 = x[1] - P.c[1], d2 = x[2] - P.c[2];
-        const double dc = std::sqrt(d0 * d0 + d1 * d1 + d2 * d2);
-        if (dc - rmax[i] >= thr[i]) continue;
-        const double xl = P.R[0] * d0 + P.R[3] * d1 + P.R[6] * d2;
-        const double yl = P.R[1] * d0 + P.R[4] * d1 + P.R[7] * d2;
-        const double zl = P.R[2] * d0 + P.R[5] * d1 + P.R[8] * d2;
-        const double d = spheroid_distance(P, xl, yl, zl);
-        if (d < 0.0) {
-          overlap[tid] = (int)t;
-          return;
-        }
-        if (d < thr[i]) local[tid].push_back({(int32_t)t, (int32_t)i});
-      }
+  cudaStream_t st = g->setup_stream;
+  int rc;
+  if (!d.parts && (rc = upload(g, &d.parts, h.parts.data(), M, "particles"))) return rc;
+  if (!d.xyz && (rc = upload(g, &d.xyz, h.xyz.data(), N * 3, "node positions"))) return rc;
+  // transient buffers (counts, overlap flag, pair offsets and pairs), freed
+  // on the set-up stream before returning
+  std::vector<void*> scratch;
+  auto tmp = [&](void** ptr, size_t bytes) -> int {
+    *ptr = nullptr;
+    if (bytes == 0) return SBIO_OK;
+    if (cudaMallocAsync(ptr, bytes, st) != cudaSuccess) {
+      cudaGetLastError();
+      return set_error(SBIO_ENOMEM, "near-set scratch (%zu bytes) failed", bytes);
     }
+    scratch.push_back(*ptr);
+    return SBIO_OK;
   };
-  std::vector<std::thread> th;
-  for (unsigned k = 0; k < nth; ++k) th.emplace_back(work, k);
-  for (auto& t : th) t.join();
-  for (unsigned k = 0; k < nth; ++k)
-    if (overlap[k] >= 0)
-      return set_error(SBIO_EOVERLAP, "node %d of particle %d lies inside another spheroid", overlap[k],
-                       (int)(overlap[k] / h.G));
-  std::vector<std::pair<int32_t, int32_t>> pairs;
-  for (auto& v : local) pairs.insert(pairs.end(), v.begin(), v.end());
-  // order (kind of source, source, target): warps share a source and its kind
-  std::sort(pairs.begin(), pairs.end(), [&](const std::pair<int32_t, int32_t>& a, const std::pair<int32_t, int32_t>& b) {
-    const int ka = h.parts[a.second].kind, kb = h.parts[b.second].kind;
-    if (ka != kb) return ka < kb;
-    if (a.second != b.second) return a.second < b.second;
-    return a.first < b.first;
-  });
-  h.pair_t.resize(pairs.size());
-  h.pair_s.resize(pairs.size());
+  struct Release {
+    std::vector<void*>& v;
+    cudaStream_t s;
+    ~Release() {
+      for (void* q : v) cudaFreeAsync(q, s);
+    }
+  } release{scratch, st};
+  int32_t* dcount = nullptr;
+  unsigned long long* dovl = nullptr;
+  if ((rc = tmp((void**)&dcount, (size_t)N * sizeof(int32_t)))) return rc;
+  if ((rc = tmp((void**)&dovl, sizeof(unsigned long long)))) return rc;
+  SBIO_CUDA_TRY(cudaMemsetAsync(dovl, 0xff, sizeof(unsigned long long), st));
+  const unsigned blocks = (unsigned)((N + 127) / 128);
+  near_sets_kernel<<<blocks, 128, 0, st>>>(M, h.G, N, d.parts, d.xyz, h.near_factor, 0, dcount, dovl, nullptr,
+                                           nullptr, nullptr, nullptr, nullptr);
+  SBIO_CUDA_TRY(cudaGetLastError());
+  std::vector<int32_t> cnt(N);
+  unsigned long long ovl = 0;
+  SBIO_CUDA_TRY(cudaMemcpyAsync(cnt.data(), dcount, N * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+  SBIO_CUDA_TRY(cudaMemcpyAsync(&ovl, dovl, sizeof(ovl), cudaMemcpyDeviceToHost, st));
+  SBIO_CUDA_TRY(cudaStreamSynchronize(st));
+  if (ovl != ~0ull)
+    return set_error(SBIO_EOVERLAP, "node %lld of particle %lld lies inside another spheroid", (long long)ovl,
+                     (long long)(ovl / h.G));
+  // offsets: pairs per node, skip lists (near + own + sentinel) per node
+  std::vector<int64_t> poff(N + 1, 0);
+  std::vector<int32_t> sptr(N + 1, 0);
+  for (int64_t t = 0; t < N; ++t) {
+    poff[t + 1] = poff[t] + cnt[t];
+    if ((int64_t)sptr[t] + cnt[t] + 2 > INT32_MAX) return set_error(SBIO_EINVAL, "skip lists exceed 2^31 entries");
+    sptr[t + 1] = sptr[t] + cnt[t] + 2;
+  }
+  const int64_t P = poff[N];
+  int64_t* dpoff = nullptr;
+  int32_t *dpt = nullptr, *dps = nullptr;
+  if ((rc = tmp((void**)&dpoff, poff.size() * sizeof(int64_t)))) return rc;
+  SBIO_CUDA_TRY(cudaMemcpyAsync(dpoff, poff.data(), poff.size() * sizeof(int64_t), cudaMemcpyHostToDevice, st));
+  if ((rc = upload(g, &d.skip_ptr, sptr.data(), sptr.size(), "skip lists"))) return rc;
+  if ((rc = dev_alloc(g, (void**)&d.skip_idx, (size_t)sptr[N] * sizeof(int32_t), "skip lists"))) return rc;
+  if ((rc = tmp((void**)&dpt, (size_t)P * sizeof(int32_t)))) return rc;
+  if ((rc = tmp((void**)&dps, (size_t)P * sizeof(int32_t)))) return rc;
+  near_sets_kernel<<<blocks, 128, 0, st>>>(M, h.G, N, d.parts, d.xyz, h.near_factor, 1, nullptr, nullptr, dpoff, dpt,
+                                           dps, d.skip_ptr, d.skip_idx);
+  SBIO_CUDA_TRY(cudaGetLastError());
+  std::vector<int32_t> pt(P), ps(P);
+  if (P > 0) {
+    SBIO_CUDA_TRY(cudaMemcpyAsync(pt.data(), dpt, P * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+    SBIO_CUDA_TRY(cudaMemcpyAsync(ps.data(), dps, P * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+  }
+  SBIO_CUDA_TRY(cudaStreamSynchronize(st));
+  // counting sort by (source kind, source); targets stay ascending per source
+  std::vector<int64_t> num(M, 0);
+  for (int64_t k = 0; k < P; ++k) num[ps[k]]++;
+  std::vector<int64_t> base(M, 0);
+  int64_t acc = 0;
   h.n_pairs_prolate = 0;
-  std::vector<int32_t> cnt(N, 0);
-  for (size_t k = 0; k < pairs.size(); ++k) {
-    h.pair_t[k] = pairs[k].first;
-    h.pair_s[k] = pairs[k].second;
-    if (h.parts[pairs[k].second].kind == SBIO_PROLATE) h.n_pairs_prolate++;
-    cnt[pairs[k].first]++;
+  for (int kind = SBIO_PROLATE; kind <= SBIO_OBLATE; ++kind)
+    for (int i = 0; i < M; ++i)
+      if (h.parts[i].kind == kind) {
+        base[i] = acc;
+        acc += num[i];
+        if (kind == SBIO_PROLATE) h.n_pairs_prolate += num[i];
+      }
+  h.pair_t.assign(P, 0);
+  h.pair_s.assign(P, 0);
+  for (int64_t k = 0; k < P; ++k) {
+    const int64_t dst = base[ps[k]]++;
+    h.pair_t[dst] = pt[k];
+    h.pair_s[dst] = ps[k];
   }
   h.far_pairs = 0;
   for (int64_t t = 0; t < N; ++t) h.far_pairs += (int64_t)(M - 1 - cnt[t]) * h.G;
   // far-field source tiles
   h.tiles.clear();
   for (int i = 0; i < M; ++i)
-    for (int s = 0; s < h.G; s += kFarTile)
-      h.tiles.push_back(make_int4(i, i * h.G + s, std::min(kFarTile, h.G - s), 0));
+    for (int s0 = 0; s0 < h.G; s0 += kFarTile)
+      h.tiles.push_back(make_int4(i, i * h.G + s0, std::min(kFarTile, h.G - s0), 0));
   return SBIO_OK;
 }
 
@@ -355,8 +404,8 @@ static int build_device(sbio_geom* g) {
   const int p = h.p, M = h.M, nm = nm_count(p), nc = (p + 1) * (p + 1);
   const int64_t N = h.N;
   int rc;
-  if ((rc = upload(g, &d.parts, h.parts.data(), M, "particles"))) return rc;
-  if ((rc = upload(g, &d.xyz, h.xyz.data(), N * 3, "node positions"))) return rc;
+  if (!d.parts && (rc = upload(g, &d.parts, h.parts.data(), M, "particles"))) return rc;
+  if (!d.xyz && (rc = upload(g, &d.xyz, h.xyz.data(), N * 3, "node positions"))) return rc;
   if ((rc = upload(g, &d.nrm, h.nrm.data(), N * 3, "node normals"))) return rc;
   if ((rc = upload(g, &d.w, h.w.data(), N, "node weights"))) return rc;
   // Legendre table at the GL nodes, trig table, modified-basis weights
@@ -435,18 +484,7 @@ static int build_device(sbio_geom* g) {
   // near pairs and far skip lists (own particle + near particles, ascending)
   if ((rc = upload(g, &d.pair_t, h.pair_t.data(), h.pair_t.size(), "near pairs"))) return rc;
   if ((rc = upload(g, &d.pair_s, h.pair_s.data(), h.pair_s.size(), "near pairs"))) return rc;
-  std::vector<std::vector<int32_t>> skip(N);
-  for (int64_t t = 0; t < N; ++t) skip[t].push_back((int32_t)(t / h.G));
-  for (size_t k = 0; k < h.pair_t.size(); ++k) skip[h.pair_t[k]].push_back(h.pair_s[k]);
-  std::vector<int32_t> sptr(N + 1, 0), sidx;
-  for (int64_t t = 0; t < N; ++t) {
-    std::sort(skip[t].begin(), skip[t].end());
-    skip[t].push_back(INT32_MAX);   // sentinel
-    sptr[t + 1] = sptr[t] + (int32_t)skip[t].size();
-    sidx.insert(sidx.end(), skip[t].begin(), skip[t].end());
-  }
-  if ((rc = upload(g, &d.skip_ptr, sptr.data(), sptr.size(), "skip lists"))) return rc;
-  if ((rc = upload(g, &d.skip_idx, sidx.data(), sidx.size(), "skip lists"))) return rc;
+  // (the far skip lists were written on the device by the near-set kernels)
   if ((rc = upload(g, &d.tiles, h.tiles.data(), h.tiles.size(), "far tiles"))) return rc;
   std::vector<double> inv(kInvTable, 0.0);
   for (int k = 1; k < kInvTable; ++k) inv[k] = 1.0 / k;
@@ -643,7 +681,7 @@ static int geom_create_impl(sbio_ctx* ctx, const sbio_spheroid* sph, int32_t M, 
   const auto t0 = clk::now();
   rc = build_host(g->h, sph, M, opts);
   const auto t1 = clk::now();
-  if (!rc) rc = build_near(g->h);
+  if (!rc) rc = build_near(g);
   const auto t2 = clk::now();
   if (!rc) rc = build_device(g);
   const auto t3 = clk::now();
