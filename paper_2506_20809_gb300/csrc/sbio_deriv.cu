@@ -118,7 +118,7 @@ __global__ void __launch_bounds__(kFarTile) far_deriv_fp64_kernel(const int4* __
 // relative to each source particle's centre through hi/lo FP32 parts, per-tile
 // partials folded into (hi, lo) pairs by TwoSum in shared memory (the same
 // scheme as the layer-potential far field).
-template <int TT, bool DO_S, bool DO_D>
+template <int TT, bool DO_S, bool DO_D, bool PK>
 __global__ void __launch_bounds__(kFarTile) far_deriv_mixed_kernel(const int4* __restrict__ tiles, int n_tiles,
                                                                    const float4* __restrict__ src32,
                                                                    const float4* __restrict__ tgt32,
@@ -128,7 +128,10 @@ __global__ void __launch_bounds__(kFarTile) far_deriv_mixed_kernel(const int4* _
                                                                    const int32_t* __restrict__ skip_idx, int64_t N,
                                                                    double* __restrict__ Sp_out,
                                                                    double* __restrict__ Dp_out) {
-  __shared__ float4 sh[2 * kFarTile];        // (y - c, -q), (d, 0)
+  // scalar form: (y - c, -q), (d, 0) per source; packed form (two targets per
+  // f32x2 operation) every value duplicated into a pair: (-y.x, -y.y),
+  // (-y.z, -q), (d.x, d.y), (d.z, -3 d.x), (-3 d.y, -3 d.z)
+  __shared__ float4 sh[(PK ? 5 : 2) * kFarTile];
   __shared__ float acc[4 * TT * kFarTile];   // per target: S' hi, lo, D' hi, lo
   __shared__ int cursor[2 * TT * kFarTile];  // per target: skip-list position, next skipped particle
   const int tid = threadIdx.x;
@@ -180,14 +183,68 @@ __global__ void __launch_bounds__(kFarTile) far_deriv_mixed_kernel(const int4* _
     if (!__syncthreads_or(mine)) continue;
     if (tid < tile.z) {
       const float4 a = src32[(int64_t)(tile.y + tid) * 2 + 0];
-      sh[tid * 2 + 0] = make_float4(a.x, a.y, a.z, -a.w);
-      sh[tid * 2 + 1] = src32[(int64_t)(tile.y + tid) * 2 + 1];
+      const float4 b = src32[(int64_t)(tile.y + tid) * 2 + 1];
+      if (PK) {
+        sh[tid * 5 + 0] = make_float4(-a.x, -a.x, -a.y, -a.y);
+        sh[tid * 5 + 1] = make_float4(-a.z, -a.z, -a.w, -a.w);
+        sh[tid * 5 + 2] = make_float4(b.x, b.x, b.y, b.y);
+        sh[tid * 5 + 3] = make_float4(b.z, b.z, -3.f * b.x, -3.f * b.x);
+        sh[tid * 5 + 4] = make_float4(-3.f * b.y, -3.f * b.y, -3.f * b.z, -3.f * b.z);
+      } else {
+        sh[tid * 2 + 0] = make_float4(a.x, a.y, a.z, -a.w);
+        sh[tid * 2 + 1] = b;
+      }
     }
     __syncthreads();
     if (mine) {
       float pS[TT], pD[TT];
 #pragma unroll
       for (int q = 0; q < TT; ++q) pS[q] = pD[q] = 0.f;
+      if constexpr (PK) {
+        constexpr int TP = TT / 2 > 0 ? TT / 2 : 1;
+        float2 Xp[TP], Yp[TP], Zp[TP], NXp[TP], NYp[TP], NZp[TP], sS2[TP], sD2[TP];
+#pragma unroll
+        for (int k = 0; k < TT / 2; ++k) {
+          Xp[k] = make_float2(X[2 * k], X[2 * k + 1]);
+          Yp[k] = make_float2(Y[2 * k], Y[2 * k + 1]);
+          Zp[k] = make_float2(Z[2 * k], Z[2 * k + 1]);
+          NXp[k] = make_float2(NX[2 * k], NX[2 * k + 1]);
+          NYp[k] = make_float2(NY[2 * k], NY[2 * k + 1]);
+          NZp[k] = make_float2(NZ[2 * k], NZ[2 * k + 1]);
+          sS2[k] = make_float2(0.f, 0.f);
+          sD2[k] = make_float2(0.f, 0.f);
+        }
+#pragma unroll 2
+        for (int j = 0; j < tile.z; ++j) {
+          const float4 A = sh[j * 5 + 0], B = sh[j * 5 + 1], Cc = sh[j * 5 + 2], Dd = sh[j * 5 + 3],
+                       Ee = sh[j * 5 + 4];
+          const float2 my0 = make_float2(A.x, A.y), my1 = make_float2(A.z, A.w), my2 = make_float2(B.x, B.y);
+          const float2 nq = make_float2(B.z, B.w), d0 = make_float2(Cc.x, Cc.y), d1 = make_float2(Cc.z, Cc.w);
+          const float2 d2 = make_float2(Dd.x, Dd.y), e0 = make_float2(Dd.z, Dd.w), e1 = make_float2(Ee.x, Ee.y);
+          const float2 e2 = make_float2(Ee.z, Ee.w);
+#pragma unroll
+          for (int k = 0; k < TT / 2; ++k) {
+            const float2 dx = __fadd2_rn(Xp[k], my0), dy = __fadd2_rn(Yp[k], my1), dz = __fadd2_rn(Zp[k], my2);
+            const float2 r2 = __ffma2_rn(dz, dz, __ffma2_rn(dy, dy, __fmul2_rn(dx, dx)));
+            const float2 ri = make_float2(rsqrt_apx(r2.x), rsqrt_apx(r2.y));
+            const float2 ri2 = __fmul2_rn(ri, ri), ri3 = __fmul2_rn(ri2, ri);
+            const float2 rn = __ffma2_rn(dz, NZp[k], __ffma2_rn(dy, NYp[k], __fmul2_rn(dx, NXp[k])));
+            if (DO_S) sS2[k] = __ffma2_rn(__fmul2_rn(nq, rn), ri3, sS2[k]);
+            if (DO_D) {
+              const float2 dr3 = __ffma2_rn(e2, dz, __ffma2_rn(e1, dy, __fmul2_rn(e0, dx)));   // -3 d.r
+              const float2 dn = __ffma2_rn(d2, NZp[k], __ffma2_rn(d1, NYp[k], __fmul2_rn(d0, NXp[k])));
+              sD2[k] = __ffma2_rn(__ffma2_rn(__fmul2_rn(dr3, rn), ri2, dn), ri3, sD2[k]);
+            }
+          }
+        }
+#pragma unroll
+        for (int k = 0; k < TT / 2; ++k) {
+          pS[2 * k] = sS2[k].x;
+          pS[2 * k + 1] = sS2[k].y;
+          pD[2 * k] = sD2[k].x;
+          pD[2 * k + 1] = sD2[k].y;
+        }
+      } else {
 #pragma unroll 2
       for (int j = 0; j < tile.z; ++j) {
         const float4 a = sh[j * 2], b = sh[j * 2 + 1];
@@ -205,6 +262,7 @@ __global__ void __launch_bounds__(kFarTile) far_deriv_mixed_kernel(const int4* _
             pD[q] = fmaf(fmaf(-3.f * dr * rn, ri2, dn), ri3, pD[q]);
           }
         }
+      }
       }
 #pragma unroll
       for (int q = 0; q < TT; ++q) {
@@ -239,7 +297,17 @@ __global__ void __launch_bounds__(kFarTile) far_deriv_mixed_kernel(const int4* _
   }
 }
 
-constexpr int kDerivTT = 4;   // targets per thread of the mixed derivative far kernel
+// Mixed derivative far kernel: 4 targets per thread in the scalar form, or 8
+// in the packed f32x2 form when the geometry's tuned Laplace far shape is a
+// packed one (far_tt < 0).
+template <int TT, bool PK, bool DO_S, bool DO_D>
+void launch_far_deriv_mixed_tt(const DevGeom& d, const GeomHost& h, double* Sp, double* Dp, cudaStream_t st) {
+  const int nt = (int)h.tiles.size();
+  const int64_t tb = (h.N + (int64_t)kFarTile * TT - 1) / ((int64_t)kFarTile * TT);
+  const dim3 grid((unsigned)tb, (unsigned)far_split_count(tb, nt, 0));
+  far_deriv_mixed_kernel<TT, DO_S, DO_D, PK><<<grid, kFarTile, 0, st>>>(d.tiles, nt, d.src32, d.tgt32, d.cen32,
+                                                                        d.nrm, d.skip_ptr, d.skip_idx, h.N, Sp, Dp);
+}
 
 template <bool DO_S, bool DO_D>
 void launch_far_deriv_sd(const DevGeom& d, const GeomHost& h, double* Sp, double* Dp, cudaStream_t st) {
@@ -249,11 +317,10 @@ void launch_far_deriv_sd(const DevGeom& d, const GeomHost& h, double* Sp, double
     const dim3 grid((unsigned)tb, (unsigned)far_split_count(tb, nt, 0));
     far_deriv_fp64_kernel<DO_S, DO_D><<<grid, kFarTile, 0, st>>>(d.tiles, nt, d.src64, d.xyz, d.nrm, d.parts,
                                                                  d.skip_ptr, d.skip_idx, h.N, Sp, Dp);
+  } else if (h.far_tt < 0) {
+    launch_far_deriv_mixed_tt<8, true, DO_S, DO_D>(d, h, Sp, Dp, st);
   } else {
-    const int64_t tb = (h.N + (int64_t)kFarTile * kDerivTT - 1) / ((int64_t)kFarTile * kDerivTT);
-    const dim3 grid((unsigned)tb, (unsigned)far_split_count(tb, nt, 0));
-    far_deriv_mixed_kernel<kDerivTT, DO_S, DO_D><<<grid, kFarTile, 0, st>>>(
-        d.tiles, nt, d.src32, d.tgt32, d.cen32, d.nrm, d.skip_ptr, d.skip_idx, h.N, Sp, Dp);
+    launch_far_deriv_mixed_tt<4, false, DO_S, DO_D>(d, h, Sp, Dp, st);
   }
   count_launch();
 }

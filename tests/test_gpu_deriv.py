@@ -100,6 +100,22 @@ def test_mixed_vs_fp64(S, stokes100):
     assert eS < TOLMIX and eD < TOLMIX
 
 
+@pytest.mark.parametrize("tt", [2, -8])
+def test_mixed_far_forms(S, stokes100, tt):
+    """Scalar (tt > 0) and packed f32x2 (tt < 0) forms of the mixed far
+    kernel stay within the mixed bound of the FP64 path."""
+    s, c, g = stokes100
+    Sp64, Dp64 = gpu_deriv(S, g, c[0], c[1], S.SBIO_FP64)
+    saved = S.sbio_geom_get_tuning(g.h)
+    try:
+        S.sbio_geom_set_launch_shape(g.h, tt, 0)
+        Spm, Dpm = gpu_deriv(S, g, c[0], c[1], S.SBIO_MIXED)
+    finally:
+        S.sbio_geom_set_launch_shape(g.h, saved["far_tt"], saved["far_splits"])
+        S.sbio_geom_set_precision(g.h, S.SBIO_FP64)
+    assert OL.normwise_rel_err(Spm, Sp64) < TOLMIX and OL.normwise_rel_err(Dpm, Dp64) < TOLMIX
+
+
 def test_sampled_against_oracle(S, stokes100):
     """100 spheroids, p = 12: sampled nodes against the oracle's method."""
     s, c, g = stokes100
