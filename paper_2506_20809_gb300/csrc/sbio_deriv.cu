@@ -304,7 +304,9 @@ template <int TT, bool PK, bool DO_S, bool DO_D>
 void launch_far_deriv_mixed_tt(const DevGeom& d, const GeomHost& h, double* Sp, double* Dp, cudaStream_t st) {
   const int nt = (int)h.tiles.size();
   const int64_t tb = (h.N + (int64_t)kFarTile * TT - 1) / ((int64_t)kFarTile * TT);
-  const dim3 grid((unsigned)tb, (unsigned)far_split_count(tb, nt, 0));
+  // the packed form takes the geometry's tuned source splits (tuned for the
+  // same packed target blocking of the Laplace kernel)
+  const dim3 grid((unsigned)tb, (unsigned)far_split_count(tb, nt, PK ? h.far_splits : 0));
   far_deriv_mixed_kernel<TT, DO_S, DO_D, PK><<<grid, kFarTile, 0, st>>>(d.tiles, nt, d.src32, d.tgt32, d.cen32,
                                                                         d.nrm, d.skip_ptr, d.skip_idx, h.N, Sp, Dp);
 }
