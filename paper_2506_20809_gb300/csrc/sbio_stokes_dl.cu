@@ -371,6 +371,116 @@ void launch_stresslet_far(const DevGeom& tg, const DevGeom& src, const GeomHost&
   count_launch();
 }
 
+// Own-node (exterior-limit) part of the double layer, separable: for the
+// thirteen expansions in groups [d0, d1), Legendre sums at the GL rows of
+// q'(u0) P, q(u0) sqrt(1-v^2) dP/dv and q(u0) m P / sqrt(1-v^2) (the
+// single-layer self tables), then Fourier sums at every node give the local
+// gradient, rotated to the global frame G_d.  Expansion d adds to the output
+//   d = j < 3 (q_j):        -X_k G_d[j] to every component k,
+//   d = 3 + 3i + j (y_i q_j): G_d[j] to component i,
+//   d = 12 (q . nu):        -G_d[k] to component k,
+// with X the node relative to the centre.  Atomic adds: the near kernels may
+// be adding to the same outputs on another stream.
+__global__ void __launch_bounds__(256) sdl_self_kernel(int p, int n_v, int n_phi, int d0, int d1,
+                                                       const PartGeom* __restrict__ parts,
+                                                       const double* __restrict__ xyz,
+                                                       const double* __restrict__ coef,
+                                                       const double* __restrict__ qu0,
+                                                       const double* __restrict__ dqu0,
+                                                       const double* __restrict__ fP,
+                                                       const double* __restrict__ fV,
+                                                       const double* __restrict__ fF,
+                                                       const double* __restrict__ trig1,
+                                                       const double* __restrict__ gl_v,
+                                                       double* __restrict__ u_out) {
+  extern __shared__ double sm[];
+  const int i = blockIdx.x;
+  const int p1 = p + 1, nc1 = (p1 + 1) * (p1 + 1), nm1 = nm_count(p1), mw1 = 2 * p1 + 1;
+  const int G = n_v * n_phi, nd = d1 - d0;
+  const PartGeom P = parts[i];
+  const double* cf = coef + (size_t)i * 13 * nc1;
+  const double* q0 = qu0 + (size_t)i * nm1;
+  const double* dq0 = dqu0 + (size_t)i * nm1;
+  // sm[((dd * 3 + qty) * n_v + j) * mw1 + ms]: qty 0 d/du, 1 sv d/dv, 2 d/dphi / sv
+  for (int idx = threadIdx.x; idx < nd * 3 * n_v * mw1; idx += blockDim.x) {
+    const int row = idx / mw1, ms = idx - row * mw1, m = ms - p1, am = m < 0 ? -m : m;
+    const int dq = row / n_v, j = row - dq * n_v, dd = dq / 3, qty = dq - 3 * dd;
+    const double* tab = (qty == 1) ? fV : (qty == 2 ? fF : fP);
+    const double* rad = (qty == 0) ? dq0 : q0;
+    const double* c = cf + (size_t)(d0 + dd) * nc1;
+    double acc = 0.0;
+    for (int n = am; n <= p1; ++n)
+      acc = fma(c[n * n + n + m] * rad[nm_index(n, am)], tab[(size_t)j * nm1 + nm_index(n, am)], acc);
+    sm[idx] = acc;
+  }
+  __syncthreads();
+  const double sgn = P.sgn, u = P.u0;
+  const double su = P.A / P.a;   // sqrt(u0^2 + sgn)
+  const double ia = 1.0 / P.a;
+  const double* R = P.R;
+  for (int l = threadIdx.x; l < G; l += blockDim.x) {
+    const int j = l / n_phi, k = l - j * n_phi;
+    const double* tr = trig1 + (size_t)k * (p1 + 1) * 2;
+    const double v = gl_v[j], sv = sqrt((1.0 - v) * (1.0 + v));
+    const double c1 = tr[2], s1 = tr[3];
+    const double iW = rsqrt(u * u + sgn * v * v);
+    const double eu0 = u * sv * c1 * iW, eu1 = u * sv * s1 * iW, eu2 = v * su * iW;
+    const double ev0 = -su * v * c1 * iW, ev1 = -su * v * s1 * iW, ev2 = u * sv * iW;
+    const int64_t t = (int64_t)i * G + l;
+    const double X[3] = {xyz[t * 3 + 0] - P.c[0], xyz[t * 3 + 1] - P.c[1], xyz[t * 3 + 2] - P.c[2]};
+    double out[3] = {0.0, 0.0, 0.0};
+    for (int dd = 0; dd < nd; ++dd) {
+      double F[3];
+      for (int qty = 0; qty < 3; ++qty) {
+        const double* L = sm + ((size_t)(dd * 3 + qty) * n_v + j) * mw1 + p1;
+        double acc;
+        if (qty == 2) {   // d/dphi: cos -> -m sin, sin -> m cos (m inside the table)
+          acc = 0.0;
+          for (int m = 1; m <= p1; ++m) acc = fma(-L[m], tr[2 * m + 1], fma(L[-m], tr[2 * m], acc));
+        } else {
+          acc = L[0];
+          for (int m = 1; m <= p1; ++m) acc = fma(L[m], tr[2 * m], fma(L[-m], tr[2 * m + 1], acc));
+        }
+        F[qty] = acc;
+      }
+      const double gu = F[0] * su * ia * iW, gv = F[1] * ia * iW, gp = F[2] * ia / su;
+      const double gl[3] = {gu * eu0 + gv * ev0 - gp * s1, gu * eu1 + gv * ev1 + gp * c1, gu * eu2 + gv * ev2};
+      double Gd[3];
+      for (int r = 0; r < 3; ++r) Gd[r] = R[r * 3 + 0] * gl[0] + R[r * 3 + 1] * gl[1] + R[r * 3 + 2] * gl[2];
+      const int d = d0 + dd;
+      if (d < 3) {
+        for (int r = 0; r < 3; ++r) out[r] -= X[r] * Gd[d];
+      } else if (d < 12) {
+        const int ii = (d - 3) / 3, jj = (d - 3) - 3 * ii;
+        out[ii] += Gd[jj];
+      } else {
+        for (int r = 0; r < 3; ++r) out[r] -= Gd[r];
+      }
+    }
+    for (int r = 0; r < 3; ++r) atomicAdd(u_out + t * 3 + r, out[r]);
+  }
+}
+
+int sdl_self(sbio_geom* g, double* u_out, cudaStream_t st) {
+  const GeomHost& h = g->h;
+  const DevGeom& d = g->d;
+  const int p1 = h.p + 1, mw1 = 2 * p1 + 1;
+  const int groups[3] = {0, 7, 13};
+  for (int k = 0; k < 2; ++k) {
+    const int nd = groups[k + 1] - groups[k];
+    const size_t smem = (size_t)nd * 3 * h.n_v * mw1 * sizeof(double);
+    if (smem > 227 * 1024) return set_error(SBIO_ENOTSUP, "Stokes double layer self: p = %d too large", h.p);
+    if (smem > 48 * 1024)
+      SBIO_CUDA_TRY(cudaFuncSetAttribute(sdl_self_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    sdl_self_kernel<<<h.M, 256, smem, st>>>(h.p, h.n_v, h.n_phi, groups[k], groups[k + 1], d.parts, d.xyz,
+                                            d.sdl_coef, d.st_qu0, d.st_dqu0, d.st_fP, d.st_fV, d.st_fF, d.st_trig1,
+                                            d.st_glv, u_out);
+    count_launch();
+    SBIO_CUDA_TRY(cudaGetLastError());
+  }
+  return SBIO_OK;
+}
+
 int sdl_prep(sbio_geom* g, const double* qhat, double* u_init, cudaStream_t st) {
   const GeomHost& h = g->h;
   const DevGeom& d = g->d;
@@ -421,11 +531,12 @@ int sbio_apply_stokes_dl(sbio_geom* g, const double* q_hat, double* u_out, void*
     SBIO_CUDA_TRY(cudaStreamWaitEvent(ns, g->ev_fork, 0));
     v.near_grid_cap = h.st_near_ctas_per_sm > 0 ? h.st_near_ctas_per_sm * sm_count() : 0;
   }
-  // own nodes (exterior limit at u = u0), then near pairs
-  nl(v, d.sdl_self_t, d.sdl_self_s, h.sdl_n_self_prolate, h.N, u_out, ns);
+  // near pairs on the (forked) near stream; the own nodes (exterior limit at
+  // u = u0) by the separable self kernel and the far field on the caller's
   if (!h.pair_t.empty()) nl(v, d.pair_t, d.pair_s, h.n_pairs_prolate, (int64_t)h.pair_t.size(), u_out, ns);
   SBIO_CUDA_TRY(cudaGetLastError());
   if (fork) SBIO_CUDA_TRY(cudaEventRecord(g->ev_join, ns));
+  if ((rc = sdl_self(g, u_out, st))) return rc;
   launch_stresslet_far(d, d, h, h.N, u_out, st);
   SBIO_CUDA_TRY(cudaGetLastError());
   if (fork) SBIO_CUDA_TRY(cudaStreamWaitEvent(st, g->ev_join, 0));
