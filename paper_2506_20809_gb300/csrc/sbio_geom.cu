@@ -593,9 +593,8 @@ static int build_device(sbio_geom* g) {
     if ((rc = dev_alloc(g, (void**)&d.st_coef, (size_t)M * 4 * nc1 * sizeof(double), "Stokes coefficients"))) return rc;
     if ((rc = dev_alloc(g, (void**)&d.st_src64, (size_t)N * 8 * sizeof(double), "Stokes fp64 sources"))) return rc;
     if ((rc = dev_alloc(g, (void**)&d.st_src32, (size_t)N * 2 * sizeof(float4), "Stokes fp32 sources"))) return rc;
-    // Stokes double layer: exterior D factor to order p+1, FP32 normals, the
-    // own-node pairs (node, owner) sorted by the owner's kind, 13 folded
-    // expansions per particle
+    // Stokes double layer: exterior D factor to order p+1, FP32 normals, 13
+    // folded expansions per particle
     std::vector<double> extd((size_t)M * nm1), Pr2(nm_count(p1 + 1));
     for (int i = 0; i < M; ++i) {
       const PartGeom& P = h.parts[i];
@@ -612,20 +611,6 @@ static int build_device(sbio_geom* g) {
     for (int64_t t = 0; t < N; ++t)
       n32[t] = make_float4((float)h.nrm[t * 3 + 0], (float)h.nrm[t * 3 + 1], (float)h.nrm[t * 3 + 2], 0.f);
     if ((rc = upload(g, &d.nrm32, n32.data(), n32.size(), "fp32 normals"))) return rc;
-    std::vector<int32_t> st_t, st_s;
-    st_t.reserve(N);
-    st_s.reserve(N);
-    for (int kind = SBIO_PROLATE; kind <= SBIO_OBLATE; ++kind) {
-      if (kind == SBIO_OBLATE) h.sdl_n_self_prolate = (int64_t)st_t.size();
-      for (int i = 0; i < M; ++i)
-        if (h.parts[i].kind == kind)
-          for (int l = 0; l < h.G; ++l) {
-            st_t.push_back((int32_t)((int64_t)i * h.G + l));
-            st_s.push_back(i);
-          }
-    }
-    if ((rc = upload(g, &d.sdl_self_t, st_t.data(), st_t.size(), "Stokes DL self pairs"))) return rc;
-    if ((rc = upload(g, &d.sdl_self_s, st_s.data(), st_s.size(), "Stokes DL self pairs"))) return rc;
     if ((rc = dev_alloc(g, (void**)&d.sdl_coef, (size_t)M * 13 * nc1 * sizeof(double), "Stokes DL coefficients")))
       return rc;
   }

@@ -67,12 +67,10 @@ struct DevGeom {
   double* st_coef = nullptr;     // M x 4 x (p+2)^2 folded coefficients (f1, f2, f3, y.f)
   double* st_src64 = nullptr;    // N x 8: y - c_own (3), w f (3), 0, 0
   float4* st_src32 = nullptr;    // N x 2: (y - c_own, w f_1), (w f_2, w f_3, 0, 0)
-  // Stokes double layer: exterior D factor to order p+1, FP32 normals, own-node
-  // pairs sorted by kind, 13 folded expansions per particle (q_1..3, y_i q_j, q.nu)
+  // Stokes double layer: exterior D factor to order p+1, FP32 normals, 13
+  // folded expansions per particle (q_1..3, y_i q_j, q.nu)
   double* sdl_ext = nullptr;     // M x nm_count(p+1)
   float4* nrm32 = nullptr;       // N: outward normal (FP32)
-  int32_t* sdl_self_t = nullptr; // N
-  int32_t* sdl_self_s = nullptr; // N
   double* sdl_coef = nullptr;    // M x 13 x (p+2)^2
 };
 
@@ -95,7 +93,6 @@ struct GeomHost {
   int near_block = 128;                      // threads per CTA of the near kernels
   int near_ctas_per_sm = 2;                  // near CTAs per SM while overlapping with the far field (0 = no cap)
   // the same three settings for the Stokes single layer (its own kernels)
-  int64_t sdl_n_self_prolate = 0;           // own-node pairs with prolate owners come first
   int st_far_tt = 2;
   int st_far_splits = 0;
   int st_near_ctas_per_sm = 0;

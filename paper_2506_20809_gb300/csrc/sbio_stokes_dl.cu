@@ -12,9 +12,10 @@
 // quadrature of the Stokes grid ((p+2) GL x (2p+4) trapezoid), folded with
 // the exterior factors of Theorems 1-2 and the normalisation; it also writes
 // the far-field sources and, for the on-surface apply, initialises the output
-// with -q/2 (principal value = exterior limit - q/2).  The near and own-node
-// pairs evaluate the gradients (sbio_stokes_dl_near.cuh); far pairs use the
-// stresslet quadrature here.
+// with -q/2 (principal value = exterior limit - q/2).  Near pairs evaluate
+// the gradients pair by pair (sbio_stokes_dl_near.cuh), the own nodes take the
+// exterior limit separably (sdl_self_kernel), far pairs use the stresslet
+// quadrature here.
 #include "sbio_internal.cuh"
 #include "sbio_stokes_dl_near.cuh"
 

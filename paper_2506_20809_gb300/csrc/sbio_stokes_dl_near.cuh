@@ -1,11 +1,10 @@
-// Near and own-node part of the Stokes double layer: for one (target, source
-// particle) pair, the gradients of the source's thirteen folded expansions
-// (order P1 = p + 1) at the target, in four passes of solid_grad over four
-// expansions each, combined as
+// Near part of the Stokes double layer (and of its evaluation at points):
+// for one (target, source particle) pair, the gradients of the source's
+// thirteen folded expansions (order P1 = p + 1) at the target, in four passes
+// of solid_grad over four expansions each, combined as
 //     D_stk_i = -X_i sum_j d_j D[q_j] + sum_j d_j D[y_i q_j] - d_i S[q . nu]
-// (X the target relative to the source centre, global frame).  At the
-// source's own nodes this is the exterior limit (u = u0); the -q/2 of the
-// principal value is written by the prep kernel.
+// (X the target relative to the source centre, global frame).  The source's
+// own nodes are evaluated separably (sdl_self_kernel).
 #pragma once
 
 #include "sbio_grad.cuh"
