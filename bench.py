@@ -63,8 +63,8 @@ def parse():
     ap.add_argument("--oracle-sample", type=int, default=48, help="targets in the oracle's timed sample")
     ap.add_argument("--far-shape", default="", help="TT,SPLITS: fixed far-field launch shape (skips the autotuner)")
     ap.add_argument("--workload", default="poly200",
-                    choices=["poly200", "stokes100", "batch64", "serve", "deriv200", "targets200", "dirichlet200",
-                             "stokespoints100", "stokesdl100"])
+                    choices=["poly200", "stokes100", "batch64", "serve", "deriv200", "targets200", "derivpoints200",
+                             "dirichlet200", "stokespoints100", "stokesdl100"])
     ap.add_argument("--rates", default="50,100,200,500,1000,2000", help="serve: arrival rates (req/s)")
     ap.add_argument("--requests", type=int, default=48, help="serve: requests per rate")
     ap.add_argument("--slots", type=int, default=4, help="serve: concurrent request slots")
@@ -751,11 +751,13 @@ def run_deriv200(args, ws, rank, lrank):
         print(json.dumps(line), flush=True)
 
 
-def run_targets200(args, ws, rank, lrank):
+def run_targets200(args, ws, rank, lrank, deriv=False):
     """S + D of the 200-spheroid, p = 16 suspension at about 124,000 points:
     shells at distances 1e-1 .. 1e-6 from every surface (20 points per
     spheroid and distance) plus 100,000 points spread through the box;
-    mixed precision, L2 flushed before every step."""
+    mixed precision, L2 flushed before every step.  With deriv: the
+    directional derivatives of S and D at the same points along seeded random
+    unit directions."""
     import torch
 
     import __graft_entry__ as GE
@@ -777,37 +779,53 @@ def run_targets200(args, ws, rank, lrank):
     sg, mg = torch.from_numpy(c[0]).cuda(), torch.from_numpy(c[1]).cuda()
     So = torch.empty(ts.T, dtype=torch.float64, device="cuda")
     Do = torch.empty_like(So)
+    if deriv:
+        import numpy as np
+
+        E = np.random.default_rng(1).standard_normal((ts.T, 3))
+        E /= np.linalg.norm(E, axis=1, keepdims=True)
+        Ed = torch.from_numpy(E).cuda()
+
+        def step():
+            S.sbio_eval_targets_deriv(ts.h, Ed, sg, mg, So, Do)
+    else:
+        def step():
+            S.sbio_eval_targets(ts.h, sg, mg, So, Do)
     st = torch.cuda.current_stream()
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
     for _ in range(args.warmup):
-        S.sbio_eval_targets(ts.h, sg, mg, So, Do)
+        step()
     clocks = ClockSampler(lrank)
     clocks.start()
     ms = []
     l0 = S.sbio_launch_count()
     for _ in range(args.steps):
         flush.zero_()
-        ms.append(_event_time(st, lambda: S.sbio_eval_targets(ts.h, sg, mg, So, Do)))
+        ms.append(_event_time(st, step))
     launches = S.sbio_launch_count() - l0
     clk = clocks.stop()
     som, dom = So.clone(), Do.clone()
     S.sbio_geom_set_precision(g.h, S.SBIO_FP64)
-    S.sbio_eval_targets(ts.h, sg, mg, So, Do)
-    t64 = _event_time(st, lambda: S.sbio_eval_targets(ts.h, sg, mg, So, Do))
+    step()
+    t64 = _event_time(st, step)
     err = {"S": float((som - So).abs().max() / So.abs().max()), "D": float((dom - Do).abs().max() / Do.abs().max())}
     mean = statistics.mean(ms)
-    ach = 19 * ts.n_far / (mean * 1e-3) / 1e12
-    line = {"metric": "point evaluations/s (Laplace S+D at arbitrary points)", "value": ts.T * 1e3 / mean,
+    ach = (DERIV_FAR_FLOP_PER_PAIR if deriv else 19) * ts.n_far / (mean * 1e-3) / 1e12
+    metric = ("point evaluations/s (Laplace grad S . e + grad D . e at arbitrary points)" if deriv else
+              "point evaluations/s (Laplace S+D at arbitrary points)")
+    line = {"metric": metric, "value": ts.T * 1e3 / mean,
             "unit": "points/s", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup, "ms_per_step": mean,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64",
             "data": "synthetic",
-            "config": {"workload": "targets200_p16", "M": susp.M, "p": susp.p, "points": ts.T,
+            "config": {"workload": "derivpoints200_p16" if deriv else "targets200_p16", "M": susp.M, "p": susp.p,
+                       "points": ts.T,
                        "near_pairs": ts.n_near, "far_pairs": ts.n_far,
                        "points_recipe": "shells at 1e-1..1e-6 (20 per spheroid and distance) + 100,000 in the box",
                        "far_launch": {"targets_per_thread": tune[0], "source_splits": tune[1]},
                        "l2": "flushed (256 MiB write) before each step"},
             "evaluations_per_s": 1e3 / mean, "target_set_setup_ms": setup_ms,
-            "roofline": {"kernel": "whole evaluation (far_mixed_kernel dominant)", "bound": "alu",
+            "roofline": {"kernel": "whole evaluation (%s dominant)" % ("far_deriv_mixed_kernel" if deriv else
+                                                                         "far_mixed_kernel"), "bound": "alu",
                          "achieved": ach, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": ach / FP32_PEAK_TFLOPS,
                          "traffic": None},
             "fp64_gpu_points_per_s": ts.T * 1e3 / t64, "rel_err_vs_fp64_gpu": err, "gpu_launches": int(launches),
@@ -1028,6 +1046,8 @@ def main():
         run_deriv200(args, ws, rank, lrank)
     elif args.workload == "targets200":
         run_targets200(args, ws, rank, lrank)
+    elif args.workload == "derivpoints200":
+        run_targets200(args, ws, rank, lrank, deriv=True)
     elif args.workload == "dirichlet200":
         run_dirichlet200(args, ws, rank, lrank)
     elif args.workload == "stokespoints100":

@@ -308,6 +308,19 @@ int sbio_targets_info(const sbio_targets* ts, int64_t* n_points, int64_t* n_near
 int sbio_eval_targets(sbio_targets* ts, const double* sigma_tilde, const double* mu_hat, double* S_out,
                       double* D_out, void* stream);
 
+/* Directional derivatives of the layer potentials at the set's points
+ * (Sec. 3.3, Theorem 3 and eq. (dSLevalformula), with the particle-to-target
+ * split of Sec. 4.1): Sp_out[t] = grad S[sigma](x_t) . e_t and
+ * Dp_out[t] = grad D[mu](x_t) . e_t, e_t = dirs[3t .. 3t+2] (device, T x 3
+ * FP64, taken as given: not normalised).  Near pairs differentiate the
+ * source's exterior expansions (at a point on a surface this is the exterior
+ * limit: S'+ = S' - sigma/2 of sbio_apply_laplace_deriv); far pairs the
+ * differentiated quadrature.  Inputs and outputs as sbio_eval_targets (either
+ * density may be NULL; each output is given exactly when its input is;
+ * outputs overwritten).  SBIO_ENOTSUP for p > 20.  Asynchronous. */
+int sbio_eval_targets_deriv(sbio_targets* ts, const double* dirs, const double* sigma_tilde, const double* mu_hat,
+                            double* Sp_out, double* Dp_out, void* stream);
+
 /* Stokes single layer (viscosity 1) at the set's points (Sec. 4.3 with the
  * particle-to-target algorithm): u_out (device, T x 3) = S_stk[f](x_t) by
  * eq. (stokes) for near pairs and the Stokeslet quadrature otherwise;

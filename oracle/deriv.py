@@ -156,3 +156,34 @@ class DerivOracle:
                 if Dp is not None:
                     Dp[sel] += Dv
         return Sp, Dp
+
+    def eval_points(self, X, NX, sigma_t=None, mu_h=None, mode="method"):
+        """Directional derivatives d/dn S[sigma] and d/dn D[mu] at arbitrary
+        points X (T, 3) in the fluid along unit directions NX (T, 3), with the
+        per-point near/far classification of the particle-to-target algorithm
+        (Sec. 4.1): near particles by the gradient of the exterior expansion,
+        far particles by the differentiated quadrature."""
+        g = self.g
+        X = np.atleast_2d(np.asarray(X, dtype=np.float64))
+        NX = np.atleast_2d(np.asarray(NX, dtype=np.float64))
+        near = g.point_near_matrix(X)
+        if mode == "exact":
+            near = np.ones_like(near)
+        Sp = np.zeros(len(X)) if sigma_t is not None else None
+        Dp = np.zeros(len(X)) if mu_h is not None else None
+        for i, P in enumerate(g.parts):
+            si = None if sigma_t is None else sigma_t[i]
+            mi = None if mu_h is None else mu_h[i]
+            for sel, kind in ((near[:, i], "near"), (~near[:, i], "far")):
+                if not np.any(sel):
+                    continue
+                if kind == "near":
+                    Sv, Dv = solid_normal_derivative(P, self.mult[i], X[sel], NX[sel], si, mi)
+                else:
+                    Sv, Dv = quadrature_deriv_eval(P, X[sel], NX[sel], si, mi)
+                if Sp is not None:
+                    Sp[sel] += Sv
+                if Dp is not None:
+                    Dp[sel] += Dv
+        return Sp, Dp
+

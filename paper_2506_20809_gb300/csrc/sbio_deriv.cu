@@ -301,30 +301,48 @@ __global__ void __launch_bounds__(kFarTile) far_deriv_mixed_kernel(const int4* _
 // in the packed f32x2 form when the geometry's tuned Laplace far shape is a
 // packed one (far_tt < 0).
 template <int TT, bool PK, bool DO_S, bool DO_D>
-void launch_far_deriv_mixed_tt(const DevGeom& d, const GeomHost& h, double* Sp, double* Dp, cudaStream_t st) {
+void launch_far_deriv_mixed_tt(const DevGeom& d, const GeomHost& h, int64_t N, double* Sp, double* Dp,
+                               cudaStream_t st) {
   const int nt = (int)h.tiles.size();
-  const int64_t tb = (h.N + (int64_t)kFarTile * TT - 1) / ((int64_t)kFarTile * TT);
+  const int64_t tb = (N + (int64_t)kFarTile * TT - 1) / ((int64_t)kFarTile * TT);
   // the packed form takes the geometry's tuned source splits (tuned for the
   // same packed target blocking of the Laplace kernel)
   const dim3 grid((unsigned)tb, (unsigned)far_split_count(tb, nt, PK ? h.far_splits : 0));
   far_deriv_mixed_kernel<TT, DO_S, DO_D, PK><<<grid, kFarTile, 0, st>>>(d.tiles, nt, d.src32, d.tgt32, d.cen32,
-                                                                        d.nrm, d.skip_ptr, d.skip_idx, h.N, Sp, Dp);
+                                                                        d.nrm, d.skip_ptr, d.skip_idx, N, Sp, Dp);
 }
 
+// N targets: the geometry's nodes, or the points of a target-set view (whose
+// xyz, tgt32, nrm and skip lists are the points').
 template <bool DO_S, bool DO_D>
-void launch_far_deriv_sd(const DevGeom& d, const GeomHost& h, double* Sp, double* Dp, cudaStream_t st) {
+void launch_far_deriv_sd(const DevGeom& d, const GeomHost& h, int64_t N, double* Sp, double* Dp, cudaStream_t st) {
   const int nt = (int)h.tiles.size();
   if (h.precision == SBIO_FP64) {
-    const int64_t tb = (h.N + kFarTile - 1) / kFarTile;
+    const int64_t tb = (N + kFarTile - 1) / kFarTile;
     const dim3 grid((unsigned)tb, (unsigned)far_split_count(tb, nt, 0));
     far_deriv_fp64_kernel<DO_S, DO_D><<<grid, kFarTile, 0, st>>>(d.tiles, nt, d.src64, d.xyz, d.nrm, d.parts,
-                                                                 d.skip_ptr, d.skip_idx, h.N, Sp, Dp);
+                                                                 d.skip_ptr, d.skip_idx, N, Sp, Dp);
   } else if (h.far_tt < 0) {
-    launch_far_deriv_mixed_tt<8, true, DO_S, DO_D>(d, h, Sp, Dp, st);
+    launch_far_deriv_mixed_tt<8, true, DO_S, DO_D>(d, h, N, Sp, Dp, st);
   } else {
-    launch_far_deriv_mixed_tt<4, false, DO_S, DO_D>(d, h, Sp, Dp, st);
+    launch_far_deriv_mixed_tt<4, false, DO_S, DO_D>(d, h, N, Sp, Dp, st);
   }
   count_launch();
+}
+
+void launch_far_deriv(const DevGeom& d, const GeomHost& h, int64_t N, double* Sp, double* Dp, cudaStream_t st) {
+  if (N <= 0) return;
+  if (Sp && Dp)
+    launch_far_deriv_sd<true, true>(d, h, N, Sp, Dp, st);
+  else if (Sp)
+    launch_far_deriv_sd<true, false>(d, h, N, Sp, Dp, st);
+  else
+    launch_far_deriv_sd<false, true>(d, h, N, Sp, Dp, st);
+}
+
+deriv_near_launcher deriv_near_for_p(int p) {
+  deriv_near_launcher nl = deriv_near_lookup_a(p);
+  return nl ? nl : deriv_near_lookup_b(p);
 }
 
 }  // namespace
@@ -333,8 +351,7 @@ int launch_laplace_deriv(sbio_geom* g, const double* sigma, const double* mu, do
                          cudaStream_t st) {
   const GeomHost& h = g->h;
   if (h.p > 20) return set_error(SBIO_ENOTSUP, "S' / D' are built for p <= 20 (p = %d)", h.p);
-  deriv_near_launcher nl = deriv_near_lookup_a(h.p);
-  if (!nl) nl = deriv_near_lookup_b(h.p);
+  deriv_near_launcher nl = deriv_near_for_p(h.p);
   if (!nl) return set_error(SBIO_ENOTSUP, "no S' / D' near-field kernel for p = %d", h.p);
   phase_mark(g, 0, st);
   // self: writes (initialises) the outputs, and the far sources and near
@@ -356,12 +373,7 @@ int launch_laplace_deriv(sbio_geom* g, const double* sigma, const double* mu, do
     SBIO_CUDA_TRY(cudaGetLastError());
   }
   phase_mark(g, 2, st);
-  if (Sp && Dp)
-    launch_far_deriv_sd<true, true>(g->d, h, Sp, Dp, st);
-  else if (Sp)
-    launch_far_deriv_sd<true, false>(g->d, h, Sp, Dp, st);
-  else
-    launch_far_deriv_sd<false, true>(g->d, h, Sp, Dp, st);
+  launch_far_deriv(g->d, h, h.N, Sp, Dp, st);
   SBIO_CUDA_TRY(cudaGetLastError());
   if (fork) SBIO_CUDA_TRY(cudaStreamWaitEvent(st, g->ev_join, 0));
   phase_mark(g, 3, st);
@@ -383,6 +395,54 @@ int sbio_apply_laplace_deriv(sbio_geom* g, const double* sigma_tilde, const doub
   if (!sigma_tilde && !mu_hat) return set_error(SBIO_EINVAL, "nothing to apply");
   SBIO_CUDA_TRY(cudaSetDevice(g->ctx->device));
   return launch_laplace_deriv(g, sigma_tilde, mu_hat, Sp_out, Dp_out, (cudaStream_t)stream);
+}
+
+int sbio_eval_targets_deriv(sbio_targets* ts, const double* dirs, const double* sigma_tilde, const double* mu_hat,
+                            double* Sp_out, double* Dp_out, void* stream) {
+  clear_error();
+  sbio_geom* g = nullptr;
+  const DevGeom* view = nullptr;
+  int64_t T = 0, n_pro = 0, n_pairs = 0;
+  int rc = targets_view(ts, &g, &view, &T, &n_pro, &n_pairs);
+  if (rc) return rc;
+  if ((sigma_tilde == nullptr) != (Sp_out == nullptr) || (mu_hat == nullptr) != (Dp_out == nullptr))
+    return set_error(SBIO_EINVAL, "each output must be given exactly when its input is");
+  if (!sigma_tilde && !mu_hat) return set_error(SBIO_EINVAL, "nothing to evaluate");
+  if (T > 0 && !dirs) return set_error(SBIO_EINVAL, "null directions");
+  const GeomHost& h = g->h;
+  if (h.p > 20) return set_error(SBIO_ENOTSUP, "S' / D' are built for p <= 20 (p = %d)", h.p);
+  deriv_near_launcher nl = deriv_near_for_p(h.p);
+  if (!nl) return set_error(SBIO_ENOTSUP, "no S' / D' near-field kernel for p = %d", h.p);
+  SBIO_CUDA_TRY(cudaSetDevice(g->ctx->device));
+  if (T == 0) return SBIO_OK;
+  cudaStream_t st = (cudaStream_t)stream;
+  if (Sp_out) SBIO_CUDA_TRY(cudaMemsetAsync(Sp_out, 0, T * sizeof(double), st));
+  if (Dp_out) SBIO_CUDA_TRY(cudaMemsetAsync(Dp_out, 0, T * sizeof(double), st));
+  // far sources and near coefficients of these densities (no self output)
+  rc = launch_synth_mode(g, sigma_tilde, mu_hat, nullptr, nullptr, 0, st);
+  if (rc) return rc;
+  // the set's view with the directions as the target "normals": the near
+  // kernel dots the expansion gradient with them, the far kernels the
+  // differentiated quadrature; source normals are not read by either
+  DevGeom v = *view;
+  v.nrm = const_cast<double*>(dirs);   // read only
+  const bool fork = g->overlap && !g->timing && g->near_stream && n_pairs > 0;
+  if (fork) {
+    SBIO_CUDA_TRY(cudaEventRecord(g->ev_fork, st));
+    SBIO_CUDA_TRY(cudaStreamWaitEvent(g->near_stream, g->ev_fork, 0));
+    v.near_grid_cap = h.near_ctas_per_sm > 0 ? h.near_ctas_per_sm * sm_count() : 0;
+    nl(v, n_pro, n_pairs, Sp_out, Dp_out, g->near_stream);
+    v.near_grid_cap = 0;
+    SBIO_CUDA_TRY(cudaGetLastError());
+    SBIO_CUDA_TRY(cudaEventRecord(g->ev_join, g->near_stream));
+  } else if (n_pairs > 0) {
+    nl(v, n_pro, n_pairs, Sp_out, Dp_out, st);
+    SBIO_CUDA_TRY(cudaGetLastError());
+  }
+  launch_far_deriv(v, h, T, Sp_out, Dp_out, st);
+  SBIO_CUDA_TRY(cudaGetLastError());
+  if (fork) SBIO_CUDA_TRY(cudaStreamWaitEvent(st, g->ev_join, 0));
+  return SBIO_OK;
 }
 
 }  // extern "C"

@@ -186,6 +186,12 @@ int launch_laplace(sbio_geom* g, const double* sigma, const double* mu, double* 
                    uint32_t parts, cudaStream_t st);
 int launch_synth(sbio_geom* g, const double* sigma, const double* mu, double* S, double* D, bool write_self,
                  cudaStream_t st);
+// A target set's view of its geometry: the geometry's device tables with the
+// set's points as targets (xyz, tgt32, near pairs, skip lists; nrm null),
+// the point count and the near pairs (the first n_pro on prolate sources).
+int targets_view(sbio_targets* ts, sbio_geom** g, const DevGeom** view, int64_t* T, int64_t* n_pro,
+                 int64_t* n_pairs);
+
 int launch_synth_mode(sbio_geom* g, const double* sigma, const double* mu, double* S, double* D, int self_mode,
                       cudaStream_t st);
 int launch_near(sbio_geom* g, double* S, double* D, cudaStream_t st);

@@ -25,8 +25,6 @@ namespace sbio {
 
 stokes_dl_near_launcher stokes_dl_near_lookup_a(int p);
 stokes_dl_near_launcher stokes_dl_near_lookup_b(int p);
-int targets_view(sbio_targets* ts, sbio_geom** g, const DevGeom** view, int64_t* T, int64_t* n_pro,
-                 int64_t* n_pairs);
 
 namespace {
 

@@ -18,9 +18,6 @@ stokes_near_launcher stokes_near_lookup_b(int p);
 stokes_point_near_launcher stokes_point_near_lookup_a(int p);
 stokes_point_near_launcher stokes_point_near_lookup_b(int p);
 
-// target-set internals shared with sbio_targets.cu
-int targets_view(sbio_targets* ts, sbio_geom** g, const DevGeom** view, int64_t* T, int64_t* n_pro,
-                 int64_t* n_pairs);
 
 namespace {
 

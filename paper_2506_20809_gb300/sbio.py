@@ -121,6 +121,7 @@ _SIGS = {
     "sbio_targets_info": (C.c_int, [_vp, C.POINTER(C.c_int64), C.POINTER(C.c_int64), C.POINTER(C.c_int64),
                                     C.POINTER(C.c_size_t)]),
     "sbio_eval_targets": (C.c_int, [_vp, _vp, _vp, _vp, _vp, _vp]),
+    "sbio_eval_targets_deriv": (C.c_int, [_vp, _vp, _vp, _vp, _vp, _vp, _vp]),
     "sbio_eval_targets_stokes": (C.c_int, [_vp, _vp, _vp, _vp, _vp]),
     "sbio_eval_targets_stokes_dl": (C.c_int, [_vp, _vp, _vp, _vp]),
     "sbio_apply_stokes_dl": (C.c_int, [_vp, _vp, _vp, _vp]),
@@ -383,6 +384,13 @@ def sbio_targets_info(ts):
 def sbio_eval_targets(ts, sigma_tilde, mu_hat, S_out, D_out, stream=None):
     """S and D at the set's points (device tensors; either input may be None)."""
     _check(_lib.sbio_eval_targets(ts, _ptr(sigma_tilde), _ptr(mu_hat), _ptr(S_out), _ptr(D_out), _stream(stream)))
+
+
+def sbio_eval_targets_deriv(ts, dirs, sigma_tilde, mu_hat, Sp_out, Dp_out, stream=None):
+    """Directional derivatives of S and D at the set's points along dirs
+    (device T x 3); device tensors, either density may be None."""
+    _check(_lib.sbio_eval_targets_deriv(ts, _ptr(dirs), _ptr(sigma_tilde), _ptr(mu_hat), _ptr(Sp_out), _ptr(Dp_out),
+                                        _stream(stream)))
 
 
 def sbio_eval_targets_stokes(ts, f_tilde, u_out, p_out=None, stream=None):

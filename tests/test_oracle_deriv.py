@@ -360,3 +360,23 @@ def test_points_inside_a_spheroid_are_rejected():
     inside = g.parts[1].center[None, :] + 0.01
     with pytest.raises(ValueError):
         O.eval_points(inside, np.zeros((2, 25)), None)
+
+
+def test_point_derivatives_are_gradients_of_the_point_values():
+    """Directional derivatives at points equal central differences of the
+    point values along the direction (method mode, the same near/far split)."""
+    p = 8
+    g = _two_particles(p, gap=1.5)
+    rng = np.random.default_rng(12)
+    sig = rng.standard_normal((2, (p + 1) ** 2)) / (1 + np.arange((p + 1) ** 2))
+    mu = rng.standard_normal((2, (p + 1) ** 2)) / (1 + np.arange((p + 1) ** 2))
+    X = _shell_points(g, [0.05, 0.3, 2.0], 4, seed=3)
+    NX = rng.standard_normal(X.shape)
+    NX /= np.linalg.norm(NX, axis=1, keepdims=True)
+    Sp, Dp = DV.DerivOracle(g).eval_points(X, NX, sig, mu, "exact")
+    O = LP.LaplaceOracle(g)
+    h = 1e-5
+    Sa, Da = O.eval_points(X + h * NX, sig, mu, "exact")
+    Sb, Db = O.eval_points(X - h * NX, sig, mu, "exact")
+    assert LP.normwise_rel_err(Sp, (Sa - Sb) / (2 * h)) < 1e-7
+    assert LP.normwise_rel_err(Dp, (Da - Db) / (2 * h)) < 1e-7
