@@ -18,12 +18,14 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 OUT_DIR = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libsbio.so")
-SOURCES = ["sbio_geom.cu", "sbio_laplace.cu", "sbio_stokes.cu", "sbio_near_pa.cu", "sbio_near_pb.cu",
-           "sbio_near_pc.cu", "sbio_near_pd.cu", "sbio_noalloc.cu", "sbio_stokes_near_pa.cu",
-           "sbio_stokes_near_pb.cu", "sbio_batch.cu", "sbio_server.cu", "sbio_deriv.cu", "sbio_deriv_near_pa.cu",
-           "sbio_deriv_near_pb.cu", "sbio_targets.cu", "sbio_solve.cu",
-           "sbio_stokes_points.cu", "sbio_stokes_points_pa.cu", "sbio_stokes_points_pb.cu",
-           "sbio_stokes_dl.cu", "sbio_stokes_dl_near_pa.cu", "sbio_stokes_dl_near_pb.cu"]
+SOURCES = ["sbio_geom.cu", "sbio_laplace.cu", "sbio_stokes.cu", "sbio_noalloc.cu", "sbio_batch.cu", "sbio_server.cu",
+           "sbio_deriv.cu", "sbio_targets.cu", "sbio_solve.cu", "sbio_stokes_points.cu", "sbio_stokes_dl.cu"]
+# near-field kernels, split by expansion order so that the unrolled variants compile in parallel
+SOURCES += [f"sbio_near_p{c}.cu" for c in "abcd"]
+SOURCES += [f"sbio_deriv_near_p{c}.cu" for c in "ab"]
+SOURCES += [f"sbio_stokes_near_p{c}.cu" for c in "abc"]
+SOURCES += [f"sbio_stokes_points_p{c}.cu" for c in "abc"]
+SOURCES += [f"sbio_stokes_dl_near_p{c}.cu" for c in "abcdefghij"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -11,6 +11,45 @@
 
 namespace sbio {
 
+// Gradient dotted with the target's direction, term by term: with nl the
+// direction in the source's frame, n_rho = c1 nl_x + s1 nl_y and
+// n_phi = c1 nl_y - s1 nl_x, the directional derivative of a term is
+// K_u Tu + K_v Tv (+ K_p Tp for the phi-derivative of its trig factor) with
+// K_u = n_rho k_ru + nl_z k_zu, K_v = n_rho k_rv + nl_z k_zv, K_p = n_phi k_p.
+template <bool DO_S, bool DO_D>
+struct DerivNearVisitor {
+  const double* __restrict__ alpha;
+  const double* __restrict__ beta;
+  double nl0, nl1, nl2;
+  double Ku, Kv, Kp, cm, sm;
+  double Sp, Dp;
+
+  __device__ __forceinline__ void begin(const GradFrame& f) {
+    const double nr = f.c1 * nl0 + f.s1 * nl1, np = f.c1 * nl1 - f.s1 * nl0;
+    Ku = fma(nr, f.k_ru, nl2 * f.k_zu);
+    Kv = fma(nr, f.k_rv, nl2 * f.k_zv);
+    Kp = np * f.k_p;
+    Sp = Dp = 0.0;
+  }
+  __device__ __forceinline__ void order(int, double c, double s) {
+    cm = c;
+    sm = s;
+  }
+  __device__ __forceinline__ void term(int n, int m, double, double Tu, double Tv, double Tp) {
+    const double bn = fma(Ku, Tu, Kv * Tv), bp = Kp * Tp;
+    const double Bc = fma(bn, cm, -bp * sm), Bs = fma(bn, sm, bp * cm);
+    const int kc = n * n + n + m, ks = n * n + n - m;
+    if (DO_S) Sp = fma(alpha[kc], Bc, fma(alpha[ks], Bs, Sp));
+    if (DO_D) Dp = fma(beta[kc], Bc, fma(beta[ks], Bs, Dp));
+  }
+  __device__ __forceinline__ void term0(int n, double, double Tu, double Tv) {
+    const double B = fma(Ku, Tu, Kv * Tv);
+    const int k = n * n + n;
+    if (DO_S) Sp = fma(alpha[k], B, Sp);
+    if (DO_D) Dp = fma(beta[k], B, Dp);
+  }
+};
+
 template <int P, int KIND, bool DO_S, bool DO_D>
 __global__ void __launch_bounds__(128) deriv_near_kernel(const int32_t* __restrict__ pair_t,
                                                          const int32_t* __restrict__ pair_s, int64_t first,
@@ -22,7 +61,6 @@ __global__ void __launch_bounds__(128) deriv_near_kernel(const int32_t* __restri
                                                          const double* __restrict__ inv_tab,
                                                          double* __restrict__ Sp_out, double* __restrict__ Dp_out) {
   constexpr int NC = (P + 1) * (P + 1);
-  constexpr int ND = (DO_S ? 1 : 0) + (DO_D ? 1 : 0);
   for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < count; r += (int64_t)gridDim.x * blockDim.x) {
     const int64_t idx = first + r;
     const int t = pair_t[idx], i = pair_s[idx];
@@ -33,23 +71,17 @@ __global__ void __launch_bounds__(128) deriv_near_kernel(const int32_t* __restri
     const double xl = G.R[0] * X0 + G.R[3] * X1 + G.R[6] * X2;
     const double yl = G.R[1] * X0 + G.R[4] * X1 + G.R[7] * X2;
     const double zl = G.R[2] * X0 + G.R[5] * X1 + G.R[8] * X2;
-    // target normal in the source's local frame
     const double n0 = nrm[(int64_t)t * 3 + 0], n1 = nrm[(int64_t)t * 3 + 1], n2 = nrm[(int64_t)t * 3 + 2];
-    const double nl0 = G.R[0] * n0 + G.R[3] * n1 + G.R[6] * n2;
-    const double nl1 = G.R[1] * n0 + G.R[4] * n1 + G.R[7] * n2;
-    const double nl2 = G.R[2] * n0 + G.R[5] * n1 + G.R[8] * n2;
-    const double* c[ND];
-    int k = 0;
-    if (DO_S) c[k++] = alpha + (size_t)i * NC;
-    if (DO_D) c[k++] = beta + (size_t)i * NC;
-    double F[ND], g[ND][3];
-    solid_grad<P, KIND, ND>(xl, yl, zl, G.a, c, inv_tab, F, g);
-    k = 0;
-    if (DO_S) {
-      atomicAdd(Sp_out + t, g[k][0] * nl0 + g[k][1] * nl1 + g[k][2] * nl2);
-      ++k;
-    }
-    if (DO_D) atomicAdd(Dp_out + t, g[k][0] * nl0 + g[k][1] * nl1 + g[k][2] * nl2);
+    DerivNearVisitor<DO_S, DO_D> vis;
+    vis.alpha = alpha + (size_t)i * NC;
+    vis.beta = beta + (size_t)i * NC;
+    // target direction in the source's local frame
+    vis.nl0 = G.R[0] * n0 + G.R[3] * n1 + G.R[6] * n2;
+    vis.nl1 = G.R[1] * n0 + G.R[4] * n1 + G.R[7] * n2;
+    vis.nl2 = G.R[2] * n0 + G.R[5] * n1 + G.R[8] * n2;
+    solid_terms<P, KIND>(xl, yl, zl, G.a, inv_tab, vis);
+    if (DO_S) atomicAdd(Sp_out + t, vis.Sp);
+    if (DO_D) atomicAdd(Dp_out + t, vis.Dp);
   }
 }
 

@@ -16,6 +16,7 @@ namespace sbio {
 
 stokes_near_launcher stokes_near_lookup_a(int p);
 stokes_near_launcher stokes_near_lookup_b(int p);
+stokes_near_launcher stokes_near_lookup_c(int p);
 
 constexpr double kInv8Pi = 0.039788735772973836;   // 1/(8 pi)
 
@@ -497,6 +498,7 @@ int launch_stokes(sbio_geom* g, const double* f, double* u, cudaStream_t st) {
   if (p > 20) return set_error(SBIO_ENOTSUP, "Stokes single layer is built for p <= 20 (p = %d)", p);
   stokes_near_launcher nl = stokes_near_lookup_a(p);
   if (!nl) nl = stokes_near_lookup_b(p);
+  if (!nl) nl = stokes_near_lookup_c(p);
   if (!nl) return set_error(SBIO_ENOTSUP, "no Stokes near-field kernel for p = %d", p);
   const int p1 = p + 1, mw1 = 2 * p1 + 1;
   phase_mark(g, 0, st);

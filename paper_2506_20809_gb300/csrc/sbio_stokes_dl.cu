@@ -7,8 +7,10 @@
 //     D_stk[q]_i = -x_i sum_j d_j D[q_j] + sum_j d_j D[y_i q_j] - d_i S[q . nu],
 // x, y measured from the source particle's centre.  Per particle the prep
 // kernel forms the thirteen exterior expansions, exact at order p + 1: the
-// q_j (plain input coefficients), the y_i q_j (plain) and q . nu (modified
-// basis, since nu sqrt(u0^2 -+ v^2) is of degree one) by the product
+// q_l (plain input coefficients), the y_i q_l (plain) and q . nu (modified
+// basis, since nu sqrt(u0^2 -+ v^2) is of degree one), with the density
+// index l of the first twelve in the particle's local frame
+// (q_l = sum_j R_jl q_j, so that sum_j d_j acts as a local divergence), by the product
 // quadrature of the Stokes grid ((p+2) GL x (2p+4) trapezoid), folded with
 // the exterior factors of Theorems 1-2 and the normalisation; it also writes
 // the far-field sources and, for the on-surface apply, initialises the output
@@ -23,8 +25,17 @@ struct sbio_targets;
 
 namespace sbio {
 
+// one lookup per translation unit of near kernels (orders 1-8, 9-12, then one each)
 stokes_dl_near_launcher stokes_dl_near_lookup_a(int p);
 stokes_dl_near_launcher stokes_dl_near_lookup_b(int p);
+stokes_dl_near_launcher stokes_dl_near_lookup_c(int p);
+stokes_dl_near_launcher stokes_dl_near_lookup_d(int p);
+stokes_dl_near_launcher stokes_dl_near_lookup_e(int p);
+stokes_dl_near_launcher stokes_dl_near_lookup_f(int p);
+stokes_dl_near_launcher stokes_dl_near_lookup_g(int p);
+stokes_dl_near_launcher stokes_dl_near_lookup_h(int p);
+stokes_dl_near_launcher stokes_dl_near_lookup_i(int p);
+stokes_dl_near_launcher stokes_dl_near_lookup_j(int p);
 
 namespace {
 
@@ -93,7 +104,7 @@ __global__ void __launch_bounds__(256) sdl_prep_kernel(
     Lq[(d * n_q + j) * mw + ms] = acc;
   }
   __syncthreads();
-  // (3) the ten products at the grid points: y_i q_j and q . (nu sqrt(w))
+  // (3) the ten products at the grid points: y_i q_l (local l) and q . (nu sqrt(w))
   const double a = P.a, u0 = P.u0, su0 = sqrt(u0 * u0 + P.sgn);
   for (int l = threadIdx.x; l < n_q * n_f; l += blockDim.x) {
     const int j = l / n_f, k = l - j * n_f;
@@ -108,13 +119,14 @@ __global__ void __launch_bounds__(256) sdl_prep_kernel(
     const double v = qv[j], sv = sqrt((1.0 - v) * (1.0 + v)), c1 = tr[2], s1 = tr[3];
     const double yl[3] = {a * su0 * sv * c1, a * su0 * sv * s1, a * u0 * v};
     const double nl[3] = {u0 * sv * c1, u0 * sv * s1, su0 * v};   // nu sqrt(u0^2 + sgn v^2), local frame
-    double yg[3], ng[3];
+    double yg[3], ng[3], ql[3];
     for (int r = 0; r < 3; ++r) {
       yg[r] = P.R[r * 3 + 0] * yl[0] + P.R[r * 3 + 1] * yl[1] + P.R[r * 3 + 2] * yl[2];
       ng[r] = P.R[r * 3 + 0] * nl[0] + P.R[r * 3 + 1] * nl[1] + P.R[r * 3 + 2] * nl[2];
+      ql[r] = P.R[0 * 3 + r] * qq[0] + P.R[1 * 3 + r] * qq[1] + P.R[2 * 3 + r] * qq[2];   // q in the local frame
     }
     for (int ii = 0; ii < 3; ++ii)
-      for (int jj = 0; jj < 3; ++jj) hv[((3 * ii + jj) * n_q + j) * n_f + k] = yg[ii] * qq[jj];
+      for (int jj = 0; jj < 3; ++jj) hv[((3 * ii + jj) * n_q + j) * n_f + k] = yg[ii] * ql[jj];
     hv[(9 * n_q + j) * n_f + k] = qq[0] * ng[0] + qq[1] * ng[1] + qq[2] * ng[2];
   }
   __syncthreads();
@@ -137,9 +149,10 @@ __global__ void __launch_bounds__(256) sdl_prep_kernel(
     const int m = k - n * n - n, am = m < 0 ? -m : m;
     double c;
     if (d < 3) {
-      c = (n <= p) ? qh[d * nc + k] : 0.0;
+      // component d of q in the local frame
+      c = (n <= p) ? P.R[0 * 3 + d] * qh[k] + P.R[1 * 3 + d] * qh[nc + k] + P.R[2 * 3 + d] * qh[2 * nc + k] : 0.0;
     } else {
-      const int e = d - 3;   // 0..8: y_i q_j, 9: q . nu
+      const int e = d - 3;   // 0..8: y_i q_l, 9: q . nu
       double acc = 0.0;
       for (int j = 0; j < n_q; ++j) acc = fma(Hm[(e * n_q + j) * mw1 + m + p1], qptab[(size_t)j * nm1 + nm_index(n, am)], acc);
       c = (m ? 1.4142135623730951 : 1.0) * acc;
@@ -374,10 +387,11 @@ void launch_stresslet_far(const DevGeom& tg, const DevGeom& src, const GeomHost&
 // thirteen expansions in groups [d0, d1), Legendre sums at the GL rows of
 // q'(u0) P, q(u0) sqrt(1-v^2) dP/dv and q(u0) m P / sqrt(1-v^2) (the
 // single-layer self tables), then Fourier sums at every node give the local
-// gradient, rotated to the global frame G_d.  Expansion d adds to the output
-//   d = j < 3 (q_j):        -X_k G_d[j] to every component k,
-//   d = 3 + 3i + j (y_i q_j): G_d[j] to component i,
-//   d = 12 (q . nu):        -G_d[k] to component k,
+// gradient g_d in the source's frame.  The density index of expansions 0..11
+// is in the local frame (q_l = sum_j R_jl q_j), so expansion d adds
+//   d = l < 3 (q_l):          -X_k g_d[l] to every component k,
+//   d = 3 + 3i + l (y_i q_l): g_d[l] to component i,
+//   d = 12 (q . nu):          -(R g_d)_k to component k,
 // with X the node relative to the centre.  Atomic adds: the near kernels may
 // be adding to the same outputs on another stream.
 __global__ void __launch_bounds__(256) sdl_self_kernel(int p, int n_v, int n_phi, int d0, int d1,
@@ -444,16 +458,15 @@ __global__ void __launch_bounds__(256) sdl_self_kernel(int p, int n_v, int n_phi
       }
       const double gu = F[0] * su * ia * iW, gv = F[1] * ia * iW, gp = F[2] * ia / su;
       const double gl[3] = {gu * eu0 + gv * ev0 - gp * s1, gu * eu1 + gv * ev1 + gp * c1, gu * eu2 + gv * ev2};
-      double Gd[3];
-      for (int r = 0; r < 3; ++r) Gd[r] = R[r * 3 + 0] * gl[0] + R[r * 3 + 1] * gl[1] + R[r * 3 + 2] * gl[2];
       const int d = d0 + dd;
       if (d < 3) {
-        for (int r = 0; r < 3; ++r) out[r] -= X[r] * Gd[d];
+        // local divergence of (D[q_l]): component d of expansion d
+        for (int r = 0; r < 3; ++r) out[r] -= X[r] * gl[d];
       } else if (d < 12) {
-        const int ii = (d - 3) / 3, jj = (d - 3) - 3 * ii;
-        out[ii] += Gd[jj];
+        const int ii = (d - 3) / 3, ll = (d - 3) - 3 * ii;
+        out[ii] += gl[ll];
       } else {
-        for (int r = 0; r < 3; ++r) out[r] -= Gd[r];
+        for (int r = 0; r < 3; ++r) out[r] -= R[r * 3 + 0] * gl[0] + R[r * 3 + 1] * gl[1] + R[r * 3 + 2] * gl[2];
       }
     }
     for (int r = 0; r < 3; ++r) atomicAdd(u_out + t * 3 + r, out[r]);
@@ -499,8 +512,14 @@ int sdl_prep(sbio_geom* g, const double* qhat, double* u_init, cudaStream_t st) 
 }
 
 stokes_dl_near_launcher sdl_near_for(int p) {
-  stokes_dl_near_launcher nl = stokes_dl_near_lookup_a(p);
-  return nl ? nl : stokes_dl_near_lookup_b(p);
+  stokes_dl_near_launcher (*const tab[])(int) = {stokes_dl_near_lookup_a, stokes_dl_near_lookup_b,
+                                                  stokes_dl_near_lookup_c, stokes_dl_near_lookup_d,
+                                                  stokes_dl_near_lookup_e, stokes_dl_near_lookup_f,
+                                                  stokes_dl_near_lookup_g, stokes_dl_near_lookup_h,
+                                                  stokes_dl_near_lookup_i, stokes_dl_near_lookup_j};
+  for (auto f : tab)
+    if (stokes_dl_near_launcher nl = f(p)) return nl;
+  return nullptr;
 }
 
 }  // namespace

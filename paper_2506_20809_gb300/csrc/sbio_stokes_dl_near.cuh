@@ -1,15 +1,76 @@
 // Near part of the Stokes double layer (and of its evaluation at points):
-// for one (target, source particle) pair, the gradients of the source's
-// thirteen folded expansions (order P1 = p + 1) at the target, in four passes
-// of solid_grad over four expansions each, combined as
+// for one (target, source particle) pair,
 //     D_stk_i = -X_i sum_j d_j D[q_j] + sum_j d_j D[y_i q_j] - d_i S[q . nu]
-// (X the target relative to the source centre, global frame).  The source's
-// own nodes are evaluated separably (sdl_self_kernel).
+// (X the target relative to the source centre, global frame).  The thirteen
+// expansions (order P1 = p + 1) are stored with the density index j turned
+// into the source's local frame (q_l = sum_j R_jl q_j, y_i q_l likewise), so
+// that the two divergences are local-frame divergences,
+//     sum_j d_j D[q_j] = sum_l d'_l D[q_l],   sum_j d_j D[y_i q_j] = sum_l d'_l D[y_i q_l],
+// and one pass of solid_terms serves them all: each term's local Cartesian
+// gradient (cos and sin parts) is formed once and contracted with the
+// coefficients of the four vector fields (3 components each) and of S[q . nu],
+// whose local gradient is rotated to the global frame at the end.  The
+// source's own nodes are evaluated separably (sdl_self_kernel).
 #pragma once
 
 #include "sbio_grad.cuh"
 
 namespace sbio {
+
+template <int NC>
+struct SdlNearVisitor {
+  const double* __restrict__ cf;   // 13 x NC: q_l (0..2), y_i q_l (3 + 3i + l), q . nu (12)
+  double k_ru, k_rv, k_zu, k_zv, k_p, c1, s1;
+  double cm, sm, tcc, tss, tsc, tcs;
+  double div, t2[3], gS[3];
+
+  __device__ __forceinline__ void begin(const GradFrame& f) {
+    k_ru = f.k_ru; k_rv = f.k_rv; k_zu = f.k_zu; k_zv = f.k_zv; k_p = f.k_p; c1 = f.c1; s1 = f.s1;
+    div = 0.0;
+#pragma unroll
+    for (int l = 0; l < 3; ++l) t2[l] = gS[l] = 0.0;
+  }
+  __device__ __forceinline__ void order(int, double c, double s) {
+    cm = c; sm = s;
+    tcc = c1 * c; tss = s1 * s; tsc = s1 * c; tcs = c1 * s;
+  }
+  // sum over the three components of field (base + l) of coefficient x gradient component l
+  __device__ __forceinline__ double field(int base, int kc, int ks, const double* Bc, const double* Bs) const {
+    double r = 0.0;
+#pragma unroll
+    for (int l = 0; l < 3; ++l) r = fma(cf[(base + l) * NC + kc], Bc[l], fma(cf[(base + l) * NC + ks], Bs[l], r));
+    return r;
+  }
+  __device__ __forceinline__ void term(int n, int m, double, double Tu, double Tv, double Tp) {
+    const double al = fma(k_ru, Tu, k_rv * Tv), z = fma(k_zu, Tu, k_zv * Tv), g = k_p * Tp;
+    const double Bc[3] = {fma(al, tcc, g * tss), fma(al, tsc, -g * tcs), z * cm};
+    const double Bs[3] = {fma(al, tcs, -g * tsc), fma(al, tss, g * tcc), z * sm};
+    const int kc = n * n + n + m, ks = n * n + n - m;
+    div += field(0, kc, ks, Bc, Bs);
+#pragma unroll
+    for (int i = 0; i < 3; ++i) t2[i] += field(3 + 3 * i, kc, ks, Bc, Bs);
+#pragma unroll
+    for (int l = 0; l < 3; ++l) gS[l] = fma(cf[12 * NC + kc], Bc[l], fma(cf[12 * NC + ks], Bs[l], gS[l]));
+  }
+  __device__ __forceinline__ void term0(int n, double, double Tu, double Tv) {
+    const double al = fma(k_ru, Tu, k_rv * Tv), z = fma(k_zu, Tu, k_zv * Tv);
+    const double B[3] = {c1 * al, s1 * al, z};
+    const int k = n * n + n;
+    double r = 0.0;
+#pragma unroll
+    for (int l = 0; l < 3; ++l) r = fma(cf[l * NC + k], B[l], r);
+    div += r;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      double ri = 0.0;
+#pragma unroll
+      for (int l = 0; l < 3; ++l) ri = fma(cf[(3 + 3 * i + l) * NC + k], B[l], ri);
+      t2[i] += ri;
+    }
+#pragma unroll
+    for (int l = 0; l < 3; ++l) gS[l] = fma(cf[12 * NC + k], B[l], gS[l]);
+  }
+};
 
 template <int P1, int KIND>
 __global__ void __launch_bounds__(128) stokes_dl_near_kernel(const int32_t* __restrict__ pair_t,
@@ -30,42 +91,16 @@ __global__ void __launch_bounds__(128) stokes_dl_near_kernel(const int32_t* __re
     const double xl = G.R[0] * X0 + G.R[3] * X1 + G.R[6] * X2;
     const double yl = G.R[1] * X0 + G.R[4] * X1 + G.R[7] * X2;
     const double zl = G.R[2] * X0 + G.R[5] * X1 + G.R[8] * X2;
-    const double* cf = coef + (size_t)i * 13 * NC;
+    SdlNearVisitor<NC> vis;
+    vis.cf = coef + (size_t)i * 13 * NC;
+    solid_terms<P1, KIND>(xl, yl, zl, G.a, inv_tab, vis);
     const double* R = G.R;
-    double div_q = 0.0, t2[3] = {0.0, 0.0, 0.0}, t3[3] = {0.0, 0.0, 0.0};
-#pragma unroll 1
-    for (int pass = 0; pass < 4; ++pass) {
-      // pass 0: q_1, q_2, q_3, q.nu; pass 1 + i: y_i q_1, y_i q_2, y_i q_3 (4th slot unused)
-      const double* c[4];
-      if (pass == 0) {
-        c[0] = cf;
-        c[1] = cf + NC;
-        c[2] = cf + 2 * NC;
-        c[3] = cf + 12 * NC;
-      } else {
-        const double* b = cf + (3 + 3 * (pass - 1)) * NC;
-        c[0] = b;
-        c[1] = b + NC;
-        c[2] = b + 2 * NC;
-        c[3] = b;
-      }
-      double F[4], g[4][3];
-      solid_grad<P1, KIND, 4>(xl, yl, zl, G.a, c, inv_tab, F, g);
-      // global gradient component k of expansion d: sum_l R[k][l] g_d[l]
-      double s = 0.0;
+    double t3[3];
 #pragma unroll
-      for (int k = 0; k < 3; ++k) s += R[k * 3 + 0] * g[k][0] + R[k * 3 + 1] * g[k][1] + R[k * 3 + 2] * g[k][2];
-      if (pass == 0) {
-        div_q = s;
-#pragma unroll
-        for (int k = 0; k < 3; ++k) t3[k] = R[k * 3 + 0] * g[3][0] + R[k * 3 + 1] * g[3][1] + R[k * 3 + 2] * g[3][2];
-      } else {
-        t2[pass - 1] = s;
-      }
-    }
-    atomicAdd(u_out + (int64_t)t * 3 + 0, -X0 * div_q + t2[0] - t3[0]);
-    atomicAdd(u_out + (int64_t)t * 3 + 1, -X1 * div_q + t2[1] - t3[1]);
-    atomicAdd(u_out + (int64_t)t * 3 + 2, -X2 * div_q + t2[2] - t3[2]);
+    for (int k = 0; k < 3; ++k) t3[k] = R[k * 3 + 0] * vis.gS[0] + R[k * 3 + 1] * vis.gS[1] + R[k * 3 + 2] * vis.gS[2];
+    atomicAdd(u_out + (int64_t)t * 3 + 0, -X0 * vis.div + vis.t2[0] - t3[0]);
+    atomicAdd(u_out + (int64_t)t * 3 + 1, -X1 * vis.div + vis.t2[1] - t3[1]);
+    atomicAdd(u_out + (int64_t)t * 3 + 2, -X2 * vis.div + vis.t2[2] - t3[2]);
   }
 }
 

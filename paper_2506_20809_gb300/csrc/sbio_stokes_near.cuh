@@ -12,8 +12,9 @@
 // sqrt(1-v^2) dP_n/dv = Pbar_n^1 for m = 0.  The velocity is then
 //     u = 1/2 { (F_1, F_2, F_3) + R [ grad F_y - sum_j X_j grad F_j ] }
 // with X the target relative to the source centre (global frame) and the
-// gradients in the source's local frame.  For the target's own particle the
-// same formulas are evaluated at the own surface node (exterior limit).
+// gradients in the source's local frame.  Since X is fixed per pair, the
+// bracket is the gradient of the single expansion F_y - sum_j X_j F_j, whose
+// coefficients are formed term by term (one gradient instead of four).
 #pragma once
 
 #include "sbio_internal.cuh"
@@ -22,19 +23,65 @@
 
 namespace sbio {
 
+// Values of S[f_1..3] and local-frame partial sums of the gradient of the one
+// combined expansion H = S[y . f] - sum_j X_j S[f_j] (X fixed per pair), so
+// that grad S[y . f] - sum_j X_j grad S[f_j] = grad H costs one gradient.
+template <int NC>
+struct StokesNearVisitor {
+  const double* __restrict__ cf;   // 4 x NC: f_1, f_2, f_3, y . f
+  double X0, X1, X2;
+  double cm, sm;
+  double F[3], Hu, Hv, Hp;
+  GradFrame fr;
+
+  __device__ __forceinline__ void begin(const GradFrame& f) {
+    fr = f;
+    F[0] = F[1] = F[2] = Hu = Hv = Hp = 0.0;
+  }
+  __device__ __forceinline__ void order(int, double c, double s) {
+    cm = c;
+    sm = s;
+  }
+  __device__ __forceinline__ double h(int k) const {
+    return fma(-X2, cf[2 * NC + k], fma(-X1, cf[NC + k], fma(-X0, cf[k], cf[3 * NC + k])));
+  }
+  __device__ __forceinline__ void term(int n, int m, double T, double Tu, double Tv, double Tp) {
+    const int kc = n * n + n + m, ks = n * n + n - m;
+    const double hc = h(kc), hs = h(ks);
+    const double a = fma(hc, cm, hs * sm), b = fma(hs, cm, -hc * sm);   // cos / d-phi parts
+    Hu = fma(a, Tu, Hu);
+    Hv = fma(a, Tv, Hv);
+    Hp = fma(b, Tp, Hp);
+#pragma unroll
+    for (int j = 0; j < 3; ++j) F[j] = fma(fma(cf[j * NC + kc], cm, cf[j * NC + ks] * sm), T, F[j]);
+  }
+  __device__ __forceinline__ void term0(int n, double T, double Tu, double Tv) {
+    const int k = n * n + n;
+    const double hk = h(k);
+    Hu = fma(hk, Tu, Hu);
+    Hv = fma(hk, Tv, Hv);
+#pragma unroll
+    for (int j = 0; j < 3; ++j) F[j] = fma(cf[j * NC + k], T, F[j]);
+  }
+};
+
 template <int P1, int KIND>
 __device__ __forceinline__ void stokes_pair(double xl, double yl, double zl, double a, const double* __restrict__ R,
                                             double X0, double X1, double X2, const double* __restrict__ coef,
                                             const double* __restrict__ inv_tab, double out[3]) {
   constexpr int NC = (P1 + 1) * (P1 + 1);
-  const double* c[4] = {coef, coef + NC, coef + 2 * NC, coef + 3 * NC};
-  double F[4], g[4][3];
-  solid_grad<P1, KIND, 4>(xl, yl, zl, a, c, inv_tab, F, g);
-  double w[3];
+  StokesNearVisitor<NC> vis;
+  vis.cf = coef;
+  vis.X0 = X0;
+  vis.X1 = X1;
+  vis.X2 = X2;
+  solid_terms<P1, KIND>(xl, yl, zl, a, inv_tab, vis);
+  const GradFrame& f = vis.fr;
+  const double rho = fma(f.k_ru, vis.Hu, f.k_rv * vis.Hv), ph = f.k_p * vis.Hp;
+  const double w[3] = {f.c1 * rho - f.s1 * ph, f.s1 * rho + f.c1 * ph, fma(f.k_zu, vis.Hu, f.k_zv * vis.Hv)};
 #pragma unroll
-  for (int k = 0; k < 3; ++k) w[k] = g[3][k] - (X0 * g[0][k] + X1 * g[1][k] + X2 * g[2][k]);
-#pragma unroll
-  for (int k = 0; k < 3; ++k) out[k] = 0.5 * (F[k] + R[k * 3 + 0] * w[0] + R[k * 3 + 1] * w[1] + R[k * 3 + 2] * w[2]);
+  for (int k = 0; k < 3; ++k)
+    out[k] = 0.5 * (vis.F[k] + R[k * 3 + 0] * w[0] + R[k * 3 + 1] * w[1] + R[k * 3 + 2] * w[2]);
 }
 
 template <int P1, int KIND>

@@ -15,8 +15,10 @@ namespace sbio {
 
 stokes_near_launcher stokes_near_lookup_a(int p);
 stokes_near_launcher stokes_near_lookup_b(int p);
+stokes_near_launcher stokes_near_lookup_c(int p);
 stokes_point_near_launcher stokes_point_near_lookup_a(int p);
 stokes_point_near_launcher stokes_point_near_lookup_b(int p);
+stokes_point_near_launcher stokes_point_near_lookup_c(int p);
 
 
 namespace {
@@ -247,11 +249,13 @@ int sbio_eval_targets_stokes(sbio_targets* ts, const double* f_tilde, double* u_
     if (p_out) {
       stokes_point_near_launcher nl = stokes_point_near_lookup_a(h.p);
       if (!nl) nl = stokes_point_near_lookup_b(h.p);
+      if (!nl) nl = stokes_point_near_lookup_c(h.p);
       if (!nl) return set_error(SBIO_ENOTSUP, "no Stokes point kernel for p = %d", h.p);
       nl(v, n_pro, n_pairs, u_out, p_out, ns);
     } else {
       stokes_near_launcher nl = stokes_near_lookup_a(h.p);
       if (!nl) nl = stokes_near_lookup_b(h.p);
+      if (!nl) nl = stokes_near_lookup_c(h.p);
       if (!nl) return set_error(SBIO_ENOTSUP, "no Stokes near-field kernel for p = %d", h.p);
       nl(v, n_pro, n_pairs, v.inv, u_out, ns);
     }
