@@ -128,10 +128,12 @@ __global__ void __launch_bounds__(kFarTile) far_deriv_mixed_kernel(const int4* _
                                                                    const int32_t* __restrict__ skip_idx, int64_t N,
                                                                    double* __restrict__ Sp_out,
                                                                    double* __restrict__ Dp_out) {
-  // scalar form: (y - c, -q), (d, 0) per source; packed form (two targets per
-  // f32x2 operation) every value duplicated into a pair: (-y.x, -y.y),
-  // (-y.z, -q), (d.x, d.y), (d.z, -3 d.x), (-3 d.y, -3 d.z)
-  __shared__ float4 sh[(PK ? 5 : 2) * kFarTile];
+  // scalar form: (y - c, -q), (d, 0) per source.  The packed form (two
+  // targets per f32x2 operation) uses the expanded distance
+  // |x - y|^2 = (|x|^2 + |y|^2) - 2 x.y, nu.(x - y) = nu.x + (nu/2).(-2y) and
+  // -3 d.(x - y) = (-3d).x + 3 d.y, d.nu = (2d).(nu/2), with per source, every
+  // value duplicated into a pair: -2y (3), |y|^2, -q, -3d (3), 3 d.y, 2d (3).
+  __shared__ float4 sh[(PK ? 6 : 2) * kFarTile];
   __shared__ float acc[4 * TT * kFarTile];   // per target: S' hi, lo, D' hi, lo
   __shared__ int cursor[2 * TT * kFarTile];  // per target: skip-list position, next skipped particle
   const int tid = threadIdx.x;
@@ -151,7 +153,15 @@ __global__ void __launch_bounds__(kFarTile) far_deriv_mixed_kernel(const int4* _
     NY[q] = (t < N) ? (float)nrm[t * 3 + 1] : 0.f;
     NZ[q] = (t < N) ? (float)nrm[t * 3 + 2] : 0.f;
   }
-  float X[TT], Y[TT], Z[TT];
+  float X[TT], Y[TT], Z[TT], XX[TT], NXX[TT];
+  if (PK) {
+#pragma unroll
+    for (int q = 0; q < TT; ++q) {   // the packed form takes nu / 2
+      NX[q] *= 0.5f;
+      NY[q] *= 0.5f;
+      NZ[q] *= 0.5f;
+    }
+  }
   unsigned skipmask = (1u << TT) - 1u;
   int cur = -1;
   for (int tl = t_lo; tl < t_hi; ++tl) {
@@ -177,6 +187,10 @@ __global__ void __launch_bounds__(kFarTile) far_deriv_mixed_kernel(const int4* _
         X[q] = (hi.x - ch.x) + (lo.x - cl.x);
         Y[q] = (hi.y - ch.y) + (lo.y - cl.y);
         Z[q] = (hi.z - ch.z) + (lo.z - cl.z);
+        if (PK) {
+          XX[q] = fmaf(Z[q], Z[q], fmaf(Y[q], Y[q], X[q] * X[q]));
+          NXX[q] = 2.f * fmaf(NZ[q], Z[q], fmaf(NY[q], Y[q], NX[q] * X[q]));   // nu.x
+        }
       }
     }
     const bool mine = skipmask != (1u << TT) - 1u;
@@ -185,11 +199,14 @@ __global__ void __launch_bounds__(kFarTile) far_deriv_mixed_kernel(const int4* _
       const float4 a = src32[(int64_t)(tile.y + tid) * 2 + 0];
       const float4 b = src32[(int64_t)(tile.y + tid) * 2 + 1];
       if (PK) {
-        sh[tid * 5 + 0] = make_float4(-a.x, -a.x, -a.y, -a.y);
-        sh[tid * 5 + 1] = make_float4(-a.z, -a.z, -a.w, -a.w);
-        sh[tid * 5 + 2] = make_float4(b.x, b.x, b.y, b.y);
-        sh[tid * 5 + 3] = make_float4(b.z, b.z, -3.f * b.x, -3.f * b.x);
-        sh[tid * 5 + 4] = make_float4(-3.f * b.y, -3.f * b.y, -3.f * b.z, -3.f * b.z);
+        const float yy = fmaf(a.z, a.z, fmaf(a.y, a.y, a.x * a.x));
+        const float dy3 = 3.f * fmaf(b.z, a.z, fmaf(b.y, a.y, b.x * a.x));
+        sh[tid * 6 + 0] = make_float4(-2.f * a.x, -2.f * a.x, -2.f * a.y, -2.f * a.y);
+        sh[tid * 6 + 1] = make_float4(-2.f * a.z, -2.f * a.z, yy, yy);
+        sh[tid * 6 + 2] = make_float4(-a.w, -a.w, -3.f * b.x, -3.f * b.x);
+        sh[tid * 6 + 3] = make_float4(-3.f * b.y, -3.f * b.y, -3.f * b.z, -3.f * b.z);
+        sh[tid * 6 + 4] = make_float4(dy3, dy3, 2.f * b.x, 2.f * b.x);
+        sh[tid * 6 + 5] = make_float4(2.f * b.y, 2.f * b.y, 2.f * b.z, 2.f * b.z);
       } else {
         sh[tid * 2 + 0] = make_float4(a.x, a.y, a.z, -a.w);
         sh[tid * 2 + 1] = b;
@@ -202,12 +219,14 @@ __global__ void __launch_bounds__(kFarTile) far_deriv_mixed_kernel(const int4* _
       for (int q = 0; q < TT; ++q) pS[q] = pD[q] = 0.f;
       if constexpr (PK) {
         constexpr int TP = TT / 2 > 0 ? TT / 2 : 1;
-        float2 Xp[TP], Yp[TP], Zp[TP], NXp[TP], NYp[TP], NZp[TP], sS2[TP], sD2[TP];
+        float2 Xp[TP], Yp[TP], Zp[TP], XXp[TP], NXXp[TP], NXp[TP], NYp[TP], NZp[TP], sS2[TP], sD2[TP];
 #pragma unroll
         for (int k = 0; k < TT / 2; ++k) {
           Xp[k] = make_float2(X[2 * k], X[2 * k + 1]);
           Yp[k] = make_float2(Y[2 * k], Y[2 * k + 1]);
           Zp[k] = make_float2(Z[2 * k], Z[2 * k + 1]);
+          XXp[k] = make_float2(XX[2 * k], XX[2 * k + 1]);
+          NXXp[k] = make_float2(NXX[2 * k], NXX[2 * k + 1]);
           NXp[k] = make_float2(NX[2 * k], NX[2 * k + 1]);
           NYp[k] = make_float2(NY[2 * k], NY[2 * k + 1]);
           NZp[k] = make_float2(NZ[2 * k], NZ[2 * k + 1]);
@@ -216,23 +235,24 @@ __global__ void __launch_bounds__(kFarTile) far_deriv_mixed_kernel(const int4* _
         }
 #pragma unroll 2
         for (int j = 0; j < tile.z; ++j) {
-          const float4 A = sh[j * 5 + 0], B = sh[j * 5 + 1], Cc = sh[j * 5 + 2], Dd = sh[j * 5 + 3],
-                       Ee = sh[j * 5 + 4];
-          const float2 my0 = make_float2(A.x, A.y), my1 = make_float2(A.z, A.w), my2 = make_float2(B.x, B.y);
-          const float2 nq = make_float2(B.z, B.w), d0 = make_float2(Cc.x, Cc.y), d1 = make_float2(Cc.z, Cc.w);
-          const float2 d2 = make_float2(Dd.x, Dd.y), e0 = make_float2(Dd.z, Dd.w), e1 = make_float2(Ee.x, Ee.y);
-          const float2 e2 = make_float2(Ee.z, Ee.w);
+          const float4 A = sh[j * 6 + 0], B = sh[j * 6 + 1], Cc = sh[j * 6 + 2], Dd = sh[j * 6 + 3],
+                       Ee = sh[j * 6 + 4], Ff = sh[j * 6 + 5];
+          const float2 m2x = make_float2(A.x, A.y), m2y = make_float2(A.z, A.w), m2z = make_float2(B.x, B.y);
+          const float2 yy = make_float2(B.z, B.w), nq = make_float2(Cc.x, Cc.y), e0 = make_float2(Cc.z, Cc.w);
+          const float2 e1 = make_float2(Dd.x, Dd.y), e2 = make_float2(Dd.z, Dd.w), dy3 = make_float2(Ee.x, Ee.y);
+          const float2 d0 = make_float2(Ee.z, Ee.w), d1 = make_float2(Ff.x, Ff.y), d2 = make_float2(Ff.z, Ff.w);
 #pragma unroll
           for (int k = 0; k < TT / 2; ++k) {
-            const float2 dx = __fadd2_rn(Xp[k], my0), dy = __fadd2_rn(Yp[k], my1), dz = __fadd2_rn(Zp[k], my2);
-            const float2 r2 = __ffma2_rn(dz, dz, __ffma2_rn(dy, dy, __fmul2_rn(dx, dx)));
+            const float2 r2 =
+                __ffma2_rn(Xp[k], m2x, __ffma2_rn(Yp[k], m2y, __ffma2_rn(Zp[k], m2z, __fadd2_rn(XXp[k], yy))));
             const float2 ri = make_float2(rsqrt_apx(r2.x), rsqrt_apx(r2.y));
             const float2 ri2 = __fmul2_rn(ri, ri), ri3 = __fmul2_rn(ri2, ri);
-            const float2 rn = __ffma2_rn(dz, NZp[k], __ffma2_rn(dy, NYp[k], __fmul2_rn(dx, NXp[k])));
+            // nu.(x - y) = nu.x + (nu/2).(-2y)
+            const float2 rn = __ffma2_rn(NZp[k], m2z, __ffma2_rn(NYp[k], m2y, __ffma2_rn(NXp[k], m2x, NXXp[k])));
             if (DO_S) sS2[k] = __ffma2_rn(__fmul2_rn(nq, rn), ri3, sS2[k]);
             if (DO_D) {
-              const float2 dr3 = __ffma2_rn(e2, dz, __ffma2_rn(e1, dy, __fmul2_rn(e0, dx)));   // -3 d.r
-              const float2 dn = __ffma2_rn(d2, NZp[k], __ffma2_rn(d1, NYp[k], __fmul2_rn(d0, NXp[k])));
+              const float2 dr3 = __ffma2_rn(e2, Zp[k], __ffma2_rn(e1, Yp[k], __ffma2_rn(e0, Xp[k], dy3)));   // -3 d.r
+              const float2 dn = __ffma2_rn(d2, NZp[k], __ffma2_rn(d1, NYp[k], __fmul2_rn(d0, NXp[k])));     // d.nu
               sD2[k] = __ffma2_rn(__ffma2_rn(__fmul2_rn(dr3, rn), ri2, dn), ri3, sD2[k]);
             }
           }
