@@ -265,7 +265,9 @@ int sbio_apply_stokes_sl_host(sbio_geom* g, const double* f_tilde_host, double* 
  * (the Stokeslet far kernel carries three accumulators per target and its
  * near field is the larger share of an apply): far_tt and far_splits as in
  * sbio_geom_set_launch_shape, near_ctas_per_sm as in sbio_geom_set_near_cap
- * (default 2, 0, 0).  SBIO_EINVAL on values outside those sets. */
+ * (default 2, 0, 0).  The double layer's stresslet far kernel follows a
+ * packed far_tt (-2, -4, -8, with far_splits) and otherwise runs its scalar
+ * form with 4 targets per thread.  SBIO_EINVAL on values outside those sets. */
 int sbio_geom_set_stokes_tuning(sbio_geom* g, int32_t far_tt, int32_t far_splits, int32_t near_ctas_per_sm);
 int sbio_geom_get_stokes_tuning(const sbio_geom* g, int32_t* far_tt, int32_t* far_splits, int32_t* near_ctas_per_sm);
 

@@ -376,10 +376,11 @@ __global__ void __launch_bounds__(kFarTile) stokes_far_mixed_kernel(const int4* 
             const float2 r2 = __ffma2_rn(dz, dz, __ffma2_rn(dy, dy, __fmul2_rn(dx, dx)));
             const float2 ri = make_float2(rsqrt_approx_f(r2.x), rsqrt_approx_f(r2.y));
             const float2 rf = __ffma2_rn(fz, dz, __ffma2_rn(fy, dy, __fmul2_rn(fx, dx)));
-            const float2 sc = __fmul2_rn(__fmul2_rn(rf, ri), __fmul2_rn(ri, ri));
-            a0[k] = __ffma2_rn(fx, ri, __ffma2_rn(sc, dx, a0[k]));
-            a1[k] = __ffma2_rn(fy, ri, __ffma2_rn(sc, dy, a1[k]));
-            a2[k] = __ffma2_rn(fz, ri, __ffma2_rn(sc, dz, a2[k]));
+            // f / r + (f.r) r / r^3 = (1/r) (f + t r), t = (f.r) / r^2
+            const float2 t = __fmul2_rn(rf, __fmul2_rn(ri, ri));
+            a0[k] = __ffma2_rn(ri, __ffma2_rn(t, dx, fx), a0[k]);
+            a1[k] = __ffma2_rn(ri, __ffma2_rn(t, dy, fy), a1[k]);
+            a2[k] = __ffma2_rn(ri, __ffma2_rn(t, dz, fz), a2[k]);
           }
         }
 #pragma unroll
@@ -399,10 +400,10 @@ __global__ void __launch_bounds__(kFarTile) stokes_far_mixed_kernel(const int4* 
             const float dx = X[q] - A.x, dy = Y[q] - A.y, dz = Z[q] - A.z;
             const float ri = rsqrt_approx_f(fmaf(dz, dz, fmaf(dy, dy, dx * dx)));
             const float rf = fmaf(dz, B.y, fmaf(dy, B.x, dx * A.w));
-            const float sc = (rf * ri) * (ri * ri);
-            p0[q] = fmaf(A.w, ri, fmaf(sc, dx, p0[q]));
-            p1[q] = fmaf(B.x, ri, fmaf(sc, dy, p1[q]));
-            p2[q] = fmaf(B.y, ri, fmaf(sc, dz, p2[q]));
+            const float t = rf * (ri * ri);
+            p0[q] = fmaf(ri, fmaf(t, dx, A.w), p0[q]);
+            p1[q] = fmaf(ri, fmaf(t, dy, B.x), p1[q]);
+            p2[q] = fmaf(ri, fmaf(t, dz, B.y), p2[q]);
           }
         }
       }

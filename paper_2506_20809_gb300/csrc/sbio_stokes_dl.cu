@@ -251,8 +251,10 @@ __global__ void __launch_bounds__(kFarTile) stresslet_far_fp64_kernel(const int4
 }
 
 // Mixed stresslet quadrature: FP32 pair sums, TT targets per thread, hi/lo
-// target offsets per source particle, per-tile TwoSum folding.
-template <int TT>
+// target offsets per source particle, per-tile TwoSum folding.  PK computes
+// two targets per f32x2 instruction, with every source value duplicated into
+// a pair in shared memory: -y (3), q (3), nu (3).
+template <int TT, bool PK>
 __global__ void __launch_bounds__(kFarTile) stresslet_far_mixed_kernel(const int4* __restrict__ tiles, int n_tiles,
                                                                        const float4* __restrict__ src32,
                                                                        const float4* __restrict__ nrm32,
@@ -261,7 +263,7 @@ __global__ void __launch_bounds__(kFarTile) stresslet_far_mixed_kernel(const int
                                                                        const int32_t* __restrict__ skip_ptr,
                                                                        const int32_t* __restrict__ skip_idx,
                                                                        int64_t N, double* __restrict__ u_out) {
-  __shared__ float4 sh[3 * kFarTile];
+  __shared__ float4 sh[(PK ? 5 : 3) * kFarTile];
   __shared__ float acc[6 * TT * kFarTile];   // per target and component: hi, lo
   __shared__ int cursor[2 * TT * kFarTile];
   const int tid = threadIdx.x;
@@ -309,15 +311,62 @@ __global__ void __launch_bounds__(kFarTile) stresslet_far_mixed_kernel(const int
     if (!__syncthreads_or(mine)) continue;
     if (tid < tile.z) {
       const int64_t j = tile.y + tid;
-      sh[tid * 3 + 0] = src32[j * 2 + 0];
-      sh[tid * 3 + 1] = src32[j * 2 + 1];
-      sh[tid * 3 + 2] = nrm32[j];
+      const float4 a = src32[j * 2 + 0], b = src32[j * 2 + 1], c = nrm32[j];
+      if (PK) {
+        sh[tid * 5 + 0] = make_float4(-a.x, -a.x, -a.y, -a.y);
+        sh[tid * 5 + 1] = make_float4(-a.z, -a.z, a.w, a.w);
+        sh[tid * 5 + 2] = make_float4(b.x, b.x, b.y, b.y);
+        sh[tid * 5 + 3] = make_float4(c.x, c.x, c.y, c.y);
+        sh[tid * 5 + 4] = make_float4(c.z, c.z, 0.f, 0.f);
+      } else {
+        sh[tid * 3 + 0] = a;
+        sh[tid * 3 + 1] = b;
+        sh[tid * 3 + 2] = c;
+      }
     }
     __syncthreads();
     if (mine) {
       float p0[TT], p1[TT], p2[TT];
 #pragma unroll
       for (int q = 0; q < TT; ++q) p0[q] = p1[q] = p2[q] = 0.f;
+      if constexpr (PK) {
+        constexpr int TP = TT / 2 > 0 ? TT / 2 : 1;
+        float2 Xp[TP], Yp[TP], Zp[TP], a0[TP], a1[TP], a2[TP];
+#pragma unroll
+        for (int k = 0; k < TP; ++k) {
+          Xp[k] = make_float2(X[2 * k], X[2 * k + 1]);
+          Yp[k] = make_float2(Y[2 * k], Y[2 * k + 1]);
+          Zp[k] = make_float2(Z[2 * k], Z[2 * k + 1]);
+          a0[k] = a1[k] = a2[k] = make_float2(0.f, 0.f);
+        }
+#pragma unroll 2
+        for (int jj = 0; jj < tile.z; ++jj) {
+          const float4 A = sh[jj * 5 + 0], B = sh[jj * 5 + 1], C = sh[jj * 5 + 2], D = sh[jj * 5 + 3],
+                       E = sh[jj * 5 + 4];
+          const float2 myx = make_float2(A.x, A.y), myy = make_float2(A.z, A.w), myz = make_float2(B.x, B.y);
+          const float2 qx = make_float2(B.z, B.w), qy = make_float2(C.x, C.y), qz = make_float2(C.z, C.w);
+          const float2 nx = make_float2(D.x, D.y), ny = make_float2(D.z, D.w), nz = make_float2(E.x, E.y);
+#pragma unroll
+          for (int k = 0; k < TP; ++k) {
+            const float2 dx = __fadd2_rn(Xp[k], myx), dy = __fadd2_rn(Yp[k], myy), dz = __fadd2_rn(Zp[k], myz);
+            const float2 r2 = __ffma2_rn(dz, dz, __ffma2_rn(dy, dy, __fmul2_rn(dx, dx)));
+            const float2 ri = make_float2(rsqrt_apx_s(r2.x), rsqrt_apx_s(r2.y));
+            const float2 ri2 = __fmul2_rn(ri, ri);
+            const float2 rq = __ffma2_rn(dz, qz, __ffma2_rn(dy, qy, __fmul2_rn(dx, qx)));
+            const float2 rn = __ffma2_rn(dz, nz, __ffma2_rn(dy, ny, __fmul2_rn(dx, nx)));
+            const float2 sc = __fmul2_rn(__fmul2_rn(rq, rn), __fmul2_rn(__fmul2_rn(ri2, ri2), ri));
+            a0[k] = __ffma2_rn(sc, dx, a0[k]);
+            a1[k] = __ffma2_rn(sc, dy, a1[k]);
+            a2[k] = __ffma2_rn(sc, dz, a2[k]);
+          }
+        }
+#pragma unroll
+        for (int k = 0; k < TP; ++k) {
+          p0[2 * k] = a0[k].x; p0[2 * k + 1] = a0[k].y;
+          p1[2 * k] = a1[k].x; p1[2 * k + 1] = a1[k].y;
+          p2[2 * k] = a2[k].x; p2[2 * k + 1] = a2[k].y;
+        }
+      } else {
 #pragma unroll 2
       for (int jj = 0; jj < tile.z; ++jj) {
         const float4 a = sh[jj * 3], b = sh[jj * 3 + 1], c = sh[jj * 3 + 2];
@@ -333,6 +382,7 @@ __global__ void __launch_bounds__(kFarTile) stresslet_far_mixed_kernel(const int
           p1[q] = fmaf(s, dy, p1[q]);
           p2[q] = fmaf(s, dz, p2[q]);
         }
+      }
       }
 #pragma unroll
       for (int q = 0; q < TT; ++q) {
@@ -361,6 +411,16 @@ __global__ void __launch_bounds__(kFarTile) stresslet_far_mixed_kernel(const int
   }
 }
 
+template <int TT, bool PK>
+void launch_stresslet_far_tt(const DevGeom& tg, const DevGeom& src, const GeomHost& h, int64_t NT, double* u,
+                             cudaStream_t st) {
+  const int nt = (int)h.tiles.size();
+  const int64_t tb = (NT + (int64_t)kFarTile * TT - 1) / ((int64_t)kFarTile * TT);
+  const dim3 grid((unsigned)tb, (unsigned)far_split_count(tb, nt, PK ? h.st_far_splits : 0));
+  stresslet_far_mixed_kernel<TT, PK><<<grid, kFarTile, 0, st>>>(src.tiles, nt, src.st_src32, src.nrm32, tg.tgt32,
+                                                                src.cen32, tg.skip_ptr, tg.skip_idx, NT, u);
+}
+
 // tg: the targets (positions, hi/lo parts, skip lists; a point set's view or
 // the geometry itself); src: the geometry, whose source-side arrays (tiles,
 // sources, source normals, centres) are always taken from it.
@@ -373,12 +433,16 @@ void launch_stresslet_far(const DevGeom& tg, const DevGeom& src, const GeomHost&
     const dim3 grid((unsigned)tb, (unsigned)far_split_count(tb, nt, 0));
     stresslet_far_fp64_kernel<<<grid, kFarTile, 0, st>>>(src.tiles, nt, src.st_src64, src.nrm, tg.xyz, src.parts,
                                                          tg.skip_ptr, tg.skip_idx, NT, u);
+  } else if (h.st_far_tt < 0) {
+    // the geometry's tuned Stokes far shape, when packed (the Stokeslet and
+    // stresslet pair costs are alike): |tt| targets per thread, tuned splits
+    switch (h.st_far_tt) {
+      case -2: launch_stresslet_far_tt<2, true>(tg, src, h, NT, u, st); break;
+      case -4: launch_stresslet_far_tt<4, true>(tg, src, h, NT, u, st); break;
+      default: launch_stresslet_far_tt<8, true>(tg, src, h, NT, u, st); break;
+    }
   } else {
-    constexpr int TT = 4;
-    const int64_t tb = (NT + (int64_t)kFarTile * TT - 1) / ((int64_t)kFarTile * TT);
-    const dim3 grid((unsigned)tb, (unsigned)far_split_count(tb, nt, 0));
-    stresslet_far_mixed_kernel<TT><<<grid, kFarTile, 0, st>>>(src.tiles, nt, src.st_src32, src.nrm32, tg.tgt32,
-                                                              src.cen32, tg.skip_ptr, tg.skip_idx, NT, u);
+    launch_stresslet_far_tt<4, false>(tg, src, h, NT, u, st);
   }
   count_launch();
 }

@@ -96,3 +96,33 @@ def test_mixed_vs_fp64(S, ctx):
     print(f"stokes dl mixed vs fp64: {rel(Um, U64):.3e}")
     assert rel(Um, U64) < TOLMIX
     g.close()
+
+
+@pytest.mark.parametrize("tt", [4, -2, -4, -8])
+def test_mixed_far_forms(S, ctx, tt):
+    """Scalar (4 targets per thread) and packed (2, 4, 8) stresslet far forms,
+    with 0 (default) and 64 source splits, stay within the mixed bound of the
+    FP64 path, at nodes and at points."""
+    s = I.config_suspension(3)
+    p = s.p
+    q = np.random.default_rng(5).standard_normal((s.M, 3, (p + 1) ** 2)) / (1 + np.arange((p + 1) ** 2))
+    g = S.Geometry(ctx, s)
+    X = I.shell_points(s, per_particle=1, seed=3, far_points=2000)
+    ts = S.TargetSet(g, X)
+    qd = torch.from_numpy(q).cuda()
+    U64 = gpu_dl(S, g, q, S.SBIO_FP64)
+    P64 = torch.empty((ts.T, 3), dtype=torch.float64, device="cuda")
+    S.sbio_eval_targets_stokes_dl(ts.h, qd, P64)
+    torch.cuda.synchronize()
+    P64 = P64.cpu().numpy()
+    for splits in (0, 64):
+        S.sbio_geom_set_stokes_tuning(g.h, tt, splits, 0)
+        Um = gpu_dl(S, g, q, S.SBIO_MIXED)
+        Pm = torch.full((ts.T, 3), float("nan"), dtype=torch.float64, device="cuda")
+        S.sbio_eval_targets_stokes_dl(ts.h, qd, Pm)
+        torch.cuda.synchronize()
+        S.sbio_geom_set_precision(g.h, S.SBIO_FP64)
+        assert rel(Um, U64) < TOLMIX, (tt, splits)
+        assert rel(Pm.cpu().numpy(), P64) < TOLMIX, (tt, splits)
+    ts.close()
+    g.close()
