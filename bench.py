@@ -33,6 +33,11 @@ sys.path.insert(0, ROOT)
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12     # SMs x FP32 lanes x FMA x max SM clock
 FP64_PEAK_TFLOPS = 1.25                               # nominal GB300 FP64 rate
 FAR_FLOP_PER_PAIR = {"SD": 19, "S": 10, "D": 14}
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one launch of
+# the mixed S+D far kernel on the 200-spheroid p = 16 suspension, from one ncu
+# capture per launch shape (targets per thread, source splits) of the current
+# kernel code; other shapes report null
+FAR_DRAM_BYTES_POLY200 = {(-8, 44): 11.57e6}
 
 
 def near_flop_per_pair(p: int) -> int:
@@ -384,7 +389,10 @@ def run_ours(args, ws, rank, lrank):
                      "bound": "alu", "achieved": achieved,
                      "peak": FP32_PEAK_TFLOPS if prec == S.SBIO_MIXED else FP64_PEAK_TFLOPS,
                      "unit": "TFLOP/s", "frac": achieved / (FP32_PEAK_TFLOPS if prec == S.SBIO_MIXED else FP64_PEAK_TFLOPS),
-                     "traffic": None,
+                     "traffic": (FAR_DRAM_BYTES_POLY200.get((tune[0], tune[1]))
+                                 if prec == S.SBIO_MIXED and args.workload == "poly200" else None),
+                     "traffic_unit": "bytes per launch (ncu dram read + write, one capture at this launch shape)",
+                     "algorithmic_bytes": None,
                      "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz" if prec == S.SBIO_MIXED
                      else "nominal FP64 1.25 TFLOP/s"},
         "roofline_near": {"kernel": "near_kernel", "bound": "alu", "unit": "TFLOP/s",
