@@ -157,7 +157,9 @@ int sbio_geom_near_pairs(const sbio_geom* g, int32_t* target, int32_t* source);
 
 /* Phase timing (measurement aid).  When enabled, every Laplace apply records
  * CUDA events on its stream before the synthesis kernel, before the near-field
- * kernels, before the far-field kernel and after it.  sbio_geom_phase_times()
+ * kernels, before the far-field kernel and after it (the Stokes applies and
+ * S' / D' likewise, their prep and self kernels counting as the first phase),
+ * with the phases run in order.  sbio_geom_phase_times()
  * synchronises on those events and returns the three durations of the last
  * apply in milliseconds (SBIO_EINVAL if timing is off). */
 int sbio_geom_enable_timing(sbio_geom* g, int32_t on);

@@ -206,7 +206,7 @@ void split_f32(double v, float& hi, float& lo);
 // *inside set when the level set (rho/A)^2 + (z/C)^2 is below 1 - tol
 double spheroid_distance_local(const PartGeom& P, double x, double y, double z, double tol, bool* inside);
 int launch_stokes_far(sbio_geom* g, double* u, cudaStream_t st);
-int launch_stokes_far_on(const DevGeom& d, const GeomHost& h, int64_t NT, double* u, cudaStream_t st);
+int launch_stokes_far_on(const DevGeom& d, const GeomHost& h, int64_t NT, double* u, double* pr, cudaStream_t st);
 int launch_stokes_prep(sbio_geom* g, const double* f, cudaStream_t st);
 int launch_laplace_deriv(sbio_geom* g, const double* sigma, const double* mu, double* Sp, double* Dp,
                          cudaStream_t st);

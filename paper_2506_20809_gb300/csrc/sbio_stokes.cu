@@ -286,16 +286,20 @@ __global__ void __launch_bounds__(kFarTile) stokes_far_fp64_kernel(const int4* _
 // Stokeslet far field for one CTA: TT targets per thread against source tiles
 // [t_lo, t_hi); two-sum accumulators and skip cursors in shared memory (as in
 // the Laplace far kernel); PK computes two targets per f32x2 instruction.
-template <int TT, bool PK>
+// PR also sums the pressure quadrature with the printed kernel
+// P = r / (4 pi |r|^3), which reuses the pair's f.r and 1/|r|: one more FMA.
+template <int TT, bool PK, bool PR>
 __global__ void __launch_bounds__(kFarTile) stokes_far_mixed_kernel(const int4* __restrict__ tiles, int n_tiles,
                                                                     const float4* __restrict__ src32,
                                                                     const float4* __restrict__ tgt32,
                                                                     const float4* __restrict__ cen32,
                                                                     const int32_t* __restrict__ skip_ptr,
                                                                     const int32_t* __restrict__ skip_idx, int64_t N,
-                                                                    double* __restrict__ u_out) {
+                                                                    double* __restrict__ u_out,
+                                                                    double* __restrict__ p_out) {
+  constexpr int NA = PR ? 4 : 3;               // accumulated quantities per target
   __shared__ float4 sh[(PK ? 3 : 2) * kFarTile];
-  __shared__ float acc[6 * TT * kFarTile];     // per target: (hi, lo) of u_x, u_y, u_z
+  __shared__ float acc[2 * NA * TT * kFarTile];   // per target: (hi, lo) of u_x, u_y, u_z (and p)
   __shared__ int cursor[2 * TT * kFarTile];
   const int tid = threadIdx.x;
   const int per = (n_tiles + gridDim.y - 1) / gridDim.y;
@@ -305,7 +309,7 @@ __global__ void __launch_bounds__(kFarTile) stokes_far_mixed_kernel(const int4* 
   for (int q = 0; q < TT; ++q) {
     const int64_t t = t0 + (int64_t)q * kFarTile;
 #pragma unroll
-    for (int c = 0; c < 6; ++c) acc[(6 * q + c) * kFarTile + tid] = 0.f;
+    for (int c = 0; c < 2 * NA; ++c) acc[(2 * NA * q + c) * kFarTile + tid] = 0.f;
     const int sp = (t < N) ? skip_ptr[t] : 0;
     cursor[(2 * q + 0) * kFarTile + tid] = sp;
     cursor[(2 * q + 1) * kFarTile + tid] = (t < N) ? skip_idx[sp] : INT32_MAX;
@@ -354,16 +358,16 @@ __global__ void __launch_bounds__(kFarTile) stokes_far_mixed_kernel(const int4* 
     }
     __syncthreads();
     if (mine) {
-      float p0[TT], p1[TT], p2[TT];
+      float p0[TT], p1[TT], p2[TT], p3[TT];
       if constexpr (PK) {
         constexpr int TP = TT / 2 > 0 ? TT / 2 : 1;
-        float2 Xp[TP], Yp[TP], Zp[TP], a0[TP], a1[TP], a2[TP];
+        float2 Xp[TP], Yp[TP], Zp[TP], a0[TP], a1[TP], a2[TP], a3[TP];
 #pragma unroll
         for (int k = 0; k < TP; ++k) {
           Xp[k] = make_float2(X[2 * k], X[2 * k + 1]);
           Yp[k] = make_float2(Y[2 * k], Y[2 * k + 1]);
           Zp[k] = make_float2(Z[2 * k], Z[2 * k + 1]);
-          a0[k] = a1[k] = a2[k] = make_float2(0.f, 0.f);
+          a0[k] = a1[k] = a2[k] = a3[k] = make_float2(0.f, 0.f);
         }
 #pragma unroll 2
         for (int j = 0; j < tile.z; ++j) {
@@ -381,6 +385,7 @@ __global__ void __launch_bounds__(kFarTile) stokes_far_mixed_kernel(const int4* 
             a0[k] = __ffma2_rn(ri, __ffma2_rn(t, dx, fx), a0[k]);
             a1[k] = __ffma2_rn(ri, __ffma2_rn(t, dy, fy), a1[k]);
             a2[k] = __ffma2_rn(ri, __ffma2_rn(t, dz, fz), a2[k]);
+            if (PR) a3[k] = __ffma2_rn(t, ri, a3[k]);   // (f.r) / r^3
           }
         }
 #pragma unroll
@@ -388,10 +393,11 @@ __global__ void __launch_bounds__(kFarTile) stokes_far_mixed_kernel(const int4* 
           p0[2 * k] = a0[k].x; p0[2 * k + 1] = a0[k].y;
           p1[2 * k] = a1[k].x; p1[2 * k + 1] = a1[k].y;
           p2[2 * k] = a2[k].x; p2[2 * k + 1] = a2[k].y;
+          p3[2 * k] = a3[k].x; p3[2 * k + 1] = a3[k].y;
         }
       } else {
 #pragma unroll
-        for (int q = 0; q < TT; ++q) p0[q] = p1[q] = p2[q] = 0.f;
+        for (int q = 0; q < TT; ++q) p0[q] = p1[q] = p2[q] = p3[q] = 0.f;
 #pragma unroll 2
         for (int j = 0; j < tile.z; ++j) {
           const float4 A = sh[j * 2], B = sh[j * 2 + 1];
@@ -404,19 +410,20 @@ __global__ void __launch_bounds__(kFarTile) stokes_far_mixed_kernel(const int4* 
             p0[q] = fmaf(ri, fmaf(t, dx, A.w), p0[q]);
             p1[q] = fmaf(ri, fmaf(t, dy, B.x), p1[q]);
             p2[q] = fmaf(ri, fmaf(t, dz, B.y), p2[q]);
+            if (PR) p3[q] = fmaf(t, ri, p3[q]);
           }
         }
       }
 #pragma unroll
       for (int q = 0; q < TT; ++q) {
         if (!((skipmask >> q) & 1u)) {
-          const float pv[3] = {p0[q], p1[q], p2[q]};
+          const float pv[4] = {p0[q], p1[q], p2[q], p3[q]};
 #pragma unroll
-          for (int c = 0; c < 3; ++c) {
+          for (int c = 0; c < NA; ++c) {
             float sum, err;
-            two_sum_f(acc[(6 * q + 2 * c) * kFarTile + tid], pv[c], sum, err);
-            acc[(6 * q + 2 * c) * kFarTile + tid] = sum;
-            acc[(6 * q + 2 * c + 1) * kFarTile + tid] += err;
+            two_sum_f(acc[(2 * NA * q + 2 * c) * kFarTile + tid], pv[c], sum, err);
+            acc[(2 * NA * q + 2 * c) * kFarTile + tid] = sum;
+            acc[(2 * NA * q + 2 * c + 1) * kFarTile + tid] += err;
           }
         }
       }
@@ -426,30 +433,42 @@ __global__ void __launch_bounds__(kFarTile) stokes_far_mixed_kernel(const int4* 
 #pragma unroll
   for (int q = 0; q < TT; ++q) {
     const int64_t t = t0 + (int64_t)q * kFarTile;
-    if (t < N)
+    if (t < N) {
       for (int c = 0; c < 3; ++c)
         atomicAdd(u_out + t * 3 + c,
-                  ((double)acc[(6 * q + 2 * c) * kFarTile + tid] + (double)acc[(6 * q + 2 * c + 1) * kFarTile + tid]) *
-                      kInv8Pi);
+                  ((double)acc[(2 * NA * q + 2 * c) * kFarTile + tid] +
+                   (double)acc[(2 * NA * q + 2 * c + 1) * kFarTile + tid]) * kInv8Pi);
+      if (PR)
+        atomicAdd(p_out + t, ((double)acc[(2 * NA * q + 6) * kFarTile + tid] +
+                              (double)acc[(2 * NA * q + 7) * kFarTile + tid]) * (2.0 * kInv8Pi));
+    }
   }
 }
 
 template <int TT, bool PK>
-static void launch_stokes_far_tt(const DevGeom& d, const GeomHost& h, int64_t NT, double* u, cudaStream_t st) {
+static void launch_stokes_far_tt(const DevGeom& d, const GeomHost& h, int64_t NT, double* u, double* pr,
+                                 cudaStream_t st) {
   const int nt = (int)h.tiles.size();
   const int64_t tb = (NT + (int64_t)kFarTile * TT - 1) / ((int64_t)kFarTile * TT);
   const dim3 grid((unsigned)tb, (unsigned)far_split_count(tb, nt, h.st_far_splits));
-  stokes_far_mixed_kernel<TT, PK><<<grid, kFarTile, 0, st>>>(d.tiles, nt, d.st_src32, d.tgt32, d.cen32, d.skip_ptr,
-                                                             d.skip_idx, NT, u);
+  if (pr)
+    stokes_far_mixed_kernel<TT, PK, true><<<grid, kFarTile, 0, st>>>(d.tiles, nt, d.st_src32, d.tgt32, d.cen32,
+                                                                     d.skip_ptr, d.skip_idx, NT, u, pr);
+  else
+    stokes_far_mixed_kernel<TT, PK, false><<<grid, kFarTile, 0, st>>>(d.tiles, nt, d.st_src32, d.tgt32, d.cen32,
+                                                                      d.skip_ptr, d.skip_idx, NT, u, nullptr);
 }
 
 // The Stokeslet far field alone (sources written by the prep kernel of the
 // same or an earlier apply) at the NT targets of `d`, in the geometry's
-// precision and Stokes launch shape.
-int launch_stokes_far_on(const DevGeom& d, const GeomHost& h, int64_t NT, double* u, cudaStream_t st) {
+// precision and Stokes launch shape.  pr (may be null): the pressure
+// quadrature is summed into it in the same pass (mixed precision only; the
+// FP64 form leaves it to a kernel of its own).
+int launch_stokes_far_on(const DevGeom& d, const GeomHost& h, int64_t NT, double* u, double* pr, cudaStream_t st) {
   if (NT <= 0) return SBIO_OK;
   const int nt = (int)h.tiles.size();
   if (h.precision == SBIO_FP64) {
+    if (pr) return set_error(SBIO_EINVAL, "the FP64 Stokeslet far kernel does not sum the pressure");
     const int64_t tb = (NT + kFarTile - 1) / kFarTile;
     const dim3 grid((unsigned)tb, (unsigned)far_split_count(tb, nt, h.st_far_splits));
     stokes_far_fp64_kernel<<<grid, kFarTile, 0, st>>>(d.tiles, nt, d.st_src64, d.xyz, d.parts, d.skip_ptr,
@@ -457,13 +476,13 @@ int launch_stokes_far_on(const DevGeom& d, const GeomHost& h, int64_t NT, double
   } else {
     // targets per thread, packed f32x2 form if negative
     switch (h.st_far_tt) {
-      case 1: launch_stokes_far_tt<1, false>(d, h, NT, u, st); break;
-      case 4: launch_stokes_far_tt<4, false>(d, h, NT, u, st); break;
-      case 8: launch_stokes_far_tt<8, false>(d, h, NT, u, st); break;
-      case -2: launch_stokes_far_tt<2, true>(d, h, NT, u, st); break;
-      case -4: launch_stokes_far_tt<4, true>(d, h, NT, u, st); break;
-      case -8: launch_stokes_far_tt<8, true>(d, h, NT, u, st); break;
-      default: launch_stokes_far_tt<2, false>(d, h, NT, u, st); break;
+      case 1: launch_stokes_far_tt<1, false>(d, h, NT, u, pr, st); break;
+      case 4: launch_stokes_far_tt<4, false>(d, h, NT, u, pr, st); break;
+      case 8: launch_stokes_far_tt<8, false>(d, h, NT, u, pr, st); break;
+      case -2: launch_stokes_far_tt<2, true>(d, h, NT, u, pr, st); break;
+      case -4: launch_stokes_far_tt<4, true>(d, h, NT, u, pr, st); break;
+      case -8: launch_stokes_far_tt<8, true>(d, h, NT, u, pr, st); break;
+      default: launch_stokes_far_tt<2, false>(d, h, NT, u, pr, st); break;
     }
   }
   count_launch();
@@ -471,7 +490,9 @@ int launch_stokes_far_on(const DevGeom& d, const GeomHost& h, int64_t NT, double
   return SBIO_OK;
 }
 
-int launch_stokes_far(sbio_geom* g, double* u, cudaStream_t st) { return launch_stokes_far_on(g->d, g->h, g->h.N, u, st); }
+int launch_stokes_far(sbio_geom* g, double* u, cudaStream_t st) {
+  return launch_stokes_far_on(g->d, g->h, g->h.N, u, nullptr, st);
+}
 
 // Per-apply Stokes sources: the y.f coefficients at order p+1 and the folded
 // near coefficients (st_coef), and the Stokeslet far sources (st_src64/32).

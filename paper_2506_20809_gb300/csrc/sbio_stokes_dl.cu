@@ -602,26 +602,35 @@ int sbio_apply_stokes_dl(sbio_geom* g, const double* q_hat, double* u_out, void*
   if (!nl) return set_error(SBIO_ENOTSUP, "no Stokes double-layer kernel for p = %d", h.p);
   SBIO_CUDA_TRY(cudaSetDevice(g->ctx->device));
   cudaStream_t st = (cudaStream_t)stream;
+  phase_mark(g, 0, st);
   int rc = sdl_prep(g, q_hat, u_out, st);   // writes -q/2 at every node
   if (rc) return rc;
   const DevGeom& d = g->d;
-  const bool fork = g->overlap && !g->timing && g->near_stream;
-  cudaStream_t ns = fork ? g->near_stream : st;
-  DevGeom v = d;
+  const bool has_pairs = !h.pair_t.empty();
+  const bool fork = g->overlap && !g->timing && g->near_stream && has_pairs;
   if (fork) {
-    SBIO_CUDA_TRY(cudaEventRecord(g->ev_fork, st));
-    SBIO_CUDA_TRY(cudaStreamWaitEvent(ns, g->ev_fork, 0));
+    // near pairs on the forked high-priority stream, beside the own nodes
+    // (exterior limit at u = u0, separable self kernel) and the far field
+    DevGeom v = d;
     v.near_grid_cap = h.st_near_ctas_per_sm > 0 ? h.st_near_ctas_per_sm * sm_count() : 0;
+    SBIO_CUDA_TRY(cudaEventRecord(g->ev_fork, st));
+    SBIO_CUDA_TRY(cudaStreamWaitEvent(g->near_stream, g->ev_fork, 0));
+    nl(v, d.pair_t, d.pair_s, h.n_pairs_prolate, (int64_t)h.pair_t.size(), u_out, g->near_stream);
+    SBIO_CUDA_TRY(cudaGetLastError());
+    SBIO_CUDA_TRY(cudaEventRecord(g->ev_join, g->near_stream));
   }
-  // near pairs on the (forked) near stream; the own nodes (exterior limit at
-  // u = u0) by the separable self kernel and the far field on the caller's
-  if (!h.pair_t.empty()) nl(v, d.pair_t, d.pair_s, h.n_pairs_prolate, (int64_t)h.pair_t.size(), u_out, ns);
-  SBIO_CUDA_TRY(cudaGetLastError());
-  if (fork) SBIO_CUDA_TRY(cudaEventRecord(g->ev_join, ns));
   if ((rc = sdl_self(g, u_out, st))) return rc;
+  // in order (no overlap, or phase timing): prep + self, near pairs, far field
+  phase_mark(g, 1, st);
+  if (!fork && has_pairs) {
+    nl(d, d.pair_t, d.pair_s, h.n_pairs_prolate, (int64_t)h.pair_t.size(), u_out, st);
+    SBIO_CUDA_TRY(cudaGetLastError());
+  }
+  phase_mark(g, 2, st);
   launch_stresslet_far(d, d, h, h.N, u_out, st);
   SBIO_CUDA_TRY(cudaGetLastError());
   if (fork) SBIO_CUDA_TRY(cudaStreamWaitEvent(st, g->ev_join, 0));
+  phase_mark(g, 3, st);
   return SBIO_OK;
 }
 

@@ -4,7 +4,9 @@
 // apply, through a view of the geometry's tables whose targets are the
 // points), and the pressure p = int P(x, y) . f dS with the printed kernel
 // P = r / (4 pi |r|^3): the divergence of the Laplace expansions for near
-// pairs (sbio_stokes_points.cuh), the smooth quadrature for far pairs here.
+// pairs (sbio_stokes_points.cuh), the smooth quadrature for far pairs (in
+// mixed precision summed by the Stokeslet far kernel in the same pass, in
+// FP64 by the kernel here).
 #include "sbio_internal.cuh"
 #include "sbio_stokes_near.cuh"
 #include "sbio_stokes_points.cuh"
@@ -28,18 +30,6 @@ constexpr double kInv4PiP = 0.07957747154594767;   // 1/(4 pi)
 struct alignas(32) pd4 {
   double x, y, z, w;
 };
-
-__device__ __forceinline__ float rsqrt_apx_p(float x) {
-  float r;
-  asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
-  return r;
-}
-
-__device__ __forceinline__ void two_sum_p(float a, float b, float& s, float& e) {
-  s = a + b;
-  const float bb = s - a;
-  e = (a - (s - bb)) + (b - bb);
-}
 
 // FP64: one target per thread; sources (y - c, w f_1), (w f_2, w f_3, 0, 0).
 __global__ void __launch_bounds__(kFarTile) pressure_far_fp64_kernel(const int4* __restrict__ tiles, int n_tiles,
@@ -99,118 +89,15 @@ __global__ void __launch_bounds__(kFarTile) pressure_far_fp64_kernel(const int4*
   if (valid) atomicAdd(p_out + t, acc * kInv4PiP);
 }
 
-// Mixed: FP32 pair sums, TT targets per thread, hi/lo target offsets per
-// source particle, per-tile partials folded by TwoSum (the far-field scheme
-// of the velocity kernels).
-template <int TT>
-__global__ void __launch_bounds__(kFarTile) pressure_far_mixed_kernel(const int4* __restrict__ tiles, int n_tiles,
-                                                                      const float4* __restrict__ src32,
-                                                                      const float4* __restrict__ tgt32,
-                                                                      const float4* __restrict__ cen32,
-                                                                      const int32_t* __restrict__ skip_ptr,
-                                                                      const int32_t* __restrict__ skip_idx,
-                                                                      int64_t N, double* __restrict__ p_out) {
-  __shared__ float4 sh[2 * kFarTile];
-  __shared__ float acc[2 * TT * kFarTile];
-  __shared__ int cursor[2 * TT * kFarTile];
-  const int tid = threadIdx.x;
-  const int per = (n_tiles + gridDim.y - 1) / gridDim.y;
-  const int t_lo = blockIdx.y * per, t_hi = min(n_tiles, t_lo + per);
-  const int64_t t0 = (int64_t)blockIdx.x * TT * kFarTile + tid;
-#pragma unroll
-  for (int q = 0; q < TT; ++q) {
-    const int64_t t = t0 + (int64_t)q * kFarTile;
-    acc[(2 * q + 0) * kFarTile + tid] = 0.f;
-    acc[(2 * q + 1) * kFarTile + tid] = 0.f;
-    const int sp = (t < N) ? skip_ptr[t] : 0;
-    cursor[(2 * q + 0) * kFarTile + tid] = sp;
-    cursor[(2 * q + 1) * kFarTile + tid] = (t < N) ? skip_idx[sp] : INT32_MAX;
-  }
-  float X[TT], Y[TT], Z[TT];
-  unsigned skipmask = (1u << TT) - 1u;
-  int cur = -1;
-  for (int tl = t_lo; tl < t_hi; ++tl) {
-    const int4 tile = tiles[tl];
-    if (tile.x != cur) {
-      cur = tile.x;
-      const float4 ch = cen32[cur * 2], cl = cen32[cur * 2 + 1];
-      skipmask = 0u;
-#pragma unroll
-      for (int q = 0; q < TT; ++q) {
-        const int64_t t = t0 + (int64_t)q * kFarTile;
-        int sp = cursor[(2 * q + 0) * kFarTile + tid];
-        int nxt = cursor[(2 * q + 1) * kFarTile + tid];
-        while (nxt < cur) nxt = skip_idx[++sp];
-        cursor[(2 * q + 0) * kFarTile + tid] = sp;
-        cursor[(2 * q + 1) * kFarTile + tid] = nxt;
-        if (t >= N || nxt == cur) skipmask |= 1u << q;
-        float4 hi = make_float4(0.f, 0.f, 0.f, 0.f), lo = hi;
-        if (t < N) {
-          hi = tgt32[t * 2];
-          lo = tgt32[t * 2 + 1];
-        }
-        X[q] = (hi.x - ch.x) + (lo.x - cl.x);
-        Y[q] = (hi.y - ch.y) + (lo.y - cl.y);
-        Z[q] = (hi.z - ch.z) + (lo.z - cl.z);
-      }
-    }
-    const bool mine = skipmask != (1u << TT) - 1u;
-    if (!__syncthreads_or(mine)) continue;
-    if (tid < tile.z) {
-      sh[tid * 2 + 0] = src32[(int64_t)(tile.y + tid) * 2 + 0];
-      sh[tid * 2 + 1] = src32[(int64_t)(tile.y + tid) * 2 + 1];
-    }
-    __syncthreads();
-    if (mine) {
-      float pp[TT];
-#pragma unroll
-      for (int q = 0; q < TT; ++q) pp[q] = 0.f;
-#pragma unroll 2
-      for (int j = 0; j < tile.z; ++j) {
-        const float4 a = sh[j * 2], b = sh[j * 2 + 1];
-#pragma unroll
-        for (int q = 0; q < TT; ++q) {
-          const float dx = X[q] - a.x, dy = Y[q] - a.y, dz = Z[q] - a.z;
-          const float ri = rsqrt_apx_p(fmaf(dz, dz, fmaf(dy, dy, dx * dx)));
-          pp[q] = fmaf(fmaf(b.y, dz, fmaf(b.x, dy, a.w * dx)), ri * ri * ri, pp[q]);
-        }
-      }
-#pragma unroll
-      for (int q = 0; q < TT; ++q) {
-        if (!((skipmask >> q) & 1u)) {
-          float sum, err;
-          two_sum_p(acc[(2 * q + 0) * kFarTile + tid], pp[q], sum, err);
-          acc[(2 * q + 0) * kFarTile + tid] = sum;
-          acc[(2 * q + 1) * kFarTile + tid] += err;
-        }
-      }
-    }
-    __syncthreads();
-  }
-#pragma unroll
-  for (int q = 0; q < TT; ++q) {
-    const int64_t t = t0 + (int64_t)q * kFarTile;
-    if (t < N)
-      atomicAdd(p_out + t,
-                ((double)acc[(2 * q + 0) * kFarTile + tid] + (double)acc[(2 * q + 1) * kFarTile + tid]) * kInv4PiP);
-  }
-}
-
-void launch_pressure_far(const DevGeom& d, const GeomHost& h, int64_t NT, double* pr, cudaStream_t st) {
+// FP64 pressure quadrature (the mixed form is summed by the Stokeslet far
+// kernel in the same pass as the velocity).
+void launch_pressure_far_fp64(const DevGeom& d, const GeomHost& h, int64_t NT, double* pr, cudaStream_t st) {
   if (NT <= 0) return;
   const int nt = (int)h.tiles.size();
-  if (h.precision == SBIO_FP64) {
-    const int64_t tb = (NT + kFarTile - 1) / kFarTile;
-    const dim3 grid((unsigned)tb, (unsigned)far_split_count(tb, nt, 0));
-    pressure_far_fp64_kernel<<<grid, kFarTile, 0, st>>>(d.tiles, nt, d.st_src64, d.xyz, d.parts, d.skip_ptr,
-                                                        d.skip_idx, NT, pr);
-  } else {
-    constexpr int TT = 4;
-    const int64_t tb = (NT + (int64_t)kFarTile * TT - 1) / ((int64_t)kFarTile * TT);
-    const dim3 grid((unsigned)tb, (unsigned)far_split_count(tb, nt, 0));
-    pressure_far_mixed_kernel<TT><<<grid, kFarTile, 0, st>>>(d.tiles, nt, d.st_src32, d.tgt32, d.cen32, d.skip_ptr,
-                                                             d.skip_idx, NT, pr);
-  }
+  const int64_t tb = (NT + kFarTile - 1) / kFarTile;
+  const dim3 grid((unsigned)tb, (unsigned)far_split_count(tb, nt, 0));
+  pressure_far_fp64_kernel<<<grid, kFarTile, 0, st>>>(d.tiles, nt, d.st_src64, d.xyz, d.parts, d.skip_ptr,
+                                                      d.skip_idx, NT, pr);
   count_launch();
 }
 
@@ -262,8 +149,9 @@ int sbio_eval_targets_stokes(sbio_targets* ts, const double* f_tilde, double* u_
     SBIO_CUDA_TRY(cudaGetLastError());
   }
   if (fork) SBIO_CUDA_TRY(cudaEventRecord(g->ev_join, ns));
-  if ((rc = launch_stokes_far_on(v, h, T, u_out, st))) return rc;
-  if (p_out) launch_pressure_far(v, h, T, p_out, st);
+  const bool fp64 = h.precision == SBIO_FP64;
+  if ((rc = launch_stokes_far_on(v, h, T, u_out, fp64 ? nullptr : p_out, st))) return rc;
+  if (p_out && fp64) launch_pressure_far_fp64(v, h, T, p_out, st);
   SBIO_CUDA_TRY(cudaGetLastError());
   if (fork) SBIO_CUDA_TRY(cudaStreamWaitEvent(st, g->ev_join, 0));
   return SBIO_OK;

@@ -102,3 +102,26 @@ def test_rejects_high_order(S, ctx):
     assert e.value.code == S.SBIO_ENOTSUP
     ts.close()
     g.close()
+
+
+@pytest.mark.parametrize("tt", [1, 4, -2, -4, -8])
+def test_far_forms_with_pressure(S, ctx, tt):
+    """Every Stokeslet far form, which in mixed precision also sums the
+    pressure in the same pass, stays within the mixed bound of FP64 for the
+    velocity and the pressure."""
+    s = I.config_suspension(3)
+    f = I.config_coefficients(s, 6, ndens=3).transpose(1, 0, 2).copy()
+    g = S.Geometry(ctx, s)
+    X = I.shell_points(s, per_particle=1, seed=11, far_points=2500)
+    ts = S.TargetSet(g, X)
+    U64, P64 = gpu_points(S, ts, f)
+    for splits in (0, 96):
+        S.sbio_geom_set_stokes_tuning(g.h, tt, splits, 0)
+        S.sbio_geom_set_precision(g.h, S.SBIO_MIXED)
+        Um, Pm = gpu_points(S, ts, f)
+        Uv, _ = gpu_points(S, ts, f, pressure=False)
+        S.sbio_geom_set_precision(g.h, S.SBIO_FP64)
+        assert rel(Um, U64) < TOLMIX and rel(Pm, P64) < TOLMIX, (tt, splits)
+        assert rel(Uv, Um) < 1e-6, (tt, splits)
+    ts.close()
+    g.close()
