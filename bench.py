@@ -53,6 +53,25 @@ METRIC = "BIO applies/s (Laplace S+D, all surface nodes)"
 # far pair of S' + D': 3 sub, 5 (r^2), 2 (r^-2, r^-3), 5 (r.nu_x), 3 (S' product
 # and FMA), 5 (d.r), 5 (d.nu_x), 2 (products), 2 + 2 (the two FMAs) = 34
 DERIV_FAR_FLOP_PER_PAIR = 34
+# far pair of the Stokeslet: 3 sub, 5 (r^2), 5 (f.r), 3 (r^-1 r^-2 products),
+# 12 (three component FMA pairs) = 28; with the pressure (f.r) r^-3 of the same
+# pair one more FMA = 30.  Stresslet: 3 sub, 5 (r^2), 5 (q.r), 5 (nu.r), 4
+# (products with r^-5), 6 (three FMAs) = 28.
+STOKES_FAR_FLOP_PER_PAIR = 28
+STOKES_P_FAR_FLOP_PER_PAIR = 30
+STRESSLET_FAR_FLOP_PER_PAIR = 28
+
+
+def sdl_near_flop_per_pair(p: int) -> int:
+    """Algorithmic FP64 flops of one Stokes double-layer near pair, as the
+    one-pass term evaluation does them, expansions of order P1 = p + 1.  Per
+    (n, m >= 1) term (cos and sin parts together): 20 for the recurrences and
+    the radial-angular factors, 21 for the local Cartesian gradient basis, 60
+    for the contraction with the thirteen expansions (30 FMA); per m = 0 term
+    47; per pair about 120 for coordinates, frame constants and the output.
+    The data-dependent Miller start of Q_n^0, Q_n^1 is not counted."""
+    p1 = p + 1
+    return (p1 * (p1 + 1) // 2) * (20 + 21 + 60) + (p1 + 1) * 47 + 120
 
 
 def parse():
@@ -461,12 +480,15 @@ def run_stokes100(args, ws, rank, lrank):
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
     for _ in range(args.warmup):
         S.sbio_apply_stokes_sl(g.h, fd, u)
+    clocks = ClockSampler(lrank)
+    clocks.start()
     ms = []
     l0 = S.sbio_launch_count()
     for _ in range(args.steps):                 # near (FP64) overlaps the Stokeslet far field (FP32)
         flush.zero_()
         ms.append(_event_time(st, lambda: S.sbio_apply_stokes_sl(g.h, fd, u)))
     launches = S.sbio_launch_count() - l0
+    clk = clocks.stop()
     # end to end through the host entry point: pinned host forces in, velocities out
     fh = torch.from_numpy(f).pin_memory()
     uh = torch.empty((g.N, 3), dtype=torch.float64).pin_memory()
@@ -493,7 +515,7 @@ def run_stokes100(args, ws, rank, lrank):
     t64 = _event_time(st, lambda: S.sbio_apply_stokes_sl(g.h, fd, u))
     err = float((um - u).abs().max() / u.abs().max())
     far_ms = statistics.mean(x[2] for x in ph)
-    ach = 28 * g.n_far / (far_ms * 1e-3) / 1e12
+    ach = STOKES_FAR_FLOP_PER_PAIR * g.n_far / (far_ms * 1e-3) / 1e12
     line = {"metric": "Stokes single-layer applies/s (all surface nodes)", "value": 1e3 / statistics.mean(ms),
             "unit": "applies/s", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": statistics.mean(ms), "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -508,8 +530,9 @@ def run_stokes100(args, ws, rank, lrank):
                          "far": far_ms},
             "roofline": {"kernel": "stokes_far_mixed_kernel", "bound": "alu", "achieved": ach,
                          "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": ach / FP32_PEAK_TFLOPS,
-                         "traffic": None},
-            "fp64_gpu_applies_per_s": 1e3 / t64, "rel_err_vs_fp64_gpu": err, "gpu_launches": int(launches)}
+                         "flop_per_pair": STOKES_FAR_FLOP_PER_PAIR, "traffic": None},
+            "fp64_gpu_applies_per_s": 1e3 / t64, "rel_err_vs_fp64_gpu": err, "gpu_launches": int(launches),
+            "clocks": clk}
     g.close()
     if rank == 0:
         print(json.dumps(line), flush=True)
@@ -553,12 +576,15 @@ def run_batch64(args, ws, rank, lrank):
     for _ in range(args.warmup):
         S.sbio_batch_apply(b, sig, mu, So, Do)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    clocks = ClockSampler(lrank)
+    clocks.start()
     ms = []
     l0 = S.sbio_launch_count()
     for _ in range(args.steps):
         flush.zero_()
         ms.append(_event_time(st, lambda: S.sbio_batch_apply(b, sig, mu, So, Do)))
     launches = S.sbio_launch_count() - l0
+    clk = clocks.stop()
     info = S.sbio_batch_info(b)
     # the same work as one apply per suspension, one after another (mixed)
     seq = _event_time(st, lambda: [S.sbio_apply_laplace(g.h, sig[k], mu[k], So[k], Do[k]) for k, g in enumerate(geoms)])
@@ -577,9 +603,14 @@ def run_batch64(args, ws, rank, lrank):
                        "persistent_grid": info["grid"], "far_targets_per_thread": best[0],
                        "l2": "flushed by a 256 MiB write before every timed step"},
             "gpairs_per_s": info["far_pairs"] / (mean * 1e-3) / 1e9,
+            "roofline": {"kernel": "whole step (far_persistent_kernel dominant)", "bound": "alu",
+                         "achieved": FAR_FLOP_PER_PAIR["SD"] * info["far_pairs"] / (mean * 1e-3) / 1e12,
+                         "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+                         "frac": FAR_FLOP_PER_PAIR["SD"] * info["far_pairs"] / (mean * 1e-3) / 1e12 / FP32_PEAK_TFLOPS,
+                         "flop_per_pair": FAR_FLOP_PER_PAIR["SD"], "traffic": None},
             "sequential_mixed_ms": seq, "fp64_plain_ms": f64,
             "speedup_vs_fp64_plain": f64 / mean, "speedup_vs_sequential_mixed": seq / mean,
-            "gpu_launches": int(launches)}
+            "gpu_launches": int(launches), "clocks": clk}
     S.sbio_batch_destroy(b)
     if rank == 0:
         print(json.dumps(line), flush=True)
@@ -922,7 +953,13 @@ def run_dirichlet200(args, ws, rank, lrank):
             "rel_residual": max(i["rel_residual"] for i in infos),
             "ms_per_iteration": ms / its if its else None, "apply_ms": apply_ms,
             "iteration_over_apply": (ms / its) / apply_ms if its else None,
-            "max_rel_err_at_shell_points": err, "gpu_launches": int(launches), "clocks": clk}
+            "max_rel_err_at_shell_points": err,
+            "roofline": {"kernel": "whole solve (far_mixed_kernel dominant; Arnoldi applies only)", "bound": "alu",
+                         "achieved": FAR_FLOP_PER_PAIR["SD"] * g.n_far * its / (ms * 1e-3) / 1e12,
+                         "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+                         "frac": FAR_FLOP_PER_PAIR["SD"] * g.n_far * its / (ms * 1e-3) / 1e12 / FP32_PEAK_TFLOPS,
+                         "flop_per_pair": FAR_FLOP_PER_PAIR["SD"], "traffic": None},
+            "gpu_launches": int(launches), "clocks": clk}
     ts.close()
     g.close()
     if rank == 0:
@@ -980,6 +1017,12 @@ def run_stokespoints100(args, ws, rank, lrank):
                        "points_recipe": "shells at 1e-1..1e-6 (10 per spheroid and distance) + 30,000 in the box",
                        "l2": "flushed (256 MiB write) before each step"},
             "evaluations_per_s": 1e3 / mean, "fp64_gpu_points_per_s": ts.T * 1e3 / t64,
+            "roofline": {"kernel": "whole evaluation (stokes_far_mixed_kernel with pressure dominant)",
+                         "bound": "alu",
+                         "achieved": STOKES_P_FAR_FLOP_PER_PAIR * ts.n_far / (mean * 1e-3) / 1e12,
+                         "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+                         "frac": STOKES_P_FAR_FLOP_PER_PAIR * ts.n_far / (mean * 1e-3) / 1e12 / FP32_PEAK_TFLOPS,
+                         "flop_per_pair": STOKES_P_FAR_FLOP_PER_PAIR, "traffic": None},
             "rel_err_vs_fp64_gpu": err, "gpu_launches": int(launches), "clocks": clk}
     ts.close()
     g.close()
@@ -1019,12 +1062,24 @@ def run_stokesdl100(args, ws, rank, lrank):
         ms.append(_event_time(st, lambda: S.sbio_apply_stokes_dl(g.h, qd, u)))
     launches = S.sbio_launch_count() - l0
     clk = clocks.stop()
+    S.sbio_geom_enable_timing(g.h, True)        # phase-timed pass, phases in order
+    ph = []
+    for _ in range(min(args.steps, 10)):
+        flush.zero_()
+        S.sbio_apply_stokes_dl(g.h, qd, u)
+        ph.append(S.sbio_geom_phase_times(g.h))
+    S.sbio_geom_enable_timing(g.h, False)
     um = u.clone()
     S.sbio_geom_set_precision(g.h, S.SBIO_FP64)
     S.sbio_apply_stokes_dl(g.h, qd, u)
     t64 = _event_time(st, lambda: S.sbio_apply_stokes_dl(g.h, qd, u))
     err = float((um - u).abs().max() / u.abs().max())
     mean = statistics.mean(ms)
+    near_ms = statistics.mean(x[1] for x in ph)
+    far_ms = statistics.mean(x[2] for x in ph)
+    near_flop = sdl_near_flop_per_pair(susp.p)
+    near_ach = near_flop * g.n_near / (near_ms * 1e-3) / 1e12
+    far_ach = STRESSLET_FAR_FLOP_PER_PAIR * g.n_far / (far_ms * 1e-3) / 1e12
     line = {"metric": "Stokes double-layer applies/s (all surface nodes)", "value": 1e3 / mean, "unit": "applies/s",
             "n_gpus": ws, "steps": args.steps, "warmup": args.warmup, "ms_per_step": mean,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64",
@@ -1032,6 +1087,14 @@ def run_stokesdl100(args, ws, rank, lrank):
             "config": {"workload": "stokesdl100_p12", "M": susp.M, "p": susp.p, "targets": g.N,
                        "near_pairs": g.n_near, "far_pairs_per_apply": g.n_far,
                        "l2": "flushed (256 MiB write) before each step"},
+            "phase_ms": {"prep_and_self": statistics.mean(x[0] for x in ph), "near": near_ms, "far": far_ms},
+            "roofline": {"kernel": "stokes_dl_near_kernel (FP64 pipe)", "bound": "alu", "achieved": near_ach,
+                         "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": near_ach / FP64_PEAK_TFLOPS,
+                         "flop_per_pair": near_flop, "traffic": None,
+                         "peak_source": "nominal GB300 FP64 1.25 TFLOP/s"},
+            "roofline_far": {"kernel": "stresslet_far_mixed_kernel", "bound": "alu", "achieved": far_ach,
+                             "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": far_ach / FP32_PEAK_TFLOPS,
+                             "flop_per_pair": STRESSLET_FAR_FLOP_PER_PAIR, "traffic": None},
             "fp64_gpu_applies_per_s": 1e3 / t64, "rel_err_vs_fp64_gpu": err, "gpu_launches": int(launches),
             "clocks": clk}
     g.close()
