@@ -458,7 +458,7 @@ void launch_stresslet_far(const DevGeom& tg, const DevGeom& src, const GeomHost&
 //   d = 12 (q . nu):          -(R g_d)_k to component k,
 // with X the node relative to the centre.  Atomic adds: the near kernels may
 // be adding to the same outputs on another stream.
-__global__ void __launch_bounds__(256) sdl_self_kernel(int p, int n_v, int n_phi, int d0, int d1,
+__global__ void __launch_bounds__(256) sdl_self_kernel(int p, int n_v, int n_phi, int n_groups,
                                                        const PartGeom* __restrict__ parts,
                                                        const double* __restrict__ xyz,
                                                        const double* __restrict__ coef,
@@ -472,6 +472,8 @@ __global__ void __launch_bounds__(256) sdl_self_kernel(int p, int n_v, int n_phi
                                                        double* __restrict__ u_out) {
   extern __shared__ double sm[];
   const int i = blockIdx.x;
+  // expansions [d0, d1) of group blockIdx.y (the groups split the thirteen evenly)
+  const int d0 = (int)(blockIdx.y * 13 / n_groups), d1 = (int)((blockIdx.y + 1) * 13 / n_groups);
   const int p1 = p + 1, nc1 = (p1 + 1) * (p1 + 1), nm1 = nm_count(p1), mw1 = 2 * p1 + 1;
   const int G = n_v * n_phi, nd = d1 - d0;
   const PartGeom P = parts[i];
@@ -541,19 +543,19 @@ int sdl_self(sbio_geom* g, double* u_out, cudaStream_t st) {
   const GeomHost& h = g->h;
   const DevGeom& d = g->d;
   const int p1 = h.p + 1, mw1 = 2 * p1 + 1;
-  const int groups[3] = {0, 7, 13};
-  for (int k = 0; k < 2; ++k) {
-    const int nd = groups[k + 1] - groups[k];
-    const size_t smem = (size_t)nd * 3 * h.n_v * mw1 * sizeof(double);
-    if (smem > 227 * 1024) return set_error(SBIO_ENOTSUP, "Stokes double layer self: p = %d too large", h.p);
-    if (smem > 48 * 1024)
-      SBIO_CUDA_TRY(cudaFuncSetAttribute(sdl_self_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    sdl_self_kernel<<<h.M, 256, smem, st>>>(h.p, h.n_v, h.n_phi, groups[k], groups[k + 1], d.parts, d.xyz,
-                                            d.sdl_coef, d.st_qu0, d.st_dqu0, d.st_fP, d.st_fV, d.st_fF, d.st_trig1,
-                                            d.st_glv, u_out);
-    count_launch();
-    SBIO_CUDA_TRY(cudaGetLastError());
-  }
+  // one launch over (particle, group of expansions): four groups of 3-4
+  // expansions give 4 M CTAs, each holding its group's Legendre sums
+  constexpr int kGroups = 4;
+  const int nd_max = (13 + kGroups - 1) / kGroups;
+  const size_t smem = (size_t)nd_max * 3 * h.n_v * mw1 * sizeof(double);
+  if (smem > 227 * 1024) return set_error(SBIO_ENOTSUP, "Stokes double layer self: p = %d too large", h.p);
+  if (smem > 48 * 1024)
+    SBIO_CUDA_TRY(cudaFuncSetAttribute(sdl_self_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  sdl_self_kernel<<<dim3(h.M, kGroups), 256, smem, st>>>(h.p, h.n_v, h.n_phi, kGroups, d.parts, d.xyz, d.sdl_coef,
+                                                         d.st_qu0, d.st_dqu0, d.st_fP, d.st_fV, d.st_fF, d.st_trig1,
+                                                         d.st_glv, u_out);
+  count_launch();
+  SBIO_CUDA_TRY(cudaGetLastError());
   return SBIO_OK;
 }
 
