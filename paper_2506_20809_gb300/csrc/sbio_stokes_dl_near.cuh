@@ -34,21 +34,21 @@ struct SdlNearVisitor {
     cm = c; sm = s;
     tcc = c1 * c; tss = s1 * s; tsc = s1 * c; tcs = c1 * s;
   }
-  // sum over the three components of field (base + l) of coefficient x gradient component l
-  __device__ __forceinline__ double field(int base, int kc, int ks, const double* Bc, const double* Bs) const {
-    double r = 0.0;
+  // acc += sum over the three components l of field (base + l) of its
+  // coefficients times gradient component l (FMAs straight into acc)
+  __device__ __forceinline__ void field(double& acc, int base, int kc, int ks, const double* Bc,
+                                        const double* Bs) const {
 #pragma unroll
-    for (int l = 0; l < 3; ++l) r = fma(cf[(base + l) * NC + kc], Bc[l], fma(cf[(base + l) * NC + ks], Bs[l], r));
-    return r;
+    for (int l = 0; l < 3; ++l) acc = fma(cf[(base + l) * NC + kc], Bc[l], fma(cf[(base + l) * NC + ks], Bs[l], acc));
   }
   __device__ __forceinline__ void term(int n, int m, double, double Tu, double Tv, double Tp) {
     const double al = fma(k_ru, Tu, k_rv * Tv), z = fma(k_zu, Tu, k_zv * Tv), g = k_p * Tp;
     const double Bc[3] = {fma(al, tcc, g * tss), fma(al, tsc, -g * tcs), z * cm};
     const double Bs[3] = {fma(al, tcs, -g * tsc), fma(al, tss, g * tcc), z * sm};
     const int kc = n * n + n + m, ks = n * n + n - m;
-    div += field(0, kc, ks, Bc, Bs);
+    field(div, 0, kc, ks, Bc, Bs);
 #pragma unroll
-    for (int i = 0; i < 3; ++i) t2[i] += field(3 + 3 * i, kc, ks, Bc, Bs);
+    for (int i = 0; i < 3; ++i) field(t2[i], 3 + 3 * i, kc, ks, Bc, Bs);
 #pragma unroll
     for (int l = 0; l < 3; ++l) gS[l] = fma(cf[12 * NC + kc], Bc[l], fma(cf[12 * NC + ks], Bs[l], gS[l]));
   }
@@ -56,17 +56,12 @@ struct SdlNearVisitor {
     const double al = fma(k_ru, Tu, k_rv * Tv), z = fma(k_zu, Tu, k_zv * Tv);
     const double B[3] = {c1 * al, s1 * al, z};
     const int k = n * n + n;
-    double r = 0.0;
 #pragma unroll
-    for (int l = 0; l < 3; ++l) r = fma(cf[l * NC + k], B[l], r);
-    div += r;
+    for (int l = 0; l < 3; ++l) div = fma(cf[l * NC + k], B[l], div);
 #pragma unroll
-    for (int i = 0; i < 3; ++i) {
-      double ri = 0.0;
+    for (int i = 0; i < 3; ++i)
 #pragma unroll
-      for (int l = 0; l < 3; ++l) ri = fma(cf[(3 + 3 * i + l) * NC + k], B[l], ri);
-      t2[i] += ri;
-    }
+      for (int l = 0; l < 3; ++l) t2[i] = fma(cf[(3 + 3 * i + l) * NC + k], B[l], t2[i]);
 #pragma unroll
     for (int l = 0; l < 3; ++l) gS[l] = fma(cf[12 * NC + k], B[l], gS[l]);
   }

@@ -52,8 +52,9 @@ struct StokesNearVisitor {
     Hu = fma(a, Tu, Hu);
     Hv = fma(a, Tv, Hv);
     Hp = fma(b, Tp, Hp);
+    const double Tc = T * cm, Ts = T * sm;
 #pragma unroll
-    for (int j = 0; j < 3; ++j) F[j] = fma(fma(cf[j * NC + kc], cm, cf[j * NC + ks] * sm), T, F[j]);
+    for (int j = 0; j < 3; ++j) F[j] = fma(cf[j * NC + kc], Tc, fma(cf[j * NC + ks], Ts, F[j]));
   }
   __device__ __forceinline__ void term0(int n, double T, double Tu, double Tv) {
     const int k = n * n + n;
