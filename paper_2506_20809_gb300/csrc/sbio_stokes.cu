@@ -131,7 +131,10 @@ __global__ void __launch_bounds__(256) stokes_prep_kernel(
 // expansions the value and the three unit-vector derivatives are inverse
 // transforms of the folded coefficients times q(u0) or q'(u0), with the
 // Ferrers tables P, sqrt(1-v^2) dP/dv and m P / sqrt(1-v^2) at the GL nodes
-// (the exterior limit of eq. (dSLevalformula) applied mode by mode).  Writes u.
+// (the exterior limit of eq. (dSLevalformula) applied mode by mode).  The
+// velocity is linear in the four expansions, so CTA (i, y) takes expansions
+// 2y and 2y + 1 of particle i and adds its share to u (zeroed beforehand):
+// 1/2 F_k to component k and -1/2 R X_k grad F_k for k < 3, 1/2 R grad F_y.
 __global__ void __launch_bounds__(256) stokes_self_kernel(int p, int n_v, int n_phi, const PartGeom* __restrict__ parts,
                                                           const double* __restrict__ xyz,
                                                           const double* __restrict__ coef,
@@ -148,11 +151,12 @@ __global__ void __launch_bounds__(256) stokes_self_kernel(int p, int n_v, int n_
   const int p1 = p + 1, nc1 = (p1 + 1) * (p1 + 1), nm1 = nm_count(p1), mw1 = 2 * p1 + 1;
   const int G = n_v * n_phi;
   const PartGeom P = parts[i];
-  const double* cf = coef + (size_t)i * 4 * nc1;
+  const int d0 = 2 * blockIdx.y;                // expansions d0, d0 + 1
+  const double* cf = coef + (size_t)i * 4 * nc1 + (size_t)d0 * nc1;
   const double* q0 = qu0 + (size_t)i * nm1;
   const double* dq0 = dqu0 + (size_t)i * nm1;
-  // L[(d * 4 + qty) * n_v + j][ms]: qty 0 value, 1 d/du, 2 sv d/dv, 3 d/dphi / sv
-  for (int idx = threadIdx.x; idx < 16 * n_v * mw1; idx += blockDim.x) {
+  // L[(dd * 4 + qty) * n_v + j][ms]: qty 0 value, 1 d/du, 2 sv d/dv, 3 d/dphi / sv
+  for (int idx = threadIdx.x; idx < 8 * n_v * mw1; idx += blockDim.x) {
     const int row = idx / mw1, ms = idx - row * mw1, m = ms - p1, am = m < 0 ? -m : m;
     const int dq = row / n_v, j = row - dq * n_v, dd = dq >> 2, qty = dq & 3;
     const double* tab = (qty == 2) ? fV : (qty == 3 ? fF : fP);
@@ -169,8 +173,8 @@ __global__ void __launch_bounds__(256) stokes_self_kernel(int p, int n_v, int n_
   for (int l = threadIdx.x; l < G; l += blockDim.x) {
     const int j = l / n_phi, k = l - j * n_phi;
     const double* tr = trig1 + (size_t)k * (p1 + 1) * 2;
-    double F[4][4];
-    for (int dq = 0; dq < 16; ++dq) {
+    double F[2][4];
+    for (int dq = 0; dq < 8; ++dq) {
       const double* L = sm + ((size_t)dq * n_v + j) * mw1 + p1;
       double acc;
       if ((dq & 3) == 3) {   // d/dphi: cos -> -m sin, sin -> m cos (m inside the table)
@@ -187,19 +191,20 @@ __global__ void __launch_bounds__(256) stokes_self_kernel(int p, int n_v, int n_
     const double iW = rsqrt(u * u + sgn * v * v);
     const double eu0 = u * sv * c1 * iW, eu1 = u * sv * s1 * iW, eu2 = v * su * iW;
     const double ev0 = -su * v * c1 * iW, ev1 = -su * v * s1 * iW, ev2 = u * sv * iW;
-    double g[4][3];
-    for (int dd = 0; dd < 4; ++dd) {
-      const double gu = F[dd][1] * su * ia * iW, gv = F[dd][2] * ia * iW, gp = F[dd][3] * ia / su;
-      g[dd][0] = gu * eu0 + gv * ev0 - gp * s1;
-      g[dd][1] = gu * eu1 + gv * ev1 + gp * c1;
-      g[dd][2] = gu * eu2 + gv * ev2;
-    }
     const int64_t t = (int64_t)i * G + l;
-    const double X0 = xyz[t * 3 + 0] - P.c[0], X1 = xyz[t * 3 + 1] - P.c[1], X2 = xyz[t * 3 + 2] - P.c[2];
-    double w[3];
-    for (int c = 0; c < 3; ++c) w[c] = g[3][c] - (X0 * g[0][c] + X1 * g[1][c] + X2 * g[2][c]);
+    const double X[3] = {xyz[t * 3 + 0] - P.c[0], xyz[t * 3 + 1] - P.c[1], xyz[t * 3 + 2] - P.c[2]};
+    double w[3] = {0.0, 0.0, 0.0}, val[3] = {0.0, 0.0, 0.0};
+    for (int dd = 0; dd < 2; ++dd) {
+      const int d = d0 + dd;
+      const double gu = F[dd][1] * su * ia * iW, gv = F[dd][2] * ia * iW, gp = F[dd][3] * ia / su;
+      const double g[3] = {gu * eu0 + gv * ev0 - gp * s1, gu * eu1 + gv * ev1 + gp * c1, gu * eu2 + gv * ev2};
+      const double wt = (d == 3) ? 1.0 : -X[d];   // grad F_y - sum_j X_j grad F_j
+      for (int c = 0; c < 3; ++c) w[c] = fma(wt, g[c], w[c]);
+      if (d < 3) val[d] = F[dd][0];
+    }
     for (int c = 0; c < 3; ++c)
-      u_out[t * 3 + c] = 0.5 * (F[c][0] + P.R[c * 3 + 0] * w[0] + P.R[c * 3 + 1] * w[1] + P.R[c * 3 + 2] * w[2]);
+      atomicAdd(u_out + t * 3 + c,
+                0.5 * (val[c] + P.R[c * 3 + 0] * w[0] + P.R[c * 3 + 1] * w[1] + P.R[c * 3 + 2] * w[2]));
   }
 }
 
@@ -526,10 +531,11 @@ int launch_stokes(sbio_geom* g, const double* f, double* u, cudaStream_t st) {
   phase_mark(g, 0, st);
   int rc0 = launch_stokes_prep(g, f, st);
   if (rc0) return rc0;
-  const size_t smem_self = (size_t)16 * h.n_v * mw1 * sizeof(double);
+  const size_t smem_self = (size_t)8 * h.n_v * mw1 * sizeof(double);
   if (smem_self > 48 * 1024)
     SBIO_CUDA_TRY(cudaFuncSetAttribute(stokes_self_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_self));
-  stokes_self_kernel<<<h.M, 256, smem_self, st>>>(p, h.n_v, h.n_phi, d.parts, d.xyz, d.st_coef, d.st_qu0, d.st_dqu0,
+  SBIO_CUDA_TRY(cudaMemsetAsync(u, 0, (size_t)h.N * 3 * sizeof(double), st));
+  stokes_self_kernel<<<dim3(h.M, 2), 256, smem_self, st>>>(p, h.n_v, h.n_phi, d.parts, d.xyz, d.st_coef, d.st_qu0, d.st_dqu0,
                                                   d.st_fP, d.st_fV, d.st_fF, d.st_trig1, d.st_glv, u);
   count_launch();
   SBIO_CUDA_TRY(cudaGetLastError());
