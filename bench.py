@@ -984,7 +984,8 @@ def run_stokespoints100(args, ws, rank, lrank):
     X = I.shell_points(susp, per_particle=10, seed=0, far_points=30000)
     ctx = S.sbio_ctx_create(lrank, 0)
     g = S.Geometry(ctx, susp, precision=S.SBIO_MIXED)
-    S.sbio_geom_autotune_stokes(g.h)
+    stune = S.sbio_geom_autotune_stokes(g.h)
+    scap = S.sbio_geom_get_stokes_tuning(g.h)["near_ctas_per_sm"]
     ts = S.TargetSet(g, X)
     fd = torch.from_numpy(f).cuda()
     u = torch.empty((ts.T, 3), dtype=torch.float64, device="cuda")
@@ -1014,6 +1015,8 @@ def run_stokespoints100(args, ws, rank, lrank):
             "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
             "config": {"workload": "stokespoints100_p12", "M": susp.M, "p": susp.p, "points": ts.T,
                        "near_pairs": ts.n_near, "far_pairs": ts.n_far,
+                       "far_launch": {"targets_per_thread": stune[0], "source_splits": stune[1]},
+                       "near_ctas_per_sm_overlapped": scap,
                        "points_recipe": "shells at 1e-1..1e-6 (10 per spheroid and distance) + 30,000 in the box",
                        "l2": "flushed (256 MiB write) before each step"},
             "evaluations_per_s": 1e3 / mean, "fp64_gpu_points_per_s": ts.T * 1e3 / t64,
@@ -1046,7 +1049,8 @@ def run_stokesdl100(args, ws, rank, lrank):
     q = I.config_coefficients(susp, 1, ndens=3).transpose(1, 0, 2).copy()
     ctx = S.sbio_ctx_create(lrank, 0)
     g = S.Geometry(ctx, susp, precision=S.SBIO_MIXED)
-    S.sbio_geom_autotune_stokes(g.h)
+    stune = S.sbio_geom_autotune_stokes(g.h)
+    scap = S.sbio_geom_get_stokes_tuning(g.h)["near_ctas_per_sm"]
     qd = torch.from_numpy(q).cuda()
     u = torch.empty((g.N, 3), dtype=torch.float64, device="cuda")
     st = torch.cuda.current_stream()
@@ -1086,6 +1090,8 @@ def run_stokesdl100(args, ws, rank, lrank):
             "data": "synthetic",
             "config": {"workload": "stokesdl100_p12", "M": susp.M, "p": susp.p, "targets": g.N,
                        "near_pairs": g.n_near, "far_pairs_per_apply": g.n_far,
+                       "far_launch": {"targets_per_thread": stune[0], "source_splits": stune[1]},
+                       "near_ctas_per_sm_overlapped": scap,
                        "l2": "flushed (256 MiB write) before each step"},
             "phase_ms": {"prep_and_self": statistics.mean(x[0] for x in ph), "near": near_ms, "far": far_ms},
             "roofline": {"kernel": "stokes_dl_near_kernel (FP64 pipe)", "bound": "alu", "achieved": near_ach,
