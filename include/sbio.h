@@ -275,10 +275,10 @@ int sbio_geom_get_stokes_tuning(const sbio_geom* g, int32_t* far_tt, int32_t* fa
 
 /* Autotuner of the Stokes kernels: as sbio_geom_autotune, timing the
  * Stokeslet far kernel and whole Stokes applies (zero forces through the
- * geometry's own workspaces).  The near cap is taken from the widest down,
- * a narrower one replacing it only when more than 1 % faster, since the same
- * cap serves calls with heavier near pairs (velocity and pressure at points).
- * SBIO_ENOTSUP for p > 20.  Synchronises `stream`. */
+ * geometry's own workspaces).  The velocity-and-pressure evaluation at
+ * points runs its near pairs at twice the tuned near cap (its near pairs cost
+ * about twice the single layer's).  SBIO_ENOTSUP for p > 20.  Synchronises
+ * `stream`. */
 int sbio_geom_autotune_stokes(sbio_geom* g, void* stream, int32_t* far_tt, int32_t* far_splits, double* far_ms);
 
 

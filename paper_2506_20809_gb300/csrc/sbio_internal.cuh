@@ -223,9 +223,6 @@ struct TuneOps {
   int* tt;
   int* splits;
   int* cap;
-  // keep the widest near cap unless a narrower one is more than 1 % faster
-  // (the tuned apply may carry less near work than other calls sharing the cap)
-  bool prefer_wide_near = false;
 };
 int tune_launch_shape(sbio_geom* g, const TuneOps& ops, double* out, cudaStream_t st, double* best_far_ms);
 

@@ -635,18 +635,14 @@ int tune_launch_shape(sbio_geom* g, const TuneOps& ops, double* out, cudaStream_
   *ops.splits = best_sp;
   // near CTAs per SM while the near field overlaps the far field: whole applies
   if (!rc && ops.whole && g->overlap && g->near_stream && !g->timing && !h.pair_t.empty()) {
-    // narrowest first; with prefer_wide_near widest first, a narrower cap
-    // replacing the best only when it is more than 1 % faster
-    const int narrow_first[4] = {1, 2, 4, 0}, wide_first[4] = {0, 4, 2, 1};
-    const int* caps = ops.prefer_wide_near ? wide_first : narrow_first;
-    const float margin = ops.prefer_wide_near ? 0.99f : 1.0f;
+    const int caps[4] = {1, 2, 4, 0};
     float best_apply = 1e30f;
     int best_cap = *ops.cap;
     for (int c = 0; c < 4 && !rc; ++c) {
       *ops.cap = caps[c];
       float m = 0.f;
       rc = time3(ops.whole, &m);
-      if (!rc && m < best_apply * margin) {
+      if (!rc && m < best_apply) {
         best_apply = m;
         best_cap = caps[c];
       }
@@ -830,7 +826,6 @@ int sbio_geom_autotune_stokes(sbio_geom* g, void* stream, int32_t* far_tt, int32
   ops.tt = &h.st_far_tt;
   ops.splits = &h.st_far_splits;
   ops.cap = &h.st_near_ctas_per_sm;
-  ops.prefer_wide_near = true;   // points with pressure carry heavier near pairs than the tuned apply
   double best = 0.0;
   rc = tune_launch_shape(g, ops, d.host_out, st, &best);
   if (rc) return rc;

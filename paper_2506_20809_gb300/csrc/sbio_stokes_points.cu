@@ -130,7 +130,11 @@ int sbio_eval_targets_stokes(sbio_targets* ts, const double* f_tilde, double* u_
   if (fork) {
     SBIO_CUDA_TRY(cudaEventRecord(g->ev_fork, st));
     SBIO_CUDA_TRY(cudaStreamWaitEvent(ns, g->ev_fork, 0));
-    v.near_grid_cap = h.st_near_ctas_per_sm > 0 ? h.st_near_ctas_per_sm * sm_count() : 0;
+    // with the pressure a near pair costs about twice the velocity-only pair
+    // the cap was tuned on (four derivative sums per expansion instead of one
+    // combined gradient), against a similar far pair: twice the CTAs
+    const int cap = h.st_near_ctas_per_sm * (p_out ? 2 : 1);
+    v.near_grid_cap = cap > 0 ? cap * sm_count() : 0;
   }
   if (n_pairs > 0) {
     if (p_out) {
