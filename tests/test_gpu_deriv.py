@@ -244,4 +244,8 @@ def test_points_invalid_arguments(S, ctx):
             S.sbio_eval_targets_deriv(ts.h, *args)
         assert e.value.code == S.SBIO_EINVAL
     ts.close()
+    # an empty set: nothing to do, no direction array needed
+    ts = S.TargetSet(g, np.zeros((0, 3)))
+    S.sbio_eval_targets_deriv(ts.h, None, x, None, out, None)
+    ts.close()
     g.close()

@@ -126,3 +126,23 @@ def test_mixed_far_forms(S, ctx, tt):
         assert rel(Pm.cpu().numpy(), P64) < TOLMIX, (tt, splits)
     ts.close()
     g.close()
+
+
+def test_stokesdl100_sampled_against_oracle(S, ctx):
+    """100 spheroids, p = 12 (the benchmark suspension): 30 sampled nodes of
+    the FP64 GPU apply against the oracle's method, and the mixed apply within
+    its bound of the same oracle values."""
+    s = I.config_suspension(3)
+    p = s.p
+    q = np.random.default_rng(4).standard_normal((s.M, 3, (p + 1) ** 2)) / (1 + np.arange((p + 1) ** 2))
+    g = S.Geometry(ctx, s)
+    U64 = gpu_dl(S, g, q, S.SBIO_FP64)
+    Um = gpu_dl(S, g, q, S.SBIO_MIXED)
+    S.sbio_geom_set_precision(g.h, S.SBIO_FP64)
+    og = OG.SuspensionGeom.from_suspension(s)
+    tg = np.sort(np.random.default_rng(12).choice(g.N, 30, replace=False))
+    Ur = OSD.StokesDLOracle(og).apply(q, "method", targets=tg)
+    scale = np.max(np.abs(U64))
+    assert np.max(np.abs(U64[tg] - Ur)) / scale < TOL64
+    assert np.max(np.abs(Um[tg] - Ur)) / scale < TOLMIX
+    g.close()

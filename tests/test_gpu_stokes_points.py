@@ -125,3 +125,22 @@ def test_far_forms_with_pressure(S, ctx, tt):
         assert rel(Uv, Um) < 1e-6, (tt, splits)
     ts.close()
     g.close()
+
+
+def test_stokes100_points_sampled_against_oracle(S, ctx):
+    """The benchmark suspension (100 spheroids, p = 12) at shell and box
+    points: 40 sampled points of the FP64 GPU evaluation (velocity and
+    pressure) against the oracle's method."""
+    s = I.config_suspension(3)
+    f = I.config_coefficients(s, 6, ndens=3).transpose(1, 0, 2).copy()
+    g = S.Geometry(ctx, s)
+    X = I.shell_points(s, per_particle=1, seed=4, far_points=2000)
+    ts = S.TargetSet(g, X)
+    U64, P64 = gpu_points(S, ts, f)
+    og = OG.SuspensionGeom.from_suspension(s)
+    sel = np.sort(np.random.default_rng(3).choice(len(X), 40, replace=False))
+    Ur, Pr = OSK.StokesOracle(og).eval_points(X[sel], f, "method")
+    assert np.max(np.abs(U64[sel] - Ur)) / np.max(np.abs(U64)) < TOL64
+    assert np.max(np.abs(P64[sel] - Pr)) / np.max(np.abs(P64)) < TOL64
+    ts.close()
+    g.close()
