@@ -231,6 +231,7 @@ int build_host(GeomHost& h, const sbio_spheroid* sph, int32_t M, const sbio_opti
 // near pairs at its offset (ascending source) and its far skip list (own and
 // near particles ascending, then a sentinel) at its CSR offset.
 __global__ void __launch_bounds__(128) near_sets_kernel(int M, int G, int64_t N, const PartGeom* __restrict__ parts,
+                                                        const float4* __restrict__ sph,
                                                         const double* __restrict__ xyz, double near_factor, int fill,
                                                         int32_t* __restrict__ count,
                                                         unsigned long long* __restrict__ overlap_min,
@@ -242,12 +243,19 @@ __global__ void __launch_bounds__(128) near_sets_kernel(int M, int G, int64_t N,
   if (t >= N) return;
   const int own = (int)(t / G);
   const double x0 = xyz[t * 3 + 0], x1 = xyz[t * 3 + 1], x2 = xyz[t * 3 + 2];
+  const float y0 = (float)x0, y1 = (float)x1, y2 = (float)x2;
   int c = 0;
   const int64_t po = fill ? pair_off[t] : 0;
   int32_t so = fill ? skip_ptr[t] : 0;
   bool own_done = false;
   for (int i = 0; i < M; ++i) {
     if (i == own) continue;
+    // FP32 prefilter against a sphere enlarged by a relative 1e-4 and an
+    // absolute 1e-3 over the FP64 test's radius (rmax + threshold): it only
+    // drops particles the FP64 test below drops too
+    const float4 b = sph[i];
+    const float e0 = y0 - b.x, e1 = y1 - b.y, e2 = y2 - b.z;
+    if (fmaf(e2, e2, fmaf(e1, e1, e0 * e0)) > b.w) continue;
     const PartGeom& P = parts[i];
     const double rmax = fmax(P.A, P.C), thr = near_factor * rmax;
     const double d0 = x0 - P.c[0], d1 = x1 - P.c[1], d2 = x2 - P.c[2];
@@ -322,8 +330,19 @@ static int build_near(sbio_geom* g) {
   if ((rc = tmp((void**)&dcount, (size_t)N * sizeof(int32_t)))) return rc;
   if ((rc = tmp((void**)&dovl, sizeof(unsigned long long)))) return rc;
   SBIO_CUDA_TRY(cudaMemsetAsync(dovl, 0xff, sizeof(unsigned long long), st));
+  // per particle: FP32 centre and the squared prefilter radius
+  std::vector<float4> sph_h(M);
+  for (int i = 0; i < M; ++i) {
+    const PartGeom& P = h.parts[i];
+    const double rmax = std::max(P.A, P.C);
+    const double rcut = (rmax + h.near_factor * rmax) * (1.0 + 1e-4) + 1e-3;
+    sph_h[i] = make_float4((float)P.c[0], (float)P.c[1], (float)P.c[2], (float)(rcut * rcut));
+  }
+  float4* dsph = nullptr;
+  if ((rc = tmp((void**)&dsph, (size_t)M * sizeof(float4)))) return rc;
+  SBIO_CUDA_TRY(cudaMemcpyAsync(dsph, sph_h.data(), (size_t)M * sizeof(float4), cudaMemcpyHostToDevice, st));
   const unsigned blocks = (unsigned)((N + 127) / 128);
-  near_sets_kernel<<<blocks, 128, 0, st>>>(M, h.G, N, d.parts, d.xyz, h.near_factor, 0, dcount, dovl, nullptr,
+  near_sets_kernel<<<blocks, 128, 0, st>>>(M, h.G, N, d.parts, dsph, d.xyz, h.near_factor, 0, dcount, dovl, nullptr,
                                            nullptr, nullptr, nullptr, nullptr);
   SBIO_CUDA_TRY(cudaGetLastError());
   std::vector<int32_t> cnt(N);
@@ -351,8 +370,8 @@ static int build_near(sbio_geom* g) {
   if ((rc = dev_alloc(g, (void**)&d.skip_idx, (size_t)sptr[N] * sizeof(int32_t), "skip lists"))) return rc;
   if ((rc = tmp((void**)&dpt, (size_t)P * sizeof(int32_t)))) return rc;
   if ((rc = tmp((void**)&dps, (size_t)P * sizeof(int32_t)))) return rc;
-  near_sets_kernel<<<blocks, 128, 0, st>>>(M, h.G, N, d.parts, d.xyz, h.near_factor, 1, nullptr, nullptr, dpoff, dpt,
-                                           dps, d.skip_ptr, d.skip_idx);
+  near_sets_kernel<<<blocks, 128, 0, st>>>(M, h.G, N, d.parts, dsph, d.xyz, h.near_factor, 1, nullptr, nullptr, dpoff,
+                                           dpt, dps, d.skip_ptr, d.skip_idx);
   SBIO_CUDA_TRY(cudaGetLastError());
   std::vector<int32_t> pt(P), ps(P);
   if (P > 0) {
