@@ -7,6 +7,8 @@
 #include <cstdio>
 #include <cstring>
 
+#include <functional>
+
 #include "sbio_internal.cuh"
 #include "sbio_near.cuh"
 
@@ -117,15 +119,6 @@ static void quat_rot(const double* q, double* R) {
   R[6] = 2 * (x * z - w * y);     R[7] = 2 * (y * z + w * x);     R[8] = 1 - 2 * (x * x + y * y);
 }
 
-double spheroid_distance_local(const PartGeom& P, double x, double y, double z, double tol, bool* inside) {
-  const double rho = std::hypot(x, y), az = std::fabs(z);
-  const double f = (rho / P.A) * (rho / P.A) + (az / P.C) * (az / P.C);
-  *inside = f < 1.0 - tol;
-  if (*inside) return 0.0;
-  if (P.C >= P.A) return ellipse_distance_hd(P.C, P.A, az, rho);
-  return ellipse_distance_hd(P.A, P.C, rho, az);
-}
-
 void split_f32(double v, float& hi, float& lo) {
   hi = (float)v;
   lo = (float)(v - (double)hi);
@@ -222,18 +215,21 @@ int build_host(GeomHost& h, const sbio_spheroid* sph, int32_t M, const sbio_opti
   return SBIO_OK;
 }
 
-// Per-target near sets (exact distances), in parallel over targets.
-// Near sets on the device.  One thread per target node loops over the
-// particles in ascending order: a bounding-sphere test, then (for candidates)
-// the exact point-to-spheroid distance; near iff below near_factor x the
-// source's major semi-axis (strict).  Count pass: near particles per node and
-// the smallest node lying inside another spheroid.  Fill pass: the node's
-// near pairs at its offset (ascending source) and its far skip list (own and
-// near particles ascending, then a sentinel) at its CSR offset.
+// Near sets on the device.  One thread per target loops over the particles
+// in ascending order: an FP32 bounding-sphere prefilter, then the FP64 sphere
+// test and (for candidates) the exact point-to-spheroid distance; near iff
+// below near_factor x the source's major semi-axis (strict).  Targets are the
+// geometry's nodes (G nodes per particle; a node's own particle is skipped and
+// heads its skip list) or arbitrary points (G = 0: no own particle).  A target
+// is inside a spheroid when the ellipsoid form is below 1 - inside_tol.
+// Count pass: near particles per target and the smallest target lying inside
+// a spheroid.  Fill pass: the target's near pairs at its offset (ascending
+// source) and its far skip list (own and near particles ascending, then a
+// sentinel) at its CSR offset.
 __global__ void __launch_bounds__(128) near_sets_kernel(int M, int G, int64_t N, const PartGeom* __restrict__ parts,
                                                         const float4* __restrict__ sph,
-                                                        const double* __restrict__ xyz, double near_factor, int fill,
-                                                        int32_t* __restrict__ count,
+                                                        const double* __restrict__ xyz, double near_factor,
+                                                        double inside_tol, int fill, int32_t* __restrict__ count,
                                                         unsigned long long* __restrict__ overlap_min,
                                                         const int64_t* __restrict__ pair_off,
                                                         int32_t* __restrict__ pair_t, int32_t* __restrict__ pair_s,
@@ -241,13 +237,13 @@ __global__ void __launch_bounds__(128) near_sets_kernel(int M, int G, int64_t N,
                                                         int32_t* __restrict__ skip_idx) {
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= N) return;
-  const int own = (int)(t / G);
+  const int own = G > 0 ? (int)(t / G) : -1;
   const double x0 = xyz[t * 3 + 0], x1 = xyz[t * 3 + 1], x2 = xyz[t * 3 + 2];
   const float y0 = (float)x0, y1 = (float)x1, y2 = (float)x2;
   int c = 0;
   const int64_t po = fill ? pair_off[t] : 0;
   int32_t so = fill ? skip_ptr[t] : 0;
-  bool own_done = false;
+  bool own_done = own < 0;
   for (int i = 0; i < M; ++i) {
     if (i == own) continue;
     // FP32 prefilter against a sphere enlarged by a relative 1e-4 and an
@@ -266,7 +262,7 @@ __global__ void __launch_bounds__(128) near_sets_kernel(int M, int G, int64_t N,
     const double zl = P.R[2] * d0 + P.R[5] * d1 + P.R[8] * d2;
     const double rho = hypot(xl, yl), az = fabs(zl);
     const double f = (rho / P.A) * (rho / P.A) + (az / P.C) * (az / P.C);
-    if (f < 1.0) {
+    if (f < 1.0 - inside_tol) {
       if (!fill) atomicMin(overlap_min, (unsigned long long)t);
       continue;
     }
@@ -291,22 +287,30 @@ __global__ void __launch_bounds__(128) near_sets_kernel(int M, int G, int64_t N,
   }
 }
 
-template <typename T>
-static int upload(sbio_geom* g, T** dst, const T* src, size_t count, const char* what);
-
-// Near pairs (sorted by source kind, source, target), far pair count,
-// source tiles and the device skip lists.
-static int build_near(sbio_geom* g) {
-  GeomHost& h = g->h;
-  DevGeom& d = g->d;
+// Near sets of n targets (device positions xyz, G nodes per particle or 0 for
+// points) on `st`: runs the count pass, returns SBIO_EOVERLAP (nodes) or
+// SBIO_EINVAL (points) with *inside the smallest target inside a spheroid,
+// allocates the skip lists through alloc_skip (CSR offsets of n + 1 entries
+// and the lists), runs the fill pass, and returns the pairs sorted by
+// (source kind, source, target) with the number on prolate sources and the
+// near count per target.  Synchronises `st`.
+int device_near_sets(sbio_geom* g, const double* xyz, int64_t n, int G, double inside_tol, cudaStream_t st,
+                     const std::function<int(const std::vector<int32_t>&, int32_t**, int32_t**)>& alloc_skip,
+                     std::vector<int32_t>& pair_t, std::vector<int32_t>& pair_s, int64_t* n_pro,
+                     std::vector<int32_t>& cnt, int64_t* inside) {
+  const GeomHost& h = g->h;
   const int M = h.M;
-  const int64_t N = h.N;
-  cudaStream_t st = g->setup_stream;
-  int rc;
-  if (!d.parts && (rc = upload(g, &d.parts, h.parts.data(), M, "particles"))) return rc;
-  if (!d.xyz && (rc = upload(g, &d.xyz, h.xyz.data(), N * 3, "node positions"))) return rc;
-  // transient buffers (counts, overlap flag, pair offsets and pairs), freed
-  // on the set-up stream before returning
+  *inside = -1;
+  pair_t.clear();
+  pair_s.clear();
+  cnt.assign(n, 0);
+  *n_pro = 0;
+  if (n == 0) {
+    int32_t *sp = nullptr, *si = nullptr;
+    return alloc_skip(std::vector<int32_t>(1, 0), &sp, &si);
+  }
+  int rc = SBIO_OK;
+  // transient buffers, freed on `st` before returning
   std::vector<void*> scratch;
   auto tmp = [&](void** ptr, size_t bytes) -> int {
     *ptr = nullptr;
@@ -327,7 +331,7 @@ static int build_near(sbio_geom* g) {
   } release{scratch, st};
   int32_t* dcount = nullptr;
   unsigned long long* dovl = nullptr;
-  if ((rc = tmp((void**)&dcount, (size_t)N * sizeof(int32_t)))) return rc;
+  if ((rc = tmp((void**)&dcount, (size_t)n * sizeof(int32_t)))) return rc;
   if ((rc = tmp((void**)&dovl, sizeof(unsigned long long)))) return rc;
   SBIO_CUDA_TRY(cudaMemsetAsync(dovl, 0xff, sizeof(unsigned long long), st));
   // per particle: FP32 centre and the squared prefilter radius
@@ -341,37 +345,38 @@ static int build_near(sbio_geom* g) {
   float4* dsph = nullptr;
   if ((rc = tmp((void**)&dsph, (size_t)M * sizeof(float4)))) return rc;
   SBIO_CUDA_TRY(cudaMemcpyAsync(dsph, sph_h.data(), (size_t)M * sizeof(float4), cudaMemcpyHostToDevice, st));
-  const unsigned blocks = (unsigned)((N + 127) / 128);
-  near_sets_kernel<<<blocks, 128, 0, st>>>(M, h.G, N, d.parts, dsph, d.xyz, h.near_factor, 0, dcount, dovl, nullptr,
-                                           nullptr, nullptr, nullptr, nullptr);
+  const unsigned blocks = (unsigned)((n + 127) / 128);
+  const PartGeom* dparts = g->d.parts;
+  near_sets_kernel<<<blocks, 128, 0, st>>>(M, G, n, dparts, dsph, xyz, h.near_factor, inside_tol, 0, dcount, dovl,
+                                           nullptr, nullptr, nullptr, nullptr, nullptr);
   SBIO_CUDA_TRY(cudaGetLastError());
-  std::vector<int32_t> cnt(N);
   unsigned long long ovl = 0;
-  SBIO_CUDA_TRY(cudaMemcpyAsync(cnt.data(), dcount, N * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+  SBIO_CUDA_TRY(cudaMemcpyAsync(cnt.data(), dcount, n * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
   SBIO_CUDA_TRY(cudaMemcpyAsync(&ovl, dovl, sizeof(ovl), cudaMemcpyDeviceToHost, st));
   SBIO_CUDA_TRY(cudaStreamSynchronize(st));
-  if (ovl != ~0ull)
-    return set_error(SBIO_EOVERLAP, "node %lld of particle %lld lies inside another spheroid", (long long)ovl,
-                     (long long)(ovl / h.G));
-  // offsets: pairs per node, skip lists (near + own + sentinel) per node
-  std::vector<int64_t> poff(N + 1, 0);
-  std::vector<int32_t> sptr(N + 1, 0);
-  for (int64_t t = 0; t < N; ++t) {
-    poff[t + 1] = poff[t] + cnt[t];
-    if ((int64_t)sptr[t] + cnt[t] + 2 > INT32_MAX) return set_error(SBIO_EINVAL, "skip lists exceed 2^31 entries");
-    sptr[t + 1] = sptr[t] + cnt[t] + 2;
+  if (ovl != ~0ull) {
+    *inside = (int64_t)ovl;
+    return G > 0 ? SBIO_EOVERLAP : SBIO_EINVAL;
   }
-  const int64_t P = poff[N];
+  // offsets: pairs per target; skip lists (near [+ own] + sentinel) per target
+  const int extra = G > 0 ? 2 : 1;
+  std::vector<int64_t> poff(n + 1, 0);
+  std::vector<int32_t> sptr(n + 1, 0);
+  for (int64_t t = 0; t < n; ++t) {
+    poff[t + 1] = poff[t] + cnt[t];
+    if ((int64_t)sptr[t] + cnt[t] + extra > INT32_MAX) return set_error(SBIO_EINVAL, "skip lists exceed 2^31 entries");
+    sptr[t + 1] = sptr[t] + cnt[t] + extra;
+  }
+  const int64_t P = poff[n];
   int64_t* dpoff = nullptr;
-  int32_t *dpt = nullptr, *dps = nullptr;
+  int32_t *dpt = nullptr, *dps = nullptr, *skip_ptr = nullptr, *skip_idx = nullptr;
   if ((rc = tmp((void**)&dpoff, poff.size() * sizeof(int64_t)))) return rc;
   SBIO_CUDA_TRY(cudaMemcpyAsync(dpoff, poff.data(), poff.size() * sizeof(int64_t), cudaMemcpyHostToDevice, st));
-  if ((rc = upload(g, &d.skip_ptr, sptr.data(), sptr.size(), "skip lists"))) return rc;
-  if ((rc = dev_alloc(g, (void**)&d.skip_idx, (size_t)sptr[N] * sizeof(int32_t), "skip lists"))) return rc;
+  if ((rc = alloc_skip(sptr, &skip_ptr, &skip_idx))) return rc;
   if ((rc = tmp((void**)&dpt, (size_t)P * sizeof(int32_t)))) return rc;
   if ((rc = tmp((void**)&dps, (size_t)P * sizeof(int32_t)))) return rc;
-  near_sets_kernel<<<blocks, 128, 0, st>>>(M, h.G, N, d.parts, dsph, d.xyz, h.near_factor, 1, nullptr, nullptr, dpoff,
-                                           dpt, dps, d.skip_ptr, d.skip_idx);
+  near_sets_kernel<<<blocks, 128, 0, st>>>(M, G, n, dparts, dsph, xyz, h.near_factor, inside_tol, 1, nullptr, nullptr,
+                                           dpoff, dpt, dps, skip_ptr, skip_idx);
   SBIO_CUDA_TRY(cudaGetLastError());
   std::vector<int32_t> pt(P), ps(P);
   if (P > 0) {
@@ -384,21 +389,51 @@ static int build_near(sbio_geom* g) {
   for (int64_t k = 0; k < P; ++k) num[ps[k]]++;
   std::vector<int64_t> base(M, 0);
   int64_t acc = 0;
-  h.n_pairs_prolate = 0;
   for (int kind = SBIO_PROLATE; kind <= SBIO_OBLATE; ++kind)
     for (int i = 0; i < M; ++i)
       if (h.parts[i].kind == kind) {
         base[i] = acc;
         acc += num[i];
-        if (kind == SBIO_PROLATE) h.n_pairs_prolate += num[i];
+        if (kind == SBIO_PROLATE) *n_pro += num[i];
       }
-  h.pair_t.assign(P, 0);
-  h.pair_s.assign(P, 0);
+  pair_t.assign(P, 0);
+  pair_s.assign(P, 0);
   for (int64_t k = 0; k < P; ++k) {
     const int64_t dst = base[ps[k]]++;
-    h.pair_t[dst] = pt[k];
-    h.pair_s[dst] = ps[k];
+    pair_t[dst] = pt[k];
+    pair_s[dst] = ps[k];
   }
+  return SBIO_OK;
+}
+
+template <typename T>
+static int upload(sbio_geom* g, T** dst, const T* src, size_t count, const char* what);
+
+// Near pairs (sorted by source kind, source, target), far pair count,
+// source tiles and the device skip lists.
+static int build_near(sbio_geom* g) {
+  GeomHost& h = g->h;
+  DevGeom& d = g->d;
+  const int M = h.M;
+  const int64_t N = h.N;
+  int rc;
+  if (!d.parts && (rc = upload(g, &d.parts, h.parts.data(), M, "particles"))) return rc;
+  if (!d.xyz && (rc = upload(g, &d.xyz, h.xyz.data(), N * 3, "node positions"))) return rc;
+  auto alloc_skip = [&](const std::vector<int32_t>& sptr, int32_t** sp, int32_t** si) -> int {
+    int r = upload(g, &d.skip_ptr, sptr.data(), sptr.size(), "skip lists");
+    if (!r) r = dev_alloc(g, (void**)&d.skip_idx, (size_t)sptr.back() * sizeof(int32_t), "skip lists");
+    *sp = d.skip_ptr;
+    *si = d.skip_idx;
+    return r;
+  };
+  std::vector<int32_t> cnt;
+  int64_t inside = -1;
+  rc = device_near_sets(g, d.xyz, N, h.G, 0.0, g->setup_stream, alloc_skip, h.pair_t, h.pair_s, &h.n_pairs_prolate,
+                        cnt, &inside);
+  if (rc == SBIO_EOVERLAP)
+    return set_error(SBIO_EOVERLAP, "node %lld of particle %lld lies inside another spheroid", (long long)inside,
+                     (long long)(inside / h.G));
+  if (rc) return rc;
   h.far_pairs = 0;
   for (int64_t t = 0; t < N; ++t) h.far_pairs += (int64_t)(M - 1 - cnt[t]) * h.G;
   // far-field source tiles

@@ -4,6 +4,7 @@
 
 #include <atomic>
 #include <cstdarg>
+#include <functional>
 #include <mutex>
 #include <string>
 #include <vector>
@@ -186,6 +187,13 @@ int launch_laplace(sbio_geom* g, const double* sigma, const double* mu, double* 
                    uint32_t parts, cudaStream_t st);
 int launch_synth(sbio_geom* g, const double* sigma, const double* mu, double* S, double* D, bool write_self,
                  cudaStream_t st);
+// Near sets on the device for n targets at device positions xyz: the
+// geometry's nodes (G nodes per particle) or points (G = 0); see sbio_geom.cu.
+int device_near_sets(sbio_geom* g, const double* xyz, int64_t n, int G, double inside_tol, cudaStream_t st,
+                     const std::function<int(const std::vector<int32_t>&, int32_t**, int32_t**)>& alloc_skip,
+                     std::vector<int32_t>& pair_t, std::vector<int32_t>& pair_s, int64_t* n_pro,
+                     std::vector<int32_t>& cnt, int64_t* inside);
+
 // A target set's view of its geometry: the geometry's device tables with the
 // set's points as targets (xyz, tgt32, near pairs, skip lists; nrm null),
 // the point count and the near pairs (the first n_pro on prolate sources).
@@ -202,9 +210,6 @@ int launch_stokes(sbio_geom* g, const double* f, double* u, cudaStream_t st);
 void launch_far_on(const DevGeom& d, const GeomHost& h, int64_t NT, double* S, double* D, cudaStream_t st);
 // host geometry helpers shared by the set-up code
 void split_f32(double v, float& hi, float& lo);
-// distance from a point in the particle's local frame to its surface;
-// *inside set when the level set (rho/A)^2 + (z/C)^2 is below 1 - tol
-double spheroid_distance_local(const PartGeom& P, double x, double y, double z, double tol, bool* inside);
 int launch_stokes_far(sbio_geom* g, double* u, cudaStream_t st);
 int launch_stokes_far_on(const DevGeom& d, const GeomHost& h, int64_t NT, double* u, double* pr, cudaStream_t st);
 int launch_stokes_prep(sbio_geom* g, const double* f, cudaStream_t st);

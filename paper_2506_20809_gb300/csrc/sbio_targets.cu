@@ -1,20 +1,19 @@
 // Particle-to-target evaluation (Sec. 4.1, "Particle-to-target algorithm"):
 // S[sigma] and D[mu] of every spheroid at arbitrary points in the fluid.
 //
-// Creation classifies each (point, spheroid) pair on the host by the exact
-// point-to-surface distance (near iff below near_factor x major semi-axis,
-// the rule used for surface nodes), and uploads the point coordinates (FP64
-// and hi/lo FP32), the near pairs (sorted by source kind, source, point) and
-// the per-point skip lists of near spheroids.  Evaluation reuses the
+// Creation uploads the point coordinates (FP64 and hi/lo FP32) and classifies
+// each (point, spheroid) pair on the device by the exact point-to-surface
+// distance (near iff below near_factor x major semi-axis, the rule used for
+// surface nodes), with the geometry's near-set kernel: the near pairs (sorted
+// by source kind, source, point) and the per-point skip lists of near
+// spheroids.  Evaluation reuses the
 // geometry's kernels through a view of its device tables in which the
 // targets are the points: the synthesis kernel writes the far sources and
 // near coefficients of the given densities (no self output: no point lies on
 // a surface in the sense of the self term), the near kernel evaluates the
 // exterior expansions at the near pairs and the far kernel sums the smooth
 // quadrature over all other spheroids.
-#include <algorithm>
-#include <thread>
-#include <utility>
+#include <cmath>
 #include <vector>
 
 #include "sbio_internal.cuh"
@@ -68,62 +67,6 @@ static void ts_free(sbio_targets* ts) {
   ts->bytes = 0;
 }
 
-// Per-point near spheroids; returns the index of a point inside a spheroid
-// (or -1) through `inside_point`.
-static void classify(const GeomHost& h, const double* xyz, int64_t T, std::vector<std::pair<int32_t, int32_t>>& pairs,
-                     int64_t* inside_point, int* inside_part) {
-  const int M = h.M;
-  std::vector<double> rmax(M), thr(M);
-  for (int i = 0; i < M; ++i) {
-    rmax[i] = std::max(h.parts[i].A, h.parts[i].C);
-    thr[i] = h.near_factor * rmax[i];
-  }
-  const unsigned nth = std::max(1u, std::min(32u, std::thread::hardware_concurrency()));
-  std::vector<std::vector<std::pair<int32_t, int32_t>>> local(nth);
-  std::vector<int64_t> bad_t(nth, -1);
-  std::vector<int> bad_i(nth, -1);
-  auto work = [&](unsigned tid) {
-    for (int64_t t = tid; t < T; t += nth) {
-      const double* x = xyz + t * 3;
-      for (int i = 0; i < M; ++i) {
-        const PartGeom& P = h.parts[i];
-        const double d0 = x[0] - P.c[0], d1 = x[1] - P.c[1], d2 = x[2] - P.c[2];
-        const double dc = std::sqrt(d0 * d0 + d1 * d1 + d2 * d2);
-        if (dc - rmax[i] >= thr[i]) continue;
-        const double xl = P.R[0] * d0 + P.R[3] * d1 + P.R[6] * d2;
-        const double yl = P.R[1] * d0 + P.R[4] * d1 + P.R[7] * d2;
-        const double zl = P.R[2] * d0 + P.R[5] * d1 + P.R[8] * d2;
-        bool inside = false;
-        const double d = spheroid_distance_local(P, xl, yl, zl, 1e-11, &inside);
-        if (inside) {
-          bad_t[tid] = t;
-          bad_i[tid] = i;
-          return;
-        }
-        if (d < thr[i]) local[tid].push_back({(int32_t)t, (int32_t)i});
-      }
-    }
-  };
-  std::vector<std::thread> th;
-  for (unsigned k = 0; k < nth; ++k) th.emplace_back(work, k);
-  for (auto& t : th) t.join();
-  *inside_point = -1;
-  for (unsigned k = 0; k < nth; ++k)
-    if (bad_t[k] >= 0) {
-      *inside_point = bad_t[k];
-      *inside_part = bad_i[k];
-      return;
-    }
-  pairs.clear();
-  for (auto& v : local) pairs.insert(pairs.end(), v.begin(), v.end());
-  std::sort(pairs.begin(), pairs.end(), [&](const std::pair<int32_t, int32_t>& a, const std::pair<int32_t, int32_t>& b) {
-    const int ka = h.parts[a.second].kind, kb = h.parts[b.second].kind;
-    if (ka != kb) return ka < kb;
-    if (a.second != b.second) return a.second < b.second;
-    return a.first < b.first;
-  });
-}
-
 int targets_view(sbio_targets* ts, sbio_geom** g, const DevGeom** view, int64_t* T, int64_t* n_pro,
                  int64_t* n_pairs) {
   if (!ts) return set_error(SBIO_EINVAL, "null target set");
@@ -151,32 +94,10 @@ int sbio_targets_create(sbio_geom* g, const double* xyz_host, int64_t T, void* s
   SBIO_CUDA_TRY(cudaSetDevice(g->ctx->device));
   cudaStream_t st = (cudaStream_t)stream;
   const GeomHost& h = g->h;
-  std::vector<std::pair<int32_t, int32_t>> pairs;
-  int64_t bad = -1;
-  int bad_i = -1;
-  classify(h, xyz_host, T, pairs, &bad, &bad_i);
-  if (bad >= 0) return set_error(SBIO_EINVAL, "point %lld lies inside spheroid %d", (long long)bad, bad_i);
   sbio_targets* ts = new sbio_targets();
   ts->g = g;
   ts->T = T;
   ts->view = g->d;
-  std::vector<int32_t> pt(pairs.size()), ps(pairs.size());
-  std::vector<std::vector<int32_t>> skip(T);
-  for (size_t k = 0; k < pairs.size(); ++k) {
-    pt[k] = pairs[k].first;
-    ps[k] = pairs[k].second;
-    if (h.parts[ps[k]].kind == SBIO_PROLATE) ts->n_pro++;
-    skip[pt[k]].push_back(ps[k]);
-  }
-  ts->n_pairs = (int64_t)pairs.size();
-  ts->far_pairs = (T * (int64_t)h.M - ts->n_pairs) * h.G;
-  std::vector<int32_t> sptr(T + 1, 0), sidx;
-  for (int64_t t = 0; t < T; ++t) {
-    std::sort(skip[t].begin(), skip[t].end());
-    skip[t].push_back(INT32_MAX);   // sentinel
-    sptr[t + 1] = sptr[t] + (int32_t)skip[t].size();
-    sidx.insert(sidx.end(), skip[t].begin(), skip[t].end());
-  }
   std::vector<float4> tgt(T * 2);
   for (int64_t t = 0; t < T; ++t) {
     float hi[3], lo[3];
@@ -188,10 +109,26 @@ int sbio_targets_create(sbio_geom* g, const double* xyz_host, int64_t T, void* s
   int rc = SBIO_OK;
   if (!rc) rc = ts_upload(ts, &v.xyz, xyz_host, (size_t)T * 3, "target points", st);
   if (!rc) rc = ts_upload(ts, &v.tgt32, tgt.data(), tgt.size(), "target points (fp32)", st);
+  // near pairs and skip lists on the device; a point inside a spheroid (the
+  // ellipsoid form below 1 - 1e-11, so that points on a surface are outside)
+  // is refused
+  std::vector<int32_t> pt, ps, cnt;
+  int64_t inside = -1;
+  if (!rc) {
+    auto alloc_skip = [&](const std::vector<int32_t>& sptr, int32_t** sp, int32_t** si) -> int {
+      int r = ts_upload(ts, &v.skip_ptr, sptr.data(), sptr.size(), "target skip lists", st);
+      if (!r) r = ts_alloc(ts, (void**)&v.skip_idx, (size_t)sptr.back() * sizeof(int32_t), "target skip lists");
+      *sp = v.skip_ptr;
+      *si = v.skip_idx;
+      return r;
+    };
+    rc = device_near_sets(g, v.xyz, T, 0, 1e-11, st, alloc_skip, pt, ps, &ts->n_pro, cnt, &inside);
+    if (rc == SBIO_EINVAL && inside >= 0) rc = set_error(SBIO_EINVAL, "point %lld lies inside a spheroid", (long long)inside);
+  }
+  ts->n_pairs = (int64_t)pt.size();
+  ts->far_pairs = (T * (int64_t)h.M - ts->n_pairs) * h.G;
   if (!rc) rc = ts_upload(ts, &v.pair_t, pt.data(), pt.size(), "target near pairs", st);
   if (!rc) rc = ts_upload(ts, &v.pair_s, ps.data(), ps.size(), "target near pairs", st);
-  if (!rc) rc = ts_upload(ts, &v.skip_ptr, sptr.data(), sptr.size(), "target skip lists", st);
-  if (!rc) rc = ts_upload(ts, &v.skip_idx, sidx.data(), sidx.size(), "target skip lists", st);
   if (!rc && cudaStreamSynchronize(st) != cudaSuccess) rc = set_error(SBIO_ECUDA, "target upload failed");
   if (rc) {
     ts_free(ts);
