@@ -225,8 +225,10 @@ int build_host(GeomHost& h, const sbio_spheroid* sph, int32_t M, const sbio_opti
 // Count pass: near particles per target and the smallest target lying inside
 // a spheroid.  Fill pass: the target's near pairs at its offset (ascending
 // source) and its far skip list (own and near particles ascending, then a
-// sentinel) at its CSR offset.
+// sentinel) at its CSR offset.  `order` (may be null) maps thread k to target
+// order[k]: spatially sorted points keep a warp's candidate particles alike.
 __global__ void __launch_bounds__(128) near_sets_kernel(int M, int G, int64_t N, const PartGeom* __restrict__ parts,
+                                                        const int32_t* __restrict__ order,
                                                         const float4* __restrict__ sph,
                                                         const double* __restrict__ xyz, double near_factor,
                                                         double inside_tol, int fill, int32_t* __restrict__ count,
@@ -235,8 +237,9 @@ __global__ void __launch_bounds__(128) near_sets_kernel(int M, int G, int64_t N,
                                                         int32_t* __restrict__ pair_t, int32_t* __restrict__ pair_s,
                                                         const int32_t* __restrict__ skip_ptr,
                                                         int32_t* __restrict__ skip_idx) {
-  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= N) return;
+  const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= N) return;
+  const int64_t t = order ? (int64_t)order[k] : k;
   const int own = G > 0 ? (int)(t / G) : -1;
   const double x0 = xyz[t * 3 + 0], x1 = xyz[t * 3 + 1], x2 = xyz[t * 3 + 2];
   const float y0 = (float)x0, y1 = (float)x1, y2 = (float)x2;
@@ -288,13 +291,15 @@ __global__ void __launch_bounds__(128) near_sets_kernel(int M, int G, int64_t N,
 }
 
 // Near sets of n targets (device positions xyz, G nodes per particle or 0 for
-// points) on `st`: runs the count pass, returns SBIO_EOVERLAP (nodes) or
+// points; order_host: optional processing order of the targets) on `st`:
+// runs the count pass, returns SBIO_EOVERLAP (nodes) or
 // SBIO_EINVAL (points) with *inside the smallest target inside a spheroid,
 // allocates the skip lists through alloc_skip (CSR offsets of n + 1 entries
 // and the lists), runs the fill pass, and returns the pairs sorted by
 // (source kind, source, target) with the number on prolate sources and the
 // near count per target.  Synchronises `st`.
-int device_near_sets(sbio_geom* g, const double* xyz, int64_t n, int G, double inside_tol, cudaStream_t st,
+int device_near_sets(sbio_geom* g, const double* xyz, int64_t n, int G, double inside_tol,
+                     const std::vector<int32_t>* order_host, cudaStream_t st,
                      const std::function<int(const std::vector<int32_t>&, int32_t**, int32_t**)>& alloc_skip,
                      std::vector<int32_t>& pair_t, std::vector<int32_t>& pair_s, int64_t* n_pro,
                      std::vector<int32_t>& cnt, int64_t* inside) {
@@ -345,10 +350,16 @@ int device_near_sets(sbio_geom* g, const double* xyz, int64_t n, int G, double i
   float4* dsph = nullptr;
   if ((rc = tmp((void**)&dsph, (size_t)M * sizeof(float4)))) return rc;
   SBIO_CUDA_TRY(cudaMemcpyAsync(dsph, sph_h.data(), (size_t)M * sizeof(float4), cudaMemcpyHostToDevice, st));
+  int32_t* dorder = nullptr;
+  if (order_host) {
+    if ((int64_t)order_host->size() != n) return set_error(SBIO_EINVAL, "near-set order of wrong length");
+    if ((rc = tmp((void**)&dorder, (size_t)n * sizeof(int32_t)))) return rc;
+    SBIO_CUDA_TRY(cudaMemcpyAsync(dorder, order_host->data(), (size_t)n * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+  }
   const unsigned blocks = (unsigned)((n + 127) / 128);
   const PartGeom* dparts = g->d.parts;
-  near_sets_kernel<<<blocks, 128, 0, st>>>(M, G, n, dparts, dsph, xyz, h.near_factor, inside_tol, 0, dcount, dovl,
-                                           nullptr, nullptr, nullptr, nullptr, nullptr);
+  near_sets_kernel<<<blocks, 128, 0, st>>>(M, G, n, dparts, dorder, dsph, xyz, h.near_factor, inside_tol, 0, dcount,
+                                           dovl, nullptr, nullptr, nullptr, nullptr, nullptr);
   SBIO_CUDA_TRY(cudaGetLastError());
   unsigned long long ovl = 0;
   SBIO_CUDA_TRY(cudaMemcpyAsync(cnt.data(), dcount, n * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
@@ -375,8 +386,8 @@ int device_near_sets(sbio_geom* g, const double* xyz, int64_t n, int G, double i
   if ((rc = alloc_skip(sptr, &skip_ptr, &skip_idx))) return rc;
   if ((rc = tmp((void**)&dpt, (size_t)P * sizeof(int32_t)))) return rc;
   if ((rc = tmp((void**)&dps, (size_t)P * sizeof(int32_t)))) return rc;
-  near_sets_kernel<<<blocks, 128, 0, st>>>(M, G, n, dparts, dsph, xyz, h.near_factor, inside_tol, 1, nullptr, nullptr,
-                                           dpoff, dpt, dps, skip_ptr, skip_idx);
+  near_sets_kernel<<<blocks, 128, 0, st>>>(M, G, n, dparts, dorder, dsph, xyz, h.near_factor, inside_tol, 1, nullptr,
+                                           nullptr, dpoff, dpt, dps, skip_ptr, skip_idx);
   SBIO_CUDA_TRY(cudaGetLastError());
   std::vector<int32_t> pt(P), ps(P);
   if (P > 0) {
@@ -428,8 +439,9 @@ static int build_near(sbio_geom* g) {
   };
   std::vector<int32_t> cnt;
   int64_t inside = -1;
-  rc = device_near_sets(g, d.xyz, N, h.G, 0.0, g->setup_stream, alloc_skip, h.pair_t, h.pair_s, &h.n_pairs_prolate,
-                        cnt, &inside);
+  // nodes in their natural order (particle-major) are already spatially coherent
+  rc = device_near_sets(g, d.xyz, N, h.G, 0.0, nullptr, g->setup_stream, alloc_skip, h.pair_t, h.pair_s,
+                        &h.n_pairs_prolate, cnt, &inside);
   if (rc == SBIO_EOVERLAP)
     return set_error(SBIO_EOVERLAP, "node %lld of particle %lld lies inside another spheroid", (long long)inside,
                      (long long)(inside / h.G));

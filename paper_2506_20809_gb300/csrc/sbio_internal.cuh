@@ -189,7 +189,8 @@ int launch_synth(sbio_geom* g, const double* sigma, const double* mu, double* S,
                  cudaStream_t st);
 // Near sets on the device for n targets at device positions xyz: the
 // geometry's nodes (G nodes per particle) or points (G = 0); see sbio_geom.cu.
-int device_near_sets(sbio_geom* g, const double* xyz, int64_t n, int G, double inside_tol, cudaStream_t st,
+int device_near_sets(sbio_geom* g, const double* xyz, int64_t n, int G, double inside_tol,
+                     const std::vector<int32_t>* order_host, cudaStream_t st,
                      const std::function<int(const std::vector<int32_t>&, int32_t**, int32_t**)>& alloc_skip,
                      std::vector<int32_t>& pair_t, std::vector<int32_t>& pair_s, int64_t* n_pro,
                      std::vector<int32_t>& cnt, int64_t* inside);

@@ -13,6 +13,7 @@
 // a surface in the sense of the self term), the near kernel evaluates the
 // exterior expansions at the near pairs and the far kernel sums the smooth
 // quadrature over all other spheroids.
+#include <algorithm>
 #include <cmath>
 #include <vector>
 
@@ -65,6 +66,32 @@ static void ts_free(sbio_targets* ts) {
   if (ts->g) ts->g->ctx->used.fetch_sub(ts->bytes);
   ts->allocs.clear();
   ts->bytes = 0;
+}
+
+// Processing order of the points for the near-set kernel: a counting sort by
+// cell of a 32 x 32 x 32 grid over the points' bounding box, so that the
+// threads of a warp hold nearby points (alike candidate spheroids).
+static void spatial_order(const double* xyz, int64_t T, std::vector<int32_t>& order) {
+  constexpr int kCells = 32;
+  double lo[3] = {xyz[0], xyz[1], xyz[2]}, hi[3] = {xyz[0], xyz[1], xyz[2]};
+  for (int64_t t = 1; t < T; ++t)
+    for (int c = 0; c < 3; ++c) {
+      lo[c] = std::min(lo[c], xyz[t * 3 + c]);
+      hi[c] = std::max(hi[c], xyz[t * 3 + c]);
+    }
+  double sc[3];
+  for (int c = 0; c < 3; ++c) sc[c] = hi[c] > lo[c] ? (kCells - 1e-9) / (hi[c] - lo[c]) : 0.0;
+  std::vector<int32_t> cell(T);
+  std::vector<int64_t> start(kCells * kCells * kCells + 1, 0);
+  for (int64_t t = 0; t < T; ++t) {
+    int q[3];
+    for (int c = 0; c < 3; ++c) q[c] = std::min(kCells - 1, std::max(0, (int)((xyz[t * 3 + c] - lo[c]) * sc[c])));
+    cell[t] = (q[2] * kCells + q[1]) * kCells + q[0];
+    start[cell[t] + 1]++;
+  }
+  for (size_t k = 1; k < start.size(); ++k) start[k] += start[k - 1];
+  order.assign(T, 0);
+  for (int64_t t = 0; t < T; ++t) order[start[cell[t]]++] = (int32_t)t;
 }
 
 int targets_view(sbio_targets* ts, sbio_geom** g, const DevGeom** view, int64_t* T, int64_t* n_pro,
@@ -122,7 +149,10 @@ int sbio_targets_create(sbio_geom* g, const double* xyz_host, int64_t T, void* s
       *si = v.skip_idx;
       return r;
     };
-    rc = device_near_sets(g, v.xyz, T, 0, 1e-11, st, alloc_skip, pt, ps, &ts->n_pro, cnt, &inside);
+    std::vector<int32_t> order;
+    if (T > 0) spatial_order(xyz_host, T, order);
+    rc = device_near_sets(g, v.xyz, T, 0, 1e-11, T > 0 ? &order : nullptr, st, alloc_skip, pt, ps, &ts->n_pro, cnt,
+                          &inside);
     if (rc == SBIO_EINVAL && inside >= 0) rc = set_error(SBIO_EINVAL, "point %lld lies inside a spheroid", (long long)inside);
   }
   ts->n_pairs = (int64_t)pt.size();
