@@ -269,8 +269,14 @@ __global__ void __launch_bounds__(128) near_sets_kernel(int M, int G, int64_t N,
       if (!fill) atomicMin(overlap_min, (unsigned long long)t);
       continue;
     }
-    const double dist = (P.C >= P.A) ? ellipse_distance_hd(P.C, P.A, az, rho) : ellipse_distance_hd(P.A, P.C, rho, az);
-    if (!(dist < thr)) continue;
+    // the spheroid holds the ball of radius min(A, C), so an outside point is
+    // at most dc - min(A, C) from it: below the threshold (with a relative
+    // margin of 1e-12) the pair is near without the exact distance
+    if (!(dc - fmin(P.A, P.C) < thr * (1.0 - 1e-12))) {
+      const double dist =
+          (P.C >= P.A) ? ellipse_distance_hd(P.C, P.A, az, rho) : ellipse_distance_hd(P.A, P.C, rho, az);
+      if (!(dist < thr)) continue;
+    }
     if (fill) {
       pair_t[po + c] = (int32_t)t;
       pair_s[po + c] = i;
