@@ -38,6 +38,8 @@ FAR_FLOP_PER_PAIR = {"SD": 19, "S": 10, "D": 14}
 # capture per launch shape (targets per thread, source splits) of the current
 # kernel code; other shapes report null
 FAR_DRAM_BYTES_POLY200 = {(-8, 44): 11.57e6}
+# the same for the mixed S' + D' far kernel (packed, expanded distance)
+DERIV_FAR_DRAM_BYTES_POLY200 = {(-8, 44): 14.35e6}
 
 
 def near_flop_per_pair(p: int) -> int:
@@ -740,7 +742,7 @@ def run_deriv200(args, ws, rank, lrank):
     c = I.config_coefficients(susp, 0)
     ctx = S.sbio_ctx_create(lrank, 0)
     g = S.Geometry(ctx, susp, precision=S.SBIO_MIXED)
-    S.sbio_geom_autotune(g.h)                   # near CTA cap for the overlapped near field
+    dtune = S.sbio_geom_autotune(g.h)           # far shape and near CTA cap for the overlapped near field
     sg, mg = torch.from_numpy(c[0]).cuda(), torch.from_numpy(c[1]).cuda()
     Sp = torch.empty(g.N, dtype=torch.float64, device="cuda")
     Dp = torch.empty_like(Sp)
@@ -782,7 +784,9 @@ def run_deriv200(args, ws, rank, lrank):
                          "far": far_ms},
             "roofline": {"kernel": "far_deriv_mixed_kernel", "bound": "alu", "achieved": ach,
                          "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": ach / FP32_PEAK_TFLOPS,
-                         "flop_per_pair": DERIV_FAR_FLOP_PER_PAIR, "traffic": None},
+                         "flop_per_pair": DERIV_FAR_FLOP_PER_PAIR,
+                         "traffic": DERIV_FAR_DRAM_BYTES_POLY200.get((dtune[0], dtune[1])),
+                         "traffic_unit": "bytes per launch (ncu dram read + write, one capture at this launch shape)"},
             "fp64_gpu_applies_per_s": 1e3 / t64, "rel_err_vs_fp64_gpu": err, "gpu_launches": int(launches),
             "clocks": clk}
     g.close()
