@@ -135,6 +135,12 @@ __device__ __forceinline__ void solid_grad(double xl, double yl, double zl, doub
 // with Fp the phi-derivative sum (d/dphi of cos m phi -> -m sin m phi).
 // The m = 0 terms n >= 1 are issued inside the order-1 sweep, which supplies
 // their v-derivative sqrt(1-v^2) dP_n/dv = Pbar_n^1.
+// Threads per CTA of the near-gradient kernels.  They hold about 250
+// registers per thread at the larger orders; 64-thread CTAs take an eighth of
+// the register file each, so that capped near CTAs share an SM with the far
+// kernel's CTAs instead of filling it.
+constexpr int kNearGradBlock = 64;
+
 struct GradFrame {
   double k_ru, k_rv, k_zu, k_zv, k_p, c1, s1;
 };

@@ -635,10 +635,10 @@ int tune_launch_shape(sbio_geom* g, const TuneOps& ops, double* out, cudaStream_
   *ops.splits = best_sp;
   // near CTAs per SM while the near field overlaps the far field: whole applies
   if (!rc && ops.whole && g->overlap && g->near_stream && !g->timing && !h.pair_t.empty()) {
-    const int caps[4] = {1, 2, 4, 0};
+    const int caps[5] = {1, 2, 4, 8, 0};
     float best_apply = 1e30f;
     int best_cap = *ops.cap;
-    for (int c = 0; c < 4 && !rc; ++c) {
+    for (int c = 0; c < 5 && !rc; ++c) {
       *ops.cap = caps[c];
       float m = 0.f;
       rc = time3(ops.whole, &m);

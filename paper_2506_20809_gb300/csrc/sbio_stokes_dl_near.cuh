@@ -68,7 +68,7 @@ struct SdlNearVisitor {
 };
 
 template <int P1, int KIND>
-__global__ void __launch_bounds__(128) stokes_dl_near_kernel(const int32_t* __restrict__ pair_t,
+__global__ void __launch_bounds__(kNearGradBlock) stokes_dl_near_kernel(const int32_t* __restrict__ pair_t,
                                                              const int32_t* __restrict__ pair_s, int64_t first,
                                                              int64_t count, const PartGeom* __restrict__ parts,
                                                              const double* __restrict__ xyz,
@@ -106,9 +106,9 @@ template <int P1, int KIND>
 static void launch_stokes_dl_near_pk(const DevGeom& d, const int32_t* pt, const int32_t* ps, int64_t first,
                                      int64_t count, double* u, cudaStream_t st) {
   if (count <= 0) return;
-  int64_t nb = (count + 127) / 128;
+  int64_t nb = (count + kNearGradBlock - 1) / kNearGradBlock;
   if (d.near_grid_cap > 0 && nb > d.near_grid_cap) nb = d.near_grid_cap;
-  stokes_dl_near_kernel<P1, KIND><<<(unsigned)nb, 128, 0, st>>>(pt, ps, first, count, d.parts, d.xyz, d.sdl_coef,
+  stokes_dl_near_kernel<P1, KIND><<<(unsigned)nb, kNearGradBlock, 0, st>>>(pt, ps, first, count, d.parts, d.xyz, d.sdl_coef,
                                                                 d.inv, u);
   count_launch();
 }

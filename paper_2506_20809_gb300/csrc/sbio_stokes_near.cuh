@@ -86,7 +86,7 @@ __device__ __forceinline__ void stokes_pair(double xl, double yl, double zl, dou
 }
 
 template <int P1, int KIND>
-__global__ void __launch_bounds__(128) stokes_near_kernel(const int32_t* __restrict__ pair_t,
+__global__ void __launch_bounds__(kNearGradBlock) stokes_near_kernel(const int32_t* __restrict__ pair_t,
                                                           const int32_t* __restrict__ pair_s, int64_t first,
                                                           int64_t count, const PartGeom* __restrict__ parts,
                                                           const double* __restrict__ xyz,
@@ -118,10 +118,10 @@ template <int P1, int KIND>
 static void launch_stokes_near_pk(const DevGeom& d, int64_t first, int64_t count, const double* inv, double* u,
                                   cudaStream_t st) {
   if (count <= 0) return;
-  int64_t nb = (count + 127) / 128;
+  int64_t nb = (count + kNearGradBlock - 1) / kNearGradBlock;
   if (d.near_grid_cap > 0 && nb > d.near_grid_cap) nb = d.near_grid_cap;
   const unsigned blocks = (unsigned)nb;
-  stokes_near_kernel<P1, KIND><<<blocks, 128, 0, st>>>(d.pair_t, d.pair_s, first, count, d.parts, d.xyz,
+  stokes_near_kernel<P1, KIND><<<blocks, kNearGradBlock, 0, st>>>(d.pair_t, d.pair_s, first, count, d.parts, d.xyz,
                                                         d.st_coef, inv, u);
   count_launch();
 }
