@@ -215,6 +215,15 @@ int sbio_apply_laplace(sbio_geom* g, const double* sigma_tilde, const double* mu
 int sbio_apply_laplace_parts(sbio_geom* g, const double* sigma_tilde, const double* mu_hat,
                              double* S_out, double* D_out, uint32_t parts, void* stream);
 
+/* One-sided surface limits (Sec. 2.4, jump conditions): as sbio_apply_laplace
+ * with, on every node's own surface, side = +1 the exterior limit
+ * D+ = D + mu/2 or side = -1 the interior limit D- = D - mu/2 (mu the
+ * density value at the node; side = 0 the principal value, as
+ * sbio_apply_laplace).  S is continuous and is the same for every side.
+ * SBIO_EINVAL for side outside {-1, 0, 1}.  Asynchronous. */
+int sbio_apply_laplace_limit(sbio_geom* g, const double* sigma_tilde, const double* mu_hat, double* S_out,
+                             double* D_out, int32_t side, void* stream);
+
 /* End-to-end apply from and to HOST memory: copies the coefficients to
  * library-owned device buffers on `stream`, applies, copies the results back
  * and synchronises `stream` before returning.  Host buffers may be pageable or
@@ -244,6 +253,15 @@ int sbio_apply_stokes_sl(sbio_geom* g, const double* f_tilde, double* u_out, voi
  * is); outputs overwritten.  SBIO_ENOTSUP for p > 20.  Asynchronous. */
 int sbio_apply_laplace_deriv(sbio_geom* g, const double* sigma_tilde, const double* mu_hat, double* Sp_out,
                              double* Dp_out, void* stream);
+
+/* One-sided limits of the normal derivatives: as sbio_apply_laplace_deriv
+ * with side = +1 the exterior limit S'+ = S' - sigma/2 or side = -1 the
+ * interior limit S'- = S' + sigma/2 on every node's own surface (sigma the
+ * density value at the node; side = 0 the principal value).  D' is
+ * continuous and is the same for every side.  SBIO_EINVAL for side outside
+ * {-1, 0, 1}.  Asynchronous. */
+int sbio_apply_laplace_deriv_limit(sbio_geom* g, const double* sigma_tilde, const double* mu_hat, double* Sp_out,
+                                   double* Dp_out, int32_t side, void* stream);
 
 /* Stokes double layer (viscosity 1) at all N nodes, principal value:
  *   D_stk[q](x)_i = 3/(4 pi) int (r.q)(r.nu) r_i / |r|^5 dS, r = x - y,

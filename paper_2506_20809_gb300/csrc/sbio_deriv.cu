@@ -368,7 +368,7 @@ deriv_near_launcher deriv_near_for_p(int p) {
 }  // namespace
 
 int launch_laplace_deriv(sbio_geom* g, const double* sigma, const double* mu, double* Sp, double* Dp,
-                         cudaStream_t st) {
+                         cudaStream_t st, int side) {
   const GeomHost& h = g->h;
   if (h.p > 20) return set_error(SBIO_ENOTSUP, "S' / D' are built for p <= 20 (p = %d)", h.p);
   deriv_near_launcher nl = deriv_near_for_p(h.p);
@@ -376,7 +376,7 @@ int launch_laplace_deriv(sbio_geom* g, const double* sigma, const double* mu, do
   phase_mark(g, 0, st);
   // self: writes (initialises) the outputs, and the far sources and near
   // coefficients of this apply
-  int rc = launch_synth_mode(g, sigma, mu, Sp, Dp, 2, st);
+  int rc = launch_synth_mode(g, sigma, mu, Sp, Dp, 2, st, side);
   if (rc) return rc;
   phase_mark(g, 1, st);
   const bool fork = g->overlap && !g->timing && g->near_stream && !h.pair_t.empty();
@@ -415,6 +415,18 @@ int sbio_apply_laplace_deriv(sbio_geom* g, const double* sigma_tilde, const doub
   if (!sigma_tilde && !mu_hat) return set_error(SBIO_EINVAL, "nothing to apply");
   SBIO_CUDA_TRY(cudaSetDevice(g->ctx->device));
   return launch_laplace_deriv(g, sigma_tilde, mu_hat, Sp_out, Dp_out, (cudaStream_t)stream);
+}
+
+int sbio_apply_laplace_deriv_limit(sbio_geom* g, const double* sigma_tilde, const double* mu_hat, double* Sp_out,
+                                   double* Dp_out, int32_t side, void* stream) {
+  clear_error();
+  if (!g) return set_error(SBIO_EINVAL, "null geometry");
+  if (side < -1 || side > 1) return set_error(SBIO_EINVAL, "side %d: -1 (interior), 0 or +1 (exterior)", side);
+  if ((sigma_tilde == nullptr) != (Sp_out == nullptr) || (mu_hat == nullptr) != (Dp_out == nullptr))
+    return set_error(SBIO_EINVAL, "each output must be given exactly when its input is");
+  if (!sigma_tilde && !mu_hat) return set_error(SBIO_EINVAL, "nothing to apply");
+  SBIO_CUDA_TRY(cudaSetDevice(g->ctx->device));
+  return launch_laplace_deriv(g, sigma_tilde, mu_hat, Sp_out, Dp_out, (cudaStream_t)stream, side);
 }
 
 int sbio_eval_targets_deriv(sbio_targets* ts, const double* dirs, const double* sigma_tilde, const double* mu_hat,

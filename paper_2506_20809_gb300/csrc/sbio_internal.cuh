@@ -183,8 +183,10 @@ inline void phase_mark(sbio_geom* g, int k, cudaStream_t st) {
 }
 
 // kernel entry points (defined in the kernel translation units)
+// side (on the own surface): 0 the principal value of D, +1 / -1 the exterior
+// / interior limit D +- mu/2 (for S' in derivative mode: S' -+ sigma/2)
 int launch_laplace(sbio_geom* g, const double* sigma, const double* mu, double* S, double* D,
-                   uint32_t parts, cudaStream_t st);
+                   uint32_t parts, cudaStream_t st, int side = 0);
 int launch_synth(sbio_geom* g, const double* sigma, const double* mu, double* S, double* D, bool write_self,
                  cudaStream_t st);
 // Near sets on the device for n targets at device positions xyz: the
@@ -202,7 +204,7 @@ int targets_view(sbio_targets* ts, sbio_geom** g, const DevGeom** view, int64_t*
                  int64_t* n_pairs);
 
 int launch_synth_mode(sbio_geom* g, const double* sigma, const double* mu, double* S, double* D, int self_mode,
-                      cudaStream_t st);
+                      cudaStream_t st, int side = 0);
 int launch_near(sbio_geom* g, double* S, double* D, cudaStream_t st);
 int launch_stokes(sbio_geom* g, const double* f, double* u, cudaStream_t st);
 // far field of the geometry's sources at the NT targets of `d` (d.xyz,
@@ -215,7 +217,7 @@ int launch_stokes_far(sbio_geom* g, double* u, cudaStream_t st);
 int launch_stokes_far_on(const DevGeom& d, const GeomHost& h, int64_t NT, double* u, double* pr, cudaStream_t st);
 int launch_stokes_prep(sbio_geom* g, const double* f, cudaStream_t st);
 int launch_laplace_deriv(sbio_geom* g, const double* sigma, const double* mu, double* Sp, double* Dp,
-                         cudaStream_t st);
+                         cudaStream_t st, int side = 0);
 
 // Launch-shape search shared by the Laplace and Stokes autotuners: times
 // far(g, out, st) for every targets-per-thread form and a ladder of source

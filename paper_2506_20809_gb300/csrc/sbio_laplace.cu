@@ -30,14 +30,16 @@ struct alignas(32) dbl4 {
 // One CTA, one particle i.  `sm` holds 2 (p+1)^2 + 4 (p+1)(2p+1) doubles.
 // write_self: 0 = no self output (zeros written where outputs are given),
 // 1 = the on-surface S and D, 2 = normal derivatives S' and D' (with the
-// derivative multiplier table passed as `mult`).
+// derivative multiplier table passed as `mult`).  side: 0 = principal value;
+// +1 / -1 = exterior / interior limit, i.e. D +- mu/2 (mode 1) and
+// S' -+ sigma/2 (mode 2) from the density values at the node.
 __device__ __forceinline__ void synth_particle(int i, double* sm, int p, int n_v, int n_phi,
                                                const PartGeom* __restrict__ parts, const double* __restrict__ xyz,
                                                const double* __restrict__ nrm, const double* __restrict__ w,
                                                const double* __restrict__ ptab, const double* __restrict__ trig,
                                                const double* __restrict__ sqrtw, const double* __restrict__ mult,
                                                const double* __restrict__ normc, const double* __restrict__ sigma,
-                                               const double* __restrict__ mu, int write_self,
+                                               const double* __restrict__ mu, int write_self, int side,
                                                double* __restrict__ S_out, double* __restrict__ D_out,
                                                double* __restrict__ src64, float4* __restrict__ src32,
                                                double* __restrict__ alpha, double* __restrict__ beta) {
@@ -112,8 +114,11 @@ __device__ __forceinline__ void synth_particle(int i, double* sm, int p, int n_v
     // Theorem 3 and its D' counterpart, in d/du), scaled by 1/h_u =
     // sqrt(u0^2 + sgn) / (a sqrt(u0^2 + sgn v^2)) on the surface (Table 2)
     const double sc = (write_self == 2) ? (P.A / P.a) / (P.a * sqrtw[(size_t)i * n_v + j]) : 1.0;
-    if (S_out) S_out[t] = write_self ? vS * sc : 0.0;
-    if (D_out) D_out[t] = write_self ? vD * sc : 0.0;
+    // one-sided limits: the jump of D is mu, that of S' is -sigma
+    const double jS = (write_self == 2) ? -0.5 * side * sig_val : 0.0;
+    const double jD = (write_self == 1) ? 0.5 * side * vm : 0.0;
+    if (S_out) S_out[t] = write_self ? fma(vS, sc, jS) : 0.0;
+    if (D_out) D_out[t] = write_self ? fma(vD, sc, jD) : 0.0;
   }
 }
 
@@ -125,13 +130,13 @@ __global__ void __launch_bounds__(256) synth_kernel(int p, int n_v, int n_phi, c
                                                     const double* __restrict__ mult,
                                                     const double* __restrict__ normc,
                                                     const double* __restrict__ sigma, const double* __restrict__ mu,
-                                                    int write_self, double* __restrict__ S_out,
+                                                    int write_self, int side, double* __restrict__ S_out,
                                                     double* __restrict__ D_out, double* __restrict__ src64,
                                                     float4* __restrict__ src32, double* __restrict__ alpha,
                                                     double* __restrict__ beta) {
   extern __shared__ double sm[];
   synth_particle(blockIdx.x, sm, p, n_v, n_phi, parts, xyz, nrm, w, ptab, trig, sqrtw, mult, normc, sigma, mu,
-                 write_self, S_out, D_out, src64, src32, alpha, beta);
+                 write_self, side, S_out, D_out, src64, src32, alpha, beta);
 }
 
 // ---------------------------------------------------------------------------
@@ -521,7 +526,7 @@ int launch_far_persistent(const FarDesc* descs, const int4* items, int n_items, 
 }
 
 int launch_synth_mode(sbio_geom* g, const double* sigma, const double* mu, double* S, double* D, int self_mode,
-                      cudaStream_t st) {
+                      cudaStream_t st, int side) {
   const GeomHost& h = g->h;
   const DevGeom& d = g->d;
   const double* mult = self_mode == 2 ? d.dmult : d.mult;
@@ -531,8 +536,8 @@ int launch_synth_mode(sbio_geom* g, const double* sigma, const double* mu, doubl
     SBIO_CUDA_TRY(cudaFuncSetAttribute(synth_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   }
   synth_kernel<<<h.M, 256, smem, st>>>(h.p, h.n_v, h.n_phi, d.parts, d.xyz, d.nrm, d.w, d.ptab, d.trig, d.sqrtw,
-                                       mult, d.normc, sigma, mu, self_mode, S, D, d.src64, d.src32, d.alpha,
-                                       d.beta);
+                                       mult, d.normc, sigma, mu, self_mode, side, S, D, d.src64, d.src32,
+                                       d.alpha, d.beta);
   count_launch();
   SBIO_CUDA_TRY(cudaGetLastError());
   return SBIO_OK;
@@ -554,9 +559,9 @@ int launch_near(sbio_geom* g, double* S, double* D, cudaStream_t st) {
 }
 
 int launch_laplace(sbio_geom* g, const double* sigma, const double* mu, double* S, double* D, uint32_t parts,
-                   cudaStream_t st) {
+                   cudaStream_t st, int side) {
   phase_mark(g, 0, st);
-  int rc = launch_synth(g, sigma, mu, S, D, (parts & SBIO_PART_SELF) != 0, st);
+  int rc = launch_synth_mode(g, sigma, mu, S, D, (parts & SBIO_PART_SELF) ? 1 : 0, st, side);
   if (rc) return rc;
   phase_mark(g, 1, st);
   // with phase timing on, run the phases in order so that each is timed alone
@@ -679,6 +684,18 @@ int sbio_apply_laplace_parts(sbio_geom* g, const double* sigma_tilde, const doub
 int sbio_apply_laplace(sbio_geom* g, const double* sigma_tilde, const double* mu_hat, double* S_out, double* D_out,
                        void* stream) {
   return sbio_apply_laplace_parts(g, sigma_tilde, mu_hat, S_out, D_out, SBIO_PART_ALL, stream);
+}
+
+int sbio_apply_laplace_limit(sbio_geom* g, const double* sigma_tilde, const double* mu_hat, double* S_out,
+                             double* D_out, int32_t side, void* stream) {
+  clear_error();
+  if (!g) return set_error(SBIO_EINVAL, "null geometry");
+  if (side < -1 || side > 1) return set_error(SBIO_EINVAL, "side %d: -1 (interior), 0 or +1 (exterior)", side);
+  if ((sigma_tilde == nullptr) != (S_out == nullptr) || (mu_hat == nullptr) != (D_out == nullptr))
+    return set_error(SBIO_EINVAL, "each output must be given exactly when its input is");
+  if (!sigma_tilde && !mu_hat) return set_error(SBIO_EINVAL, "nothing to apply");
+  SBIO_CUDA_TRY(cudaSetDevice(g->ctx->device));
+  return launch_laplace(g, sigma_tilde, mu_hat, S_out, D_out, SBIO_PART_ALL, (cudaStream_t)stream, side);
 }
 
 int sbio_apply_laplace_host(sbio_geom* g, const double* sigma_host, const double* mu_host, double* S_host,

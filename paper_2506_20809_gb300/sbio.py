@@ -122,6 +122,8 @@ _SIGS = {
                                     C.POINTER(C.c_size_t)]),
     "sbio_eval_targets": (C.c_int, [_vp, _vp, _vp, _vp, _vp, _vp]),
     "sbio_eval_targets_deriv": (C.c_int, [_vp, _vp, _vp, _vp, _vp, _vp, _vp]),
+    "sbio_apply_laplace_limit": (C.c_int, [_vp, _vp, _vp, _vp, _vp, C.c_int32, _vp]),
+    "sbio_apply_laplace_deriv_limit": (C.c_int, [_vp, _vp, _vp, _vp, _vp, C.c_int32, _vp]),
     "sbio_eval_targets_stokes": (C.c_int, [_vp, _vp, _vp, _vp, _vp]),
     "sbio_eval_targets_stokes_dl": (C.c_int, [_vp, _vp, _vp, _vp]),
     "sbio_apply_stokes_dl": (C.c_int, [_vp, _vp, _vp, _vp]),
@@ -384,6 +386,18 @@ def sbio_targets_info(ts):
 def sbio_eval_targets(ts, sigma_tilde, mu_hat, S_out, D_out, stream=None):
     """S and D at the set's points (device tensors; either input may be None)."""
     _check(_lib.sbio_eval_targets(ts, _ptr(sigma_tilde), _ptr(mu_hat), _ptr(S_out), _ptr(D_out), _stream(stream)))
+
+
+def sbio_apply_laplace_limit(g, sigma_tilde, mu_hat, S_out, D_out, side, stream=None):
+    """S and the one-sided limit of D (side +1 exterior, -1 interior, 0 principal value)."""
+    _check(_lib.sbio_apply_laplace_limit(g, _ptr(sigma_tilde), _ptr(mu_hat), _ptr(S_out), _ptr(D_out), side,
+                                         _stream(stream)))
+
+
+def sbio_apply_laplace_deriv_limit(g, sigma_tilde, mu_hat, Sp_out, Dp_out, side, stream=None):
+    """The one-sided limit of S' (side +1 exterior, -1 interior, 0 principal value) and D'."""
+    _check(_lib.sbio_apply_laplace_deriv_limit(g, _ptr(sigma_tilde), _ptr(mu_hat), _ptr(Sp_out), _ptr(Dp_out), side,
+                                               _stream(stream)))
 
 
 def sbio_eval_targets_deriv(ts, dirs, sigma_tilde, mu_hat, Sp_out, Dp_out, stream=None):

@@ -264,3 +264,61 @@ def test_poly200_mixed_vs_fp64(S, poly200):
     eS, eD = OL.normwise_rel_err(Sm, S64), OL.normwise_rel_err(Dm, D64)
     print(f"mixed vs fp64: S {eS:.3e} D {eD:.3e}")
     assert eS < TOLMIX and eD < TOLMIX
+
+
+def gpu_limit(S, geom, sig, mu, side, deriv=False):
+    sg = None if sig is None else torch.from_numpy(np.ascontiguousarray(sig)).cuda()
+    mg = None if mu is None else torch.from_numpy(np.ascontiguousarray(mu)).cuda()
+    So = None if sig is None else torch.full((geom.N,), float("nan"), dtype=torch.float64, device="cuda")
+    Do = None if mu is None else torch.full((geom.N,), float("nan"), dtype=torch.float64, device="cuda")
+    fn = S.sbio_apply_laplace_deriv_limit if deriv else S.sbio_apply_laplace_limit
+    fn(geom.h, sg, mg, So, Do, side)
+    torch.cuda.synchronize()
+    return (None if So is None else So.cpu().numpy(), None if Do is None else Do.cpu().numpy())
+
+
+def test_one_sided_limits(S, lattice):
+    """D+- = D +- mu/2 and S'+- = S' -+ sigma/2 at every node (the density
+    values from the oracle's synthesis); S and D' are the same on both sides."""
+    s, c, g, og, O = lattice
+    S.sbio_geom_set_precision(g.h, S.SBIO_FP64)
+    sval = np.concatenate([OL.density_values(P, c[0][i], None)[0] for i, P in enumerate(og.parts)])
+    mval = np.concatenate([OL.density_values(P, None, c[1][i])[1] for i, P in enumerate(og.parts)])
+    S0, D0 = gpu_limit(S, g, c[0], c[1], 0)
+    Sp0, Dp0 = gpu_limit(S, g, c[0], c[1], 0, deriv=True)
+    for side in (1, -1):
+        Ss, Ds = gpu_limit(S, g, c[0], c[1], side)
+        assert np.max(np.abs(Ss - S0)) <= 1e-13 * np.max(np.abs(S0))
+        assert np.max(np.abs(Ds - (D0 + 0.5 * side * mval))) <= 1e-13 * np.max(np.abs(D0))
+        Sps, Dps = gpu_limit(S, g, c[0], c[1], side, deriv=True)
+        assert np.max(np.abs(Sps - (Sp0 - 0.5 * side * sval))) <= 1e-12 * np.max(np.abs(Sp0))
+        assert np.max(np.abs(Dps - Dp0)) <= 1e-13 * np.max(np.abs(Dp0))
+    with pytest.raises(S.SbioError) as e:
+        gpu_limit(S, g, c[0], c[1], 2)
+    assert e.value.code == S.SBIO_EINVAL
+
+
+@pytest.mark.parametrize("kind,A,C", [(0, 0.7, 1.6), (1, 1.5, 0.6)])
+def test_limits_gauss_and_conductor(S, ctx, kind, A, C):
+    """One spheroid of each kind.  Gauss's law for mu = 1: D+ = 0 and D- = -1
+    at every node; the conductor (equilibrium) density: S'+ = -sigma and
+    S'- = 0."""
+    q = np.array([0.8, 0.1, -0.5, 0.3])
+    one = I.Suspension(np.array([kind], np.int32), np.array([A]), np.array([C]), np.zeros((1, 3)),
+                       (q / np.linalg.norm(q))[None], 8)
+    mu = np.zeros((1, 81))
+    mu[0, 0] = math.sqrt(4 * math.pi)   # mu = 1 (Y_00 = 1 / sqrt(4 pi))
+    sig = np.zeros((1, 81))
+    sig[0, 0] = 1.0
+    g = S.Geometry(ctx, one, precision=S.SBIO_FP64)
+    _, Dp = gpu_limit(S, g, None, mu, 1)
+    _, Dm = gpu_limit(S, g, None, mu, -1)
+    assert np.max(np.abs(Dp)) < 1e-12
+    assert np.max(np.abs(Dm + 1.0)) < 1e-12
+    og = OG.SuspensionGeom.from_suspension(one)
+    sval, _ = OL.density_values(og.parts[0], sig[0], None)
+    Spp, _ = gpu_limit(S, g, sig, None, 1, deriv=True)
+    Spm, _ = gpu_limit(S, g, sig, None, -1, deriv=True)
+    assert np.max(np.abs(Spp + sval)) < 1e-12 * np.max(np.abs(sval))
+    assert np.max(np.abs(Spm)) < 1e-12 * np.max(np.abs(sval))
+    g.close()
