@@ -1,5 +1,5 @@
-// Value and gradient of ND exterior single-layer-type expansions of one
-// source particle at a target (eq. (dSLevalformula) in Cartesian form):
+// Gradients of the exterior single-layer-type expansions of one source
+// particle at a target (eq. (dSLevalformula) in Cartesian form):
 //     F_d   = sum c_d[nm] q_n^|m|(u) Pbar_n^|m|(v) trig_m(phi)
 //     grad F_d = e_u dF/du / h_u + e_v dF/dv / h_v + e_phi dF/dphi / h_phi
 // with q the exterior radial functions (Miller sweeps for m = 0, 1, then the
@@ -8,8 +8,7 @@
 // m Pbar / sqrt(1-v^2) = m D_n with D_n^m = Pbar_n^m / sqrt(1-v^2) (m >= 1),
 // and sqrt(1-v^2) dP_n/dv = Pbar_n^1 for m = 0.  (xl, yl, zl): target in the
 // source's local frame; c_d: coefficients with the exterior factor and the
-// normalisation folded in, index n^2 + n + m, orders n <= P1.  Outputs F_d and
-// the gradients g_d in the source's local frame.
+// normalisation folded in, index n^2 + n + m.
 #pragma once
 
 #include "sbio_internal.cuh"
@@ -17,107 +16,13 @@
 
 namespace sbio {
 
-template <int P1, int KIND, int ND>
-__device__ __forceinline__ void solid_grad(double xl, double yl, double zl, double a, const double* const* coef,
-                                           const double* __restrict__ inv_tab, double F[ND], double g[ND][3]) {
-  constexpr double sgn = (KIND == SBIO_PROLATE) ? -1.0 : 1.0;
-  const SphCoord sc = to_spheroidal(xl, yl, zl, a, KIND);
-  const double u = sc.u, v = sc.v, sv = sc.sv;
-  const double u2s = u * u + sgn;
-  const double rsu = rsqrt(u2s);
-  const double su = u2s * rsu;
-  const double inv_den = rsu * rsu;
-  double qa[P1 + 3], qb[P1 + 3];
-  miller_q01<P1 + 1, KIND>(u, rsu, inv_tab, qb, qa);   // qb = Q^0, qa = Q^1, n = 0..P1+2
-  const double c = u * rsu;
-  double Fu[ND], Fv[ND], Fp[ND];
-#pragma unroll
-  for (int d = 0; d < ND; ++d) F[d] = Fu[d] = Fv[d] = Fp[d] = 0.0;
-  double cm = 1.0, sm = 0.0;
-  const double c1 = sc.cph, s1 = sc.sph;
-  double dmm = 1.0;   // D_m^m = (2m-1)!! sv^(m-1)
-#pragma unroll
-  for (int m = 0; m <= P1; ++m) {
-    double* qm;
-    if (m == 0) {
-      qm = qb;
-    } else if (m == 1) {
-      qm = qa;
-    } else {
-      double* q1p = (m & 1) ? qb : qa;
-      double* q2p = (m & 1) ? qa : qb;
-      const double cc = -2.0 * (m - 1) * c;
-#pragma unroll
-      for (int n = m; n <= P1 + 1; ++n) q2p[n] = cc * q1p[n] + ((n - m + 2.0) * (n + m - 1.0)) * q2p[n];
-      qm = q2p;
-    }
-    if (m == 0) {
-      double pprev = 0.0, pcur = 1.0;
-#pragma unroll
-      for (int n = 0; n <= P1; ++n) {
-        const double dq = (-sgn * (n + 1.0) * qm[n + 1] - (n + 1.0) * u * qm[n]) * inv_den;
-        const double T = qm[n] * pcur, Tu = dq * pcur;
-#pragma unroll
-        for (int d = 0; d < ND; ++d) {
-          const double al = coef[d][n * n + n];
-          F[d] = fma(al, T, F[d]);
-          Fu[d] = fma(al, Tu, Fu[d]);
-        }
-        const double pnext = ((2.0 * n + 1.0) / (n + 1.0)) * (v * pcur) - ((double)n / (n + 1.0)) * pprev;
-        pprev = pcur;
-        pcur = pnext;
-      }
-    } else {
-      if (m >= 2) dmm *= (2.0 * m - 1.0) * sv;
-      double dprev = 0.0, dcur = dmm;
-#pragma unroll
-      for (int n = m; n <= P1; ++n) {
-        const double dnext = ((2.0 * n + 1.0) / (n - m + 1.0)) * (v * dcur) - ((double)(n + m) / (n - m + 1.0)) * dprev;
-        const double pb = sv * dcur;
-        const double dq = (-sgn * (n - m + 1.0) * qm[n + 1] - (n + 1.0) * u * qm[n]) * inv_den;
-        const double T = qm[n] * pb, Tu = dq * pb;
-        const double Tv = qm[n] * ((n + 1.0) * v * dcur - (n - m + 1.0) * dnext);
-        const double Tp = qm[n] * (m * dcur);
-        const double Tc = T * cm, Ts = T * sm, Tuc = Tu * cm, Tus = Tu * sm, Tvc = Tv * cm, Tvs = Tv * sm;
-        const double Tpc = -Tp * sm, Tps = Tp * cm;
-#pragma unroll
-        for (int d = 0; d < ND; ++d) {
-          const double ac = coef[d][n * n + n + m], as = coef[d][n * n + n - m];
-          F[d] = fma(ac, Tc, fma(as, Ts, F[d]));
-          Fu[d] = fma(ac, Tuc, fma(as, Tus, Fu[d]));
-          Fv[d] = fma(ac, Tvc, fma(as, Tvs, Fv[d]));
-          Fp[d] = fma(ac, Tpc, fma(as, Tps, Fp[d]));
-        }
-        if (m == 1) {
-          // delayed m = 0 v-derivative: sqrt(1-v^2) dP_n/dv = Pbar_n^1 = sv D_n^1
-          const double T0 = qb[n] * pb;
-#pragma unroll
-          for (int d = 0; d < ND; ++d) Fv[d] = fma(coef[d][n * n + n], T0, Fv[d]);
-        }
-        dprev = dcur;
-        dcur = dnext;
-      }
-    }
-    const double cn = cm * c1 - sm * s1;
-    sm = sm * c1 + cm * s1;
-    cm = cn;
-  }
-  // gradients in the local frame
-  const double W2 = u * u + sgn * v * v;
-  const double iW = rsqrt(W2);
-  const double ia = 1.0 / a;
-  const double eu0 = u * sv * c1 * iW, eu1 = u * sv * s1 * iW, eu2 = v * su * iW;
-  const double ev0 = -su * v * c1 * iW, ev1 = -su * v * s1 * iW, ev2 = u * sv * iW;
-#pragma unroll
-  for (int d = 0; d < ND; ++d) {
-    const double gu = Fu[d] * su * ia * iW, gv = Fv[d] * ia * iW, gp = Fp[d] * ia * rsu;
-    g[d][0] = gu * eu0 + gv * ev0 - gp * s1;
-    g[d][1] = gu * eu1 + gv * ev1 + gp * c1;
-    g[d][2] = gu * eu2 + gv * ev2;
-  }
-}
+// Threads per CTA of the Stokes near-gradient kernels.  They hold about 250
+// registers per thread at the larger orders; a 64-thread CTA takes a quarter
+// of an SM's register file (a 128-thread one half), so that capped near CTAs
+// share an SM with the far kernel's CTAs instead of filling it.
+constexpr int kNearGradBlock = 64;
 
-// Term-by-term form of the same evaluation.  For every term of the exterior
+// Term-by-term evaluation.  For every term of the exterior
 // expansions at a target, solid_terms hands the visitor the radial-angular
 // factors without the azimuthal trig:
 //     T  = q_n^m(u) Pbar_n^m(v),       Tu = d/du [q_n^m] Pbar_n^m(v),
@@ -135,12 +40,6 @@ __device__ __forceinline__ void solid_grad(double xl, double yl, double zl, doub
 // with Fp the phi-derivative sum (d/dphi of cos m phi -> -m sin m phi).
 // The m = 0 terms n >= 1 are issued inside the order-1 sweep, which supplies
 // their v-derivative sqrt(1-v^2) dP_n/dv = Pbar_n^1.
-// Threads per CTA of the near-gradient kernels.  They hold about 250
-// registers per thread at the larger orders; 64-thread CTAs take an eighth of
-// the register file each, so that capped near CTAs share an SM with the far
-// kernel's CTAs instead of filling it.
-constexpr int kNearGradBlock = 64;
-
 struct GradFrame {
   double k_ru, k_rv, k_zu, k_zv, k_p, c1, s1;
 };
