@@ -5,7 +5,8 @@
 //             block, tile range) work items from an atomic counter, longest
 //             first, until all suspensions' far fields are done;
 //   branch B: after all syntheses, the near-field kernels of every suspension
-//             (FP64), which run beside the FP32 far field on the same SMs.
+//             (FP64) spread over several streams, so that their small grids
+//             run side by side when SM slots are free.
 // The graph is captured on the first apply and replayed while the caller
 // passes the same buffers; the per-suspension far descriptors live in device
 // memory and are refreshed before every replay.
@@ -27,6 +28,11 @@ struct sbio_batch {
   int64_t far_pairs = 0;
   cudaStream_t sa = nullptr, sb = nullptr;
   cudaEvent_t ev_fork = nullptr, ev_synth = nullptr, ev_near = nullptr;
+  // near branch: the suspensions' near kernels spread over several streams so
+  // that their small grids run side by side in the far kernel's spare slots
+  static constexpr int kNearStreams = 8;
+  cudaStream_t sn[kNearStreams] = {};
+  cudaEvent_t ev_nj[kNearStreams] = {};
   cudaGraphExec_t exec = nullptr;
   std::vector<const void*> captured;   // buffers baked into the graph
   int kernels_per_apply = 0;           // kernel nodes of the captured graph
@@ -67,7 +73,10 @@ static int build_items(sbio_batch* b) {
   int dev = 0, sms = 152;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  // six resident far CTAs per SM leave registers for the near kernels
+  // at least as many CTAs as fit: the far field holds the SMs until its item
+  // queue is empty (running the FP64 near kernels in slots left beside it
+  // measured slower); the near kernels of the suspensions then run side by
+  // side on their streams
   b->grid = std::max(1, std::min(b->n_items, sms * 6));
   return SBIO_OK;
 }
@@ -89,12 +98,16 @@ static int capture(sbio_batch* b, const double* const* sigma, const double* cons
   cudaStreamWaitEvent(b->sb, b->ev_fork, 0);
   for (size_t s = 0; s < b->geoms.size() && !rc; ++s) rc = launch_synth(b->geoms[s], sigma[s], mu[s], S[s], D[s], true, b->sa);
   cudaEventRecord(b->ev_synth, b->sa);
-  cudaStreamWaitEvent(b->sb, b->ev_synth, 0);
-  for (size_t s = 0; s < b->geoms.size() && !rc; ++s) rc = launch_near(b->geoms[s], S[s], D[s], b->sb);
+  for (int k = 0; k < sbio_batch::kNearStreams; ++k) cudaStreamWaitEvent(b->sn[k], b->ev_synth, 0);
+  for (size_t s = 0; s < b->geoms.size() && !rc; ++s)
+    rc = launch_near(b->geoms[s], S[s], D[s], b->sn[s % sbio_batch::kNearStreams]);
+  for (int k = 0; k < sbio_batch::kNearStreams; ++k) cudaEventRecord(b->ev_nj[k], b->sn[k]);
+  cudaStreamWaitEvent(b->sb, b->ev_synth, 0);   // the fork stream joins too (unused otherwise)
   cudaEventRecord(b->ev_near, b->sb);
   if (!rc) cudaMemsetAsync(b->d_counter, 0, sizeof(int), b->sa);
   if (!rc && b->n_items > 0)
     rc = launch_far_persistent(b->d_desc, b->d_items, b->n_items, b->d_counter, b->far_tt, b->grid, b->sa);
+  for (int k = 0; k < sbio_batch::kNearStreams; ++k) cudaStreamWaitEvent(b->sa, b->ev_nj[k], 0);
   cudaStreamWaitEvent(b->sa, b->ev_near, 0);
   cudaError_t e = cudaStreamEndCapture(b->sa, &graph);
   // capture records launches without running them: count them per replay instead
@@ -150,6 +163,10 @@ int sbio_batch_create(sbio_ctx* ctx, sbio_geom* const* geoms, int32_t n, sbio_ba
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev_fork, cudaEventDisableTiming);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev_synth, cudaEventDisableTiming);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev_near, cudaEventDisableTiming);
+  for (int k = 0; k < sbio_batch::kNearStreams && e == cudaSuccess; ++k) {
+    e = cudaStreamCreateWithFlags(&b->sn[k], cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev_nj[k], cudaEventDisableTiming);
+  }
   int rc = (e == cudaSuccess) ? build_items(b) : set_error(SBIO_ENOMEM, "batch allocation failed: %s", cudaGetErrorString(e));
   if (rc) {
     sbio_batch_destroy(b);
@@ -172,6 +189,10 @@ int sbio_batch_destroy(sbio_batch* b) {
   if (b->ev_fork) cudaEventDestroy(b->ev_fork);
   if (b->ev_synth) cudaEventDestroy(b->ev_synth);
   if (b->ev_near) cudaEventDestroy(b->ev_near);
+  for (int k = 0; k < sbio_batch::kNearStreams; ++k) {
+    if (b->sn[k]) cudaStreamDestroy(b->sn[k]);
+    if (b->ev_nj[k]) cudaEventDestroy(b->ev_nj[k]);
+  }
   delete b;
   return SBIO_OK;
 }
