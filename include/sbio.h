@@ -276,6 +276,13 @@ int sbio_apply_laplace_deriv_limit(sbio_geom* g, const double* sigma_tilde, cons
  * p > 20.  Asynchronous. */
 int sbio_apply_stokes_dl(sbio_geom* g, const double* q_hat, double* u_out, void* stream);
 
+/* One-sided limits of the Stokes double layer on every node's own surface:
+ * side = +1 the exterior limit (principal value + q/2), side = -1 the
+ * interior limit (principal value - q/2), side = 0 the principal value (as
+ * sbio_apply_stokes_dl); q the density at the node.  SBIO_EINVAL for side
+ * outside {-1, 0, 1}.  Asynchronous. */
+int sbio_apply_stokes_dl_limit(sbio_geom* g, const double* q_hat, double* u_out, int32_t side, void* stream);
+
 /* End-to-end Stokes apply from and to HOST memory (f_tilde_host M x 3 x
  * (p+1)^2, u_host N x 3): copies in through library-owned device buffers on
  * `stream`, applies, copies out and synchronises `stream` before returning. */

@@ -50,7 +50,7 @@ __global__ void __launch_bounds__(256) sdl_prep_kernel(
     const double* __restrict__ qv, const double* __restrict__ qw, const double* __restrict__ qptab,
     const double* __restrict__ qtrig, const double* __restrict__ extS1, const double* __restrict__ extD1,
     const double* __restrict__ normc1, const double* __restrict__ qhat, double* __restrict__ coef_out,
-    double* __restrict__ src64, float4* __restrict__ src32, double* __restrict__ u_init) {
+    double* __restrict__ src64, float4* __restrict__ src32, double* __restrict__ u_init, double init_factor) {
   extern __shared__ double sm[];
   const int i = blockIdx.x;
   const int p1 = p + 1, nc = (p + 1) * (p + 1), nc1 = (p1 + 1) * (p1 + 1);
@@ -93,7 +93,7 @@ __global__ void __launch_bounds__(256) sdl_prep_kernel(
     src32[t * 2 + 0] = make_float4((float)y0, (float)y1, (float)y2, (float)(wt * qq[0]));
     src32[t * 2 + 1] = make_float4((float)(wt * qq[1]), (float)(wt * qq[2]), 0.f, 0.f);
     if (u_init)
-      for (int d = 0; d < 3; ++d) u_init[t * 3 + d] = -0.5 * qq[d];
+      for (int d = 0; d < 3; ++d) u_init[t * 3 + d] = init_factor * qq[d];
   }
   __syncthreads();
   // (2) q at the product-quadrature rows
@@ -561,7 +561,10 @@ int sdl_self(sbio_geom* g, double* u_out, cudaStream_t st) {
   return SBIO_OK;
 }
 
-int sdl_prep(sbio_geom* g, const double* qhat, double* u_init, cudaStream_t st) {
+// u_init (may be null) is set to init_factor q at every node: -1/2 for the
+// principal value, 0 for the exterior limit, -1 for the interior limit (the
+// near, own-node and far parts add the exterior-limit field).
+int sdl_prep(sbio_geom* g, const double* qhat, double* u_init, cudaStream_t st, double init_factor = -0.5) {
   const GeomHost& h = g->h;
   const DevGeom& d = g->d;
   const int p = h.p, p1 = p + 1, nc = (p + 1) * (p + 1), mw = 2 * p + 1, mw1 = 2 * p1 + 1;
@@ -573,7 +576,7 @@ int sdl_prep(sbio_geom* g, const double* qhat, double* u_init, cudaStream_t st) 
     SBIO_CUDA_TRY(cudaFuncSetAttribute(sdl_prep_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   sdl_prep_kernel<<<h.M, 256, smem, st>>>(p, h.n_v, h.n_phi, h.n_q, h.n_f, d.parts, d.xyz, d.w, d.ptab, d.trig,
                                           d.st_qv, d.st_qw, d.st_qptab, d.st_qtrig, d.st_ext, d.sdl_ext, d.st_normc,
-                                          qhat, d.sdl_coef, d.st_src64, d.st_src32, u_init);
+                                          qhat, d.sdl_coef, d.st_src64, d.st_src32, u_init, init_factor);
   count_launch();
   SBIO_CUDA_TRY(cudaGetLastError());
   return SBIO_OK;
@@ -605,9 +608,10 @@ using namespace sbio;
 
 extern "C" {
 
-int sbio_apply_stokes_dl(sbio_geom* g, const double* q_hat, double* u_out, void* stream) {
+int sbio_apply_stokes_dl_limit(sbio_geom* g, const double* q_hat, double* u_out, int32_t side, void* stream) {
   clear_error();
   if (!g || !q_hat || !u_out) return set_error(SBIO_EINVAL, "null argument");
+  if (side < -1 || side > 1) return set_error(SBIO_EINVAL, "side %d: -1 (interior), 0 or +1 (exterior)", side);
   const GeomHost& h = g->h;
   if (h.p > 20) return set_error(SBIO_ENOTSUP, "Stokes double layer is built for p <= 20 (p = %d)", h.p);
   stokes_dl_near_launcher nl = sdl_near_for(h.p);
@@ -615,7 +619,9 @@ int sbio_apply_stokes_dl(sbio_geom* g, const double* q_hat, double* u_out, void*
   SBIO_CUDA_TRY(cudaSetDevice(g->ctx->device));
   cudaStream_t st = (cudaStream_t)stream;
   phase_mark(g, 0, st);
-  int rc = sdl_prep(g, q_hat, u_out, st);   // writes -q/2 at every node
+  // the rest of the apply adds the exterior limit: start from -q/2 (principal
+  // value), 0 (exterior) or -q (interior) at every node
+  int rc = sdl_prep(g, q_hat, u_out, st, -0.5 * (1 - side));
   if (rc) return rc;
   const DevGeom& d = g->d;
   const bool has_pairs = !h.pair_t.empty();
@@ -644,6 +650,10 @@ int sbio_apply_stokes_dl(sbio_geom* g, const double* q_hat, double* u_out, void*
   if (fork) SBIO_CUDA_TRY(cudaStreamWaitEvent(st, g->ev_join, 0));
   phase_mark(g, 3, st);
   return SBIO_OK;
+}
+
+int sbio_apply_stokes_dl(sbio_geom* g, const double* q_hat, double* u_out, void* stream) {
+  return sbio_apply_stokes_dl_limit(g, q_hat, u_out, 0, stream);
 }
 
 int sbio_eval_targets_stokes_dl(sbio_targets* ts, const double* q_hat, double* u_out, void* stream) {

@@ -123,6 +123,7 @@ _SIGS = {
     "sbio_eval_targets": (C.c_int, [_vp, _vp, _vp, _vp, _vp, _vp]),
     "sbio_eval_targets_deriv": (C.c_int, [_vp, _vp, _vp, _vp, _vp, _vp, _vp]),
     "sbio_apply_laplace_limit": (C.c_int, [_vp, _vp, _vp, _vp, _vp, C.c_int32, _vp]),
+    "sbio_apply_stokes_dl_limit": (C.c_int, [_vp, _vp, _vp, C.c_int32, _vp]),
     "sbio_apply_laplace_deriv_limit": (C.c_int, [_vp, _vp, _vp, _vp, _vp, C.c_int32, _vp]),
     "sbio_eval_targets_stokes": (C.c_int, [_vp, _vp, _vp, _vp, _vp]),
     "sbio_eval_targets_stokes_dl": (C.c_int, [_vp, _vp, _vp, _vp]),
@@ -415,6 +416,11 @@ def sbio_eval_targets_stokes(ts, f_tilde, u_out, p_out=None, stream=None):
 def sbio_apply_stokes_dl(g, q_hat, u_out, stream=None):
     """Stokes double layer (principal value) at all nodes; device tensors."""
     _check(_lib.sbio_apply_stokes_dl(g, _ptr(q_hat), _ptr(u_out), _stream(stream)))
+
+
+def sbio_apply_stokes_dl_limit(g, q_hat, u_out, side, stream=None):
+    """Stokes double layer at all nodes, one-sided limit (+1 exterior, -1 interior, 0 principal value)."""
+    _check(_lib.sbio_apply_stokes_dl_limit(g, _ptr(q_hat), _ptr(u_out), side, _stream(stream)))
 
 
 def sbio_eval_targets_stokes_dl(ts, q_hat, u_out, stream=None):

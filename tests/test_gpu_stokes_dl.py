@@ -146,3 +146,37 @@ def test_stokesdl100_sampled_against_oracle(S, ctx):
     assert np.max(np.abs(U64[tg] - Ur)) / scale < TOL64
     assert np.max(np.abs(Um[tg] - Ur)) / scale < TOLMIX
     g.close()
+
+
+def test_limits_of_a_rigid_motion(S, ctx):
+    """A rigid motion q on one particle: its exterior limit is 0 and its
+    interior limit -q on that particle's surface (the field is 0 outside and
+    -q inside); at the other particles' nodes all sides agree."""
+    p = 10
+    s = I.rsa_suspension(3, 0.1, 77, p)
+    og = OG.SuspensionGeom.from_suspension(s)
+    rng = np.random.default_rng(5)
+    P = og.parts[1]
+    vals = rng.standard_normal(3)[None, :] + np.cross(rng.standard_normal(3)[None, :], P.x - P.center)
+    q = np.zeros((3, 3, (p + 1) ** 2))
+    q[1] = np.stack([OS.analysis(P, vals[:, k]) for k in range(3)])
+    g = S.Geometry(ctx, s, precision=S.SBIO_FP64)
+    qd = torch.from_numpy(q).cuda()
+    out = {}
+    for side in (0, 1, -1):
+        u = torch.full((g.N, 3), float("nan"), dtype=torch.float64, device="cuda")
+        S.sbio_apply_stokes_dl_limit(g.h, qd, u, side)
+        torch.cuda.synchronize()
+        out[side] = u.cpu().numpy()
+    G = og.G
+    scale = np.max(np.abs(vals))
+    assert np.max(np.abs(out[1][G:2 * G])) < 1e-11 * scale
+    assert np.max(np.abs(out[-1][G:2 * G] + vals)) < 1e-11 * scale
+    assert np.max(np.abs(out[0][G:2 * G] + 0.5 * vals)) < 1e-11 * scale
+    rest = np.r_[0:G, 2 * G:3 * G]
+    assert np.max(np.abs(out[1][rest] - out[0][rest])) <= 1e-14 * scale
+    assert np.max(np.abs(out[-1][rest] - out[0][rest])) <= 1e-14 * scale
+    with pytest.raises(S.SbioError) as e:
+        S.sbio_apply_stokes_dl_limit(g.h, qd, torch.zeros((g.N, 3), dtype=torch.float64, device="cuda"), 3)
+    assert e.value.code == S.SBIO_EINVAL
+    g.close()
