@@ -32,6 +32,9 @@ sys.path.insert(0, ROOT)
 
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12     # SMs x FP32 lanes x FMA x max SM clock
 FP64_PEAK_TFLOPS = 1.25                               # nominal GB300 FP64 rate
+# MUFU rsqrt rate of the XU pipe: one warp instruction per 4 cycles per SM
+# sub-partition (ncu's XU peak), i.e. 32 per clock per SM
+SFU_PEAK_PER_S = 152 * 32 * 2.070e9
 FAR_FLOP_PER_PAIR = {"SD": 19, "S": 10, "D": 14}
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one launch of
 # the mixed S+D far kernel on the 200-spheroid p = 16 suspension, from one ncu
@@ -416,6 +419,10 @@ def run_ours(args, ws, rank, lrank):
                      "algorithmic_bytes": None,
                      "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz" if prec == S.SBIO_MIXED
                      else "nominal FP64 1.25 TFLOP/s"},
+        "sfu": {"kernel": "far_mixed_kernel" if prec == S.SBIO_MIXED else "far_fp64_kernel",
+                "unit": "rsqrt/s", "achieved": geom.n_far / (far_mean * 1e-3), "peak": SFU_PEAK_PER_S,
+                "frac": geom.n_far / (far_mean * 1e-3) / SFU_PEAK_PER_S,
+                "note": "one rsqrt per far pair; FP32 MUFU in the mixed form"},
         "roofline_near": {"kernel": "near_kernel", "bound": "alu", "unit": "TFLOP/s",
                           "achieved": near_flop_per_pair(susp.p) * geom.n_near / (statistics.mean(near_ms) * 1e-3) / 1e12,
                           "peak": FP64_PEAK_TFLOPS,
