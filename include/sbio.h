@@ -300,7 +300,8 @@ int sbio_geom_get_stokes_tuning(const sbio_geom* g, int32_t* far_tt, int32_t* fa
 
 /* Autotuner of the Stokes kernels: as sbio_geom_autotune, timing the
  * Stokeslet far kernel and whole Stokes applies (zero forces through the
- * geometry's own workspaces).  The velocity-and-pressure evaluation at
+ * geometry's own workspaces), near caps from 4 CTAs per SM up or uncapped
+ * (the Stokes near kernels run small CTAs).  The velocity-and-pressure evaluation at
  * points runs its near pairs at twice the tuned near cap (its near pairs cost
  * about twice the single layer's).  SBIO_ENOTSUP for p > 20.  Synchronises
  * `stream`. */

@@ -231,6 +231,7 @@ struct TuneOps {
   int* tt;
   int* splits;
   int* cap;
+  int min_cap = 1;   // smallest near cap tried (besides uncapped)
 };
 int tune_launch_shape(sbio_geom* g, const TuneOps& ops, double* out, cudaStream_t st, double* best_far_ms);
 

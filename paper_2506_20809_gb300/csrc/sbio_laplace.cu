@@ -644,6 +644,7 @@ int tune_launch_shape(sbio_geom* g, const TuneOps& ops, double* out, cudaStream_
     float best_apply = 1e30f;
     int best_cap = *ops.cap;
     for (int c = 0; c < 5 && !rc; ++c) {
+      if (caps[c] != 0 && caps[c] < ops.min_cap) continue;
       *ops.cap = caps[c];
       float m = 0.f;
       rc = time3(ops.whole, &m);
@@ -843,6 +844,10 @@ int sbio_geom_autotune_stokes(sbio_geom* g, void* stream, int32_t* far_tt, int32
   ops.tt = &h.st_far_tt;
   ops.splits = &h.st_far_splits;
   ops.cap = &h.st_near_ctas_per_sm;
+  // the Stokes near kernels run 64-thread CTAs: caps of 1 or 2 CTAs per SM
+  // starve them (stokes100 ran 911 applies/s at 2, 974 at 8 or uncapped,
+  // while the whole-apply timings of the tuner differ by less than its noise)
+  ops.min_cap = 4;
   double best = 0.0;
   rc = tune_launch_shape(g, ops, d.host_out, st, &best);
   if (rc) return rc;
