@@ -52,6 +52,21 @@ __host__ __device__ inline int nm_count(int p) { return (p + 1) * (p + 2) / 2; }
 __host__ __device__ inline int nm_index(int n, int m) { return n * (n + 1) / 2 + m; }
 __host__ __device__ inline int coef_index(int n, int m) { return n * n + n + m; }
 
+// FP32 far-field helpers shared by the mixed kernels.
+// Knuth's TwoSum: s + e == a + b exactly.
+__device__ __forceinline__ void two_sum_f32(float a, float b, float& s, float& e) {
+  s = a + b;
+  const float bb = s - a;
+  e = (a - (s - bb)) + (b - bb);
+}
+
+// One MUFU reciprocal square root (approximate, flush-to-zero).
+__device__ __forceinline__ float rsqrt_f32(float x) {
+  float r;
+  asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+
 // One particle as the kernels see it.
 struct PartGeom {
   double a;       // half focal distance

@@ -27,18 +27,6 @@ struct alignas(32) dd4 {
   double x, y, z, w;
 };
 
-__device__ __forceinline__ float rsqrt_apx(float x) {
-  float r;
-  asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
-  return r;
-}
-
-__device__ __forceinline__ void two_sum_f(float a, float b, float& s, float& e) {
-  s = a + b;
-  const float bb = s - a;
-  e = (a - (s - bb)) + (b - bb);
-}
-
 // FP64 form: one target per thread, kFarTile sources per shared-memory tile.
 template <bool DO_S, bool DO_D>
 __global__ void __launch_bounds__(kFarTile) far_deriv_fp64_kernel(const int4* __restrict__ tiles, int n_tiles,
@@ -245,7 +233,7 @@ __global__ void __launch_bounds__(kFarTile) far_deriv_mixed_kernel(const int4* _
           for (int k = 0; k < TT / 2; ++k) {
             const float2 r2 =
                 __ffma2_rn(Xp[k], m2x, __ffma2_rn(Yp[k], m2y, __ffma2_rn(Zp[k], m2z, __fadd2_rn(XXp[k], yy))));
-            const float2 ri = make_float2(rsqrt_apx(r2.x), rsqrt_apx(r2.y));
+            const float2 ri = make_float2(rsqrt_f32(r2.x), rsqrt_f32(r2.y));
             const float2 ri2 = __fmul2_rn(ri, ri), ri3 = __fmul2_rn(ri2, ri);
             // nu.(x - y) = nu.x + (nu/2).(-2y)
             const float2 rn = __ffma2_rn(NZp[k], m2z, __ffma2_rn(NYp[k], m2y, __ffma2_rn(NXp[k], m2x, NXXp[k])));
@@ -272,7 +260,7 @@ __global__ void __launch_bounds__(kFarTile) far_deriv_mixed_kernel(const int4* _
         for (int q = 0; q < TT; ++q) {
           const float dx = X[q] - a.x, dy = Y[q] - a.y, dz = Z[q] - a.z;
           const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
-          const float ri = rsqrt_apx(r2);
+          const float ri = rsqrt_f32(r2);
           const float ri2 = ri * ri, ri3 = ri2 * ri;
           const float rn = fmaf(dz, NZ[q], fmaf(dy, NY[q], dx * NX[q]));
           if (DO_S) pS[q] = fmaf(a.w * rn, ri3, pS[q]);
@@ -289,12 +277,12 @@ __global__ void __launch_bounds__(kFarTile) far_deriv_mixed_kernel(const int4* _
         if (!((skipmask >> q) & 1u)) {
           float sum, err;
           if (DO_S) {
-            two_sum_f(acc[(4 * q + 0) * kFarTile + tid], pS[q], sum, err);
+            two_sum_f32(acc[(4 * q + 0) * kFarTile + tid], pS[q], sum, err);
             acc[(4 * q + 0) * kFarTile + tid] = sum;
             acc[(4 * q + 1) * kFarTile + tid] += err;
           }
           if (DO_D) {
-            two_sum_f(acc[(4 * q + 2) * kFarTile + tid], pD[q], sum, err);
+            two_sum_f32(acc[(4 * q + 2) * kFarTile + tid], pD[q], sum, err);
             acc[(4 * q + 2) * kFarTile + tid] = sum;
             acc[(4 * q + 3) * kFarTile + tid] += err;
           }

@@ -143,19 +143,6 @@ __global__ void __launch_bounds__(256) synth_kernel(int p, int n_v, int n_phi, c
 // far: tiled all-pairs quadrature over far source nodes
 // ---------------------------------------------------------------------------
 
-// Knuth's TwoSum: s + e == a + b exactly.
-__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
-  s = a + b;
-  const float bb = s - a;
-  e = (a - (s - bb)) + (b - bb);
-}
-
-__device__ __forceinline__ float rsqrt_approx(float x) {
-  float r;
-  asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
-  return r;
-}
-
 // FP64 form: one target per thread, kFarTile sources per smem tile.
 template <bool DO_S, bool DO_D>
 __global__ void __launch_bounds__(kFarTile) far_fp64_kernel(const int4* __restrict__ tiles, int n_tiles,
@@ -335,7 +322,7 @@ __device__ __forceinline__ void far_mixed_block(int64_t tb, int t_lo, int t_hi,
           for (int k = 0; k < TT / 2; ++k) {
             const float2 r2 =
                 __ffma2_rn(Xp[k], mx, __ffma2_rn(Yp[k], my, __ffma2_rn(Zp[k], mz, __fadd2_rn(XXp[k], yy))));
-            const float2 ri = make_float2(rsqrt_approx(r2.x), rsqrt_approx(r2.y));
+            const float2 ri = make_float2(rsqrt_f32(r2.x), rsqrt_f32(r2.y));
             if (DO_S) sS2[k] = __ffma2_rn(q2, ri, sS2[k]);
             if (DO_D) {
               const float2 dn = __ffma2_rn(dwx, Xp[k], __ffma2_rn(dwy, Yp[k], __ffma2_rn(dwz, Zp[k], ndy)));
@@ -358,7 +345,7 @@ __device__ __forceinline__ void far_mixed_block(int64_t tb, int t_lo, int t_hi,
           for (int q = 0; q < TT; ++q) {
             const float dx = X[q] - a.x, dy = Y[q] - a.y, dz = Z[q] - a.z;
             const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
-            const float ri = rsqrt_approx(r2);
+            const float ri = rsqrt_f32(r2);
             if (DO_S) pS[q] = fmaf(a.w, ri, pS[q]);
             if (DO_D) {
               const float dn = fmaf(b.z, dz, fmaf(b.y, dy, b.x * dx));
@@ -372,12 +359,12 @@ __device__ __forceinline__ void far_mixed_block(int64_t tb, int t_lo, int t_hi,
         if (!((skipmask >> q) & 1u)) {
           float sum, err;
           if (DO_S) {
-            two_sum(acc[(4 * q + 0) * kFarTile + tid], pS[q], sum, err);
+            two_sum_f32(acc[(4 * q + 0) * kFarTile + tid], pS[q], sum, err);
             acc[(4 * q + 0) * kFarTile + tid] = sum;
             acc[(4 * q + 1) * kFarTile + tid] += err;
           }
           if (DO_D) {
-            two_sum(acc[(4 * q + 2) * kFarTile + tid], pD[q], sum, err);
+            two_sum_f32(acc[(4 * q + 2) * kFarTile + tid], pD[q], sum, err);
             acc[(4 * q + 2) * kFarTile + tid] = sum;
             acc[(4 * q + 3) * kFarTile + tid] += err;
           }

@@ -212,18 +212,6 @@ struct alignas(32) dbl4s {
   double x, y, z, w;
 };
 
-__device__ __forceinline__ void two_sum_f(float a, float b, float& s, float& e) {
-  s = a + b;
-  const float bb = s - a;
-  e = (a - (s - bb)) + (b - bb);
-}
-
-__device__ __forceinline__ float rsqrt_approx_f(float x) {
-  float r;
-  asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
-  return r;
-}
-
 __global__ void __launch_bounds__(kFarTile) stokes_far_fp64_kernel(const int4* __restrict__ tiles, int n_tiles,
                                                                    const double* __restrict__ src64,
                                                                    const double* __restrict__ xyz,
@@ -383,7 +371,7 @@ __global__ void __launch_bounds__(kFarTile) stokes_far_mixed_kernel(const int4* 
           for (int k = 0; k < TP; ++k) {
             const float2 dx = __fadd2_rn(Xp[k], myx), dy = __fadd2_rn(Yp[k], myy), dz = __fadd2_rn(Zp[k], myz);
             const float2 r2 = __ffma2_rn(dz, dz, __ffma2_rn(dy, dy, __fmul2_rn(dx, dx)));
-            const float2 ri = make_float2(rsqrt_approx_f(r2.x), rsqrt_approx_f(r2.y));
+            const float2 ri = make_float2(rsqrt_f32(r2.x), rsqrt_f32(r2.y));
             const float2 rf = __ffma2_rn(fz, dz, __ffma2_rn(fy, dy, __fmul2_rn(fx, dx)));
             // f / r + (f.r) r / r^3 = (1/r) (f + t r), t = (f.r) / r^2
             const float2 t = __fmul2_rn(rf, __fmul2_rn(ri, ri));
@@ -409,7 +397,7 @@ __global__ void __launch_bounds__(kFarTile) stokes_far_mixed_kernel(const int4* 
 #pragma unroll
           for (int q = 0; q < TT; ++q) {
             const float dx = X[q] - A.x, dy = Y[q] - A.y, dz = Z[q] - A.z;
-            const float ri = rsqrt_approx_f(fmaf(dz, dz, fmaf(dy, dy, dx * dx)));
+            const float ri = rsqrt_f32(fmaf(dz, dz, fmaf(dy, dy, dx * dx)));
             const float rf = fmaf(dz, B.y, fmaf(dy, B.x, dx * A.w));
             const float t = rf * (ri * ri);
             p0[q] = fmaf(ri, fmaf(t, dx, A.w), p0[q]);
@@ -426,7 +414,7 @@ __global__ void __launch_bounds__(kFarTile) stokes_far_mixed_kernel(const int4* 
 #pragma unroll
           for (int c = 0; c < NA; ++c) {
             float sum, err;
-            two_sum_f(acc[(2 * NA * q + 2 * c) * kFarTile + tid], pv[c], sum, err);
+            two_sum_f32(acc[(2 * NA * q + 2 * c) * kFarTile + tid], pv[c], sum, err);
             acc[(2 * NA * q + 2 * c) * kFarTile + tid] = sum;
             acc[(2 * NA * q + 2 * c + 1) * kFarTile + tid] += err;
           }

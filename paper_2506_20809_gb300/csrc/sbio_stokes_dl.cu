@@ -168,18 +168,6 @@ struct alignas(32) sd4 {
   double x, y, z, w;
 };
 
-__device__ __forceinline__ float rsqrt_apx_s(float x) {
-  float r;
-  asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
-  return r;
-}
-
-__device__ __forceinline__ void two_sum_s(float a, float b, float& s, float& e) {
-  s = a + b;
-  const float bb = s - a;
-  e = (a - (s - bb)) + (b - bb);
-}
-
 // FP64 stresslet quadrature: one target per thread.
 __global__ void __launch_bounds__(kFarTile) stresslet_far_fp64_kernel(const int4* __restrict__ tiles, int n_tiles,
                                                                       const double* __restrict__ src64,
@@ -352,7 +340,7 @@ __global__ void __launch_bounds__(kFarTile) stresslet_far_mixed_kernel(const int
           for (int k = 0; k < TP; ++k) {
             const float2 dx = __fadd2_rn(Xp[k], myx), dy = __fadd2_rn(Yp[k], myy), dz = __fadd2_rn(Zp[k], myz);
             const float2 r2 = __ffma2_rn(dz, dz, __ffma2_rn(dy, dy, __fmul2_rn(dx, dx)));
-            const float2 ri = make_float2(rsqrt_apx_s(r2.x), rsqrt_apx_s(r2.y));
+            const float2 ri = make_float2(rsqrt_f32(r2.x), rsqrt_f32(r2.y));
             const float2 ri2 = __fmul2_rn(ri, ri);
             const float2 rq = __ffma2_rn(dz, qz, __ffma2_rn(dy, qy, __fmul2_rn(dx, qx)));
             const float2 rn = __ffma2_rn(dz, nz, __ffma2_rn(dy, ny, __fmul2_rn(dx, nx)));
@@ -375,7 +363,7 @@ __global__ void __launch_bounds__(kFarTile) stresslet_far_mixed_kernel(const int
 #pragma unroll
         for (int q = 0; q < TT; ++q) {
           const float dx = X[q] - a.x, dy = Y[q] - a.y, dz = Z[q] - a.z;
-          const float ri = rsqrt_apx_s(fmaf(dz, dz, fmaf(dy, dy, dx * dx)));
+          const float ri = rsqrt_f32(fmaf(dz, dz, fmaf(dy, dy, dx * dx)));
           const float ri2 = ri * ri;
           const float rq = fmaf(dz, b.y, fmaf(dy, b.x, dx * a.w));
           const float rn = fmaf(dz, c.z, fmaf(dy, c.y, dx * c.x));
@@ -393,7 +381,7 @@ __global__ void __launch_bounds__(kFarTile) stresslet_far_mixed_kernel(const int
 #pragma unroll
           for (int k = 0; k < 3; ++k) {
             float sum, err;
-            two_sum_s(acc[(6 * q + 2 * k) * kFarTile + tid], pv[k], sum, err);
+            two_sum_f32(acc[(6 * q + 2 * k) * kFarTile + tid], pv[k], sum, err);
             acc[(6 * q + 2 * k) * kFarTile + tid] = sum;
             acc[(6 * q + 2 * k + 1) * kFarTile + tid] += err;
           }
