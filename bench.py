@@ -93,7 +93,7 @@ def parse():
     ap.add_argument("--far-shape", default="", help="TT,SPLITS: fixed far-field launch shape (skips the autotuner)")
     ap.add_argument("--workload", default="poly200",
                     choices=["poly200", "stokes100", "batch64", "serve", "deriv200", "targets200", "derivpoints200",
-                             "dirichlet200", "stokespoints100", "stokesdl100"])
+                             "dirichlet200", "stokespoints100", "stokesdl100", "stokesdlpoints100"])
     ap.add_argument("--rates", default="50,100,200,500,1000,2000", help="serve: arrival rates (req/s)")
     ap.add_argument("--requests", type=int, default=48, help="serve: requests per rate")
     ap.add_argument("--slots", type=int, default=4, help="serve: concurrent request slots")
@@ -977,10 +977,11 @@ def run_dirichlet200(args, ws, rank, lrank):
         print(json.dumps(line), flush=True)
 
 
-def run_stokespoints100(args, ws, rank, lrank):
+def run_stokespoints100(args, ws, rank, lrank, dl=False):
     """Stokes velocity and pressure of the 100-spheroid, p = 12 suspension at
     shell points (1e-1 .. 1e-6, 10 per spheroid and distance) plus 30,000
-    points in the box; mixed precision, L2 flushed before every step."""
+    points in the box; mixed precision, L2 flushed before every step.  With
+    dl: the Stokes double layer of three densities at the same points."""
     import torch
 
     import __graft_entry__ as GE
@@ -1003,40 +1004,51 @@ def run_stokespoints100(args, ws, rank, lrank):
     pr = torch.empty(ts.T, dtype=torch.float64, device="cuda")
     st = torch.cuda.current_stream()
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    if dl:
+        def step():
+            S.sbio_eval_targets_stokes_dl(ts.h, fd, u)
+    else:
+        def step():
+            S.sbio_eval_targets_stokes(ts.h, fd, u, pr)
     for _ in range(args.warmup):
-        S.sbio_eval_targets_stokes(ts.h, fd, u, pr)
+        step()
     clocks = ClockSampler(lrank)
     clocks.start()
     ms = []
     l0 = S.sbio_launch_count()
     for _ in range(args.steps):
         flush.zero_()
-        ms.append(_event_time(st, lambda: S.sbio_eval_targets_stokes(ts.h, fd, u, pr)))
+        ms.append(_event_time(st, step))
     launches = S.sbio_launch_count() - l0
     clk = clocks.stop()
     um, pm = u.clone(), pr.clone()
     S.sbio_geom_set_precision(g.h, S.SBIO_FP64)
-    S.sbio_eval_targets_stokes(ts.h, fd, u, pr)
-    t64 = _event_time(st, lambda: S.sbio_eval_targets_stokes(ts.h, fd, u, pr))
-    err = {"u": float((um - u).abs().max() / u.abs().max()), "p": float((pm - pr).abs().max() / pr.abs().max())}
+    step()
+    t64 = _event_time(st, step)
+    err = {"u": float((um - u).abs().max() / u.abs().max())}
+    if not dl:
+        err["p"] = float((pm - pr).abs().max() / pr.abs().max())
     mean = statistics.mean(ms)
-    line = {"metric": "point evaluations/s (Stokes velocity + pressure at arbitrary points)",
+    far_flop = STRESSLET_FAR_FLOP_PER_PAIR if dl else STOKES_P_FAR_FLOP_PER_PAIR
+    line = {"metric": ("point evaluations/s (Stokes double layer at arbitrary points)" if dl else
+                       "point evaluations/s (Stokes velocity + pressure at arbitrary points)"),
             "value": ts.T * 1e3 / mean, "unit": "points/s", "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": mean, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
-            "config": {"workload": "stokespoints100_p12", "M": susp.M, "p": susp.p, "points": ts.T,
+            "config": {"workload": "stokesdlpoints100_p12" if dl else "stokespoints100_p12", "M": susp.M, "p": susp.p, "points": ts.T,
                        "near_pairs": ts.n_near, "far_pairs": ts.n_far,
                        "far_launch": {"targets_per_thread": stune[0], "source_splits": stune[1]},
                        "near_ctas_per_sm_overlapped": scap,
                        "points_recipe": "shells at 1e-1..1e-6 (10 per spheroid and distance) + 30,000 in the box",
                        "l2": "flushed (256 MiB write) before each step"},
             "evaluations_per_s": 1e3 / mean, "fp64_gpu_points_per_s": ts.T * 1e3 / t64,
-            "roofline": {"kernel": "whole evaluation (stokes_far_mixed_kernel with pressure dominant)",
+            "roofline": {"kernel": ("whole evaluation (stresslet_far_mixed_kernel dominant)" if dl else
+                                    "whole evaluation (stokes_far_mixed_kernel with pressure dominant)"),
                          "bound": "alu",
-                         "achieved": STOKES_P_FAR_FLOP_PER_PAIR * ts.n_far / (mean * 1e-3) / 1e12,
+                         "achieved": far_flop * ts.n_far / (mean * 1e-3) / 1e12,
                          "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
-                         "frac": STOKES_P_FAR_FLOP_PER_PAIR * ts.n_far / (mean * 1e-3) / 1e12 / FP32_PEAK_TFLOPS,
-                         "flop_per_pair": STOKES_P_FAR_FLOP_PER_PAIR, "traffic": None},
+                         "frac": far_flop * ts.n_far / (mean * 1e-3) / 1e12 / FP32_PEAK_TFLOPS,
+                         "flop_per_pair": far_flop, "traffic": None},
             "rel_err_vs_fp64_gpu": err, "gpu_launches": int(launches), "clocks": clk}
     ts.close()
     g.close()
@@ -1140,6 +1152,8 @@ def main():
         run_dirichlet200(args, ws, rank, lrank)
     elif args.workload == "stokespoints100":
         run_stokespoints100(args, ws, rank, lrank)
+    elif args.workload == "stokesdlpoints100":
+        run_stokespoints100(args, ws, rank, lrank, dl=True)
     elif args.workload == "stokesdl100":
         run_stokesdl100(args, ws, rank, lrank)
     else:

@@ -661,9 +661,23 @@ int sbio_eval_targets_stokes_dl(sbio_targets* ts, const double* q_hat, double* u
   if (T == 0) return SBIO_OK;
   SBIO_CUDA_TRY(cudaMemsetAsync(u_out, 0, T * 3 * sizeof(double), st));
   if ((rc = sdl_prep(g, q_hat, nullptr, st))) return rc;
-  if (n_pairs > 0) nl(*view, view->pair_t, view->pair_s, n_pro, n_pairs, u_out, st);
+  // near pairs on the geometry's high-priority stream beside the far field
+  // (as in the on-surface apply), unless phases are timed one by one
+  const bool fork = g->overlap && !g->timing && g->near_stream && n_pairs > 0;
+  if (fork) {
+    DevGeom v = *view;   // a copy: the near grid cap is per launch
+    v.near_grid_cap = sdl_near_cap(h) * sm_count();
+    SBIO_CUDA_TRY(cudaEventRecord(g->ev_fork, st));
+    SBIO_CUDA_TRY(cudaStreamWaitEvent(g->near_stream, g->ev_fork, 0));
+    nl(v, v.pair_t, v.pair_s, n_pro, n_pairs, u_out, g->near_stream);
+    SBIO_CUDA_TRY(cudaGetLastError());
+    SBIO_CUDA_TRY(cudaEventRecord(g->ev_join, g->near_stream));
+  } else if (n_pairs > 0) {
+    nl(*view, view->pair_t, view->pair_s, n_pro, n_pairs, u_out, st);
+  }
   launch_stresslet_far(*view, g->d, h, T, u_out, st);
   SBIO_CUDA_TRY(cudaGetLastError());
+  if (fork) SBIO_CUDA_TRY(cudaStreamWaitEvent(st, g->ev_join, 0));
   return SBIO_OK;
 }
 
