@@ -30,30 +30,84 @@ import time
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12     # SMs x FP32 lanes x FMA x max SM clock
-FP64_PEAK_TFLOPS = 1.25                               # nominal GB300 FP64 rate
-# MUFU rsqrt rate of the XU pipe: one warp instruction per 4 cycles per SM
-# sub-partition (ncu's XU peak), i.e. 32 per clock per SM
-SFU_PEAK_PER_S = 152 * 32 * 2.070e9
+# Roofline basis: the device's multiprocessor count and the median SM clock
+# sampled during the timed region (set by set_peak_basis; the defaults are
+# GB300's 152 SMs at the 2070 MHz maximum until a run has measured them).
+_PEAK_BASIS = {"sms": 152, "mhz": 2070.0, "source": "default: 152 SMs at 2070 MHz (not yet measured)"}
+FP64_NOMINAL_TFLOPS = 1.25                            # GB300 FP64 rate (datasheet), context only
+
+
+def set_peak_basis(device, clk):
+    """SM count from the device properties, clock from the sampled median
+    (nvidia-smi during the timed region), else the device's maximum."""
+    import torch
+
+    sms = torch.cuda.get_device_properties(device).multi_processor_count
+    mhz = clk["sm_mhz"] if clk and clk.get("sm_mhz") else 2070.0
+    _PEAK_BASIS.update(sms=sms, mhz=mhz,
+                       source=f"derived: {sms} SMs x 128 FP32 lanes x 2 flop x {mhz:.0f} MHz (median sampled SM clock)"
+                       if clk and clk.get("sm_mhz") else f"derived: {sms} SMs x 128 FP32 lanes x 2 flop x 2070 MHz")
+
+
+def fp32_peak():
+    """FP32 FMA peak in TFLOP/s: SMs x 128 lanes x 2 flop x clock."""
+    return _PEAK_BASIS["sms"] * 128 * 2 * _PEAK_BASIS["mhz"] * 1e6 / 1e12
+
+
+def sfu_peak():
+    """MUFU rsqrt peak per second: the XU pipe issues one warp instruction per
+    4 cycles per SM sub-partition (ncu's XU peak), i.e. 32 per clock per SM."""
+    return _PEAK_BASIS["sms"] * 32 * _PEAK_BASIS["mhz"] * 1e6
+
+
+_MEASURED = {}
+
+
+def measure_device_peaks(S, device):
+    """Pipe rates of this GPU from the library's microbenchmarks (measured
+    once per process, outside every timed region)."""
+    if not _MEASURED:
+        _MEASURED.update(S.sbio_measure_peaks(device))
+    return dict(_MEASURED)
+
+
+def fp64_peak():
+    """FP64 FMA peak in TFLOP/s: the measured DFMA rate when this process has
+    measured it, else the nominal 1.25 TFLOP/s."""
+    return _MEASURED.get("fp64_dfma_tflops") or FP64_NOMINAL_TFLOPS
+
+
+def fp64_peak_source():
+    return ("measured: FP64 FMA chains at full occupancy (sbio_measure_peaks)" if _MEASURED.get("fp64_dfma_tflops")
+            else "nominal GB300 FP64 1.25 TFLOP/s")
+
+
 FAR_FLOP_PER_PAIR = {"SD": 19, "S": 10, "D": 14}
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one launch of
 # the mixed S+D far kernel on the 200-spheroid p = 16 suspension, from one ncu
 # capture per launch shape (targets per thread, source splits) of the current
-# kernel code; other shapes report null
-FAR_DRAM_BYTES_POLY200 = {(-8, 44): 11.57e6}
+# kernel code, with the profile summary it comes from; other shapes report null
+FAR_DRAM_BYTES_POLY200 = {(-8, 44): (11.57e6, "profiles/far_mixed_packed_expanded_poly200.md")}
 # the same for the mixed S' + D' far kernel (packed, expanded distance)
-DERIV_FAR_DRAM_BYTES_POLY200 = {(-8, 44): 14.35e6}
+DERIV_FAR_DRAM_BYTES_POLY200 = {(-8, 44): (14.35e6, "profiles/far_deriv_packed_poly200.md")}
 
 
 def near_flop_per_pair(p: int) -> int:
-    """Algorithmic FP64 flops of one near (target, source) pair for S and D:
-    the two contractions (FMA over (p+1)^2 coefficients each), the radial x
-    angular product per (n, |m|), the order recurrence of Q (3 flops) and the
-    Ferrers recurrence (4 flops) per (n, |m|), and about 12 flops of angle
-    recurrence and cos/sin combination per order m.  The data-dependent Miller
-    start of Q_n^0, Q_n^1 is not counted."""
+    """Algorithmic FP64 flops of one near (target, source) pair for S and D
+    without its data-dependent Miller start: the two contractions (FMA over
+    (p+1)^2 coefficients each), the radial x angular product per (n, |m|),
+    the order recurrence of Q (3 flops) and the Ferrers recurrence (4 flops)
+    per (n, |m|), about 12 flops of angle recurrence and cos/sin combination
+    per order m, about 40 for the local and spheroidal coordinates, and the
+    unrolled part of the two Miller sweeps (p + 2 steps of two three-term
+    recurrences, 6 flops each, and the normalisation of 2 (p + 2) values)."""
     nm = (p + 1) * (p + 2) // 2
-    return 4 * (p + 1) ** 2 + nm * (1 + 3 + 4) + 12 * (p + 1)
+    return 4 * (p + 1) ** 2 + nm * (1 + 3 + 4) + 12 * (p + 1) + 40 + 12 * (p + 2) + 2 * (p + 2)
+
+
+# one rolled Miller step (m = 0 and m = 1 together): 5 + 4 flops for the two
+# recurrences (FMA = 2) and 2 for the running index and (2n + 1) u
+MILLER_FLOP_PER_STEP = 11
 METRIC = "BIO applies/s (Laplace S+D, all surface nodes)"
 # far pair of S' + D': 3 sub, 5 (r^2), 2 (r^-2, r^-3), 5 (r.nu_x), 3 (S' product
 # and FMA), 5 (d.r), 5 (d.nu_x), 2 (products), 2 + 2 (the two FMAs) = 34
@@ -89,14 +143,20 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64-context", action="store_true")
     ap.add_argument("--no-all-cores", action="store_true", help="skip the all-cores oracle timing")
-    ap.add_argument("--oracle-sample", type=int, default=48, help="targets in the oracle's timed sample")
+    ap.add_argument("--oracle-sample", type=int, default=96, help="targets in the oracle's timed sample")
     ap.add_argument("--far-shape", default="", help="TT,SPLITS: fixed far-field launch shape (skips the autotuner)")
     ap.add_argument("--workload", default="poly200",
                     choices=["poly200", "stokes100", "batch64", "serve", "deriv200", "targets200", "derivpoints200",
-                             "dirichlet200", "stokespoints100", "stokesdl100", "stokesdlpoints100"])
-    ap.add_argument("--rates", default="50,100,200,500,1000,2000", help="serve: arrival rates (req/s)")
-    ap.add_argument("--requests", type=int, default=48, help="serve: requests per rate")
+                             "dirichlet200", "stokespoints100", "stokesdl100", "stokesdlpoints100",
+                             "lattice8", "far_sweep"])
+    ap.add_argument("--rates", default="2,5,10,20,30,50,200", help="serve: arrival rates (req/s)")
+    ap.add_argument("--requests", type=int, default=600, help="serve: at most this many requests per rate")
     ap.add_argument("--slots", type=int, default=4, help="serve: concurrent request slots")
+    ap.add_argument("--serve-seconds", type=float, default=20.0, help="serve: arrival window per rate (s)")
+    ap.add_argument("--serve-pool", type=int, default=32, help="serve: distinct suspensions drawn for the stream")
+    ap.add_argument("--headline-only", action="store_true",
+                    help="poly200: skip the batched, served and Stokes sub-objects")
+    ap.add_argument("--sweep-M", default="200,500,1000,2000", help="far_sweep: particle counts")
     return ap.parse_args()
 
 
@@ -177,11 +237,31 @@ class ClockSampler:
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def oracle_sample_time(npz_path, n_sample, p_threads=1, seed=1, start_at=None):
-    """Time the oracle's O-method apply on a bounded sample of targets in a
-    fresh single-threaded process; returns (seconds, targets, N).  With
-    start_at (a time.time() value) the process waits until then before the
-    timed part, so that several processes run it together."""
+def stratified_targets(near_count, n, offset=0.5, seed=0):
+    """n targets spread evenly over the targets ordered by their number of
+    near particles (ties in a seeded random order), so near-heavy and
+    far-only targets enter the sample in proportion; `offset` in (0, 1)
+    shifts the picks, giving disjoint samples for different offsets."""
+    import numpy as np
+
+    N = len(near_count)
+    perm = np.random.default_rng(seed).permutation(N)
+    order = perm[np.argsort(near_count[perm], kind="stable")]
+    pick = np.minimum(((np.arange(n) + offset) * N / n).astype(np.int64), N - 1)
+    return np.sort(order[pick])
+
+
+def oracle_sample_time(npz_path, targets, start_at=None):
+    """Time the oracle's O-method apply on the given targets in a fresh
+    single-threaded process (the near sets of the sample are computed before
+    the timed part); returns (seconds, targets, N).  With start_at (a
+    time.time() value) the process waits until then before the timed part,
+    so that several processes run it together."""
+    import numpy as np
+
+    fd, tpath = tempfile.mkstemp(suffix=".npy")
+    os.close(fd)
+    np.save(tpath, np.asarray(targets, dtype=np.int64))
     code = f"""
 import os, sys, time, json
 import numpy as np
@@ -192,7 +272,7 @@ d = np.load({npz_path!r})
 s = I.Suspension(d['kind'], d['A'], d['C'], d['center'], d['quat'], int(d['p']))
 og = OG.SuspensionGeom.from_suspension(s)
 O = OL.LaplaceOracle(og)
-tg = np.sort(np.random.default_rng({seed}).choice(og.N, {n_sample}, replace=False))
+tg = np.load({tpath!r})
 near = og.near_matrix(tg)
 og.near_matrix = lambda targets=None: near
 start_at = {start_at!r}
@@ -203,27 +283,49 @@ O.apply(d['sig'], d['mu'], 'method', targets=tg)
 t1 = time.perf_counter()
 print(json.dumps({{"seconds": t1 - t0, "targets": len(tg), "N": og.N}}))
 """
-    env = dict(os.environ, OMP_NUM_THREADS=str(p_threads), OPENBLAS_NUM_THREADS=str(p_threads),
-               MKL_NUM_THREADS=str(p_threads), CUDA_VISIBLE_DEVICES="")
-    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env)
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
+               CUDA_VISIBLE_DEVICES="")
+    try:
+        r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env)
+    finally:
+        os.unlink(tpath)
     if r.returncode != 0:
         raise RuntimeError(r.stderr[-2000:])
     out = json.loads(r.stdout.strip().splitlines()[-1])
     return out["seconds"], out["targets"], out["N"]
 
 
-def oracle_all_cores(npz_path, n_sample, cores):
-    """The same oracle sample on `cores` concurrent single-threaded processes
-    (disjoint random target samples), started together; returns
-    (targets per second over all processes, wall seconds, processes)."""
+def oracle_all_cores(npz_path, near_count, n_sample, cores):
+    """The oracle on `cores` concurrent single-threaded processes, each on
+    its own stratified sample of n_sample targets (disjoint picks), started
+    together; returns (targets per second over all processes, wall seconds,
+    processes)."""
     import concurrent.futures as cf
 
-    start_at = time.time() + 20.0       # after every process has loaded numpy and the geometry
+    start_at = time.time() + 30.0       # after every process has loaded numpy and the geometry
+    samples = [stratified_targets(near_count, n_sample, offset=(k + 0.5) / cores, seed=1) for k in range(cores)]
     with cf.ThreadPoolExecutor(cores) as ex:
-        res = list(ex.map(lambda k: oracle_sample_time(npz_path, n_sample, 1, seed=100 + k, start_at=start_at),
-                          range(cores)))
+        res = list(ex.map(lambda k: oracle_sample_time(npz_path, samples[k], start_at=start_at), range(cores)))
     wall = max(r[0] for r in res)
     return sum(r[1] for r in res) / wall, wall, cores
+
+
+def cpu_model():
+    """CPU model name from lscpu (or /proc/cpuinfo), for the CPU baseline."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith(("model name", "cpu model")):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    return "unknown"
 
 
 def make_workload():
@@ -259,10 +361,16 @@ def config_dict(susp, n_near, n_far, N):
 def run_reference(args, ws, rank):
     if rank != 0:
         return
+    import numpy as np
+
+    from oracle import geometry as OG
+
     susp, coef, path = make_workload()
+    near_count = OG.SuspensionGeom.from_suspension(susp).near_matrix().sum(axis=1)
     times = []
     for k in range(args.warmup + args.steps):
-        sec, nt, N = oracle_sample_time(path, args.oracle_sample)
+        tg = stratified_targets(near_count, args.oracle_sample, offset=(k + 0.5) / (args.warmup + args.steps))
+        sec, nt, N = oracle_sample_time(path, tg)
         if k >= args.warmup:
             times.append(sec * N / nt)       # seconds per full apply
     os.unlink(path)
@@ -272,14 +380,20 @@ def run_reference(args, ws, rank):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": per_apply * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": "poly200_p16_laplace_SD", "M": susp.M, "p": susp.p,
-                       "sample": f"{args.oracle_sample} random targets per step, scaled to all {N}"},
-            "cpu_baseline": {"value": val, "unit": "applies/s", "cores": 1, "kind": "oracle",
-                             "sample": f"{args.oracle_sample} of {N} targets per step, single thread"},
+                       "sample": f"{args.oracle_sample} stratified targets per step (by near-particle count), "
+                                 f"scaled to all {N}"},
+            "cpu_baseline": {"value": val, "unit": "applies/s", "cores": 1, "kind": "oracle", "cpu": cpu_model(),
+                             "sample": f"{args.oracle_sample} of {N} targets per step, stratified by near-particle "
+                                       f"count, single thread"},
             "e2e": {"value": val, "unit": "applies/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
 
 def run_ours(args, ws, rank, lrank):
+    """The headline line: poly200 S + D applies/s (device-timed, L2 flushed),
+    end to end through the host-memory entry point, the far and near
+    rooflines against derived and measured peaks, the FP64 GPU form and the
+    oracle's CPU time.  Returns the line (printed by the caller)."""
     import numpy as np
     import torch
 
@@ -294,6 +408,7 @@ def run_ours(args, ws, rank, lrank):
     ctx = S.sbio_ctx_create(lrank, 0)
     prec = S.SBIO_MIXED if args.precision == "mixed" else S.SBIO_FP64
     geom = S.Geometry(ctx, susp, precision=prec)
+    peaks = measure_device_peaks(S, lrank)
     if args.far_shape:
         tt, sp = (int(x) for x in args.far_shape.split(","))
         S.sbio_geom_set_launch_shape(geom.h, tt, sp)
@@ -302,7 +417,10 @@ def run_ours(args, ws, rank, lrank):
         tune = S.sbio_geom_autotune(geom.h)
     tuning = S.sbio_geom_get_tuning(geom.h)
     setup_ms = S.sbio_geom_setup_times(geom.h)
+    n_pairs, miller_steps = S.sbio_geom_near_work(geom.h)
+    near_t, _ = S.sbio_geom_near_pairs(geom.h)
     N = geom.N
+    near_count = np.bincount(near_t, minlength=N)
     sig = torch.from_numpy(coef[0]).to(dev)
     mu = torch.from_numpy(coef[1]).to(dev)
     So = torch.empty(N, dtype=torch.float64, device=dev)
@@ -330,6 +448,7 @@ def run_ours(args, ws, rank, lrank):
     launches = S.sbio_launch_count() - l0
     barrier(ws)
     clk = clocks.stop()
+    set_peak_basis(lrank, clk)
     step_ms = [e0.elapsed_time(e1) for e0, e1 in evs]
     total_s = allmax(ws, sum(step_ms) / 1e3)
     value = args.steps * ws / total_s
@@ -396,6 +515,12 @@ def run_ours(args, ws, rank, lrank):
     far_mean = statistics.mean(far_ms)
     far_flop = FAR_FLOP_PER_PAIR["SD"] * geom.n_far
     achieved = far_flop / (far_mean * 1e-3) / 1e12
+    pk32 = fp32_peak() if prec == S.SBIO_MIXED else fp64_peak()
+    traffic = FAR_DRAM_BYTES_POLY200.get((tune[0], tune[1])) if prec == S.SBIO_MIXED else None
+    near_mean = statistics.mean(near_ms)
+    near_fixed = near_flop_per_pair(susp.p)
+    near_flop = near_fixed * n_pairs + MILLER_FLOP_PER_STEP * miller_steps
+    near_ach = near_flop / (near_mean * 1e-3) / 1e12
     lat = sorted(step_ms)
     line = {
         "metric": METRIC, "value": value, "unit": "applies/s", "n_gpus": ws, "steps": args.steps,
@@ -407,28 +532,40 @@ def run_ours(args, ws, rank, lrank):
                                                         "near_ctas_per_sm_overlapped": tuning["near_ctas_per_sm"]}),
         "gpairs_per_s": geom.n_far / (statistics.mean(step_ms) * 1e-3) / 1e9,
         "latency_ms": {"p50": lat[len(lat) // 2], "p99": lat[min(len(lat) - 1, int(0.99 * len(lat)))]},
-        "phase_ms": {"synth": statistics.mean(synth_ms), "near": statistics.mean(near_ms), "far": far_mean,
+        "phase_ms": {"synth": statistics.mean(synth_ms), "near": near_mean, "far": far_mean,
                      "in_order_apply": statistics.mean(inorder_ms)},
         "roofline": {"kernel": "far_mixed_kernel" if prec == S.SBIO_MIXED else "far_fp64_kernel",
-                     "bound": "alu", "achieved": achieved,
-                     "peak": FP32_PEAK_TFLOPS if prec == S.SBIO_MIXED else FP64_PEAK_TFLOPS,
-                     "unit": "TFLOP/s", "frac": achieved / (FP32_PEAK_TFLOPS if prec == S.SBIO_MIXED else FP64_PEAK_TFLOPS),
-                     "traffic": (FAR_DRAM_BYTES_POLY200.get((tune[0], tune[1]))
-                                 if prec == S.SBIO_MIXED and args.workload == "poly200" else None),
-                     "traffic_unit": "bytes per launch (ncu dram read + write, one capture at this launch shape)",
+                     "bound": "alu", "achieved": achieved, "peak": pk32, "unit": "TFLOP/s",
+                     "frac": achieved / pk32,
+                     "traffic": traffic[0] if traffic else None,
+                     "traffic_source": (f"{traffic[1]} (ncu dram read + write, one capture at this launch shape)"
+                                        if traffic else None),
                      "algorithmic_bytes": None,
-                     "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz" if prec == S.SBIO_MIXED
-                     else "nominal FP64 1.25 TFLOP/s"},
+                     "flop_per_pair": FAR_FLOP_PER_PAIR["SD"], "pairs_per_launch": geom.n_far,
+                     "peak_source": _PEAK_BASIS["source"] if prec == S.SBIO_MIXED else fp64_peak_source(),
+                     "measured_peaks": {
+                         "ffma2_tflops": peaks["fp32_ffma2_tflops"],
+                         "frac_of_measured_ffma2": achieved / peaks["fp32_ffma2_tflops"],
+                         "pairmix_pairs_per_s": peaks["pairmix_pairs_per_s"],
+                         "frac_of_pairmix": geom.n_far / (far_mean * 1e-3) / peaks["pairmix_pairs_per_s"],
+                         "note": "measured by sbio_measure_peaks on this GPU: f32x2 FMA chains, and the packed far "
+                                 "pair's register arithmetic (11 f32x2 + 2 MUFU per 2 pairs) with no memory "
+                                 "traffic"} if prec == S.SBIO_MIXED else None},
         "sfu": {"kernel": "far_mixed_kernel" if prec == S.SBIO_MIXED else "far_fp64_kernel",
-                "unit": "rsqrt/s", "achieved": geom.n_far / (far_mean * 1e-3), "peak": SFU_PEAK_PER_S,
-                "frac": geom.n_far / (far_mean * 1e-3) / SFU_PEAK_PER_S,
+                "unit": "rsqrt/s", "achieved": geom.n_far / (far_mean * 1e-3), "peak": sfu_peak(),
+                "frac": geom.n_far / (far_mean * 1e-3) / sfu_peak(),
+                "measured_peak": peaks["rsqrt_per_s"],
+                "frac_of_measured": geom.n_far / (far_mean * 1e-3) / peaks["rsqrt_per_s"],
                 "note": "one rsqrt per far pair; FP32 MUFU in the mixed form"},
-        "roofline_near": {"kernel": "near_kernel", "bound": "alu", "unit": "TFLOP/s",
-                          "achieved": near_flop_per_pair(susp.p) * geom.n_near / (statistics.mean(near_ms) * 1e-3) / 1e12,
-                          "peak": FP64_PEAK_TFLOPS,
-                          "frac": near_flop_per_pair(susp.p) * geom.n_near / (statistics.mean(near_ms) * 1e-3) / 1e12
-                          / FP64_PEAK_TFLOPS, "flop_per_pair": near_flop_per_pair(susp.p),
-                          "peak_source": "nominal GB300 FP64 1.25 TFLOP/s"},
+        "roofline_near": {"kernel": "near_kernel", "bound": "alu", "unit": "TFLOP/s", "achieved": near_ach,
+                          "peak": fp64_peak(), "frac": near_ach / fp64_peak(),
+                          "frac_of_nominal": near_ach / FP64_NOMINAL_TFLOPS,
+                          "flop_per_pair": near_flop / max(1, n_pairs),
+                          "flop_count": f"{near_fixed} per pair without the Miller start + {MILLER_FLOP_PER_STEP} per "
+                                        f"rolled Miller step ({miller_steps} steps over {n_pairs} pairs, counted "
+                                        f"by sbio_geom_near_work)",
+                          "peak_source": fp64_peak_source()},
+        "measured_peaks": peaks,
         "e2e": {"value": e2e_val, "unit": "applies/s", "h2d_bytes_per_step": int(hs.nbytes + hm.nbytes),
                 "d2h_bytes_per_step": int(hS.nbytes + hD.nbytes)},
         "gpu_launches": int(launches),
@@ -440,20 +577,22 @@ def run_ours(args, ws, rank, lrank):
     geom.close()
     S.sbio_ctx_destroy(ctx)
     if rank == 0 and not args.no_cpu_baseline:
-        sec, nt, NN = oracle_sample_time(path, args.oracle_sample)
+        tg = stratified_targets(near_count, args.oracle_sample)
+        sec, nt, NN = oracle_sample_time(path, tg)
         per_apply = sec * NN / nt
         line["cpu_baseline"] = {"value": 1.0 / per_apply, "unit": "applies/s", "cores": 1, "kind": "oracle",
-                                "sample": f"{nt} random targets of {NN} ({sec:.1f} s), scaled to a full apply"}
-        cores = max(1, min(os.cpu_count() or 1, 16))
+                                "cpu": cpu_model(),
+                                "sample": f"{nt} of {NN} targets stratified by near-particle count ({sec:.1f} s), "
+                                          f"scaled to a full apply"}
+        cores = os.cpu_count() or 1
         if cores > 1 and not args.no_all_cores:
-            tps, wall, nproc = oracle_all_cores(path, args.oracle_sample, cores)
+            tps, wall, nproc = oracle_all_cores(path, near_count, args.oracle_sample, cores)
             line["cpu_baseline_all_cores"] = {
-                "value": tps / NN, "unit": "applies/s", "cores": nproc, "kind": "oracle",
-                "sample": f"{nproc} concurrent single-threaded processes, {args.oracle_sample} targets each "
-                          f"({wall:.1f} s wall), scaled to a full apply"}
+                "value": tps / NN, "unit": "applies/s", "cores": nproc, "kind": "oracle", "cpu": cpu_model(),
+                "sample": f"{nproc} concurrent single-threaded processes (os.cpu_count()), {args.oracle_sample} "
+                          f"stratified targets each, disjoint ({wall:.1f} s wall), scaled to a full apply"}
     os.unlink(path)
-    if rank == 0:
-        print(json.dumps(line), flush=True)
+    return line
 
 
 def _event_time(stream, fn):
@@ -498,6 +637,7 @@ def run_stokes100(args, ws, rank, lrank):
         ms.append(_event_time(st, lambda: S.sbio_apply_stokes_sl(g.h, fd, u)))
     launches = S.sbio_launch_count() - l0
     clk = clocks.stop()
+    set_peak_basis(lrank, clk)
     # end to end through the host entry point: pinned host forces in, velocities out
     fh = torch.from_numpy(f).pin_memory()
     uh = torch.empty((g.N, 3), dtype=torch.float64).pin_memory()
@@ -538,13 +678,12 @@ def run_stokes100(args, ws, rank, lrank):
             "phase_ms": {"prep_and_self": statistics.mean(x[0] for x in ph), "near": statistics.mean(x[1] for x in ph),
                          "far": far_ms},
             "roofline": {"kernel": "stokes_far_mixed_kernel", "bound": "alu", "achieved": ach,
-                         "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": ach / FP32_PEAK_TFLOPS,
+                         "peak": fp32_peak(), "unit": "TFLOP/s", "frac": ach / fp32_peak(),
                          "flop_per_pair": STOKES_FAR_FLOP_PER_PAIR, "traffic": None},
             "fp64_gpu_applies_per_s": 1e3 / t64, "rel_err_vs_fp64_gpu": err, "gpu_launches": int(launches),
             "clocks": clk}
     g.close()
-    if rank == 0:
-        print(json.dumps(line), flush=True)
+    return line
 
 
 def run_batch64(args, ws, rank, lrank):
@@ -594,6 +733,7 @@ def run_batch64(args, ws, rank, lrank):
         ms.append(_event_time(st, lambda: S.sbio_batch_apply(b, sig, mu, So, Do)))
     launches = S.sbio_launch_count() - l0
     clk = clocks.stop()
+    set_peak_basis(lrank, clk)
     info = S.sbio_batch_info(b)
     # the same work as one apply per suspension, one after another (mixed)
     seq = _event_time(st, lambda: [S.sbio_apply_laplace(g.h, sig[k], mu[k], So[k], Do[k]) for k, g in enumerate(geoms)])
@@ -614,36 +754,36 @@ def run_batch64(args, ws, rank, lrank):
             "gpairs_per_s": info["far_pairs"] / (mean * 1e-3) / 1e9,
             "roofline": {"kernel": "whole step (far_persistent_kernel dominant)", "bound": "alu",
                          "achieved": FAR_FLOP_PER_PAIR["SD"] * info["far_pairs"] / (mean * 1e-3) / 1e12,
-                         "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
-                         "frac": FAR_FLOP_PER_PAIR["SD"] * info["far_pairs"] / (mean * 1e-3) / 1e12 / FP32_PEAK_TFLOPS,
+                         "peak": fp32_peak(), "unit": "TFLOP/s",
+                         "frac": FAR_FLOP_PER_PAIR["SD"] * info["far_pairs"] / (mean * 1e-3) / 1e12 / fp32_peak(),
                          "flop_per_pair": FAR_FLOP_PER_PAIR["SD"], "traffic": None},
-            "sequential_mixed_ms": seq, "fp64_plain_ms": f64,
+            "sequential_mixed_ms": seq, "fp64_plain_ms": f64, "fp64_plain_applies_per_s": len(geoms) * 1e3 / f64,
             "speedup_vs_fp64_plain": f64 / mean, "speedup_vs_sequential_mixed": seq / mean,
             "gpu_launches": int(launches), "clocks": clk}
     S.sbio_batch_destroy(b)
-    if rank == 0:
-        print(json.dumps(line), flush=True)
+    return line
 
 
 def run_serve(args, ws, rank, lrank):
-    import math
+    """Served form: a Poisson stream of BIO-apply requests (Laplace S + D or
+    Stokes single layer with probability 1/2, 10 applies each with fresh
+    coefficients) into the library's continuous-batching server.  Every
+    request brings its own geometry: a suspension of the pool (M log-uniform
+    in [20, 500], p from {8, 12, 16}) moved by a seeded random rigid motion,
+    so the server builds a new geometry for every request, inside the
+    request's latency.  Rates span below and above the saturation knee; per
+    rate the stream runs `--serve-seconds` of arrivals (at most `--requests`
+    requests).  The plain FP64 server and the mixed server run the same
+    eight requests submitted together (throughput at saturation)."""
+    import queue
+    import threading
+
     import numpy as np
     import torch
 
     from paper_2506_20809_gb300 import inputs as I
 
-    # a pool of request geometries (drawn before CUDA starts), sampled by the stream
-    rng = np.random.default_rng(2024)
-    specs = []
-    for k in range(16):
-        M = int(round(math.exp(rng.uniform(math.log(20), math.log(500)))))
-        specs.append((M, int(rng.choice([8, 12, 16]))))
-    import concurrent.futures as cf
-    import multiprocessing as mp
-
-    with cf.ProcessPoolExecutor(max_workers=min(16, os.cpu_count() or 1), mp_context=mp.get_context("spawn")) as ex:
-        pool = list(ex.map(I.rsa_suspension, [m for m, _ in specs], [0.20] * 16, range(1000, 1016),
-                           [p for _, p in specs]))
+    pool = I.serve_pool(args.serve_pool, seed=0, workers=min(32, os.cpu_count() or 1))   # before CUDA starts
     import __graft_entry__ as GE
 
     GE.build()
@@ -653,84 +793,93 @@ def run_serve(args, ws, rank, lrank):
     ctx = S.sbio_ctx_create(lrank, 0)
     free, total = torch.cuda.mem_get_info()
     budget = int(0.5 * free)
+    # ten coefficient sets per pool member, per operator (read-only, shared by its requests)
+    crng = np.random.default_rng([rank, 4242])
+    coefs = []
+    for s in pool:
+        lap = np.ascontiguousarray(np.stack([I.coefficients(crng, s.M, s.p, 2).transpose(1, 0, 2)
+                                             for _ in range(10)]))
+        sto = np.ascontiguousarray(np.stack([I.coefficients(crng, s.M, s.p, 3) for _ in range(10)]))
+        coefs.append((lap, sto))
 
-    def stream_of(rate, seed, precision, n_req):
-        reqs = I.poisson_requests(rate, 1e9, seed=seed, M_range=(20, 500), max_requests=n_req)
-        prepared = []
-        for k, r in enumerate(reqs):
-            s = pool[r["seed"] % len(pool)]
-            op = S.SBIO_OP_LAPLACE if r["op"] == "laplace" else S.SBIO_OP_STOKES
-            N = s.M * (s.p + 1) * 2 * (s.p + 1)
-            nc = (s.p + 1) ** 2
-            crng = np.random.default_rng([seed, k])
-            if op == S.SBIO_OP_LAPLACE:
-                coef = np.ascontiguousarray(np.stack([I.coefficients(crng, s.M, s.p, 2).transpose(1, 0, 2)
-                                                      for _ in range(10)]))
-                out = np.zeros((10, 2 * N))
-            else:
-                coef = np.ascontiguousarray(np.stack([I.coefficients(crng, s.M, s.p, 3) for _ in range(10)]))
-                out = np.zeros((10, N, 3))
-            sph = S.make_spheroids(s.kind, s.A, s.C, s.center, s.quat)
-            prepared.append((r["t"], op, sph, s.p, coef, out))
+    def request(k, op_is_laplace):
+        s = I.rigid_motion(pool[k % len(pool)], seed=k)
+        sph = S.make_spheroids(s.kind, s.A, s.C, s.center, s.quat)
+        N = s.M * (s.p + 1) * 2 * (s.p + 1)
+        lap, sto = coefs[k % len(pool)]
+        if op_is_laplace:
+            return S.SBIO_OP_LAPLACE, sph, s.p, lap, (10, 2 * N)
+        return S.SBIO_OP_STOKES, sph, s.p, sto, (10, N, 3)
+
+    def run_stream(arrivals, precision):
+        """arrivals: list of (t, k, op_is_laplace).  Returns latencies (ms)
+        and the makespan (s) from the first arrival to the last result."""
         srv = S.sbio_server_create(ctx, args.slots, budget)
+        done = queue.Queue()
+        lat = []
+
+        def waiter():
+            while True:
+                item = done.get()
+                if item is None:
+                    return
+                t, keep = item
+                st, l, _ = S.sbio_server_wait(srv, t, 3600.0)
+                assert st == 0, st
+                lat.append(l)
+                del keep                      # the request's host buffers can go now
+
+        th = threading.Thread(target=waiter)
+        th.start()
+        prepared = [(ta,) + request(k, lapl) for ta, k, lapl in arrivals]
         t0 = time.perf_counter()
-        tickets = []
-        for (ta, op, sph, p, coef, out) in prepared:
+        for ta, op, sph, p, coef, oshape in prepared:
             delay = t0 + ta - time.perf_counter()
             if delay > 0:
                 time.sleep(delay)
-            tickets.append(S.sbio_server_submit(srv, op, sph, p, coef, out, 10, precision=precision))
-        lat = []
-        for t in tickets:
-            stt, l, svc = S.sbio_server_wait(srv, t, 3600.0)
-            assert stt == 0
-            lat.append(l)
+            out = np.empty(oshape)
+            t = S.sbio_server_submit(srv, op, sph, p, coef, out, 10, precision=precision)
+            done.put((t, (out, sph)))
+        done.put(None)
+        th.join()
         makespan = time.perf_counter() - t0
         S.sbio_server_destroy(srv)
-        lat.sort()
-        return {"rate": rate, "requests": len(lat), "applies_per_s": 10 * len(lat) / makespan,
-                "p50_ms": lat[len(lat) // 2], "p99_ms": lat[min(len(lat) - 1, int(0.99 * len(lat)))],
-                "makespan_s": makespan}
-
-    # where a request's time goes: geometry set-up (host phases) against its
-    # ten applies (Laplace S + D, mixed, one at a time)
-    prof = []
-    st = torch.cuda.current_stream()
-    for s in pool:
-        t0 = time.perf_counter()
-        g = S.Geometry(ctx, s, precision=S.SBIO_MIXED)
-        torch.cuda.synchronize()
-        create_ms = (time.perf_counter() - t0) * 1e3
-        host, near, dev = S.sbio_geom_setup_times(g.h)
-        c = I.config_coefficients(s, 0)
-        sg, mg = torch.from_numpy(c[0]).cuda(), torch.from_numpy(c[1]).cuda()
-        So = torch.empty(g.N, dtype=torch.float64, device="cuda")
-        Do = torch.empty_like(So)
-        S.sbio_apply_laplace(g.h, sg, mg, So, Do)
-        ap = _event_time(st, lambda: [S.sbio_apply_laplace(g.h, sg, mg, So, Do) for _ in range(10)])
-        prof.append({"M": s.M, "p": s.p, "create_ms": create_ms, "host_nodes_ms": host, "near_sets_ms": near,
-                     "device_tables_ms": dev, "ten_applies_ms": ap})
-        g.close()
-    profile = {"geometries": prof, "total_create_ms": sum(x["create_ms"] for x in prof),
-               "total_ten_applies_ms": sum(x["ten_applies_ms"] for x in prof)}
+        return sorted(lat), makespan
 
     rates = [float(x) for x in args.rates.split(",")]
-    rows = [stream_of(r, 7, S.SBIO_MIXED, args.requests) for r in rates]
-    ref = stream_of(rates[-1], 7, S.SBIO_FP64, min(12, args.requests))
-    mixed_same = stream_of(rates[-1], 7, S.SBIO_MIXED, min(12, args.requests))
-    best = max(rows, key=lambda r: r["applies_per_s"])
+    rows = []
+    for rate in rates:
+        reqs = I.poisson_requests(rate, args.serve_seconds, seed=7, max_requests=args.requests)
+        arrivals = [(r["t"], r["seed"], r["op"] == "laplace") for r in reqs]
+        lat, makespan = run_stream(arrivals, S.SBIO_MIXED)
+        rows.append({"rate": rate, "requests": len(lat), "window_s": args.serve_seconds,
+                     "applies_per_s": 10 * len(lat) / makespan,
+                     "p50_ms": lat[len(lat) // 2], "p99_ms": lat[min(len(lat) - 1, int(0.99 * len(lat)))],
+                     "makespan_s": makespan})
+    # the knee: the highest rate whose median latency stays within 1.5x of the lowest rate's
+    base = rows[0]["p50_ms"]
+    flat = [r["rate"] for r in rows if r["p50_ms"] <= 1.5 * base]
+    sat = max(rows, key=lambda r: r["applies_per_s"])
+    eight = [(0.0, 900 + k, k % 2 == 0) for k in range(8)]
+    lat64, mk64 = run_stream(eight, S.SBIO_FP64)
+    latm, mkm = run_stream(eight, S.SBIO_MIXED)
     line = {"metric": "served BIO applies/s (Poisson stream, 10 applies per request) and p50/p99 latency",
-            "value": best["applies_per_s"], "unit": "applies/s", "n_gpus": ws, "steps": len(rates),
+            "value": sat["applies_per_s"], "unit": "applies/s", "n_gpus": ws, "steps": len(rates),
             "warmup": 0, "ms_per_step": None, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f32+f64", "data": "synthetic",
-            "config": {"workload": "serve", "slots": args.slots, "requests_per_rate": args.requests,
-                       "pool": [{"M": m, "p": p} for m, p in specs], "mem_budget_bytes": budget,
-                       "ops": "Laplace S+D or Stokes single layer, probability 1/2"},
-            "sweep": rows, "pool_profile": profile, "fp64_plain_at_max_rate": ref,
-            "mixed_same_requests_as_fp64": mixed_same,
-            "speedup_vs_fp64_plain": mixed_same["applies_per_s"] / ref["applies_per_s"]}
-    if rank == 0:
-        print(json.dumps(line), flush=True)
+            "config": {"workload": "serve", "slots": args.slots, "window_s_per_rate": args.serve_seconds,
+                       "max_requests_per_rate": args.requests, "pool": [{"M": s.M, "p": s.p} for s in pool],
+                       "request_geometry": "pool suspension moved by a seeded random rigid motion (new geometry "
+                                           "built by the server inside every request's latency)",
+                       "mem_budget_bytes": budget, "ops": "Laplace S+D or Stokes single layer, probability 1/2"},
+            "sweep": rows,
+            "knee": {"flat_up_to_rate": max(flat), "p50_ms_at_lowest_rate": base,
+                     "saturation_applies_per_s": sat["applies_per_s"]},
+            "fp64_plain": {"requests": 8, "applies_per_s": 80 / mk64, "p50_ms": lat64[4]},
+            "mixed_same_requests": {"requests": 8, "applies_per_s": 80 / mkm, "p50_ms": latm[4]},
+            "speedup_vs_fp64_plain": mk64 / mkm}
+    S.sbio_ctx_destroy(ctx)
+    return line
 
 
 def run_deriv200(args, ws, rank, lrank):
@@ -766,6 +915,7 @@ def run_deriv200(args, ws, rank, lrank):
         ms.append(_event_time(st, lambda: S.sbio_apply_laplace_deriv(g.h, sg, mg, Sp, Dp)))
     launches = S.sbio_launch_count() - l0
     clk = clocks.stop()
+    set_peak_basis(lrank, clk)
     S.sbio_geom_enable_timing(g.h, True)
     ph = []
     for _ in range(min(args.steps, 10)):
@@ -790,15 +940,14 @@ def run_deriv200(args, ws, rank, lrank):
             "phase_ms": {"self": statistics.mean(x[0] for x in ph), "near": statistics.mean(x[1] for x in ph),
                          "far": far_ms},
             "roofline": {"kernel": "far_deriv_mixed_kernel", "bound": "alu", "achieved": ach,
-                         "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": ach / FP32_PEAK_TFLOPS,
+                         "peak": fp32_peak(), "unit": "TFLOP/s", "frac": ach / fp32_peak(),
                          "flop_per_pair": DERIV_FAR_FLOP_PER_PAIR,
                          "traffic": DERIV_FAR_DRAM_BYTES_POLY200.get((dtune[0], dtune[1])),
                          "traffic_unit": "bytes per launch (ncu dram read + write, one capture at this launch shape)"},
             "fp64_gpu_applies_per_s": 1e3 / t64, "rel_err_vs_fp64_gpu": err, "gpu_launches": int(launches),
             "clocks": clk}
     g.close()
-    if rank == 0:
-        print(json.dumps(line), flush=True)
+    return line
 
 
 def run_targets200(args, ws, rank, lrank, deriv=False):
@@ -854,6 +1003,7 @@ def run_targets200(args, ws, rank, lrank, deriv=False):
         ms.append(_event_time(st, step))
     launches = S.sbio_launch_count() - l0
     clk = clocks.stop()
+    set_peak_basis(lrank, clk)
     som, dom = So.clone(), Do.clone()
     S.sbio_geom_set_precision(g.h, S.SBIO_FP64)
     step()
@@ -876,14 +1026,13 @@ def run_targets200(args, ws, rank, lrank, deriv=False):
             "evaluations_per_s": 1e3 / mean, "target_set_setup_ms": setup_ms,
             "roofline": {"kernel": "whole evaluation (%s dominant)" % ("far_deriv_mixed_kernel" if deriv else
                                                                          "far_mixed_kernel"), "bound": "alu",
-                         "achieved": ach, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": ach / FP32_PEAK_TFLOPS,
+                         "achieved": ach, "peak": fp32_peak(), "unit": "TFLOP/s", "frac": ach / fp32_peak(),
                          "traffic": None},
             "fp64_gpu_points_per_s": ts.T * 1e3 / t64, "rel_err_vs_fp64_gpu": err, "gpu_launches": int(launches),
             "clocks": clk}
     ts.close()
     g.close()
-    if rank == 0:
-        print(json.dumps(line), flush=True)
+    return line
 
 
 def _charges_potential(xs, qs, X, chunk=4096):
@@ -936,6 +1085,7 @@ def run_dirichlet200(args, ws, rank, lrank):
         infos.append(S.sbio_solve_dirichlet(g.h, f, mu, **kw))
     launches = S.sbio_launch_count() - l0
     clk = clocks.stop()
+    set_peak_basis(lrank, clk)
     # one plain apply for the per-iteration comparison
     stream = torch.cuda.current_stream()
     So = torch.empty(g.N, dtype=torch.float64, device="cuda")
@@ -967,14 +1117,13 @@ def run_dirichlet200(args, ws, rank, lrank):
             "max_rel_err_at_shell_points": err,
             "roofline": {"kernel": "whole solve (far_mixed_kernel dominant; Arnoldi applies only)", "bound": "alu",
                          "achieved": FAR_FLOP_PER_PAIR["SD"] * g.n_far * its / (ms * 1e-3) / 1e12,
-                         "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
-                         "frac": FAR_FLOP_PER_PAIR["SD"] * g.n_far * its / (ms * 1e-3) / 1e12 / FP32_PEAK_TFLOPS,
+                         "peak": fp32_peak(), "unit": "TFLOP/s",
+                         "frac": FAR_FLOP_PER_PAIR["SD"] * g.n_far * its / (ms * 1e-3) / 1e12 / fp32_peak(),
                          "flop_per_pair": FAR_FLOP_PER_PAIR["SD"], "traffic": None},
             "gpu_launches": int(launches), "clocks": clk}
     ts.close()
     g.close()
-    if rank == 0:
-        print(json.dumps(line), flush=True)
+    return line
 
 
 def run_stokespoints100(args, ws, rank, lrank, dl=False):
@@ -1021,6 +1170,7 @@ def run_stokespoints100(args, ws, rank, lrank, dl=False):
         ms.append(_event_time(st, step))
     launches = S.sbio_launch_count() - l0
     clk = clocks.stop()
+    set_peak_basis(lrank, clk)
     um, pm = u.clone(), pr.clone()
     S.sbio_geom_set_precision(g.h, S.SBIO_FP64)
     step()
@@ -1038,7 +1188,8 @@ def run_stokespoints100(args, ws, rank, lrank, dl=False):
             "config": {"workload": "stokesdlpoints100_p12" if dl else "stokespoints100_p12", "M": susp.M, "p": susp.p, "points": ts.T,
                        "near_pairs": ts.n_near, "far_pairs": ts.n_far,
                        "far_launch": {"targets_per_thread": stune[0], "source_splits": stune[1]},
-                       "near_ctas_per_sm_overlapped": scap,
+                       # the double layer's near pairs run at the tuned cap but at least 4 CTAs per SM
+                       "near_ctas_per_sm_overlapped": max(4, scap) if (dl and scap > 0) else scap,
                        "points_recipe": "shells at 1e-1..1e-6 (10 per spheroid and distance) + 30,000 in the box",
                        "l2": "flushed (256 MiB write) before each step"},
             "evaluations_per_s": 1e3 / mean, "fp64_gpu_points_per_s": ts.T * 1e3 / t64,
@@ -1046,14 +1197,13 @@ def run_stokespoints100(args, ws, rank, lrank, dl=False):
                                     "whole evaluation (stokes_far_mixed_kernel with pressure dominant)"),
                          "bound": "alu",
                          "achieved": far_flop * ts.n_far / (mean * 1e-3) / 1e12,
-                         "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
-                         "frac": far_flop * ts.n_far / (mean * 1e-3) / 1e12 / FP32_PEAK_TFLOPS,
+                         "peak": fp32_peak(), "unit": "TFLOP/s",
+                         "frac": far_flop * ts.n_far / (mean * 1e-3) / 1e12 / fp32_peak(),
                          "flop_per_pair": far_flop, "traffic": None},
             "rel_err_vs_fp64_gpu": err, "gpu_launches": int(launches), "clocks": clk}
     ts.close()
     g.close()
-    if rank == 0:
-        print(json.dumps(line), flush=True)
+    return line
 
 
 def run_stokesdl100(args, ws, rank, lrank):
@@ -1089,6 +1239,7 @@ def run_stokesdl100(args, ws, rank, lrank):
         ms.append(_event_time(st, lambda: S.sbio_apply_stokes_dl(g.h, qd, u)))
     launches = S.sbio_launch_count() - l0
     clk = clocks.stop()
+    set_peak_basis(lrank, clk)
     S.sbio_geom_enable_timing(g.h, True)        # phase-timed pass, phases in order
     ph = []
     for _ in range(min(args.steps, 10)):
@@ -1114,21 +1265,176 @@ def run_stokesdl100(args, ws, rank, lrank):
             "config": {"workload": "stokesdl100_p12", "M": susp.M, "p": susp.p, "targets": g.N,
                        "near_pairs": g.n_near, "far_pairs_per_apply": g.n_far,
                        "far_launch": {"targets_per_thread": stune[0], "source_splits": stune[1]},
-                       "near_ctas_per_sm_overlapped": scap,
+                       "near_ctas_per_sm_overlapped": max(4, scap) if scap > 0 else scap,
                        "l2": "flushed (256 MiB write) before each step"},
             "phase_ms": {"prep_and_self": statistics.mean(x[0] for x in ph), "near": near_ms, "far": far_ms},
             "roofline": {"kernel": "stokes_dl_near_kernel (FP64 pipe)", "bound": "alu", "achieved": near_ach,
-                         "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": near_ach / FP64_PEAK_TFLOPS,
+                         "peak": fp64_peak(), "unit": "TFLOP/s", "frac": near_ach / fp64_peak(),
                          "flop_per_pair": near_flop, "traffic": None,
                          "peak_source": "nominal GB300 FP64 1.25 TFLOP/s"},
             "roofline_far": {"kernel": "stresslet_far_mixed_kernel", "bound": "alu", "achieved": far_ach,
-                             "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": far_ach / FP32_PEAK_TFLOPS,
+                             "peak": fp32_peak(), "unit": "TFLOP/s", "frac": far_ach / fp32_peak(),
                              "flop_per_pair": STRESSLET_FAR_FLOP_PER_PAIR, "traffic": None},
             "fp64_gpu_applies_per_s": 1e3 / t64, "rel_err_vs_fp64_gpu": err, "gpu_launches": int(launches),
             "clocks": clk}
     g.close()
-    if rank == 0:
-        print(json.dumps(line), flush=True)
+    return line
+
+
+def run_lattice8(args, ws, rank, lrank):
+    """The 8-spheroid lattice at p = 8 (1296 targets) in plain FP64: a
+    latency-bound apply; per-apply CUDA-event times give p50 / p99."""
+    import torch
+
+    from paper_2506_20809_gb300 import inputs as I
+
+    import __graft_entry__ as GE
+
+    GE.build()
+    from paper_2506_20809_gb300 import sbio as S
+
+    torch.cuda.set_device(lrank)
+    susp = I.config_suspension(1)
+    coef = I.config_coefficients(susp, 0)
+    ctx = S.sbio_ctx_create(lrank, 0)
+    g = S.Geometry(ctx, susp, precision=S.SBIO_FP64)
+    sig, mu = torch.from_numpy(coef[0]).cuda(), torch.from_numpy(coef[1]).cuda()
+    So = torch.empty(g.N, dtype=torch.float64, device="cuda")
+    Do = torch.empty_like(So)
+    st = torch.cuda.current_stream()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    for _ in range(max(3, args.warmup)):
+        S.sbio_apply_laplace(g.h, sig, mu, So, Do)
+    clocks = ClockSampler(lrank)
+    clocks.start()
+    steps = max(args.steps, 200)
+    ms = []
+    l0 = S.sbio_launch_count()
+    for _ in range(steps):
+        flush.zero_()
+        ms.append(_event_time(st, lambda: S.sbio_apply_laplace(g.h, sig, mu, So, Do)))
+    launches = S.sbio_launch_count() - l0
+    clk = clocks.stop()
+    set_peak_basis(lrank, clk)
+    hs = torch.from_numpy(coef[0]).pin_memory().numpy()
+    hm = torch.from_numpy(coef[1]).pin_memory().numpy()
+    hS = torch.empty(g.N, dtype=torch.float64).pin_memory().numpy()
+    hD = torch.empty(g.N, dtype=torch.float64).pin_memory().numpy()
+    S.sbio_apply_laplace_host(g.h, hs, hm, hS, hD)
+    e2e = []
+    for _ in range(steps):
+        t0 = time.perf_counter()
+        S.sbio_apply_laplace_host(g.h, hs, hm, hS, hD)
+        e2e.append((time.perf_counter() - t0) * 1e3)
+    S.sbio_geom_set_precision(g.h, S.SBIO_MIXED)
+    mixed = [_event_time(st, lambda: S.sbio_apply_laplace(g.h, sig, mu, So, Do)) for _ in range(50)]
+    lat = sorted(ms)
+    el = sorted(e2e)
+    line = {"metric": "BIO applies/s (Laplace S+D, all surface nodes, plain FP64) and p50/p99 latency",
+            "value": 1e3 / statistics.mean(ms), "unit": "applies/s", "n_gpus": ws, "steps": steps,
+            "warmup": max(3, args.warmup), "ms_per_step": statistics.mean(ms), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "lattice8_p8_laplace_SD_fp64", "M": susp.M, "p": susp.p, "targets": g.N,
+                       "near_pairs": g.n_near, "far_pairs_per_apply": g.n_far,
+                       "l2": "flushed (256 MiB write) before each step"},
+            "latency_ms": {"p50": lat[len(lat) // 2], "p99": lat[min(len(lat) - 1, int(0.99 * len(lat)))]},
+            "e2e": {"value": 1e3 / statistics.mean(e2e), "unit": "applies/s",
+                    "h2d_bytes_per_step": int(hs.nbytes + hm.nbytes), "d2h_bytes_per_step": int(hS.nbytes + hD.nbytes),
+                    "p50_ms": el[len(el) // 2], "p99_ms": el[min(len(el) - 1, int(0.99 * len(el)))]},
+            "mixed_applies_per_s": 1e3 / statistics.mean(mixed),
+            "gpu_launches": int(launches), "clocks": clk}
+    g.close()
+    S.sbio_ctx_destroy(ctx)
+    return line
+
+
+def _sweep_member(args):
+    M, seed = args
+    from paper_2506_20809_gb300 import inputs as I
+
+    return I.rsa_suspension(M, 0.20, seed, 16, ar_range=(1.2, 5.0), name=f"poly{M}")
+
+
+def run_far_sweep(args, ws, rank, lrank):
+    """The poly200 recipe (AR U[1.2, 5], major U[0.5, 1.5], 20 %, gap 0.05,
+    p = 16) at growing particle counts: the direct far field's time and pair
+    rate per apply, and the whole mixed apply, to show where the O(N^2) sum
+    stops being the kernel of choice."""
+    import concurrent.futures as cf
+    import multiprocessing as mp
+
+    import torch
+
+    Ms = [int(x) for x in args.sweep_M.split(",")]
+    with cf.ProcessPoolExecutor(max_workers=len(Ms), mp_context=mp.get_context("spawn")) as ex:
+        susps = list(ex.map(_sweep_member, [(M, 0) for M in Ms]))   # before CUDA starts
+    from paper_2506_20809_gb300 import inputs as I
+
+    import __graft_entry__ as GE
+
+    GE.build()
+    from paper_2506_20809_gb300 import sbio as S
+
+    torch.cuda.set_device(lrank)
+    ctx = S.sbio_ctx_create(lrank, 0)
+    st = torch.cuda.current_stream()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    rows = []
+    clocks = ClockSampler(lrank)
+    clocks.start()
+    for susp in susps:
+        coef = I.config_coefficients(susp, 0)
+        g = S.Geometry(ctx, susp, precision=S.SBIO_MIXED)
+        tune = S.sbio_geom_autotune(g.h)
+        sig, mu = torch.from_numpy(coef[0]).cuda(), torch.from_numpy(coef[1]).cuda()
+        So = torch.empty(g.N, dtype=torch.float64, device="cuda")
+        Do = torch.empty_like(So)
+        for _ in range(2):
+            S.sbio_apply_laplace(g.h, sig, mu, So, Do)
+        reps = 5 if g.n_far < 1e11 else 3
+        whole = []
+        for _ in range(reps):
+            flush.zero_()
+            whole.append(_event_time(st, lambda: S.sbio_apply_laplace(g.h, sig, mu, So, Do)))
+        S.sbio_geom_enable_timing(g.h, True)
+        far = []
+        for _ in range(reps):
+            flush.zero_()
+            S.sbio_apply_laplace(g.h, sig, mu, So, Do)
+            far.append(S.sbio_geom_phase_times(g.h)[2])
+        S.sbio_geom_enable_timing(g.h, False)
+        far_ms = statistics.median(far)
+        rows.append({"M": susp.M, "targets": g.N, "near_pairs": g.n_near, "far_pairs": g.n_far,
+                     "far_launch": {"targets_per_thread": tune[0], "source_splits": tune[1]},
+                     "direct_far_ms": far_ms, "direct_gpairs_per_s": g.n_far / (far_ms * 1e-3) / 1e9,
+                     "apply_ms": statistics.median(whole),
+                     "far_frac_of_fp32_peak": FAR_FLOP_PER_PAIR["SD"] * g.n_far / (far_ms * 1e-3) / 1e12 / fp32_peak()})
+        g.close()
+    clk = clocks.stop()
+    set_peak_basis(lrank, clk)
+    for r in rows:
+        r["far_frac_of_fp32_peak"] = FAR_FLOP_PER_PAIR["SD"] * r["far_pairs"] / (r["direct_far_ms"] * 1e-3) / 1e12 / fp32_peak()
+    big = rows[-1]
+    line = {"metric": "Laplace S+D apply time vs suspension size (direct tiled far field, mixed)",
+            "value": 1e3 / big["apply_ms"], "unit": "applies/s", "n_gpus": ws, "steps": len(rows), "warmup": 2,
+            "ms_per_step": big["apply_ms"], "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32+f64", "data": "synthetic",
+            "config": {"workload": "far_sweep_p16", "M": Ms, "p": 16,
+                       "geometry": "AR U[1.2,5], major U[0.5,1.5], phi=20%, gap>=0.05, RSA seed 0",
+                       "l2": "flushed (256 MiB write) before each step"},
+            "sweep": rows, "clocks": clk}
+    S.sbio_ctx_destroy(ctx)
+    return line
+
+
+def _sub(fn, keys, *a, **k):
+    """Run a secondary workload for the headline line and keep the keys a
+    reader needs; a failure is recorded instead of losing the line."""
+    try:
+        line = fn(*a, **k)
+    except Exception as e:   # noqa: BLE001
+        return {"error": f"{type(e).__name__}: {e}"[:500]}
+    return {key: line[key] for key in keys if key in line}
 
 
 def main():
@@ -1136,28 +1442,48 @@ def main():
     ws, rank, lrank = dist_setup()
     if args.impl == "reference":
         run_reference(args, ws, rank)
+        line = None
     elif args.workload == "stokes100":
-        run_stokes100(args, ws, rank, lrank)
+        line = run_stokes100(args, ws, rank, lrank)
     elif args.workload == "batch64":
-        run_batch64(args, ws, rank, lrank)
+        line = run_batch64(args, ws, rank, lrank)
     elif args.workload == "serve":
-        run_serve(args, ws, rank, lrank)
+        line = run_serve(args, ws, rank, lrank)
     elif args.workload == "deriv200":
-        run_deriv200(args, ws, rank, lrank)
+        line = run_deriv200(args, ws, rank, lrank)
     elif args.workload == "targets200":
-        run_targets200(args, ws, rank, lrank)
+        line = run_targets200(args, ws, rank, lrank)
     elif args.workload == "derivpoints200":
-        run_targets200(args, ws, rank, lrank, deriv=True)
+        line = run_targets200(args, ws, rank, lrank, deriv=True)
     elif args.workload == "dirichlet200":
-        run_dirichlet200(args, ws, rank, lrank)
+        line = run_dirichlet200(args, ws, rank, lrank)
     elif args.workload == "stokespoints100":
-        run_stokespoints100(args, ws, rank, lrank)
+        line = run_stokespoints100(args, ws, rank, lrank)
     elif args.workload == "stokesdlpoints100":
-        run_stokespoints100(args, ws, rank, lrank, dl=True)
+        line = run_stokespoints100(args, ws, rank, lrank, dl=True)
     elif args.workload == "stokesdl100":
-        run_stokesdl100(args, ws, rank, lrank)
+        line = run_stokesdl100(args, ws, rank, lrank)
+    elif args.workload == "lattice8":
+        line = run_lattice8(args, ws, rank, lrank)
+    elif args.workload == "far_sweep":
+        line = run_far_sweep(args, ws, rank, lrank)
     else:
-        run_ours(args, ws, rank, lrank)
+        line = run_ours(args, ws, rank, lrank)
+        if not args.headline_only:
+            # the batched (64 suspensions per step), served (Poisson stream)
+            # and Stokes single-layer forms, each beside its plain FP64 form
+            line["batched"] = _sub(run_batch64, ["metric", "value", "unit", "ms_per_step", "gpairs_per_s",
+                                                 "roofline", "fp64_plain_ms", "fp64_plain_applies_per_s",
+                                                 "speedup_vs_fp64_plain", "speedup_vs_sequential_mixed",
+                                                 "config"], args, ws, rank, lrank)
+            line["served"] = _sub(run_serve, ["metric", "value", "unit", "sweep", "knee", "fp64_plain",
+                                              "mixed_same_requests", "speedup_vs_fp64_plain", "config"],
+                                  args, ws, rank, lrank)
+            line["stokes100"] = _sub(run_stokes100, ["metric", "value", "unit", "ms_per_step", "e2e", "roofline",
+                                                     "fp64_gpu_applies_per_s", "rel_err_vs_fp64_gpu", "config"],
+                                     args, ws, rank, lrank)
+    if rank == 0 and line is not None:
+        print(json.dumps(line), flush=True)
     if ws > 1:
         import torch.distributed as dist
 

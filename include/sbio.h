@@ -111,6 +111,35 @@ const char* sbio_last_error(const sbio_ctx* ctx);
  * (all contexts); used to count launches inside a timed region. */
 int64_t sbio_launch_count(void);
 
+/* Measured pipe rates of one GPU (no counterpart in the paper: the roofline
+ * denominators of the hot path's kernels, which no copy or GEMM benchmark
+ * gives).  Each rate comes from a kernel of independent dependency chains at
+ * full occupancy (8 CTAs of 256 threads per SM), timed with CUDA events after
+ * a warm-up launch on a private stream:
+ *   fp32_ffma_tflops / fp32_ffma2_tflops: scalar FMA and packed f32x2 FMA
+ *     (2 flop per FMA);
+ *   rsqrt_per_s: MUFU rsqrt.approx.f32 per second;
+ *   fp64_dfma_tflops: FP64 FMA;
+ *   pairmix_pairs_per_s: far-field S + D pairs per second with the packed
+ *     far kernel's register arithmetic per two pairs (11 f32x2 instructions,
+ *     2 rsqrt) and no memory traffic, i.e. the rate the far kernel could
+ *     reach if staging and bookkeeping cost nothing;
+ *   sm_clock_mhz: SM clock during the kernels (%clock64 over %globaltimer);
+ *   sms: multiprocessor count.
+ * Synchronous; allocates 48 bytes of device memory for the duration of the
+ * call.  Errors: SBIO_EINVAL (device out of range, null out), SBIO_ECUDA. */
+typedef struct {
+  double fp32_ffma_tflops;
+  double fp32_ffma2_tflops;
+  double rsqrt_per_s;
+  double fp64_dfma_tflops;
+  double pairmix_pairs_per_s;
+  double sm_clock_mhz;
+  int32_t sms;
+  int32_t reserved;
+} sbio_peaks;
+int sbio_measure_peaks(int32_t device, sbio_peaks* out);
+
 /* Create a context on CUDA device `device`.  mem_budget_bytes bounds the
  * device memory that geometries of this context may hold (0 = no bound);
  * geometry creation that would exceed it fails with SBIO_ENOMEM. */
@@ -163,6 +192,14 @@ int sbio_geom_near_pairs(const sbio_geom* g, int32_t* target, int32_t* source);
  * synchronises on those events and returns the three durations of the last
  * apply in milliseconds (SBIO_EINVAL if timing is off). */
 int sbio_geom_enable_timing(sbio_geom* g, int32_t on);
+
+/* Work of the S + D near field (Algorithm 1, near branch), for the roofline
+ * count: n_pairs (target, near particle) pairs, and miller_steps = the sum
+ * over the pairs of the rolled backward-recurrence steps the kernel runs
+ * above the top order before its unrolled part (about 19 / acosh(u) or
+ * 19 / asinh(u) per pair, data dependent).  Runs one counting kernel on the
+ * legacy default stream and synchronises.  Either output may be NULL. */
+int sbio_geom_near_work(sbio_geom* g, int64_t* n_pairs, int64_t* miller_steps);
 int sbio_geom_phase_times(sbio_geom* g, double* ms_synth, double* ms_near, double* ms_far);
 
 /* Launch shape of the far-field kernels: far_tt targets per thread of the
@@ -537,7 +574,10 @@ int sbio_server_destroy(sbio_server* s);
  * (cudaGetSymbolAddress) with that device current; make that first call
  * before any stream capture.  All calls share the one array: calls whose GPU
  * work overlaps (other streams, other host threads) race and must be
- * serialised by the caller.  Nothing in the array needs to start at zero. */
+ * serialised by the caller.  Nothing in the array needs to start at zero.
+ * The tables are staged from a host buffer that is freed when the call
+ * returns, so a call on a stream that is being captured fails with
+ * SBIO_EINVAL. */
 int sbio_apply_self_noalloc(const sbio_spheroid* sph, int32_t M, int32_t p, int32_t n_phi,
                             const double* sigma_tilde, const double* mu_hat, double* S_out,
                             double* D_out, void* stream);

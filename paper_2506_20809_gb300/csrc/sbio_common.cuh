@@ -159,11 +159,18 @@ __host__ __device__ inline SphCoord to_spheroidal(double x, double y, double z, 
   return o;
 }
 
-// Number of extra Miller steps for relative start error < ~1e-16.
+// Largest aspect ratio accepted: the Miller sweeps start about 19/mu steps
+// above the top order, mu = atanh(1/aspect ratio) on the surface, which is
+// 38,000 steps at this bound.
+constexpr double kMaxAspectRatio = 2000.0;
+constexpr int kMaxMillerExtra = 1 << 16;
+
+// Number of extra Miller steps for relative start error < ~1e-16
+// (e^{-2 mu K} < 1e-16 with mu = acosh(u) or asinh(u)).
 __host__ __device__ inline int miller_extra(double u, double sgn) {
   const double mu = log(u + sqrt(u * u + sgn));   // acosh(u) or asinh(u)
-  int K = (int)ceil(19.0 / mu) + 2;
-  if (K > 400) K = 400;
+  const double k = ceil(19.0 / mu) + 2.0;
+  int K = k > (double)kMaxMillerExtra ? kMaxMillerExtra : (int)k;
   if (K < 4) K = 4;
   return K;
 }

@@ -368,14 +368,13 @@ int launch_laplace_deriv(sbio_geom* g, const double* sigma, const double* mu, do
   if (rc) return rc;
   phase_mark(g, 1, st);
   const bool fork = g->overlap && !g->timing && g->near_stream && !h.pair_t.empty();
+  SideFork sf;
   if (fork) {
-    SBIO_CUDA_TRY(cudaEventRecord(g->ev_fork, st));
-    SBIO_CUDA_TRY(cudaStreamWaitEvent(g->near_stream, g->ev_fork, 0));
+    SBIO_CUDA_TRY(sf.fork(g, st));
     g->d.near_grid_cap = h.near_ctas_per_sm > 0 ? h.near_ctas_per_sm * sm_count() : 0;
     nl(g->d, h.n_pairs_prolate, (int64_t)h.pair_t.size(), Sp, Dp, g->near_stream);
     g->d.near_grid_cap = 0;
     SBIO_CUDA_TRY(cudaGetLastError());
-    SBIO_CUDA_TRY(cudaEventRecord(g->ev_join, g->near_stream));
   } else if (!h.pair_t.empty()) {
     nl(g->d, h.n_pairs_prolate, (int64_t)h.pair_t.size(), Sp, Dp, st);
     SBIO_CUDA_TRY(cudaGetLastError());
@@ -383,7 +382,7 @@ int launch_laplace_deriv(sbio_geom* g, const double* sigma, const double* mu, do
   phase_mark(g, 2, st);
   launch_far_deriv(g->d, h, h.N, Sp, Dp, st);
   SBIO_CUDA_TRY(cudaGetLastError());
-  if (fork) SBIO_CUDA_TRY(cudaStreamWaitEvent(st, g->ev_join, 0));
+  SBIO_CUDA_TRY(sf.join());
   phase_mark(g, 3, st);
   return SBIO_OK;
 }
@@ -447,21 +446,20 @@ int sbio_eval_targets_deriv(sbio_targets* ts, const double* dirs, const double* 
   DevGeom v = *view;
   v.nrm = const_cast<double*>(dirs);   // read only
   const bool fork = g->overlap && !g->timing && g->near_stream && n_pairs > 0;
+  SideFork sf;
   if (fork) {
-    SBIO_CUDA_TRY(cudaEventRecord(g->ev_fork, st));
-    SBIO_CUDA_TRY(cudaStreamWaitEvent(g->near_stream, g->ev_fork, 0));
+    SBIO_CUDA_TRY(sf.fork(g, st));
     v.near_grid_cap = h.near_ctas_per_sm > 0 ? h.near_ctas_per_sm * sm_count() : 0;
     nl(v, n_pro, n_pairs, Sp_out, Dp_out, g->near_stream);
     v.near_grid_cap = 0;
     SBIO_CUDA_TRY(cudaGetLastError());
-    SBIO_CUDA_TRY(cudaEventRecord(g->ev_join, g->near_stream));
   } else if (n_pairs > 0) {
     nl(v, n_pro, n_pairs, Sp_out, Dp_out, st);
     SBIO_CUDA_TRY(cudaGetLastError());
   }
   launch_far_deriv(v, h, T, Sp_out, Dp_out, st);
   SBIO_CUDA_TRY(cudaGetLastError());
-  if (fork) SBIO_CUDA_TRY(cudaStreamWaitEvent(st, g->ev_join, 0));
+  SBIO_CUDA_TRY(sf.join());
   return SBIO_OK;
 }
 

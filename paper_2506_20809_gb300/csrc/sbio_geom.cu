@@ -150,6 +150,9 @@ int validate(const sbio_spheroid* sph, int32_t M, const sbio_options* o) {
       return set_error(SBIO_EINVAL, "particle %d: prolate needs C > A (spheres are not supported)", i);
     if (s.kind == SBIO_OBLATE && !(s.C < s.A * (1.0 - 1e-9)))
       return set_error(SBIO_EINVAL, "particle %d: oblate needs C < A (spheres are not supported)", i);
+    const double ar = std::max(s.A, s.C) / std::min(s.A, s.C);
+    if (!(ar <= kMaxAspectRatio))
+      return set_error(SBIO_EINVAL, "particle %d: aspect ratio %g above the supported %g", i, ar, kMaxAspectRatio);
     const double qn = std::sqrt(s.quat[0] * s.quat[0] + s.quat[1] * s.quat[1] + s.quat[2] * s.quat[2] + s.quat[3] * s.quat[3]);
     if (!(std::fabs(qn - 1.0) <= 1e-6)) return set_error(SBIO_EINVAL, "particle %d: quaternion norm %g", i, qn);
     for (int k = 0; k < 3; ++k)
@@ -558,8 +561,18 @@ static int build_device(sbio_geom* g) {
   if ((rc = upload(g, &d.pair_s, h.pair_s.data(), h.pair_s.size(), "near pairs"))) return rc;
   // (the far skip lists were written on the device by the near-set kernels)
   if ((rc = upload(g, &d.tiles, h.tiles.data(), h.tiles.size(), "far tiles"))) return rc;
-  std::vector<double> inv(kInvTable, 0.0);
-  for (int k = 1; k < kInvTable; ++k) inv[k] = 1.0 / k;
+  // 1/k table of the near kernels' Miller sweeps, long enough for the most
+  // elongated particle: targets lie on or outside every surface, so u >= u0
+  // and the sweep needs at most ceil(19 / mu(u0)) + 2 steps above the top
+  // order (mu = atanh(minor / major semi-axis) at u0)
+  int inv_len = kInvTable;
+  for (const PartGeom& P : h.parts) {
+    const int need = miller_extra(P.u0, P.sgn) + 2 * kMaxP + 40;
+    inv_len = std::max(inv_len, need);
+  }
+  std::vector<double> inv(inv_len, 0.0);
+  for (int k = 1; k < inv_len; ++k) inv[k] = 1.0 / k;
+  inv[0] = (double)inv_len;
   if ((rc = upload(g, &d.inv, inv.data(), inv.size(), "inverse table"))) return rc;
   // FP32 hi/lo target positions and centres for the mixed far field
   std::vector<float4> tgt(N * 2), cen(M * 2);

@@ -40,7 +40,7 @@ struct DevGeom {
   int32_t* skip_ptr = nullptr;   // N+1 CSR of per-target skipped particles (own + near), ascending
   int32_t* skip_idx = nullptr;
   int4* tiles = nullptr;         // far source tiles (particle, first node, count, -)
-  double* inv = nullptr;         // 1/k, k < kInvTable (k = 0 holds 0)
+  double* inv = nullptr;         // 1/k for k >= 1; entry 0 holds the table length (sized per geometry)
   int near_grid_cap = 0;         // > 0: at most this many near CTAs (grid-stride), set while overlapping
   float4* tgt32 = nullptr;       // N x 2: hi, lo parts of the global node position
   float4* cen32 = nullptr;       // M x 2: hi, lo parts of the centres
@@ -181,6 +181,34 @@ int launch_far_persistent(const FarDesc* descs, const int4* items, int n_items, 
 inline void phase_mark(sbio_geom* g, int k, cudaStream_t st) {
   if (g->timing && g->ev[k]) cudaEventRecord(g->ev[k], st);
 }
+
+// Near-field work forked from the caller's stream onto the geometry's
+// high-priority stream, joined back on every exit path: if an apply returns
+// an error after the fork, the caller's stream still waits for the kernels
+// already queued on the side stream, so the next call on that stream cannot
+// overwrite the workspaces they read or race their atomic adds.
+struct SideFork {
+  cudaStream_t main = nullptr, side = nullptr;
+  cudaEvent_t join_ev = nullptr;
+  bool open = false;
+  cudaError_t fork(sbio_geom* g, cudaStream_t caller) {
+    main = caller;
+    side = g->near_stream;
+    join_ev = g->ev_join;
+    cudaError_t e = cudaEventRecord(g->ev_fork, caller);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(side, g->ev_fork, 0);
+    open = (e == cudaSuccess);
+    return e;
+  }
+  cudaError_t join() {
+    if (!open) return cudaSuccess;
+    open = false;
+    cudaError_t e = cudaEventRecord(join_ev, side);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(main, join_ev, 0);
+    return e;
+  }
+  ~SideFork() { join(); }
+};
 
 // kernel entry points (defined in the kernel translation units)
 // side (on the own surface): 0 the principal value of D, +1 / -1 the exterior

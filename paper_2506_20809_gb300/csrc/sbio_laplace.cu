@@ -512,6 +512,39 @@ int launch_far_persistent(const FarDesc* descs, const int4* items, int n_items, 
   return SBIO_OK;
 }
 
+// Miller steps of every near pair of the S + D kernel (order P = p): the
+// same start index as miller_q01 (K ~ 19/mu above the top order, clamped to
+// the geometry's 1/k table), summed into one counter.  Diagnostic: it gives
+// the near field's data-dependent FP64 work, which a per-pair constant
+// cannot.
+__global__ void __launch_bounds__(256) near_work_kernel(const int32_t* __restrict__ pair_t,
+                                                        const int32_t* __restrict__ pair_s, int64_t count,
+                                                        const PartGeom* __restrict__ parts,
+                                                        const double* __restrict__ xyz,
+                                                        const double* __restrict__ inv_tab, int P,
+                                                        unsigned long long* __restrict__ steps) {
+  unsigned long long k_sum = 0;
+  for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < count; r += (int64_t)gridDim.x * blockDim.x) {
+    const int t = pair_t[r], i = pair_s[r];
+    const PartGeom& G = parts[i];
+    const double dx = xyz[(int64_t)t * 3 + 0] - G.c[0];
+    const double dy = xyz[(int64_t)t * 3 + 1] - G.c[1];
+    const double dz = xyz[(int64_t)t * 3 + 2] - G.c[2];
+    const double xl = G.R[0] * dx + G.R[3] * dy + G.R[6] * dz;
+    const double yl = G.R[1] * dx + G.R[4] * dy + G.R[7] * dz;
+    const double zl = G.R[2] * dx + G.R[5] * dy + G.R[8] * dz;
+    const SphCoord sc = to_spheroidal(xl, yl, zl, G.a, G.kind);
+    const double u = sc.u;
+    const float muf = logf((float)u + sqrtf((float)(u * u + G.sgn)));
+    int K = (int)ceilf(19.0f / muf) + 2;
+    const int kmax = (int)inv_tab[0] - P - 8;
+    K = K < 4 ? 4 : (K > kmax ? kmax : K);
+    k_sum += (unsigned long long)K;
+  }
+  for (int o = 16; o > 0; o >>= 1) k_sum += __shfl_down_sync(0xffffffffu, k_sum, o);
+  if ((threadIdx.x & 31) == 0 && k_sum) atomicAdd(steps, k_sum);
+}
+
 int launch_synth_mode(sbio_geom* g, const double* sigma, const double* mu, double* S, double* D, int self_mode,
                       cudaStream_t st, int side) {
   const GeomHost& h = g->h;
@@ -554,15 +587,14 @@ int launch_laplace(sbio_geom* g, const double* sigma, const double* mu, double* 
   // with phase timing on, run the phases in order so that each is timed alone
   const bool fork = g->overlap && !g->timing && g->near_stream && (parts & SBIO_PART_NEAR) &&
                     (parts & SBIO_PART_FAR) && !g->h.pair_t.empty();
+  SideFork sf;
   if (fork) {
-    SBIO_CUDA_TRY(cudaEventRecord(g->ev_fork, st));
-    SBIO_CUDA_TRY(cudaStreamWaitEvent(g->near_stream, g->ev_fork, 0));
+    SBIO_CUDA_TRY(sf.fork(g, st));
     // a few near CTAs per SM leave room for the far kernel's CTAs
     g->d.near_grid_cap = g->h.near_ctas_per_sm > 0 ? g->h.near_ctas_per_sm * sm_count() : 0;
     rc = launch_near(g, S, D, g->near_stream);
     g->d.near_grid_cap = 0;
     if (rc) return rc;
-    SBIO_CUDA_TRY(cudaEventRecord(g->ev_join, g->near_stream));
   } else if (parts & SBIO_PART_NEAR) {
     rc = launch_near(g, S, D, st);
     if (rc) return rc;
@@ -572,7 +604,7 @@ int launch_laplace(sbio_geom* g, const double* sigma, const double* mu, double* 
     launch_far(g, S, D, st);
     SBIO_CUDA_TRY(cudaGetLastError());
   }
-  if (fork) SBIO_CUDA_TRY(cudaStreamWaitEvent(st, g->ev_join, 0));
+  SBIO_CUDA_TRY(sf.join());
   phase_mark(g, 3, st);
   return SBIO_OK;
 }
@@ -727,6 +759,32 @@ int sbio_geom_set_near_cap(sbio_geom* g, int32_t ctas_per_sm) {
   if (!g) return set_error(SBIO_EINVAL, "null geometry");
   if (ctas_per_sm < 0) return set_error(SBIO_EINVAL, "ctas_per_sm must be >= 0");
   g->h.near_ctas_per_sm = ctas_per_sm;
+  return SBIO_OK;
+}
+
+int sbio_geom_near_work(sbio_geom* g, int64_t* n_pairs, int64_t* miller_steps) {
+  clear_error();
+  if (!g) return set_error(SBIO_EINVAL, "null geometry");
+  SBIO_CUDA_TRY(cudaSetDevice(g->ctx->device));
+  const int64_t np = (int64_t)g->h.pair_t.size();
+  unsigned long long steps = 0;
+  if (np > 0) {
+    unsigned long long* d_steps = nullptr;
+    SBIO_CUDA_TRY(cudaMalloc(&d_steps, sizeof(unsigned long long)));
+    cudaError_t e = cudaMemset(d_steps, 0, sizeof(unsigned long long));
+    if (e == cudaSuccess) {
+      const int64_t nb = std::min<int64_t>((np + 255) / 256, (int64_t)sm_count() * 8);
+      near_work_kernel<<<(unsigned)nb, 256>>>(g->d.pair_t, g->d.pair_s, np, g->d.parts, g->d.xyz, g->d.inv, g->h.p,
+                                              d_steps);
+      count_launch();
+      e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpy(&steps, d_steps, sizeof(steps), cudaMemcpyDeviceToHost);
+    cudaFree(d_steps);
+    if (e != cudaSuccess) return set_error(SBIO_ECUDA, "near work count failed: %s", cudaGetErrorString(e));
+  }
+  if (n_pairs) *n_pairs = np;
+  if (miller_steps) *miller_steps = (int64_t)steps;
   return SBIO_OK;
 }
 

@@ -16,7 +16,10 @@
 
 namespace sbio {
 
-// Inverse-integer table used by the rolled part of the Miller sweep.
+// Inverse-integer table used by the rolled part of the Miller sweep: entry k
+// holds 1/k for k >= 1, entry 0 the table's length.  The geometry sizes the
+// table from its most elongated particle (at least kInvTable entries), so that
+// the sweep can always start its full K steps above the top order.
 constexpr int kInvTable = 512;
 
 // Q family for m = 0 and m = 1, n = 0..P+1, normalised (see sbio_common.cuh).
@@ -27,7 +30,8 @@ __device__ __forceinline__ void miller_q01(double u, double rsu, const double* _
   // start index above the top order; rolled part in FP64 with tabulated 1/n
   const float muf = logf((float)u + sqrtf((float)(u * u + sgn)));
   int K = (int)ceilf(19.0f / muf) + 2;
-  K = K < 4 ? 4 : (K > kInvTable - P - 8 ? kInvTable - P - 8 : K);
+  const int kmax = (int)inv_tab[0] - P - 8;
+  K = K < 4 ? 4 : (K > kmax ? kmax : K);
   int n = P + 1 + K;
   double a0 = 0.0, b0 = 1.0, a1 = 0.0, b1 = 1.0;   // q_{n+1}, q_n
   double nd = (double)n;

@@ -178,11 +178,22 @@ extern "C" int sbio_apply_self_noalloc(const sbio_spheroid* sph, int32_t M, int3
       normc[coef_index(n, m)] = std::sqrt((2.0 * n + 1.0) / (4.0 * kPi) * kfact(n, am)) * (m ? std::sqrt(2.0) : 1.0);
     }
 
+  // The tables are staged from `img`, which is freed when this call returns.
+  // Outside stream capture the pageable copy has read it before the call
+  // returns; a captured copy would instead keep the host address and read it
+  // at every replay, so calls on a capturing stream are refused (before any
+  // other CUDA call).
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  SBIO_CUDA_TRY(cudaStreamIsCapturing(st, &cap));
+  if (cap != cudaStreamCaptureStatusNone)
+    return set_error(SBIO_EINVAL,
+                     "sbio_apply_self_noalloc stages its tables from host memory freed on return; it cannot be "
+                     "called on a stream that is being captured");
   void* base = nullptr;
   rc = scratch_address(&base);
   if (rc) return rc;
   unsigned char* b = static_cast<unsigned char*>(base);
-  cudaStream_t st = (cudaStream_t)stream;
   // pageable source: the copy is staged before the call returns, so `img` may go
   SBIO_CUDA_TRY(cudaMemcpyAsync(b, img.data(), tables_end, cudaMemcpyHostToDevice, st));
   const int nmw = 2 * p + 1;

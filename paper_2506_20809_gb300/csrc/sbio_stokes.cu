@@ -531,14 +531,13 @@ int launch_stokes(sbio_geom* g, const double* f, double* u, cudaStream_t st) {
   // the FP64 near kernels run beside the FP32 Stokeslet kernel unless phases
   // are being timed one by one
   const bool fork = g->overlap && !g->timing && g->near_stream && !h.pair_t.empty();
+  SideFork sf;
   if (fork) {
-    SBIO_CUDA_TRY(cudaEventRecord(g->ev_fork, st));
-    SBIO_CUDA_TRY(cudaStreamWaitEvent(g->near_stream, g->ev_fork, 0));
+    SBIO_CUDA_TRY(sf.fork(g, st));
     g->d.near_grid_cap = h.st_near_ctas_per_sm > 0 ? h.st_near_ctas_per_sm * sm_count() : 0;
     nl(g->d, h.n_pairs_prolate, (int64_t)h.pair_t.size(), d.inv, u, g->near_stream);
     g->d.near_grid_cap = 0;
     SBIO_CUDA_TRY(cudaGetLastError());
-    SBIO_CUDA_TRY(cudaEventRecord(g->ev_join, g->near_stream));
   } else if (!h.pair_t.empty()) {
     nl(d, h.n_pairs_prolate, (int64_t)h.pair_t.size(), d.inv, u, st);
     SBIO_CUDA_TRY(cudaGetLastError());
@@ -546,7 +545,7 @@ int launch_stokes(sbio_geom* g, const double* f, double* u, cudaStream_t st) {
   phase_mark(g, 2, st);
   int rc = launch_stokes_far(g, u, st);
   if (rc) return rc;
-  if (fork) SBIO_CUDA_TRY(cudaStreamWaitEvent(st, g->ev_join, 0));
+  SBIO_CUDA_TRY(sf.join());
   phase_mark(g, 3, st);
   return SBIO_OK;
 }

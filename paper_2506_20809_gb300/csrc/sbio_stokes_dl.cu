@@ -614,16 +614,15 @@ int sbio_apply_stokes_dl_limit(sbio_geom* g, const double* q_hat, double* u_out,
   const DevGeom& d = g->d;
   const bool has_pairs = !h.pair_t.empty();
   const bool fork = g->overlap && !g->timing && g->near_stream && has_pairs;
+  SideFork sf;
   if (fork) {
     // near pairs on the forked high-priority stream, beside the own nodes
     // (exterior limit at u = u0, separable self kernel) and the far field
     DevGeom v = d;
     v.near_grid_cap = sdl_near_cap(h) * sm_count();
-    SBIO_CUDA_TRY(cudaEventRecord(g->ev_fork, st));
-    SBIO_CUDA_TRY(cudaStreamWaitEvent(g->near_stream, g->ev_fork, 0));
+    SBIO_CUDA_TRY(sf.fork(g, st));
     nl(v, d.pair_t, d.pair_s, h.n_pairs_prolate, (int64_t)h.pair_t.size(), u_out, g->near_stream);
     SBIO_CUDA_TRY(cudaGetLastError());
-    SBIO_CUDA_TRY(cudaEventRecord(g->ev_join, g->near_stream));
   }
   if ((rc = sdl_self(g, u_out, st))) return rc;
   // in order (no overlap, or phase timing): prep + self, near pairs, far field
@@ -635,7 +634,7 @@ int sbio_apply_stokes_dl_limit(sbio_geom* g, const double* q_hat, double* u_out,
   phase_mark(g, 2, st);
   launch_stresslet_far(d, d, h, h.N, u_out, st);
   SBIO_CUDA_TRY(cudaGetLastError());
-  if (fork) SBIO_CUDA_TRY(cudaStreamWaitEvent(st, g->ev_join, 0));
+  SBIO_CUDA_TRY(sf.join());
   phase_mark(g, 3, st);
   return SBIO_OK;
 }
@@ -664,20 +663,20 @@ int sbio_eval_targets_stokes_dl(sbio_targets* ts, const double* q_hat, double* u
   // near pairs on the geometry's high-priority stream beside the far field
   // (as in the on-surface apply), unless phases are timed one by one
   const bool fork = g->overlap && !g->timing && g->near_stream && n_pairs > 0;
+  SideFork sf;
   if (fork) {
     DevGeom v = *view;   // a copy: the near grid cap is per launch
     v.near_grid_cap = sdl_near_cap(h) * sm_count();
-    SBIO_CUDA_TRY(cudaEventRecord(g->ev_fork, st));
-    SBIO_CUDA_TRY(cudaStreamWaitEvent(g->near_stream, g->ev_fork, 0));
+    SBIO_CUDA_TRY(sf.fork(g, st));
     nl(v, v.pair_t, v.pair_s, n_pro, n_pairs, u_out, g->near_stream);
     SBIO_CUDA_TRY(cudaGetLastError());
-    SBIO_CUDA_TRY(cudaEventRecord(g->ev_join, g->near_stream));
   } else if (n_pairs > 0) {
     nl(*view, view->pair_t, view->pair_s, n_pro, n_pairs, u_out, st);
+    SBIO_CUDA_TRY(cudaGetLastError());
   }
   launch_stresslet_far(*view, g->d, h, T, u_out, st);
   SBIO_CUDA_TRY(cudaGetLastError());
-  if (fork) SBIO_CUDA_TRY(cudaStreamWaitEvent(st, g->ev_join, 0));
+  SBIO_CUDA_TRY(sf.join());
   return SBIO_OK;
 }
 

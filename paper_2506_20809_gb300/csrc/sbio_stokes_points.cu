@@ -127,9 +127,9 @@ int sbio_eval_targets_stokes(sbio_targets* ts, const double* f_tilde, double* u_
   DevGeom v = *view;   // a copy: the near grid cap is per launch
   const bool fork = g->overlap && !g->timing && g->near_stream && n_pairs > 0;
   cudaStream_t ns = fork ? g->near_stream : st;
+  SideFork sf;
   if (fork) {
-    SBIO_CUDA_TRY(cudaEventRecord(g->ev_fork, st));
-    SBIO_CUDA_TRY(cudaStreamWaitEvent(ns, g->ev_fork, 0));
+    SBIO_CUDA_TRY(sf.fork(g, st));
     // with the pressure a near pair costs about twice the velocity-only pair
     // the cap was tuned on (four derivative sums per expansion instead of one
     // combined gradient), against a similar far pair: twice the CTAs
@@ -152,12 +152,11 @@ int sbio_eval_targets_stokes(sbio_targets* ts, const double* f_tilde, double* u_
     }
     SBIO_CUDA_TRY(cudaGetLastError());
   }
-  if (fork) SBIO_CUDA_TRY(cudaEventRecord(g->ev_join, ns));
   const bool fp64 = h.precision == SBIO_FP64;
   if ((rc = launch_stokes_far_on(v, h, T, u_out, fp64 ? nullptr : p_out, st))) return rc;
   if (p_out && fp64) launch_pressure_far_fp64(v, h, T, p_out, st);
   SBIO_CUDA_TRY(cudaGetLastError());
-  if (fork) SBIO_CUDA_TRY(cudaStreamWaitEvent(st, g->ev_join, 0));
+  SBIO_CUDA_TRY(sf.join());
   return SBIO_OK;
 }
 

@@ -214,21 +214,20 @@ int sbio_eval_targets(sbio_targets* ts, const double* sigma_tilde, const double*
   // the FP64 near pairs run beside the FP32 far field on the geometry's
   // high-priority stream (capped CTAs per SM), as in the on-surface apply
   const bool fork = g->overlap && !g->timing && g->near_stream && ts->n_pairs > 0;
+  SideFork sf;
   if (fork) {
-    SBIO_CUDA_TRY(cudaEventRecord(g->ev_fork, st));
-    SBIO_CUDA_TRY(cudaStreamWaitEvent(g->near_stream, g->ev_fork, 0));
+    SBIO_CUDA_TRY(sf.fork(g, st));
     ts->view.near_grid_cap = h.near_ctas_per_sm > 0 ? h.near_ctas_per_sm * sm_count() : 0;
     nl(ts->view, ts->n_pro, ts->n_pairs, ts->view.inv, S_out, D_out, g->near_stream);
     ts->view.near_grid_cap = 0;
     SBIO_CUDA_TRY(cudaGetLastError());
-    SBIO_CUDA_TRY(cudaEventRecord(g->ev_join, g->near_stream));
   } else if (ts->n_pairs > 0) {
     nl(ts->view, ts->n_pro, ts->n_pairs, ts->view.inv, S_out, D_out, st);
     SBIO_CUDA_TRY(cudaGetLastError());
   }
   launch_far_on(ts->view, h, ts->T, S_out, D_out, st);
   SBIO_CUDA_TRY(cudaGetLastError());
-  if (fork) SBIO_CUDA_TRY(cudaStreamWaitEvent(st, g->ev_join, 0));
+  SBIO_CUDA_TRY(sf.join());
   return SBIO_OK;
 }
 

@@ -375,3 +375,98 @@ def interior_charges(s: Suspension, per_particle: int = 2, seed: int = 0, spread
     xs = np.concatenate([s.center[i] + (rng.uniform(-spread, spread, (per_particle, 3))
                                         * np.array([s.A[i], s.A[i], s.C[i]])) @ R[i].T for i in range(s.M)])
     return xs, rng.uniform(-0.5, 0.5, len(xs))
+
+
+def elongated_pair(ar: float, kind0: int, p: int, gap: float = 0.1, tilt: float = 0.7) -> Suspension:
+    """Two spheroids for the aspect-ratio tests (the paper's stress tests run
+    prolates up to aspect ratio 64): particle 0 has major semi-axis 1 and
+    aspect ratio `ar` (prolate: C = 1, A = 1/ar; oblate: A = 1, C = 1/ar),
+    centred at the origin with the identity orientation; particle 1, a
+    prolate A = 0.25, C = 0.5 tilted by `tilt` about x, sits beyond the tip
+    (prolate) or the rim (oblate) of particle 0 with its centre `gap` + 0.25
+    beyond it."""
+    if kind0 == PROLATE:
+        A0, C0 = 1.0 / ar, 1.0
+        c1 = np.array([0.0, 0.0, C0 + gap + 0.25])
+    else:
+        A0, C0 = 1.0, 1.0 / ar
+        c1 = np.array([A0 + gap + 0.25, 0.0, 0.0])
+    kind = np.array([kind0, PROLATE], np.int32)
+    A = np.array([A0, 0.25])
+    C = np.array([C0, 0.5])
+    quat = np.array([[1.0, 0.0, 0.0, 0.0], [math.cos(tilt / 2), math.sin(tilt / 2), 0.0, 0.0]])
+    center = np.stack([np.zeros(3), c1])
+    return Suspension(kind, A, C, center, quat, p, f"elongated{ar:g}")
+
+
+def extreme_points(s: Suspension, i: int, distances=(1e-1, 1e-2, 1e-3), n_side: int = 8) -> np.ndarray:
+    """Points at distance d outside the most curved and the flattest parts of
+    spheroid i: on the symmetry axis beyond both poles, and in the equatorial
+    plane beyond the rim at n_side angles (exact distance d in both places,
+    where the outward normal is along the offset).  Returns (T, 3); points
+    inside another spheroid are dropped."""
+    R = _quat_to_matrix(s.quat)
+    pts = []
+    for d in distances:
+        pts.append(np.array([[0.0, 0.0, s.C[i] + d], [0.0, 0.0, -(s.C[i] + d)]]))
+        ang = 2 * math.pi * (np.arange(n_side) + 0.25) / n_side
+        r = s.A[i] + d
+        pts.append(np.stack([r * np.cos(ang), r * np.sin(ang), np.zeros(n_side)], -1))
+    X = np.concatenate(pts) @ R[i].T + s.center[i]
+    keep = np.ones(len(X), bool)
+    for j in range(s.M):
+        if j == i:
+            continue
+        xl = (X - s.center[j]) @ R[j]
+        f = (xl[:, 0] ** 2 + xl[:, 1] ** 2) / s.A[j] ** 2 + xl[:, 2] ** 2 / s.C[j] ** 2
+        keep &= f > 1.0 + 1e-9
+    return np.ascontiguousarray(X[keep])
+
+
+def _quat_mul(a: np.ndarray, b: np.ndarray) -> np.ndarray:
+    """Hamilton product a b of (w, x, y, z) quaternions (b may be (M, 4))."""
+    aw, ax, ay, az = a
+    bw, bx, by, bz = b[..., 0], b[..., 1], b[..., 2], b[..., 3]
+    return np.stack([aw * bw - ax * bx - ay * by - az * bz,
+                     aw * bx + ax * bw + ay * bz - az * by,
+                     aw * by - ax * bz + ay * bw + az * bx,
+                     aw * bz + ax * by - ay * bx + az * bw], axis=-1)
+
+
+def rigid_motion(s: Suspension, seed: int, shift: float = 10.0) -> Suspension:
+    """The same suspension moved as a whole by a seeded random rotation (about
+    its centroid) and translation (U(-shift, shift)^3): a new geometry with
+    the same gaps and shapes, used to give every request of a served stream
+    its own geometry without a fresh placement."""
+    rng = np.random.default_rng([seed, 161803])
+    q = random_quaternions(rng, 1)[0]
+    R = _quat_to_matrix(q[None])[0]
+    c0 = s.center.mean(axis=0)
+    center = (s.center - c0) @ R.T + c0 + rng.uniform(-shift, shift, 3)
+    quat = _quat_mul(q, s.quat)
+    quat /= np.linalg.norm(quat, axis=1, keepdims=True)
+    return Suspension(s.kind.copy(), s.A.copy(), s.C.copy(), center, quat, s.p, s.name)
+
+
+def _serve_member(args):
+    k, seed, M_range, p_choices, phi = args
+    rng = np.random.default_rng([seed, k, 92821])
+    M = int(round(math.exp(rng.uniform(math.log(M_range[0]), math.log(M_range[1])))))
+    p = int(rng.choice(p_choices))
+    return rsa_suspension(M, phi, 1000 + 97 * seed + k, p, name=f"serve{k}")
+
+
+def serve_pool(n: int, seed: int = 0, M_range=(20, 500), p_choices=(8, 12, 16), phi: float = 0.20,
+               workers: int = 1):
+    """Suspensions for the served stream: M log-uniform in M_range, p from
+    p_choices, shapes and placement as the 200-particle workload at volume
+    fraction phi.  workers > 1 draws them in spawned processes (same
+    result)."""
+    jobs = [(k, seed, tuple(M_range), tuple(p_choices), phi) for k in range(n)]
+    if workers <= 1:
+        return [_serve_member(j) for j in jobs]
+    import concurrent.futures as cf
+    import multiprocessing as mp
+
+    with cf.ProcessPoolExecutor(max_workers=workers, mp_context=mp.get_context("spawn")) as ex:
+        return list(ex.map(_serve_member, jobs))

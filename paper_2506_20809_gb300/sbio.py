@@ -66,6 +66,12 @@ class sbio_solve_info(C.Structure):
                 ("rel_residual", C.c_double), ("ms", C.c_double)]
 
 
+class sbio_peaks(C.Structure):
+    _fields_ = [("fp32_ffma_tflops", C.c_double), ("fp32_ffma2_tflops", C.c_double), ("rsqrt_per_s", C.c_double),
+                ("fp64_dfma_tflops", C.c_double), ("pairmix_pairs_per_s", C.c_double),
+                ("sm_clock_mhz", C.c_double), ("sms", C.c_int32), ("reserved", C.c_int32)]
+
+
 class SbioError(RuntimeError):
     def __init__(self, code, msg):
         super().__init__(f"{ERRNAMES.get(code, code)}: {msg}")
@@ -146,6 +152,8 @@ _SIGS = {
     "sbio_server_stats": (C.c_int, [_vp, C.POINTER(C.c_int64), C.POINTER(C.c_int64), C.POINTER(C.c_int32),
                                     C.POINTER(C.c_int32), C.POINTER(C.c_size_t)]),
     "sbio_server_destroy": (C.c_int, [_vp]),
+    "sbio_measure_peaks": (C.c_int, [C.c_int32, C.POINTER(sbio_peaks)]),
+    "sbio_geom_near_work": (C.c_int, [_vp, C.POINTER(C.c_int64), C.POINTER(C.c_int64)]),
     "sbio_apply_self_noalloc": (C.c_int, [C.POINTER(sbio_spheroid), C.c_int32, C.c_int32, C.c_int32, _vp, _vp,
                                           _vp, _vp, _vp]),
 }
@@ -450,6 +458,21 @@ def sbio_geom_autotune_stokes(g, stream=None):
     a, b, c = C.c_int32(), C.c_int32(), C.c_double()
     _check(_lib.sbio_geom_autotune_stokes(g, _stream(stream), C.byref(a), C.byref(b), C.byref(c)))
     return a.value, b.value, c.value
+
+
+def sbio_geom_near_work(g):
+    """(near pairs, total Miller steps over them) of the S + D near kernel."""
+    a, b = C.c_int64(), C.c_int64()
+    _check(_lib.sbio_geom_near_work(g, C.byref(a), C.byref(b)))
+    return a.value, b.value
+
+
+def sbio_measure_peaks(device=0):
+    """Measured FP32 / f32x2 / MUFU rsqrt / FP64 rates and the far pair's
+    register-only rate of one GPU (see include/sbio.h); returns a dict."""
+    out = sbio_peaks()
+    _check(_lib.sbio_measure_peaks(device, C.byref(out)))
+    return {k: getattr(out, k) for k, _ in sbio_peaks._fields_ if k != "reserved"}
 
 
 def sbio_apply_self_noalloc(spheroids, p, sigma_tilde, mu_hat, S_out, D_out, n_phi=0, stream=None):

@@ -83,3 +83,37 @@ def test_batch_rejects_fp64_geometries(S):
     assert e.value.code == S.SBIO_EINVAL
     g.close()
     S.sbio_ctx_destroy(ctx)
+
+
+def test_batch_against_oracle_sampled(S):
+    """Each suspension of one batched step against the CPU oracle's method on
+    sampled targets, at the mixed bound; the batch spans the batched
+    workload's ranges, including a suspension with M >= 300 and one at
+    p = 20."""
+    from oracle import geometry as OG
+    from oracle import laplace as OL
+
+    ctx = S.sbio_ctx_create(0, 0)
+    specs = [(320, 20, 0.15), (40, 8, 0.25), (12, 12, 0.05), (90, 16, 0.20)]
+    susps = [I.rsa_suspension(M, phi, 640 + k, p, name=f"bo{k}") for k, (M, p, phi) in enumerate(specs)]
+    geoms = [S.Geometry(ctx, s, precision=S.SBIO_MIXED) for s in susps]
+    coefs = [I.config_coefficients(s, 11 + k) for k, s in enumerate(susps)]
+    sig = [torch.from_numpy(c[0]).cuda() for c in coefs]
+    mu = [torch.from_numpy(c[1]).cuda() for c in coefs]
+    outS = [torch.full((g.N,), float("nan"), dtype=torch.float64, device="cuda") for g in geoms]
+    outD = [torch.full_like(o, float("nan")) for o in outS]
+    b = S.sbio_batch_create(ctx, geoms)
+    S.sbio_batch_apply(b, sig, mu, outS, outD)
+    torch.cuda.synchronize()
+    for k, (s, g, c) in enumerate(zip(susps, geoms, coefs)):
+        og = OG.SuspensionGeom.from_suspension(s)
+        tg = np.sort(np.random.default_rng(k).choice(g.N, 20, replace=False))
+        Sr, Dr = OL.LaplaceOracle(og).apply(c[0], c[1], "method", targets=tg)
+        eS = np.max(np.abs(outS[k].cpu().numpy()[tg] - Sr)) / np.max(np.abs(Sr))
+        eD = np.max(np.abs(outD[k].cpu().numpy()[tg] - Dr)) / np.max(np.abs(Dr))
+        print(f"batch suspension {k} (M={s.M}, p={s.p}): S {eS:.2e} D {eD:.2e}")
+        assert eS < TOLMIX and eD < TOLMIX, (k, eS, eD)
+    S.sbio_batch_destroy(b)
+    for g in geoms:
+        g.close()
+    S.sbio_ctx_destroy(ctx)

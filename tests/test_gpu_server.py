@@ -116,3 +116,29 @@ def test_invalid_request_rejected(S):
     assert e.value.code == S.SBIO_EINVAL
     S.sbio_server_destroy(srv)
     S.sbio_ctx_destroy(ctx)
+
+
+def test_served_results_against_oracle_sampled(S):
+    """One Laplace S + D and one Stokes request served together (mixed
+    precision) against the CPU oracle's method on sampled targets, for every
+    apply of each request, at the mixed bound."""
+    from oracle import geometry as OG
+    from oracle import laplace as OL
+    from oracle import stokes as OSt
+
+    ctx = S.sbio_ctx_create(0, 0)
+    reqs = [r for r in make_requests() if r["s"].M in (14, 5)]     # one Laplace (M 14, p 8), one Stokes (M 5, p 12)
+    assert sorted(r["op"] for r in reqs) == ["laplace", "stokes"]
+    outs, _ = run(S, ctx, reqs, 2)
+    for k, (r, out) in enumerate(zip(reqs, outs)):
+        og = OG.SuspensionGeom.from_suspension(r["s"])
+        tg = np.sort(np.random.default_rng(k).choice(r["N"], 25, replace=False))
+        for a in range(NAPPLY):
+            if r["op"] == "laplace":
+                Sr, Dr = OL.LaplaceOracle(og).apply(r["coef"][a, 0], r["coef"][a, 1], "method", targets=tg)
+                for got, ref in ((out[a][:r["N"]][tg], Sr), (out[a][r["N"]:][tg], Dr)):
+                    assert np.max(np.abs(got - ref)) / np.max(np.abs(ref)) < 1e-6
+            else:
+                Ur = OSt.StokesOracle(og).apply(r["coef"][a], "method", targets=tg)
+                assert np.max(np.abs(out[a][tg] - Ur)) / np.max(np.abs(Ur)) < 1e-6
+    S.sbio_ctx_destroy(ctx)

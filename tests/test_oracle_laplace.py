@@ -70,6 +70,32 @@ def test_capacitance(kind, A, C):
     np.testing.assert_allclose(Sx, q * radial / (4 * math.pi * a), rtol=1e-12)
 
 
+@pytest.mark.parametrize("kind,A,C", [(0, 1 / 64, 1.0), (1, 1.0, 1 / 64), (0, 1 / 26, 1.0), (1, 1.0, 0.1)])
+def test_capacitance_high_aspect_ratio(kind, A, C):
+    """The conductor at aspect ratios up to 64 (the paper's stress tests):
+    constant surface potential, the textbook capacitance, and the exterior
+    potential q Q_0(u) / (4 pi a) down to 1e-3 from the surface, where u is
+    within 1e-4 of u0 = 1 (prolate) and Q_0 varies fastest."""
+    p = 12
+    P, _, _ = _particle(kind, A, C, p)
+    mult = LP.multipliers(kind, P.a, P.u0, p)
+    sig = np.zeros((p + 1) ** 2)
+    sig[0] = 1.0
+    S, _ = LP.self_values(P, mult, sig, None)
+    assert np.ptp(S) < 1e-12 * abs(S.mean())
+    sval, _ = LP.density_values(P, sig, None)
+    q = np.sum(P.w * sval)
+    u0, a = P.u0, P.a
+    ref = 8 * math.pi * a / math.log((u0 + 1) / (u0 - 1)) if kind == 0 else 4 * math.pi * a / math.atan(1 / u0)
+    assert abs(q / S.mean() / ref - 1) < 1e-11
+    k = np.arange(0, len(P.x), 7)
+    x = np.concatenate([P.x[k] + d * P.nrm[k] for d in (1e-3, 1e-2, 1e-1, 1.0)])
+    Sx, _ = LP.solid_eval(P, mult, x, sig, None)
+    u, _, _ = P.to_spheroidal(x)
+    radial = 0.5 * np.log((u + 1) / (u - 1)) if kind == 0 else np.arctan(1 / u)
+    np.testing.assert_allclose(Sx, q * radial / (4 * math.pi * a), rtol=1e-11)
+
+
 @pytest.mark.parametrize("kind,A,C", SHAPES)
 def test_gauss_law_double_layer(kind, A, C):
     """D[1] = -1/2 on the surface (principal value), 0 outside, -1 inside."""

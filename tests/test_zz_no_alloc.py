@@ -72,3 +72,30 @@ def test_noalloc_rejects_requests_beyond_the_fixed_array(S):
         S.sbio_apply_self_noalloc(sph, susp.p, sig, None, out, None)
     assert e.value.code == S.SBIO_EINVAL
     assert "scratch" in str(e.value)
+
+
+def test_noalloc_refuses_a_capturing_stream(S):
+    # the tables are staged from a host buffer freed when the call returns,
+    # so a call recorded into a graph would read freed memory at replay:
+    # the entry point refuses a stream that is being captured
+    susp = I.config_suspension(1)
+    coef = I.config_coefficients(susp, 0)
+    sig = torch.from_numpy(coef[0]).cuda()
+    sph = S.make_spheroids(susp.kind, susp.A, susp.C, susp.center, susp.quat)
+    out = torch.zeros(susp.M * (susp.p + 1) * 2 * (susp.p + 1), dtype=torch.float64, device="cuda")
+    side = torch.cuda.Stream()
+    x = torch.zeros(4, device="cuda")
+    graph = torch.cuda.CUDAGraph()
+    err = None
+    torch.cuda.synchronize()
+    with torch.cuda.graph(graph, stream=side):
+        x.add_(1.0)                              # keeps the captured graph non-empty
+        try:
+            S.sbio_apply_self_noalloc(sph, susp.p, sig, None, out, None, stream=side.cuda_stream)
+        except S.SbioError as e:
+            err = e
+    assert err is not None and err.code == S.SBIO_EINVAL
+    assert "captured" in str(err)
+    graph.replay()
+    torch.cuda.synchronize()
+    assert float(x[0]) == 1.0
