@@ -119,30 +119,37 @@ class Particle:
 
 
 def cart_to_spheroidal(xl, kind, a):
-    """Inverse of Table 1 through focal distances in the meridian plane.
-    prolate: foci (rho, z) = (0, +-a):  u = (r+ + r-)/(2a), v = z/(a u)
-    oblate:  focal ring (rho, z) = (+-a, 0): sqrt(u^2+1) = (d+ + d-)/(2a),
-             u = sqrt(((d+ + d-)/(2a))^2 - 1), v = z/(a u)."""
+    """Inverse of Table 1.  With X = rho/a, Z = z/a and s = u^2 - 1 (prolate)
+    or s = u^2 (oblate), Table 1 gives X^2 = s (1 - v^2) and Z^2 = (s + 1) v^2
+    (prolate), X^2 = (s + 1)(1 - v^2) and Z^2 = s v^2 (oblate), so s is the
+    positive root of
+        prolate: s^2 + (1 - X^2 - Z^2) s - X^2 = 0,
+        oblate:  s^2 + (1 - X^2 - Z^2) s - Z^2 = 0,
+    taken in the form without cancellation (c / q or q with the sign of the
+    linear coefficient).  sqrt(1 - v^2) = X / sqrt(s) (prolate) or
+    X / sqrt(s + 1) (oblate) is exact on the symmetry axis, so v is taken from
+    it where |v| > 1/2 (v = +-1 exactly on the axis) and as Z / u elsewhere."""
     xl = np.asarray(xl, dtype=np.float64)
     rho = np.hypot(xl[..., 0], xl[..., 1])
     z = xl[..., 2]
     phi = np.arctan2(xl[..., 1], xl[..., 0])
-    if kind == PROLATE:
-        rp = np.hypot(rho, z - a)
-        rm = np.hypot(rho, z + a)
-        u = (rp + rm) / (2.0 * a)
-        v = np.clip(z / (a * u), -1.0, 1.0)
-    else:
-        dp = np.hypot(rho - a, z)
-        dm = np.hypot(rho + a, z)
-        cu = (dp + dm) / (2.0 * a)
-        u = np.sqrt(np.maximum(cu * cu - 1.0, 0.0))
-        # near the focal disk (u -> 0) use |v| = sqrt(1 - ((d- - d+)/(2a))^2)
-        cv = (dm - dp) / (2.0 * a)
-        v_disk = np.sign(z) * np.sqrt(np.maximum(1.0 - cv * cv, 0.0))
-        with np.errstate(divide="ignore", invalid="ignore"):
-            v_ax = z / (a * u)
-        v = np.clip(np.where(u > 0.05, v_ax, v_disk), -1.0, 1.0)
+    X = rho / a
+    Z = z / a
+    B = (1.0 - X) * (1.0 + X) - Z * Z
+    c = X * X if kind == PROLATE else Z * Z
+    disc = np.sqrt(B * B + 4.0 * c)
+    with np.errstate(divide="ignore", invalid="ignore"):
+        s = np.where(B > 0.0, 2.0 * c / (B + disc), 0.5 * (disc - B))
+        if kind == PROLATE:
+            u = np.sqrt(1.0 + s)
+            sv = np.where(s > 0.0, X / np.sqrt(s), 1.0)
+        else:
+            u = np.sqrt(s)
+            sv = X / np.sqrt(1.0 + s)
+        sv = np.minimum(sv, 1.0)
+        v_lin = np.where(u > 0.0, Z / u, 0.0)
+    v_pol = np.sign(Z) * np.sqrt(np.maximum(1.0 - sv * sv, 0.0))
+    v = np.clip(np.where(np.abs(v_lin) > 0.5, v_pol, v_lin), -1.0, 1.0)
     return u, v, phi
 
 

@@ -301,3 +301,21 @@ def test_planted_sign_error_is_caught(monkeypatch):
     Sx, _ = LP.solid_eval(P, bad, x, sig, None)
     assert LP.normwise_rel_err(Sg, Sb) < 1e-11
     assert LP.normwise_rel_err(Sx, Sb) > 1e-3
+
+
+@pytest.mark.parametrize("kind,A,C", [(0, 1 / 64, 1.0), (1, 1.0, 0.1), (0, 1.0, 2.0), (1, 1.5, 0.75)])
+def test_coordinate_inverse_round_trip(kind, A, C):
+    """Table 1 and its inverse: points built from (u, v, phi) come back to
+    (u, v) within rounding, including points on the symmetry axis (v = +-1
+    exactly, so every m > 0 harmonic vanishes there), next to the focal
+    segment or ring, and close to the equator."""
+    a, u0 = G.spheroid_params(kind, A, C)
+    rng = np.random.default_rng(3)
+    for u in (u0 * (1 + 1e-3), u0 * 1.5, 3.0 * u0 + 0.5):
+        v = np.concatenate([[-1.0, 1.0, 0.0, 1e-9, -1e-9], rng.uniform(-1, 1, 40), 1 - 10.0 ** -rng.uniform(2, 9, 10)])
+        phi = rng.uniform(0, 2 * math.pi, v.shape)
+        xl = G.local_point(kind, a, np.full(v.shape, u), v, phi)
+        u2, v2, _ = G.cart_to_spheroidal(xl, kind, a)
+        np.testing.assert_allclose(u2, u, rtol=1e-13)
+        np.testing.assert_allclose(v2, v, atol=2e-13)
+        assert v2[0] == -1.0 and v2[1] == 1.0
