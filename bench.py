@@ -1404,20 +1404,49 @@ def run_far_sweep(args, ws, rank, lrank):
             far.append(S.sbio_geom_phase_times(g.h)[2])
         S.sbio_geom_enable_timing(g.h, False)
         far_ms = statistics.median(far)
-        rows.append({"M": susp.M, "targets": g.N, "near_pairs": g.n_near, "far_pairs": g.n_far,
-                     "far_launch": {"targets_per_thread": tune[0], "source_splits": tune[1]},
-                     "direct_far_ms": far_ms, "direct_gpairs_per_s": g.n_far / (far_ms * 1e-3) / 1e9,
-                     "apply_ms": statistics.median(whole),
-                     "far_frac_of_fp32_peak": FAR_FLOP_PER_PAIR["SD"] * g.n_far / (far_ms * 1e-3) / 1e12 / fp32_peak()})
+        Sd, Dd = So.clone(), Do.clone()
+        row = {"M": susp.M, "targets": g.N, "near_pairs": g.n_near, "far_pairs": g.n_far,
+               "far_launch": {"targets_per_thread": tune[0], "source_splits": tune[1]},
+               "direct_far_ms": far_ms, "direct_gpairs_per_s": g.n_far / (far_ms * 1e-3) / 1e9,
+               "apply_ms": statistics.median(whole),
+               "far_frac_of_fp32_peak": FAR_FLOP_PER_PAIR["SD"] * g.n_far / (far_ms * 1e-3) / 1e12 / fp32_peak()}
+        # the same applies with the treecode far field (order 16, theta 0.5)
+        t0 = time.perf_counter()
+        S.sbio_geom_set_far_method(g.h, S.SBIO_FAR_TREE, 0.5, 16)
+        build_ms = (time.perf_counter() - t0) * 1e3
+        info = S.sbio_geom_tree_info(g.h)
+        for _ in range(2):
+            S.sbio_apply_laplace(g.h, sig, mu, So, Do)
+        twhole = []
+        for _ in range(reps):
+            flush.zero_()
+            twhole.append(_event_time(st, lambda: S.sbio_apply_laplace(g.h, sig, mu, So, Do)))
+        S.sbio_geom_enable_timing(g.h, True)
+        tfar = []
+        for _ in range(reps):
+            flush.zero_()
+            S.sbio_apply_laplace(g.h, sig, mu, So, Do)
+            tfar.append(S.sbio_geom_phase_times(g.h)[2])
+        S.sbio_geom_enable_timing(g.h, False)
+        S.sbio_apply_laplace(g.h, sig, mu, So, Do)
+        torch.cuda.synchronize()
+        row["tree"] = {"order": 16, "theta": 0.5, "far_ms": statistics.median(tfar),
+                       "apply_ms": statistics.median(twhole), "setup_ms": build_ms,
+                       "speedup_far_vs_direct": far_ms / statistics.median(tfar),
+                       "rel_err_vs_direct_mixed": {"S": float((So - Sd).abs().max() / Sd.abs().max()),
+                                                   "D": float((Do - Dd).abs().max() / Dd.abs().max())},
+                       "m2p_evaluations": info["m2p_pairs"], "direct_pairs": info["direct_pairs"],
+                       "direct_pair_fraction": info["direct_pairs"] / g.n_far, "tree_nodes": info["nodes"]}
+        rows.append(row)
         g.close()
     clk = clocks.stop()
     set_peak_basis(lrank, clk)
     for r in rows:
         r["far_frac_of_fp32_peak"] = FAR_FLOP_PER_PAIR["SD"] * r["far_pairs"] / (r["direct_far_ms"] * 1e-3) / 1e12 / fp32_peak()
     big = rows[-1]
-    line = {"metric": "Laplace S+D apply time vs suspension size (direct tiled far field, mixed)",
-            "value": 1e3 / big["apply_ms"], "unit": "applies/s", "n_gpus": ws, "steps": len(rows), "warmup": 2,
-            "ms_per_step": big["apply_ms"], "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+    line = {"metric": "Laplace S+D apply time vs suspension size (direct tiled far field and treecode, mixed)",
+            "value": 1e3 / big["tree"]["apply_ms"], "unit": "applies/s", "n_gpus": ws, "steps": len(rows), "warmup": 2,
+            "ms_per_step": big["tree"]["apply_ms"], "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f32+f64", "data": "synthetic",
             "config": {"workload": "far_sweep_p16", "M": Ms, "p": 16,
                        "geometry": "AR U[1.2,5], major U[0.5,1.5], phi=20%, gap>=0.05, RSA seed 0",

@@ -345,6 +345,36 @@ int sbio_geom_get_stokes_tuning(const sbio_geom* g, int32_t* far_tt, int32_t* fa
 int sbio_geom_autotune_stokes(sbio_geom* g, void* stream, int32_t* far_tt, int32_t* far_splits, double* far_ms);
 
 
+/* ---- far field by a particle treecode -----------------------------------
+ * The paper evaluates the far field with an FMM (Sec. 4.1 "Far-field"); past
+ * a few hundred particles the O(N^2) direct sum here grows too slow, and a
+ * treecode can replace it for mixed-precision S + D applies at the nodes
+ * (sbio_apply_laplace / _parts / _host with both operators): a binary tree
+ * over the particles, solid-harmonic multipoles of order `order` (8, 12 or
+ * 16) of every node's sources (charges q = w sigma for S, dipoles
+ * d = w mu nu for D), accepted for a group of 256 consecutive targets when
+ * every target is at least r_node / theta from the node's centre and the
+ * node holds none of the group's own or near particles; every other particle
+ * is summed directly with the per-target skip lists.  The result is the same
+ * discrete far sum (Sec. 4.1 quadrature over the far particles' nodes) up to
+ * the truncation of the expansions, about (theta)^(order+1) relative per
+ * node.  SBIO_FAR_TREE builds the tree and lists on the host (synchronises
+ * the device); SBIO_FAR_DIRECT (theta, order ignored) returns to the direct
+ * sum.  FP64 geometries and the other operators keep the direct sum.
+ * Errors: SBIO_EINVAL (method, theta outside (0.05, 1), order), SBIO_ENOMEM,
+ * SBIO_ECUDA. */
+#define SBIO_FAR_DIRECT 0
+#define SBIO_FAR_TREE 1
+int sbio_geom_set_far_method(sbio_geom* g, int32_t method, double theta, int32_t order);
+
+/* Sizes of the treecode far field per apply: tree nodes, target groups,
+ * (target, multipole node) evaluations, the (target, source node) pairs those
+ * evaluations stand for, and the (target, source node) pairs summed
+ * directly; the last two add up to the geometry's far pair count (every far
+ * pair is covered once).  SBIO_EINVAL if the geometry uses the direct sum. */
+int sbio_geom_tree_info(const sbio_geom* g, int64_t* n_nodes, int64_t* n_groups, int64_t* m2p_pairs,
+                        int64_t* m2p_source_pairs, int64_t* direct_pairs);
+
 /* ---- particle-to-target evaluation (Sec. 4.1, "Particle-to-target
  * algorithm") ---------------------------------------------------------------
  * S[sigma] and D[mu] of every spheroid of a geometry at T arbitrary points in

@@ -23,7 +23,7 @@ LIB = os.path.join(PKG, "libsbio.so")
 LIB_HASH = LIB + ".srchash"
 SOURCES = ["sbio_geom.cu", "sbio_laplace.cu", "sbio_stokes.cu", "sbio_noalloc.cu", "sbio_batch.cu", "sbio_server.cu",
            "sbio_deriv.cu", "sbio_targets.cu", "sbio_solve.cu", "sbio_stokes_points.cu", "sbio_stokes_dl.cu",
-           "sbio_peaks.cu"]
+           "sbio_peaks.cu", "sbio_tree.cu"]
 # near-field kernels, split by expansion order so that the unrolled variants compile in parallel
 SOURCES += [f"sbio_near_p{c}.cu" for c in "abcd"]
 SOURCES += [f"sbio_deriv_near_p{c}.cu" for c in "ab"]

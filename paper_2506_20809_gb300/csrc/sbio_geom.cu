@@ -712,6 +712,8 @@ static int build_device(sbio_geom* g) {
 
 static void free_geom(sbio_geom* g) {
   if (!g) return;
+  tree_free(g->tree);   // host tables only; its device arrays are in g->allocs
+  g->tree = nullptr;
   if (g->near_stream) {
     cudaStreamSynchronize(g->near_stream);
     cudaStreamDestroy(g->near_stream);

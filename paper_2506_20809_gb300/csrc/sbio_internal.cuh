@@ -101,6 +101,11 @@ struct GeomHost {
 
 }  // namespace sbio
 
+namespace sbio {
+struct TreeFar;   // particle treecode far field (sbio_tree.cu)
+void tree_free(TreeFar* t);
+}  // namespace sbio
+
 struct sbio_geom {
   sbio_ctx* ctx = nullptr;
   sbio::GeomHost h;
@@ -123,6 +128,9 @@ struct sbio_geom {
   cudaStream_t near_stream = nullptr;
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   std::atomic<int> n_target_sets{0};       // live sbio_targets of this geometry
+  // far field by the particle treecode instead of the direct sum (mixed
+  // precision applies at the nodes only); null = direct
+  sbio::TreeFar* tree = nullptr;
 };
 
 namespace sbio {
@@ -176,6 +184,13 @@ struct FarDesc {
 };
 int launch_far_persistent(const FarDesc* descs, const int4* items, int n_items, int* counter, int tt, int grid,
                           cudaStream_t st);
+// Direct part of the treecode far field: items (target block of 256 targets,
+// first tile, end tile) over a tile list; the geometry's mixed far pair sum
+// (2 packed targets per thread) with its skip lists; defined in sbio_laplace.cu.
+void launch_far_tile_items(const DevGeom& d, const int4* tiles, const int4* items, int n_items, int64_t N,
+                           double* S, double* D, cudaStream_t st);
+// the treecode far field of one apply (sbio_tree.cu)
+int launch_tree_far(sbio_geom* g, double* S, double* D, cudaStream_t st);
 
 // record phase event k (0..3) when timing is enabled
 inline void phase_mark(sbio_geom* g, int k, cudaStream_t st) {

@@ -400,6 +400,29 @@ __global__ void __launch_bounds__(kFarTile) far_mixed_kernel(const int4* __restr
                                       S_out, D_out);
 }
 
+// Direct part of the treecode far field: one CTA per item (target block of
+// 256 targets, tile range of a block-specific tile list).
+__global__ void __launch_bounds__(kFarTile) far_tile_items_kernel(const int4* __restrict__ items,
+                                                                  const int4* __restrict__ tiles,
+                                                                  const float4* __restrict__ src32,
+                                                                  const float4* __restrict__ tgt32,
+                                                                  const float4* __restrict__ cen32,
+                                                                  const int32_t* __restrict__ skip_ptr,
+                                                                  const int32_t* __restrict__ skip_idx, int64_t N,
+                                                                  double* __restrict__ S_out,
+                                                                  double* __restrict__ D_out) {
+  const int4 w = items[blockIdx.x];
+  far_mixed_block<2, true, true, true>(w.x, w.y, w.z, tiles, src32, tgt32, cen32, skip_ptr, skip_idx, N, S_out, D_out);
+}
+
+void launch_far_tile_items(const DevGeom& d, const int4* tiles, const int4* items, int n_items, int64_t N,
+                           double* S, double* D, cudaStream_t st) {
+  if (n_items <= 0) return;
+  far_tile_items_kernel<<<n_items, kFarTile, 0, st>>>(items, tiles, d.src32, d.tgt32, d.cen32, d.skip_ptr,
+                                                      d.skip_idx, N, S, D);
+  count_launch();
+}
+
 // Number of source splits so that the grid holds about `waves` resident
 // rounds of CTAs on the device (never more splits than tiles).
 int sm_count() {
@@ -472,6 +495,11 @@ void launch_far_on(const DevGeom& d, const GeomHost& h, int64_t NT, double* S, d
 }
 
 static void launch_far(sbio_geom* g, double* S, double* D, cudaStream_t st) {
+  // the treecode replaces the direct sum for mixed S + D applies at the nodes
+  if (g->tree && g->h.precision == SBIO_MIXED && S && D) {
+    launch_tree_far(g, S, D, st);
+    return;
+  }
   launch_far_on(g->d, g->h, g->h.N, S, D, st);
 }
 
@@ -821,7 +849,12 @@ int sbio_geom_autotune(sbio_geom* g, void* stream, int32_t* far_tt, int32_t* far
   ops.splits = &h.far_splits;
   ops.cap = &h.near_ctas_per_sm;
   double best = 0.0;
+  // the direct kernel's shapes are tuned with the direct far field, also
+  // when the geometry uses the treecode (whose direct part has a fixed shape)
+  TreeFar* tree = g->tree;
+  g->tree = nullptr;
   rc = tune_launch_shape(g, ops, d.host_out, st, &best);
+  g->tree = tree;
   if (rc) return rc;
   if (far_tt) *far_tt = h.far_tt;
   if (far_splits) *far_splits = h.far_splits;

@@ -1,0 +1,695 @@
+// Far field by a particle treecode (mixed precision), for suspensions past
+// the size where the O(N^2) direct sum stops being the kernel of choice.  The
+// paper evaluates its far field with an FMM (Sec. 4.1 "Far-field", Sec. 4.2);
+// this is a Barnes-Hut style treecode over the particles with solid-harmonic
+// multipoles, built to reproduce the same discrete far sum as the direct
+// kernel: the smooth quadrature over the nodes of every particle that is
+// neither the target's own nor one of its near particles.
+//
+// Expansions.  With the solid harmonics (m >= 0; P_n^m with the
+// Condon-Shortley phase)
+//     R_n^m(r) = r^n P_n^m(cos t) e^{i m p} / (n+m)!,
+//     I_n^m(r) = (n-m)! P_n^m(cos t) e^{i m p} / r^{n+1},
+// R_n^{-m} = (-1)^m conj(R_n^m), likewise I, the addition theorem reads
+//     1 / |x - y| = sum_{n, |m| <= n} conj(R_n^m(y - c)) I_n^m(x - c),  |y-c| < |x-c|,
+// so a cluster of charges q_j and dipoles d_j about c has the multipoles
+//     M_n^m = sum_j q_j conj(R_n^m(y_j - c))                       (S)
+//     M_n^m = sum_j d_j . grad conj(R_n^m)(y_j - c)                 (D)
+// and its potential is sum_n [M_n^0 I_n^0 + 2 Re sum_{m>0} M_n^m I_n^m].
+// The dipole moments use the ladder relations d/dz R_n^m = R_{n-1}^m,
+// (d/dx + i d/dy) R_n^m = R_{n-1}^{m+1}, (d/dx - i d/dy) R_n^m = -R_{n-1}^{m-1}:
+//     d . grad conj(R_n^m) = d_z conj R_{n-1}^m + delta conj R_{n-1}^{m+1}
+//                            - conj(delta) conj R_{n-1}^{m-1},  delta = (d_x + i d_y)/2.
+// A parent's multipoles are its children's translated by
+//     M'_n^m = sum_{k <= n, |l| <= k} conj(R_k^l(c - c')) M_{n-k}^{m-l}.
+// Both harmonics follow three-term recurrences in Cartesian coordinates
+// (x, y, z, r^2), so no trigonometric function is evaluated.
+//
+// Tree and lists (host, once per geometry and accuracy setting).  A binary
+// tree over the particles, split at the median centre along the longest
+// extent; a leaf is one particle (its centre and major semi-axis bound all of
+// its nodes).  Targets are taken in groups of 256 consecutive nodes (the
+// direct kernel's target block).  For each group a walk from the root accepts
+// a node when, for every target of the group, |x - c_n| >= r_n / theta and
+// the node holds none of the group's own or near particles; a leaf that is
+// not accepted goes to the group's direct list, evaluated by the direct
+// mixed kernel with the per-target skip lists, so each (target, particle)
+// pair outside the target's own and near set is counted exactly once.
+//
+// Per apply: leaf multipoles from the FP32 sources (FP32 per warp, FP64
+// across warps), translations up the tree in FP64, conversion to FP32, then
+// the direct part and the multipole evaluations (FP32, per-node sums folded
+// by TwoSum), each added atomically into the FP64 outputs.
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
+#include "sbio_internal.cuh"
+
+namespace sbio {
+
+constexpr int kTreeGroup = 2 * kFarTile;   // targets per group (direct kernel: 2 per thread)
+constexpr int kTreeChunkNodes = 16;        // multipole nodes per evaluation CTA
+constexpr int kTreeChunkTiles = 32;        // direct source tiles per CTA
+constexpr double kInv4PiTree = 0.07957747154594767;
+
+struct TreeNodeH {
+  double c[3];
+  double r;
+  int first, count;   // particle range in tree order
+  int child[2];
+  int level;
+};
+
+struct TreeFar {
+  int order = 16;
+  double theta = 0.5;
+  int n_nodes = 0, n_levels = 0, n_groups = 0;
+  std::vector<TreeNodeH> nodes;
+  std::vector<int> perm;                     // tree position -> particle
+  std::vector<int> pos;                      // particle -> tree position
+  std::vector<std::vector<int>> levels;      // internal node ids per level
+  int64_t m2p_pairs = 0, direct_pairs = 0, m2p_entries = 0, direct_tiles = 0;
+  int64_t m2p_source_pairs = 0;   // (target, source node) pairs the accepted nodes stand for
+  // device
+  double* d_geo = nullptr;        // n_nodes x 4: centre, radius
+  float4* d_c32 = nullptr;        // n_nodes x 2: hi, lo parts of the centre
+  int* d_child = nullptr;         // n_nodes x 2
+  int* d_leaf = nullptr;          // particle -> node id
+  int* d_levels = nullptr;        // internal node ids, level by level (deepest last)
+  std::vector<int> level_off;     // offsets into d_levels
+  double2* d_M = nullptr;         // n_nodes x 2 x NM: FP64 multipoles (S, D)
+  float2* d_M32 = nullptr;        // n_nodes x 2 x NM: FP32, m > 0 doubled
+  int4* d_tiles = nullptr;        // direct source tiles, group after group
+  int4* d_ditems = nullptr;       // (group, first tile, end tile, 0)
+  int n_ditems = 0;
+  int* d_mlist = nullptr;         // accepted node ids, group after group
+  int4* d_mitems = nullptr;       // (group, first entry, end entry, 0)
+  int n_mitems = 0;
+};
+
+void tree_free(TreeFar* t) { delete t; }
+
+__host__ __device__ constexpr int tree_nm(int p) { return (p + 1) * (p + 2) / 2; }
+__host__ __device__ inline int tree_idx(int n, int m) { return n * (n + 1) / 2 + m; }
+
+// ---------------------------------------------------------------------------
+// kernels
+// ---------------------------------------------------------------------------
+
+// Leaf multipoles about each particle's centre from its nodes' FP32 sources
+// (y - c, q), (d, 0).  One CTA (4 warps) per particle; lane m of a warp owns
+// column m of the harmonics and all warps step through n together, so the
+// dipole terms can take R_{n-1}^{m+-1} from the neighbouring lanes.
+template <int PF>
+__global__ void __launch_bounds__(128) tree_p2m_kernel(int G, const float4* __restrict__ src32,
+                                                       const int* __restrict__ leaf, double2* __restrict__ Mout) {
+  constexpr int NM = tree_nm(PF);
+  __shared__ float red[4][32][PF + 1][4];
+  const int i = blockIdx.x;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int m = lane;
+  float aSr[PF + 1], aSi[PF + 1], aDr[PF + 1], aDi[PF + 1];
+#pragma unroll
+  for (int n = 0; n <= PF; ++n) aSr[n] = aSi[n] = aDr[n] = aDi[n] = 0.f;
+  for (int j = warp; j < G; j += 4) {
+    const float4 A = src32[((int64_t)i * G + j) * 2 + 0];
+    const float4 B = src32[((int64_t)i * G + j) * 2 + 1];
+    const float x = A.x, y = A.y, z = A.z, q = A.w;
+    const float r2 = fmaf(z, z, fmaf(y, y, x * x));
+    const float dr = 0.5f * B.x, di = 0.5f * B.y, dz = B.z;   // delta = (d_x + i d_y) / 2
+    // R_m^m = (-(x + i y) / 2)^m / m!
+    float mr = 1.f, mi = 0.f;
+#pragma unroll
+    for (int k = 1; k <= PF; ++k) {
+      if (k <= m) {
+        const float s = -0.5f / (float)k;
+        const float tr = s * (x * mr - y * mi), ti = s * (x * mi + y * mr);
+        mr = tr;
+        mi = ti;
+      }
+    }
+    float r1r = 0.f, r1i = 0.f, r2r = 0.f, r2i = 0.f;   // R_{n-1}^m, R_{n-2}^m of this lane's column
+#pragma unroll
+    for (int n = 0; n <= PF; ++n) {
+      float cr, ci;
+      if (n < m) {
+        cr = ci = 0.f;
+      } else if (n == m) {
+        cr = mr;
+        ci = mi;
+      } else if (n == m + 1) {
+        cr = z * r1r;
+        ci = z * r1i;
+      } else {
+        const float f = 1.f / (float)((n - m) * (n + m));
+        const float a = (float)(2 * n - 1) * z;
+        cr = (a * r1r - r2 * r2r) * f;
+        ci = (a * r1i - r2 * r2i) * f;
+      }
+      // R_{n-1} of the neighbouring columns (zero where the column has not started)
+      const float upr = __shfl_down_sync(0xffffffffu, r1r, 1), upi = __shfl_down_sync(0xffffffffu, r1i, 1);
+      const float dnr = __shfl_up_sync(0xffffffffu, r1r, 1), dni = __shfl_up_sync(0xffffffffu, r1i, 1);
+      if (m <= PF && n >= m) {
+        aSr[n] = fmaf(q, cr, aSr[n]);
+        aSi[n] = fmaf(-q, ci, aSi[n]);
+        if (n >= 1) {
+          float er = dz * r1r, ei = -dz * r1i;                   // d_z conj R_{n-1}^m
+          er += dr * upr + di * upi;                              // delta conj R_{n-1}^{m+1}
+          ei += di * upr - dr * upi;
+          if (m >= 1) {                                           // - conj(delta) conj R_{n-1}^{m-1}
+            er -= dr * dnr - di * dni;
+            ei += dr * dni + di * dnr;
+          } else {                                                // m = 0: + conj(delta) R_{n-1}^{1}
+            er += dr * upr + di * upi;
+            ei += dr * upi - di * upr;
+          }
+          aDr[n] += er;
+          aDi[n] += ei;
+        }
+      }
+      r2r = r1r;
+      r2i = r1i;
+      r1r = cr;
+      r1i = ci;
+    }
+  }
+#pragma unroll
+  for (int n = 0; n <= PF; ++n) {
+    red[warp][lane][n][0] = aSr[n];
+    red[warp][lane][n][1] = aSi[n];
+    red[warp][lane][n][2] = aDr[n];
+    red[warp][lane][n][3] = aDi[n];
+  }
+  __syncthreads();
+  const int node = leaf[i];
+  for (int k = threadIdx.x; k < NM; k += blockDim.x) {
+    int n = 0;
+    while (tree_idx(n + 1, 0) <= k) ++n;
+    const int mm = k - tree_idx(n, 0);
+    double sr = 0, si = 0, er = 0, ei = 0;
+#pragma unroll
+    for (int w = 0; w < 4; ++w) {
+      sr += red[w][mm][n][0];
+      si += red[w][mm][n][1];
+      er += red[w][mm][n][2];
+      ei += red[w][mm][n][3];
+    }
+    Mout[((int64_t)node * 2 + 0) * NM + k] = make_double2(sr, si);
+    Mout[((int64_t)node * 2 + 1) * NM + k] = make_double2(er, ei);
+  }
+}
+
+// R_k^l(b), l >= 0, k <= PF, in FP64 (serial; one thread)
+template <int PF>
+__device__ void regular_harmonics(double x, double y, double z, double2* R) {
+  const double r2 = x * x + y * y + z * z;
+  double mr = 1.0, mi = 0.0;
+  for (int m = 0; m <= PF; ++m) {
+    if (m > 0) {
+      const double s = -0.5 / m;
+      const double tr = s * (x * mr - y * mi), ti = s * (x * mi + y * mr);
+      mr = tr;
+      mi = ti;
+    }
+    R[tree_idx(m, m)] = make_double2(mr, mi);
+    if (m + 1 <= PF) R[tree_idx(m + 1, m)] = make_double2(z * mr, z * mi);
+    for (int n = m + 2; n <= PF; ++n) {
+      const double f = 1.0 / ((double)(n - m) * (n + m));
+      const double2 a = R[tree_idx(n - 1, m)], b = R[tree_idx(n - 2, m)];
+      R[tree_idx(n, m)] = make_double2(((2 * n - 1) * z * a.x - r2 * b.x) * f, ((2 * n - 1) * z * a.y - r2 * b.y) * f);
+    }
+  }
+}
+
+// value of a stored (n, m >= 0) table at order l of either sign, for tables
+// of real sources: T_n^{-l} = (-1)^l conj(T_n^l)
+__device__ __forceinline__ double2 signed_order(const double2* T, int n, int l) {
+  if (l >= 0) return T[tree_idx(n, l)];
+  const double2 v = T[tree_idx(n, -l)];
+  return (l & 1) ? make_double2(-v.x, v.y) : make_double2(v.x, -v.y);
+}
+
+// One tree level: each internal node's multipoles from its two children's.
+template <int PF>
+__global__ void __launch_bounds__(128) tree_m2m_kernel(const int* __restrict__ ids, const int* __restrict__ child,
+                                                       const double* __restrict__ geo, double2* __restrict__ Mt) {
+  constexpr int NM = tree_nm(PF);
+  __shared__ double2 Rb[2][NM];
+  __shared__ double2 Mc[2][2][NM];
+  const int node = ids[blockIdx.x];
+  const int ch[2] = {child[node * 2 + 0], child[node * 2 + 1]};
+  if (threadIdx.x == 0 || threadIdx.x == 32) {
+    const int k = threadIdx.x == 0 ? 0 : 1;
+    const int c = ch[k];
+    regular_harmonics<PF>(geo[c * 4 + 0] - geo[node * 4 + 0], geo[c * 4 + 1] - geo[node * 4 + 1],
+                          geo[c * 4 + 2] - geo[node * 4 + 2], Rb[k]);
+  }
+  for (int k = threadIdx.x; k < 4 * NM; k += blockDim.x) {
+    const int c = k / (2 * NM), rest = k - c * 2 * NM;
+    Mc[c][rest / NM][rest % NM] = Mt[((int64_t)ch[c] * 2 + rest / NM) * NM + rest % NM];
+  }
+  __syncthreads();
+  for (int k = threadIdx.x; k < 2 * NM; k += blockDim.x) {
+    const int kind = k / NM, idx = k - kind * NM;
+    int n = 0;
+    while (tree_idx(n + 1, 0) <= idx) ++n;
+    const int m = idx - tree_idx(n, 0);
+    double ar = 0.0, ai = 0.0;
+    for (int c = 0; c < 2; ++c)
+      for (int kk = 0; kk <= n; ++kk)
+        for (int l = -kk; l <= kk; ++l) {
+          const int nn = n - kk, mm = m - l;
+          if (mm > nn || mm < -nn) continue;
+          const double2 r = signed_order(Rb[c], kk, l);
+          const double2 v = signed_order(Mc[c][kind], nn, mm);
+          // conj(r) * v
+          ar += r.x * v.x + r.y * v.y;
+          ai += r.x * v.y - r.y * v.x;
+        }
+    Mt[((int64_t)node * 2 + kind) * NM + idx] = make_double2(ar, ai);
+  }
+}
+
+// FP32 copy of every node's multipoles with the m > 0 terms doubled, so the
+// evaluation is sum_{n, m >= 0} Re(M I)
+template <int PF>
+__global__ void tree_to_f32_kernel(int64_t total, const double2* __restrict__ Mt, float2* __restrict__ M32) {
+  constexpr int NM = tree_nm(PF);
+  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < total; k += (int64_t)gridDim.x * blockDim.x) {
+    const int idx = (int)(k % NM);
+    int n = 0;
+    while (tree_idx(n + 1, 0) <= idx) ++n;
+    const double w = (idx - tree_idx(n, 0)) > 0 ? 2.0 : 1.0;
+    const double2 v = Mt[k];
+    M32[k] = make_float2((float)(w * v.x), (float)(w * v.y));
+  }
+}
+
+// Multipole evaluation: one CTA per (group of 256 targets, up to
+// kTreeChunkNodes accepted nodes), two targets per thread.
+template <int PF>
+__global__ void __launch_bounds__(kFarTile) tree_m2p_kernel(const int4* __restrict__ items, const int* __restrict__ mlist,
+                                                            const float4* __restrict__ c32,
+                                                            const float2* __restrict__ M32,
+                                                            const float4* __restrict__ tgt32, int64_t N,
+                                                            double* __restrict__ S_out, double* __restrict__ D_out) {
+  constexpr int NM = tree_nm(PF);
+  __shared__ float2 cf[2 * NM];
+  __shared__ float4 cc[2];
+  const int4 it = items[blockIdx.x];
+  const int tid = threadIdx.x;
+  int64_t t[2];
+  float4 xh[2], xl[2];
+  float hS[2], lS[2], hD[2], lD[2];
+#pragma unroll
+  for (int q = 0; q < 2; ++q) {
+    t[q] = (int64_t)it.x * kTreeGroup + q * kFarTile + tid;
+    xh[q] = xl[q] = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (t[q] < N) {
+      xh[q] = tgt32[t[q] * 2 + 0];
+      xl[q] = tgt32[t[q] * 2 + 1];
+    }
+    hS[q] = lS[q] = hD[q] = lD[q] = 0.f;
+  }
+  for (int e = it.y; e < it.z; ++e) {
+    const int node = mlist[e];
+    __syncthreads();
+    for (int k = tid; k < 2 * NM; k += kFarTile) cf[k] = M32[(int64_t)node * 2 * NM + k];
+    if (tid < 2) cc[tid] = c32[node * 2 + tid];
+    __syncthreads();
+    const float4 ch = cc[0], cl = cc[1];
+    float X[2], Y[2], Z[2], ir2[2], zs[2], Ir[2], Ii[2], sS[2], sD[2];
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+      X[q] = (xh[q].x - ch.x) + (xl[q].x - cl.x);
+      Y[q] = (xh[q].y - ch.y) + (xl[q].y - cl.y);
+      Z[q] = (xh[q].z - ch.z) + (xl[q].z - cl.z);
+      const float r2 = fmaf(Z[q], Z[q], fmaf(Y[q], Y[q], X[q] * X[q]));
+      const float ri = rsqrt_f32(r2);
+      ir2[q] = ri * ri;
+      zs[q] = Z[q] * ir2[q];
+      X[q] *= ir2[q];
+      Y[q] *= ir2[q];
+      Ir[q] = ri;      // I_m^m, starting at I_0^0 = 1 / r
+      Ii[q] = 0.f;
+      sS[q] = sD[q] = 0.f;
+    }
+#pragma unroll
+    for (int m = 0; m <= PF; ++m) {
+      float ar[2], ai[2], br[2], bi[2];   // I_{n-1}^m, I_{n-2}^m
+#pragma unroll
+      for (int q = 0; q < 2; ++q) {
+        if (m > 0) {
+          // I_m^m = -(2m - 1) (x + i y) / r^2 I_{m-1}^{m-1}
+          const float s = -(float)(2 * m - 1);
+          const float tr = s * (X[q] * Ir[q] - Y[q] * Ii[q]), ti = s * (X[q] * Ii[q] + Y[q] * Ir[q]);
+          Ir[q] = tr;
+          Ii[q] = ti;
+        }
+        const float2 a = cf[tree_idx(m, m)], b = cf[NM + tree_idx(m, m)];
+        sS[q] = fmaf(a.x, Ir[q], fmaf(-a.y, Ii[q], sS[q]));
+        sD[q] = fmaf(b.x, Ir[q], fmaf(-b.y, Ii[q], sD[q]));
+        ar[q] = Ir[q];
+        ai[q] = Ii[q];
+        br[q] = bi[q] = 0.f;
+      }
+#pragma unroll
+      for (int n = m + 1; n <= PF; ++n) {
+        const float2 a = cf[tree_idx(n, m)], b = cf[NM + tree_idx(n, m)];
+        const float kz = (float)(2 * n - 1);
+        const float kb = (float)((n - 1 - m) * (n - 1 + m));
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+          // I_n^m = ((2n - 1) z I_{n-1}^m - (n-1-m)(n-1+m) I_{n-2}^m) / r^2
+          const float u = kz * zs[q], v = kb * ir2[q];
+          const float cr = fmaf(u, ar[q], -v * br[q]), ci = fmaf(u, ai[q], -v * bi[q]);
+          sS[q] = fmaf(a.x, cr, fmaf(-a.y, ci, sS[q]));
+          sD[q] = fmaf(b.x, cr, fmaf(-b.y, ci, sD[q]));
+          br[q] = ar[q];
+          bi[q] = ai[q];
+          ar[q] = cr;
+          ai[q] = ci;
+        }
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+      float s, e;
+      two_sum_f32(hS[q], sS[q], s, e);
+      hS[q] = s;
+      lS[q] += e;
+      two_sum_f32(hD[q], sD[q], s, e);
+      hD[q] = s;
+      lD[q] += e;
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < 2; ++q)
+    if (t[q] < N) {
+      atomicAdd(S_out + t[q], ((double)hS[q] + (double)lS[q]) * kInv4PiTree);
+      atomicAdd(D_out + t[q], ((double)hD[q] + (double)lD[q]) * kInv4PiTree);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// host: tree, lists, launches
+// ---------------------------------------------------------------------------
+
+static int build_nodes(TreeFar& T, const GeomHost& h, int lo, int hi, int level) {
+  const int id = (int)T.nodes.size();
+  T.nodes.push_back(TreeNodeH());
+  double bmin[3] = {1e300, 1e300, 1e300}, bmax[3] = {-1e300, -1e300, -1e300};
+  for (int k = lo; k < hi; ++k) {
+    const PartGeom& P = h.parts[T.perm[k]];
+    const double R = std::max(P.A, P.C);
+    for (int c = 0; c < 3; ++c) {
+      bmin[c] = std::min(bmin[c], P.c[c] - R);
+      bmax[c] = std::max(bmax[c], P.c[c] + R);
+    }
+  }
+  TreeNodeH nd;
+  double r = 0.0;
+  for (int c = 0; c < 3; ++c) nd.c[c] = 0.5 * (bmin[c] + bmax[c]);
+  for (int k = lo; k < hi; ++k) {
+    const PartGeom& P = h.parts[T.perm[k]];
+    const double d = std::sqrt((P.c[0] - nd.c[0]) * (P.c[0] - nd.c[0]) + (P.c[1] - nd.c[1]) * (P.c[1] - nd.c[1]) +
+                               (P.c[2] - nd.c[2]) * (P.c[2] - nd.c[2]));
+    r = std::max(r, d + std::max(P.A, P.C));
+  }
+  nd.r = r;
+  nd.first = lo;
+  nd.count = hi - lo;
+  nd.child[0] = nd.child[1] = -1;
+  nd.level = level;
+  T.n_levels = std::max(T.n_levels, level + 1);
+  if (hi - lo > 1) {
+    double cmin[3] = {1e300, 1e300, 1e300}, cmax[3] = {-1e300, -1e300, -1e300};
+    for (int k = lo; k < hi; ++k)
+      for (int c = 0; c < 3; ++c) {
+        cmin[c] = std::min(cmin[c], h.parts[T.perm[k]].c[c]);
+        cmax[c] = std::max(cmax[c], h.parts[T.perm[k]].c[c]);
+      }
+    int ax = 0;
+    for (int c = 1; c < 3; ++c)
+      if (cmax[c] - cmin[c] > cmax[ax] - cmin[ax]) ax = c;
+    std::stable_sort(T.perm.begin() + lo, T.perm.begin() + hi,
+                     [&](int a, int b) { return h.parts[a].c[ax] < h.parts[b].c[ax]; });
+    const int mid = lo + (hi - lo) / 2;
+    T.nodes[id] = nd;
+    const int c0 = build_nodes(T, h, lo, mid, level + 1);
+    const int c1 = build_nodes(T, h, mid, hi, level + 1);
+    T.nodes[id].child[0] = c0;
+    T.nodes[id].child[1] = c1;
+    return id;
+  }
+  T.nodes[id] = nd;
+  return id;
+}
+
+template <typename V>
+static int upload_vec(sbio_geom* g, V** dst, const std::vector<V>& v, const char* what) {
+  if (v.empty()) {
+    *dst = nullptr;
+    return SBIO_OK;
+  }
+  int rc = dev_alloc(g, (void**)dst, v.size() * sizeof(V), what);
+  if (rc) return rc;
+  SBIO_CUDA_TRY(cudaMemcpy(*dst, v.data(), v.size() * sizeof(V), cudaMemcpyHostToDevice));
+  return SBIO_OK;
+}
+
+static int build_tree(sbio_geom* g, TreeFar& T) {
+  const GeomHost& h = g->h;
+  const int M = h.M, G = h.G;
+  const int64_t N = h.N;
+  T.perm.resize(M);
+  for (int i = 0; i < M; ++i) T.perm[i] = i;
+  T.nodes.clear();
+  T.nodes.reserve(2 * M);
+  T.n_levels = 0;
+  build_nodes(T, h, 0, M, 0);
+  T.n_nodes = (int)T.nodes.size();
+  T.pos.assign(M, 0);
+  for (int k = 0; k < M; ++k) T.pos[T.perm[k]] = k;
+  std::vector<int> leaf(M, -1);
+  T.levels.assign(T.n_levels, {});
+  for (int id = 0; id < T.n_nodes; ++id) {
+    const TreeNodeH& nd = T.nodes[id];
+    if (nd.count == 1) leaf[T.perm[nd.first]] = id;
+    else T.levels[nd.level].push_back(id);
+  }
+  // per group: own and near particles (the far sum skips them for the
+  // targets concerned; a multipole node may hold none of them)
+  const int n_groups = (int)((N + kTreeGroup - 1) / kTreeGroup);
+  T.n_groups = n_groups;
+  std::vector<std::vector<int>> excl(n_groups);
+  std::vector<std::vector<std::pair<int, int>>> excl_cnt(n_groups);   // (particle, targets of the group skipping it)
+  for (int gi = 0; gi < n_groups; ++gi) {
+    const int64_t t0 = (int64_t)gi * kTreeGroup, t1 = std::min<int64_t>(N, t0 + kTreeGroup);
+    for (int64_t t = t0; t < t1; ++t) excl[gi].push_back((int)(t / G));
+  }
+  for (size_t k = 0; k < h.pair_t.size(); ++k) excl[h.pair_t[k] / kTreeGroup].push_back(h.pair_s[k]);
+  for (int gi = 0; gi < n_groups; ++gi) {
+    std::vector<int>& e = excl[gi];
+    std::sort(e.begin(), e.end());
+    for (size_t k = 0; k < e.size();) {
+      size_t j = k;
+      while (j < e.size() && e[j] == e[k]) ++j;
+      excl_cnt[gi].push_back({e[k], (int)(j - k)});
+      k = j;
+    }
+    e.erase(std::unique(e.begin(), e.end()), e.end());
+  }
+  const int tiles_per_part = (G + kFarTile - 1) / kFarTile;
+  std::vector<int4> dtiles, ditems, mitems;
+  std::vector<int> mlist;
+  T.m2p_pairs = T.direct_pairs = T.m2p_source_pairs = 0;
+  std::vector<int> stack, dlist, epos;
+  for (int gi = 0; gi < n_groups; ++gi) {
+    const int64_t t0 = (int64_t)gi * kTreeGroup, t1 = std::min<int64_t>(N, t0 + kTreeGroup);
+    double bmin[3] = {1e300, 1e300, 1e300}, bmax[3] = {-1e300, -1e300, -1e300};
+    for (int64_t t = t0; t < t1; ++t)
+      for (int c = 0; c < 3; ++c) {
+        bmin[c] = std::min(bmin[c], h.xyz[t * 3 + c]);
+        bmax[c] = std::max(bmax[c], h.xyz[t * 3 + c]);
+      }
+    double cg[3], rg = 0.0;
+    for (int c = 0; c < 3; ++c) cg[c] = 0.5 * (bmin[c] + bmax[c]);
+    for (int64_t t = t0; t < t1; ++t) {
+      double d2 = 0.0;
+      for (int c = 0; c < 3; ++c) d2 += (h.xyz[t * 3 + c] - cg[c]) * (h.xyz[t * 3 + c] - cg[c]);
+      rg = std::max(rg, std::sqrt(d2));
+    }
+    epos.clear();
+    for (int e : excl[gi]) epos.push_back(T.pos[e]);
+    std::sort(epos.begin(), epos.end());
+    dlist.clear();
+    const size_t m0 = mlist.size();
+    stack.assign(1, 0);
+    while (!stack.empty()) {
+      const int id = stack.back();
+      stack.pop_back();
+      const TreeNodeH& nd = T.nodes[id];
+      const double dist = std::sqrt((nd.c[0] - cg[0]) * (nd.c[0] - cg[0]) + (nd.c[1] - cg[1]) * (nd.c[1] - cg[1]) +
+                                    (nd.c[2] - cg[2]) * (nd.c[2] - cg[2]));
+      const auto it = std::lower_bound(epos.begin(), epos.end(), nd.first);
+      const bool holds_excluded = it != epos.end() && *it < nd.first + nd.count;
+      if (!holds_excluded && dist >= rg + nd.r / T.theta) {
+        mlist.push_back(id);
+      } else if (nd.count == 1) {
+        dlist.push_back(T.perm[nd.first]);
+      } else {
+        stack.push_back(nd.child[1]);
+        stack.push_back(nd.child[0]);
+      }
+    }
+    T.m2p_pairs += (int64_t)(mlist.size() - m0) * (t1 - t0);
+    for (size_t k = m0; k < mlist.size(); ++k) T.m2p_source_pairs += (int64_t)T.nodes[mlist[k]].count * G * (t1 - t0);
+    for (size_t k = m0; k < mlist.size(); k += kTreeChunkNodes)
+      mitems.push_back(make_int4(gi, (int)k, (int)std::min(mlist.size(), k + kTreeChunkNodes), 0));
+    // direct list in ascending particle order (the kernel's skip-list walk needs it)
+    std::sort(dlist.begin(), dlist.end());
+    const int d0 = (int)dtiles.size();
+    for (int i : dlist) {
+      for (int k = 0; k < tiles_per_part; ++k) dtiles.push_back(h.tiles[(size_t)i * tiles_per_part + k]);
+      const auto ec = std::lower_bound(excl_cnt[gi].begin(), excl_cnt[gi].end(), std::make_pair(i, -1));
+      const int skipped = (ec != excl_cnt[gi].end() && ec->first == i) ? ec->second : 0;
+      T.direct_pairs += (int64_t)((t1 - t0) - skipped) * G;
+    }
+    for (int k = d0; k < (int)dtiles.size(); k += kTreeChunkTiles)
+      ditems.push_back(make_int4(gi, k, std::min((int)dtiles.size(), k + kTreeChunkTiles), 0));
+  }
+  T.m2p_entries = (int64_t)mlist.size();
+  T.direct_tiles = (int64_t)dtiles.size();
+  // longest items first (the tail of the grid is then short)
+  std::stable_sort(ditems.begin(), ditems.end(), [](const int4& a, const int4& b) { return a.z - a.y > b.z - b.y; });
+  std::stable_sort(mitems.begin(), mitems.end(), [](const int4& a, const int4& b) { return a.z - a.y > b.z - b.y; });
+  // device tables
+  std::vector<double> geo(T.n_nodes * 4);
+  std::vector<float4> c32(T.n_nodes * 2);
+  std::vector<int> child(T.n_nodes * 2), lev;
+  for (int id = 0; id < T.n_nodes; ++id) {
+    const TreeNodeH& nd = T.nodes[id];
+    float hi[3], lo[3];
+    for (int c = 0; c < 3; ++c) {
+      geo[id * 4 + c] = nd.c[c];
+      split_f32(nd.c[c], hi[c], lo[c]);
+    }
+    geo[id * 4 + 3] = nd.r;
+    c32[id * 2 + 0] = make_float4(hi[0], hi[1], hi[2], 0.f);
+    c32[id * 2 + 1] = make_float4(lo[0], lo[1], lo[2], 0.f);
+    child[id * 2 + 0] = nd.child[0];
+    child[id * 2 + 1] = nd.child[1];
+  }
+  T.level_off.assign(1, 0);
+  for (int l = T.n_levels - 1; l >= 0; --l) {   // deepest level first
+    lev.insert(lev.end(), T.levels[l].begin(), T.levels[l].end());
+    T.level_off.push_back((int)lev.size());
+  }
+  const int NM = tree_nm(T.order);
+  int rc;
+  if ((rc = upload_vec(g, &T.d_geo, geo, "tree nodes"))) return rc;
+  if ((rc = upload_vec(g, &T.d_c32, c32, "tree centres"))) return rc;
+  if ((rc = upload_vec(g, &T.d_child, child, "tree children"))) return rc;
+  if ((rc = upload_vec(g, &T.d_leaf, leaf, "tree leaves"))) return rc;
+  if ((rc = upload_vec(g, &T.d_levels, lev, "tree levels"))) return rc;
+  if ((rc = upload_vec(g, &T.d_tiles, dtiles, "tree direct tiles"))) return rc;
+  if ((rc = upload_vec(g, &T.d_ditems, ditems, "tree direct items"))) return rc;
+  if ((rc = upload_vec(g, &T.d_mlist, mlist, "tree multipole lists"))) return rc;
+  if ((rc = upload_vec(g, &T.d_mitems, mitems, "tree multipole items"))) return rc;
+  T.n_ditems = (int)ditems.size();
+  T.n_mitems = (int)mitems.size();
+  if ((rc = dev_alloc(g, (void**)&T.d_M, sizeof(double2) * 2 * NM * (size_t)T.n_nodes, "tree multipoles"))) return rc;
+  if ((rc = dev_alloc(g, (void**)&T.d_M32, sizeof(float2) * 2 * NM * (size_t)T.n_nodes, "tree multipoles (FP32)")))
+    return rc;
+  return SBIO_OK;
+}
+
+template <int PF>
+static int tree_apply(sbio_geom* g, TreeFar& T, double* S, double* D, cudaStream_t st) {
+  const GeomHost& h = g->h;
+  const DevGeom& d = g->d;
+  constexpr int NM = tree_nm(PF);
+  tree_p2m_kernel<PF><<<h.M, 128, 0, st>>>(h.G, d.src32, T.d_leaf, T.d_M);
+  count_launch();
+  for (size_t l = 0; l + 1 < T.level_off.size(); ++l) {
+    const int n = T.level_off[l + 1] - T.level_off[l];
+    if (n <= 0) continue;
+    tree_m2m_kernel<PF><<<n, 128, 0, st>>>(T.d_levels + T.level_off[l], T.d_child, T.d_geo, T.d_M);
+    count_launch();
+  }
+  const int64_t total = (int64_t)T.n_nodes * 2 * NM;
+  tree_to_f32_kernel<PF><<<(unsigned)std::min<int64_t>((total + 255) / 256, 4096), 256, 0, st>>>(total, T.d_M, T.d_M32);
+  count_launch();
+  launch_far_tile_items(d, T.d_tiles, T.d_ditems, T.n_ditems, h.N, S, D, st);
+  if (T.n_mitems > 0) {
+    tree_m2p_kernel<PF><<<T.n_mitems, kFarTile, 0, st>>>(T.d_mitems, T.d_mlist, T.d_c32, T.d_M32, d.tgt32, h.N, S, D);
+    count_launch();
+  }
+  SBIO_CUDA_TRY(cudaGetLastError());
+  return SBIO_OK;
+}
+
+int launch_tree_far(sbio_geom* g, double* S, double* D, cudaStream_t st) {
+  TreeFar& T = *g->tree;
+  switch (T.order) {
+    case 8: return tree_apply<8>(g, T, S, D, st);
+    case 12: return tree_apply<12>(g, T, S, D, st);
+    default: return tree_apply<16>(g, T, S, D, st);
+  }
+}
+
+}  // namespace sbio
+
+using namespace sbio;
+
+extern "C" {
+
+int sbio_geom_set_far_method(sbio_geom* g, int32_t method, double theta, int32_t order) {
+  clear_error();
+  if (!g) return set_error(SBIO_EINVAL, "null geometry");
+  if (method == SBIO_FAR_DIRECT) {
+    if (g->tree) {
+      cudaSetDevice(g->ctx->device);
+      cudaDeviceSynchronize();   // no apply may still read the lists being dropped
+      tree_free(g->tree);
+      g->tree = nullptr;
+    }
+    return SBIO_OK;
+  }
+  if (method != SBIO_FAR_TREE) return set_error(SBIO_EINVAL, "far method %d unknown", method);
+  if (!(theta > 0.05 && theta < 1.0)) return set_error(SBIO_EINVAL, "theta = %g must be in (0.05, 1)", theta);
+  if (order != 8 && order != 12 && order != 16)
+    return set_error(SBIO_EINVAL, "treecode order %d: 8, 12 or 16", order);
+  SBIO_CUDA_TRY(cudaSetDevice(g->ctx->device));
+  SBIO_CUDA_TRY(cudaDeviceSynchronize());
+  // a new setting rebuilds the lists (their device arrays stay with the
+  // geometry until it is destroyed)
+  TreeFar* t = new TreeFar();
+  t->order = order;
+  t->theta = theta;
+  const int rc = build_tree(g, *t);
+  if (rc) {
+    delete t;
+    return rc;
+  }
+  tree_free(g->tree);
+  g->tree = t;
+  return SBIO_OK;
+}
+
+int sbio_geom_tree_info(const sbio_geom* g, int64_t* n_nodes, int64_t* n_groups, int64_t* m2p_pairs,
+                        int64_t* m2p_source_pairs, int64_t* direct_pairs) {
+  clear_error();
+  if (!g) return set_error(SBIO_EINVAL, "null geometry");
+  if (!g->tree) return set_error(SBIO_EINVAL, "the geometry's far field is the direct sum");
+  if (n_nodes) *n_nodes = g->tree->n_nodes;
+  if (n_groups) *n_groups = g->tree->n_groups;
+  if (m2p_pairs) *m2p_pairs = g->tree->m2p_pairs;
+  if (m2p_source_pairs) *m2p_source_pairs = g->tree->m2p_source_pairs;
+  if (direct_pairs) *direct_pairs = g->tree->direct_pairs;
+  return SBIO_OK;
+}
+
+}  // extern "C"

@@ -153,6 +153,9 @@ _SIGS = {
                                     C.POINTER(C.c_int32), C.POINTER(C.c_size_t)]),
     "sbio_server_destroy": (C.c_int, [_vp]),
     "sbio_measure_peaks": (C.c_int, [C.c_int32, C.POINTER(sbio_peaks)]),
+    "sbio_geom_set_far_method": (C.c_int, [_vp, C.c_int32, C.c_double, C.c_int32]),
+    "sbio_geom_tree_info": (C.c_int, [_vp, C.POINTER(C.c_int64), C.POINTER(C.c_int64), C.POINTER(C.c_int64),
+                                      C.POINTER(C.c_int64), C.POINTER(C.c_int64)]),
     "sbio_geom_near_work": (C.c_int, [_vp, C.POINTER(C.c_int64), C.POINTER(C.c_int64)]),
     "sbio_apply_self_noalloc": (C.c_int, [C.POINTER(sbio_spheroid), C.c_int32, C.c_int32, C.c_int32, _vp, _vp,
                                           _vp, _vp, _vp]),
@@ -458,6 +461,23 @@ def sbio_geom_autotune_stokes(g, stream=None):
     a, b, c = C.c_int32(), C.c_int32(), C.c_double()
     _check(_lib.sbio_geom_autotune_stokes(g, _stream(stream), C.byref(a), C.byref(b), C.byref(c)))
     return a.value, b.value, c.value
+
+
+SBIO_FAR_DIRECT = 0
+SBIO_FAR_TREE = 1
+
+
+def sbio_geom_set_far_method(g, method, theta=0.5, order=16):
+    """Far field by the direct sum (SBIO_FAR_DIRECT) or the particle treecode
+    (SBIO_FAR_TREE, mixed S + D applies at the nodes)."""
+    _check(_lib.sbio_geom_set_far_method(g, method, theta, order))
+
+
+def sbio_geom_tree_info(g):
+    a, b, c, d, e = C.c_int64(), C.c_int64(), C.c_int64(), C.c_int64(), C.c_int64()
+    _check(_lib.sbio_geom_tree_info(g, C.byref(a), C.byref(b), C.byref(c), C.byref(d), C.byref(e)))
+    return {"nodes": a.value, "groups": b.value, "m2p_pairs": c.value, "m2p_source_pairs": d.value,
+            "direct_pairs": e.value}
 
 
 def sbio_geom_near_work(g):

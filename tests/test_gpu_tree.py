@@ -1,0 +1,105 @@
+"""The treecode far field (C ABI sbio_geom_set_far_method with
+SBIO_FAR_TREE) against the direct far sum it replaces: every far (target,
+source node) pair covered exactly once, the whole mixed apply within the
+stated bound of the plain FP64 GPU apply and of the CPU oracle's method on
+sampled targets, at the orders and opening angles offered."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from oracle import geometry as OG
+from oracle import laplace as OL
+from paper_2506_20809_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+TOLMIX = 1e-6
+# stated bounds of the treecode apply against FP64 (normwise), per (order, theta)
+TREE_BOUND = {(16, 0.5): 1e-6, (12, 0.5): 3e-6, (8, 0.4): 3e-5}
+
+
+@pytest.fixture(scope="module")
+def S():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    import __graft_entry__ as G
+
+    G.build()
+    import paper_2506_20809_gb300.sbio as S
+
+    return S
+
+
+@pytest.fixture(scope="module")
+def ctx(S):
+    return S.sbio_ctx_create(0, 0)
+
+
+def _apply(S, g, c):
+    sig = torch.from_numpy(c[0]).cuda()
+    mu = torch.from_numpy(c[1]).cuda()
+    So = torch.full((g.N,), float("nan"), dtype=torch.float64, device="cuda")
+    Do = torch.full_like(So, float("nan"))
+    S.sbio_apply_laplace(g.h, sig, mu, So, Do)
+    torch.cuda.synchronize()
+    return So.cpu().numpy(), Do.cpu().numpy()
+
+
+@pytest.mark.parametrize("M,p,seed", [(60, 8, 31), (120, 12, 32), (90, 16, 33)])
+def test_tree_matches_fp64_direct(S, ctx, M, p, seed):
+    s = I.rsa_suspension(M, 0.20, seed, p, name="tree")
+    c = I.config_coefficients(s, seed)
+    g = S.Geometry(ctx, s, precision=S.SBIO_FP64)
+    S64, D64 = _apply(S, g, c)
+    S.sbio_geom_set_precision(g.h, S.SBIO_MIXED)
+    for (order, theta), bound in TREE_BOUND.items():
+        S.sbio_geom_set_far_method(g.h, S.SBIO_FAR_TREE, theta, order)
+        info = S.sbio_geom_tree_info(g.h)
+        assert info["nodes"] == 2 * M - 1
+        assert info["m2p_source_pairs"] + info["direct_pairs"] == g.n_far
+        St, Dt = _apply(S, g, c)
+        eS, eD = OL.normwise_rel_err(St, S64), OL.normwise_rel_err(Dt, D64)
+        print(f"M={M} p={p} order={order} theta={theta}: S {eS:.2e} D {eD:.2e}, "
+              f"m2p {info['m2p_pairs']:.3e} direct {info['direct_pairs']:.3e}")
+        assert eS < bound and eD < bound, (order, theta, eS, eD)
+    S.sbio_geom_set_far_method(g.h, S.SBIO_FAR_DIRECT)
+    Sd, Dd = _apply(S, g, c)
+    assert OL.normwise_rel_err(Sd, S64) < TOLMIX and OL.normwise_rel_err(Dd, D64) < TOLMIX
+    g.close()
+
+
+def test_tree_against_oracle_sampled(S, ctx):
+    """A 400-particle suspension of the 200-particle recipe (p = 12): the
+    treecode apply against the oracle's method on sampled targets."""
+    s = I.rsa_suspension(400, 0.20, 41, 12, name="tree400")
+    c = I.config_coefficients(s, 2)
+    g = S.Geometry(ctx, s, precision=S.SBIO_MIXED)
+    S.sbio_geom_set_far_method(g.h, S.SBIO_FAR_TREE, 0.5, 16)
+    St, Dt = _apply(S, g, c)
+    og = OG.SuspensionGeom.from_suspension(s)
+    tg = np.sort(np.random.default_rng(5).choice(g.N, 40, replace=False))
+    Sr, Dr = OL.LaplaceOracle(og).apply(c[0], c[1], "method", targets=tg)
+    eS = np.max(np.abs(St[tg] - Sr)) / np.max(np.abs(Sr))
+    eD = np.max(np.abs(Dt[tg] - Dr)) / np.max(np.abs(Dr))
+    print(f"tree400 vs oracle: S {eS:.2e} D {eD:.2e}")
+    assert eS < TREE_BOUND[(16, 0.5)] and eD < TREE_BOUND[(16, 0.5)]
+    g.close()
+
+
+def test_tree_single_operator_and_fp64_keep_direct(S, ctx):
+    """S-only applies and FP64 geometries use the direct sum: identical to the
+    direct results."""
+    s = I.rsa_suspension(30, 0.2, 43, 8, name="tree30")
+    c = I.config_coefficients(s, 1)
+    g = S.Geometry(ctx, s, precision=S.SBIO_FP64)
+    S64, D64 = _apply(S, g, c)
+    S.sbio_geom_set_far_method(g.h, S.SBIO_FAR_TREE, 0.5, 16)
+    S64t, D64t = _apply(S, g, c)
+    assert np.array_equal(np.isnan(S64t), np.isnan(S64))
+    assert OL.normwise_rel_err(S64t, S64) < 1e-13 and OL.normwise_rel_err(D64t, D64) < 1e-13
+    with pytest.raises(S.SbioError) as e:
+        S.sbio_geom_set_far_method(g.h, S.SBIO_FAR_TREE, 1.5, 16)
+    assert e.value.code == S.SBIO_EINVAL
+    with pytest.raises(S.SbioError):
+        S.sbio_geom_set_far_method(g.h, S.SBIO_FAR_TREE, 0.5, 10)
+    g.close()
