@@ -184,10 +184,11 @@ struct FarDesc {
 };
 int launch_far_persistent(const FarDesc* descs, const int4* items, int n_items, int* counter, int tt, int grid,
                           cudaStream_t st);
-// Direct part of the treecode far field: items (target block of 256 targets,
-// first tile, end tile) over a tile list; the geometry's mixed far pair sum
-// (2 packed targets per thread) with its skip lists; defined in sbio_laplace.cu.
-void launch_far_tile_items(const DevGeom& d, const int4* tiles, const int4* items, int n_items, int64_t N,
+// Direct part of the treecode far field: items (target group, first tile,
+// end tile) over a tile list, groups = [first, end) target ranges of at most
+// 256 targets; the geometry's mixed far pair sum (2 packed targets per
+// thread) with its skip lists; defined in sbio_laplace.cu.
+void launch_far_tile_items(const DevGeom& d, const int2* groups, const int4* tiles, const int4* items, int n_items,
                            double* S, double* D, cudaStream_t st);
 // the treecode far field of one apply (sbio_tree.cu)
 int launch_tree_far(sbio_geom* g, double* S, double* D, cudaStream_t st);

@@ -213,17 +213,17 @@ __global__ void __launch_bounds__(kFarTile) far_fp64_kernel(const int4* __restri
 // their own centre, so the FP32 difference X - y_rel carries an error
 // relative to |x - y| rather than to the box size.  Each tile's FP32 partial
 // sum is folded into an (hi, lo) pair by TwoSum.
-// One CTA: targets of target block `tb` (kFarTile * TT consecutive nodes, TT
-// per thread) against source tiles [t_lo, t_hi).  Only the target positions
+// One CTA: targets [t_first, min(t_end, t_first + kFarTile * TT)) (TT per
+// thread, target t_first + tid + q kFarTile) against source tiles [t_lo, t_hi).  Only the target positions
 // relative to the current source particle and the running tile partials live
 // in registers; the two-sum accumulators and the skip-list cursors live in
 // shared memory and are touched once per tile.
 template <int TT, bool DO_S, bool DO_D, bool PK>
-__device__ __forceinline__ void far_mixed_block(int64_t tb, int t_lo, int t_hi,
+__device__ __forceinline__ void far_mixed_block(int64_t t_first, int64_t t_end, int t_lo, int t_hi,
                                                 const int4* __restrict__ tiles, const float4* __restrict__ src32,
                                                 const float4* __restrict__ tgt32, const float4* __restrict__ cen32,
                                                 const int32_t* __restrict__ skip_ptr,
-                                                const int32_t* __restrict__ skip_idx, int64_t N,
+                                                const int32_t* __restrict__ skip_idx,
                                                 double* __restrict__ S_out, double* __restrict__ D_out) {
   // tile of sources: scalar form (y - c, q), (d, 0).  The packed form uses
   // the expanded distance |x - y|^2 = (|x|^2 + |y|^2) - 2 x.y and
@@ -234,7 +234,7 @@ __device__ __forceinline__ void far_mixed_block(int64_t tb, int t_lo, int t_hi,
   __shared__ float acc[4 * TT * kFarTile];   // per target: S hi, S lo, D hi, D lo
   __shared__ int cursor[2 * TT * kFarTile];  // per target: skip-list position, next skipped particle
   const int tid = threadIdx.x;
-  const int64_t t0 = tb * TT * kFarTile + tid;
+  const int64_t t0 = t_first + tid;
 #pragma unroll
   for (int q = 0; q < TT; ++q) {
     const int64_t t = t0 + (int64_t)q * kFarTile;
@@ -242,9 +242,9 @@ __device__ __forceinline__ void far_mixed_block(int64_t tb, int t_lo, int t_hi,
     acc[(4 * q + 1) * kFarTile + tid] = 0.f;
     acc[(4 * q + 2) * kFarTile + tid] = 0.f;
     acc[(4 * q + 3) * kFarTile + tid] = 0.f;
-    const int sp = (t < N) ? skip_ptr[t] : 0;
+    const int sp = (t < t_end) ? skip_ptr[t] : 0;
     cursor[(2 * q + 0) * kFarTile + tid] = sp;
-    cursor[(2 * q + 1) * kFarTile + tid] = (t < N) ? skip_idx[sp] : INT32_MAX;
+    cursor[(2 * q + 1) * kFarTile + tid] = (t < t_end) ? skip_idx[sp] : INT32_MAX;
   }
   float X[TT], Y[TT], Z[TT], XX[TT];
   unsigned skipmask = (1u << TT) - 1u;
@@ -263,9 +263,9 @@ __device__ __forceinline__ void far_mixed_block(int64_t tb, int t_lo, int t_hi,
         while (nxt < cur) nxt = skip_idx[++sp];
         cursor[(2 * q + 0) * kFarTile + tid] = sp;
         cursor[(2 * q + 1) * kFarTile + tid] = nxt;
-        if (t >= N || nxt == cur) skipmask |= 1u << q;
+        if (t >= t_end || nxt == cur) skipmask |= 1u << q;
         float4 hi = make_float4(0.f, 0.f, 0.f, 0.f), lo = hi;
-        if (t < N) {
+        if (t < t_end) {
           hi = tgt32[t * 2];
           lo = tgt32[t * 2 + 1];
         }
@@ -376,7 +376,7 @@ __device__ __forceinline__ void far_mixed_block(int64_t tb, int t_lo, int t_hi,
 #pragma unroll
   for (int q = 0; q < TT; ++q) {
     const int64_t t = t0 + (int64_t)q * kFarTile;
-    if (t < N) {
+    if (t < t_end) {
       if (DO_S)
         atomicAdd(S_out + t, ((double)acc[(4 * q + 0) * kFarTile + tid] + (double)acc[(4 * q + 1) * kFarTile + tid]) * kInv4Pi);
       if (DO_D)
@@ -396,30 +396,34 @@ __global__ void __launch_bounds__(kFarTile) far_mixed_kernel(const int4* __restr
                                                              double* __restrict__ S_out, double* __restrict__ D_out) {
   const int per = (n_tiles + gridDim.y - 1) / gridDim.y;
   const int t_lo = blockIdx.y * per, t_hi = min(n_tiles, t_lo + per);
-  far_mixed_block<TT, DO_S, DO_D, PK>(blockIdx.x, t_lo, t_hi, tiles, src32, tgt32, cen32, skip_ptr, skip_idx, N,
-                                      S_out, D_out);
+  far_mixed_block<TT, DO_S, DO_D, PK>((int64_t)blockIdx.x * TT * kFarTile, N, t_lo, t_hi, tiles, src32, tgt32, cen32,
+                                      skip_ptr, skip_idx, S_out, D_out);
 }
 
-// Direct part of the treecode far field: one CTA per item (target block of
-// 256 targets, tile range of a block-specific tile list).
+// Direct part of the treecode far field: one CTA per item (target group of
+// at most 256 targets [groups[g].x, groups[g].y), tile range of the group's
+// tile list).
 __global__ void __launch_bounds__(kFarTile) far_tile_items_kernel(const int4* __restrict__ items,
+                                                                  const int2* __restrict__ groups,
                                                                   const int4* __restrict__ tiles,
                                                                   const float4* __restrict__ src32,
                                                                   const float4* __restrict__ tgt32,
                                                                   const float4* __restrict__ cen32,
                                                                   const int32_t* __restrict__ skip_ptr,
-                                                                  const int32_t* __restrict__ skip_idx, int64_t N,
+                                                                  const int32_t* __restrict__ skip_idx,
                                                                   double* __restrict__ S_out,
                                                                   double* __restrict__ D_out) {
   const int4 w = items[blockIdx.x];
-  far_mixed_block<2, true, true, true>(w.x, w.y, w.z, tiles, src32, tgt32, cen32, skip_ptr, skip_idx, N, S_out, D_out);
+  const int2 grp = groups[w.x];
+  far_mixed_block<2, true, true, true>(grp.x, grp.y, w.y, w.z, tiles, src32, tgt32, cen32, skip_ptr, skip_idx, S_out,
+                                       D_out);
 }
 
-void launch_far_tile_items(const DevGeom& d, const int4* tiles, const int4* items, int n_items, int64_t N,
+void launch_far_tile_items(const DevGeom& d, const int2* groups, const int4* tiles, const int4* items, int n_items,
                            double* S, double* D, cudaStream_t st) {
   if (n_items <= 0) return;
-  far_tile_items_kernel<<<n_items, kFarTile, 0, st>>>(items, tiles, d.src32, d.tgt32, d.cen32, d.skip_ptr,
-                                                      d.skip_idx, N, S, D);
+  far_tile_items_kernel<<<n_items, kFarTile, 0, st>>>(items, groups, tiles, d.src32, d.tgt32, d.cen32, d.skip_ptr,
+                                                      d.skip_idx, S, D);
   count_launch();
 }
 
@@ -519,8 +523,8 @@ __global__ void __launch_bounds__(kFarTile) far_persistent_kernel(const FarDesc*
     if (it >= n_items) break;
     const int4 w = items[it];
     const FarDesc& D = descs[w.x];
-    far_mixed_block<TT, true, true, PK>(w.y, w.z, w.w, D.tiles, D.src32, D.tgt32, D.cen32, D.skip_ptr, D.skip_idx,
-                                        D.N, D.S, D.D);
+    far_mixed_block<TT, true, true, PK>((int64_t)w.y * TT * kFarTile, D.N, w.z, w.w, D.tiles, D.src32, D.tgt32,
+                                        D.cen32, D.skip_ptr, D.skip_idx, D.S, D.D);
   }
 }
 

@@ -28,8 +28,8 @@
 // Tree and lists (host, once per geometry and accuracy setting).  A binary
 // tree over the particles, split at the median centre along the longest
 // extent; a leaf is one particle (its centre and major semi-axis bound all of
-// its nodes).  Targets are taken in groups of 256 consecutive nodes (the
-// direct kernel's target block).  For each group a walk from the root accepts
+// its nodes).  Targets are taken in groups of at most 256 consecutive nodes
+// of one particle (the direct kernel's target block).  For each group a walk from the root accepts
 // a node when, for every target of the group, |x - c_n| >= r_n / theta and
 // the node holds none of the group's own or near particles; a leaf that is
 // not accepted goes to the group's direct list, evaluated by the direct
@@ -48,7 +48,7 @@
 
 namespace sbio {
 
-constexpr int kTreeGroup = 2 * kFarTile;   // targets per group (direct kernel: 2 per thread)
+constexpr int kTreeGroup = 2 * kFarTile;   // most targets per group (direct kernel: 2 per thread)
 constexpr int kTreeChunkNodes = 16;        // multipole nodes per evaluation CTA
 constexpr int kTreeChunkTiles = 32;        // direct source tiles per CTA
 constexpr double kInv4PiTree = 0.07957747154594767;
@@ -80,6 +80,7 @@ struct TreeFar {
   std::vector<int> level_off;     // offsets into d_levels
   double2* d_M = nullptr;         // n_nodes x 2 x NM: FP64 multipoles (S, D)
   float2* d_M32 = nullptr;        // n_nodes x 2 x NM: FP32, m > 0 doubled
+  int2* d_groups = nullptr;       // target range [first, end) of every group
   int4* d_tiles = nullptr;        // direct source tiles, group after group
   int4* d_ditems = nullptr;       // (group, first tile, end tile, 0)
   int n_ditems = 0;
@@ -286,25 +287,28 @@ __global__ void tree_to_f32_kernel(int64_t total, const double2* __restrict__ Mt
   }
 }
 
-// Multipole evaluation: one CTA per (group of 256 targets, up to
+// Multipole evaluation: one CTA per (group of at most 256 targets, up to
 // kTreeChunkNodes accepted nodes), two targets per thread.
 template <int PF>
-__global__ void __launch_bounds__(kFarTile) tree_m2p_kernel(const int4* __restrict__ items, const int* __restrict__ mlist,
+__global__ void __launch_bounds__(kFarTile) tree_m2p_kernel(const int4* __restrict__ items, const int2* __restrict__ groups,
+                                                            const int* __restrict__ mlist,
                                                             const float4* __restrict__ c32,
                                                             const float2* __restrict__ M32,
-                                                            const float4* __restrict__ tgt32, int64_t N,
+                                                            const float4* __restrict__ tgt32,
                                                             double* __restrict__ S_out, double* __restrict__ D_out) {
   constexpr int NM = tree_nm(PF);
   __shared__ float2 cf[2 * NM];
   __shared__ float4 cc[2];
   const int4 it = items[blockIdx.x];
+  const int2 grp = groups[it.x];
+  const int64_t N = grp.y;
   const int tid = threadIdx.x;
   int64_t t[2];
   float4 xh[2], xl[2];
   float hS[2], lS[2], hD[2], lD[2];
 #pragma unroll
   for (int q = 0; q < 2; ++q) {
-    t[q] = (int64_t)it.x * kTreeGroup + q * kFarTile + tid;
+    t[q] = (int64_t)grp.x + q * kFarTile + tid;
     xh[q] = xl[q] = make_float4(0.f, 0.f, 0.f, 0.f);
     if (t[q] < N) {
       xh[q] = tgt32[t[q] * 2 + 0];
@@ -462,7 +466,6 @@ static int upload_vec(sbio_geom* g, V** dst, const std::vector<V>& v, const char
 static int build_tree(sbio_geom* g, TreeFar& T) {
   const GeomHost& h = g->h;
   const int M = h.M, G = h.G;
-  const int64_t N = h.N;
   T.perm.resize(M);
   for (int i = 0; i < M; ++i) T.perm[i] = i;
   T.nodes.clear();
@@ -481,15 +484,26 @@ static int build_tree(sbio_geom* g, TreeFar& T) {
   }
   // per group: own and near particles (the far sum skips them for the
   // targets concerned; a multipole node may hold none of them)
-  const int n_groups = (int)((N + kTreeGroup - 1) / kTreeGroup);
+  // groups never straddle particles (a group's bounding sphere is then a
+  // part of one surface): each particle's G nodes in ceil(G / 256) runs of
+  // nearly equal length
+  const int chunks = (G + kTreeGroup - 1) / kTreeGroup;
+  const int cs = (G + chunks - 1) / chunks;
+  const int n_groups = M * chunks;
   T.n_groups = n_groups;
+  std::vector<int2> groups(n_groups);
+  for (int i = 0; i < M; ++i)
+    for (int c = 0; c < chunks; ++c) {
+      const int64_t t0 = (int64_t)i * G + (int64_t)c * cs;
+      const int64_t t1 = std::min<int64_t>((int64_t)(i + 1) * G, t0 + cs);
+      groups[(size_t)i * chunks + c] = make_int2((int)t0, (int)std::max(t0, t1));
+    }
+  auto group_of = [&](int64_t t) { return (int)((t / G) * chunks + (t % G) / cs); };
   std::vector<std::vector<int>> excl(n_groups);
   std::vector<std::vector<std::pair<int, int>>> excl_cnt(n_groups);   // (particle, targets of the group skipping it)
-  for (int gi = 0; gi < n_groups; ++gi) {
-    const int64_t t0 = (int64_t)gi * kTreeGroup, t1 = std::min<int64_t>(N, t0 + kTreeGroup);
-    for (int64_t t = t0; t < t1; ++t) excl[gi].push_back((int)(t / G));
-  }
-  for (size_t k = 0; k < h.pair_t.size(); ++k) excl[h.pair_t[k] / kTreeGroup].push_back(h.pair_s[k]);
+  for (int gi = 0; gi < n_groups; ++gi)
+    for (int64_t t = groups[gi].x; t < groups[gi].y; ++t) excl[gi].push_back((int)(t / G));
+  for (size_t k = 0; k < h.pair_t.size(); ++k) excl[group_of(h.pair_t[k])].push_back(h.pair_s[k]);
   for (int gi = 0; gi < n_groups; ++gi) {
     std::vector<int>& e = excl[gi];
     std::sort(e.begin(), e.end());
@@ -507,7 +521,8 @@ static int build_tree(sbio_geom* g, TreeFar& T) {
   T.m2p_pairs = T.direct_pairs = T.m2p_source_pairs = 0;
   std::vector<int> stack, dlist, epos;
   for (int gi = 0; gi < n_groups; ++gi) {
-    const int64_t t0 = (int64_t)gi * kTreeGroup, t1 = std::min<int64_t>(N, t0 + kTreeGroup);
+    const int64_t t0 = groups[gi].x, t1 = groups[gi].y;
+    if (t1 <= t0) continue;
     double bmin[3] = {1e300, 1e300, 1e300}, bmax[3] = {-1e300, -1e300, -1e300};
     for (int64_t t = t0; t < t1; ++t)
       for (int c = 0; c < 3; ++c) {
@@ -594,6 +609,7 @@ static int build_tree(sbio_geom* g, TreeFar& T) {
   if ((rc = upload_vec(g, &T.d_child, child, "tree children"))) return rc;
   if ((rc = upload_vec(g, &T.d_leaf, leaf, "tree leaves"))) return rc;
   if ((rc = upload_vec(g, &T.d_levels, lev, "tree levels"))) return rc;
+  if ((rc = upload_vec(g, &T.d_groups, groups, "tree target groups"))) return rc;
   if ((rc = upload_vec(g, &T.d_tiles, dtiles, "tree direct tiles"))) return rc;
   if ((rc = upload_vec(g, &T.d_ditems, ditems, "tree direct items"))) return rc;
   if ((rc = upload_vec(g, &T.d_mlist, mlist, "tree multipole lists"))) return rc;
@@ -622,9 +638,10 @@ static int tree_apply(sbio_geom* g, TreeFar& T, double* S, double* D, cudaStream
   const int64_t total = (int64_t)T.n_nodes * 2 * NM;
   tree_to_f32_kernel<PF><<<(unsigned)std::min<int64_t>((total + 255) / 256, 4096), 256, 0, st>>>(total, T.d_M, T.d_M32);
   count_launch();
-  launch_far_tile_items(d, T.d_tiles, T.d_ditems, T.n_ditems, h.N, S, D, st);
+  launch_far_tile_items(d, T.d_groups, T.d_tiles, T.d_ditems, T.n_ditems, S, D, st);
   if (T.n_mitems > 0) {
-    tree_m2p_kernel<PF><<<T.n_mitems, kFarTile, 0, st>>>(T.d_mitems, T.d_mlist, T.d_c32, T.d_M32, d.tgt32, h.N, S, D);
+    tree_m2p_kernel<PF><<<T.n_mitems, kFarTile, 0, st>>>(T.d_mitems, T.d_groups, T.d_mlist, T.d_c32, T.d_M32, d.tgt32,
+                                                         S, D);
     count_launch();
   }
   SBIO_CUDA_TRY(cudaGetLastError());
