@@ -1422,11 +1422,12 @@ def run_far_sweep(args, ws, rank, lrank):
             flush.zero_()
             twhole.append(_event_time(st, lambda: S.sbio_apply_laplace(g.h, sig, mu, So, Do)))
         S.sbio_geom_enable_timing(g.h, True)
-        tfar = []
+        tfar, tph = [], []
         for _ in range(reps):
             flush.zero_()
             S.sbio_apply_laplace(g.h, sig, mu, So, Do)
             tfar.append(S.sbio_geom_phase_times(g.h)[2])
+            tph.append(S.sbio_geom_tree_phase_times(g.h))
         S.sbio_geom_enable_timing(g.h, False)
         S.sbio_apply_laplace(g.h, sig, mu, So, Do)
         torch.cuda.synchronize()
@@ -1436,7 +1437,9 @@ def run_far_sweep(args, ws, rank, lrank):
                        "rel_err_vs_direct_mixed": {"S": float((So - Sd).abs().max() / Sd.abs().max()),
                                                    "D": float((Do - Dd).abs().max() / Dd.abs().max())},
                        "m2p_evaluations": info["m2p_pairs"], "direct_pairs": info["direct_pairs"],
-                       "direct_pair_fraction": info["direct_pairs"] / g.n_far, "tree_nodes": info["nodes"]}
+                       "direct_pair_fraction": info["direct_pairs"] / g.n_far, "tree_nodes": info["nodes"],
+                       "phase_ms": dict(zip(("leaf_multipoles", "translations", "direct", "evaluations"),
+                                            [statistics.median(x[k] for x in tph) for k in range(4)]))}
         rows.append(row)
         g.close()
     clk = clocks.stop()

@@ -375,6 +375,13 @@ int sbio_geom_set_far_method(sbio_geom* g, int32_t method, double theta, int32_t
 int sbio_geom_tree_info(const sbio_geom* g, int64_t* n_nodes, int64_t* n_groups, int64_t* m2p_pairs,
                         int64_t* m2p_source_pairs, int64_t* direct_pairs);
 
+/* Durations (ms) of the treecode phases of the last apply made with phase
+ * timing on (sbio_geom_enable_timing): ms[0] leaf multipoles, ms[1]
+ * translations up the tree and the FP32 copy, ms[2] the direct part, ms[3]
+ * the multipole evaluations.  Synchronises on the last phase's event.
+ * SBIO_EINVAL if the far field is direct or timing is off. */
+int sbio_geom_tree_phase_times(sbio_geom* g, double* ms);
+
 /* ---- particle-to-target evaluation (Sec. 4.1, "Particle-to-target
  * algorithm") ---------------------------------------------------------------
  * S[sigma] and D[mu] of every spheroid of a geometry at T arbitrary points in

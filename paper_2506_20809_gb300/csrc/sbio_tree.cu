@@ -87,6 +87,13 @@ struct TreeFar {
   int* d_mlist = nullptr;         // accepted node ids, group after group
   int4* d_mitems = nullptr;       // (group, first entry, end entry, 0)
   int n_mitems = 0;
+  // phase events of the last apply while the geometry's timing is on:
+  // leaf multipoles | translations + FP32 copy | direct part | evaluations
+  cudaEvent_t ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+  ~TreeFar() {
+    for (cudaEvent_t& e : ev)
+      if (e) cudaEventDestroy(e);
+  }
 };
 
 void tree_free(TreeFar* t) { delete t; }
@@ -627,8 +634,11 @@ static int tree_apply(sbio_geom* g, TreeFar& T, double* S, double* D, cudaStream
   const GeomHost& h = g->h;
   const DevGeom& d = g->d;
   constexpr int NM = tree_nm(PF);
+  const bool timed = g->timing && T.ev[0];
+  if (timed) cudaEventRecord(T.ev[0], st);
   tree_p2m_kernel<PF><<<h.M, 128, 0, st>>>(h.G, d.src32, T.d_leaf, T.d_M);
   count_launch();
+  if (timed) cudaEventRecord(T.ev[1], st);
   for (size_t l = 0; l + 1 < T.level_off.size(); ++l) {
     const int n = T.level_off[l + 1] - T.level_off[l];
     if (n <= 0) continue;
@@ -638,12 +648,15 @@ static int tree_apply(sbio_geom* g, TreeFar& T, double* S, double* D, cudaStream
   const int64_t total = (int64_t)T.n_nodes * 2 * NM;
   tree_to_f32_kernel<PF><<<(unsigned)std::min<int64_t>((total + 255) / 256, 4096), 256, 0, st>>>(total, T.d_M, T.d_M32);
   count_launch();
+  if (timed) cudaEventRecord(T.ev[2], st);
   launch_far_tile_items(d, T.d_groups, T.d_tiles, T.d_ditems, T.n_ditems, S, D, st);
+  if (timed) cudaEventRecord(T.ev[3], st);
   if (T.n_mitems > 0) {
     tree_m2p_kernel<PF><<<T.n_mitems, kFarTile, 0, st>>>(T.d_mitems, T.d_groups, T.d_mlist, T.d_c32, T.d_M32, d.tgt32,
                                                          S, D);
     count_launch();
   }
+  if (timed) cudaEventRecord(T.ev[4], st);
   SBIO_CUDA_TRY(cudaGetLastError());
   return SBIO_OK;
 }
@@ -686,6 +699,7 @@ int sbio_geom_set_far_method(sbio_geom* g, int32_t method, double theta, int32_t
   TreeFar* t = new TreeFar();
   t->order = order;
   t->theta = theta;
+  for (cudaEvent_t& e : t->ev) SBIO_CUDA_TRY(cudaEventCreate(&e));
   const int rc = build_tree(g, *t);
   if (rc) {
     delete t;
@@ -693,6 +707,20 @@ int sbio_geom_set_far_method(sbio_geom* g, int32_t method, double theta, int32_t
   }
   tree_free(g->tree);
   g->tree = t;
+  return SBIO_OK;
+}
+
+int sbio_geom_tree_phase_times(sbio_geom* g, double* ms) {
+  clear_error();
+  if (!g || !ms) return set_error(SBIO_EINVAL, "null argument");
+  if (!g->tree) return set_error(SBIO_EINVAL, "the geometry's far field is the direct sum");
+  if (!g->timing) return set_error(SBIO_EINVAL, "phase timing is off (sbio_geom_enable_timing)");
+  SBIO_CUDA_TRY(cudaEventSynchronize(g->tree->ev[4]));
+  for (int k = 0; k < 4; ++k) {
+    float t = 0.f;
+    SBIO_CUDA_TRY(cudaEventElapsedTime(&t, g->tree->ev[k], g->tree->ev[k + 1]));
+    ms[k] = t;
+  }
   return SBIO_OK;
 }
 

@@ -154,6 +154,7 @@ _SIGS = {
     "sbio_server_destroy": (C.c_int, [_vp]),
     "sbio_measure_peaks": (C.c_int, [C.c_int32, C.POINTER(sbio_peaks)]),
     "sbio_geom_set_far_method": (C.c_int, [_vp, C.c_int32, C.c_double, C.c_int32]),
+    "sbio_geom_tree_phase_times": (C.c_int, [_vp, _vp]),
     "sbio_geom_tree_info": (C.c_int, [_vp, C.POINTER(C.c_int64), C.POINTER(C.c_int64), C.POINTER(C.c_int64),
                                       C.POINTER(C.c_int64), C.POINTER(C.c_int64)]),
     "sbio_geom_near_work": (C.c_int, [_vp, C.POINTER(C.c_int64), C.POINTER(C.c_int64)]),
@@ -471,6 +472,14 @@ def sbio_geom_set_far_method(g, method, theta=0.5, order=16):
     """Far field by the direct sum (SBIO_FAR_DIRECT) or the particle treecode
     (SBIO_FAR_TREE, mixed S + D applies at the nodes)."""
     _check(_lib.sbio_geom_set_far_method(g, method, theta, order))
+
+
+def sbio_geom_tree_phase_times(g):
+    """(leaf multipoles, translations, direct part, evaluations) in ms of the
+    last timed apply."""
+    out = (C.c_double * 4)()
+    _check(_lib.sbio_geom_tree_phase_times(g, out))
+    return tuple(out)
 
 
 def sbio_geom_tree_info(g):
