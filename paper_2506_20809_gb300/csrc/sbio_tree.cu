@@ -239,44 +239,54 @@ __device__ __forceinline__ double2 signed_order(const double2* T, int n, int l) 
 }
 
 // One tree level: each internal node's multipoles from its two children's.
+// The 2 NM outputs of a node are spread over gridDim.y CTAs of kM2MThreads
+// threads (one output per thread), so that the short top levels still use
+// many SMs: the translation is FP64 and the FP64 pipe is the bound.
+constexpr int kM2MThreads = 64;
+
 template <int PF>
-__global__ void __launch_bounds__(128) tree_m2m_kernel(const int* __restrict__ ids, const int* __restrict__ child,
-                                                       const double* __restrict__ geo, double2* __restrict__ Mt) {
+__global__ void __launch_bounds__(kM2MThreads) tree_m2m_kernel(const int* __restrict__ ids,
+                                                               const int* __restrict__ child,
+                                                               const double* __restrict__ geo,
+                                                               double2* __restrict__ Mt) {
   constexpr int NM = tree_nm(PF);
   __shared__ double2 Rb[2][NM];
   __shared__ double2 Mc[2][2][NM];
   const int node = ids[blockIdx.x];
-  const int ch[2] = {child[node * 2 + 0], child[node * 2 + 1]};
+  const int ch0 = child[node * 2 + 0], ch1 = child[node * 2 + 1];
   if (threadIdx.x == 0 || threadIdx.x == 32) {
     const int k = threadIdx.x == 0 ? 0 : 1;
-    const int c = ch[k];
+    const int c = k ? ch1 : ch0;
     regular_harmonics<PF>(geo[c * 4 + 0] - geo[node * 4 + 0], geo[c * 4 + 1] - geo[node * 4 + 1],
                           geo[c * 4 + 2] - geo[node * 4 + 2], Rb[k]);
   }
   for (int k = threadIdx.x; k < 4 * NM; k += blockDim.x) {
     const int c = k / (2 * NM), rest = k - c * 2 * NM;
-    Mc[c][rest / NM][rest % NM] = Mt[((int64_t)ch[c] * 2 + rest / NM) * NM + rest % NM];
+    Mc[c][rest / NM][rest % NM] = Mt[((int64_t)(c ? ch1 : ch0) * 2 + rest / NM) * NM + rest % NM];
   }
   __syncthreads();
-  for (int k = threadIdx.x; k < 2 * NM; k += blockDim.x) {
-    const int kind = k / NM, idx = k - kind * NM;
-    int n = 0;
-    while (tree_idx(n + 1, 0) <= idx) ++n;
-    const int m = idx - tree_idx(n, 0);
-    double ar = 0.0, ai = 0.0;
-    for (int c = 0; c < 2; ++c)
-      for (int kk = 0; kk <= n; ++kk)
-        for (int l = -kk; l <= kk; ++l) {
-          const int nn = n - kk, mm = m - l;
-          if (mm > nn || mm < -nn) continue;
-          const double2 r = signed_order(Rb[c], kk, l);
-          const double2 v = signed_order(Mc[c][kind], nn, mm);
-          // conj(r) * v
-          ar += r.x * v.x + r.y * v.y;
-          ai += r.x * v.y - r.y * v.x;
-        }
-    Mt[((int64_t)node * 2 + kind) * NM + idx] = make_double2(ar, ai);
+  const int k = blockIdx.y * blockDim.x + threadIdx.x;
+  if (k >= 2 * NM) return;
+  const int kind = k / NM, idx = k - kind * NM;
+  int n = 0;
+  while (tree_idx(n + 1, 0) <= idx) ++n;
+  const int m = idx - tree_idx(n, 0);
+  double ar = 0.0, ai = 0.0;
+  for (int c = 0; c < 2; ++c) {
+    for (int kk = 0; kk <= n; ++kk) {
+      const int nn = n - kk;
+      // |m - l| <= nn and |l| <= kk
+      const int l_lo = max(-kk, m - nn), l_hi = min(kk, m + nn);
+      for (int l = l_lo; l <= l_hi; ++l) {
+        const double2 r = signed_order(Rb[c], kk, l);
+        const double2 v = signed_order(Mc[c][kind], nn, m - l);
+        // conj(r) * v
+        ar = fma(r.x, v.x, fma(r.y, v.y, ar));
+        ai = fma(r.x, v.y, fma(-r.y, v.x, ai));
+      }
+    }
   }
+  Mt[((int64_t)node * 2 + kind) * NM + idx] = make_double2(ar, ai);
 }
 
 // FP32 copy of every node's multipoles with the m > 0 terms doubled, so the
@@ -295,7 +305,10 @@ __global__ void tree_to_f32_kernel(int64_t total, const double2* __restrict__ Mt
 }
 
 // Multipole evaluation: one CTA per (group of at most 256 targets, up to
-// kTreeChunkNodes accepted nodes), two targets per thread.
+// kTreeChunkNodes accepted nodes), two targets per thread packed into one
+// f32x2 lane pair (sm_100+ packed FP32), so each recurrence and contraction
+// step issues once for both.  The node's coefficients are staged in shared
+// memory already broadcast to lane pairs: (re, re, -im, -im).
 template <int PF>
 __global__ void __launch_bounds__(kFarTile) tree_m2p_kernel(const int4* __restrict__ items, const int2* __restrict__ groups,
                                                             const int* __restrict__ mlist,
@@ -304,7 +317,7 @@ __global__ void __launch_bounds__(kFarTile) tree_m2p_kernel(const int4* __restri
                                                             const float4* __restrict__ tgt32,
                                                             double* __restrict__ S_out, double* __restrict__ D_out) {
   constexpr int NM = tree_nm(PF);
-  __shared__ float2 cf[2 * NM];
+  __shared__ float4 cf[2 * NM];
   __shared__ float4 cc[2];
   const int4 it = items[blockIdx.x];
   const int2 grp = groups[it.x];
@@ -326,71 +339,71 @@ __global__ void __launch_bounds__(kFarTile) tree_m2p_kernel(const int4* __restri
   for (int e = it.y; e < it.z; ++e) {
     const int node = mlist[e];
     __syncthreads();
-    for (int k = tid; k < 2 * NM; k += kFarTile) cf[k] = M32[(int64_t)node * 2 * NM + k];
+    for (int k = tid; k < 2 * NM; k += kFarTile) {
+      const float2 v = M32[(int64_t)node * 2 * NM + k];
+      cf[k] = make_float4(v.x, v.x, -v.y, -v.y);
+    }
     if (tid < 2) cc[tid] = c32[node * 2 + tid];
     __syncthreads();
     const float4 ch = cc[0], cl = cc[1];
-    float X[2], Y[2], Z[2], ir2[2], zs[2], Ir[2], Ii[2], sS[2], sD[2];
+    float Xs[2], Ys[2], Zs[2], I2[2], R0[2];
 #pragma unroll
     for (int q = 0; q < 2; ++q) {
-      X[q] = (xh[q].x - ch.x) + (xl[q].x - cl.x);
-      Y[q] = (xh[q].y - ch.y) + (xl[q].y - cl.y);
-      Z[q] = (xh[q].z - ch.z) + (xl[q].z - cl.z);
-      const float r2 = fmaf(Z[q], Z[q], fmaf(Y[q], Y[q], X[q] * X[q]));
+      const float X = (xh[q].x - ch.x) + (xl[q].x - cl.x);
+      const float Y = (xh[q].y - ch.y) + (xl[q].y - cl.y);
+      const float Z = (xh[q].z - ch.z) + (xl[q].z - cl.z);
+      const float r2 = fmaf(Z, Z, fmaf(Y, Y, X * X));
       const float ri = rsqrt_f32(r2);
-      ir2[q] = ri * ri;
-      zs[q] = Z[q] * ir2[q];
-      X[q] *= ir2[q];
-      Y[q] *= ir2[q];
-      Ir[q] = ri;      // I_m^m, starting at I_0^0 = 1 / r
-      Ii[q] = 0.f;
-      sS[q] = sD[q] = 0.f;
+      I2[q] = ri * ri;
+      Xs[q] = X * I2[q];
+      Ys[q] = Y * I2[q];
+      Zs[q] = Z * I2[q];
+      R0[q] = ri;
     }
+    const float2 xs = make_float2(Xs[0], Xs[1]), ys = make_float2(Ys[0], Ys[1]);
+    const float2 zs = make_float2(Zs[0], Zs[1]), ir2 = make_float2(I2[0], I2[1]);
+    float2 Ir = make_float2(R0[0], R0[1]), Ii = make_float2(0.f, 0.f);   // I_m^m, from I_0^0 = 1 / r
+    float2 sS = make_float2(0.f, 0.f), sD = make_float2(0.f, 0.f);
 #pragma unroll
     for (int m = 0; m <= PF; ++m) {
-      float ar[2], ai[2], br[2], bi[2];   // I_{n-1}^m, I_{n-2}^m
-#pragma unroll
-      for (int q = 0; q < 2; ++q) {
-        if (m > 0) {
-          // I_m^m = -(2m - 1) (x + i y) / r^2 I_{m-1}^{m-1}
-          const float s = -(float)(2 * m - 1);
-          const float tr = s * (X[q] * Ir[q] - Y[q] * Ii[q]), ti = s * (X[q] * Ii[q] + Y[q] * Ir[q]);
-          Ir[q] = tr;
-          Ii[q] = ti;
-        }
-        const float2 a = cf[tree_idx(m, m)], b = cf[NM + tree_idx(m, m)];
-        sS[q] = fmaf(a.x, Ir[q], fmaf(-a.y, Ii[q], sS[q]));
-        sD[q] = fmaf(b.x, Ir[q], fmaf(-b.y, Ii[q], sD[q]));
-        ar[q] = Ir[q];
-        ai[q] = Ii[q];
-        br[q] = bi[q] = 0.f;
+      if (m > 0) {
+        // I_m^m = -(2m - 1) (x + i y) / r^2 I_{m-1}^{m-1}
+        const float2 s2 = make_float2(-(float)(2 * m - 1), -(float)(2 * m - 1));
+        const float2 wr = __fmul2_rn(s2, xs), wi = __fmul2_rn(s2, ys);
+        const float2 tr = __ffma2_rn(wr, Ir, __fmul2_rn(make_float2(-wi.x, -wi.y), Ii));
+        const float2 ti = __ffma2_rn(wr, Ii, __fmul2_rn(wi, Ir));
+        Ir = tr;
+        Ii = ti;
       }
+      {
+        const float4 a = cf[tree_idx(m, m)], b = cf[NM + tree_idx(m, m)];
+        sS = __ffma2_rn(make_float2(a.x, a.y), Ir, __ffma2_rn(make_float2(a.z, a.w), Ii, sS));
+        sD = __ffma2_rn(make_float2(b.x, b.y), Ir, __ffma2_rn(make_float2(b.z, b.w), Ii, sD));
+      }
+      float2 ar = Ir, ai = Ii, br = make_float2(0.f, 0.f), bi = make_float2(0.f, 0.f);   // I_{n-1}^m, I_{n-2}^m
 #pragma unroll
       for (int n = m + 1; n <= PF; ++n) {
-        const float2 a = cf[tree_idx(n, m)], b = cf[NM + tree_idx(n, m)];
-        const float kz = (float)(2 * n - 1);
-        const float kb = (float)((n - 1 - m) * (n - 1 + m));
-#pragma unroll
-        for (int q = 0; q < 2; ++q) {
-          // I_n^m = ((2n - 1) z I_{n-1}^m - (n-1-m)(n-1+m) I_{n-2}^m) / r^2
-          const float u = kz * zs[q], v = kb * ir2[q];
-          const float cr = fmaf(u, ar[q], -v * br[q]), ci = fmaf(u, ai[q], -v * bi[q]);
-          sS[q] = fmaf(a.x, cr, fmaf(-a.y, ci, sS[q]));
-          sD[q] = fmaf(b.x, cr, fmaf(-b.y, ci, sD[q]));
-          br[q] = ar[q];
-          bi[q] = ai[q];
-          ar[q] = cr;
-          ai[q] = ci;
-        }
+        // I_n^m = ((2n - 1) z I_{n-1}^m - (n-1-m)(n-1+m) I_{n-2}^m) / r^2
+        const float kz = (float)(2 * n - 1), kb = -(float)((n - 1 - m) * (n - 1 + m));
+        const float2 u = __fmul2_rn(make_float2(kz, kz), zs), v = __fmul2_rn(make_float2(kb, kb), ir2);
+        const float2 cr = __ffma2_rn(u, ar, __fmul2_rn(v, br)), ci = __ffma2_rn(u, ai, __fmul2_rn(v, bi));
+        const float4 a = cf[tree_idx(n, m)], b = cf[NM + tree_idx(n, m)];
+        sS = __ffma2_rn(make_float2(a.x, a.y), cr, __ffma2_rn(make_float2(a.z, a.w), ci, sS));
+        sD = __ffma2_rn(make_float2(b.x, b.y), cr, __ffma2_rn(make_float2(b.z, b.w), ci, sD));
+        br = ar;
+        bi = ai;
+        ar = cr;
+        ai = ci;
       }
     }
+    const float pS[2] = {sS.x, sS.y}, pD[2] = {sD.x, sD.y};
 #pragma unroll
     for (int q = 0; q < 2; ++q) {
       float s, e;
-      two_sum_f32(hS[q], sS[q], s, e);
+      two_sum_f32(hS[q], pS[q], s, e);
       hS[q] = s;
       lS[q] += e;
-      two_sum_f32(hD[q], sD[q], s, e);
+      two_sum_f32(hD[q], pD[q], s, e);
       hD[q] = s;
       lD[q] += e;
     }
@@ -642,7 +655,8 @@ static int tree_apply(sbio_geom* g, TreeFar& T, double* S, double* D, cudaStream
   for (size_t l = 0; l + 1 < T.level_off.size(); ++l) {
     const int n = T.level_off[l + 1] - T.level_off[l];
     if (n <= 0) continue;
-    tree_m2m_kernel<PF><<<n, 128, 0, st>>>(T.d_levels + T.level_off[l], T.d_child, T.d_geo, T.d_M);
+    const dim3 grid((unsigned)n, (unsigned)((2 * NM + kM2MThreads - 1) / kM2MThreads));
+    tree_m2m_kernel<PF><<<grid, kM2MThreads, 0, st>>>(T.d_levels + T.level_off[l], T.d_child, T.d_geo, T.d_M);
     count_launch();
   }
   const int64_t total = (int64_t)T.n_nodes * 2 * NM;
