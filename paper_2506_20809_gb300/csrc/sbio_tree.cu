@@ -36,8 +36,10 @@
 // mixed kernel with the per-target skip lists, so each (target, particle)
 // pair outside the target's own and near set is counted exactly once.
 //
-// Per apply: leaf multipoles from the FP32 sources (FP32 per warp, FP64
-// across warps), translations up the tree in FP64, conversion to FP32, then
+// Per apply: leaf multipoles from the FP32 sources (FP32 per warp with TwoSum
+// compensation for the orders n < 4 that carry most of the far field, FP64
+// across warps), translations up the tree in FP64 for the nodes the lists
+// read, conversion to FP32, then
 // the direct part and the multipole evaluations (FP32, per-node sums folded
 // by TwoSum), each added atomically into the FP64 outputs.
 #include <algorithm>
@@ -71,6 +73,7 @@ struct TreeFar {
   std::vector<std::vector<int>> levels;      // internal node ids per level
   int64_t m2p_pairs = 0, direct_pairs = 0, m2p_entries = 0, direct_tiles = 0;
   int64_t m2p_source_pairs = 0;   // (target, source node) pairs the accepted nodes stand for
+  int n_translated = 0;            // internal nodes whose multipoles are formed per apply
   // device
   double* d_geo = nullptr;        // n_nodes x 4: centre, radius
   float4* d_c32 = nullptr;        // n_nodes x 2: hi, lo parts of the centre
@@ -113,13 +116,18 @@ template <int PF>
 __global__ void __launch_bounds__(128) tree_p2m_kernel(int G, const float4* __restrict__ src32,
                                                        const int* __restrict__ leaf, double2* __restrict__ Mout) {
   constexpr int NM = tree_nm(PF);
+  constexpr int NC = 4;   // orders n < NC carry TwoSum compensation (they dominate the far field)
   __shared__ float red[4][32][PF + 1][4];
+  __shared__ float redc[4][32][NC][4];
   const int i = blockIdx.x;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int m = lane;
   float aSr[PF + 1], aSi[PF + 1], aDr[PF + 1], aDi[PF + 1];
+  float cSr[NC], cSi[NC], cDr[NC], cDi[NC];
 #pragma unroll
   for (int n = 0; n <= PF; ++n) aSr[n] = aSi[n] = aDr[n] = aDi[n] = 0.f;
+#pragma unroll
+  for (int n = 0; n < NC; ++n) cSr[n] = cSi[n] = cDr[n] = cDi[n] = 0.f;
   for (int j = warp; j < G; j += 4) {
     const float4 A = src32[((int64_t)i * G + j) * 2 + 0];
     const float4 B = src32[((int64_t)i * G + j) * 2 + 1];
@@ -159,8 +167,18 @@ __global__ void __launch_bounds__(128) tree_p2m_kernel(int G, const float4* __re
       const float upr = __shfl_down_sync(0xffffffffu, r1r, 1), upi = __shfl_down_sync(0xffffffffu, r1i, 1);
       const float dnr = __shfl_up_sync(0xffffffffu, r1r, 1), dni = __shfl_up_sync(0xffffffffu, r1i, 1);
       if (m <= PF && n >= m) {
-        aSr[n] = fmaf(q, cr, aSr[n]);
-        aSi[n] = fmaf(-q, ci, aSi[n]);
+        if (n < NC) {
+          float s2, e2;
+          two_sum_f32(aSr[n], q * cr, s2, e2);
+          aSr[n] = s2;
+          cSr[n] += e2;
+          two_sum_f32(aSi[n], -q * ci, s2, e2);
+          aSi[n] = s2;
+          cSi[n] += e2;
+        } else {
+          aSr[n] = fmaf(q, cr, aSr[n]);
+          aSi[n] = fmaf(-q, ci, aSi[n]);
+        }
         if (n >= 1) {
           float er = dz * r1r, ei = -dz * r1i;                   // d_z conj R_{n-1}^m
           er += dr * upr + di * upi;                              // delta conj R_{n-1}^{m+1}
@@ -172,8 +190,18 @@ __global__ void __launch_bounds__(128) tree_p2m_kernel(int G, const float4* __re
             er += dr * upr + di * upi;
             ei += dr * upi - di * upr;
           }
-          aDr[n] += er;
-          aDi[n] += ei;
+          if (n < NC) {
+            float s2, e2;
+            two_sum_f32(aDr[n], er, s2, e2);
+            aDr[n] = s2;
+            cDr[n] += e2;
+            two_sum_f32(aDi[n], ei, s2, e2);
+            aDi[n] = s2;
+            cDi[n] += e2;
+          } else {
+            aDr[n] += er;
+            aDi[n] += ei;
+          }
         }
       }
       r2r = r1r;
@@ -189,6 +217,13 @@ __global__ void __launch_bounds__(128) tree_p2m_kernel(int G, const float4* __re
     red[warp][lane][n][2] = aDr[n];
     red[warp][lane][n][3] = aDi[n];
   }
+#pragma unroll
+  for (int n = 0; n < NC; ++n) {
+    redc[warp][lane][n][0] = cSr[n];
+    redc[warp][lane][n][1] = cSi[n];
+    redc[warp][lane][n][2] = cDr[n];
+    redc[warp][lane][n][3] = cDi[n];
+  }
   __syncthreads();
   const int node = leaf[i];
   for (int k = threadIdx.x; k < NM; k += blockDim.x) {
@@ -202,6 +237,12 @@ __global__ void __launch_bounds__(128) tree_p2m_kernel(int G, const float4* __re
       si += red[w][mm][n][1];
       er += red[w][mm][n][2];
       ei += red[w][mm][n][3];
+      if (n < NC) {
+        sr += redc[w][mm][n][0];
+        si += redc[w][mm][n][1];
+        er += redc[w][mm][n][2];
+        ei += redc[w][mm][n][3];
+      }
     }
     Mout[((int64_t)node * 2 + 0) * NM + k] = make_double2(sr, si);
     Mout[((int64_t)node * 2 + 1) * NM + k] = make_double2(er, ei);
@@ -617,9 +658,24 @@ static int build_tree(sbio_geom* g, TreeFar& T) {
     child[id * 2 + 0] = nd.child[0];
     child[id * 2 + 1] = nd.child[1];
   }
+  // translations only where a list reads the result: a node is needed if it
+  // is accepted somewhere or lies below an accepted node (nodes come in
+  // depth-first pre-order, so a parent precedes its children); the top
+  // levels, whose nodes are too large to be accepted, are skipped
+  std::vector<char> needed(T.n_nodes, 0);
+  for (int id : mlist) needed[id] = 1;
+  for (int id = 0; id < T.n_nodes; ++id)
+    if (needed[id])
+      for (int c : T.nodes[id].child)
+        if (c >= 0) needed[c] = 1;
+  T.n_translated = 0;
   T.level_off.assign(1, 0);
   for (int l = T.n_levels - 1; l >= 0; --l) {   // deepest level first
-    lev.insert(lev.end(), T.levels[l].begin(), T.levels[l].end());
+    for (int id : T.levels[l])
+      if (needed[id]) {
+        lev.push_back(id);
+        ++T.n_translated;
+      }
     T.level_off.push_back((int)lev.size());
   }
   const int NM = tree_nm(T.order);
