@@ -575,9 +575,12 @@ def run_ours(args, ws, rank, lrank):
                          "frac_of_measured_ffma2": achieved / peaks["fp32_ffma2_tflops"],
                          "pairmix_pairs_per_s": peaks["pairmix_pairs_per_s"],
                          "frac_of_pairmix": geom.n_far / (far_mean * 1e-3) / peaks["pairmix_pairs_per_s"],
-                         "note": "measured by sbio_measure_peaks on this GPU: f32x2 FMA chains, and the packed far "
+                         "pairsmem_pairs_per_s": peaks["pairsmem_pairs_per_s"],
+                         "frac_of_pairsmem": geom.n_far / (far_mean * 1e-3) / peaks["pairsmem_pairs_per_s"],
+                         "note": "measured by sbio_measure_peaks on this GPU: f32x2 FMA chains; the packed far "
                                  "pair's register arithmetic (11 f32x2 + 2 MUFU per 2 pairs) with no memory "
-                                 "traffic"} if prec == S.SBIO_MIXED else None},
+                                 "traffic (pairmix); the same fed from shared memory as the kernel does, without "
+                                 "tiles or barriers (pairsmem)"} if prec == S.SBIO_MIXED else None},
         "sfu": {"kernel": "far_mixed_kernel" if prec == S.SBIO_MIXED else "far_fp64_kernel",
                 "unit": "rsqrt/s", "achieved": geom.n_far / (far_mean * 1e-3), "peak": sfu_peak(),
                 "frac": geom.n_far / (far_mean * 1e-3) / sfu_peak(),

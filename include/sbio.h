@@ -124,6 +124,9 @@ int64_t sbio_launch_count(void);
  *     far kernel's register arithmetic per two pairs (11 f32x2 instructions,
  *     2 rsqrt) and no memory traffic, i.e. the rate the far kernel could
  *     reach if staging and bookkeeping cost nothing;
+ *   pairsmem_pairs_per_s: the same pairs with the sources read from shared
+ *     memory as the far kernel reads them (five 16-byte loads per source,
+ *     8 targets per thread) but without tiles, skip lists or barriers;
  *   sm_clock_mhz: SM clock during the kernels (%clock64 over %globaltimer);
  *   sms: multiprocessor count.
  * Synchronous; allocates 48 bytes of device memory for the duration of the
@@ -134,6 +137,7 @@ typedef struct {
   double rsqrt_per_s;
   double fp64_dfma_tflops;
   double pairmix_pairs_per_s;
+  double pairsmem_pairs_per_s;
   double sm_clock_mhz;
   int32_t sms;
   int32_t reserved;

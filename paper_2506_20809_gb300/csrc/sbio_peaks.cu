@@ -160,6 +160,61 @@ __global__ void __launch_bounds__(kPeakThreads) pairmix_kernel(int iters, float 
   if (s == -1.2345f) sink[0] = s;
 }
 
+// The same pair fed from shared memory as the far kernel feeds it: 128
+// sources staged once per CTA with every operand duplicated into an f32x2
+// pair (five 16-byte loads per source), 8 targets per thread, no tiles, skip
+// lists or barriers inside the loop.  Counted as 8 pairs per source per thread.
+__global__ void __launch_bounds__(128) pairsmem_kernel(int reps, float b, float c, float* sink, double* mhz) {
+  ClockProbe cp;
+  cp.start();
+  __shared__ float4 sh[5 * 128];
+  const int tid = threadIdx.x;
+  {
+    const float y0 = b * (float)(tid % 7), y1 = c * (float)(tid % 5), y2 = -b * (float)(tid % 3);
+    const float yy = y0 * y0 + y1 * y1 + y2 * y2;
+    sh[tid * 5 + 0] = make_float4(-2.f * y0, -2.f * y0, -2.f * y1, -2.f * y1);
+    sh[tid * 5 + 1] = make_float4(-2.f * y2, -2.f * y2, yy, yy);
+    sh[tid * 5 + 2] = make_float4(c, c, -b, -b);
+    sh[tid * 5 + 3] = make_float4(b, b, c, c);
+    sh[tid * 5 + 4] = make_float4(b, b, 0.f, 0.f);
+  }
+  __syncthreads();
+  constexpr int TP = 4;
+  float2 Xp[TP], Yp[TP], Zp[TP], XXp[TP], sS[TP], sD[TP];
+#pragma unroll
+  for (int k = 0; k < TP; ++k) {
+    const float x0 = 3.f + 0.01f * tid + k, x1 = 2.f - 0.01f * k, x2 = 4.f + 0.001f * tid;
+    Xp[k] = make_float2(x0, x0 + 0.1f);
+    Yp[k] = make_float2(x1, x1 - 0.1f);
+    Zp[k] = make_float2(x2, x2 + 0.2f);
+    XXp[k] = make_float2(x0 * x0 + x1 * x1 + x2 * x2,
+                         (x0 + .1f) * (x0 + .1f) + (x1 - .1f) * (x1 - .1f) + (x2 + .2f) * (x2 + .2f));
+    sS[k] = sD[k] = make_float2(0.f, 0.f);
+  }
+  for (int r = 0; r < reps; ++r) {
+#pragma unroll 1
+    for (int j = 0; j < 128; ++j) {
+      const float4 A = sh[j * 5 + 0], B = sh[j * 5 + 1], Cc = sh[j * 5 + 2], Dd = sh[j * 5 + 3], Ee = sh[j * 5 + 4];
+      const float2 mx = make_float2(A.x, A.y), my = make_float2(A.z, A.w), mz = make_float2(B.x, B.y);
+      const float2 yy = make_float2(B.z, B.w), q2 = make_float2(Cc.x, Cc.y), ndy = make_float2(Cc.z, Cc.w);
+      const float2 dwx = make_float2(Dd.x, Dd.y), dwy = make_float2(Dd.z, Dd.w), dwz = make_float2(Ee.x, Ee.y);
+#pragma unroll
+      for (int k = 0; k < TP; ++k) {
+        const float2 r2 = __ffma2_rn(Xp[k], mx, __ffma2_rn(Yp[k], my, __ffma2_rn(Zp[k], mz, __fadd2_rn(XXp[k], yy))));
+        const float2 ri = make_float2(rsqrt_f32(r2.x), rsqrt_f32(r2.y));
+        sS[k] = __ffma2_rn(q2, ri, sS[k]);
+        const float2 dn = __ffma2_rn(dwx, Xp[k], __ffma2_rn(dwy, Yp[k], __ffma2_rn(dwz, Zp[k], ndy)));
+        sD[k] = __ffma2_rn(__fmul2_rn(dn, ri), __fmul2_rn(ri, ri), sD[k]);
+      }
+    }
+  }
+  cp.stop(mhz);
+  float s = 0.f;
+#pragma unroll
+  for (int k = 0; k < TP; ++k) s += sS[k].x + sS[k].y + sD[k].x + sD[k].y;
+  if (s == -1.2345f) sink[0] = s;
+}
+
 }  // namespace
 
 }  // namespace sbio
@@ -183,11 +238,11 @@ extern "C" int sbio_measure_peaks(int32_t device, sbio_peaks* out) {
   cudaError_t err = cudaEventCreate(&e0);
   if (err == cudaSuccess) err = cudaEventCreate(&e1);
   if (err == cudaSuccess) err = cudaMalloc(&sink, sizeof(float));
-  if (err == cudaSuccess) err = cudaMalloc(&mhz, 5 * sizeof(double));
-  if (err == cudaSuccess) err = cudaMemsetAsync(mhz, 0, 5 * sizeof(double), st);
+  if (err == cudaSuccess) err = cudaMalloc(&mhz, 6 * sizeof(double));
+  if (err == cudaSuccess) err = cudaMemsetAsync(mhz, 0, 6 * sizeof(double), st);
   const dim3 grid((unsigned)(sms * kPeakCtasPerSm)), block(kPeakThreads);
   const double threads = (double)grid.x * block.x;
-  double ms[5] = {0, 0, 0, 0, 0};
+  double ms[6] = {0, 0, 0, 0, 0, 0};
   // rounds per thread: each kernel runs for a few milliseconds at full rate
   const int it_f32 = 4096, it_mufu = 512, it_f64 = 512, it_mix = 2048;
   auto timed = [&](int k, auto launch) {
@@ -207,8 +262,11 @@ extern "C" int sbio_measure_peaks(int32_t device, sbio_peaks* out) {
   timed(2, [&] { rsqrt_kernel<<<grid, block, 0, st>>>(it_mufu, 1.5f, 0.f, sink, mhz + 2); });
   timed(3, [&] { dfma_kernel<<<grid, block, 0, st>>>(it_f64, 0.999, 1e-3, sink, mhz + 3); });
   timed(4, [&] { pairmix_kernel<<<grid, block, 0, st>>>(it_mix, 0.999f, 1e-3f, sink, mhz + 4); });
-  count_launch(10);
-  double clk[5] = {0, 0, 0, 0, 0};
+  const int reps_smem = 32;
+  const dim3 grid_smem((unsigned)(sms * 16));
+  timed(5, [&] { pairsmem_kernel<<<grid_smem, 128, 0, st>>>(reps_smem, 0.1f, 0.2f, sink, mhz + 5); });
+  count_launch(12);
+  double clk[6] = {0, 0, 0, 0, 0, 0};
   if (err == cudaSuccess) err = cudaMemcpy(clk, mhz, sizeof(clk), cudaMemcpyDeviceToHost);
   if (sink) cudaFree(sink);
   if (mhz) cudaFree(mhz);
@@ -223,6 +281,7 @@ extern "C" int sbio_measure_peaks(int32_t device, sbio_peaks* out) {
   out->rsqrt_per_s = threads * it_mufu * 4 * kChains / (ms[2] * s);
   out->fp64_dfma_tflops = threads * it_f64 * kChains * 2.0 / (ms[3] * s) / 1e12;
   out->pairmix_pairs_per_s = threads * it_mix * 4 * 2.0 / (ms[4] * s);
+  out->pairsmem_pairs_per_s = (double)grid_smem.x * 128 * reps_smem * 128 * 8.0 / (ms[5] * s);
   double c = 0.0;
   int nc = 0;
   for (double v : clk)

@@ -69,6 +69,7 @@ class sbio_solve_info(C.Structure):
 class sbio_peaks(C.Structure):
     _fields_ = [("fp32_ffma_tflops", C.c_double), ("fp32_ffma2_tflops", C.c_double), ("rsqrt_per_s", C.c_double),
                 ("fp64_dfma_tflops", C.c_double), ("pairmix_pairs_per_s", C.c_double),
+                ("pairsmem_pairs_per_s", C.c_double),
                 ("sm_clock_mhz", C.c_double), ("sms", C.c_int32), ("reserved", C.c_int32)]
 
 

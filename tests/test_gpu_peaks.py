@@ -34,3 +34,5 @@ def test_measured_peaks_are_plausible(S):
     assert 0 < pk["fp64_dfma_tflops"] < 1.05 * pk["sms"] * 64 * 2 * ghz / 1e3
     # the pair mix can go no faster than its FP32 share allows (11 f32x2 per 2 pairs)
     assert 0 < pk["pairmix_pairs_per_s"] < 1.05 * pk["fp32_ffma2_tflops"] * 1e12 / 22.0
+    # fed from shared memory the pair cannot be faster than from registers
+    assert 0 < pk["pairsmem_pairs_per_s"] < 1.05 * pk["pairmix_pairs_per_s"]
