@@ -55,9 +55,10 @@ def fp32_peak():
 
 
 def sfu_peak():
-    """MUFU rsqrt peak per second: the XU pipe issues one warp instruction per
-    4 cycles per SM sub-partition (ncu's XU peak), i.e. 32 per clock per SM."""
-    return _PEAK_BASIS["sms"] * 32 * _PEAK_BASIS["mhz"] * 1e6
+    """MUFU rsqrt peak per second: 16 per clock per SM, the rate the rsqrt
+    chains of sbio_measure_peaks reach on GB300 (4.99e12 /s on 152 SMs at
+    2.06 GHz; ncu's XU percentage is relative to twice that)."""
+    return _PEAK_BASIS["sms"] * 16 * _PEAK_BASIS["mhz"] * 1e6
 
 
 _MEASURED = {}
