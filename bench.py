@@ -744,14 +744,10 @@ def run_batch64(args, ws, rank, lrank):
     Do = [torch.empty_like(o) for o in So]
     st = torch.cuda.current_stream()
     b = S.sbio_batch_create(ctx, geoms)
-    best = None
-    for tt in (1, 2, 4, 8, -2, -4, -8):                # autotune the persistent far kernel
-        S.sbio_batch_set_far_tt(b, tt)
-        S.sbio_batch_apply(b, sig, mu, So, Do)
-        t = min(_event_time(st, lambda: S.sbio_batch_apply(b, sig, mu, So, Do)) for _ in range(2))
-        if best is None or t < best[1]:
-            best = (tt, t)
-    S.sbio_batch_set_far_tt(b, best[0])
+    # the library's batch autotuner: far targets per thread, near CTA size, persistent grid
+    t0 = time.perf_counter()
+    best = S.sbio_batch_autotune(b, sig, mu, So, Do)
+    tune_s = time.perf_counter() - t0
     for _ in range(args.warmup):
         S.sbio_batch_apply(b, sig, mu, So, Do)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
@@ -780,7 +776,9 @@ def run_batch64(args, ws, rank, lrank):
             "config": {"workload": "batch64", "suspensions": 64, "suspensions_on_rank0": len(susps),
                        "M": [s.M for s in susps], "p": [s.p for s in susps],
                        "far_pairs_per_step": info["far_pairs"], "work_items": info["n_items"],
-                       "persistent_grid": info["grid"], "far_targets_per_thread": best[0],
+                       "persistent_grid": info["grid"],
+                       "autotuned": {"far_targets_per_thread": best[0], "near_threads_per_cta": best[1],
+                                     "far_ctas_per_sm": best[2], "step_ms": best[3], "tuner_s": tune_s},
                        "l2": "flushed by a 256 MiB write before every timed step"},
             "gpairs_per_s": info["far_pairs"] / (mean * 1e-3) / 1e9,
             "roofline": {"kernel": "whole step (far_persistent_kernel dominant)", "bound": "alu",

@@ -535,6 +535,19 @@ int sbio_batch_set_far_tt(sbio_batch* b, int32_t far_tt);
 
 /* sigma, mu, S_out, D_out: host arrays of n device pointers (layouts as in
  * sbio_apply_laplace for each suspension).  Asynchronous on `stream`. */
+/* Autotuner of a batch (the launch shapes are the library's to choose, the
+ * tuner the project writes): times whole batched steps (CUDA events on
+ * `stream`, best of two after one warm replay, graph recaptured per shape)
+ * over the persistent far kernel's targets per thread (1, 2, 4, 8 scalar;
+ * 2, 4, 8 packed), then the near kernels' thread-group size (64 or 128
+ * threads per CTA, set on every geometry of the batch), then the persistent
+ * grid (4, 5, 6 or 8 CTAs per SM), keeps the fastest and reports it (any
+ * output may be NULL; step_ms is its step time).  The buffers are those of
+ * sbio_batch_apply and are overwritten.  Synchronises `stream`. */
+int sbio_batch_autotune(sbio_batch* b, const double* const* sigma, const double* const* mu, double* const* S_out,
+                        double* const* D_out, void* stream, int32_t* far_tt, int32_t* near_block,
+                        int32_t* ctas_per_sm, double* step_ms);
+
 int sbio_batch_apply(sbio_batch* b, const double* const* sigma, const double* const* mu,
                      double* const* S_out, double* const* D_out, void* stream);
 

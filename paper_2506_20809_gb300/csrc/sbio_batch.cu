@@ -25,6 +25,7 @@ struct sbio_batch {
   int* d_counter = nullptr;
   int far_tt = 2;
   int grid = 0;
+  int ctas_per_sm = 6;                 // persistent far grid = SMs x this
   int64_t far_pairs = 0;
   cudaStream_t sa = nullptr, sb = nullptr;
   cudaEvent_t ev_fork = nullptr, ev_synth = nullptr, ev_near = nullptr;
@@ -77,7 +78,7 @@ static int build_items(sbio_batch* b) {
   // queue is empty (running the FP64 near kernels in slots left beside it
   // measured slower); the near kernels of the suspensions then run side by
   // side on their streams
-  b->grid = std::max(1, std::min(b->n_items, sms * 6));
+  b->grid = std::max(1, std::min(b->n_items, sms * b->ctas_per_sm));
   return SBIO_OK;
 }
 
@@ -135,6 +136,9 @@ static int capture(sbio_batch* b, const double* const* sigma, const double* cons
 using namespace sbio;
 
 extern "C" {
+
+int sbio_batch_apply(sbio_batch* b, const double* const* sigma, const double* const* mu, double* const* S_out,
+                     double* const* D_out, void* stream);
 
 int sbio_batch_create(sbio_ctx* ctx, sbio_geom* const* geoms, int32_t n, sbio_batch** out) {
   clear_error();
@@ -216,6 +220,87 @@ int sbio_batch_set_far_tt(sbio_batch* b, int32_t tt) {
   b->far_tt = tt;
   drop_graph(b);
   return build_items(b);
+}
+
+int sbio_batch_autotune(sbio_batch* b, const double* const* sigma, const double* const* mu, double* const* S_out,
+                        double* const* D_out, void* stream, int32_t* far_tt, int32_t* near_block,
+                        int32_t* ctas_per_sm, double* step_ms) {
+  clear_error();
+  if (!b || !sigma || !mu || !S_out || !D_out) return set_error(SBIO_EINVAL, "null argument");
+  SBIO_CUDA_TRY(cudaSetDevice(b->ctx->device));
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  SBIO_CUDA_TRY(cudaEventCreate(&e0));
+  SBIO_CUDA_TRY(cudaEventCreate(&e1));
+  // one warm replay, then the best of two timed replays of the whole step
+  auto time_step = [&](double* ms) -> int {
+    int rc = sbio_batch_apply(b, sigma, mu, S_out, D_out, stream);
+    if (rc) return rc;
+    double best = 1e300;
+    for (int r = 0; r < 2; ++r) {
+      SBIO_CUDA_TRY(cudaEventRecord(e0, st));
+      rc = sbio_batch_apply(b, sigma, mu, S_out, D_out, stream);
+      if (rc) return rc;
+      SBIO_CUDA_TRY(cudaEventRecord(e1, st));
+      SBIO_CUDA_TRY(cudaEventSynchronize(e1));
+      float t = 0.f;
+      SBIO_CUDA_TRY(cudaEventElapsedTime(&t, e0, e1));
+      best = std::min(best, (double)t);
+    }
+    *ms = best;
+    return SBIO_OK;
+  };
+  auto set_near_block = [&](int nb) {
+    for (sbio_geom* g : b->geoms) g->d.near_block = nb;
+  };
+  auto configure = [&](int tt, int nb, int cps) -> int {
+    SBIO_CUDA_TRY(cudaStreamSynchronize(st));
+    SBIO_CUDA_TRY(cudaStreamSynchronize(b->sa));
+    set_near_block(nb);
+    b->far_tt = tt;
+    b->ctas_per_sm = cps;
+    drop_graph(b);   // the launch shapes are baked into the captured graph
+    return build_items(b);
+  };
+  int best_tt = b->far_tt, best_nb = b->geoms[0]->d.near_block, best_cps = b->ctas_per_sm;
+  double best = 1e300;
+  int rc = SBIO_OK;
+  // targets per thread of the persistent far kernel (scalar and packed)
+  for (int tt : {1, 2, 4, 8, -2, -4, -8}) {
+    double ms = 0.0;
+    if ((rc = configure(tt, best_nb, best_cps)) || (rc = time_step(&ms))) break;
+    if (ms < best) {
+      best = ms;
+      best_tt = tt;
+    }
+  }
+  // near thread-group size, then the persistent grid (fewer far CTAs per SM
+  // leave slots for the near kernels of the other graph branch)
+  for (int nb : {64, 128}) {
+    double ms = 0.0;
+    if (rc || (rc = configure(best_tt, nb, best_cps)) || (rc = time_step(&ms))) break;
+    if (ms < best) {
+      best = ms;
+      best_nb = nb;
+    }
+  }
+  for (int cps : {4, 5, 6, 8}) {
+    double ms = 0.0;
+    if (rc || (rc = configure(best_tt, best_nb, cps)) || (rc = time_step(&ms))) break;
+    if (ms < best) {
+      best = ms;
+      best_cps = cps;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (rc) return rc;
+  if ((rc = configure(best_tt, best_nb, best_cps))) return rc;
+  if (far_tt) *far_tt = best_tt;
+  if (near_block) *near_block = best_nb;
+  if (ctas_per_sm) *ctas_per_sm = best_cps;
+  if (step_ms) *step_ms = best;
+  return SBIO_OK;
 }
 
 int sbio_batch_apply(sbio_batch* b, const double* const* sigma, const double* const* mu, double* const* S_out,

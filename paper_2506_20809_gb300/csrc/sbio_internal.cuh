@@ -42,6 +42,7 @@ struct DevGeom {
   int4* tiles = nullptr;         // far source tiles (particle, first node, count, -)
   double* inv = nullptr;         // 1/k for k >= 1; entry 0 holds the table length (sized per geometry)
   int near_grid_cap = 0;         // > 0: at most this many near CTAs (grid-stride), set while overlapping
+  int near_block = 128;          // threads per CTA of the S + D near kernel (64 or 128; tunable)
   float4* tgt32 = nullptr;       // N x 2: hi, lo parts of the global node position
   float4* cen32 = nullptr;       // M x 2: hi, lo parts of the centres
   // workspaces written by every apply

@@ -43,7 +43,7 @@ template <int P, int KIND>
 static void launch_near_pk(const DevGeom& d, int64_t first, int64_t count, const double* inv_tab, double* S,
                            double* D, cudaStream_t st) {
   if (count <= 0) return;
-  const int threads = 128;
+  const int threads = d.near_block == 64 ? 64 : 128;
   int64_t nb = (count + threads - 1) / threads;
   if (d.near_grid_cap > 0 && nb > d.near_grid_cap) nb = d.near_grid_cap;
   const unsigned blocks = (unsigned)nb;

@@ -146,6 +146,9 @@ _SIGS = {
                                   C.POINTER(C.c_int32)]),
     "sbio_batch_set_far_tt": (C.c_int, [_vp, C.c_int32]),
     "sbio_batch_apply": (C.c_int, [_vp, C.POINTER(_vp), C.POINTER(_vp), C.POINTER(_vp), C.POINTER(_vp), _vp]),
+    "sbio_batch_autotune": (C.c_int, [_vp, C.POINTER(_vp), C.POINTER(_vp), C.POINTER(_vp), C.POINTER(_vp), _vp,
+                                      C.POINTER(C.c_int32), C.POINTER(C.c_int32), C.POINTER(C.c_int32),
+                                      C.POINTER(C.c_double)]),
     "sbio_server_create": (C.c_int, [_vp, C.c_int32, C.c_size_t, C.POINTER(_vp)]),
     "sbio_server_submit": (C.c_int, [_vp, C.POINTER(sbio_request), C.POINTER(C.c_int64)]),
     "sbio_server_wait": (C.c_int, [_vp, C.c_int64, C.c_double, C.POINTER(C.c_int32), C.POINTER(C.c_double),
@@ -543,6 +546,15 @@ def sbio_batch_set_far_tt(b, tt):
 def sbio_batch_apply(b, sigmas, mus, S_outs, D_outs, stream=None):
     _check(_lib.sbio_batch_apply(b, _ptr_array(sigmas), _ptr_array(mus), _ptr_array(S_outs), _ptr_array(D_outs),
                                  _stream(stream)))
+
+
+def sbio_batch_autotune(b, sigmas, mus, S_outs, D_outs, stream=None):
+    """Library autotuner of a batch (far targets per thread, near CTA size,
+    persistent grid); returns (far_tt, near_block, ctas_per_sm, step_ms)."""
+    a, nb, c, ms = C.c_int32(), C.c_int32(), C.c_int32(), C.c_double()
+    _check(_lib.sbio_batch_autotune(b, _ptr_array(sigmas), _ptr_array(mus), _ptr_array(S_outs), _ptr_array(D_outs),
+                                    _stream(stream), C.byref(a), C.byref(nb), C.byref(c), C.byref(ms)))
+    return a.value, nb.value, c.value, ms.value
 
 
 def sbio_server_create(ctx, n_slots, mem_budget_bytes=0):

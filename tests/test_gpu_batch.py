@@ -117,3 +117,41 @@ def test_batch_against_oracle_sampled(S):
     for g in geoms:
         g.close()
     S.sbio_ctx_destroy(ctx)
+
+
+def test_batch_autotune_in_library(S):
+    """The library's batch autotuner picks a far shape, a near CTA size and a
+    persistent grid from its sets, and the batch still matches the
+    single-geometry FP64 path afterwards."""
+    ctx = S.sbio_ctx_create(0, 0)
+    specs = [(9, 8), (25, 12), (14, 16)]
+    susps = [I.rsa_suspension(M, 0.15, 700 + k, p, name=f"bt{k}") for k, (M, p) in enumerate(specs)]
+    geoms = [S.Geometry(ctx, s, precision=S.SBIO_MIXED) for s in susps]
+    sig, mu, ref = [], [], []
+    for s, g in zip(susps, geoms):
+        c = I.config_coefficients(s, 9)
+        sig.append(torch.from_numpy(c[0]).cuda())
+        mu.append(torch.from_numpy(c[1]).cuda())
+        So = torch.empty(g.N, dtype=torch.float64, device="cuda")
+        Do = torch.empty_like(So)
+        S.sbio_geom_set_precision(g.h, S.SBIO_FP64)
+        S.sbio_apply_laplace(g.h, sig[-1], mu[-1], So, Do)
+        S.sbio_geom_set_precision(g.h, S.SBIO_MIXED)
+        ref.append((So.cpu().numpy(), Do.cpu().numpy()))
+    outS = [torch.empty(g.N, dtype=torch.float64, device="cuda") for g in geoms]
+    outD = [torch.empty_like(o) for o in outS]
+    b = S.sbio_batch_create(ctx, geoms)
+    tt, nb, cps, ms = S.sbio_batch_autotune(b, sig, mu, outS, outD)
+    assert tt in (1, 2, 4, 8, -2, -4, -8) and nb in (64, 128) and cps in (4, 5, 6, 8) and ms > 0
+    assert S.sbio_batch_info(b)["far_tt"] == tt
+    for o in outS + outD:
+        o.fill_(float("nan"))
+    S.sbio_batch_apply(b, sig, mu, outS, outD)
+    torch.cuda.synchronize()
+    for k, (Sr, Dr) in enumerate(ref):
+        assert relerr(outS[k].cpu().numpy(), Sr) < TOLMIX
+        assert relerr(outD[k].cpu().numpy(), Dr) < TOLMIX
+    S.sbio_batch_destroy(b)
+    for g in geoms:
+        g.close()
+    S.sbio_ctx_destroy(ctx)
