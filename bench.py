@@ -764,6 +764,27 @@ def run_batch64(args, ws, rank, lrank):
     info = S.sbio_batch_info(b)
     # the same work as one apply per suspension, one after another (mixed)
     seq = _event_time(st, lambda: [S.sbio_apply_laplace(g.h, sig[k], mu[k], So[k], Do[k]) for k, g in enumerate(geoms)])
+    Sd = [o.clone() for o in So]
+    Dd = [o.clone() for o in Do]
+    # the same batch with the treecode far field on every suspension
+    for g in geoms:
+        S.sbio_geom_set_far_method(g.h, S.SBIO_FAR_TREE, 0.5, 16)
+    bt = S.sbio_batch_create(ctx, geoms)
+    for _ in range(3):
+        S.sbio_batch_apply(bt, sig, mu, So, Do)
+    tms = []
+    for _ in range(args.steps):
+        flush.zero_()
+        tms.append(_event_time(st, lambda: S.sbio_batch_apply(bt, sig, mu, So, Do)))
+    torch.cuda.synchronize()
+    terr = {"S": max(float((a - b_).abs().max() / b_.abs().max()) for a, b_ in zip(So, Sd)),
+            "D": max(float((a - b_).abs().max() / b_.abs().max()) for a, b_ in zip(Do, Dd))}
+    tree_line = {"applies_per_s": len(geoms) * 1e3 / statistics.mean(tms), "ms_per_step": statistics.mean(tms),
+                 "rel_err_vs_direct_mixed": terr,
+                 "far_method": "particle treecode per suspension (order 16, theta 0.5), on the graph's branches"}
+    S.sbio_batch_destroy(bt)
+    for g in geoms:
+        S.sbio_geom_set_far_method(g.h, S.SBIO_FAR_DIRECT)
     # plain FP64 form, one apply per suspension
     for g in geoms:
         S.sbio_geom_set_precision(g.h, S.SBIO_FP64)
@@ -788,6 +809,7 @@ def run_batch64(args, ws, rank, lrank):
                          "flop_per_pair": FAR_FLOP_PER_PAIR["SD"], "traffic": None},
             "sequential_mixed_ms": seq, "fp64_plain_ms": f64, "fp64_plain_applies_per_s": len(geoms) * 1e3 / f64,
             "speedup_vs_fp64_plain": f64 / mean, "speedup_vs_sequential_mixed": seq / mean,
+            "tree": tree_line,
             "gpu_launches": int(launches), "clocks": clk}
     S.sbio_batch_destroy(b)
     return line
@@ -1536,7 +1558,7 @@ def main():
             line["batched"] = _sub(run_batch64, ["metric", "value", "unit", "ms_per_step", "gpairs_per_s",
                                                  "roofline", "fp64_plain_ms", "fp64_plain_applies_per_s",
                                                  "speedup_vs_fp64_plain", "speedup_vs_sequential_mixed",
-                                                 "config"], args, ws, rank, lrank)
+                                                 "tree", "config"], args, ws, rank, lrank)
             line["served"] = _sub(run_serve, ["metric", "value", "unit", "sweep", "knee", "fp64_plain",
                                               "mixed_same_requests", "speedup_vs_fp64_plain", "config"],
                                   args, ws, rank, lrank)

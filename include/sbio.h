@@ -516,7 +516,10 @@ int sbio_solve_neumann(sbio_geom* g, const double* g_nodes, double tol, int32_t 
  * items from an atomic counter, longest first.  No data is shared between
  * suspensions (they are independent problems).  The graph is captured on the
  * first apply and replayed while the same buffers are passed; new buffers
- * trigger a re-capture (which synchronises `stream`). */
+ * trigger a re-capture (which synchronises `stream`).  A geometry whose far
+ * field is the treecode (sbio_geom_set_far_method, set before
+ * sbio_batch_create) has its treecode kernels in the graph on the near
+ * branches instead of items of the persistent kernel. */
 typedef struct sbio_batch sbio_batch;
 
 /* geoms: host array of n geometry handles, kept alive by the caller until

@@ -26,6 +26,7 @@ struct sbio_batch {
   int far_tt = 2;
   int grid = 0;
   int ctas_per_sm = 6;                 // persistent far grid = SMs x this
+  int n_tree = 0;                      // suspensions whose far field is the treecode
   int64_t far_pairs = 0;
   cudaStream_t sa = nullptr, sb = nullptr;
   cudaEvent_t ev_fork = nullptr, ev_synth = nullptr, ev_near = nullptr;
@@ -49,6 +50,7 @@ static int build_items(sbio_batch* b) {
   std::vector<Item> items;
   const int tt = b->far_tt < 0 ? -b->far_tt : b->far_tt;
   for (size_t s = 0; s < b->geoms.size(); ++s) {
+    if (b->geoms[s]->tree) continue;   // its far field runs as treecode launches in the graph
     const GeomHost& h = b->geoms[s]->h;
     const int nt = (int)h.tiles.size();
     const int64_t tb = (h.N + (int64_t)kFarTile * tt - 1) / ((int64_t)kFarTile * tt);
@@ -100,8 +102,13 @@ static int capture(sbio_batch* b, const double* const* sigma, const double* cons
   for (size_t s = 0; s < b->geoms.size() && !rc; ++s) rc = launch_synth(b->geoms[s], sigma[s], mu[s], S[s], D[s], true, b->sa);
   cudaEventRecord(b->ev_synth, b->sa);
   for (int k = 0; k < sbio_batch::kNearStreams; ++k) cudaStreamWaitEvent(b->sn[k], b->ev_synth, 0);
-  for (size_t s = 0; s < b->geoms.size() && !rc; ++s)
-    rc = launch_near(b->geoms[s], S[s], D[s], b->sn[s % sbio_batch::kNearStreams]);
+  // suspensions with a treecode far field run it on the near streams, beside
+  // the persistent direct kernel of the others, followed by their near field
+  for (size_t s = 0; s < b->geoms.size() && !rc; ++s) {
+    cudaStream_t ns = b->sn[s % sbio_batch::kNearStreams];
+    if (b->geoms[s]->tree) rc = launch_tree_far(b->geoms[s], S[s], D[s], ns);
+    if (!rc) rc = launch_near(b->geoms[s], S[s], D[s], ns);
+  }
   for (int k = 0; k < sbio_batch::kNearStreams; ++k) cudaEventRecord(b->ev_nj[k], b->sn[k]);
   cudaStreamWaitEvent(b->sb, b->ev_synth, 0);   // the fork stream joins too (unused otherwise)
   cudaEventRecord(b->ev_near, b->sb);
@@ -157,6 +164,7 @@ int sbio_batch_create(sbio_ctx* ctx, sbio_geom* const* geoms, int32_t n, sbio_ba
   for (int k = 0; k < n; ++k) {
     const sbio_geom* g = geoms[k];
     b->far_pairs += g->h.far_pairs;
+    if (g->tree) ++b->n_tree;
     b->h_desc[k] = FarDesc{g->d.tiles, g->d.src32, g->d.tgt32, g->d.cen32, g->d.skip_ptr, g->d.skip_idx, g->h.N,
                            nullptr, nullptr};
   }

@@ -103,3 +103,33 @@ def test_tree_single_operator_and_fp64_keep_direct(S, ctx):
     with pytest.raises(S.SbioError):
         S.sbio_geom_set_far_method(g.h, S.SBIO_FAR_TREE, 0.5, 10)
     g.close()
+
+
+def test_batch_with_treecode_suspensions(S, ctx):
+    """A batch mixing treecode and direct far fields (one CUDA graph) gives
+    each suspension's FP64 result within the treecode bound."""
+    specs = [(40, 8), (120, 12), (15, 16)]
+    susps = [I.rsa_suspension(M, 0.2, 800 + k, p, name=f"tb{k}") for k, (M, p) in enumerate(specs)]
+    geoms = [S.Geometry(ctx, s, precision=S.SBIO_MIXED) for s in susps]
+    sig, mu, ref = [], [], []
+    for s, g in zip(susps, geoms):
+        c = I.config_coefficients(s, 4)
+        sig.append(torch.from_numpy(c[0]).cuda())
+        mu.append(torch.from_numpy(c[1]).cuda())
+        S.sbio_geom_set_precision(g.h, S.SBIO_FP64)
+        ref.append(_apply(S, g, c))
+        S.sbio_geom_set_precision(g.h, S.SBIO_MIXED)
+    S.sbio_geom_set_far_method(geoms[0].h, S.SBIO_FAR_TREE, 0.5, 16)
+    S.sbio_geom_set_far_method(geoms[1].h, S.SBIO_FAR_TREE, 0.5, 16)
+    outS = [torch.full((g.N,), float("nan"), dtype=torch.float64, device="cuda") for g in geoms]
+    outD = [torch.full_like(o, float("nan")) for o in outS]
+    b = S.sbio_batch_create(ctx, geoms)
+    for _ in range(2):                                  # capture, then replay
+        S.sbio_batch_apply(b, sig, mu, outS, outD)
+        torch.cuda.synchronize()
+        for k, (Sr, Dr) in enumerate(ref):
+            assert OL.normwise_rel_err(outS[k].cpu().numpy(), Sr) < TREE_BOUND[(16, 0.5)]
+            assert OL.normwise_rel_err(outD[k].cpu().numpy(), Dr) < TREE_BOUND[(16, 0.5)]
+    S.sbio_batch_destroy(b)
+    for g in geoms:
+        g.close()
