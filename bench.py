@@ -1565,6 +1565,8 @@ def main():
             line["stokes100"] = _sub(run_stokes100, ["metric", "value", "unit", "ms_per_step", "e2e", "roofline",
                                                      "fp64_gpu_applies_per_s", "rel_err_vs_fp64_gpu", "config"],
                                      args, ws, rank, lrank)
+            line["lattice8"] = _sub(run_lattice8, ["metric", "value", "unit", "ms_per_step", "latency_ms", "e2e",
+                                                   "mixed_applies_per_s", "config"], args, ws, rank, lrank)
     if rank == 0 and line is not None:
         print(json.dumps(line), flush=True)
     if ws > 1:
