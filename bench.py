@@ -155,6 +155,7 @@ def parse():
     ap.add_argument("--slots", type=int, default=4, help="serve: concurrent request slots")
     ap.add_argument("--serve-seconds", type=float, default=20.0, help="serve: arrival window per rate (s)")
     ap.add_argument("--serve-pool", type=int, default=32, help="serve: distinct suspensions drawn for the stream")
+    ap.add_argument("--serve-direct", action="store_true", help="serve: direct far field for Laplace requests")
     ap.add_argument("--headline-only", action="store_true",
                     help="poly200: skip the batched, served and Stokes sub-objects")
     ap.add_argument("--sweep-M", default="200,500,1000,2000", help="far_sweep: particle counts")
@@ -862,7 +863,9 @@ def run_serve(args, ws, rank, lrank):
             return S.SBIO_OP_LAPLACE, sph, s.p, lap, (10, 2 * N)
         return S.SBIO_OP_STOKES, sph, s.p, sto, (10, N, 3)
 
-    def run_stream(arrivals, precision):
+    tree_flag = 0 if args.serve_direct else S.SBIO_REQ_TREE
+
+    def run_stream(arrivals, precision, flags=None):
         """arrivals: list of (t, k, op_is_laplace).  Returns latencies (ms)
         and the makespan (s) from the first arrival to the last result."""
         srv = S.sbio_server_create(ctx, args.slots, budget)
@@ -889,7 +892,8 @@ def run_serve(args, ws, rank, lrank):
             if delay > 0:
                 time.sleep(delay)
             out = np.empty(oshape)
-            t = S.sbio_server_submit(srv, op, sph, p, coef, out, 10, precision=precision)
+            fl = (tree_flag if flags is None else flags) if precision == S.SBIO_MIXED else 0
+            t = S.sbio_server_submit(srv, op, sph, p, coef, out, 10, precision=precision, flags=fl)
             done.put((t, (out, sph)))
         done.put(None)
         th.join()
@@ -914,6 +918,7 @@ def run_serve(args, ws, rank, lrank):
     eight = [(0.0, 900 + k, k % 2 == 0) for k in range(8)]
     lat64, mk64 = run_stream(eight, S.SBIO_FP64)
     latm, mkm = run_stream(eight, S.SBIO_MIXED)
+    latd, mkd = run_stream(eight, S.SBIO_MIXED, flags=0)
     line = {"metric": "served BIO applies/s (Poisson stream, 10 applies per request) and p50/p99 latency",
             "value": sat["applies_per_s"], "unit": "applies/s", "n_gpus": ws, "steps": len(rates),
             "warmup": 0, "ms_per_step": None, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -922,12 +927,15 @@ def run_serve(args, ws, rank, lrank):
                        "max_requests_per_rate": args.requests, "pool": [{"M": s.M, "p": s.p} for s in pool],
                        "request_geometry": "pool suspension moved by a seeded random rigid motion (new geometry "
                                            "built by the server inside every request's latency)",
-                       "mem_budget_bytes": budget, "ops": "Laplace S+D or Stokes single layer, probability 1/2"},
+                       "mem_budget_bytes": budget, "ops": "Laplace S+D or Stokes single layer, probability 1/2",
+                       "laplace_far_field": "direct sum" if args.serve_direct else
+                       "treecode (order 16, theta 0.5; SBIO_REQ_TREE), built inside each request"},
             "sweep": rows,
             "knee": {"flat_up_to_rate": max(flat), "p50_ms_at_lowest_rate": base,
                      "saturation_applies_per_s": sat["applies_per_s"]},
             "fp64_plain": {"requests": 8, "applies_per_s": 80 / mk64, "p50_ms": lat64[4]},
             "mixed_same_requests": {"requests": 8, "applies_per_s": 80 / mkm, "p50_ms": latm[4]},
+            "mixed_direct_far_same_requests": {"requests": 8, "applies_per_s": 80 / mkd, "p50_ms": latd[4]},
             "speedup_vs_fp64_plain": mk64 / mkm}
     S.sbio_ctx_destroy(ctx)
     return line
@@ -1560,7 +1568,8 @@ def main():
                                                  "speedup_vs_fp64_plain", "speedup_vs_sequential_mixed",
                                                  "tree", "config"], args, ws, rank, lrank)
             line["served"] = _sub(run_serve, ["metric", "value", "unit", "sweep", "knee", "fp64_plain",
-                                              "mixed_same_requests", "speedup_vs_fp64_plain", "config"],
+                                              "mixed_same_requests", "mixed_direct_far_same_requests",
+                                              "speedup_vs_fp64_plain", "config"],
                                   args, ws, rank, lrank)
             line["stokes100"] = _sub(run_stokes100, ["metric", "value", "unit", "ms_per_step", "e2e", "roofline",
                                                      "fp64_gpu_applies_per_s", "rel_err_vs_fp64_gpu", "config"],

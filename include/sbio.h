@@ -544,7 +544,9 @@ int sbio_batch_set_far_tt(sbio_batch* b, int32_t far_tt);
  * over the persistent far kernel's targets per thread (1, 2, 4, 8 scalar;
  * 2, 4, 8 packed), then the near kernels' thread-group size (64 or 128
  * threads per CTA, set on every geometry of the batch), then the persistent
- * grid (4, 5, 6 or 8 CTAs per SM), keeps the fastest and reports it (any
+ * grid (2, 3, 4, 5, 6 or 8 CTAs per SM; below 4 the near kernels of the
+ * graph's other branch find free SM slots beside it), keeps the fastest and
+ * reports it (any
  * output may be NULL; step_ms is its step time).  The buffers are those of
  * sbio_batch_apply and are overwritten.  Synchronises `stream`. */
 int sbio_batch_autotune(sbio_batch* b, const double* const* sigma, const double* const* mu, double* const* S_out,
@@ -574,12 +576,15 @@ typedef struct sbio_server sbio_server;
  * 2 x N each; Stokes: N x 3 each).  Both buffers stay owned by the caller and
  * must stay valid until sbio_server_wait returns for the ticket; sph is copied
  * at submission. */
+#define SBIO_REQ_TREE 1u  /* request flag: far field by the treecode (order 16, theta 0.5;
+                             mixed-precision Laplace requests, see sbio_geom_set_far_method) */
+
 typedef struct {
   int32_t op;
   int32_t n_applies;
   const sbio_spheroid* sph;
   int32_t M;
-  int32_t reserved;
+  int32_t flags;   /* 0 or SBIO_REQ_TREE */
   sbio_options opts;
   const double* coef_host;
   double* out_host;

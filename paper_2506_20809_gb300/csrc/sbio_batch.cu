@@ -292,7 +292,7 @@ int sbio_batch_autotune(sbio_batch* b, const double* const* sigma, const double*
       best_nb = nb;
     }
   }
-  for (int cps : {4, 5, 6, 8}) {
+  for (int cps : {2, 3, 4, 5, 6, 8}) {
     double ms = 0.0;
     if (rc || (rc = configure(best_tt, best_nb, cps)) || (rc = time_step(&ms))) break;
     if (ms < best) {

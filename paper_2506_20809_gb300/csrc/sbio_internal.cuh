@@ -193,6 +193,8 @@ void launch_far_tile_items(const DevGeom& d, const int2* groups, const int4* til
                            double* S, double* D, cudaStream_t st);
 // the treecode far field of one apply (sbio_tree.cu)
 int launch_tree_far(sbio_geom* g, double* S, double* D, cudaStream_t st);
+// build and attach a treecode (order, theta) with its uploads ordered on st
+int tree_attach_async(sbio_geom* g, int order, double theta, cudaStream_t st);
 
 // record phase event k (0..3) when timing is enabled
 inline void phase_mark(sbio_geom* g, int k, cudaStream_t st) {

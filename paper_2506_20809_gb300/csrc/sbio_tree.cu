@@ -90,6 +90,9 @@ struct TreeFar {
   int* d_mlist = nullptr;         // accepted node ids, group after group
   int4* d_mitems = nullptr;       // (group, first entry, end entry, 0)
   int n_mitems = 0;
+  // host images of the uploaded tables (kept until the tree is dropped, so
+  // that an upload queued on a stream may read them after the build returns)
+  std::vector<std::vector<char>> host_images;
   // phase events of the last apply while the geometry's timing is on:
   // leaf multipoles | translations + FP32 copy | direct part | evaluations
   cudaEvent_t ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
@@ -512,19 +515,24 @@ static int build_nodes(TreeFar& T, const GeomHost& h, int lo, int hi, int level)
   return id;
 }
 
+// Device copy of a host table, ordered on `st`; the host bytes are kept in
+// the tree until it is dropped.
 template <typename V>
-static int upload_vec(sbio_geom* g, V** dst, const std::vector<V>& v, const char* what) {
+static int upload_vec(sbio_geom* g, TreeFar& T, V** dst, const std::vector<V>& v, const char* what,
+                      cudaStream_t st) {
   if (v.empty()) {
     *dst = nullptr;
     return SBIO_OK;
   }
   int rc = dev_alloc(g, (void**)dst, v.size() * sizeof(V), what);
   if (rc) return rc;
-  SBIO_CUDA_TRY(cudaMemcpy(*dst, v.data(), v.size() * sizeof(V), cudaMemcpyHostToDevice));
+  T.host_images.emplace_back(reinterpret_cast<const char*>(v.data()),
+                             reinterpret_cast<const char*>(v.data()) + v.size() * sizeof(V));
+  SBIO_CUDA_TRY(cudaMemcpyAsync(*dst, T.host_images.back().data(), v.size() * sizeof(V), cudaMemcpyHostToDevice, st));
   return SBIO_OK;
 }
 
-static int build_tree(sbio_geom* g, TreeFar& T) {
+static int build_tree(sbio_geom* g, TreeFar& T, cudaStream_t st) {
   const GeomHost& h = g->h;
   const int M = h.M, G = h.G;
   T.perm.resize(M);
@@ -680,16 +688,16 @@ static int build_tree(sbio_geom* g, TreeFar& T) {
   }
   const int NM = tree_nm(T.order);
   int rc;
-  if ((rc = upload_vec(g, &T.d_geo, geo, "tree nodes"))) return rc;
-  if ((rc = upload_vec(g, &T.d_c32, c32, "tree centres"))) return rc;
-  if ((rc = upload_vec(g, &T.d_child, child, "tree children"))) return rc;
-  if ((rc = upload_vec(g, &T.d_leaf, leaf, "tree leaves"))) return rc;
-  if ((rc = upload_vec(g, &T.d_levels, lev, "tree levels"))) return rc;
-  if ((rc = upload_vec(g, &T.d_groups, groups, "tree target groups"))) return rc;
-  if ((rc = upload_vec(g, &T.d_tiles, dtiles, "tree direct tiles"))) return rc;
-  if ((rc = upload_vec(g, &T.d_ditems, ditems, "tree direct items"))) return rc;
-  if ((rc = upload_vec(g, &T.d_mlist, mlist, "tree multipole lists"))) return rc;
-  if ((rc = upload_vec(g, &T.d_mitems, mitems, "tree multipole items"))) return rc;
+  if ((rc = upload_vec(g, T, &T.d_geo, geo, "tree nodes", st))) return rc;
+  if ((rc = upload_vec(g, T, &T.d_c32, c32, "tree centres", st))) return rc;
+  if ((rc = upload_vec(g, T, &T.d_child, child, "tree children", st))) return rc;
+  if ((rc = upload_vec(g, T, &T.d_leaf, leaf, "tree leaves", st))) return rc;
+  if ((rc = upload_vec(g, T, &T.d_levels, lev, "tree levels", st))) return rc;
+  if ((rc = upload_vec(g, T, &T.d_groups, groups, "tree target groups", st))) return rc;
+  if ((rc = upload_vec(g, T, &T.d_tiles, dtiles, "tree direct tiles", st))) return rc;
+  if ((rc = upload_vec(g, T, &T.d_ditems, ditems, "tree direct items", st))) return rc;
+  if ((rc = upload_vec(g, T, &T.d_mlist, mlist, "tree multipole lists", st))) return rc;
+  if ((rc = upload_vec(g, T, &T.d_mitems, mitems, "tree multipole items", st))) return rc;
   T.n_ditems = (int)ditems.size();
   T.n_mitems = (int)mitems.size();
   if ((rc = dev_alloc(g, (void**)&T.d_M, sizeof(double2) * 2 * NM * (size_t)T.n_nodes, "tree multipoles"))) return rc;
@@ -728,6 +736,26 @@ static int tree_apply(sbio_geom* g, TreeFar& T, double* S, double* D, cudaStream
   }
   if (timed) cudaEventRecord(T.ev[4], st);
   SBIO_CUDA_TRY(cudaGetLastError());
+  return SBIO_OK;
+}
+
+// Builds and attaches a treecode to a geometry that has none, uploading its
+// lists in order on `st` without synchronising the device (used by the
+// serving engine, whose other slots keep running meanwhile).
+int tree_attach_async(sbio_geom* g, int order, double theta, cudaStream_t st) {
+  if (g->tree) return set_error(SBIO_EINVAL, "the geometry already has a treecode");
+  TreeFar* t = new TreeFar();
+  t->order = order;
+  t->theta = theta;
+  int rc = SBIO_OK;
+  for (cudaEvent_t& e : t->ev)
+    if (!rc && cudaEventCreate(&e) != cudaSuccess) rc = set_error(SBIO_ECUDA, "treecode event creation failed");
+  if (!rc) rc = build_tree(g, *t, st);
+  if (rc) {
+    delete t;
+    return rc;
+  }
+  g->tree = t;
   return SBIO_OK;
 }
 
@@ -770,7 +798,8 @@ int sbio_geom_set_far_method(sbio_geom* g, int32_t method, double theta, int32_t
   t->order = order;
   t->theta = theta;
   for (cudaEvent_t& e : t->ev) SBIO_CUDA_TRY(cudaEventCreate(&e));
-  const int rc = build_tree(g, *t);
+  int rc = build_tree(g, *t, nullptr);
+  if (!rc && cudaStreamSynchronize(nullptr) != cudaSuccess) rc = set_error(SBIO_ECUDA, "treecode upload failed");
   if (rc) {
     delete t;
     return rc;

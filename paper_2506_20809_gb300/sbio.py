@@ -48,7 +48,7 @@ class sbio_options(C.Structure):
 
 class sbio_request(C.Structure):
     _fields_ = [("op", C.c_int32), ("n_applies", C.c_int32), ("sph", C.c_void_p), ("M", C.c_int32),
-                ("reserved", C.c_int32), ("opts", sbio_options), ("coef_host", C.c_void_p),
+                ("flags", C.c_int32), ("opts", sbio_options), ("coef_host", C.c_void_p),
                 ("out_host", C.c_void_p)]
 
 
@@ -563,11 +563,15 @@ def sbio_server_create(ctx, n_slots, mem_budget_bytes=0):
     return h
 
 
+SBIO_REQ_TREE = 1
+
+
 def sbio_server_submit(srv, op, spheroids, p, coef_host, out_host, n_applies, near_factor=1.0,
-                       precision=SBIO_MIXED, n_phi=0):
+                       precision=SBIO_MIXED, n_phi=0, flags=0):
     """coef_host / out_host: C-contiguous float64 numpy arrays kept alive by
-    the caller until sbio_server_wait returns for the ticket."""
-    req = sbio_request(op, n_applies, C.cast(spheroids, C.c_void_p), len(spheroids), 0,
+    the caller until sbio_server_wait returns for the ticket.  flags:
+    SBIO_REQ_TREE for the treecode far field (mixed Laplace requests)."""
+    req = sbio_request(op, n_applies, C.cast(spheroids, C.c_void_p), len(spheroids), flags,
                        sbio_options(p, n_phi, near_factor, 1, precision), coef_host.ctypes.data,
                        out_host.ctypes.data)
     t = C.c_int64()

@@ -142,3 +142,45 @@ def test_served_results_against_oracle_sampled(S):
                 Ur = OSt.StokesOracle(og).apply(r["coef"][a], "method", targets=tg)
                 assert np.max(np.abs(out[a][tg] - Ur)) / np.max(np.abs(Ur)) < 1e-6
     S.sbio_ctx_destroy(ctx)
+
+
+def test_treecode_requests_alone_in_mix_and_against_direct(S):
+    """Laplace requests with the treecode flag: the same alone and in a mix
+    with direct and Stokes requests, and within the treecode bound of the
+    direct-field results."""
+    ctx = S.sbio_ctx_create(0, 0)
+    base = make_requests()
+    big = I.rsa_suspension(90, 0.2, 777, 8, name="srvtree")
+    nc = 81
+    rng = np.random.default_rng(77)
+    coef = np.ascontiguousarray(np.stack([I.coefficients(rng, 90, 8, 2).transpose(1, 0, 2) for _ in range(NAPPLY)]))
+    N = 90 * 9 * 18
+    reqs = base + [{"s": big, "p": 8, "op": "laplace", "coef": coef, "N": N, "nc": nc}]
+
+    def run_flags(rs, slots, tree_for):
+        srv = S.sbio_server_create(ctx, slots, 0)
+        outs, tickets, keep = [], [], []
+        for r in rs:
+            op = S.SBIO_OP_LAPLACE if r["op"] == "laplace" else S.SBIO_OP_STOKES
+            out = np.zeros((NAPPLY, 2 * r["N"]) if r["op"] == "laplace" else (NAPPLY, r["N"], 3))
+            sph = S.make_spheroids(r["s"].kind, r["s"].A, r["s"].C, r["s"].center, r["s"].quat)
+            keep.append(sph)
+            outs.append(out)
+            fl = S.SBIO_REQ_TREE if r is tree_for else 0
+            tickets.append(S.sbio_server_submit(srv, op, sph, r["p"], r["coef"], out, NAPPLY, flags=fl))
+        for t in tickets:
+            st, _, _ = S.sbio_server_wait(srv, t, 600.0)
+            assert st == 0
+        S.sbio_server_destroy(srv)
+        return outs
+
+    tree_req = reqs[-1]
+    alone = run_flags([tree_req], 1, tree_req)[0]
+    mixed = run_flags(reqs, 4, tree_req)[-1]
+    direct = run_flags([tree_req], 1, None)[0]
+    assert np.max(np.abs(alone - mixed)) <= 1e-12 * np.max(np.abs(alone))
+    for a in range(NAPPLY):
+        for part in (slice(0, N), slice(N, 2 * N)):
+            ref = direct[a][part]
+            assert np.max(np.abs(alone[a][part] - ref)) / np.max(np.abs(ref)) < 1e-6
+    S.sbio_ctx_destroy(ctx)

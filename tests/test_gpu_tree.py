@@ -133,3 +133,50 @@ def test_batch_with_treecode_suspensions(S, ctx):
     S.sbio_batch_destroy(b)
     for g in geoms:
         g.close()
+
+
+@pytest.mark.parametrize("M", [1, 2, 5])
+def test_tree_tiny_suspensions(S, ctx, M):
+    """One, two and five particles: the tree degenerates (a lone leaf, a
+    root over two leaves) and the far field must still match the direct sum
+    (with one particle there is none)."""
+    s = I.rsa_suspension(M, 0.1, 900 + M, 6, name="tiny")
+    c = I.config_coefficients(s, M)
+    g = S.Geometry(ctx, s, precision=S.SBIO_FP64)
+    S64, D64 = _apply(S, g, c)
+    S.sbio_geom_set_precision(g.h, S.SBIO_MIXED)
+    S.sbio_geom_set_far_method(g.h, S.SBIO_FAR_TREE, 0.5, 16)
+    info = S.sbio_geom_tree_info(g.h)
+    assert info["nodes"] == 2 * M - 1
+    assert info["m2p_source_pairs"] + info["direct_pairs"] == g.n_far
+    St, Dt = _apply(S, g, c)
+    assert OL.normwise_rel_err(St, S64) < TREE_BOUND[(16, 0.5)]
+    assert OL.normwise_rel_err(Dt, D64) < TREE_BOUND[(16, 0.5)]
+    g.close()
+
+
+def test_tree_settings_switch_and_rebuild(S, ctx):
+    """Changing order and opening angle rebuilds the lists, returning to the
+    direct sum restores its result exactly, and timing the phases works."""
+    s = I.rsa_suspension(80, 0.2, 910, 8, name="switch")
+    c = I.config_coefficients(s, 2)
+    g = S.Geometry(ctx, s, precision=S.SBIO_MIXED)
+    Sd, Dd = _apply(S, g, c)
+    S.sbio_geom_set_far_method(g.h, S.SBIO_FAR_TREE, 0.5, 16)
+    a = S.sbio_geom_tree_info(g.h)
+    S.sbio_geom_set_far_method(g.h, S.SBIO_FAR_TREE, 0.3, 12)
+    b = S.sbio_geom_tree_info(g.h)
+    assert b["direct_pairs"] > a["direct_pairs"]          # a smaller angle opens more nodes
+    assert b["m2p_source_pairs"] + b["direct_pairs"] == g.n_far
+    S.sbio_geom_enable_timing(g.h, True)
+    St, Dt = _apply(S, g, c)
+    ph = S.sbio_geom_tree_phase_times(g.h)
+    S.sbio_geom_enable_timing(g.h, False)
+    assert all(x >= 0 for x in ph) and sum(ph) > 0
+    assert OL.normwise_rel_err(St, Sd) < TREE_BOUND[(12, 0.5)]
+    S.sbio_geom_set_far_method(g.h, S.SBIO_FAR_DIRECT)
+    Sd2, Dd2 = _apply(S, g, c)
+    assert np.array_equal(Sd2, Sd) or OL.normwise_rel_err(Sd2, Sd) < 1e-13
+    with pytest.raises(S.SbioError):
+        S.sbio_geom_tree_info(g.h)
+    g.close()
