@@ -38,8 +38,9 @@
 //
 // Per apply: leaf multipoles from the FP32 sources (FP32 per warp with TwoSum
 // compensation for the orders n < 4 that carry most of the far field, FP64
-// across warps), translations up the tree in FP64 for the nodes the lists
-// read, conversion to FP32, then
+// across warps), translations up the tree for the nodes the lists read (FP64
+// for the orders n < 8, FP32 above, where a coefficient weighs at most
+// theta^n of the field), conversion to FP32, then
 // the direct part and the multipole evaluations (FP32, per-node sums folded
 // by TwoSum), each added atomically into the FP64 outputs.
 #include <algorithm>
@@ -287,6 +288,7 @@ __device__ __forceinline__ double2 signed_order(const double2* T, int n, int l) 
 // threads (one output per thread), so that the short top levels still use
 // many SMs: the translation is FP64 and the FP64 pipe is the bound.
 constexpr int kM2MThreads = 64;
+constexpr int kM2MExactOrders = 8;   // output orders n below this are translated in FP64
 
 template <int PF>
 __global__ void __launch_bounds__(kM2MThreads) tree_m2m_kernel(const int* __restrict__ ids,
@@ -316,19 +318,41 @@ __global__ void __launch_bounds__(kM2MThreads) tree_m2m_kernel(const int* __rest
   while (tree_idx(n + 1, 0) <= idx) ++n;
   const int m = idx - tree_idx(n, 0);
   double ar = 0.0, ai = 0.0;
-  for (int c = 0; c < 2; ++c) {
-    for (int kk = 0; kk <= n; ++kk) {
-      const int nn = n - kk;
-      // |m - l| <= nn and |l| <= kk
-      const int l_lo = max(-kk, m - nn), l_hi = min(kk, m + nn);
-      for (int l = l_lo; l <= l_hi; ++l) {
-        const double2 r = signed_order(Rb[c], kk, l);
-        const double2 v = signed_order(Mc[c][kind], nn, m - l);
-        // conj(r) * v
-        ar = fma(r.x, v.x, fma(r.y, v.y, ar));
-        ai = fma(r.x, v.y, fma(-r.y, v.x, ai));
+  if (n < kM2MExactOrders) {
+    for (int c = 0; c < 2; ++c) {
+      for (int kk = 0; kk <= n; ++kk) {
+        const int nn = n - kk;
+        // |m - l| <= nn and |l| <= kk
+        const int l_lo = max(-kk, m - nn), l_hi = min(kk, m + nn);
+        for (int l = l_lo; l <= l_hi; ++l) {
+          const double2 r = signed_order(Rb[c], kk, l);
+          const double2 v = signed_order(Mc[c][kind], nn, m - l);
+          // conj(r) * v
+          ar = fma(r.x, v.x, fma(r.y, v.y, ar));
+          ai = fma(r.x, v.y, fma(-r.y, v.x, ai));
+        }
       }
     }
+  } else {
+    // orders n >= kM2MExactOrders hold most of the terms but weigh at most
+    // theta^n of the node's field at any accepted target: FP32 products and
+    // sums (their rounding is below 1e-9 of the field) at 64x the FP64 rate
+    float fr = 0.f, fi = 0.f;
+    for (int c = 0; c < 2; ++c) {
+      for (int kk = 0; kk <= n; ++kk) {
+        const int nn = n - kk;
+        const int l_lo = max(-kk, m - nn), l_hi = min(kk, m + nn);
+        for (int l = l_lo; l <= l_hi; ++l) {
+          const double2 r = signed_order(Rb[c], kk, l);
+          const double2 v = signed_order(Mc[c][kind], nn, m - l);
+          const float rx = (float)r.x, ry = (float)r.y, vx = (float)v.x, vy = (float)v.y;
+          fr = fmaf(rx, vx, fmaf(ry, vy, fr));
+          fi = fmaf(rx, vy, fmaf(-ry, vx, fi));
+        }
+      }
+    }
+    ar = fr;
+    ai = fi;
   }
   Mt[((int64_t)node * 2 + kind) * NM + idx] = make_double2(ar, ai);
 }
