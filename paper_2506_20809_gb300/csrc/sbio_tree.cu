@@ -253,28 +253,6 @@ __global__ void __launch_bounds__(128) tree_p2m_kernel(int G, const float4* __re
   }
 }
 
-// R_k^l(b), l >= 0, k <= PF, in FP64 (serial; one thread)
-template <int PF>
-__device__ void regular_harmonics(double x, double y, double z, double2* R) {
-  const double r2 = x * x + y * y + z * z;
-  double mr = 1.0, mi = 0.0;
-  for (int m = 0; m <= PF; ++m) {
-    if (m > 0) {
-      const double s = -0.5 / m;
-      const double tr = s * (x * mr - y * mi), ti = s * (x * mi + y * mr);
-      mr = tr;
-      mi = ti;
-    }
-    R[tree_idx(m, m)] = make_double2(mr, mi);
-    if (m + 1 <= PF) R[tree_idx(m + 1, m)] = make_double2(z * mr, z * mi);
-    for (int n = m + 2; n <= PF; ++n) {
-      const double f = 1.0 / ((double)(n - m) * (n + m));
-      const double2 a = R[tree_idx(n - 1, m)], b = R[tree_idx(n - 2, m)];
-      R[tree_idx(n, m)] = make_double2(((2 * n - 1) * z * a.x - r2 * b.x) * f, ((2 * n - 1) * z * a.y - r2 * b.y) * f);
-    }
-  }
-}
-
 // value of a stored (n, m >= 0) table at order l of either sign, for tables
 // of real sources: T_n^{-l} = (-1)^l conj(T_n^l)
 __device__ __forceinline__ double2 signed_order(const double2* T, int n, int l) {
@@ -300,11 +278,37 @@ __global__ void __launch_bounds__(kM2MThreads) tree_m2m_kernel(const int* __rest
   __shared__ double2 Mc[2][2][NM];
   const int node = ids[blockIdx.x];
   const int ch0 = child[node * 2 + 0], ch1 = child[node * 2 + 1];
-  if (threadIdx.x == 0 || threadIdx.x == 32) {
-    const int k = threadIdx.x == 0 ? 0 : 1;
-    const int c = k ? ch1 : ch0;
-    regular_harmonics<PF>(geo[c * 4 + 0] - geo[node * 4 + 0], geo[c * 4 + 1] - geo[node * 4 + 1],
-                          geo[c * 4 + 2] - geo[node * 4 + 2], Rb[k]);
+  // R_k^l of the two child offsets, one column l per thread (lanes 0..PF of
+  // warp 0 for the first child, of warp 1 for the second): the FP64 pipe
+  // issues at 1/64 of the FP32 rate, so a serial recurrence by one thread
+  // would set the time of the whole level
+  {
+    const int k = threadIdx.x >> 5, l = threadIdx.x & 31;
+    if (l <= PF) {
+      const int c = k ? ch1 : ch0;
+      const double x = geo[c * 4 + 0] - geo[node * 4 + 0], y = geo[c * 4 + 1] - geo[node * 4 + 1],
+                   z = geo[c * 4 + 2] - geo[node * 4 + 2];
+      const double r2 = x * x + y * y + z * z;
+      double mr = 1.0, mi = 0.0;   // R_l^l = (-(x + i y) / 2)^l / l!
+      for (int q = 1; q <= l; ++q) {
+        const double sc = -0.5 / q;
+        const double tr = sc * (x * mr - y * mi), ti = sc * (x * mi + y * mr);
+        mr = tr;
+        mi = ti;
+      }
+      double2* R = Rb[k];
+      R[tree_idx(l, l)] = make_double2(mr, mi);
+      double ar = mr, ai = mi, br = 0.0, bi = 0.0;   // R_{n-1}^l, R_{n-2}^l
+      for (int n = l + 1; n <= PF; ++n) {
+        const double f = 1.0 / ((double)(n - l) * (n + l));
+        const double cr = ((2 * n - 1) * z * ar - r2 * br) * f, ci = ((2 * n - 1) * z * ai - r2 * bi) * f;
+        R[tree_idx(n, l)] = make_double2(cr, ci);
+        br = ar;
+        bi = ai;
+        ar = cr;
+        ai = ci;
+      }
+    }
   }
   for (int k = threadIdx.x; k < 4 * NM; k += blockDim.x) {
     const int c = k / (2 * NM), rest = k - c * 2 * NM;
