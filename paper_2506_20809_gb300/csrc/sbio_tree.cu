@@ -261,6 +261,12 @@ __device__ __forceinline__ double2 signed_order(const double2* T, int n, int l) 
   return (l & 1) ? make_double2(-v.x, v.y) : make_double2(v.x, -v.y);
 }
 
+__device__ __forceinline__ float2 signed_order32(const float2* T, int n, int l) {
+  if (l >= 0) return T[tree_idx(n, l)];
+  const float2 v = T[tree_idx(n, -l)];
+  return (l & 1) ? make_float2(-v.x, v.y) : make_float2(v.x, -v.y);
+}
+
 // One tree level: each internal node's multipoles from its two children's.
 // The 2 NM outputs of a node are spread over gridDim.y CTAs of kM2MThreads
 // threads (one output per thread), so that the short top levels still use
@@ -276,6 +282,8 @@ __global__ void __launch_bounds__(kM2MThreads) tree_m2m_kernel(const int* __rest
   constexpr int NM = tree_nm(PF);
   __shared__ double2 Rb[2][NM];
   __shared__ double2 Mc[2][2][NM];
+  __shared__ float2 Rb32[2][NM];       // FP32 copies for the high orders (converted once:
+  __shared__ float2 Mc32[2][2][NM];    // double-to-float conversions run at the FP64 rate)
   const int node = ids[blockIdx.x];
   const int ch0 = child[node * 2 + 0], ch1 = child[node * 2 + 1];
   // R_k^l of the two child offsets, one column l per thread (lanes 0..PF of
@@ -312,7 +320,14 @@ __global__ void __launch_bounds__(kM2MThreads) tree_m2m_kernel(const int* __rest
   }
   for (int k = threadIdx.x; k < 4 * NM; k += blockDim.x) {
     const int c = k / (2 * NM), rest = k - c * 2 * NM;
-    Mc[c][rest / NM][rest % NM] = Mt[((int64_t)(c ? ch1 : ch0) * 2 + rest / NM) * NM + rest % NM];
+    const double2 v = Mt[((int64_t)(c ? ch1 : ch0) * 2 + rest / NM) * NM + rest % NM];
+    Mc[c][rest / NM][rest % NM] = v;
+    Mc32[c][rest / NM][rest % NM] = make_float2((float)v.x, (float)v.y);
+  }
+  __syncthreads();
+  for (int k = threadIdx.x; k < 2 * NM; k += blockDim.x) {
+    const double2 v = Rb[k / NM][k % NM];
+    Rb32[k / NM][k % NM] = make_float2((float)v.x, (float)v.y);
   }
   __syncthreads();
   const int k = blockIdx.y * blockDim.x + threadIdx.x;
@@ -347,11 +362,10 @@ __global__ void __launch_bounds__(kM2MThreads) tree_m2m_kernel(const int* __rest
         const int nn = n - kk;
         const int l_lo = max(-kk, m - nn), l_hi = min(kk, m + nn);
         for (int l = l_lo; l <= l_hi; ++l) {
-          const double2 r = signed_order(Rb[c], kk, l);
-          const double2 v = signed_order(Mc[c][kind], nn, m - l);
-          const float rx = (float)r.x, ry = (float)r.y, vx = (float)v.x, vy = (float)v.y;
-          fr = fmaf(rx, vx, fmaf(ry, vy, fr));
-          fi = fmaf(rx, vy, fmaf(-ry, vx, fi));
+          const float2 r = signed_order32(Rb32[c], kk, l);
+          const float2 v = signed_order32(Mc32[c][kind], nn, m - l);
+          fr = fmaf(r.x, v.x, fmaf(r.y, v.y, fr));
+          fi = fmaf(r.x, v.y, fmaf(-r.y, v.x, fi));
         }
       }
     }
