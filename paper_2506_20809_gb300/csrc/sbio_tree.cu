@@ -113,16 +113,18 @@ __host__ __device__ inline int tree_idx(int n, int m) { return n * (n + 1) / 2 +
 // ---------------------------------------------------------------------------
 
 // Leaf multipoles about each particle's centre from its nodes' FP32 sources
-// (y - c, q), (d, 0).  One CTA (4 warps) per particle; lane m of a warp owns
+// (y - c, q), (d, 0).  One CTA (8 warps) per particle; lane m of a warp owns
 // column m of the harmonics and all warps step through n together, so the
 // dipole terms can take R_{n-1}^{m+-1} from the neighbouring lanes.
+constexpr int kP2MWarps = 8;
+
 template <int PF>
-__global__ void __launch_bounds__(128) tree_p2m_kernel(int G, const float4* __restrict__ src32,
+__global__ void __launch_bounds__(32 * kP2MWarps) tree_p2m_kernel(int G, const float4* __restrict__ src32,
                                                        const int* __restrict__ leaf, double2* __restrict__ Mout) {
   constexpr int NM = tree_nm(PF);
   constexpr int NC = 4;   // orders n < NC carry TwoSum compensation (they dominate the far field)
-  __shared__ float red[4][32][PF + 1][4];
-  __shared__ float redc[4][32][NC][4];
+  __shared__ float red[kP2MWarps][PF + 1][PF + 1][4];   // [warp][column m][order n]
+  __shared__ float redc[kP2MWarps][PF + 1][NC][4];
   const int i = blockIdx.x;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int m = lane;
@@ -132,7 +134,7 @@ __global__ void __launch_bounds__(128) tree_p2m_kernel(int G, const float4* __re
   for (int n = 0; n <= PF; ++n) aSr[n] = aSi[n] = aDr[n] = aDi[n] = 0.f;
 #pragma unroll
   for (int n = 0; n < NC; ++n) cSr[n] = cSi[n] = cDr[n] = cDi[n] = 0.f;
-  for (int j = warp; j < G; j += 4) {
+  for (int j = warp; j < G; j += kP2MWarps) {
     const float4 A = src32[((int64_t)i * G + j) * 2 + 0];
     const float4 B = src32[((int64_t)i * G + j) * 2 + 1];
     const float x = A.x, y = A.y, z = A.z, q = A.w;
@@ -214,19 +216,21 @@ __global__ void __launch_bounds__(128) tree_p2m_kernel(int G, const float4* __re
       r1i = ci;
     }
   }
+  if (lane <= PF) {
 #pragma unroll
-  for (int n = 0; n <= PF; ++n) {
-    red[warp][lane][n][0] = aSr[n];
-    red[warp][lane][n][1] = aSi[n];
-    red[warp][lane][n][2] = aDr[n];
-    red[warp][lane][n][3] = aDi[n];
-  }
+    for (int n = 0; n <= PF; ++n) {
+      red[warp][lane][n][0] = aSr[n];
+      red[warp][lane][n][1] = aSi[n];
+      red[warp][lane][n][2] = aDr[n];
+      red[warp][lane][n][3] = aDi[n];
+    }
 #pragma unroll
-  for (int n = 0; n < NC; ++n) {
-    redc[warp][lane][n][0] = cSr[n];
-    redc[warp][lane][n][1] = cSi[n];
-    redc[warp][lane][n][2] = cDr[n];
-    redc[warp][lane][n][3] = cDi[n];
+    for (int n = 0; n < NC; ++n) {
+      redc[warp][lane][n][0] = cSr[n];
+      redc[warp][lane][n][1] = cSi[n];
+      redc[warp][lane][n][2] = cDr[n];
+      redc[warp][lane][n][3] = cDi[n];
+    }
   }
   __syncthreads();
   const int node = leaf[i];
@@ -236,7 +240,7 @@ __global__ void __launch_bounds__(128) tree_p2m_kernel(int G, const float4* __re
     const int mm = k - tree_idx(n, 0);
     double sr = 0, si = 0, er = 0, ei = 0;
 #pragma unroll
-    for (int w = 0; w < 4; ++w) {
+    for (int w = 0; w < kP2MWarps; ++w) {
       sr += red[w][mm][n][0];
       si += red[w][mm][n][1];
       er += red[w][mm][n][2];
@@ -755,7 +759,7 @@ static int tree_apply(sbio_geom* g, TreeFar& T, double* S, double* D, cudaStream
   constexpr int NM = tree_nm(PF);
   const bool timed = g->timing && T.ev[0];
   if (timed) cudaEventRecord(T.ev[0], st);
-  tree_p2m_kernel<PF><<<h.M, 128, 0, st>>>(h.G, d.src32, T.d_leaf, T.d_M);
+  tree_p2m_kernel<PF><<<h.M, 32 * kP2MWarps, 0, st>>>(h.G, d.src32, T.d_leaf, T.d_M);
   count_launch();
   if (timed) cudaEventRecord(T.ev[1], st);
   for (size_t l = 0; l + 1 < T.level_off.size(); ++l) {
