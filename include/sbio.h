@@ -352,8 +352,12 @@ int sbio_geom_autotune_stokes(sbio_geom* g, void* stream, int32_t* far_tt, int32
 /* ---- far field by a particle treecode -----------------------------------
  * The paper evaluates the far field with an FMM (Sec. 4.1 "Far-field"); past
  * a few hundred particles the O(N^2) direct sum here grows too slow, and a
- * treecode can replace it for mixed-precision S + D applies at the nodes
- * (sbio_apply_laplace / _parts / _host with both operators): a binary tree
+ * treecode can replace it for mixed-precision applies at the nodes of the
+ * Laplace S + D (sbio_apply_laplace / _parts / _host with both operators) and
+ * of the Stokes single layer (sbio_apply_stokes_sl, its Stokeslet written as
+ * 8 pi u_i = S[F_i] + (x - c)_i D[F] - D[(y - c)_i F] with F = w f, i.e.
+ * four charge and four dipole channels about each node's centre c): a binary
+ * tree
  * over the particles, solid-harmonic multipoles of order `order` (8, 12 or
  * 16) of every node's sources (charges q = w sigma for S, dipoles
  * d = w mu nu for D), accepted for a group of 256 consecutive targets when
@@ -364,7 +368,8 @@ int sbio_geom_autotune_stokes(sbio_geom* g, void* stream, int32_t* far_tt, int32
  * the truncation of the expansions, about (theta)^(order+1) relative per
  * node.  SBIO_FAR_TREE builds the tree and lists on the host (synchronises
  * the device); SBIO_FAR_DIRECT (theta, order ignored) returns to the direct
- * sum.  FP64 geometries and the other operators keep the direct sum.
+ * sum.  FP64 geometries, evaluations at points and the other operators keep
+ * the direct sum.
  * Errors: SBIO_EINVAL (method, theta outside (0.05, 1), order), SBIO_ENOMEM,
  * SBIO_ECUDA. */
 #define SBIO_FAR_DIRECT 0
@@ -577,7 +582,7 @@ typedef struct sbio_server sbio_server;
  * must stay valid until sbio_server_wait returns for the ticket; sph is copied
  * at submission. */
 #define SBIO_REQ_TREE 1u  /* request flag: far field by the treecode (order 16, theta 0.5;
-                             mixed-precision Laplace requests, see sbio_geom_set_far_method) */
+                             mixed-precision requests, see sbio_geom_set_far_method) */
 
 typedef struct {
   int32_t op;

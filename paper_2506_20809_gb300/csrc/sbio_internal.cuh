@@ -195,6 +195,11 @@ void launch_far_tile_items(const DevGeom& d, const int2* groups, const int4* til
 int launch_tree_far(sbio_geom* g, double* S, double* D, cudaStream_t st);
 // build and attach a treecode (order, theta) with its uploads ordered on st
 int tree_attach_async(sbio_geom* g, int order, double theta, cudaStream_t st);
+// the Stokes single layer's far field by the treecode (sbio_tree.cu) and its
+// direct part (sbio_stokes.cu)
+int launch_tree_stokes_far(sbio_geom* g, double* u, cudaStream_t st);
+void launch_stokes_far_tile_items(const DevGeom& d, const int2* groups, const int4* tiles, const int4* items,
+                                  int n_items, double* u, cudaStream_t st);
 
 // record phase event k (0..3) when timing is enabled
 inline void phase_mark(sbio_geom* g, int k, cudaStream_t st) {

@@ -931,7 +931,10 @@ int sbio_geom_autotune_stokes(sbio_geom* g, void* stream, int32_t* far_tt, int32
   // while the whole-apply timings of the tuner differ by less than its noise)
   ops.min_cap = 4;
   double best = 0.0;
+  TreeFar* tree = g->tree;   // tune the direct Stokeslet kernel's shapes
+  g->tree = nullptr;
   rc = tune_launch_shape(g, ops, d.host_out, st, &best);
+  g->tree = tree;
   if (rc) return rc;
   if (far_tt) *far_tt = h.st_far_tt;
   if (far_splits) *far_splits = h.st_far_splits;

@@ -74,8 +74,8 @@ static int run_job(sbio_server* s, Job* j, cudaStream_t st) {
   const int64_t N = g->h.N;
   const size_t nc = (size_t)(o.p + 1) * (o.p + 1) * r.M;
   const bool stokes = r.op == SBIO_OP_STOKES;
-  // the treecode far field for mixed Laplace requests that ask for it
-  if (!stokes && (r.flags & SBIO_REQ_TREE) && o.precision == SBIO_MIXED && r.M > 1) {
+  // the treecode far field for mixed requests that ask for it
+  if ((r.flags & SBIO_REQ_TREE) && o.precision == SBIO_MIXED && r.M > 1) {
     rc = tree_attach_async(g, 16, 0.5, st);
     if (rc) {
       geom_destroy_async(g, st);

@@ -281,23 +281,21 @@ __global__ void __launch_bounds__(kFarTile) stokes_far_fp64_kernel(const int4* _
 // the Laplace far kernel); PK computes two targets per f32x2 instruction.
 // PR also sums the pressure quadrature with the printed kernel
 // P = r / (4 pi |r|^3), which reuses the pair's f.r and 1/|r|: one more FMA.
+// One CTA: targets [t_first, min(N, t_first + kFarTile * TT)) against source
+// tiles [t_lo, t_hi) (the launch grid or a treecode group's tile list).
 template <int TT, bool PK, bool PR>
-__global__ void __launch_bounds__(kFarTile) stokes_far_mixed_kernel(const int4* __restrict__ tiles, int n_tiles,
-                                                                    const float4* __restrict__ src32,
-                                                                    const float4* __restrict__ tgt32,
-                                                                    const float4* __restrict__ cen32,
-                                                                    const int32_t* __restrict__ skip_ptr,
-                                                                    const int32_t* __restrict__ skip_idx, int64_t N,
-                                                                    double* __restrict__ u_out,
-                                                                    double* __restrict__ p_out) {
+__device__ __forceinline__ void stokes_far_block(int64_t t_first, int64_t N, int t_lo, int t_hi,
+                                                 const int4* __restrict__ tiles, const float4* __restrict__ src32,
+                                                 const float4* __restrict__ tgt32, const float4* __restrict__ cen32,
+                                                 const int32_t* __restrict__ skip_ptr,
+                                                 const int32_t* __restrict__ skip_idx, double* __restrict__ u_out,
+                                                 double* __restrict__ p_out) {
   constexpr int NA = PR ? 4 : 3;               // accumulated quantities per target
   __shared__ float4 sh[(PK ? 3 : 2) * kFarTile];
   __shared__ float acc[2 * NA * TT * kFarTile];   // per target: (hi, lo) of u_x, u_y, u_z (and p)
   __shared__ int cursor[2 * TT * kFarTile];
   const int tid = threadIdx.x;
-  const int per = (n_tiles + gridDim.y - 1) / gridDim.y;
-  const int t_lo = blockIdx.y * per, t_hi = min(n_tiles, t_lo + per);
-  const int64_t t0 = (int64_t)blockIdx.x * TT * kFarTile + tid;
+  const int64_t t0 = t_first + tid;
 #pragma unroll
   for (int q = 0; q < TT; ++q) {
     const int64_t t = t0 + (int64_t)q * kFarTile;
@@ -436,6 +434,42 @@ __global__ void __launch_bounds__(kFarTile) stokes_far_mixed_kernel(const int4* 
                               (double)acc[(2 * NA * q + 7) * kFarTile + tid]) * (2.0 * kInv8Pi));
     }
   }
+  __syncthreads();   // the shared arrays may be reused by a following block of the same CTA
+}
+
+template <int TT, bool PK, bool PR>
+__global__ void __launch_bounds__(kFarTile) stokes_far_mixed_kernel(const int4* __restrict__ tiles, int n_tiles,
+                                                                    const float4* __restrict__ src32,
+                                                                    const float4* __restrict__ tgt32,
+                                                                    const float4* __restrict__ cen32,
+                                                                    const int32_t* __restrict__ skip_ptr,
+                                                                    const int32_t* __restrict__ skip_idx, int64_t N,
+                                                                    double* __restrict__ u_out,
+                                                                    double* __restrict__ p_out) {
+  const int per = (n_tiles + gridDim.y - 1) / gridDim.y;
+  const int t_lo = blockIdx.y * per, t_hi = min(n_tiles, t_lo + per);
+  stokes_far_block<TT, PK, PR>((int64_t)blockIdx.x * TT * kFarTile, N, t_lo, t_hi, tiles, src32, tgt32, cen32,
+                               skip_ptr, skip_idx, u_out, p_out);
+}
+
+// Direct part of the Stokes treecode far field: one CTA per item (target
+// group [groups[g].x, groups[g].y), tile range of the group's tile list).
+__global__ void __launch_bounds__(kFarTile) stokes_far_tile_items_kernel(
+    const int4* __restrict__ items, const int2* __restrict__ groups, const int4* __restrict__ tiles,
+    const float4* __restrict__ src32, const float4* __restrict__ tgt32, const float4* __restrict__ cen32,
+    const int32_t* __restrict__ skip_ptr, const int32_t* __restrict__ skip_idx, double* __restrict__ u_out) {
+  const int4 w = items[blockIdx.x];
+  const int2 grp = groups[w.x];
+  stokes_far_block<2, true, false>(grp.x, grp.y, w.y, w.z, tiles, src32, tgt32, cen32, skip_ptr, skip_idx, u_out,
+                                   nullptr);
+}
+
+void launch_stokes_far_tile_items(const DevGeom& d, const int2* groups, const int4* tiles, const int4* items,
+                                  int n_items, double* u, cudaStream_t st) {
+  if (n_items <= 0) return;
+  stokes_far_tile_items_kernel<<<n_items, kFarTile, 0, st>>>(items, groups, tiles, d.st_src32, d.tgt32, d.cen32,
+                                                             d.skip_ptr, d.skip_idx, u);
+  count_launch();
 }
 
 template <int TT, bool PK>
@@ -484,6 +518,8 @@ int launch_stokes_far_on(const DevGeom& d, const GeomHost& h, int64_t NT, double
 }
 
 int launch_stokes_far(sbio_geom* g, double* u, cudaStream_t st) {
+  // the treecode replaces the direct Stokeslet sum for mixed applies at the nodes
+  if (g->tree && g->h.precision == SBIO_MIXED) return launch_tree_stokes_far(g, u, st);
   return launch_stokes_far_on(g->d, g->h, g->h.N, u, nullptr, st);
 }
 

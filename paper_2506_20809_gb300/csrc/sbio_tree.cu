@@ -84,6 +84,10 @@ struct TreeFar {
   std::vector<int> level_off;     // offsets into d_levels
   double2* d_M = nullptr;         // n_nodes x 2 x NM: FP64 multipoles (S, D)
   float2* d_M32 = nullptr;        // n_nodes x 2 x NM: FP32, m > 0 doubled
+  // Stokes single layer: 4 channel planes of n_nodes x 2 x NM (charges F_1,
+  // F_2, F_3, 0 with dipoles F, (y-c)_x F, (y-c)_y F, (y-c)_z F)
+  double2* d_SM = nullptr;
+  float2* d_SM32 = nullptr;
   int2* d_groups = nullptr;       // target range [first, end) of every group
   int4* d_tiles = nullptr;        // direct source tiles, group after group
   int4* d_ditems = nullptr;       // (group, first tile, end tile, 0)
@@ -118,7 +122,10 @@ __host__ __device__ inline int tree_idx(int n, int m) { return n * (n + 1) / 2 +
 // dipole terms can take R_{n-1}^{m+-1} from the neighbouring lanes.
 constexpr int kP2MWarps = 8;
 
-template <int PF>
+// SRC = 0: the Laplace sources (y - c, q), (d, 0).  SRC = 1..4: channel
+// SRC - 1 of the Stokes sources (y - c, F_1), (F_2, F_3, 0, 0), F = w f:
+// charges F_1, F_2, F_3, 0 and dipoles F, (y - c)_x F, (y - c)_y F, (y - c)_z F.
+template <int PF, int SRC>
 __global__ void __launch_bounds__(32 * kP2MWarps) tree_p2m_kernel(int G, const float4* __restrict__ src32,
                                                        const int* __restrict__ leaf, double2* __restrict__ Mout) {
   constexpr int NM = tree_nm(PF);
@@ -137,9 +144,22 @@ __global__ void __launch_bounds__(32 * kP2MWarps) tree_p2m_kernel(int G, const f
   for (int j = warp; j < G; j += kP2MWarps) {
     const float4 A = src32[((int64_t)i * G + j) * 2 + 0];
     const float4 B = src32[((int64_t)i * G + j) * 2 + 1];
-    const float x = A.x, y = A.y, z = A.z, q = A.w;
+    const float x = A.x, y = A.y, z = A.z;
+    float q, ddx, ddy, ddz;
+    if (SRC == 0) {
+      q = A.w;
+      ddx = B.x;
+      ddy = B.y;
+      ddz = B.z;
+    } else {
+      const float w = SRC == 1 ? 1.f : (SRC == 2 ? x : (SRC == 3 ? y : z));
+      q = SRC == 1 ? A.w : (SRC == 2 ? B.x : (SRC == 3 ? B.y : 0.f));
+      ddx = w * A.w;
+      ddy = w * B.x;
+      ddz = w * B.y;
+    }
     const float r2 = fmaf(z, z, fmaf(y, y, x * x));
-    const float dr = 0.5f * B.x, di = 0.5f * B.y, dz = B.z;   // delta = (d_x + i d_y) / 2
+    const float dr = 0.5f * ddx, di = 0.5f * ddy, dz = ddz;   // delta = (d_x + i d_y) / 2
     // R_m^m = (-(x + i y) / 2)^m / m!
     float mr = 1.f, mi = 0.f;
 #pragma unroll
@@ -278,11 +298,17 @@ __device__ __forceinline__ float2 signed_order32(const float2* T, int n, int l) 
 constexpr int kM2MThreads = 64;
 constexpr int kM2MExactOrders = 8;   // output orders n below this are translated in FP64
 
+// Several channel planes at once (blockIdx.z, planes `plane` double2 apart,
+// as the Stokes channels): a plane z >= 1 with `shifted` set carries dipoles
+// weighted by (y - c)_{z-1} of its own node's centre, so before translation
+// each child's dipole part gets (c_child - c_parent)_{z-1} times plane 0's
+// dipole part (the weight moves with the expansion centre).
 template <int PF>
 __global__ void __launch_bounds__(kM2MThreads) tree_m2m_kernel(const int* __restrict__ ids,
                                                                const int* __restrict__ child,
                                                                const double* __restrict__ geo,
-                                                               double2* __restrict__ Mt) {
+                                                               double2* __restrict__ Mbase, int64_t plane,
+                                                               int shifted) {
   constexpr int NM = tree_nm(PF);
   __shared__ double2 Rb[2][NM];
   __shared__ double2 Mc[2][2][NM];
@@ -290,6 +316,8 @@ __global__ void __launch_bounds__(kM2MThreads) tree_m2m_kernel(const int* __rest
   __shared__ float2 Mc32[2][2][NM];    // double-to-float conversions run at the FP64 rate)
   const int node = ids[blockIdx.x];
   const int ch0 = child[node * 2 + 0], ch1 = child[node * 2 + 1];
+  double2* __restrict__ Mt = Mbase + blockIdx.z * plane;
+  const int axis = (shifted && blockIdx.z > 0) ? (int)blockIdx.z - 1 : -1;
   // R_k^l of the two child offsets, one column l per thread (lanes 0..PF of
   // warp 0 for the first child, of warp 1 for the second): the FP64 pipe
   // issues at 1/64 of the FP32 rate, so a serial recurrence by one thread
@@ -324,7 +352,13 @@ __global__ void __launch_bounds__(kM2MThreads) tree_m2m_kernel(const int* __rest
   }
   for (int k = threadIdx.x; k < 4 * NM; k += blockDim.x) {
     const int c = k / (2 * NM), rest = k - c * 2 * NM;
-    const double2 v = Mt[((int64_t)(c ? ch1 : ch0) * 2 + rest / NM) * NM + rest % NM];
+    const int cn = c ? ch1 : ch0;
+    double2 v = Mt[((int64_t)cn * 2 + rest / NM) * NM + rest % NM];
+    if (axis >= 0 && rest >= NM) {
+      const double b = geo[cn * 4 + axis] - geo[node * 4 + axis];
+      const double2 v0 = Mbase[((int64_t)cn * 2 + 1) * NM + rest % NM];
+      v = make_double2(fma(b, v0.x, v.x), fma(b, v0.y, v.y));
+    }
     Mc[c][rest / NM][rest % NM] = v;
     Mc32[c][rest / NM][rest % NM] = make_float2((float)v.x, (float)v.y);
   }
@@ -504,6 +538,124 @@ __global__ void __launch_bounds__(kFarTile) tree_m2p_kernel(const int4* __restri
       atomicAdd(S_out + t[q], ((double)hS[q] + (double)lS[q]) * kInv4PiTree);
       atomicAdd(D_out + t[q], ((double)hD[q] + (double)lD[q]) * kInv4PiTree);
     }
+}
+
+// Stokes single layer from the four channel planes: per target
+//   8 pi u_i = S[F_i] + (x - c)_i D[F] - D[(y - c)_i F]
+// (the Stokeslet f/r + (r.f) r/r^3 written through Laplace charges and
+// dipoles about the node's centre c), two targets per thread packed in f32x2.
+template <int PF>
+__global__ void __launch_bounds__(kFarTile) tree_m2p_stokes_kernel(
+    const int4* __restrict__ items, const int2* __restrict__ groups, const int* __restrict__ mlist,
+    const float4* __restrict__ c32, const float2* __restrict__ M32, int64_t plane, const float4* __restrict__ tgt32,
+    double* __restrict__ u_out) {
+  constexpr int NM = tree_nm(PF);
+  constexpr double kInv8Pi = 0.039788735772973836;
+  __shared__ float4 cf[8 * NM];   // (plane z, kind k) block (2 z + k) of NM coefficients
+  __shared__ float4 cc[2];
+  const int4 it = items[blockIdx.x];
+  const int2 grp = groups[it.x];
+  const int64_t N = grp.y;
+  const int tid = threadIdx.x;
+  int64_t t[2];
+  float4 xh[2], xl[2];
+  float hU[2][3], lU[2][3];
+#pragma unroll
+  for (int q = 0; q < 2; ++q) {
+    t[q] = (int64_t)grp.x + q * kFarTile + tid;
+    xh[q] = xl[q] = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (t[q] < N) {
+      xh[q] = tgt32[t[q] * 2 + 0];
+      xl[q] = tgt32[t[q] * 2 + 1];
+    }
+#pragma unroll
+    for (int c = 0; c < 3; ++c) hU[q][c] = lU[q][c] = 0.f;
+  }
+  for (int e = it.y; e < it.z; ++e) {
+    const int node = mlist[e];
+    __syncthreads();
+    for (int k = tid; k < 8 * NM; k += kFarTile) {
+      const int blk = k / NM, idx = k - blk * NM;   // blk = 2 z + kind
+      const float2 v = M32[(blk >> 1) * plane + ((int64_t)node * 2 + (blk & 1)) * NM + idx];
+      cf[k] = make_float4(v.x, v.x, -v.y, -v.y);
+    }
+    if (tid < 2) cc[tid] = c32[node * 2 + tid];
+    __syncthreads();
+    const float4 ch = cc[0], cl = cc[1];
+    float Xr[2], Yr[2], Zr[2], Xs[2], Ys[2], Zs[2], I2[2], R0[2];
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+      Xr[q] = (xh[q].x - ch.x) + (xl[q].x - cl.x);
+      Yr[q] = (xh[q].y - ch.y) + (xl[q].y - cl.y);
+      Zr[q] = (xh[q].z - ch.z) + (xl[q].z - cl.z);
+      const float r2 = fmaf(Zr[q], Zr[q], fmaf(Yr[q], Yr[q], Xr[q] * Xr[q]));
+      const float ri = rsqrt_f32(r2);
+      I2[q] = ri * ri;
+      Xs[q] = Xr[q] * I2[q];
+      Ys[q] = Yr[q] * I2[q];
+      Zs[q] = Zr[q] * I2[q];
+      R0[q] = ri;
+    }
+    const float2 xs = make_float2(Xs[0], Xs[1]), ys = make_float2(Ys[0], Ys[1]);
+    const float2 zs = make_float2(Zs[0], Zs[1]), ir2 = make_float2(I2[0], I2[1]);
+    float2 Ir = make_float2(R0[0], R0[1]), Ii = make_float2(0.f, 0.f);
+    float2 acc[8];
+#pragma unroll
+    for (int b = 0; b < 8; ++b) acc[b] = make_float2(0.f, 0.f);
+#pragma unroll
+    for (int m = 0; m <= PF; ++m) {
+      if (m > 0) {
+        const float2 s2 = make_float2(-(float)(2 * m - 1), -(float)(2 * m - 1));
+        const float2 wr = __fmul2_rn(s2, xs), wi = __fmul2_rn(s2, ys);
+        const float2 tr = __ffma2_rn(wr, Ir, __fmul2_rn(make_float2(-wi.x, -wi.y), Ii));
+        const float2 ti = __ffma2_rn(wr, Ii, __fmul2_rn(wi, Ir));
+        Ir = tr;
+        Ii = ti;
+      }
+#pragma unroll
+      for (int b = 0; b < 8; ++b) {
+        const float4 a = cf[b * NM + tree_idx(m, m)];
+        acc[b] = __ffma2_rn(make_float2(a.x, a.y), Ir, __ffma2_rn(make_float2(a.z, a.w), Ii, acc[b]));
+      }
+      float2 ar = Ir, ai = Ii, br = make_float2(0.f, 0.f), bi = make_float2(0.f, 0.f);
+#pragma unroll
+      for (int n = m + 1; n <= PF; ++n) {
+        const float kz = (float)(2 * n - 1), kb = -(float)((n - 1 - m) * (n - 1 + m));
+        const float2 u = __fmul2_rn(make_float2(kz, kz), zs), v = __fmul2_rn(make_float2(kb, kb), ir2);
+        const float2 cr = __ffma2_rn(u, ar, __fmul2_rn(v, br)), ci = __ffma2_rn(u, ai, __fmul2_rn(v, bi));
+#pragma unroll
+        for (int b = 0; b < 8; ++b) {
+          const float4 a = cf[b * NM + tree_idx(n, m)];
+          acc[b] = __ffma2_rn(make_float2(a.x, a.y), cr, __ffma2_rn(make_float2(a.z, a.w), ci, acc[b]));
+        }
+        br = ar;
+        bi = ai;
+        ar = cr;
+        ai = ci;
+      }
+    }
+    // acc[2 z] = S of plane z (charges F_1, F_2, F_3, 0), acc[2 z + 1] = D of plane z
+    const float Sx[2] = {acc[0].x, acc[0].y}, Sy[2] = {acc[2].x, acc[2].y}, Sz[2] = {acc[4].x, acc[4].y};
+    const float D0[2] = {acc[1].x, acc[1].y}, Dx[2] = {acc[3].x, acc[3].y}, Dy[2] = {acc[5].x, acc[5].y},
+                Dz[2] = {acc[7].x, acc[7].y};
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+      const float uv[3] = {fmaf(Xr[q], D0[q], Sx[q] - Dx[q]), fmaf(Yr[q], D0[q], Sy[q] - Dy[q]),
+                           fmaf(Zr[q], D0[q], Sz[q] - Dz[q])};
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        float s2, e2;
+        two_sum_f32(hU[q][c], uv[c], s2, e2);
+        hU[q][c] = s2;
+        lU[q][c] += e2;
+      }
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < 2; ++q)
+    if (t[q] < N)
+#pragma unroll
+      for (int c = 0; c < 3; ++c) atomicAdd(u_out + t[q] * 3 + c, ((double)hU[q][c] + (double)lU[q][c]) * kInv8Pi);
 }
 
 // ---------------------------------------------------------------------------
@@ -749,6 +901,11 @@ static int build_tree(sbio_geom* g, TreeFar& T, cudaStream_t st) {
   if ((rc = dev_alloc(g, (void**)&T.d_M, sizeof(double2) * 2 * NM * (size_t)T.n_nodes, "tree multipoles"))) return rc;
   if ((rc = dev_alloc(g, (void**)&T.d_M32, sizeof(float2) * 2 * NM * (size_t)T.n_nodes, "tree multipoles (FP32)")))
     return rc;
+  if ((rc = dev_alloc(g, (void**)&T.d_SM, sizeof(double2) * 8 * NM * (size_t)T.n_nodes, "tree Stokes multipoles")))
+    return rc;
+  if ((rc = dev_alloc(g, (void**)&T.d_SM32, sizeof(float2) * 8 * NM * (size_t)T.n_nodes,
+                      "tree Stokes multipoles (FP32)")))
+    return rc;
   return SBIO_OK;
 }
 
@@ -759,14 +916,14 @@ static int tree_apply(sbio_geom* g, TreeFar& T, double* S, double* D, cudaStream
   constexpr int NM = tree_nm(PF);
   const bool timed = g->timing && T.ev[0];
   if (timed) cudaEventRecord(T.ev[0], st);
-  tree_p2m_kernel<PF><<<h.M, 32 * kP2MWarps, 0, st>>>(h.G, d.src32, T.d_leaf, T.d_M);
+  tree_p2m_kernel<PF, 0><<<h.M, 32 * kP2MWarps, 0, st>>>(h.G, d.src32, T.d_leaf, T.d_M);
   count_launch();
   if (timed) cudaEventRecord(T.ev[1], st);
   for (size_t l = 0; l + 1 < T.level_off.size(); ++l) {
     const int n = T.level_off[l + 1] - T.level_off[l];
     if (n <= 0) continue;
     const dim3 grid((unsigned)n, (unsigned)((2 * NM + kM2MThreads - 1) / kM2MThreads));
-    tree_m2m_kernel<PF><<<grid, kM2MThreads, 0, st>>>(T.d_levels + T.level_off[l], T.d_child, T.d_geo, T.d_M);
+    tree_m2m_kernel<PF><<<grid, kM2MThreads, 0, st>>>(T.d_levels + T.level_off[l], T.d_child, T.d_geo, T.d_M, 0, 0);
     count_launch();
   }
   const int64_t total = (int64_t)T.n_nodes * 2 * NM;
@@ -803,6 +960,54 @@ int tree_attach_async(sbio_geom* g, int order, double theta, cudaStream_t st) {
   }
   g->tree = t;
   return SBIO_OK;
+}
+
+template <int PF>
+static int tree_apply_stokes(sbio_geom* g, TreeFar& T, double* u, cudaStream_t st) {
+  const GeomHost& h = g->h;
+  const DevGeom& d = g->d;
+  constexpr int NM = tree_nm(PF);
+  const int64_t plane = (int64_t)T.n_nodes * 2 * NM;
+  const bool timed = g->timing && T.ev[0];
+  if (timed) cudaEventRecord(T.ev[0], st);
+  tree_p2m_kernel<PF, 1><<<h.M, 32 * kP2MWarps, 0, st>>>(h.G, d.st_src32, T.d_leaf, T.d_SM + 0 * plane);
+  tree_p2m_kernel<PF, 2><<<h.M, 32 * kP2MWarps, 0, st>>>(h.G, d.st_src32, T.d_leaf, T.d_SM + 1 * plane);
+  tree_p2m_kernel<PF, 3><<<h.M, 32 * kP2MWarps, 0, st>>>(h.G, d.st_src32, T.d_leaf, T.d_SM + 2 * plane);
+  tree_p2m_kernel<PF, 4><<<h.M, 32 * kP2MWarps, 0, st>>>(h.G, d.st_src32, T.d_leaf, T.d_SM + 3 * plane);
+  count_launch(4);
+  if (timed) cudaEventRecord(T.ev[1], st);
+  for (size_t l = 0; l + 1 < T.level_off.size(); ++l) {
+    const int n = T.level_off[l + 1] - T.level_off[l];
+    if (n <= 0) continue;
+    const dim3 grid((unsigned)n, (unsigned)((2 * NM + kM2MThreads - 1) / kM2MThreads), 4);
+    tree_m2m_kernel<PF><<<grid, kM2MThreads, 0, st>>>(T.d_levels + T.level_off[l], T.d_child, T.d_geo, T.d_SM, plane,
+                                                      1);
+    count_launch();
+  }
+  const int64_t total = 4 * plane;
+  tree_to_f32_kernel<PF><<<(unsigned)std::min<int64_t>((total + 255) / 256, 4096), 256, 0, st>>>(total, T.d_SM,
+                                                                                                 T.d_SM32);
+  count_launch();
+  if (timed) cudaEventRecord(T.ev[2], st);
+  launch_stokes_far_tile_items(d, T.d_groups, T.d_tiles, T.d_ditems, T.n_ditems, u, st);
+  if (timed) cudaEventRecord(T.ev[3], st);
+  if (T.n_mitems > 0) {
+    tree_m2p_stokes_kernel<PF><<<T.n_mitems, kFarTile, 0, st>>>(T.d_mitems, T.d_groups, T.d_mlist, T.d_c32, T.d_SM32,
+                                                                plane, d.tgt32, u);
+    count_launch();
+  }
+  if (timed) cudaEventRecord(T.ev[4], st);
+  SBIO_CUDA_TRY(cudaGetLastError());
+  return SBIO_OK;
+}
+
+int launch_tree_stokes_far(sbio_geom* g, double* u, cudaStream_t st) {
+  TreeFar& T = *g->tree;
+  switch (T.order) {
+    case 8: return tree_apply_stokes<8>(g, T, u, st);
+    case 12: return tree_apply_stokes<12>(g, T, u, st);
+    default: return tree_apply_stokes<16>(g, T, u, st);
+  }
 }
 
 int launch_tree_far(sbio_geom* g, double* S, double* D, cudaStream_t st) {

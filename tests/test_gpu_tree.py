@@ -180,3 +180,45 @@ def test_tree_settings_switch_and_rebuild(S, ctx):
     with pytest.raises(S.SbioError):
         S.sbio_geom_tree_info(g.h)
     g.close()
+
+
+def _stokes(S, g, f):
+    u = torch.full((g.N, 3), float("nan"), dtype=torch.float64, device="cuda")
+    S.sbio_apply_stokes_sl(g.h, torch.from_numpy(np.ascontiguousarray(f)).cuda(), u)
+    torch.cuda.synchronize()
+    return u.cpu().numpy()
+
+
+@pytest.mark.parametrize("M,p,seed", [(50, 8, 51), (100, 12, 52)])
+def test_stokes_tree_matches_fp64_direct(S, ctx, M, p, seed):
+    """The Stokes single layer with the treecode far field (four charge and
+    four dipole channels per node) against the plain FP64 direct apply."""
+    s = I.rsa_suspension(M, 0.15, seed, p, ar_range=(1.5, 4.0), name="stree")
+    f = I.config_coefficients(s, seed, ndens=3).transpose(1, 0, 2).copy()
+    g = S.Geometry(ctx, s, precision=S.SBIO_FP64)
+    U64 = _stokes(S, g, f)
+    S.sbio_geom_set_precision(g.h, S.SBIO_MIXED)
+    Ud = _stokes(S, g, f)
+    S.sbio_geom_set_far_method(g.h, S.SBIO_FAR_TREE, 0.5, 16)
+    Ut = _stokes(S, g, f)
+    e = OL.normwise_rel_err(Ut, U64)
+    print(f"stokes tree M={M} p={p}: {e:.2e} (direct mixed {OL.normwise_rel_err(Ud, U64):.2e})")
+    assert e < TREE_BOUND[(16, 0.5)]
+    g.close()
+
+
+def test_stokes_tree_against_oracle_sampled(S, ctx):
+    from oracle import stokes as OSt
+
+    s = I.rsa_suspension(200, 0.15, 61, 10, ar_range=(1.5, 4.0), name="stree200")
+    f = I.config_coefficients(s, 3, ndens=3).transpose(1, 0, 2).copy()
+    g = S.Geometry(ctx, s, precision=S.SBIO_MIXED)
+    S.sbio_geom_set_far_method(g.h, S.SBIO_FAR_TREE, 0.5, 16)
+    Ut = _stokes(S, g, f)
+    og = OG.SuspensionGeom.from_suspension(s)
+    tg = np.sort(np.random.default_rng(8).choice(g.N, 30, replace=False))
+    Ur = OSt.StokesOracle(og).apply(f, "method", targets=tg)
+    e = np.max(np.abs(Ut[tg] - Ur)) / np.max(np.abs(Ur))
+    print(f"stokes tree200 vs oracle: {e:.2e}")
+    assert e < TREE_BOUND[(16, 0.5)]
+    g.close()
