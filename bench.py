@@ -691,10 +691,23 @@ def run_stokes100(args, ws, rank, lrank):
         ph.append(S.sbio_geom_phase_times(g.h))
     S.sbio_geom_enable_timing(g.h, False)
     um = u.clone()
+    # the same apply with the treecode far field (order 16, theta 0.5)
+    S.sbio_geom_set_far_method(g.h, S.SBIO_FAR_TREE, 0.5, 16)
+    for _ in range(3):
+        S.sbio_apply_stokes_sl(g.h, fd, u)
+    tms = []
+    for _ in range(args.steps):
+        flush.zero_()
+        tms.append(_event_time(st, lambda: S.sbio_apply_stokes_sl(g.h, fd, u)))
+    ut = u.clone()
+    S.sbio_geom_set_far_method(g.h, S.SBIO_FAR_DIRECT)
     S.sbio_geom_set_precision(g.h, S.SBIO_FP64)
     S.sbio_apply_stokes_sl(g.h, fd, u)
     t64 = _event_time(st, lambda: S.sbio_apply_stokes_sl(g.h, fd, u))
     err = float((um - u).abs().max() / u.abs().max())
+    tree_line = {"applies_per_s": 1e3 / statistics.mean(tms), "ms_per_step": statistics.mean(tms),
+                 "rel_err_vs_fp64_gpu": float((ut - u).abs().max() / u.abs().max()),
+                 "far_method": "particle treecode, 4 charge + 4 dipole channels, order 16, theta 0.5"}
     far_ms = statistics.mean(x[2] for x in ph)
     ach = STOKES_FAR_FLOP_PER_PAIR * g.n_far / (far_ms * 1e-3) / 1e12
     line = {"metric": "Stokes single-layer applies/s (all surface nodes)", "value": 1e3 / statistics.mean(ms),
@@ -712,8 +725,8 @@ def run_stokes100(args, ws, rank, lrank):
             "roofline": {"kernel": "stokes_far_mixed_kernel", "bound": "alu", "achieved": ach,
                          "peak": fp32_peak(), "unit": "TFLOP/s", "frac": ach / fp32_peak(),
                          "flop_per_pair": STOKES_FAR_FLOP_PER_PAIR, "traffic": None},
-            "fp64_gpu_applies_per_s": 1e3 / t64, "rel_err_vs_fp64_gpu": err, "gpu_launches": int(launches),
-            "clocks": clk}
+            "fp64_gpu_applies_per_s": 1e3 / t64, "rel_err_vs_fp64_gpu": err, "tree": tree_line,
+            "gpu_launches": int(launches), "clocks": clk}
     g.close()
     return line
 
@@ -1572,7 +1585,8 @@ def main():
                                               "speedup_vs_fp64_plain", "config"],
                                   args, ws, rank, lrank)
             line["stokes100"] = _sub(run_stokes100, ["metric", "value", "unit", "ms_per_step", "e2e", "roofline",
-                                                     "fp64_gpu_applies_per_s", "rel_err_vs_fp64_gpu", "config"],
+                                                     "fp64_gpu_applies_per_s", "rel_err_vs_fp64_gpu", "tree",
+                                                     "config"],
                                      args, ws, rank, lrank)
             line["lattice8"] = _sub(run_lattice8, ["metric", "value", "unit", "ms_per_step", "latency_ms", "e2e",
                                                    "mixed_applies_per_s", "config"], args, ws, rank, lrank)
