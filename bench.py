@@ -1512,6 +1512,26 @@ def run_far_sweep(args, ws, rank, lrank):
                        "direct_pair_fraction": info["direct_pairs"] / g.n_far, "tree_nodes": info["nodes"],
                        "phase_ms": dict(zip(("leaf_multipoles", "translations", "direct", "evaluations"),
                                             [statistics.median(x[k] for x in tph) for k in range(4)]))}
+        # the Stokes single layer on the same suspension, direct and treecode
+        S.sbio_geom_set_far_method(g.h, S.SBIO_FAR_DIRECT)
+        f = I.config_coefficients(susp, 1, ndens=3).transpose(1, 0, 2).copy()
+        fd = torch.from_numpy(f).cuda()
+        u = torch.empty((g.N, 3), dtype=torch.float64, device="cuda")
+        S.sbio_apply_stokes_sl(g.h, fd, u)
+        sd = []
+        for _ in range(reps):
+            flush.zero_()
+            sd.append(_event_time(st, lambda: S.sbio_apply_stokes_sl(g.h, fd, u)))
+        ud = u.clone()
+        S.sbio_geom_set_far_method(g.h, S.SBIO_FAR_TREE, 0.5, 16)
+        S.sbio_apply_stokes_sl(g.h, fd, u)
+        stt = []
+        for _ in range(reps):
+            flush.zero_()
+            stt.append(_event_time(st, lambda: S.sbio_apply_stokes_sl(g.h, fd, u)))
+        torch.cuda.synchronize()
+        row["stokes"] = {"direct_apply_ms": statistics.median(sd), "tree_apply_ms": statistics.median(stt),
+                         "rel_err_tree_vs_direct_mixed": float((u - ud).abs().max() / ud.abs().max())}
         rows.append(row)
         g.close()
     clk = clocks.stop()
