@@ -582,7 +582,8 @@ typedef struct sbio_server sbio_server;
  * must stay valid until sbio_server_wait returns for the ticket; sph is copied
  * at submission. */
 #define SBIO_REQ_TREE 1u  /* request flag: far field by the treecode (order 16, theta 0.5;
-                             mixed-precision requests, see sbio_geom_set_far_method) */
+                             mixed-precision requests with at least 50,000 nodes,
+                             see sbio_geom_set_far_method; smaller ones stay direct) */
 
 typedef struct {
   int32_t op;

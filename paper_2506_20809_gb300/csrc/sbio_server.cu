@@ -65,6 +65,8 @@ static size_t estimate_bytes(int32_t M, const sbio_options& o) {
   return (size_t)(N * 420 + (int64_t)M * (nc1 * 8 * 12 + 4096) + (4 << 20));
 }
 
+constexpr int64_t kServeTreeMinNodes = 50000;
+
 static int run_job(sbio_server* s, Job* j, cudaStream_t st) {
   const sbio_request& r = j->req;
   sbio_geom* g = nullptr;
@@ -74,8 +76,10 @@ static int run_job(sbio_server* s, Job* j, cudaStream_t st) {
   const int64_t N = g->h.N;
   const size_t nc = (size_t)(o.p + 1) * (o.p + 1) * r.M;
   const bool stokes = r.op == SBIO_OP_STOKES;
-  // the treecode far field for mixed requests that ask for it
-  if ((r.flags & SBIO_REQ_TREE) && o.precision == SBIO_MIXED && r.M > 1) {
+  // the treecode far field for mixed requests that ask for it and are large
+  // enough to gain from it (below about 50,000 nodes its fixed costs make it
+  // slower than the direct sum)
+  if ((r.flags & SBIO_REQ_TREE) && o.precision == SBIO_MIXED && r.M > 1 && N >= kServeTreeMinNodes) {
     rc = tree_attach_async(g, 16, 0.5, st);
     if (rc) {
       geom_destroy_async(g, st);

@@ -145,17 +145,18 @@ def test_served_results_against_oracle_sampled(S):
 
 
 def test_treecode_requests_alone_in_mix_and_against_direct(S):
-    """Laplace requests with the treecode flag: the same alone and in a mix
-    with direct and Stokes requests, and within the treecode bound of the
-    direct-field results."""
+    """A Laplace request with the treecode flag, large enough (67,600 nodes)
+    for the server to use it: the same alone and in a mix with direct and
+    Stokes requests, and within the treecode bound of the direct-field
+    results."""
     ctx = S.sbio_ctx_create(0, 0)
     base = make_requests()
-    big = I.rsa_suspension(90, 0.2, 777, 8, name="srvtree")
-    nc = 81
+    big = I.rsa_suspension(200, 0.2, 777, 12, name="srvtree")
+    nc = 169
     rng = np.random.default_rng(77)
-    coef = np.ascontiguousarray(np.stack([I.coefficients(rng, 90, 8, 2).transpose(1, 0, 2) for _ in range(NAPPLY)]))
-    N = 90 * 9 * 18
-    reqs = base + [{"s": big, "p": 8, "op": "laplace", "coef": coef, "N": N, "nc": nc}]
+    coef = np.ascontiguousarray(np.stack([I.coefficients(rng, 200, 12, 2).transpose(1, 0, 2) for _ in range(NAPPLY)]))
+    N = 200 * 13 * 26
+    reqs = base + [{"s": big, "p": 12, "op": "laplace", "coef": coef, "N": N, "nc": nc}]
 
     def run_flags(rs, slots, tree_for):
         srv = S.sbio_server_create(ctx, slots, 0)
