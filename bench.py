@@ -150,10 +150,10 @@ def parse():
                     choices=["poly200", "stokes100", "batch64", "serve", "deriv200", "targets200", "derivpoints200",
                              "dirichlet200", "stokespoints100", "stokesdl100", "stokesdlpoints100",
                              "lattice8", "far_sweep"])
-    ap.add_argument("--rates", default="2,5,10,20,30,50,200", help="serve: arrival rates (req/s)")
-    ap.add_argument("--requests", type=int, default=600, help="serve: at most this many requests per rate")
+    ap.add_argument("--rates", default="5,10,20,30,50,200", help="serve: arrival rates (req/s)")
+    ap.add_argument("--requests", type=int, default=2000, help="serve: at most this many requests per rate")
     ap.add_argument("--slots", type=int, default=4, help="serve: concurrent request slots")
-    ap.add_argument("--serve-seconds", type=float, default=20.0, help="serve: arrival window per rate (s)")
+    ap.add_argument("--serve-seconds", type=float, default=30.0, help="serve: arrival window per rate (s)")
     ap.add_argument("--serve-pool", type=int, default=32, help="serve: distinct suspensions drawn for the stream")
     ap.add_argument("--serve-direct", action="store_true", help="serve: direct far field for Laplace requests")
     ap.add_argument("--headline-only", action="store_true",

@@ -225,8 +225,11 @@ int sbio_geom_get_tuning(const sbio_geom* g, int32_t* far_tt, int32_t* far_split
  * zero-strength sources written by one self-only pass into the geometry's
  * own workspaces) and keeps the fastest; then, when the near field overlaps
  * the far field, times whole applies for a few near CTA caps and keeps the
- * fastest.  Reports the far shape (outputs may be NULL).  Synchronises
- * `stream`; the workspaces hold no caller data afterwards. */
+ * fastest (with a treecode attached, also the treecode's own near cap, by
+ * whole applies with the treecode).  The direct kernel's shape is tuned with
+ * the direct sum also when a treecode is attached.  Reports the far shape
+ * (outputs may be NULL).  Synchronises `stream`; the workspaces hold no
+ * caller data afterwards. */
 int sbio_geom_autotune(sbio_geom* g, void* stream, int32_t* far_tt, int32_t* far_splits, double* far_ms);
 
 /* Near/far overlap (default on): the FP64 near-field kernels of an apply run
@@ -369,12 +372,23 @@ int sbio_geom_autotune_stokes(sbio_geom* g, void* stream, int32_t* far_tt, int32
  * node.  SBIO_FAR_TREE builds the tree and lists on the host (synchronises
  * the device); SBIO_FAR_DIRECT (theta, order ignored) returns to the direct
  * sum.  FP64 geometries, evaluations at points and the other operators keep
- * the direct sum.
+ * the direct sum.  When the geometry overlaps its near field with the far
+ * field (sbio_geom_set_overlap), an apply with the treecode runs the direct
+ * part on a stream of the tree's own beside the multipole phases, and
+ * SBIO_FAR_TREE also picks the near kernels' CTA cap for such applies by
+ * timing whole Laplace applies of zero densities (kept apart from the direct
+ * sum's cap: see sbio_geom_set_tree_near_cap; sbio_geom_autotune retunes it).
  * Errors: SBIO_EINVAL (method, theta outside (0.05, 1), order), SBIO_ENOMEM,
  * SBIO_ECUDA. */
 #define SBIO_FAR_DIRECT 0
 #define SBIO_FAR_TREE 1
 int sbio_geom_set_far_method(sbio_geom* g, int32_t method, double theta, int32_t order);
+
+/* Near-field CTAs per SM while the near field overlaps a treecode far field
+ * (as sbio_geom_set_near_cap for the direct sum; default 2, 0 = no cap).
+ * The getter's output may not be NULL.  SBIO_EINVAL for a negative cap. */
+int sbio_geom_set_tree_near_cap(sbio_geom* g, int32_t ctas_per_sm);
+int sbio_geom_get_tree_near_cap(const sbio_geom* g, int32_t* ctas_per_sm);
 
 /* Sizes of the treecode far field per apply: tree nodes, target groups,
  * (target, multipole node) evaluations, the (target, source node) pairs those

@@ -94,6 +94,7 @@ struct GeomHost {
   int far_splits = 0;
   int near_block = 128;                      // threads per CTA of the near kernels
   int near_ctas_per_sm = 2;                  // near CTAs per SM while overlapping with the far field (0 = no cap)
+  int tree_near_ctas_per_sm = 2;             // the same while the treecode computes the far field
   // the same three settings for the Stokes single layer (its own kernels)
   int st_far_tt = 2;
   int st_far_splits = 0;
@@ -215,12 +216,13 @@ struct SideFork {
   cudaStream_t main = nullptr, side = nullptr;
   cudaEvent_t join_ev = nullptr;
   bool open = false;
-  cudaError_t fork(sbio_geom* g, cudaStream_t caller) {
+  cudaError_t fork(sbio_geom* g, cudaStream_t caller) { return fork_on(caller, g->near_stream, g->ev_fork, g->ev_join); }
+  cudaError_t fork_on(cudaStream_t caller, cudaStream_t to, cudaEvent_t fork_ev, cudaEvent_t join_with) {
     main = caller;
-    side = g->near_stream;
-    join_ev = g->ev_join;
-    cudaError_t e = cudaEventRecord(g->ev_fork, caller);
-    if (e == cudaSuccess) e = cudaStreamWaitEvent(side, g->ev_fork, 0);
+    side = to;
+    join_ev = join_with;
+    cudaError_t e = cudaEventRecord(fork_ev, caller);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(side, fork_ev, 0);
     open = (e == cudaSuccess);
     return e;
   }
@@ -286,6 +288,8 @@ struct TuneOps {
   int min_cap = 1;   // smallest near cap tried (besides uncapped)
 };
 int tune_launch_shape(sbio_geom* g, const TuneOps& ops, double* out, cudaStream_t st, double* best_far_ms);
+// the near CTA cap alone (*ops.cap) by whole applies, with the far field as set
+int tune_near_cap(sbio_geom* g, const TuneOps& ops, double* out, cudaStream_t st);
 
 // source splits of the far-field grid (gridDim.y) for `target_blocks` target
 // CTAs; `requested` > 0 forces the count

@@ -498,9 +498,13 @@ void launch_far_on(const DevGeom& d, const GeomHost& h, int64_t NT, double* S, d
   count_launch();
 }
 
+// the treecode replaces the direct sum for mixed S + D applies at the nodes
+static bool far_by_tree(const sbio_geom* g, const double* S, const double* D) {
+  return g->tree && g->h.precision == SBIO_MIXED && S && D;
+}
+
 static void launch_far(sbio_geom* g, double* S, double* D, cudaStream_t st) {
-  // the treecode replaces the direct sum for mixed S + D applies at the nodes
-  if (g->tree && g->h.precision == SBIO_MIXED && S && D) {
+  if (far_by_tree(g, S, D)) {
     launch_tree_far(g, S, D, st);
     return;
   }
@@ -622,8 +626,10 @@ int launch_laplace(sbio_geom* g, const double* sigma, const double* mu, double* 
   SideFork sf;
   if (fork) {
     SBIO_CUDA_TRY(sf.fork(g, st));
-    // a few near CTAs per SM leave room for the far kernel's CTAs
-    g->d.near_grid_cap = g->h.near_ctas_per_sm > 0 ? g->h.near_ctas_per_sm * sm_count() : 0;
+    // a few near CTAs per SM leave room for the far kernels' CTAs (the direct
+    // sum and the treecode's phases want different shares)
+    const int cap = far_by_tree(g, S, D) ? g->h.tree_near_ctas_per_sm : g->h.near_ctas_per_sm;
+    g->d.near_grid_cap = cap > 0 ? cap * sm_count() : 0;
     rc = launch_near(g, S, D, g->near_stream);
     g->d.near_grid_cap = 0;
     if (rc) return rc;
@@ -689,28 +695,52 @@ int tune_launch_shape(sbio_geom* g, const TuneOps& ops, double* out, cudaStream_
   }
   *ops.tt = best_tt;
   *ops.splits = best_sp;
-  // near CTAs per SM while the near field overlaps the far field: whole applies
-  if (!rc && ops.whole && g->overlap && g->near_stream && !g->timing && !h.pair_t.empty()) {
-    const int caps[5] = {1, 2, 4, 8, 0};
-    float best_apply = 1e30f;
-    int best_cap = *ops.cap;
-    for (int c = 0; c < 5 && !rc; ++c) {
-      if (caps[c] != 0 && caps[c] < ops.min_cap) continue;
-      *ops.cap = caps[c];
-      float m = 0.f;
-      rc = time3(ops.whole, &m);
-      if (!rc && m < best_apply) {
-        best_apply = m;
-        best_cap = caps[c];
-      }
-    }
-    *ops.cap = best_cap;
-  }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   if (rc) return rc;
   SBIO_CUDA_TRY(cudaGetLastError());
   *best_far_ms = best;
+  // near CTAs per SM while the near field overlaps the far field
+  return tune_near_cap(g, ops, out, st);
+}
+
+int tune_near_cap(sbio_geom* g, const TuneOps& ops, double* out, cudaStream_t st) {
+  if (!ops.whole || !g->overlap || !g->near_stream || g->timing || g->h.pair_t.empty()) return SBIO_OK;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  SBIO_CUDA_TRY(cudaEventCreate(&e0));
+  if (cudaEventCreate(&e1) != cudaSuccess) {
+    cudaEventDestroy(e0);
+    return set_error(SBIO_ECUDA, "event create failed");
+  }
+  // whole applies, median of five after one warm-up, per cap
+  const int caps[7] = {1, 2, 3, 4, 6, 8, 0};
+  float best_apply = 1e30f;
+  int best_cap = *ops.cap;
+  int rc = SBIO_OK;
+  for (int c = 0; c < 7 && !rc; ++c) {
+    if (caps[c] != 0 && caps[c] < ops.min_cap) continue;
+    *ops.cap = caps[c];
+    rc = ops.whole(g, out, st);
+    float t[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
+    for (int k = 0; k < 5 && !rc; ++k) {
+      cudaEventRecord(e0, st);
+      rc = ops.whole(g, out, st);
+      cudaEventRecord(e1, st);
+      if (!rc && cudaEventSynchronize(e1) != cudaSuccess) rc = set_error(SBIO_ECUDA, "autotune timing failed");
+      if (!rc) cudaEventElapsedTime(&t[k], e0, e1);
+    }
+    std::sort(t, t + 5);
+    const float m = t[2];
+    if (!rc && m < best_apply) {
+      best_apply = m;
+      best_cap = caps[c];
+    }
+  }
+  *ops.cap = best_cap;
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (rc) return rc;
+  SBIO_CUDA_TRY(cudaGetLastError());
   return SBIO_OK;
 }
 
@@ -860,6 +890,12 @@ int sbio_geom_autotune(sbio_geom* g, void* stream, int32_t* far_tt, int32_t* far
   rc = tune_launch_shape(g, ops, d.host_out, st, &best);
   g->tree = tree;
   if (rc) return rc;
+  if (tree) {
+    // the near kernels' share beside the treecode's phases
+    ops.cap = &h.tree_near_ctas_per_sm;
+    rc = tune_near_cap(g, ops, d.host_out, st);
+    if (rc) return rc;
+  }
   if (far_tt) *far_tt = h.far_tt;
   if (far_splits) *far_splits = h.far_splits;
   if (far_ms) *far_ms = best;

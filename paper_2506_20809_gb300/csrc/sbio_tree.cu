@@ -101,9 +101,16 @@ struct TreeFar {
   // phase events of the last apply while the geometry's timing is on:
   // leaf multipoles | translations + FP32 copy | direct part | evaluations
   cudaEvent_t ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+  // the direct part runs on its own stream beside the multipole phases (it
+  // needs no multipoles); null when the geometry runs its phases in order
+  cudaStream_t side = nullptr;
+  cudaEvent_t side_fork = nullptr, side_join = nullptr;
   ~TreeFar() {
     for (cudaEvent_t& e : ev)
       if (e) cudaEventDestroy(e);
+    if (side_fork) cudaEventDestroy(side_fork);
+    if (side_join) cudaEventDestroy(side_join);
+    if (side) cudaStreamDestroy(side);
   }
 };
 
@@ -916,6 +923,14 @@ static int tree_apply(sbio_geom* g, TreeFar& T, double* S, double* D, cudaStream
   constexpr int NM = tree_nm(PF);
   const bool timed = g->timing && T.ev[0];
   if (timed) cudaEventRecord(T.ev[0], st);
+  // untimed: the direct part first, on the side stream, beside the multipole
+  // phases (both add into S and D atomically)
+  SideFork sf;
+  const bool forked = !timed && T.side && g->overlap;
+  if (forked) {
+    SBIO_CUDA_TRY(sf.fork_on(st, T.side, T.side_fork, T.side_join));
+    launch_far_tile_items(d, T.d_groups, T.d_tiles, T.d_ditems, T.n_ditems, S, D, T.side);
+  }
   tree_p2m_kernel<PF, 0><<<h.M, 32 * kP2MWarps, 0, st>>>(h.G, d.src32, T.d_leaf, T.d_M);
   count_launch();
   if (timed) cudaEventRecord(T.ev[1], st);
@@ -930,7 +945,7 @@ static int tree_apply(sbio_geom* g, TreeFar& T, double* S, double* D, cudaStream
   tree_to_f32_kernel<PF><<<(unsigned)std::min<int64_t>((total + 255) / 256, 4096), 256, 0, st>>>(total, T.d_M, T.d_M32);
   count_launch();
   if (timed) cudaEventRecord(T.ev[2], st);
-  launch_far_tile_items(d, T.d_groups, T.d_tiles, T.d_ditems, T.n_ditems, S, D, st);
+  if (!forked) launch_far_tile_items(d, T.d_groups, T.d_tiles, T.d_ditems, T.n_ditems, S, D, st);
   if (timed) cudaEventRecord(T.ev[3], st);
   if (T.n_mitems > 0) {
     tree_m2p_kernel<PF><<<T.n_mitems, kFarTile, 0, st>>>(T.d_mitems, T.d_groups, T.d_mlist, T.d_c32, T.d_M32, d.tgt32,
@@ -939,6 +954,7 @@ static int tree_apply(sbio_geom* g, TreeFar& T, double* S, double* D, cudaStream
   }
   if (timed) cudaEventRecord(T.ev[4], st);
   SBIO_CUDA_TRY(cudaGetLastError());
+  SBIO_CUDA_TRY(sf.join());
   return SBIO_OK;
 }
 
@@ -970,6 +986,12 @@ static int tree_apply_stokes(sbio_geom* g, TreeFar& T, double* u, cudaStream_t s
   const int64_t plane = (int64_t)T.n_nodes * 2 * NM;
   const bool timed = g->timing && T.ev[0];
   if (timed) cudaEventRecord(T.ev[0], st);
+  SideFork sf;   // the direct part beside the multipole phases, as for Laplace
+  const bool forked = !timed && T.side && g->overlap;
+  if (forked) {
+    SBIO_CUDA_TRY(sf.fork_on(st, T.side, T.side_fork, T.side_join));
+    launch_stokes_far_tile_items(d, T.d_groups, T.d_tiles, T.d_ditems, T.n_ditems, u, T.side);
+  }
   tree_p2m_kernel<PF, 1><<<h.M, 32 * kP2MWarps, 0, st>>>(h.G, d.st_src32, T.d_leaf, T.d_SM + 0 * plane);
   tree_p2m_kernel<PF, 2><<<h.M, 32 * kP2MWarps, 0, st>>>(h.G, d.st_src32, T.d_leaf, T.d_SM + 1 * plane);
   tree_p2m_kernel<PF, 3><<<h.M, 32 * kP2MWarps, 0, st>>>(h.G, d.st_src32, T.d_leaf, T.d_SM + 2 * plane);
@@ -989,7 +1011,7 @@ static int tree_apply_stokes(sbio_geom* g, TreeFar& T, double* u, cudaStream_t s
                                                                                                  T.d_SM32);
   count_launch();
   if (timed) cudaEventRecord(T.ev[2], st);
-  launch_stokes_far_tile_items(d, T.d_groups, T.d_tiles, T.d_ditems, T.n_ditems, u, st);
+  if (!forked) launch_stokes_far_tile_items(d, T.d_groups, T.d_tiles, T.d_ditems, T.n_ditems, u, st);
   if (timed) cudaEventRecord(T.ev[3], st);
   if (T.n_mitems > 0) {
     tree_m2p_stokes_kernel<PF><<<T.n_mitems, kFarTile, 0, st>>>(T.d_mitems, T.d_groups, T.d_mlist, T.d_c32, T.d_SM32,
@@ -998,6 +1020,7 @@ static int tree_apply_stokes(sbio_geom* g, TreeFar& T, double* u, cudaStream_t s
   }
   if (timed) cudaEventRecord(T.ev[4], st);
   SBIO_CUDA_TRY(cudaGetLastError());
+  SBIO_CUDA_TRY(sf.join());
   return SBIO_OK;
 }
 
@@ -1048,8 +1071,15 @@ int sbio_geom_set_far_method(sbio_geom* g, int32_t method, double theta, int32_t
   TreeFar* t = new TreeFar();
   t->order = order;
   t->theta = theta;
-  for (cudaEvent_t& e : t->ev) SBIO_CUDA_TRY(cudaEventCreate(&e));
-  int rc = build_tree(g, *t, nullptr);
+  int rc = SBIO_OK;
+  for (cudaEvent_t& e : t->ev)
+    if (!rc && cudaEventCreate(&e) != cudaSuccess) rc = set_error(SBIO_ECUDA, "treecode event creation failed");
+  if (!rc && g->overlap &&
+      (cudaStreamCreateWithFlags(&t->side, cudaStreamNonBlocking) != cudaSuccess ||
+       cudaEventCreateWithFlags(&t->side_fork, cudaEventDisableTiming) != cudaSuccess ||
+       cudaEventCreateWithFlags(&t->side_join, cudaEventDisableTiming) != cudaSuccess))
+    rc = set_error(SBIO_ECUDA, "treecode stream creation failed");
+  if (!rc) rc = build_tree(g, *t, nullptr);
   if (!rc && cudaStreamSynchronize(nullptr) != cudaSuccess) rc = set_error(SBIO_ECUDA, "treecode upload failed");
   if (rc) {
     delete t;
@@ -1057,6 +1087,39 @@ int sbio_geom_set_far_method(sbio_geom* g, int32_t method, double theta, int32_t
   }
   tree_free(g->tree);
   g->tree = t;
+  // the near kernels' CTA cap beside the treecode's phases, by whole applies
+  // of zero densities (the apply writes finite sources first)
+  if (g->overlap && g->near_stream && !g->timing && !g->h.pair_t.empty()) {
+    const size_t nc = (size_t)(g->h.p + 1) * (g->h.p + 1) * g->h.M;
+    SBIO_CUDA_TRY(cudaMemsetAsync(g->d.host_in, 0, 2 * nc * sizeof(double), nullptr));
+    TuneOps ops;
+    ops.far = nullptr;
+    ops.whole = [](sbio_geom* gg, double* out, cudaStream_t s) {
+      const size_t n = (size_t)(gg->h.p + 1) * (gg->h.p + 1) * gg->h.M;
+      return launch_laplace(gg, gg->d.host_in, gg->d.host_in + n, out, out + gg->h.N, SBIO_PART_ALL, s);
+    };
+    ops.tt = nullptr;
+    ops.splits = nullptr;
+    ops.cap = &g->h.tree_near_ctas_per_sm;
+    rc = tune_near_cap(g, ops, g->d.host_out, nullptr);
+    if (!rc && cudaStreamSynchronize(nullptr) != cudaSuccess) rc = set_error(SBIO_ECUDA, "near cap tuning failed");
+    if (rc) return rc;
+  }
+  return SBIO_OK;
+}
+
+int sbio_geom_set_tree_near_cap(sbio_geom* g, int32_t ctas_per_sm) {
+  clear_error();
+  if (!g) return set_error(SBIO_EINVAL, "null geometry");
+  if (ctas_per_sm < 0) return set_error(SBIO_EINVAL, "ctas_per_sm must be >= 0");
+  g->h.tree_near_ctas_per_sm = ctas_per_sm;
+  return SBIO_OK;
+}
+
+int sbio_geom_get_tree_near_cap(const sbio_geom* g, int32_t* ctas_per_sm) {
+  clear_error();
+  if (!g || !ctas_per_sm) return set_error(SBIO_EINVAL, "null argument");
+  *ctas_per_sm = g->h.tree_near_ctas_per_sm;
   return SBIO_OK;
 }
 

@@ -107,6 +107,8 @@ _SIGS = {
     "sbio_geom_set_launch_shape": (C.c_int, [_vp, C.c_int32, C.c_int32]),
     "sbio_geom_set_overlap": (C.c_int, [_vp, C.c_int32]),
     "sbio_geom_set_near_cap": (C.c_int, [_vp, C.c_int32]),
+    "sbio_geom_set_tree_near_cap": (C.c_int, [_vp, C.c_int32]),
+    "sbio_geom_get_tree_near_cap": (C.c_int, [_vp, C.POINTER(C.c_int32)]),
     "sbio_geom_get_tuning": (C.c_int, [_vp, C.POINTER(C.c_int32), C.POINTER(C.c_int32), C.POINTER(C.c_int32)]),
     "sbio_geom_autotune": (C.c_int, [_vp, _vp, C.POINTER(C.c_int32), C.POINTER(C.c_int32),
                                      C.POINTER(C.c_double)]),
@@ -297,6 +299,16 @@ def sbio_geom_set_overlap(g, on=True):
 
 def sbio_geom_set_near_cap(g, ctas_per_sm):
     _check(_lib.sbio_geom_set_near_cap(g, ctas_per_sm))
+
+
+def sbio_geom_set_tree_near_cap(g, ctas_per_sm):
+    _check(_lib.sbio_geom_set_tree_near_cap(g, ctas_per_sm))
+
+
+def sbio_geom_get_tree_near_cap(g):
+    a = C.c_int32()
+    _check(_lib.sbio_geom_get_tree_near_cap(g, C.byref(a)))
+    return a.value
 
 
 def sbio_geom_get_tuning(g):

@@ -222,3 +222,36 @@ def test_stokes_tree_against_oracle_sampled(S, ctx):
     print(f"stokes tree200 vs oracle: {e:.2e}")
     assert e < TREE_BOUND[(16, 0.5)]
     g.close()
+
+
+def test_tree_forked_phases_equal_in_order(S, ctx):
+    """With overlap on, the treecode's direct part runs on its own stream
+    beside the multipole phases and the near kernels beside both; the result
+    is the in-order apply's up to the order of the atomic additions.  The
+    treecode's near cap is tuned when the treecode is attached, kept apart
+    from the direct sum's, and settable."""
+    s = I.rsa_suspension(150, 0.20, 71, 12, name="treefork")
+    c = I.config_coefficients(s, 71)
+    f = I.config_coefficients(s, 72, ndens=3).transpose(1, 0, 2).copy()
+    g = S.Geometry(ctx, s, precision=S.SBIO_MIXED)
+    S.sbio_geom_set_near_cap(g.h, 1)
+    S.sbio_geom_set_far_method(g.h, S.SBIO_FAR_TREE, 0.5, 16)
+    assert S.sbio_geom_get_tree_near_cap(g.h) in (0, 1, 2, 3, 4, 6, 8)
+    assert S.sbio_geom_get_tuning(g.h)["near_ctas_per_sm"] == 1
+    outs = {}
+    for cap in (1, 3):
+        S.sbio_geom_set_tree_near_cap(g.h, cap)
+        assert S.sbio_geom_get_tree_near_cap(g.h) == cap
+        S.sbio_geom_set_overlap(g.h, True)
+        outs[cap] = _apply(S, g, c) + (_stokes(S, g, f),)
+    S.sbio_geom_set_overlap(g.h, False)
+    Si, Di = _apply(S, g, c)
+    Ui = _stokes(S, g, f)
+    for cap, (Sf, Df, Uf) in outs.items():
+        assert np.isfinite(Sf).all() and np.isfinite(Df).all() and np.isfinite(Uf).all()
+        assert OL.normwise_rel_err(Sf, Si) < 1e-12, cap
+        assert OL.normwise_rel_err(Df, Di) < 1e-12, cap
+        assert OL.normwise_rel_err(Uf, Ui) < 1e-12, cap
+    with pytest.raises(S.SbioError):
+        S.sbio_geom_set_tree_near_cap(g.h, -1)
+    g.close()
