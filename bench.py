@@ -537,6 +537,8 @@ def run_ours(args, ws, rank, lrank):
                 "rel_err_vs_fp64_gpu": {"S": float((So - S64).abs().max() / S64.abs().max()),
                                         "D": float((Do - D64).abs().max() / D64.abs().max())},
                 "m2p_evaluations": info["m2p_pairs"], "direct_pairs": info["direct_pairs"],
+                "m2p_evaluations_by_order": S.sbio_geom_tree_order_counts(geom.h, S.SBIO_OP_LAPLACE),
+                "near_ctas_per_sm_beside_tree": S.sbio_geom_get_tree_near_cap(geom.h),
                 "note": "same apply with the far field by the treecode instead of the direct sum; the headline "
                         "value above is the direct tiled sum"}
             S.sbio_geom_set_far_method(geom.h, S.SBIO_FAR_DIRECT)
@@ -1509,6 +1511,8 @@ def run_far_sweep(args, ws, rank, lrank):
                        "rel_err_vs_direct_mixed": {"S": float((So - Sd).abs().max() / Sd.abs().max()),
                                                    "D": float((Do - Dd).abs().max() / Dd.abs().max())},
                        "m2p_evaluations": info["m2p_pairs"], "direct_pairs": info["direct_pairs"],
+                       "m2p_evaluations_by_order": S.sbio_geom_tree_order_counts(g.h, S.SBIO_OP_LAPLACE),
+                       "near_ctas_per_sm_beside_tree": S.sbio_geom_get_tree_near_cap(g.h),
                        "direct_pair_fraction": info["direct_pairs"] / g.n_far, "tree_nodes": info["nodes"],
                        "phase_ms": dict(zip(("leaf_multipoles", "translations", "direct", "evaluations"),
                                             [statistics.median(x[k] for x in tph) for k in range(4)]))}

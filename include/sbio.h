@@ -369,7 +369,8 @@ int sbio_geom_autotune_stokes(sbio_geom* g, void* stream, int32_t* far_tt, int32
  * is summed directly with the per-target skip lists.  The result is the same
  * discrete far sum (Sec. 4.1 quadrature over the far particles' nodes) up to
  * the truncation of the expansions, about (theta)^(order+1) relative per
- * node.  SBIO_FAR_TREE builds the tree and lists on the host (synchronises
+ * node (nodes farther than r_node / theta are evaluated at a lower order
+ * with the same bound: sbio_geom_tree_order_counts).  SBIO_FAR_TREE builds the tree and lists on the host (synchronises
  * the device); SBIO_FAR_DIRECT (theta, order ignored) returns to the direct
  * sum.  FP64 geometries, evaluations at points and the other operators keep
  * the direct sum.  When the geometry overlaps its near field with the far
@@ -397,6 +398,19 @@ int sbio_geom_get_tree_near_cap(const sbio_geom* g, int32_t* ctas_per_sm);
  * pair is covered once).  SBIO_EINVAL if the geometry uses the direct sum. */
 int sbio_geom_tree_info(const sbio_geom* g, int64_t* n_nodes, int64_t* n_groups, int64_t* m2p_pairs,
                         int64_t* m2p_source_pairs, int64_t* direct_pairs);
+
+/* The (target, multipole node) evaluations per apply of operator `op`
+ * (SBIO_OP_LAPLACE: S + D; SBIO_OP_STOKES: the Stokes single layer) by
+ * evaluation order: evals[0], [1], [2] at orders 8, 12 and 16 (they add up
+ * to m2p_pairs of sbio_geom_tree_info).  An accepted node is evaluated at the
+ * lowest of these orders E (at most the treecode's order P) with
+ * rho^(E+1) <= s theta^(P+1), rho = r_node / (distance from the target
+ * group's centre to the node's centre - the group's radius) <= theta, and
+ * s = 1 for Laplace (the truncation bound of every evaluation stays that of
+ * order P at theta), s = 1/10 for Stokes (eight channels per node).
+ * SBIO_EINVAL for a null argument, an unknown operator or a geometry
+ * without a treecode. */
+int sbio_geom_tree_order_counts(const sbio_geom* g, int32_t op, int64_t* evals);
 
 /* Durations (ms) of the treecode phases of the last apply made with phase
  * timing on (sbio_geom_enable_timing): ms[0] leaf multipoles, ms[1]

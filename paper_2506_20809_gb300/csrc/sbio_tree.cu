@@ -35,6 +35,13 @@
 // not accepted goes to the group's direct list, evaluated by the direct
 // mixed kernel with the per-target skip lists, so each (target, particle)
 // pair outside the target's own and near set is counted exactly once.
+// An accepted node is evaluated at the lowest order E of {8, 12, 16} (at
+// most the tree's order P) whose truncation factor rho^(E+1), with
+// rho = r_n / (|c_g - c_n| - R_g) over the group's bounding sphere, is no
+// larger than s theta^(P+1), theta^(P+1) being the factor of the worst node
+// accepted at order P: s = 1 for the Laplace S + D (the per-node bound stays
+// that of order P at theta), s = 1/10 for the Stokes single layer, whose
+// eight channels add the truncation errors of more terms.
 //
 // Per apply: leaf multipoles from the FP32 sources (FP32 per warp with TwoSum
 // compensation for the orders n < 4 that carry most of the far field, FP64
@@ -45,6 +52,7 @@
 // by TwoSum), each added atomically into the FP64 outputs.
 #include <algorithm>
 #include <cmath>
+#include <type_traits>
 #include <vector>
 
 #include "sbio_internal.cuh"
@@ -92,9 +100,14 @@ struct TreeFar {
   int4* d_tiles = nullptr;        // direct source tiles, group after group
   int4* d_ditems = nullptr;       // (group, first tile, end tile, 0)
   int n_ditems = 0;
-  int* d_mlist = nullptr;         // accepted node ids, group after group
-  int4* d_mitems = nullptr;       // (group, first entry, end entry, 0)
-  int n_mitems = 0;
+  // evaluation lists, one per operator (0 Laplace, 1 Stokes: the orders
+  // differ, the accepted nodes do not)
+  struct EvalLists {
+    int* d_mlist = nullptr;          // accepted node ids, group after group, by order class
+    int4* d_mitems = nullptr;        // (group, first entry, end entry, order class), by class
+    int off[4] = {0, 0, 0, 0};       // items of evaluation order 8 + 4 c: [off[c], off[c + 1])
+    int64_t evals_by_order[3] = {0, 0, 0};
+  } ev_lists[2];
   // host images of the uploaded tables (kept until the tree is dropped, so
   // that an upload queued on a stream may read them after the build returns)
   std::vector<std::vector<char>> host_images;
@@ -440,14 +453,15 @@ __global__ void tree_to_f32_kernel(int64_t total, const double2* __restrict__ Mt
 // f32x2 lane pair (sm_100+ packed FP32), so each recurrence and contraction
 // step issues once for both.  The node's coefficients are staged in shared
 // memory already broadcast to lane pairs: (re, re, -im, -im).
-template <int PF>
+template <int PF, int PE>
 __global__ void __launch_bounds__(kFarTile) tree_m2p_kernel(const int4* __restrict__ items, const int2* __restrict__ groups,
                                                             const int* __restrict__ mlist,
                                                             const float4* __restrict__ c32,
                                                             const float2* __restrict__ M32,
                                                             const float4* __restrict__ tgt32,
                                                             double* __restrict__ S_out, double* __restrict__ D_out) {
-  constexpr int NM = tree_nm(PF);
+  constexpr int NMF = tree_nm(PF);   // stored coefficients per node and operator
+  constexpr int NM = tree_nm(PE);    // evaluated ones (orders n <= PE)
   __shared__ float4 cf[2 * NM];
   __shared__ float4 cc[2];
   const int4 it = items[blockIdx.x];
@@ -471,7 +485,8 @@ __global__ void __launch_bounds__(kFarTile) tree_m2p_kernel(const int4* __restri
     const int node = mlist[e];
     __syncthreads();
     for (int k = tid; k < 2 * NM; k += kFarTile) {
-      const float2 v = M32[(int64_t)node * 2 * NM + k];
+      const int op = k >= NM ? 1 : 0;
+      const float2 v = M32[((int64_t)node * 2 + op) * NMF + (k - op * NM)];
       cf[k] = make_float4(v.x, v.x, -v.y, -v.y);
     }
     if (tid < 2) cc[tid] = c32[node * 2 + tid];
@@ -496,7 +511,7 @@ __global__ void __launch_bounds__(kFarTile) tree_m2p_kernel(const int4* __restri
     float2 Ir = make_float2(R0[0], R0[1]), Ii = make_float2(0.f, 0.f);   // I_m^m, from I_0^0 = 1 / r
     float2 sS = make_float2(0.f, 0.f), sD = make_float2(0.f, 0.f);
 #pragma unroll
-    for (int m = 0; m <= PF; ++m) {
+    for (int m = 0; m <= PE; ++m) {
       if (m > 0) {
         // I_m^m = -(2m - 1) (x + i y) / r^2 I_{m-1}^{m-1}
         const float2 s2 = make_float2(-(float)(2 * m - 1), -(float)(2 * m - 1));
@@ -513,7 +528,7 @@ __global__ void __launch_bounds__(kFarTile) tree_m2p_kernel(const int4* __restri
       }
       float2 ar = Ir, ai = Ii, br = make_float2(0.f, 0.f), bi = make_float2(0.f, 0.f);   // I_{n-1}^m, I_{n-2}^m
 #pragma unroll
-      for (int n = m + 1; n <= PF; ++n) {
+      for (int n = m + 1; n <= PE; ++n) {
         // I_n^m = ((2n - 1) z I_{n-1}^m - (n-1-m)(n-1+m) I_{n-2}^m) / r^2
         const float kz = (float)(2 * n - 1), kb = -(float)((n - 1 - m) * (n - 1 + m));
         const float2 u = __fmul2_rn(make_float2(kz, kz), zs), v = __fmul2_rn(make_float2(kb, kb), ir2);
@@ -551,14 +566,17 @@ __global__ void __launch_bounds__(kFarTile) tree_m2p_kernel(const int4* __restri
 //   8 pi u_i = S[F_i] + (x - c)_i D[F] - D[(y - c)_i F]
 // (the Stokeslet f/r + (r.f) r/r^3 written through Laplace charges and
 // dipoles about the node's centre c), two targets per thread packed in f32x2.
-template <int PF>
-__global__ void __launch_bounds__(kFarTile) tree_m2p_stokes_kernel(
+template <int PF, int PE>
+__global__ void __launch_bounds__(kFarTile, 4) tree_m2p_stokes_kernel(
     const int4* __restrict__ items, const int2* __restrict__ groups, const int* __restrict__ mlist,
     const float4* __restrict__ c32, const float2* __restrict__ M32, int64_t plane, const float4* __restrict__ tgt32,
     double* __restrict__ u_out) {
-  constexpr int NM = tree_nm(PF);
+  constexpr int NMF = tree_nm(PF);   // stored coefficients per node, plane and kind
+  constexpr int NM = tree_nm(PE);    // evaluated ones (orders n <= PE)
   constexpr double kInv8Pi = 0.039788735772973836;
-  __shared__ float4 cf[8 * NM];   // (plane z, kind k) block (2 z + k) of NM coefficients
+  // blocks b = 0..6 of NM coefficients: (plane z, kind k) = (b / 2, b % 2); the
+  // charges of plane 3 are zero and not read (its dipoles are block 6)
+  __shared__ float4 cf[7 * NM];
   __shared__ float4 cc[2];
   const int4 it = items[blockIdx.x];
   const int2 grp = groups[it.x];
@@ -581,9 +599,10 @@ __global__ void __launch_bounds__(kFarTile) tree_m2p_stokes_kernel(
   for (int e = it.y; e < it.z; ++e) {
     const int node = mlist[e];
     __syncthreads();
-    for (int k = tid; k < 8 * NM; k += kFarTile) {
-      const int blk = k / NM, idx = k - blk * NM;   // blk = 2 z + kind
-      const float2 v = M32[(blk >> 1) * plane + ((int64_t)node * 2 + (blk & 1)) * NM + idx];
+    for (int k = tid; k < 7 * NM; k += kFarTile) {
+      const int b = k / NM, idx = k - b * NM;
+      const int blk = b < 6 ? b : 7;   // 2 z + kind
+      const float2 v = M32[(blk >> 1) * plane + ((int64_t)node * 2 + (blk & 1)) * NMF + idx];
       cf[k] = make_float4(v.x, v.x, -v.y, -v.y);
     }
     if (tid < 2) cc[tid] = c32[node * 2 + tid];
@@ -606,11 +625,11 @@ __global__ void __launch_bounds__(kFarTile) tree_m2p_stokes_kernel(
     const float2 xs = make_float2(Xs[0], Xs[1]), ys = make_float2(Ys[0], Ys[1]);
     const float2 zs = make_float2(Zs[0], Zs[1]), ir2 = make_float2(I2[0], I2[1]);
     float2 Ir = make_float2(R0[0], R0[1]), Ii = make_float2(0.f, 0.f);
-    float2 acc[8];
+    float2 acc[7];
 #pragma unroll
-    for (int b = 0; b < 8; ++b) acc[b] = make_float2(0.f, 0.f);
+    for (int b = 0; b < 7; ++b) acc[b] = make_float2(0.f, 0.f);
 #pragma unroll
-    for (int m = 0; m <= PF; ++m) {
+    for (int m = 0; m <= PE; ++m) {
       if (m > 0) {
         const float2 s2 = make_float2(-(float)(2 * m - 1), -(float)(2 * m - 1));
         const float2 wr = __fmul2_rn(s2, xs), wi = __fmul2_rn(s2, ys);
@@ -620,18 +639,18 @@ __global__ void __launch_bounds__(kFarTile) tree_m2p_stokes_kernel(
         Ii = ti;
       }
 #pragma unroll
-      for (int b = 0; b < 8; ++b) {
+      for (int b = 0; b < 7; ++b) {
         const float4 a = cf[b * NM + tree_idx(m, m)];
         acc[b] = __ffma2_rn(make_float2(a.x, a.y), Ir, __ffma2_rn(make_float2(a.z, a.w), Ii, acc[b]));
       }
       float2 ar = Ir, ai = Ii, br = make_float2(0.f, 0.f), bi = make_float2(0.f, 0.f);
 #pragma unroll
-      for (int n = m + 1; n <= PF; ++n) {
+      for (int n = m + 1; n <= PE; ++n) {
         const float kz = (float)(2 * n - 1), kb = -(float)((n - 1 - m) * (n - 1 + m));
         const float2 u = __fmul2_rn(make_float2(kz, kz), zs), v = __fmul2_rn(make_float2(kb, kb), ir2);
         const float2 cr = __ffma2_rn(u, ar, __fmul2_rn(v, br)), ci = __ffma2_rn(u, ai, __fmul2_rn(v, bi));
 #pragma unroll
-        for (int b = 0; b < 8; ++b) {
+        for (int b = 0; b < 7; ++b) {
           const float4 a = cf[b * NM + tree_idx(n, m)];
           acc[b] = __ffma2_rn(make_float2(a.x, a.y), cr, __ffma2_rn(make_float2(a.z, a.w), ci, acc[b]));
         }
@@ -641,10 +660,11 @@ __global__ void __launch_bounds__(kFarTile) tree_m2p_stokes_kernel(
         ai = ci;
       }
     }
-    // acc[2 z] = S of plane z (charges F_1, F_2, F_3, 0), acc[2 z + 1] = D of plane z
+    // acc[2 z] = S of plane z < 3 (charges F_1, F_2, F_3), acc[2 z + 1] = D of
+    // plane z < 3, acc[6] = D of plane 3
     const float Sx[2] = {acc[0].x, acc[0].y}, Sy[2] = {acc[2].x, acc[2].y}, Sz[2] = {acc[4].x, acc[4].y};
     const float D0[2] = {acc[1].x, acc[1].y}, Dx[2] = {acc[3].x, acc[3].y}, Dy[2] = {acc[5].x, acc[5].y},
-                Dz[2] = {acc[7].x, acc[7].y};
+                Dz[2] = {acc[6].x, acc[6].y};
 #pragma unroll
     for (int q = 0; q < 2; ++q) {
       const float uv[3] = {fmaf(Xr[q], D0[q], Sx[q] - Dx[q]), fmaf(Yr[q], D0[q], Sy[q] - Dy[q]),
@@ -790,10 +810,15 @@ static int build_tree(sbio_geom* g, TreeFar& T, cudaStream_t st) {
     e.erase(std::unique(e.begin(), e.end()), e.end());
   }
   const int tiles_per_part = (G + kFarTile - 1) / kFarTile;
-  std::vector<int4> dtiles, ditems, mitems;
-  std::vector<int> mlist;
+  std::vector<int4> dtiles, ditems, mitems[2];
+  std::vector<int> mlist[2];
   T.m2p_pairs = T.direct_pairs = T.m2p_source_pairs = 0;
-  std::vector<int> stack, dlist, epos;
+  std::vector<int> stack, dlist, epos, accepted;
+  std::vector<int> cls[2][3];   // accepted nodes of a group by operator and evaluation order 8, 12, 16
+  const double worst = std::pow(T.theta, T.order + 1);
+  const double margin[2] = {1.0, 0.1};
+  for (auto& L : T.ev_lists)
+    for (int64_t& v : L.evals_by_order) v = 0;
   for (int gi = 0; gi < n_groups; ++gi) {
     const int64_t t0 = groups[gi].x, t1 = groups[gi].y;
     if (t1 <= t0) continue;
@@ -814,7 +839,9 @@ static int build_tree(sbio_geom* g, TreeFar& T, cudaStream_t st) {
     for (int e : excl[gi]) epos.push_back(T.pos[e]);
     std::sort(epos.begin(), epos.end());
     dlist.clear();
-    const size_t m0 = mlist.size();
+    accepted.clear();
+    for (auto& op : cls)
+      for (auto& v : op) v.clear();
     stack.assign(1, 0);
     while (!stack.empty()) {
       const int id = stack.back();
@@ -825,7 +852,13 @@ static int build_tree(sbio_geom* g, TreeFar& T, cudaStream_t st) {
       const auto it = std::lower_bound(epos.begin(), epos.end(), nd.first);
       const bool holds_excluded = it != epos.end() && *it < nd.first + nd.count;
       if (!holds_excluded && dist >= rg + nd.r / T.theta) {
-        mlist.push_back(id);
+        const double rho = nd.r / (dist - rg);
+        accepted.push_back(id);
+        for (int op = 0; op < 2; ++op) {
+          int c = 0;
+          while (8 + 4 * c < T.order && std::pow(rho, 9 + 4 * c) > margin[op] * worst) ++c;
+          cls[op][c].push_back(id);
+        }
       } else if (nd.count == 1) {
         dlist.push_back(T.perm[nd.first]);
       } else {
@@ -833,10 +866,17 @@ static int build_tree(sbio_geom* g, TreeFar& T, cudaStream_t st) {
         stack.push_back(nd.child[0]);
       }
     }
-    T.m2p_pairs += (int64_t)(mlist.size() - m0) * (t1 - t0);
-    for (size_t k = m0; k < mlist.size(); ++k) T.m2p_source_pairs += (int64_t)T.nodes[mlist[k]].count * G * (t1 - t0);
-    for (size_t k = m0; k < mlist.size(); k += kTreeChunkNodes)
-      mitems.push_back(make_int4(gi, (int)k, (int)std::min(mlist.size(), k + kTreeChunkNodes), 0));
+    for (int op = 0; op < 2; ++op)
+      for (int c = 0; c < 3; ++c) {
+        std::vector<int>& ml = mlist[op];
+        const size_t k0 = ml.size();
+        ml.insert(ml.end(), cls[op][c].begin(), cls[op][c].end());
+        for (size_t k = k0; k < ml.size(); k += kTreeChunkNodes)
+          mitems[op].push_back(make_int4(gi, (int)k, (int)std::min(ml.size(), k + kTreeChunkNodes), c));
+        T.ev_lists[op].evals_by_order[c] += (int64_t)cls[op][c].size() * (t1 - t0);
+      }
+    T.m2p_pairs += (int64_t)accepted.size() * (t1 - t0);
+    for (int id : accepted) T.m2p_source_pairs += (int64_t)T.nodes[id].count * G * (t1 - t0);
     // direct list in ascending particle order (the kernel's skip-list walk needs it)
     std::sort(dlist.begin(), dlist.end());
     const int d0 = (int)dtiles.size();
@@ -849,11 +889,19 @@ static int build_tree(sbio_geom* g, TreeFar& T, cudaStream_t st) {
     for (int k = d0; k < (int)dtiles.size(); k += kTreeChunkTiles)
       ditems.push_back(make_int4(gi, k, std::min((int)dtiles.size(), k + kTreeChunkTiles), 0));
   }
-  T.m2p_entries = (int64_t)mlist.size();
+  T.m2p_entries = (int64_t)mlist[0].size();
   T.direct_tiles = (int64_t)dtiles.size();
-  // longest items first (the tail of the grid is then short)
+  // longest items first (the tail of the grid is then short), within each order class
   std::stable_sort(ditems.begin(), ditems.end(), [](const int4& a, const int4& b) { return a.z - a.y > b.z - b.y; });
-  std::stable_sort(mitems.begin(), mitems.end(), [](const int4& a, const int4& b) { return a.z - a.y > b.z - b.y; });
+  for (int op = 0; op < 2; ++op) {
+    std::vector<int4>& mi = mitems[op];
+    std::stable_sort(mi.begin(), mi.end(), [](const int4& a, const int4& b) {
+      return a.w != b.w ? a.w < b.w : a.z - a.y > b.z - b.y;
+    });
+    for (int c = 0; c <= 3; ++c)
+      T.ev_lists[op].off[c] =
+          (int)(std::lower_bound(mi.begin(), mi.end(), c, [](const int4& a, int cc) { return a.w < cc; }) - mi.begin());
+  }
   // device tables
   std::vector<double> geo(T.n_nodes * 4);
   std::vector<float4> c32(T.n_nodes * 2);
@@ -876,7 +924,7 @@ static int build_tree(sbio_geom* g, TreeFar& T, cudaStream_t st) {
   // depth-first pre-order, so a parent precedes its children); the top
   // levels, whose nodes are too large to be accepted, are skipped
   std::vector<char> needed(T.n_nodes, 0);
-  for (int id : mlist) needed[id] = 1;
+  for (int id : mlist[0]) needed[id] = 1;
   for (int id = 0; id < T.n_nodes; ++id)
     if (needed[id])
       for (int c : T.nodes[id].child)
@@ -901,10 +949,11 @@ static int build_tree(sbio_geom* g, TreeFar& T, cudaStream_t st) {
   if ((rc = upload_vec(g, T, &T.d_groups, groups, "tree target groups", st))) return rc;
   if ((rc = upload_vec(g, T, &T.d_tiles, dtiles, "tree direct tiles", st))) return rc;
   if ((rc = upload_vec(g, T, &T.d_ditems, ditems, "tree direct items", st))) return rc;
-  if ((rc = upload_vec(g, T, &T.d_mlist, mlist, "tree multipole lists", st))) return rc;
-  if ((rc = upload_vec(g, T, &T.d_mitems, mitems, "tree multipole items", st))) return rc;
+  for (int op = 0; op < 2; ++op) {
+    if ((rc = upload_vec(g, T, &T.ev_lists[op].d_mlist, mlist[op], "tree multipole lists", st))) return rc;
+    if ((rc = upload_vec(g, T, &T.ev_lists[op].d_mitems, mitems[op], "tree multipole items", st))) return rc;
+  }
   T.n_ditems = (int)ditems.size();
-  T.n_mitems = (int)mitems.size();
   if ((rc = dev_alloc(g, (void**)&T.d_M, sizeof(double2) * 2 * NM * (size_t)T.n_nodes, "tree multipoles"))) return rc;
   if ((rc = dev_alloc(g, (void**)&T.d_M32, sizeof(float2) * 2 * NM * (size_t)T.n_nodes, "tree multipoles (FP32)")))
     return rc;
@@ -947,11 +996,19 @@ static int tree_apply(sbio_geom* g, TreeFar& T, double* S, double* D, cudaStream
   if (timed) cudaEventRecord(T.ev[2], st);
   if (!forked) launch_far_tile_items(d, T.d_groups, T.d_tiles, T.d_ditems, T.n_ditems, S, D, st);
   if (timed) cudaEventRecord(T.ev[3], st);
-  if (T.n_mitems > 0) {
-    tree_m2p_kernel<PF><<<T.n_mitems, kFarTile, 0, st>>>(T.d_mitems, T.d_groups, T.d_mlist, T.d_c32, T.d_M32, d.tgt32,
-                                                         S, D);
+  // the evaluations, one launch per evaluation order (8, 12, 16 up to PF)
+  const TreeFar::EvalLists& L = T.ev_lists[0];
+  auto m2p = [&](auto pe, int c) {
+    constexpr int PE = decltype(pe)::value;
+    const int n = L.off[c + 1] - L.off[c];
+    if (n <= 0) return;
+    tree_m2p_kernel<PF, PE><<<n, kFarTile, 0, st>>>(L.d_mitems + L.off[c], T.d_groups, L.d_mlist, T.d_c32, T.d_M32,
+                                                    d.tgt32, S, D);
     count_launch();
-  }
+  };
+  m2p(std::integral_constant<int, 8>(), 0);
+  if constexpr (PF >= 12) m2p(std::integral_constant<int, 12>(), 1);
+  if constexpr (PF >= 16) m2p(std::integral_constant<int, 16>(), 2);
   if (timed) cudaEventRecord(T.ev[4], st);
   SBIO_CUDA_TRY(cudaGetLastError());
   SBIO_CUDA_TRY(sf.join());
@@ -1013,11 +1070,18 @@ static int tree_apply_stokes(sbio_geom* g, TreeFar& T, double* u, cudaStream_t s
   if (timed) cudaEventRecord(T.ev[2], st);
   if (!forked) launch_stokes_far_tile_items(d, T.d_groups, T.d_tiles, T.d_ditems, T.n_ditems, u, st);
   if (timed) cudaEventRecord(T.ev[3], st);
-  if (T.n_mitems > 0) {
-    tree_m2p_stokes_kernel<PF><<<T.n_mitems, kFarTile, 0, st>>>(T.d_mitems, T.d_groups, T.d_mlist, T.d_c32, T.d_SM32,
-                                                                plane, d.tgt32, u);
+  const TreeFar::EvalLists& L = T.ev_lists[1];
+  auto m2p = [&](auto pe, int c) {
+    constexpr int PE = decltype(pe)::value;
+    const int n = L.off[c + 1] - L.off[c];
+    if (n <= 0) return;
+    tree_m2p_stokes_kernel<PF, PE><<<n, kFarTile, 0, st>>>(L.d_mitems + L.off[c], T.d_groups, L.d_mlist, T.d_c32,
+                                                           T.d_SM32, plane, d.tgt32, u);
     count_launch();
-  }
+  };
+  m2p(std::integral_constant<int, 8>(), 0);
+  if constexpr (PF >= 12) m2p(std::integral_constant<int, 12>(), 1);
+  if constexpr (PF >= 16) m2p(std::integral_constant<int, 16>(), 2);
   if (timed) cudaEventRecord(T.ev[4], st);
   SBIO_CUDA_TRY(cudaGetLastError());
   SBIO_CUDA_TRY(sf.join());
@@ -1134,6 +1198,16 @@ int sbio_geom_tree_phase_times(sbio_geom* g, double* ms) {
     SBIO_CUDA_TRY(cudaEventElapsedTime(&t, g->tree->ev[k], g->tree->ev[k + 1]));
     ms[k] = t;
   }
+  return SBIO_OK;
+}
+
+int sbio_geom_tree_order_counts(const sbio_geom* g, int32_t op, int64_t* evals) {
+  clear_error();
+  if (!g || !evals) return set_error(SBIO_EINVAL, "null argument");
+  if (op != SBIO_OP_LAPLACE && op != SBIO_OP_STOKES) return set_error(SBIO_EINVAL, "operator %d unknown", op);
+  if (!g->tree) return set_error(SBIO_EINVAL, "the geometry's far field is the direct sum");
+  const TreeFar::EvalLists& L = g->tree->ev_lists[op == SBIO_OP_STOKES ? 1 : 0];
+  for (int c = 0; c < 3; ++c) evals[c] = L.evals_by_order[c];
   return SBIO_OK;
 }
 

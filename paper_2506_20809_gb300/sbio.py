@@ -108,6 +108,7 @@ _SIGS = {
     "sbio_geom_set_overlap": (C.c_int, [_vp, C.c_int32]),
     "sbio_geom_set_near_cap": (C.c_int, [_vp, C.c_int32]),
     "sbio_geom_set_tree_near_cap": (C.c_int, [_vp, C.c_int32]),
+    "sbio_geom_tree_order_counts": (C.c_int, [_vp, C.c_int32, C.POINTER(C.c_int64)]),
     "sbio_geom_get_tree_near_cap": (C.c_int, [_vp, C.POINTER(C.c_int32)]),
     "sbio_geom_get_tuning": (C.c_int, [_vp, C.POINTER(C.c_int32), C.POINTER(C.c_int32), C.POINTER(C.c_int32)]),
     "sbio_geom_autotune": (C.c_int, [_vp, _vp, C.POINTER(C.c_int32), C.POINTER(C.c_int32),
@@ -503,6 +504,14 @@ def sbio_geom_tree_info(g):
     _check(_lib.sbio_geom_tree_info(g, C.byref(a), C.byref(b), C.byref(c), C.byref(d), C.byref(e)))
     return {"nodes": a.value, "groups": b.value, "m2p_pairs": c.value, "m2p_source_pairs": d.value,
             "direct_pairs": e.value}
+
+
+def sbio_geom_tree_order_counts(g, op=0):
+    """(target, multipole node) evaluations per apply of operator `op`
+    (SBIO_OP_LAPLACE or SBIO_OP_STOKES) at orders 8, 12, 16."""
+    a = (C.c_int64 * 3)()
+    _check(_lib.sbio_geom_tree_order_counts(g, op, a))
+    return {8: a[0], 12: a[1], 16: a[2]}
 
 
 def sbio_geom_near_work(g):

@@ -57,6 +57,18 @@ def test_tree_matches_fp64_direct(S, ctx, M, p, seed):
         info = S.sbio_geom_tree_info(g.h)
         assert info["nodes"] == 2 * M - 1
         assert info["m2p_source_pairs"] + info["direct_pairs"] == g.n_far
+        # evaluations split by order, none above the treecode's order
+        oc = S.sbio_geom_tree_order_counts(g.h, S.SBIO_OP_LAPLACE)
+        ocs = S.sbio_geom_tree_order_counts(g.h, S.SBIO_OP_STOKES)
+        assert sum(oc.values()) == info["m2p_pairs"] == sum(ocs.values())
+        assert all(v == 0 for e, v in oc.items() if e > order)
+        assert all(v == 0 for e, v in ocs.items() if e > order)
+        # the Stokes lists keep a tenfold margin: never a lower order than Laplace's
+        assert ocs[8] <= oc[8] and ocs[8] + ocs[12] <= oc[8] + oc[12]
+        if order == 16 and M >= 90:
+            assert oc[8] > 0 and oc[12] > 0 and oc[16] > 0
+        with pytest.raises(S.SbioError):
+            S.sbio_geom_tree_order_counts(g.h, 7)
         St, Dt = _apply(S, g, c)
         eS, eD = OL.normwise_rel_err(St, S64), OL.normwise_rel_err(Dt, D64)
         print(f"M={M} p={p} order={order} theta={theta}: S {eS:.2e} D {eD:.2e}, "
