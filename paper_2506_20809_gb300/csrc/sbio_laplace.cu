@@ -713,11 +713,11 @@ int tune_near_cap(sbio_geom* g, const TuneOps& ops, double* out, cudaStream_t st
     return set_error(SBIO_ECUDA, "event create failed");
   }
   // whole applies, median of five after one warm-up, per cap
-  const int caps[7] = {1, 2, 3, 4, 6, 8, 0};
+  const int caps[6] = {1, 2, 3, 4, 8, 0};
   float best_apply = 1e30f;
   int best_cap = *ops.cap;
   int rc = SBIO_OK;
-  for (int c = 0; c < 7 && !rc; ++c) {
+  for (int c = 0; c < 6 && !rc; ++c) {
     if (caps[c] != 0 && caps[c] < ops.min_cap) continue;
     *ops.cap = caps[c];
     rc = ops.whole(g, out, st);

@@ -248,7 +248,7 @@ def test_tree_forked_phases_equal_in_order(S, ctx):
     g = S.Geometry(ctx, s, precision=S.SBIO_MIXED)
     S.sbio_geom_set_near_cap(g.h, 1)
     S.sbio_geom_set_far_method(g.h, S.SBIO_FAR_TREE, 0.5, 16)
-    assert S.sbio_geom_get_tree_near_cap(g.h) in (0, 1, 2, 3, 4, 6, 8)
+    assert S.sbio_geom_get_tree_near_cap(g.h) in (0, 1, 2, 3, 4, 8)
     assert S.sbio_geom_get_tuning(g.h)["near_ctas_per_sm"] == 1
     outs = {}
     for cap in (1, 3):
