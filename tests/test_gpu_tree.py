@@ -45,7 +45,7 @@ def _apply(S, g, c):
     return So.cpu().numpy(), Do.cpu().numpy()
 
 
-@pytest.mark.parametrize("M,p,seed", [(60, 8, 31), (120, 12, 32), (90, 16, 33)])
+@pytest.mark.parametrize("M,p,seed", [(60, 8, 31), (120, 12, 32), (90, 16, 33), (50, 20, 34)])
 def test_tree_matches_fp64_direct(S, ctx, M, p, seed):
     s = I.rsa_suspension(M, 0.20, seed, p, name="tree")
     c = I.config_coefficients(s, seed)
@@ -201,7 +201,7 @@ def _stokes(S, g, f):
     return u.cpu().numpy()
 
 
-@pytest.mark.parametrize("M,p,seed", [(50, 8, 51), (100, 12, 52)])
+@pytest.mark.parametrize("M,p,seed", [(50, 8, 51), (100, 12, 52), (60, 20, 53)])
 def test_stokes_tree_matches_fp64_direct(S, ctx, M, p, seed):
     """The Stokes single layer with the treecode far field (four charge and
     four dipole channels per node) against the plain FP64 direct apply."""
