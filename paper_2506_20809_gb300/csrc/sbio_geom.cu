@@ -704,6 +704,8 @@ static int build_device(sbio_geom* g) {
   if ((rc = dev_alloc(g, (void**)&d.src32, (size_t)N * 2 * sizeof(float4), "fp32 sources"))) return rc;
   if ((rc = dev_alloc(g, (void**)&d.alpha, (size_t)M * nc * sizeof(double), "near S coefficients"))) return rc;
   if ((rc = dev_alloc(g, (void**)&d.beta, (size_t)M * nc * sizeof(double), "near D coefficients"))) return rc;
+  if ((rc = dev_alloc(g, (void**)&d.alpha32, (size_t)M * nc * sizeof(float), "near S coefficients (FP32)"))) return rc;
+  if ((rc = dev_alloc(g, (void**)&d.beta32, (size_t)M * nc * sizeof(float), "near D coefficients (FP32)"))) return rc;
   if ((rc = dev_alloc(g, (void**)&d.host_in, (size_t)3 * M * nc * sizeof(double), "host staging"))) return rc;
   if ((rc = dev_alloc(g, (void**)&d.host_out, (size_t)3 * N * sizeof(double), "host staging"))) return rc;
   SBIO_CUDA_TRY(cudaStreamSynchronize(g->setup_stream));

@@ -50,6 +50,8 @@ struct DevGeom {
   float4* src32 = nullptr;       // N x 2: (y - c_own, q), (d, 0)
   double* alpha = nullptr;       // M x (p+1)^2 folded exterior S coefficients
   double* beta = nullptr;        // M x (p+1)^2 folded exterior D coefficients
+  float* alpha32 = nullptr;      // M x (p+1)^2: sigma (the mixed near form's S coefficients)
+  float* beta32 = nullptr;       // M x (p+1)^2: mu extD / extS (its D coefficients)
   double* host_in = nullptr;     // 2 x M x (p+1)^2 staging for the host-memory entry point
   double* host_out = nullptr;    // 2 x N
   // Stokes single layer (Sec. 4.3): tables, pairs and workspaces
@@ -159,7 +161,8 @@ void geom_destroy_async(sbio_geom* g, cudaStream_t st);
 int dev_alloc(sbio_geom* g, void** ptr, size_t bytes, const char* what);
 
 struct DevGeom;
-typedef void (*near_launcher)(const DevGeom&, int64_t, int64_t, const double*, double*, double*, cudaStream_t);
+// mixed: the FP32-contraction form (SBIO_MIXED geometries), else plain FP64
+typedef void (*near_launcher)(const DevGeom&, int64_t, int64_t, const double*, double*, double*, bool, cudaStream_t);
 near_launcher near_lookup_a(int p);
 near_launcher near_lookup_b(int p);
 near_launcher near_lookup_c(int p);

@@ -42,7 +42,8 @@ __device__ __forceinline__ void synth_particle(int i, double* sm, int p, int n_v
                                                const double* __restrict__ mu, int write_self, int side,
                                                double* __restrict__ S_out, double* __restrict__ D_out,
                                                double* __restrict__ src64, float4* __restrict__ src32,
-                                               double* __restrict__ alpha, double* __restrict__ beta) {
+                                               double* __restrict__ alpha, double* __restrict__ beta,
+                                               float* __restrict__ alpha32, float* __restrict__ beta32) {
   const int nc = (p + 1) * (p + 1), nm = nm_count(p), nmw = 2 * p + 1;
   const int G = n_v * n_phi;
   double* c_sig = sm;                 // nc
@@ -60,6 +61,11 @@ __device__ __forceinline__ void synth_particle(int i, double* sm, int p, int n_v
     c_mu[k] = cmu;
     alpha[(size_t)i * nc + k] = mlt[0 * nm + nm_index(n, am)] * normc[k] * cs;
     beta[(size_t)i * nc + k] = mlt[1 * nm + nm_index(n, am)] * normc[k] * cmu;
+    // the mixed near form's coefficients: alpha = extS N sigma, beta = extS N (mu extD / extS)
+    if (alpha32) {
+      alpha32[(size_t)i * nc + k] = (float)cs;
+      beta32[(size_t)i * nc + k] = (float)(cmu * (mlt[1 * nm + nm_index(n, am)] / mlt[0 * nm + nm_index(n, am)]));
+    }
   }
   __syncthreads();
   // stage 1: Legendre sums  F[j][m] = sum_n c_nm sqrt2^[m!=0] N P(v_j)
@@ -133,10 +139,11 @@ __global__ void __launch_bounds__(256) synth_kernel(int p, int n_v, int n_phi, c
                                                     int write_self, int side, double* __restrict__ S_out,
                                                     double* __restrict__ D_out, double* __restrict__ src64,
                                                     float4* __restrict__ src32, double* __restrict__ alpha,
-                                                    double* __restrict__ beta) {
+                                                    double* __restrict__ beta, float* __restrict__ alpha32,
+                                                    float* __restrict__ beta32) {
   extern __shared__ double sm[];
   synth_particle(blockIdx.x, sm, p, n_v, n_phi, parts, xyz, nrm, w, ptab, trig, sqrtw, mult, normc, sigma, mu,
-                 write_self, side, S_out, D_out, src64, src32, alpha, beta);
+                 write_self, side, S_out, D_out, src64, src32, alpha, beta, alpha32, beta32);
 }
 
 // ---------------------------------------------------------------------------
@@ -593,7 +600,7 @@ int launch_synth_mode(sbio_geom* g, const double* sigma, const double* mu, doubl
   }
   synth_kernel<<<h.M, 256, smem, st>>>(h.p, h.n_v, h.n_phi, d.parts, d.xyz, d.nrm, d.w, d.ptab, d.trig, d.sqrtw,
                                        mult, d.normc, sigma, mu, self_mode, side, S, D, d.src64, d.src32,
-                                       d.alpha, d.beta);
+                                       d.alpha, d.beta, d.alpha32, d.beta32);
   count_launch();
   SBIO_CUDA_TRY(cudaGetLastError());
   return SBIO_OK;
@@ -609,7 +616,7 @@ int launch_near(sbio_geom* g, double* S, double* D, cudaStream_t st) {
   if (h.pair_t.empty()) return SBIO_OK;
   near_launcher f = near_for_p(h.p);
   if (!f) return set_error(SBIO_ENOTSUP, "no near-field kernel for p = %d", h.p);
-  f(g->d, h.n_pairs_prolate, (int64_t)h.pair_t.size(), g->d.inv, S, D, st);
+  f(g->d, h.n_pairs_prolate, (int64_t)h.pair_t.size(), g->d.inv, S, D, h.precision == SBIO_MIXED, st);
   SBIO_CUDA_TRY(cudaGetLastError());
   return SBIO_OK;
 }

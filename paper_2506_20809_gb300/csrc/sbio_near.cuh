@@ -146,4 +146,104 @@ __device__ __forceinline__ void near_pair(double xl, double yl, double zl, doubl
   D = accD;
 }
 
+// Mixed-precision form for SBIO_MIXED geometries.  The coordinates, the
+// Miller sweep and the order recurrence of the Q family stay FP64 as in
+// near_pair; each radial value enters as rho_nm = extS_nm q_n^m(u), the
+// exterior S multiplier times Q (of order one for a target outside the
+// source, since Q decreases away from the surface), rounded to FP32.  The
+// Ferrers functions run normalised in FP32, Pbar_n^m = N_n^m P_n^m with N the
+// surface-harmonic normalisation (sqrt 2 for m != 0), by the three-term
+// recurrence in n; the n sums run in FP32 with TwoSum compensation, the m
+// sums with the angle recurrence in FP64.  Coefficients A = sigma and
+// B = mu extD / extS in FP32, so that alpha q P = A rho Pbar and
+// beta q P = B rho Pbar term by term.  On GB300 the FP64 pipe runs at 1/64
+// of the FP32 rate; this form issues about 1,200 FP64 instructions per pair
+// at p = 16 against about 2,050.
+template <int P>
+struct PbarTab {
+  float mm[P + 1];                  // Pbar_m^m = mm[m] sv Pbar_{m-1}^{m-1} (m >= 1); mm[0] = Pbar_0^0
+  float a[(P + 1) * (P + 2) / 2];   // Pbar_n^m = a v Pbar_{n-1}^m - b Pbar_{n-2}^m, at nm_index(n, m)
+  float b[(P + 1) * (P + 2) / 2];   // (a used for n >= m + 1, b for n >= m + 2, zero below)
+};
+
+template <int P, int KIND, bool DO_S, bool DO_D>
+__device__ __forceinline__ void near_pair_mixed(double xl, double yl, double zl, double a,
+                                                const float* __restrict__ A32, const float* __restrict__ B32,
+                                                const double* __restrict__ extS, const double* __restrict__ inv_tab,
+                                                const PbarTab<P>& tab, double& S, double& D) {
+  constexpr double sgn = (KIND == SBIO_PROLATE) ? -1.0 : 1.0;
+  const SphCoord sc = to_spheroidal(xl, yl, zl, a, KIND);
+  const double u = sc.u;
+  const float v32 = (float)sc.v, sv32 = (float)sc.sv;
+  const double rsu = rsqrt(u * u + sgn);
+  double qa[P + 2], qb[P + 2];   // Q^{m-1}, Q^{m-2} (rotating roles)
+  miller_q01<P, KIND>(u, rsu, inv_tab, qb, qa);   // qb = Q^0, qa = Q^1
+  const double c = u * rsu;
+  double cm = 1.0, sm = 0.0;
+  const double c1 = sc.cph, s1 = sc.sph;
+  float pmm = tab.mm[0];                          // Pbar_m^m(v)
+  double accS = 0.0, accD = 0.0;
+#pragma unroll
+  for (int m = 0; m <= P; ++m) {
+    double* qm;
+    if (m == 0) {
+      qm = qb;
+    } else if (m == 1) {
+      qm = qa;
+    } else {
+      double* q1p = (m & 1) ? qb : qa;
+      double* q2p = (m & 1) ? qa : qb;
+      const double cc = -2.0 * (m - 1) * c;
+#pragma unroll
+      for (int n = m; n <= P; ++n) q2p[n] = cc * q1p[n] + ((n - m + 2.0) * (n + m - 1.0)) * q2p[n];
+      qm = q2p;
+    }
+    if (m > 0) pmm *= tab.mm[m] * sv32;
+    float Sc = 0.f, Scl = 0.f, Ss = 0.f, Ssl = 0.f, Dc = 0.f, Dcl = 0.f, Ds = 0.f, Dsl = 0.f;
+    float pprev = 0.f, pcur = pmm;
+#pragma unroll
+    for (int n = m; n <= P; ++n) {
+      const float T = (float)(extS[nm_index(n, m)] * qm[n]) * pcur;
+      float s, e;
+      if (DO_S) {
+        two_sum_f32(Sc, A32[n * n + n + m] * T, s, e);
+        Sc = s;
+        Scl += e;
+        if (m > 0) {
+          two_sum_f32(Ss, A32[n * n + n - m] * T, s, e);
+          Ss = s;
+          Ssl += e;
+        }
+      }
+      if (DO_D) {
+        two_sum_f32(Dc, B32[n * n + n + m] * T, s, e);
+        Dc = s;
+        Dcl += e;
+        if (m > 0) {
+          two_sum_f32(Ds, B32[n * n + n - m] * T, s, e);
+          Ds = s;
+          Dsl += e;
+        }
+      }
+      if (n < P) {
+        const float pnext = fmaf(tab.a[nm_index(n + 1, m)] * v32, pcur, -tab.b[nm_index(n + 1, m)] * pprev);
+        pprev = pcur;
+        pcur = pnext;
+      }
+    }
+    if (m == 0) {
+      accS += (double)(Sc + Scl);
+      accD += (double)(Dc + Dcl);
+    } else {
+      accS = fma((double)(Sc + Scl), cm, fma((double)(Ss + Ssl), sm, accS));
+      accD = fma((double)(Dc + Dcl), cm, fma((double)(Ds + Dsl), sm, accD));
+    }
+    const double cn = cm * c1 - sm * s1;
+    sm = sm * c1 + cm * s1;
+    cm = cn;
+  }
+  S = accS;
+  D = accD;
+}
+
 }  // namespace sbio

@@ -32,7 +32,8 @@ __global__ void synth_kernel(int p, int n_v, int n_phi, const PartGeom* __restri
                              const double* __restrict__ sigma, const double* __restrict__ mu, int write_self,
                              int side, double* __restrict__ S_out, double* __restrict__ D_out,
                              double* __restrict__ src64,
-                             float4* __restrict__ src32, double* __restrict__ alpha, double* __restrict__ beta);
+                             float4* __restrict__ src32, double* __restrict__ alpha, double* __restrict__ beta,
+                             float* __restrict__ alpha32, float* __restrict__ beta32);
 
 constexpr size_t kNoAllocScratchBytes = size_t(8) << 20;
 
@@ -207,7 +208,7 @@ extern "C" int sbio_apply_self_noalloc(const sbio_spheroid* sph, int32_t M, int3
       reinterpret_cast<const double*>(b + o_sqrtw), reinterpret_cast<const double*>(b + o_mult),
       reinterpret_cast<const double*>(b + o_normc), sigma_tilde, mu_hat, 1, 0, S_out, D_out,
       reinterpret_cast<double*>(b + o_src64), reinterpret_cast<float4*>(b + o_src32),
-      reinterpret_cast<double*>(b + o_alpha), reinterpret_cast<double*>(b + o_beta));
+      reinterpret_cast<double*>(b + o_alpha), reinterpret_cast<double*>(b + o_beta), nullptr, nullptr);
   count_launch();
   SBIO_CUDA_TRY(cudaGetLastError());
   return SBIO_OK;

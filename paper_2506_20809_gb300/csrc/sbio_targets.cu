@@ -218,11 +218,11 @@ int sbio_eval_targets(sbio_targets* ts, const double* sigma_tilde, const double*
   if (fork) {
     SBIO_CUDA_TRY(sf.fork(g, st));
     ts->view.near_grid_cap = h.near_ctas_per_sm > 0 ? h.near_ctas_per_sm * sm_count() : 0;
-    nl(ts->view, ts->n_pro, ts->n_pairs, ts->view.inv, S_out, D_out, g->near_stream);
+    nl(ts->view, ts->n_pro, ts->n_pairs, ts->view.inv, S_out, D_out, h.precision == SBIO_MIXED, g->near_stream);
     ts->view.near_grid_cap = 0;
     SBIO_CUDA_TRY(cudaGetLastError());
   } else if (ts->n_pairs > 0) {
-    nl(ts->view, ts->n_pro, ts->n_pairs, ts->view.inv, S_out, D_out, st);
+    nl(ts->view, ts->n_pro, ts->n_pairs, ts->view.inv, S_out, D_out, h.precision == SBIO_MIXED, st);
     SBIO_CUDA_TRY(cudaGetLastError());
   }
   launch_far_on(ts->view, h, ts->T, S_out, D_out, st);
