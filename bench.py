@@ -610,8 +610,9 @@ def run_ours(args, ws, rank, lrank):
         "near_mixed": {"kernel": "near_kernel_mixed", "ms": near_mean,
                        "pairs_per_s": n_pairs / (near_mean * 1e-3),
                        "speedup_vs_fp64_near": (near64_ms / near_mean) if near64_ms else None,
-                       "note": "coordinates, Miller sweep and Q order recurrence in FP64; rho = extS q rounded to "
-                               "FP32, normalised Ferrers recurrence and compensated n sums in FP32, m sums in FP64"}
+                       "note": "coordinates, Miller sweep, Q order recurrence and angle recurrence in FP64; "
+                               "rho = extS q rounded to FP32, normalised Ferrers recurrence and TwoSum-compensated "
+                               "n and m sums in FP32"}
         if prec == S.SBIO_MIXED else None,
         "measured_peaks": peaks,
         "e2e": {"value": e2e_val, "unit": "applies/s", "h2d_bytes_per_step": int(hs.nbytes + hm.nbytes),

@@ -29,12 +29,15 @@ struct sbio_batch {
   int n_tree = 0;                      // suspensions whose far field is the treecode
   int64_t far_pairs = 0;
   cudaStream_t sa = nullptr, sb = nullptr;
-  cudaEvent_t ev_fork = nullptr, ev_synth = nullptr, ev_near = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_near = nullptr;
   // near branch: the suspensions' near kernels spread over several streams so
   // that their small grids run side by side in the far kernel's spare slots
   static constexpr int kNearStreams = 8;
   cudaStream_t sn[kNearStreams] = {};
   cudaEvent_t ev_nj[kNearStreams] = {};
+  // the same streams run the suspensions' synthesis kernels (small grids, one
+  // per suspension) side by side first; the far kernel waits for all of them
+  cudaEvent_t ev_sj[kNearStreams] = {};
   cudaGraphExec_t exec = nullptr;
   std::vector<const void*> captured;   // buffers baked into the graph
   int kernels_per_apply = 0;           // kernel nodes of the captured graph
@@ -99,18 +102,38 @@ static int capture(sbio_batch* b, const double* const* sigma, const double* cons
   int rc = SBIO_OK;
   cudaEventRecord(b->ev_fork, b->sa);
   cudaStreamWaitEvent(b->sb, b->ev_fork, 0);
-  for (size_t s = 0; s < b->geoms.size() && !rc; ++s) rc = launch_synth(b->geoms[s], sigma[s], mu[s], S[s], D[s], true, b->sa);
-  cudaEventRecord(b->ev_synth, b->sa);
-  for (int k = 0; k < sbio_batch::kNearStreams; ++k) cudaStreamWaitEvent(b->sn[k], b->ev_synth, 0);
-  // suspensions with a treecode far field run it on the near streams, beside
-  // the persistent direct kernel of the others, followed by their near field
-  for (size_t s = 0; s < b->geoms.size() && !rc; ++s) {
-    cudaStream_t ns = b->sn[s % sbio_batch::kNearStreams];
+  for (int k = 0; k < sbio_batch::kNearStreams; ++k) cudaStreamWaitEvent(b->sn[k], b->ev_fork, 0);
+  // branch of each suspension: longest first to the least loaded stream, by
+  // a cost of M (p + 1)^2 (the synthesis and near work both grow with it)
+  const size_t ns_count = b->geoms.size();
+  std::vector<int> branch(ns_count, 0), order(ns_count);
+  for (size_t s = 0; s < ns_count; ++s) order[s] = (int)s;
+  auto cost = [&](int s) { const GeomHost& h = b->geoms[s]->h; return (double)h.M * (h.p + 1) * (h.p + 1); };
+  std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return cost(x) > cost(y); });
+  double load[sbio_batch::kNearStreams] = {};
+  for (int s : order) {
+    int k = 0;
+    for (int j = 1; j < sbio_batch::kNearStreams; ++j)
+      if (load[j] < load[k]) k = j;
+    branch[s] = k;
+    load[k] += cost(s);
+  }
+  // synthesis of every suspension on its branch, then the far kernel waits
+  // for all branches' synthesis
+  for (size_t s = 0; s < ns_count && !rc; ++s)
+    rc = launch_synth(b->geoms[s], sigma[s], mu[s], S[s], D[s], true, b->sn[branch[s]]);
+  for (int k = 0; k < sbio_batch::kNearStreams; ++k) {
+    cudaEventRecord(b->ev_sj[k], b->sn[k]);
+    cudaStreamWaitEvent(b->sa, b->ev_sj[k], 0);
+  }
+  // suspensions with a treecode far field run it on their branch, beside the
+  // persistent direct kernel of the others, followed by their near field
+  for (size_t s = 0; s < ns_count && !rc; ++s) {
+    cudaStream_t ns = b->sn[branch[s]];
     if (b->geoms[s]->tree) rc = launch_tree_far(b->geoms[s], S[s], D[s], ns);
     if (!rc) rc = launch_near(b->geoms[s], S[s], D[s], ns);
   }
   for (int k = 0; k < sbio_batch::kNearStreams; ++k) cudaEventRecord(b->ev_nj[k], b->sn[k]);
-  cudaStreamWaitEvent(b->sb, b->ev_synth, 0);   // the fork stream joins too (unused otherwise)
   cudaEventRecord(b->ev_near, b->sb);
   if (!rc) cudaMemsetAsync(b->d_counter, 0, sizeof(int), b->sa);
   if (!rc && b->n_items > 0)
@@ -173,11 +196,11 @@ int sbio_batch_create(sbio_ctx* ctx, sbio_geom* const* geoms, int32_t n, sbio_ba
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->sa, cudaStreamNonBlocking);
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->sb, cudaStreamNonBlocking);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev_fork, cudaEventDisableTiming);
-  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev_synth, cudaEventDisableTiming);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev_near, cudaEventDisableTiming);
   for (int k = 0; k < sbio_batch::kNearStreams && e == cudaSuccess; ++k) {
     e = cudaStreamCreateWithFlags(&b->sn[k], cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev_nj[k], cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev_sj[k], cudaEventDisableTiming);
   }
   int rc = (e == cudaSuccess) ? build_items(b) : set_error(SBIO_ENOMEM, "batch allocation failed: %s", cudaGetErrorString(e));
   if (rc) {
@@ -199,11 +222,11 @@ int sbio_batch_destroy(sbio_batch* b) {
   if (b->sa) cudaStreamDestroy(b->sa);
   if (b->sb) cudaStreamDestroy(b->sb);
   if (b->ev_fork) cudaEventDestroy(b->ev_fork);
-  if (b->ev_synth) cudaEventDestroy(b->ev_synth);
   if (b->ev_near) cudaEventDestroy(b->ev_near);
   for (int k = 0; k < sbio_batch::kNearStreams; ++k) {
     if (b->sn[k]) cudaStreamDestroy(b->sn[k]);
     if (b->ev_nj[k]) cudaEventDestroy(b->ev_nj[k]);
+    if (b->ev_sj[k]) cudaEventDestroy(b->ev_sj[k]);
   }
   delete b;
   return SBIO_OK;

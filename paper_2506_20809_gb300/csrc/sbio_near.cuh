@@ -153,12 +153,13 @@ __device__ __forceinline__ void near_pair(double xl, double yl, double zl, doubl
 // source, since Q decreases away from the surface), rounded to FP32.  The
 // Ferrers functions run normalised in FP32, Pbar_n^m = N_n^m P_n^m with N the
 // surface-harmonic normalisation (sqrt 2 for m != 0), by the three-term
-// recurrence in n; the n sums run in FP32 with TwoSum compensation, the m
-// sums with the angle recurrence in FP64.  Coefficients A = sigma and
-// B = mu extD / extS in FP32, so that alpha q P = A rho Pbar and
-// beta q P = B rho Pbar term by term.  On GB300 the FP64 pipe runs at 1/64
-// of the FP32 rate; this form issues about 1,200 FP64 instructions per pair
-// at p = 16 against about 2,050.
+// recurrence in n; the n and m sums run in FP32 with TwoSum compensation,
+// the angle recurrence in FP64 (cos and sin of m phi rounded once per m).
+// Coefficients A = sigma and B = mu extD / extS in FP32, so that
+// alpha q P = A rho Pbar and beta q P = B rho Pbar term by term.  On GB300
+// the FP64 pipe runs at 1/64 of the FP32 rate (conversions between the two
+// formats included); this form issues about 1,100 FP64-pipe instructions
+// per pair at p = 16 against about 2,050.
 template <int P>
 struct PbarTab {
   float mm[P + 1];                  // Pbar_m^m = mm[m] sv Pbar_{m-1}^{m-1} (m >= 1); mm[0] = Pbar_0^0
@@ -182,7 +183,7 @@ __device__ __forceinline__ void near_pair_mixed(double xl, double yl, double zl,
   double cm = 1.0, sm = 0.0;
   const double c1 = sc.cph, s1 = sc.sph;
   float pmm = tab.mm[0];                          // Pbar_m^m(v)
-  double accS = 0.0, accD = 0.0;
+  float aSh = 0.f, aSl = 0.f, aDh = 0.f, aDl = 0.f;   // compensated m sums
 #pragma unroll
   for (int m = 0; m <= P; ++m) {
     double* qm;
@@ -231,19 +232,35 @@ __device__ __forceinline__ void near_pair_mixed(double xl, double yl, double zl,
         pcur = pnext;
       }
     }
-    if (m == 0) {
-      accS += (double)(Sc + Scl);
-      accD += (double)(Dc + Dcl);
-    } else {
-      accS = fma((double)(Sc + Scl), cm, fma((double)(Ss + Ssl), sm, accS));
-      accD = fma((double)(Dc + Dcl), cm, fma((double)(Ds + Dsl), sm, accD));
+    // the angle factors come from the FP64 recurrence, rounded once per order
+    const float cmf = (float)cm, smf = (float)sm;
+    float s2, e2;
+    if (DO_S) {
+      two_sum_f32(aSh, (Sc + Scl) * cmf, s2, e2);
+      aSh = s2;
+      aSl += e2;
+      if (m > 0) {
+        two_sum_f32(aSh, (Ss + Ssl) * smf, s2, e2);
+        aSh = s2;
+        aSl += e2;
+      }
+    }
+    if (DO_D) {
+      two_sum_f32(aDh, (Dc + Dcl) * cmf, s2, e2);
+      aDh = s2;
+      aDl += e2;
+      if (m > 0) {
+        two_sum_f32(aDh, (Ds + Dsl) * smf, s2, e2);
+        aDh = s2;
+        aDl += e2;
+      }
     }
     const double cn = cm * c1 - sm * s1;
     sm = sm * c1 + cm * s1;
     cm = cn;
   }
-  S = accS;
-  D = accD;
+  S = (double)aSh + (double)aSl;
+  D = (double)aDh + (double)aDl;
 }
 
 }  // namespace sbio
