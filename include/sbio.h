@@ -56,7 +56,11 @@ extern "C" {
 
 #define SBIO_FP64 0   /* every kernel in FP64 */
 #define SBIO_MIXED 1  /* far-field pair sums in FP32 with two-sum compensated
-                         accumulation, near field and self term in FP64 */
+                         accumulation; self term in FP64; the S + D near
+                         field with coordinates, Q recurrences and angles in
+                         FP64 and the Ferrers recurrence and the
+                         contraction in compensated FP32 (the derivative,
+                         Stokes and double-layer near fields stay FP64) */
 
 #define SBIO_PART_SELF 1u  /* on-surface self interaction (Sec. 4.1 "Near-field") */
 #define SBIO_PART_NEAR 2u  /* neighbour particles by the exterior expansion */
@@ -232,7 +236,7 @@ int sbio_geom_get_tuning(const sbio_geom* g, int32_t* far_tt, int32_t* far_split
  * caller data afterwards. */
 int sbio_geom_autotune(sbio_geom* g, void* stream, int32_t* far_tt, int32_t* far_splits, double* far_ms);
 
-/* Near/far overlap (default on): the FP64 near-field kernels of an apply run
+/* Near/far overlap (default on): the near-field kernels of an apply run
  * on a high-priority stream forked from the caller's stream, beside the FP32
  * far-field kernel, and are joined back before the call's work ends on the
  * caller's stream.  Phase timing (sbio_geom_enable_timing) runs the phases in
