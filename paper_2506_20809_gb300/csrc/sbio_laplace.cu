@@ -220,12 +220,13 @@ __global__ void __launch_bounds__(kFarTile) far_fp64_kernel(const int4* __restri
 // their own centre, so the FP32 difference X - y_rel carries an error
 // relative to |x - y| rather than to the box size.  Each tile's FP32 partial
 // sum is folded into an (hi, lo) pair by TwoSum.
-// One CTA: targets [t_first, min(t_end, t_first + kFarTile * TT)) (TT per
-// thread, target t_first + tid + q kFarTile) against source tiles [t_lo, t_hi).  Only the target positions
+// One CTA of NT threads: targets [t_first, min(t_end, t_first + NT * TT)) (TT per
+// thread, target t_first + tid + q NT) against source tiles [t_lo, t_hi) of up
+// to kFarTile sources.  Only the target positions
 // relative to the current source particle and the running tile partials live
 // in registers; the two-sum accumulators and the skip-list cursors live in
 // shared memory and are touched once per tile.
-template <int TT, bool DO_S, bool DO_D, bool PK>
+template <int TT, bool DO_S, bool DO_D, bool PK, int NT = kFarTile>
 __device__ __forceinline__ void far_mixed_block(int64_t t_first, int64_t t_end, int t_lo, int t_hi,
                                                 const int4* __restrict__ tiles, const float4* __restrict__ src32,
                                                 const float4* __restrict__ tgt32, const float4* __restrict__ cen32,
@@ -238,20 +239,20 @@ __device__ __forceinline__ void far_mixed_block(int64_t t_first, int64_t t_end, 
   // 13; per source it holds every value duplicated into an f32x2 pair:
   // (-2y.x, -2y.y), (-2y.z, |y|^2), (q, -d.y), (d.x, d.y), (d.z, 0)
   __shared__ float4 sh[(PK ? 5 : 2) * kFarTile];
-  __shared__ float acc[4 * TT * kFarTile];   // per target: S hi, S lo, D hi, D lo
-  __shared__ int cursor[2 * TT * kFarTile];  // per target: skip-list position, next skipped particle
+  __shared__ float acc[4 * TT * NT];   // per target: S hi, S lo, D hi, D lo
+  __shared__ int cursor[2 * TT * NT];  // per target: skip-list position, next skipped particle
   const int tid = threadIdx.x;
   const int64_t t0 = t_first + tid;
 #pragma unroll
   for (int q = 0; q < TT; ++q) {
-    const int64_t t = t0 + (int64_t)q * kFarTile;
-    acc[(4 * q + 0) * kFarTile + tid] = 0.f;
-    acc[(4 * q + 1) * kFarTile + tid] = 0.f;
-    acc[(4 * q + 2) * kFarTile + tid] = 0.f;
-    acc[(4 * q + 3) * kFarTile + tid] = 0.f;
+    const int64_t t = t0 + (int64_t)q * NT;
+    acc[(4 * q + 0) * NT + tid] = 0.f;
+    acc[(4 * q + 1) * NT + tid] = 0.f;
+    acc[(4 * q + 2) * NT + tid] = 0.f;
+    acc[(4 * q + 3) * NT + tid] = 0.f;
     const int sp = (t < t_end) ? skip_ptr[t] : 0;
-    cursor[(2 * q + 0) * kFarTile + tid] = sp;
-    cursor[(2 * q + 1) * kFarTile + tid] = (t < t_end) ? skip_idx[sp] : INT32_MAX;
+    cursor[(2 * q + 0) * NT + tid] = sp;
+    cursor[(2 * q + 1) * NT + tid] = (t < t_end) ? skip_idx[sp] : INT32_MAX;
   }
   float X[TT], Y[TT], Z[TT], XX[TT];
   unsigned skipmask = (1u << TT) - 1u;
@@ -264,12 +265,12 @@ __device__ __forceinline__ void far_mixed_block(int64_t t_first, int64_t t_end, 
       skipmask = 0u;
 #pragma unroll
       for (int q = 0; q < TT; ++q) {
-        const int64_t t = t0 + (int64_t)q * kFarTile;
-        int sp = cursor[(2 * q + 0) * kFarTile + tid];
-        int nxt = cursor[(2 * q + 1) * kFarTile + tid];
+        const int64_t t = t0 + (int64_t)q * NT;
+        int sp = cursor[(2 * q + 0) * NT + tid];
+        int nxt = cursor[(2 * q + 1) * NT + tid];
         while (nxt < cur) nxt = skip_idx[++sp];
-        cursor[(2 * q + 0) * kFarTile + tid] = sp;
-        cursor[(2 * q + 1) * kFarTile + tid] = nxt;
+        cursor[(2 * q + 0) * NT + tid] = sp;
+        cursor[(2 * q + 1) * NT + tid] = nxt;
         if (t >= t_end || nxt == cur) skipmask |= 1u << q;
         float4 hi = make_float4(0.f, 0.f, 0.f, 0.f), lo = hi;
         if (t < t_end) {
@@ -284,20 +285,39 @@ __device__ __forceinline__ void far_mixed_block(int64_t t_first, int64_t t_end, 
     }
     const bool mine = skipmask != (1u << TT) - 1u;
     if (!__syncthreads_or(mine)) continue;
-    if (tid < tile.z) {
-      const float4 a = src32[(int64_t)(tile.y + tid) * 2 + 0];
-      const float4 b = src32[(int64_t)(tile.y + tid) * 2 + 1];
-      if (PK) {
-        const float yy = fmaf(a.z, a.z, fmaf(a.y, a.y, a.x * a.x));
-        const float dy = fmaf(b.z, a.z, fmaf(b.y, a.y, b.x * a.x));
-        sh[tid * 5 + 0] = make_float4(-2.f * a.x, -2.f * a.x, -2.f * a.y, -2.f * a.y);
-        sh[tid * 5 + 1] = make_float4(-2.f * a.z, -2.f * a.z, yy, yy);
-        sh[tid * 5 + 2] = make_float4(a.w, a.w, -dy, -dy);
-        sh[tid * 5 + 3] = make_float4(b.x, b.x, b.y, b.y);
-        sh[tid * 5 + 4] = make_float4(b.z, b.z, 0.f, 0.f);
-      } else {
-        sh[tid * 2 + 0] = a;
-        sh[tid * 2 + 1] = b;
+    if constexpr (NT == kFarTile) {
+      if (tid < tile.z) {
+        const float4 a = src32[(int64_t)(tile.y + tid) * 2 + 0];
+        const float4 b = src32[(int64_t)(tile.y + tid) * 2 + 1];
+        if (PK) {
+          const float yy = fmaf(a.z, a.z, fmaf(a.y, a.y, a.x * a.x));
+          const float dy = fmaf(b.z, a.z, fmaf(b.y, a.y, b.x * a.x));
+          sh[tid * 5 + 0] = make_float4(-2.f * a.x, -2.f * a.x, -2.f * a.y, -2.f * a.y);
+          sh[tid * 5 + 1] = make_float4(-2.f * a.z, -2.f * a.z, yy, yy);
+          sh[tid * 5 + 2] = make_float4(a.w, a.w, -dy, -dy);
+          sh[tid * 5 + 3] = make_float4(b.x, b.x, b.y, b.y);
+          sh[tid * 5 + 4] = make_float4(b.z, b.z, 0.f, 0.f);
+        } else {
+          sh[tid * 2 + 0] = a;
+          sh[tid * 2 + 1] = b;
+        }
+      }
+    } else {
+      for (int sidx = tid; sidx < tile.z; sidx += NT) {
+        const float4 a = src32[(int64_t)(tile.y + sidx) * 2 + 0];
+        const float4 b = src32[(int64_t)(tile.y + sidx) * 2 + 1];
+        if (PK) {
+          const float yy = fmaf(a.z, a.z, fmaf(a.y, a.y, a.x * a.x));
+          const float dy = fmaf(b.z, a.z, fmaf(b.y, a.y, b.x * a.x));
+          sh[sidx * 5 + 0] = make_float4(-2.f * a.x, -2.f * a.x, -2.f * a.y, -2.f * a.y);
+          sh[sidx * 5 + 1] = make_float4(-2.f * a.z, -2.f * a.z, yy, yy);
+          sh[sidx * 5 + 2] = make_float4(a.w, a.w, -dy, -dy);
+          sh[sidx * 5 + 3] = make_float4(b.x, b.x, b.y, b.y);
+          sh[sidx * 5 + 4] = make_float4(b.z, b.z, 0.f, 0.f);
+        } else {
+          sh[sidx * 2 + 0] = a;
+          sh[sidx * 2 + 1] = b;
+        }
       }
     }
     __syncthreads();
@@ -366,14 +386,14 @@ __device__ __forceinline__ void far_mixed_block(int64_t t_first, int64_t t_end, 
         if (!((skipmask >> q) & 1u)) {
           float sum, err;
           if (DO_S) {
-            two_sum_f32(acc[(4 * q + 0) * kFarTile + tid], pS[q], sum, err);
-            acc[(4 * q + 0) * kFarTile + tid] = sum;
-            acc[(4 * q + 1) * kFarTile + tid] += err;
+            two_sum_f32(acc[(4 * q + 0) * NT + tid], pS[q], sum, err);
+            acc[(4 * q + 0) * NT + tid] = sum;
+            acc[(4 * q + 1) * NT + tid] += err;
           }
           if (DO_D) {
-            two_sum_f32(acc[(4 * q + 2) * kFarTile + tid], pD[q], sum, err);
-            acc[(4 * q + 2) * kFarTile + tid] = sum;
-            acc[(4 * q + 3) * kFarTile + tid] += err;
+            two_sum_f32(acc[(4 * q + 2) * NT + tid], pD[q], sum, err);
+            acc[(4 * q + 2) * NT + tid] = sum;
+            acc[(4 * q + 3) * NT + tid] += err;
           }
         }
       }
@@ -382,12 +402,12 @@ __device__ __forceinline__ void far_mixed_block(int64_t t_first, int64_t t_end, 
   }
 #pragma unroll
   for (int q = 0; q < TT; ++q) {
-    const int64_t t = t0 + (int64_t)q * kFarTile;
+    const int64_t t = t0 + (int64_t)q * NT;
     if (t < t_end) {
       if (DO_S)
-        atomicAdd(S_out + t, ((double)acc[(4 * q + 0) * kFarTile + tid] + (double)acc[(4 * q + 1) * kFarTile + tid]) * kInv4Pi);
+        atomicAdd(S_out + t, ((double)acc[(4 * q + 0) * NT + tid] + (double)acc[(4 * q + 1) * NT + tid]) * kInv4Pi);
       if (DO_D)
-        atomicAdd(D_out + t, ((double)acc[(4 * q + 2) * kFarTile + tid] + (double)acc[(4 * q + 3) * kFarTile + tid]) * kInv4Pi);
+        atomicAdd(D_out + t, ((double)acc[(4 * q + 2) * NT + tid] + (double)acc[(4 * q + 3) * NT + tid]) * kInv4Pi);
     }
   }
   __syncthreads();   // the shared arrays are reused by the next block of a persistent CTA
@@ -410,7 +430,10 @@ __global__ void __launch_bounds__(kFarTile) far_mixed_kernel(const int4* __restr
 // Direct part of the treecode far field: one CTA per item (target group of
 // at most 256 targets [groups[g].x, groups[g].y), tile range of the group's
 // tile list).
-__global__ void __launch_bounds__(kFarTile) far_tile_items_kernel(const int4* __restrict__ items,
+// 4 targets per thread over 64 threads: a group's 256 targets in one CTA, each
+// staged source serving 4 targets per thread (the group tiles are the same)
+constexpr int kItemThreads = 64;
+__global__ void __launch_bounds__(kItemThreads) far_tile_items_kernel(const int4* __restrict__ items,
                                                                   const int2* __restrict__ groups,
                                                                   const int4* __restrict__ tiles,
                                                                   const float4* __restrict__ src32,
@@ -422,15 +445,15 @@ __global__ void __launch_bounds__(kFarTile) far_tile_items_kernel(const int4* __
                                                                   double* __restrict__ D_out) {
   const int4 w = items[blockIdx.x];
   const int2 grp = groups[w.x];
-  far_mixed_block<2, true, true, true>(grp.x, grp.y, w.y, w.z, tiles, src32, tgt32, cen32, skip_ptr, skip_idx, S_out,
-                                       D_out);
+  far_mixed_block<4, true, true, true, kItemThreads>(grp.x, grp.y, w.y, w.z, tiles, src32, tgt32, cen32, skip_ptr,
+                                                     skip_idx, S_out, D_out);
 }
 
 void launch_far_tile_items(const DevGeom& d, const int2* groups, const int4* tiles, const int4* items, int n_items,
                            double* S, double* D, cudaStream_t st) {
   if (n_items <= 0) return;
-  far_tile_items_kernel<<<n_items, kFarTile, 0, st>>>(items, groups, tiles, d.src32, d.tgt32, d.cen32, d.skip_ptr,
-                                                      d.skip_idx, S, D);
+  far_tile_items_kernel<<<n_items, kItemThreads, 0, st>>>(items, groups, tiles, d.src32, d.tgt32, d.cen32,
+                                                          d.skip_ptr, d.skip_idx, S, D);
   count_launch();
 }
 
